@@ -1,0 +1,444 @@
+"""FP64 oracle of the F-BMP method: kernel estimate (Algorithm 1) and the
+per-band HRMS solve (Algorithm 2), following the paper's steps in its order.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Image-domain loops live in ``oracle.c`` (plain C, FP64); the small n x n
+kernel-grid algebra (ADMM, Appendix A) is numpy in FP64, with numpy's FFT,
+sort and dense linear algebra used as library steps.
+
+Readings of passages the paper leaves open are marked READING; each one is
+listed in the repository's design notes.
+"""
+from __future__ import annotations
+
+import ctypes
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from ._clib import lib
+
+
+def f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------
+# Parameters (Sec. IV-F, "Parameter Setting")
+# ----------------------------------------------------------------------------
+@dataclass
+class KernelParams:
+    lambda_omega: float = 10.0
+    l: int = 2            # READING: box half-width on the LR grid; paper silent
+    alpha1: float = 1.0
+    alpha2: float = 0.006
+    mu1: float = 100.0
+    mu2: float = 100.0
+    mu3: float = 100.0
+    rho: float = 0.5
+    t_max: int = 10000
+    th: float = 1e-5
+
+
+@dataclass
+class HrmsParams:
+    lam: float = 2e-4
+    r: int = 1
+    eps: float = 1.0      # READING: never given; on the [0, 255] scale
+    tol: float = 1e-12    # relative residual of each linear solve
+    max_iter: int = 100000
+    exact_weight: bool = False   # READING: Z-step weight lam (paper) or lam|w|
+
+
+# ----------------------------------------------------------------------------
+# Image-domain operators (C)
+# ----------------------------------------------------------------------------
+def blur_decimate(z, u, c: int) -> np.ndarray:
+    """D B(u) z (Sec. II-A)."""
+    z, u = f64(z), f64(u)
+    H, W = z.shape
+    R = u.shape[0] // 2
+    out = np.empty((H // c, W // c))
+    lib().or_blur_decimate(z, H, W, u, R, c, out)
+    return out
+
+
+def blur_decimate_adj(v, u, c: int) -> np.ndarray:
+    """B(u)^T D^T v."""
+    v, u = f64(v), f64(u)
+    h, w = v.shape
+    R = u.shape[0] // 2
+    out = np.empty((h * c, w * c))
+    lib().or_blur_decimate_adj(v, h * c, w * c, u, R, c, out)
+    return out
+
+
+def laplacian(z) -> np.ndarray:
+    """L z, the 5-point Laplacian S of Eq. reg2, circular."""
+    z = f64(z)
+    out = np.empty_like(z)
+    lib().or_laplacian(z, z.shape[0], z.shape[1], out)
+    return out
+
+
+@dataclass
+class PanStats:
+    I: np.ndarray
+    mu: np.ndarray
+    var: np.ndarray
+    s: np.ndarray
+    r: int
+    eps: float
+
+
+def pan_stats(Y, r: int, eps: float) -> PanStats:
+    """I = L Y, window mean, population variance, s = 1/(var + eps)
+    (Algorithm 2 step 3; Eq. ac_h_compute)."""
+    Y = f64(Y)
+    H, W = Y.shape
+    I, mu, var, s = (np.empty_like(Y) for _ in range(4))
+    lib().or_pan_stats(Y, H, W, r, eps, I, mu, var, s)
+    return PanStats(I, mu, var, s, r, eps)
+
+
+def matting_apply(alpha, st: PanStats) -> np.ndarray:
+    """M alpha for the matting matrix of I (Eq. matting_matrix)."""
+    alpha = f64(alpha)
+    out = np.empty_like(alpha)
+    lib().or_matting_apply(alpha, st.I, st.mu, st.s, alpha.shape[0],
+                           alpha.shape[1], st.r, out)
+    return out
+
+
+def guided_filter(q, st: PanStats) -> np.ndarray:
+    """Guided filter of q with guide I (Eq. ac_h_compute): the L-hat of
+    Eq. Z_solution when q = L Z0."""
+    q = f64(q)
+    out = np.empty_like(q)
+    lib().or_guided_filter(q, st.I, st.mu, st.s, q.shape[0], q.shape[1],
+                           st.r, out)
+    return out
+
+
+def box_filter(a, half: int) -> np.ndarray:
+    """Unit-gain (2 half + 1)^2 box, circular (u1, u2 of Eq. objective3)."""
+    a = f64(a)
+    out = np.empty_like(a)
+    lib().or_box_filter(a, a.shape[0], a.shape[1], half, out)
+    return out
+
+
+_ZERO = np.zeros(1)
+
+
+def apply_z0_system(z, u, c: int, st: PanStats, lam: float) -> np.ndarray:
+    """(B^T D^T D B + lam L^T M L) z (Eq. Z_ini_matting)."""
+    z, u = f64(z), f64(u)
+    out = np.empty_like(z)
+    lib().or_apply_system(z.shape[0], z.shape[1], c, u, u.shape[0] // 2,
+                          st.I, st.mu, st.s, st.r, lam, 0, z, out)
+    return out
+
+
+def apply_zstep_system(z, u, c: int, lam: float) -> np.ndarray:
+    """(B^T D^T D B + lam L^T L) z (Eq. Z_solution)."""
+    z, u = f64(z), f64(u)
+    out = np.empty_like(z)
+    lib().or_apply_system(z.shape[0], z.shape[1], c, u, u.shape[0] // 2,
+                          _ZERO, _ZERO, _ZERO, 0, lam, 1, z, out)
+    return out
+
+
+def cg_solve(op: int, b, u, c: int, lam: float, st: PanStats | None,
+             x0=None, tol: float = 1e-12, max_iter: int = 100000):
+    """CG on the Z0 system (op 0) or the Z-step system (op 1).
+    Returns (x, iterations, true relative residual)."""
+    b, u = f64(b), f64(u)
+    H, W = b.shape
+    x = np.zeros_like(b) if x0 is None else f64(x0).copy()
+    rel = ctypes.c_double(0.0)
+    if st is None:
+        I = mu = s = _ZERO
+        r = 0
+    else:
+        I, mu, s, r = st.I, st.mu, st.s, st.r
+    it = lib().or_cg(H, W, c, u, u.shape[0] // 2, I, mu, s, r, lam, op, b, x,
+                     tol, max_iter, ctypes.byref(rel))
+    return x, it, rel.value
+
+
+def kernel_normal_eq(Y, f, c: int, R: int):
+    """E^T E and E^T f with E = D C(Y) (Eq. z_update, Eq. z_solution)."""
+    Y, f = f64(Y), f64(f)
+    H, W = Y.shape
+    nn = (2 * R + 1) ** 2
+    EtE = np.empty((nn, nn))
+    Etf = np.empty(nn)
+    lib().or_kernel_normal_eq(Y, H, W, c, R, f, EtE, Etf)
+    return EtE, Etf
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 2: the per-band HRMS solve
+# ----------------------------------------------------------------------------
+def solve_band(x_lr, u, c: int, st: PanStats, p: HrmsParams, z_init=None):
+    """One band of Algorithm 2: Z0 (Eq. Z_ini_matting, by CG), then the
+    A, C step (Eq. ac_h_compute) as a guided filter, then the Z step
+    (Eq. Z_solution), solved exactly (CG to tolerance p.tol)."""
+    b = blur_decimate_adj(x_lr, u, c)
+    z0, it0, rel0 = cg_solve(0, b, u, c, p.lam, st, z_init, p.tol, p.max_iter)
+    lhat = guided_filter(laplacian(z0), st)
+    lam_z = p.lam * ((2 * p.r + 1) ** 2 if p.exact_weight else 1.0)
+    rhs = b + lam_z * laplacian(lhat)
+    z, it1, rel1 = cg_solve(1, rhs, u, c, lam_z, None, z0, p.tol, p.max_iter)
+    return {"Z": z, "Z0": z0, "iters_z0": it0, "relres_z0": rel0,
+            "iters_z": it1, "relres_z": rel1, "b": b, "lhat": lhat}
+
+
+def solve_hrms(X, Y, u, c: int, p: HrmsParams | None = None,
+               threads: int = 1, z_init=None):
+    """Algorithm 2 over all bands ("for i = 1..N, do in parallel"), with the
+    bands spread over ``threads`` host threads. Returns the per-band dicts and
+    the stacked Z, Z0."""
+    p = p or HrmsParams()
+    X = f64(X)
+    st = pan_stats(Y, p.r, p.eps)
+    N = X.shape[0]
+
+    def one(b):
+        zi = None if z_init is None else z_init[b]
+        return solve_band(X[b], u, c, st, p, zi)
+
+    if threads > 1:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            out = list(ex.map(one, range(N)))
+    else:
+        out = [one(b) for b in range(N)]
+    return {"Z": np.stack([o["Z"] for o in out]),
+            "Z0": np.stack([o["Z0"] for o in out]),
+            "bands": out, "stats": st}
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 1: blur kernel estimation
+# ----------------------------------------------------------------------------
+def estimate_omega(X, Y, c: int, l: int, lam_omega: float, bands=None):
+    """Spectral weights (Eq. objective3): least squares of
+    B(u1) X' omega against D B(u2) Y plus (lam_omega/2)||G omega||^2, G the
+    first differences of consecutive weights, by its normal equations.
+    READING: u1 is the (2l+1)^2 unit box on the LR grid and u2 the
+    (2cl+1)^2 unit box on the HR grid (the same physical half-width)."""
+    X = f64(X)
+    if bands is not None:
+        X = X[list(bands)]
+    Np = X.shape[0]
+    A = np.stack([box_filter(X[k], l).ravel() for k in range(Np)], axis=1)
+    bvec = box_filter(Y, c * l)[::c, ::c].ravel()
+    G = np.zeros((max(Np - 1, 0), Np))
+    for k in range(Np - 1):
+        G[k, k], G[k, k + 1] = -1.0, 1.0
+    lhs = A.T @ A + lam_omega * (G.T @ G)
+    return np.linalg.solve(lhs, A.T @ bvec)
+
+
+def simplex_project(v) -> np.ndarray:
+    """Euclidean projection onto {s >= 0, sum s = 1} (Eq. simplex), by the
+    sort-based method of Wang and Carreira-Perpinan (2013)."""
+    v = f64(v).ravel()
+    srt = np.sort(v)[::-1]
+    css = np.cumsum(srt)
+    j = np.arange(1, v.size + 1)
+    rho = np.nonzero(srt + (1.0 - css) / j > 0)[0][-1] + 1
+    tau = (1.0 - css[rho - 1]) / rho
+    return np.maximum(v + tau, 0.0)
+
+
+def shrink2(e, t: float) -> np.ndarray:
+    """Row-wise group soft threshold, rows along axis 0 (Eq. x_update):
+    max(||e|| - t, 0) e / ||e||."""
+    nrm = np.sqrt(np.sum(e * e, axis=0))
+    scale = np.where(nrm > t, (nrm - t) / np.where(nrm > 0, nrm, 1.0), 0.0)
+    return e * scale
+
+
+# Circular forward differences on the n x n kernel grid (READING: circular,
+# as the FFT diagonalisation of Appendix A requires):
+#   (Dh u)(i, j) = u(i, j+1) - u(i, j),  (Dv u)(i, j) = u(i+1, j) - u(i, j).
+def Dh(a):
+    return np.roll(a, -1, axis=1) - a
+
+
+def Dv(a):
+    return np.roll(a, -1, axis=0) - a
+
+
+def DhT(a):
+    return np.roll(a, 1, axis=1) - a
+
+
+def DvT(a):
+    return np.roll(a, 1, axis=0) - a
+
+
+def grad(u):
+    """nabla u = [Dh u, Dv u] (Eq. reg1)."""
+    return np.stack([Dh(u), Dv(u)])
+
+
+def sym_grad(p1, p2):
+    """E(p) = [Dh p1, (Dv p1 + Dh p2)/2, (Dv p1 + Dh p2)/2, Dv p2] (Eq. reg1)."""
+    m = 0.5 * (Dv(p1) + Dh(p2))
+    return np.stack([Dh(p1), m, m, Dv(p2)])
+
+
+def det3(a):
+    """|.| of Appendix A, elementwise over frequencies."""
+    return (a[0][0] * a[1][1] * a[2][2] + a[0][1] * a[1][2] * a[2][0]
+            + a[0][2] * a[1][0] * a[2][1] - a[0][2] * a[1][1] * a[2][0]
+            - a[0][1] * a[1][0] * a[2][2] - a[0][0] * a[2][1] * a[1][2])
+
+
+def up_system_symbols(n: int, kp: KernelParams):
+    """Fourier symbols of the {u, p} block system (Eq. block_toeplitz), with
+    the mu3 coupling to z added to d1 (READING: the {u,p} argmin of
+    Eq. subproblems omits the (mu3/2)||z - u - Lambda3||^2 term; without it
+    d1 vanishes at DC and u is undetermined)."""
+    k = np.arange(n)
+    dh = (np.exp(2j * np.pi * k / n) - 1.0)[None, :] * np.ones((n, 1))
+    dv = (np.exp(2j * np.pi * k / n) - 1.0)[:, None] * np.ones((1, n))
+    a1, a2 = kp.alpha1 * kp.mu1, kp.alpha2 * kp.mu2
+    d1 = a1 * (np.abs(dh) ** 2 + np.abs(dv) ** 2) + kp.mu3
+    d2 = a1 + a2 * np.abs(dh) ** 2 + 0.5 * a2 * np.abs(dv) ** 2
+    d3 = a1 + a2 * np.abs(dv) ** 2 + 0.5 * a2 * np.abs(dh) ** 2
+    d4 = -a1 * dh
+    d5 = -a1 * dv
+    d6 = 0.5 * a2 * np.conj(dh) * dv
+    return [[d1 + 0j, np.conj(d4), np.conj(d5)],
+            [d4, d2 + 0j, np.conj(d6)],
+            [d5, d6, d3 + 0j]]
+
+
+def up_rhs(x, y, z, L1, L2, L3, kp: KernelParams):
+    """B1, B2, B3 of Appendix A (with + mu3 (z - Lambda3) in B1). The two
+    middle columns of y and Lambda2 enter through their mean, which equals
+    either one when they agree."""
+    a1, a2 = kp.alpha1 * kp.mu1, kp.alpha2 * kp.mu2
+    q = y - L2
+    q23 = 0.5 * (q[1] + q[2])
+    B1 = a1 * (DhT(x[0] - L1[0]) + DvT(x[1] - L1[1])) + kp.mu3 * (z - L3)
+    B2 = a1 * (L1[0] - x[0]) + a2 * (DhT(q[0]) + DvT(q23))
+    B3 = a1 * (L1[1] - x[1]) + a2 * (DvT(q[3]) + DhT(q23))
+    return B1, B2, B3
+
+
+def up_solve(x, y, z, L1, L2, L3, kp: KernelParams):
+    """{u, p} subproblem by FFT and Cramer's rule (Eq. u_p_solution)."""
+    n = z.shape[0]
+    S = up_system_symbols(n, kp)
+    Bh = [np.fft.fft2(B) for B in up_rhs(x, y, z, L1, L2, L3, kp)]
+    den = det3(S)
+    out = []
+    for col in range(3):
+        M = [[Bh[row] if j == col else S[row][j] for j in range(3)]
+             for row in range(3)]
+        out.append(np.real(np.fft.ifft2(det3(M) / den)))
+    return out  # u, p1, p2
+
+
+@dataclass
+class AdmmResult:
+    kernel: np.ndarray          # z at exit, in the simplex
+    u: np.ndarray
+    iters: int
+    converged: bool
+    primal: dict = field(default_factory=dict)
+
+
+def admm(EtE, Etf, R: int, kp: KernelParams | None = None) -> AdmmResult:
+    """Algorithm 1's loop (Eq. subproblems, generalized ADMM).
+    READING (init, paper silent): u0 = z0 = 1/n^2, p, x, y, Lambdas = 0.
+    READING (order): the {u,p} step uses the x, y, z just computed.
+    READING (output): the kernel returned is z, which lies in the simplex."""
+    kp = kp or KernelParams()
+    n = 2 * R + 1
+    nn = n * n
+    Q = np.linalg.inv(f64(EtE) + kp.mu3 * np.eye(nn))
+    Etf = f64(Etf)
+    u = np.full((n, n), 1.0 / nn)
+    z = u.copy()
+    p1 = np.zeros((n, n))
+    p2 = np.zeros((n, n))
+    x = np.zeros((2, n, n))
+    y = np.zeros((4, n, n))
+    L1 = np.zeros((2, n, n))
+    L2 = np.zeros((4, n, n))
+    L3 = np.zeros((n, n))
+    it, conv = 0, False
+    for t in range(kp.t_max):
+        x = shrink2(grad(u) - np.stack([p1, p2]) + L1, 1.0 / kp.mu1)
+        y = shrink2(sym_grad(p1, p2) + L2, 1.0 / kp.mu2)
+        z = simplex_project(Q @ (Etf + kp.mu3 * (u + L3).ravel())).reshape(n, n)
+        u_new, p1, p2 = up_solve(x, y, z, L1, L2, L3, kp)
+        L1 = L1 + kp.rho * (grad(u_new) - np.stack([p1, p2]) - x)
+        L2 = L2 + kp.rho * (sym_grad(p1, p2) - y)
+        L3 = L3 + kp.rho * (u_new - z)
+        change = np.linalg.norm(u - u_new) / np.linalg.norm(u_new)
+        u = u_new
+        it = t + 1
+        if change < kp.th:
+            conv = True
+            break
+    primal = {
+        "x": float(np.linalg.norm(grad(u) - np.stack([p1, p2]) - x)),
+        "y": float(np.linalg.norm(sym_grad(p1, p2) - y)),
+        "z": float(np.linalg.norm(u - z)),
+    }
+    return AdmmResult(z, u, it, conv, primal)
+
+
+def estimate_kernel(X, Y, c: int, R: int, kp: KernelParams | None = None,
+                    omega=None, bands=None):
+    """Algorithm 1: omega (Eq. objective3) unless given, then E^T E, E^T f
+    and the ADMM loop. Returns (kernel n x n, omega, AdmmResult)."""
+    kp = kp or KernelParams()
+    X = f64(X)
+    Xp = X if bands is None else X[list(bands)]
+    if omega is None:
+        omega = estimate_omega(Xp, Y, c, kp.l, kp.lambda_omega)
+    f = np.tensordot(f64(omega), Xp, axes=1)
+    EtE, Etf = kernel_normal_eq(Y, f, c, R)
+    res = admm(EtE, Etf, R, kp)
+    return res.kernel, f64(omega), res
+
+
+def pansharpen(X, Y, c: int, R: int, kp: KernelParams | None = None,
+               hp: HrmsParams | None = None, threads: int = 1, omega=None):
+    """The two-stage scheme (Sec. III-C): Algorithm 1 once, then
+    Algorithm 2 once, no outer loop."""
+    kernel, omega, res = estimate_kernel(X, Y, c, R, kp, omega)
+    out = solve_hrms(X, Y, kernel, c, hp, threads)
+    out.update({"kernel": kernel, "omega": omega, "admm": res})
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Metrics used for reporting (Eq. psnr_def, Eq. relative_error_kernel)
+# ----------------------------------------------------------------------------
+def rel_l2(a, b) -> float:
+    a, b = f64(a), f64(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def psnr(est, ref, border: int = 0) -> float:
+    est, ref = f64(est), f64(ref)
+    if border:
+        est = est[..., border:-border, border:-border]
+        ref = ref[..., border:-border, border:-border]
+    mse = np.mean((est - ref) ** 2)
+    return float(20.0 * np.log10(255.0 / np.sqrt(mse)))
+
+
+def kernel_error_pct(est, ref) -> float:
+    return 100.0 * rel_l2(est, ref)
