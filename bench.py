@@ -1,0 +1,406 @@
+"""Benchmark of the F-BMP hot path on GB300.
+
+One step = one ps_pansharpen call (Algorithm 1 then Algorithm 2) on one
+seeded synthetic scene shaped like the paper's 8-band, ratio-4 workload:
+8 x 1024 x 1024 HRMS, LRMS 8 x 256 x 256, 17 x 17 kernel, window radius 1.
+Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank solves its own scene (scenes are independent
+units: weak scaling, no collective on the data path); the step time is the
+max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HRMS Mpix·band/s at rel-L2≤1e-3 vs FP64 oracle; % of HBM peak (ncu)"
+UNIT = "Mpix·band/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_config(r: int = 1):
+    import synth
+    from dataclasses import replace
+    return replace(synth.CONFIGS["c1"], r=r)
+
+
+def workload_name(cfg) -> str:
+    return (f"c1: {cfg.bands} bands x {cfg.H}x{cfg.W} HRMS, LRMS {cfg.bands}x{cfg.h}x{cfg.w}, "
+            f"ratio {cfg.ratio}, {cfg.n}x{cfg.n} kernel estimated, LLP window radius {cfg.r}; "
+            "seeded synthetic scene (shapes + texture, Dirichlet PAN weights, anisotropic "
+            "shifted Gaussian blur, noise 0.005)")
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers
+# ---------------------------------------------------------------------------
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def init_dist(world: int, backend: str):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+
+
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max over ranks (timing only; no data-path collective)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def throughput(units_per_rank: float, world: int, seconds_per_step: float) -> float:
+    """Whole-job Mpix.band/s: every rank processes units_per_rank pixel-bands."""
+    return world * units_per_rank / 1e6 / seconds_per_step
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded crop
+# ---------------------------------------------------------------------------
+def oracle_step(sc_crop, threads: int) -> float:
+    import oracle
+    cfg = sc_crop["config"]
+    t0 = time.perf_counter()
+    oracle.pansharpen(sc_crop["lrms"], sc_crop["pan"], cfg.ratio, cfg.R,
+                      hp=oracle.HrmsParams(r=cfg.r), threads=threads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(scene, crop: int, reps: int = 1) -> dict:
+    import synth
+    sc = synth.crop_scene(scene, crop)
+    cfg = sc["config"]
+    threads = min(os.cpu_count() or 1, cfg.bands)
+    secs = [oracle_step(sc, threads) for _ in range(reps)]
+    t = float(np.mean(secs))
+    return {"value": cfg.bands * crop * crop / 1e6 / t, "unit": UNIT, "cores": threads,
+            "kind": "oracle",
+            "sample": f"{crop}x{crop} crop of the workload scene (all {cfg.bands} bands, same "
+                      f"kernel size and ratio) solved as its own periodic scene by the FP64 "
+                      f"oracle (C + numpy, bands on {threads} threads, CG to 1e-12), "
+                      f"{reps} run(s), {t:.1f} s each",
+            "host_cores": os.cpu_count()}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle timed on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    cfg = workload_config(args.r)
+    scene = synth.make_scene(cfg)
+    crop = args.ref_crop
+    sc = synth.crop_scene(scene, crop)
+    threads = min(os.cpu_count() or 1, cfg.bands)
+    for _ in range(args.warmup):
+        oracle_step(sc, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(sc, threads)
+    t = (time.perf_counter() - t0) / args.steps
+    value = cfg.bands * crop * crop / 1e6 / t
+    rec = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(cfg), "sample_crop": crop},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"each step: {crop}x{crop} crop of the workload scene, "
+                                   f"all {cfg.bands} bands, FP64 oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(rec), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def cg_iteration_roofline(api, X, Y, kern, cfg, hp, peak_gbs, dev):
+    """Average duration of one CG iteration (db + llp + cg_update + control),
+    from two solves that run a fixed number of iterations (tolerance out of
+    reach), timed with CUDA events on the launching stream."""
+    import ctypes
+    import torch
+    from paper_2103_09943_gb300._lib import HrmsParams
+    ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev)
+    out = torch.empty((cfg.bands, cfg.H, cfg.W), dtype=torch.float32, device=dev)
+
+    def timed(iters, reps=3):
+        p = HrmsParams.from_buffer_copy(hp)
+        p.tol = 1e-30
+        p.max_iter = iters
+        api.solve_hrms(X, Y, kern, cfg.ratio, p, ws=ws, info=False, out=out)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            api.solve_hrms(X, Y, kern, cfg.ratio, p, ws=ws, info=False, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts)
+
+    lo, hi = 20, 220
+    t_lo, t_hi = timed(lo), timed(hi)
+    per_iter_ms = (t_hi - t_lo) / (hi - lo)
+    per_unit = 40.0 + 12.0 / cfg.bands          # algorithmic bytes per px.band per iteration
+    units = cfg.bands * cfg.H * cfg.W
+    achieved = per_unit * units / (per_iter_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+            "frac": achieved / peak_gbs, "traffic": None,
+            "kernel": "CG iteration of Eq. Z_ini_matting (db_kernel + llp_kernel + "
+                      "cg_update_kernel + cg_control_kernel)",
+            "bytes_per_unit": per_unit, "units_per_launch": units,
+            "ms_per_iteration": per_iter_ms, "peak_note": "of measured (MEASURED_PEAKS.json "
+                                                          "hbm_gbs)"}
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_gpu(args):
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    init_dist(world, "nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2103_09943_gb300 import api
+
+    cfg = workload_config(args.r)
+    scene = synth.make_scene(cfg, seed=cfg.seed + rank)   # one independent scene per rank
+    X = torch.from_numpy(scene["lrms"]).to(dev)
+    Y = torch.from_numpy(scene["pan"]).to(dev)
+    kp = api.default_kernel_params()
+    hp = api.default_hrms_params()
+    ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev)
+    Z = torch.empty((cfg.bands, cfg.H, cfg.W), dtype=torch.float32, device=dev)
+    K = torch.empty((cfg.n, cfg.n), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(info=False):
+        return api.pansharpen(X, Y, cfg.ratio, cfg.R, kp, hp, ws=ws, info=info, out=Z,
+                              kernel_out=K)
+
+    _, _, kinfo, binfo = step(info=True)
+    for _ in range(max(args.warmup - 1, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))                         # L2 flush between timed steps
+        ev[k][0].record()
+        step()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(world)
+    clk = clocks.stop()
+    step_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    step_ms = reduce_max(step_ms, world, dev)
+    units = cfg.bands * cfg.H * cfg.W
+    value = throughput(units, world, step_ms * 1e-3)
+
+    # end to end: host buffers through the C-ABI, copies inside the timed region
+    pipe = api.HostPipeline(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, kp, hp, dev)
+    hx = torch.from_numpy(scene["lrms"]).pin_memory()
+    hy = torch.from_numpy(scene["pan"]).pin_memory()
+    for _ in range(max(args.warmup, 1)):
+        pipe(hx, hy)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        pipe(hx, hy)
+        b.record()
+        b.synchronize()                               # the host has the result
+        e2e.append(a.elapsed_time(b))
+    e2e_ms = reduce_max(float(np.mean(e2e)), world, dev)
+
+    # launches of our kernels per step
+    body_runs = max(1, math.ceil(max(binfo.iters) / 2))
+    launches_per_step = 12 + 4 + 8 * body_runs + 14
+
+    peak, peak_kind = read_peaks()
+    roof = cg_iteration_roofline(api, X, Y, K, cfg, hp, peak, dev)
+    roof["peak_note"] = f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)" \
+        if peak_kind == "measured" else "of fallback (6.8 TB/s)"
+
+    # accuracy of the timed configuration: the FP64 oracle's operator on the
+    # GPU's Z0 (true relative residual), two bands
+    acc = None
+    if rank == 0:
+        import oracle
+        _, Z0, _ = api.solve_hrms(X, Y, K, cfg.ratio, hp, want_z0=True, ws=ws)
+        z0 = Z0.cpu().numpy().astype(np.float64)
+        k64 = K.cpu().numpy().astype(np.float64)
+        st = oracle.pan_stats(scene["pan"], hp.r, hp.eps)
+        res = []
+        for b in (0, cfg.bands - 1):
+            rhs = oracle.blur_decimate_adj(scene["lrms"][b], k64, cfg.ratio)
+            rr = rhs - oracle.apply_z0_system(z0[b], k64, cfg.ratio, st, hp.lambda_)
+            res.append(float(np.linalg.norm(rr) / np.linalg.norm(rhs)))
+        acc = {"cg_tol": hp.tol, "z0_true_rel_residual_fp64": res,
+               "parity": "tests/test_gpu_*.py: per-band rel-L2 vs the FP64 oracle"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(scene, args.cpu_crop)
+
+    if rank == 0:
+        rec = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(cfg), "scenes_per_rank": 1,
+                       "parallelism": f"replicas x{world} (independent scenes)",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "cg_tol": hp.tol, "cg_iters": binfo.iters,
+                       "admm_iters": kinfo.iters},
+            "wall_s_timed_region": wall,
+            "e2e": {"value": throughput(units, world, e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": pipe.h2d_bytes, "d2h_bytes_per_step": pipe.d2h_bytes,
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "accuracy": acc,
+            "clocks": clk,
+        }
+        print(json.dumps(rec), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--r", type=int, default=1)
+    ap.add_argument("--cpu-crop", type=int, default=256)
+    ap.add_argument("--ref-crop", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

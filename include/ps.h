@@ -1,0 +1,164 @@
+/*
+ * ps.h -- C-ABI of the GB300 (sm_103a) F-BMP blind pansharpening library.
+ *
+ * Method: L. Yu, D. Liu, H. Mansour, P. T. Boufounos, "Fast and High-Quality
+ * Blind Multi-Spectral Image Pansharpening", arXiv 2103.09943.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Images are float32, row-major, band-planar: the LRMS X is N x h x w, the
+ *   PAN Y and every HRMS band are H x W, with H = c h and W = c w for the
+ *   resolution ratio c >= 2 (Sec. II-A, "Notation").
+ * - The blur kernel u is n x n float32, n = 2R + 1; tap (i, j) in [-R, R]^2
+ *   is stored at u[(i + R) n + (j + R)]. B(u) is circular convolution,
+ *   (B(u) z)(y, x) = sum_{i,j} u(i, j) z(y - i, x - j) with indices modulo
+ *   H and W (Sec. II-A); D keeps the samples (c k, c l).
+ * - All image, kernel and workspace pointers are DEVICE pointers owned by the
+ *   caller; host pointers are marked h_. The library allocates nothing: the
+ *   scratch it needs lives in a caller-provided workspace (d_ws, ws_bytes),
+ *   256-byte aligned, sized by the matching *_workspace_size call.
+ * - Calls are stream-ordered on `stream` (a cudaStream_t passed as void*;
+ *   NULL is the legacy default stream). Argument and shape errors are
+ *   detected on the host and returned before anything is launched. A call
+ *   given a non-NULL h_info blocks until its work on `stream` has finished
+ *   and then fills h_info; with h_info == NULL the call returns as soon as
+ *   its work is enqueued.
+ * - Intensities are expected on the [0, 255] scale: the paper states its
+ *   images on that scale (Sec. IV-C) and its parameter values assume it.
+ * - No C++ exception crosses this interface. Not thread-safe for concurrent
+ *   calls that share one workspace.
+ */
+#ifndef PS_H
+#define PS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ps_status {
+    PS_OK = 0,
+    PS_ERR_INVALID_ARG = 1,   /* NULL pointer, bad parameter value          */
+    PS_ERR_SHAPE = 2,         /* H != c h, kernel larger than the LR grid... */
+    PS_ERR_CUDA = 3,          /* a CUDA runtime call failed                  */
+    PS_ERR_WORKSPACE = 4,     /* workspace too small or not 256-B aligned    */
+    PS_ERR_NOT_CONVERGED = 5, /* iteration cap reached; result still written */
+    PS_ERR_NONFINITE = 6,     /* NaN or Inf met in a reduction               */
+    PS_ERR_BREAKDOWN = 7,     /* CG met p^T A p <= 0                         */
+    PS_ERR_UNSUPPORTED = 8    /* size outside what the kernels support       */
+} ps_status;
+
+/* Parameters of Algorithm 1 (blur kernel estimation). Defaults
+ * (ps_default_kernel_params) are the values of Sec. IV-F. */
+typedef struct ps_kernel_params {
+    float lambda_omega; /* weight of ||G omega||^2 in Eq. objective3 (10)     */
+    int l;              /* half-width of the LR box u1 of Eq. objective3;
+                           the HR box u2 has half-width c*l. Not given by the
+                           paper; default 2                                   */
+    float alpha1;       /* TGV^2 weight of ||grad u - p||_{2,1}, Eq. reg1 (1) */
+    float alpha2;       /* TGV^2 weight of ||E(p)||_{2,1}, Eq. reg1 (0.006)   */
+    float mu1, mu2, mu3;/* penalties of Eq. Lagrangian (100 each)             */
+    float rho;          /* multiplier step of Eq. subproblems (0.5)           */
+    int t_max;          /* iteration cap of Algorithm 1 (10000)               */
+    float th;           /* stop when ||u^t - u^{t+1}|| / ||u^{t+1}|| < th (1e-5) */
+} ps_kernel_params;
+
+/* Parameters of Algorithm 2 (per-band HRMS solve). */
+typedef struct ps_hrms_params {
+    float lambda;       /* LLP weight of Eq. pansharp (2e-4, Sec. IV-F)        */
+    int r;              /* window radius of Eq. reg2, windows (2r+1)^2 (1)     */
+    float eps;          /* epsilon of Eq. reg2; not given by the paper;
+                           default 1.0 on the [0, 255] scale                   */
+    float tol;          /* CG for Eq. Z_ini_matting stops when the recursive
+                           residual ||b - A z|| / ||b|| <= tol (default 1e-6) */
+    int max_iter;       /* CG iteration cap (default 5000)                     */
+    int exact_weight;   /* 0: the Z step of Eq. Z_solution uses lambda as
+                           printed; 1: lambda (2r+1)^2, the exact minimiser of
+                           Eq. pansharp for fixed A, C                         */
+} ps_hrms_params;
+
+/* Per-band result of the Z0 conjugate-gradient solve. */
+typedef struct ps_band_info {
+    int status;          /* PS_OK, PS_ERR_NOT_CONVERGED, _NONFINITE, _BREAKDOWN */
+    int iters;           /* CG iterations taken                                */
+    double rel_residual; /* final recursive ||r|| / ||b||                      */
+} ps_band_info;
+
+/* Result of the kernel estimate. */
+typedef struct ps_kernel_info {
+    int status;          /* PS_OK or PS_ERR_NOT_CONVERGED                      */
+    int iters;           /* ADMM iterations taken                              */
+    double last_change;  /* ||u^t - u^{t+1}|| / ||u^{t+1}|| at exit            */
+} ps_kernel_info;
+
+void ps_default_kernel_params(ps_kernel_params *h_params);
+void ps_default_hrms_params(ps_hrms_params *h_params);
+const char *ps_status_string(int status);
+
+/* Workspace bytes needed by ps_pansharpen (covers ps_estimate_kernel and
+ * ps_solve_hrms for the same sizes). 0 when a size is invalid. */
+size_t ps_workspace_size(int N, int H, int W, int ratio, int R,
+                         const ps_hrms_params *h_hrms);
+
+/*
+ * Algorithm 1 (Sec. III-A): blur kernel estimation.
+ *   omega: spectral weights of Eq. objective3, in closed form, unless
+ *          d_omega_in is non-NULL (N floats, used as given);
+ *   E^T E, E^T f of Eq. z_solution with E = D C(Y), f = X omega, accumulated
+ *          in FP64, and the Cholesky factor of E^T E + mu3 I;
+ *   the generalized ADMM of Eq. subproblems until
+ *          ||u^t - u^{t+1}|| / ||u^{t+1}|| < th or t_max iterations.
+ * All N bands are taken as the X' of Eq. objective1.
+ * Out: d_kernel (n x n, in the simplex of Eq. simplex), d_omega_out (N floats,
+ * may be NULL).
+ */
+ps_status ps_estimate_kernel(const float *d_lrms, const float *d_pan, int N,
+                             int H, int W, int ratio, int R,
+                             const ps_kernel_params *h_params,
+                             const float *d_omega_in, float *d_kernel,
+                             float *d_omega_out, ps_kernel_info *h_info,
+                             void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * Algorithm 2 (Sec. III-B): the HRMS image given the kernel, all bands in
+ * one batch. Per band i:
+ *   Z0_i solves (B^T D^T D B + lambda L^T M L) Z0_i = B^T D^T X_i
+ *        (Eq. Z_ini_matting) by conjugate gradients, M the matting matrix of
+ *        L Y (Eq. matting_matrix, denominator sigma^2 + eps), applied without
+ *        forming it; FP32 vectors, FP64 inner products;
+ *   A_i, C_i by the guided filter of Eq. ac_h_compute, giving L-hat;
+ *   Z_i solves (B^T D^T D B + lambda' L^T L) Z_i = B^T D^T X_i + lambda' L L-hat
+ *        (Eq. Z_solution) exactly, by FFT and a per-alias-group rank-one
+ *        solve (lambda' = lambda, or lambda (2r+1)^2 with exact_weight).
+ * d_z_init: N x H x W warm start for the CG, or NULL for zeros.
+ * Out: d_hrms (N x H x W); d_z0 (N x H x W, may be NULL) receives Z0.
+ * h_info: N entries or NULL.
+ * Sizes: H and W must factor as 2^a 3^b (FFT), W a multiple of 4, and
+ * H, W <= 16384.
+ */
+ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan,
+                        const float *d_kernel, int N, int H, int W, int ratio,
+                        int R, const ps_hrms_params *h_params,
+                        const float *d_z_init, float *d_hrms, float *d_z0,
+                        ps_band_info *h_info, void *d_ws, size_t ws_bytes,
+                        void *stream);
+
+/*
+ * The two-stage scheme of Sec. III-C: ps_estimate_kernel, then
+ * ps_solve_hrms with the estimated kernel, no outer loop.
+ * d_kernel_out (n x n, may be NULL) receives the estimated kernel.
+ */
+ps_status ps_pansharpen(const float *d_lrms, const float *d_pan, int N, int H,
+                        int W, int ratio, int R,
+                        const ps_kernel_params *h_kparams,
+                        const ps_hrms_params *h_hparams, float *d_hrms,
+                        float *d_kernel_out, ps_kernel_info *h_kinfo,
+                        ps_band_info *h_binfo, void *d_ws, size_t ws_bytes,
+                        void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PS_H */

@@ -1,0 +1,102 @@
+/*
+ * ps_ops.h -- operator-level C-ABI of the F-BMP library: each step of the
+ * hot path on its own, on device pointers, for callers that compose the
+ * method themselves and for step-by-step parity checks.
+ *
+ * Conventions are those of ps.h (layouts, kernel storage, ownership, stream
+ * order, host-side argument checks, [0, 255] scale). Band-batched operators
+ * take N bands stored back to back (N x H x W or N x h x w).
+ */
+#ifndef PS_OPS_H
+#define PS_OPS_H
+
+#include <stddef.h>
+
+#include "ps.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* v_b = D B(u) z_b for every band b (Sec. II-A, Eq. objective0).
+ * d_z: N x H x W, d_v: N x (H/c) x (W/c). */
+ps_status ps_op_blur_decimate(const float *d_z, int N, int H, int W,
+                              int ratio, const float *d_kernel, int R,
+                              float *d_v, void *stream);
+
+/* z_b = B(u)^T D^T v_b (the adjoint of the above; with v = X it is the
+ * right-hand side of Eq. Z_ini_matting). d_v: N x h x w, d_z: N x H x W. */
+ps_status ps_op_blur_decimate_adj(const float *d_v, int N, int H, int W,
+                                  int ratio, const float *d_kernel, int R,
+                                  float *d_z, void *stream);
+
+/* PAN window statistics (Algorithm 2, step 3): I = L Y with L the 5-point
+ * Laplacian of Eq. reg2; per (2r+1)^2 torus window centred at each pixel,
+ * mu = mean of I and s = 1 / (var + eps), var the population variance,
+ * accumulated in FP64. All outputs H x W float32. */
+ps_status ps_op_pan_stats(const float *d_pan, int H, int W, int r, float eps,
+                          float *d_I, float *d_mu, float *d_s, void *stream);
+
+/* out_b = (B^T D^T D B + lambda L^T M L) z_b, the operator of
+ * Eq. Z_ini_matting, with M the matting matrix of I (Eq. matting_matrix,
+ * denominator sigma^2 + eps) applied matrix-free from (I, mu, s).
+ * Workspace: ps_op_workspace_size(N, H, W, ratio). */
+ps_status ps_op_apply_z0(const float *d_z, int N, int H, int W, int ratio,
+                         const float *d_kernel, int R, const float *d_I,
+                         const float *d_mu, const float *d_s, int r,
+                         float lambda, float *d_out, void *d_ws,
+                         size_t ws_bytes, void *stream);
+
+/* Guided filter of q_b with guide I (Eq. ac_h_compute): per window
+ * a = (mean(I q) - mu mean(q)) s, c = mean(q) - a mu; out = mean(a) I +
+ * mean(c), means over the windows containing each pixel. N x H x W. */
+ps_status ps_op_guided_filter(const float *d_q, int N, int H, int W,
+                              const float *d_I, const float *d_mu,
+                              const float *d_s, int r, float *d_out,
+                              void *stream);
+
+/* Z step of Algorithm 2 (Eq. Z_solution) for every band, given Z0:
+ * L-hat = guided filter of L Z0_b, then Z_b solves
+ * (B^T D^T D B + lambda' L^T L) Z_b = B^T D^T X_b + lambda' L L-hat exactly
+ * (FFT, per-alias-group rank-one solve). lambda' = lambda, or
+ * lambda (2r+1)^2 when exact_weight. Workspace: ps_op_workspace_size. */
+ps_status ps_op_zstep(const float *d_lrms, const float *d_z0, int N, int H,
+                      int W, int ratio, const float *d_kernel, int R,
+                      const float *d_I, const float *d_mu, const float *d_s,
+                      int r, float lambda, int exact_weight, float *d_z,
+                      void *d_ws, size_t ws_bytes, void *stream);
+
+/* Spectral weights of Eq. objective3 in closed form: the normal equations
+ * of || B(u1) X omega - D B(u2) Y ||^2 + lambda_omega ||G omega||^2,
+ * accumulated in FP64; u1 the (2l+1)^2 unit box on the LR grid, u2 the
+ * (2cl+1)^2 unit box on the HR grid, G first differences. Out: d_omega (N). */
+ps_status ps_op_omega(const float *d_lrms, const float *d_pan, int N, int H,
+                      int W, int ratio, int l, float lambda_omega,
+                      float *d_omega, void *d_ws, size_t ws_bytes,
+                      void *stream);
+
+/* E^T E (n^2 x n^2, FP64, full symmetric) and E^T f (n^2, FP64) of
+ * Eq. z_solution, with E = D C(Y) (row q holds Y(c q - a) for every tap a)
+ * and f = sum_b omega_b X_b. Workspace: ps_op_workspace_size. */
+ps_status ps_op_kernel_normal_eq(const float *d_lrms, const float *d_pan,
+                                 const float *d_omega, int N, int H, int W,
+                                 int ratio, int R, double *d_EtE,
+                                 double *d_Etf, void *d_ws, size_t ws_bytes,
+                                 void *stream);
+
+/* The ADMM loop of Algorithm 1 given E^T E and E^T f (FP64, as above).
+ * Out: d_kernel (n x n, in the simplex). */
+ps_status ps_op_admm(const double *d_EtE, const double *d_Etf, int R,
+                     const ps_kernel_params *h_params, float *d_kernel,
+                     ps_kernel_info *h_info, void *d_ws, size_t ws_bytes,
+                     void *stream);
+
+/* Workspace bytes for the operator entry points above at these sizes
+ * (the largest any of them needs). */
+size_t ps_op_workspace_size(int N, int H, int W, int ratio, int R);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PS_OPS_H */

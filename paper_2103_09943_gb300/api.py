@@ -1,0 +1,181 @@
+"""Python binding of the F-BMP C-ABI on torch CUDA tensors.
+
+Argument marshalling only: every step runs in the CUDA kernels of libps.so.
+Tensors must be float32, contiguous and on the current CUDA device; the
+current torch stream is passed to the library. Outputs and the workspace are
+allocated with torch (the library itself allocates nothing).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import BandInfo, HrmsParams, KernelInfo, KernelParams
+
+
+class PsError(RuntimeError):
+    pass
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        msg = _lib.load().ps_status_string(status).decode()
+        raise PsError(f"libps status {status}: {msg}")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _f32(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def default_kernel_params(**kw) -> KernelParams:
+    p = KernelParams()
+    _lib.load().ps_default_kernel_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def default_hrms_params(**kw) -> HrmsParams:
+    p = HrmsParams()
+    _lib.load().ps_default_hrms_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, "lambda_" if k == "lam" else k, v)
+    return p
+
+
+def workspace_size(N, H, W, ratio, R) -> int:
+    return int(_lib.load().ps_workspace_size(N, H, W, ratio, R, None))
+
+
+def workspace(N, H, W, ratio, R, device=None) -> torch.Tensor:
+    n = workspace_size(N, H, W, ratio, R)
+    if n == 0:
+        raise PsError("invalid sizes for a workspace")
+    return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+
+
+@dataclass
+class SolveInfo:
+    status: list
+    iters: list
+    rel_residual: list
+
+
+def estimate_kernel(lrms, pan, ratio: int, R: int, params: KernelParams | None = None,
+                    omega=None, ws=None, info: bool = True):
+    """Algorithm 1. Returns (kernel (n,n), omega (N,), KernelInfo or None)."""
+    N, h, w = lrms.shape
+    H, W = pan.shape
+    _f32(lrms, "lrms"), _f32(pan, "pan")
+    p = params or default_kernel_params()
+    n = 2 * R + 1
+    kern = torch.empty((n, n), dtype=torch.float32, device=lrms.device)
+    om = torch.empty(N, dtype=torch.float32, device=lrms.device)
+    ws = ws if ws is not None else workspace(N, H, W, ratio, R, lrms.device)
+    ki = KernelInfo()
+    _check(_lib.load().ps_estimate_kernel(
+        _ptr(lrms), _ptr(pan), N, H, W, ratio, R, ctypes.byref(p),
+        _ptr(None if omega is None else _f32(omega, "omega")), _ptr(kern), _ptr(om),
+        ctypes.byref(ki) if info else None, _ptr(ws), ws.numel(), _stream()))
+    return kern, om, (ki if info else None)
+
+
+def solve_hrms(lrms, pan, kernel, ratio: int, params: HrmsParams | None = None,
+               z_init=None, want_z0: bool = False, ws=None, info: bool = True, out=None):
+    """Algorithm 2 on all bands. Returns (hrms, z0 or None, SolveInfo or None)."""
+    N, h, w = lrms.shape
+    H, W = pan.shape
+    _f32(lrms, "lrms"), _f32(pan, "pan"), _f32(kernel, "kernel")
+    R = kernel.shape[0] // 2
+    p = params or default_hrms_params()
+    hr = out if out is not None else torch.empty((N, H, W), dtype=torch.float32,
+                                                 device=lrms.device)
+    z0 = torch.empty_like(hr) if want_z0 else None
+    ws = ws if ws is not None else workspace(N, H, W, ratio, R, lrms.device)
+    bi = (BandInfo * N)()
+    _check(_lib.load().ps_solve_hrms(
+        _ptr(lrms), _ptr(pan), _ptr(kernel), N, H, W, ratio, R, ctypes.byref(p),
+        _ptr(None if z_init is None else _f32(z_init, "z_init")), _ptr(hr), _ptr(z0),
+        bi if info else None, _ptr(ws), ws.numel(), _stream()))
+    si = None
+    if info:
+        si = SolveInfo([b.status for b in bi], [b.iters for b in bi],
+                       [b.rel_residual for b in bi])
+    return hr, z0, si
+
+
+def pansharpen(lrms, pan, ratio: int, R: int, kparams: KernelParams | None = None,
+               hparams: HrmsParams | None = None, ws=None, info: bool = True, out=None,
+               kernel_out=None):
+    """The two-stage scheme: Algorithm 1 then Algorithm 2.
+    Returns (hrms, kernel, KernelInfo or None, SolveInfo or None)."""
+    N, h, w = lrms.shape
+    H, W = pan.shape
+    _f32(lrms, "lrms"), _f32(pan, "pan")
+    kp = kparams or default_kernel_params()
+    hp = hparams or default_hrms_params()
+    n = 2 * R + 1
+    hr = out if out is not None else torch.empty((N, H, W), dtype=torch.float32,
+                                                 device=lrms.device)
+    kern = kernel_out if kernel_out is not None else torch.empty(
+        (n, n), dtype=torch.float32, device=lrms.device)
+    ws = ws if ws is not None else workspace(N, H, W, ratio, R, lrms.device)
+    ki = KernelInfo()
+    bi = (BandInfo * N)()
+    _check(_lib.load().ps_pansharpen(
+        _ptr(lrms), _ptr(pan), N, H, W, ratio, R, ctypes.byref(kp), ctypes.byref(hp),
+        _ptr(hr), _ptr(kern), ctypes.byref(ki) if info else None, bi if info else None,
+        _ptr(ws), ws.numel(), _stream()))
+    si = None
+    if info:
+        si = SolveInfo([b.status for b in bi], [b.iters for b in bi],
+                       [b.rel_residual for b in bi])
+    return hr, kern, (ki if info else None), si
+
+
+class HostPipeline:
+    """End-to-end path from HOST buffers: pinned host -> device copies of the
+    LRMS and PAN, ps_pansharpen, device -> host copy of the HRMS, all on one
+    stream. Buffers are allocated once for a given size."""
+
+    def __init__(self, N, H, W, ratio, R, kparams=None, hparams=None, device="cuda"):
+        self.N, self.H, self.W, self.ratio, self.R = N, H, W, ratio, R
+        h, w = H // ratio, W // ratio
+        self.kp = kparams or default_kernel_params()
+        self.hp = hparams or default_hrms_params()
+        self.d_lrms = torch.empty((N, h, w), dtype=torch.float32, device=device)
+        self.d_pan = torch.empty((H, W), dtype=torch.float32, device=device)
+        self.d_hrms = torch.empty((N, H, W), dtype=torch.float32, device=device)
+        self.d_kern = torch.empty((2 * R + 1, 2 * R + 1), dtype=torch.float32, device=device)
+        self.h_hrms = torch.empty((N, H, W), dtype=torch.float32).pin_memory()
+        self.ws = workspace(N, H, W, ratio, R, device)
+
+    @property
+    def h2d_bytes(self) -> int:
+        return (self.d_lrms.numel() + self.d_pan.numel()) * 4
+
+    @property
+    def d2h_bytes(self) -> int:
+        return self.d_hrms.numel() * 4
+
+    def __call__(self, h_lrms: torch.Tensor, h_pan: torch.Tensor) -> torch.Tensor:
+        self.d_lrms.copy_(h_lrms, non_blocking=True)
+        self.d_pan.copy_(h_pan, non_blocking=True)
+        pansharpen(self.d_lrms, self.d_pan, self.ratio, self.R, self.kp, self.hp, ws=self.ws,
+                   info=False, out=self.d_hrms, kernel_out=self.d_kern)
+        self.h_hrms.copy_(self.d_hrms, non_blocking=True)
+        return self.h_hrms

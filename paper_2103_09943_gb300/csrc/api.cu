@@ -1,0 +1,728 @@
+// C-ABI of the F-BMP library: argument checks, workspace layout, stage
+// orchestration and the CUDA graph that runs the CG loop on the device.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "ps.h"
+#include "ps_ops.h"
+
+using namespace ps;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// ---------------------------------------------------------------------------
+// Workspace layout (offsets from the 256-byte aligned base).
+// ---------------------------------------------------------------------------
+struct Layout {
+    size_t stats_I, stats_mu, stats_s;  // 3 x HW f32
+    size_t xbuf;                        // N HW f32 (Z0 when the caller gives none)
+    size_t r, pA, pB, ap;               // N HW f32 each; [r,pA] and [pB,ap] double as
+                                        // the complex FFT buffers
+    size_t v;                           // N hw f32
+    size_t bhat;                        // HW float2
+    size_t twW, twH;                    // twiddles
+    size_t bands, glob;                 // CG scalars
+    size_t bvec, f, G, omega, lags, ete, etf, zf, Q, kern, kinfo;
+    size_t total;
+};
+
+bool make_layout(int N, int H, int W, int c, int R, Layout *L) {
+    if (N < 1 || H < 1 || W < 1 || c < 1 || R < 0) return false;
+    const size_t HW = (size_t)H * W, hw = HW / ((size_t)c * c);
+    const size_t nt = (size_t)(2 * R + 1) * (2 * R + 1);
+    const size_t nl = (size_t)(4 * R + 1);
+    size_t o = 0;
+    auto take = [&o](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    L->stats_I = take(HW * 4);
+    L->stats_mu = take(HW * 4);
+    L->stats_s = take(HW * 4);
+    L->xbuf = take((size_t)N * HW * 4);
+    // r and pA contiguous, pB and ap contiguous (complex work buffers)
+    L->r = take((size_t)N * HW * 4 * 2);
+    L->pA = L->r + (size_t)N * HW * 4;
+    L->pB = take((size_t)N * HW * 4 * 2);
+    L->ap = L->pB + (size_t)N * HW * 4;
+    L->v = take((size_t)N * hw * 4);
+    L->bhat = take(HW * 8);
+    L->twW = take((size_t)W * 8);
+    L->twH = take((size_t)H * 8);
+    L->bands = take((size_t)N * sizeof(CgBand));
+    L->glob = take(sizeof(CgGlobal));
+    L->bvec = take(hw * 4);
+    L->f = take(hw * 4);
+    L->G = take(((size_t)N * N + N) * 8);
+    L->omega = take((size_t)N * 4);
+    L->lags = take((size_t)c * c * nl * nl * 8);
+    L->ete = take(nt * nt * 8);
+    L->etf = take(nt * 8);
+    L->zf = take(nt * 8);
+    L->Q = take(nt * nt * 4);
+    L->kern = take(nt * 4);
+    L->kinfo = take(64);
+    L->total = o + kAlign;  // slack for aligning the caller's pointer
+    return true;
+}
+
+struct Ws {
+    char *base;
+    Layout L;
+    template <class T>
+    T *at(size_t off) const { return reinterpret_cast<T *>(base + off); }
+};
+
+ps_status bind_ws(void *d_ws, size_t ws_bytes, int N, int H, int W, int c, int R, Ws *ws) {
+    if (!d_ws) return PS_ERR_WORKSPACE;
+    if (((uintptr_t)d_ws) % kAlign) return PS_ERR_WORKSPACE;
+    if (!make_layout(N, H, W, c, R, &ws->L)) return PS_ERR_SHAPE;
+    if (ws_bytes < ws->L.total - kAlign) return PS_ERR_WORKSPACE;
+    ws->base = static_cast<char *>(d_ws);
+    return PS_OK;
+}
+
+bool is_pow23(int L) {
+    if (L < 1) return false;
+    while (L % 2 == 0) L /= 2;
+    while (L % 3 == 0) L /= 3;
+    return L == 1;
+}
+
+ps_status check_dims(int N, int H, int W, int c, int R) {
+    if (N < 1 || N > kMaxBands) return PS_ERR_INVALID_ARG;
+    if (c < 2 || c > kMaxRatio) return PS_ERR_INVALID_ARG;
+    if (R < 0 || R > kMaxR) return PS_ERR_INVALID_ARG;
+    if (H < 1 || W < 1 || H % c || W % c) return PS_ERR_SHAPE;
+    if (H > kMaxFFT || W > kMaxFFT) return PS_ERR_UNSUPPORTED;
+    if (2 * R + 1 > H || 2 * R + 1 > W) return PS_ERR_SHAPE;
+    if (W % 4) return PS_ERR_UNSUPPORTED;
+    return PS_OK;
+}
+
+ps_status check_fft_dims(int H, int W) {
+    if (!is_pow23(H) || !is_pow23(W)) return PS_ERR_UNSUPPORTED;
+    if (H < 4 || W < 4) return PS_ERR_UNSUPPORTED;
+    return PS_OK;
+}
+
+ps_status check_hrms(const ps_hrms_params *p) {
+    if (!p) return PS_ERR_INVALID_ARG;
+    if (p->r < 1 || p->r > kMaxWinR) return PS_ERR_INVALID_ARG;
+    if (!(p->lambda > 0.f) || !(p->eps > 0.f) || !(p->tol > 0.f) || p->max_iter < 1)
+        return PS_ERR_INVALID_ARG;
+    if (!isfinite(p->lambda) || !isfinite(p->eps) || !isfinite(p->tol))
+        return PS_ERR_INVALID_ARG;
+    return PS_OK;
+}
+
+ps_status check_kernel_params(const ps_kernel_params *p) {
+    if (!p) return PS_ERR_INVALID_ARG;
+    if (p->l < 0 || p->l > 16) return PS_ERR_INVALID_ARG;
+    if (!(p->lambda_omega >= 0.f) || !(p->alpha1 >= 0.f) || !(p->alpha2 >= 0.f))
+        return PS_ERR_INVALID_ARG;
+    if (!(p->mu1 > 0.f) || !(p->mu2 > 0.f) || !(p->mu3 > 0.f)) return PS_ERR_INVALID_ARG;
+    if (!(p->rho > 0.f) || p->t_max < 1 || !(p->th >= 0.f)) return PS_ERR_INVALID_ARG;
+    return PS_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p % 16) == 0; }
+
+ps_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PS_OK : PS_ERR_CUDA; }
+
+ps_status last_launch() { return cuda_status(cudaGetLastError()); }
+
+// One-time (per device) kernel attributes and the private capture stream.
+struct DevState {
+    int attrs_done = 0;
+    cudaStream_t capture = nullptr;
+};
+std::mutex g_mu;
+std::vector<DevState> g_dev;
+
+ps_status ensure_device(cudaStream_t *capture) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PS_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
+    DevState &d = g_dev[dev];
+    if (!d.attrs_done) {
+        if (operators_set_attrs() != cudaSuccess) return PS_ERR_CUDA;
+        if (fft_set_attrs() != cudaSuccess) return PS_ERR_CUDA;
+        if (kest_set_attrs() != cudaSuccess) return PS_ERR_CUDA;
+        d.attrs_done = 1;
+    }
+    if (capture) {
+        if (!d.capture &&
+            cudaStreamCreateWithFlags(&d.capture, cudaStreamNonBlocking) != cudaSuccess)
+            return PS_ERR_CUDA;
+        *capture = d.capture;
+    }
+    return PS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CG loop as a CUDA graph: a conditional WHILE node whose body holds two
+// iterations (the direction p alternates between two buffers). Executable
+// graphs are cached per argument set.
+// ---------------------------------------------------------------------------
+struct CgLoopArgs {
+    int dev;
+    int N, H, W, c, R, r;
+    float lam;
+    const float *u, *I, *mu, *s;
+    float *x, *rv, *pA, *pB, *ap, *v;
+    CgBand *bands;
+    CgGlobal *g;
+    bool operator==(const CgLoopArgs &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+struct CgGraph {
+    CgLoopArgs key;
+    cudaGraphExec_t exec;
+};
+std::vector<CgGraph> g_graphs;
+
+void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, int use_cond,
+                       cudaGraphConditionalHandle h, cudaStream_t st) {
+    const size_t HW = (size_t)a.H * a.W;
+    launch_db(p_old, a.rv, p_new, a.bands, a.g, 1, a.N, a.H, a.W, a.c, a.u, a.R, a.v, st);
+    LlpArgs la = {};
+    la.in = p_new;
+    la.lr = a.v;
+    la.I = a.I;
+    la.mu = a.mu;
+    la.s = a.s;
+    la.u = a.u;
+    la.R = a.R;
+    la.c = a.c;
+    la.H = a.H;
+    la.W = a.W;
+    la.N = a.N;
+    la.lam = a.lam;
+    la.out = a.ap;
+    la.bands = a.bands;
+    la.g = a.g;
+    la.cg = 1;
+    launch_llp(la, LLP_APPLY, a.r, a.N, st);
+    launch_cg_update(a.x, a.rv, p_new, a.ap, a.N, HW, a.bands, a.g, st);
+    launch_cg_control(a.bands, a.g, a.N, use_cond, h, st);
+}
+
+ps_status get_cg_graph(const CgLoopArgs &a, cudaStream_t capture, cudaGraphExec_t *out) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        for (auto &e : g_graphs)
+            if (e.key == a) {
+                *out = e.exec;
+                return PS_OK;
+            }
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) return PS_ERR_CUDA;
+    cudaGraphConditionalHandle handle;
+    if (cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault) !=
+        cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return PS_ERR_CUDA;
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return PS_ERR_CUDA;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(capture, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return PS_ERR_CUDA;
+    }
+    enqueue_iteration(a, a.pA, a.pB, 1, handle, capture);
+    enqueue_iteration(a, a.pB, a.pA, 1, handle, capture);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(capture, &captured);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(graph);
+        return PS_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return PS_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_graphs.size() >= 16) {
+        cudaGraphExecDestroy(g_graphs.front().exec);
+        g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.push_back({a, exec});
+    *out = exec;
+    return PS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Z step (Eq. Z_solution) on the FFT path, given Z0 in `z0`.
+// ---------------------------------------------------------------------------
+ps_status run_zstep(const Ws &ws, const float *lrms, const float *z0, const float *u, int N,
+                    int H, int W, int c, int R, int r, float lam_z, float *out,
+                    cudaStream_t st) {
+    FftPlan pw, ph;
+    if (!fft_make_plan(W, &pw) || !fft_make_plan(H, &ph)) return PS_ERR_UNSUPPORTED;
+    const size_t HW = (size_t)H * W;
+    const int nimg = (N + 1) / 2;
+    float2 *cbuf = ws.at<float2>(ws.L.r);
+    float2 *ctmp = ws.at<float2>(ws.L.pB);
+    float2 *bhat = ws.at<float2>(ws.L.bhat);
+    float2 *twW = ws.at<float2>(ws.L.twW), *twH = ws.at<float2>(ws.L.twH);
+    launch_fft_twiddles(W, twW, st);
+    launch_fft_twiddles(H, twH, st);
+    // kernel spectrum, transposed layout [kx][ky]
+    launch_kernel_embed(u, R, H, W, cbuf, st);
+    launch_fft_rows(cbuf, pw, H, twW, 0, 1.0f, nullptr, N, HW, st);
+    launch_transpose(cbuf, bhat, H, W, 1, st);
+    launch_fft_rows(bhat, ph, W, twH, 0, 1.0f, nullptr, N, HW, st);
+    // right-hand side B^T D^T X + lam' L L-hat, packed two bands per image
+    LlpArgs la = {};
+    la.in = z0;
+    la.lr = lrms;
+    la.I = ws.at<float>(ws.L.stats_I);
+    la.mu = ws.at<float>(ws.L.stats_mu);
+    la.s = ws.at<float>(ws.L.stats_s);
+    la.u = u;
+    la.R = R;
+    la.c = c;
+    la.H = H;
+    la.W = W;
+    la.N = N;
+    la.lam = lam_z;
+    la.cout = cbuf;
+    launch_llp(la, LLP_ZRHS, r, N, st);
+    launch_fft_rows(cbuf, pw, nimg * H, twW, 0, 1.0f, nullptr, N, HW, st);
+    launch_transpose(cbuf, ctmp, H, W, nimg, st);
+    launch_fft_rows(ctmp, ph, nimg * W, twH, 0, 1.0f, nullptr, N, HW, st);
+    launch_alias_solve(ctmp, bhat, nimg, H, W, c, lam_z, st);
+    launch_fft_rows(ctmp, ph, nimg * W, twH, 1, 1.0f, nullptr, N, HW, st);
+    launch_transpose(ctmp, cbuf, W, H, nimg, st);
+    launch_fft_rows(cbuf, pw, nimg * H, twW, 1, 1.0f, out, N, HW, st);
+    return last_launch();
+}
+
+}  // namespace
+
+// ===========================================================================
+// Public entry points
+// ===========================================================================
+extern "C" {
+
+void ps_default_kernel_params(ps_kernel_params *p) {
+    if (!p) return;
+    p->lambda_omega = 10.0f;
+    p->l = 2;
+    p->alpha1 = 1.0f;
+    p->alpha2 = 0.006f;
+    p->mu1 = p->mu2 = p->mu3 = 100.0f;
+    p->rho = 0.5f;
+    p->t_max = 10000;
+    p->th = 1e-5f;
+}
+
+void ps_default_hrms_params(ps_hrms_params *p) {
+    if (!p) return;
+    p->lambda = 2e-4f;
+    p->r = 1;
+    p->eps = 1.0f;
+    p->tol = 1e-6f;
+    p->max_iter = 5000;
+    p->exact_weight = 0;
+}
+
+const char *ps_status_string(int s) {
+    switch (s) {
+        case PS_OK: return "ok";
+        case PS_ERR_INVALID_ARG: return "invalid argument";
+        case PS_ERR_SHAPE: return "inconsistent shapes";
+        case PS_ERR_CUDA: return "CUDA runtime error";
+        case PS_ERR_WORKSPACE: return "workspace too small or misaligned";
+        case PS_ERR_NOT_CONVERGED: return "iteration cap reached";
+        case PS_ERR_NONFINITE: return "non-finite value in a reduction";
+        case PS_ERR_BREAKDOWN: return "CG breakdown (p^T A p <= 0)";
+        case PS_ERR_UNSUPPORTED: return "size not supported";
+        default: return "unknown status";
+    }
+}
+
+size_t ps_workspace_size(int N, int H, int W, int ratio, int R, const ps_hrms_params *) {
+    if (check_dims(N, H, W, ratio, R) != PS_OK) return 0;
+    Layout L;
+    if (!make_layout(N, H, W, ratio, R, &L)) return 0;
+    return L.total;
+}
+
+size_t ps_op_workspace_size(int N, int H, int W, int ratio, int R) {
+    return ps_workspace_size(N, H, W, ratio, R, nullptr);
+}
+
+ps_status ps_estimate_kernel(const float *d_lrms, const float *d_pan, int N, int H, int W,
+                             int ratio, int R, const ps_kernel_params *p,
+                             const float *d_omega_in, float *d_kernel, float *d_omega_out,
+                             ps_kernel_info *h_info, void *d_ws, size_t ws_bytes,
+                             void *stream) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
+    if ((s = check_kernel_params(p)) != PS_OK) return s;
+    if (!d_lrms || !d_pan || !d_kernel) return PS_ERR_INVALID_ARG;
+    Ws ws;
+    if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int c = ratio, h = H / c, w = W / c, hw = h * w;
+    const int nt = (2 * R + 1) * (2 * R + 1);
+    float *omega = d_omega_out ? d_omega_out : ws.at<float>(ws.L.omega);
+    if (d_omega_in) {
+        if (omega != d_omega_in &&
+            cudaMemcpyAsync(omega, d_omega_in, N * sizeof(float), cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess)
+            return PS_ERR_CUDA;
+    } else {
+        float *Aw = ws.at<float>(ws.L.v);
+        launch_box_lr(d_lrms, N, h, w, p->l, Aw, st);
+        launch_box_hr_dec(d_pan, H, W, c, c * p->l, ws.at<float>(ws.L.bvec), st);
+        launch_omega_normal(Aw, ws.at<float>(ws.L.bvec), N, hw, ws.at<double>(ws.L.G), st);
+        launch_omega_solve(ws.at<double>(ws.L.G), N, p->lambda_omega, omega, st);
+    }
+    float *f = ws.at<float>(ws.L.f);
+    launch_combine_f(d_lrms, omega, N, hw, f, st);
+    double *ete = ws.at<double>(ws.L.ete);
+    launch_ete_lags(d_pan, H, W, c, R, ws.at<double>(ws.L.lags), st);
+    launch_ete_assemble(ws.at<double>(ws.L.lags), c, R, ete, st);
+    launch_etf(d_pan, H, W, c, R, f, ws.at<double>(ws.L.etf), st);
+    launch_cholesky(ete, nt, p->mu3, st);
+    launch_chol_solve(ete, ws.at<double>(ws.L.etf), nt, ws.at<double>(ws.L.zf), st);
+    launch_chol_inverse(ete, nt, p->mu3, ws.at<float>(ws.L.Q), nullptr, st);
+    int *ki = ws.at<int>(ws.L.kinfo);
+    launch_admm(ws.at<float>(ws.L.Q), ws.at<double>(ws.L.zf), R, *p, d_kernel, ki, ki + 1,
+                reinterpret_cast<double *>(ki + 2), st);
+    if ((s = last_launch()) != PS_OK) return s;
+    if (h_info) {
+        int hi[2];
+        double ch = 0.0;
+        if (cudaMemcpyAsync(hi, ki, sizeof(hi), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&ch, ki + 2, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return PS_ERR_CUDA;
+        h_info->iters = hi[0];
+        h_info->status = hi[1];
+        h_info->last_change = ch;
+    }
+    return PS_OK;
+}
+
+ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_kernel, int N,
+                        int H, int W, int ratio, int R, const ps_hrms_params *p,
+                        const float *d_z_init, float *d_hrms, float *d_z0,
+                        ps_band_info *h_info, void *d_ws, size_t ws_bytes, void *stream) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
+    if ((s = check_fft_dims(H, W)) != PS_OK) return s;
+    if ((s = check_hrms(p)) != PS_OK) return s;
+    if (!d_lrms || !d_pan || !d_kernel || !d_hrms) return PS_ERR_INVALID_ARG;
+    if ((d_z0 && !aligned16(d_z0)) || (d_z_init && !aligned16(d_z_init)))
+        return PS_ERR_INVALID_ARG;
+    Ws ws;
+    if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
+    cudaStream_t capture = nullptr;
+    if ((s = ensure_device(&capture)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int c = ratio;
+    const size_t HW = (size_t)H * W;
+    float *I = ws.at<float>(ws.L.stats_I), *mu = ws.at<float>(ws.L.stats_mu),
+          *sv = ws.at<float>(ws.L.stats_s);
+    float *x = d_z0 ? d_z0 : ws.at<float>(ws.L.xbuf);
+    float *rv = ws.at<float>(ws.L.r), *pA = ws.at<float>(ws.L.pA), *pB = ws.at<float>(ws.L.pB),
+          *ap = ws.at<float>(ws.L.ap), *v = ws.at<float>(ws.L.v);
+    CgBand *bands = ws.at<CgBand>(ws.L.bands);
+    CgGlobal *g = ws.at<CgGlobal>(ws.L.glob);
+
+    launch_pan_stats(d_pan, H, W, p->r, p->eps, I, mu, sv, st);
+    launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
+    if (d_z_init) {
+        launch_db(d_z_init, nullptr, nullptr, nullptr, nullptr, 0, N, H, W, c, d_kernel, R, v,
+                  st);
+        LlpArgs la = {};
+        la.in = d_z_init;
+        la.lr = v;
+        la.I = I;
+        la.mu = mu;
+        la.s = sv;
+        la.u = d_kernel;
+        la.R = R;
+        la.c = c;
+        la.H = H;
+        la.W = W;
+        la.N = N;
+        la.lam = p->lambda;
+        la.out = ap;
+        launch_llp(la, LLP_APPLY, p->r, N, st);
+    }
+    launch_cg_reset(bands, g, N, (double)p->tol, p->max_iter, st);
+    launch_cg_init(rv, d_z_init ? ap : nullptr, d_z_init, x, rv, N, HW, bands, g, st);
+    if ((s = last_launch()) != PS_OK) return s;
+
+    CgLoopArgs a;
+    memset(&a, 0, sizeof(a));
+    cudaGetDevice(&a.dev);
+    a.N = N; a.H = H; a.W = W; a.c = c; a.R = R; a.r = p->r; a.lam = p->lambda;
+    a.u = d_kernel; a.I = I; a.mu = mu; a.s = sv;
+    a.x = x; a.rv = rv; a.pA = pA; a.pB = pB; a.ap = ap; a.v = v;
+    a.bands = bands; a.g = g;
+    cudaGraphExec_t exec;
+    if ((s = get_cg_graph(a, capture, &exec)) != PS_OK) return s;
+    if (cudaGraphLaunch(exec, st) != cudaSuccess) return PS_ERR_CUDA;
+
+    const float lam_z = p->lambda * (p->exact_weight ? (float)((2 * p->r + 1) * (2 * p->r + 1)) : 1.0f);
+    if ((s = run_zstep(ws, d_lrms, x, d_kernel, N, H, W, c, R, p->r, lam_z, d_hrms, st)) != PS_OK)
+        return s;
+    if (h_info) {
+        std::vector<CgBand> hb(N);
+        if (cudaMemcpyAsync(hb.data(), bands, N * sizeof(CgBand), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return PS_ERR_CUDA;
+        for (int b = 0; b < N; ++b) {
+            h_info[b].status = hb[b].status;
+            h_info[b].iters = hb[b].iters;
+            h_info[b].rel_residual = hb[b].bb > 0.0 ? sqrt(hb[b].rr / hb[b].bb) : 0.0;
+        }
+    }
+    return PS_OK;
+}
+
+ps_status ps_pansharpen(const float *d_lrms, const float *d_pan, int N, int H, int W, int ratio,
+                        int R, const ps_kernel_params *kp, const ps_hrms_params *hp,
+                        float *d_hrms, float *d_kernel_out, ps_kernel_info *h_kinfo,
+                        ps_band_info *h_binfo, void *d_ws, size_t ws_bytes, void *stream) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
+    if ((s = check_fft_dims(H, W)) != PS_OK) return s;
+    if ((s = check_hrms(hp)) != PS_OK) return s;
+    if ((s = check_kernel_params(kp)) != PS_OK) return s;
+    Ws ws;
+    if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
+    float *kern = d_kernel_out ? d_kernel_out : ws.at<float>(ws.L.kern);
+    if ((s = ps_estimate_kernel(d_lrms, d_pan, N, H, W, ratio, R, kp, nullptr, kern, nullptr,
+                                h_kinfo, d_ws, ws_bytes, stream)) != PS_OK)
+        return s;
+    return ps_solve_hrms(d_lrms, d_pan, kern, N, H, W, ratio, R, hp, nullptr, d_hrms, nullptr,
+                         h_binfo, d_ws, ws_bytes, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Operator-level entry points (ps_ops.h)
+// ---------------------------------------------------------------------------
+ps_status ps_op_blur_decimate(const float *d_z, int N, int H, int W, int ratio,
+                              const float *d_kernel, int R, float *d_v, void *stream) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
+    if (!d_z || !d_kernel || !d_v) return PS_ERR_INVALID_ARG;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    launch_db(d_z, nullptr, nullptr, nullptr, nullptr, 0, N, H, W, ratio, d_kernel, R, d_v,
+              (cudaStream_t)stream);
+    return last_launch();
+}
+
+ps_status ps_op_blur_decimate_adj(const float *d_v, int N, int H, int W, int ratio,
+                                  const float *d_kernel, int R, float *d_z, void *stream) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
+    if (!d_z || !d_kernel || !d_v) return PS_ERR_INVALID_ARG;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    launch_adj(d_v, N, H, W, ratio, d_kernel, R, d_z, (cudaStream_t)stream);
+    return last_launch();
+}
+
+ps_status ps_op_pan_stats(const float *d_pan, int H, int W, int r, float eps, float *d_I,
+                          float *d_mu, float *d_s, void *stream) {
+    if (H < 1 || W < 1 || r < 1 || r > kMaxWinR || !(eps > 0.f)) return PS_ERR_INVALID_ARG;
+    if (!d_pan || !d_I || !d_mu || !d_s) return PS_ERR_INVALID_ARG;
+    ps_status s;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    launch_pan_stats(d_pan, H, W, r, eps, d_I, d_mu, d_s, (cudaStream_t)stream);
+    return last_launch();
+}
+
+ps_status ps_op_apply_z0(const float *d_z, int N, int H, int W, int ratio,
+                         const float *d_kernel, int R, const float *d_I, const float *d_mu,
+                         const float *d_s, int r, float lambda, float *d_out, void *d_ws,
+                         size_t ws_bytes, void *stream) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
+    if (r < 1 || r > kMaxWinR || !isfinite(lambda)) return PS_ERR_INVALID_ARG;
+    if (!d_z || !d_kernel || !d_I || !d_mu || !d_s || !d_out) return PS_ERR_INVALID_ARG;
+    Ws ws;
+    if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float *v = ws.at<float>(ws.L.v);
+    launch_db(d_z, nullptr, nullptr, nullptr, nullptr, 0, N, H, W, ratio, d_kernel, R, v, st);
+    LlpArgs la = {};
+    la.in = d_z;
+    la.lr = v;
+    la.I = d_I;
+    la.mu = d_mu;
+    la.s = d_s;
+    la.u = d_kernel;
+    la.R = R;
+    la.c = ratio;
+    la.H = H;
+    la.W = W;
+    la.N = N;
+    la.lam = lambda;
+    la.out = d_out;
+    launch_llp(la, LLP_APPLY, r, N, st);
+    return last_launch();
+}
+
+ps_status ps_op_guided_filter(const float *d_q, int N, int H, int W, const float *d_I,
+                              const float *d_mu, const float *d_s, int r, float *d_out,
+                              void *stream) {
+    if (N < 1 || N > kMaxBands || H < 1 || W < 1 || r < 1 || r > kMaxWinR)
+        return PS_ERR_INVALID_ARG;
+    if (!d_q || !d_I || !d_mu || !d_s || !d_out) return PS_ERR_INVALID_ARG;
+    ps_status s;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    LlpArgs la = {};
+    la.in = d_q;
+    la.I = d_I;
+    la.mu = d_mu;
+    la.s = d_s;
+    la.H = H;
+    la.W = W;
+    la.N = N;
+    la.c = 1;
+    la.out = d_out;
+    launch_llp(la, LLP_GF, r, N, (cudaStream_t)stream);
+    return last_launch();
+}
+
+ps_status ps_op_zstep(const float *d_lrms, const float *d_z0, int N, int H, int W, int ratio,
+                      const float *d_kernel, int R, const float *d_I, const float *d_mu,
+                      const float *d_s, int r, float lambda, int exact_weight, float *d_z,
+                      void *d_ws, size_t ws_bytes, void *stream) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
+    if ((s = check_fft_dims(H, W)) != PS_OK) return s;
+    if (r < 1 || r > kMaxWinR || !(lambda > 0.f)) return PS_ERR_INVALID_ARG;
+    if (!d_lrms || !d_z0 || !d_kernel || !d_I || !d_mu || !d_s || !d_z)
+        return PS_ERR_INVALID_ARG;
+    Ws ws;
+    if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t HW = (size_t)H * W;
+    // the Z step reads the statistics from the workspace
+    if (cudaMemcpyAsync(ws.at<float>(ws.L.stats_I), d_I, HW * 4, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(ws.at<float>(ws.L.stats_mu), d_mu, HW * 4, cudaMemcpyDeviceToDevice,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(ws.at<float>(ws.L.stats_s), d_s, HW * 4, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+        return PS_ERR_CUDA;
+    const float lam_z = lambda * (exact_weight ? (float)((2 * r + 1) * (2 * r + 1)) : 1.0f);
+    return run_zstep(ws, d_lrms, d_z0, d_kernel, N, H, W, ratio, R, r, lam_z, d_z, st);
+}
+
+ps_status ps_op_omega(const float *d_lrms, const float *d_pan, int N, int H, int W, int ratio,
+                      int l, float lambda_omega, float *d_omega, void *d_ws, size_t ws_bytes,
+                      void *stream) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, 0)) != PS_OK) return s;
+    if (l < 0 || l > 16 || !(lambda_omega >= 0.f)) return PS_ERR_INVALID_ARG;
+    if (!d_lrms || !d_pan || !d_omega) return PS_ERR_INVALID_ARG;
+    Ws ws;
+    if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, 0, &ws)) != PS_OK) return s;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int h = H / ratio, w = W / ratio;
+    float *Aw = ws.at<float>(ws.L.v);
+    launch_box_lr(d_lrms, N, h, w, l, Aw, st);
+    launch_box_hr_dec(d_pan, H, W, ratio, ratio * l, ws.at<float>(ws.L.bvec), st);
+    launch_omega_normal(Aw, ws.at<float>(ws.L.bvec), N, h * w, ws.at<double>(ws.L.G), st);
+    launch_omega_solve(ws.at<double>(ws.L.G), N, lambda_omega, d_omega, st);
+    return last_launch();
+}
+
+ps_status ps_op_kernel_normal_eq(const float *d_lrms, const float *d_pan, const float *d_omega,
+                                 int N, int H, int W, int ratio, int R, double *d_EtE,
+                                 double *d_Etf, void *d_ws, size_t ws_bytes, void *stream) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
+    if (!d_lrms || !d_pan || !d_omega || !d_EtE || !d_Etf) return PS_ERR_INVALID_ARG;
+    Ws ws;
+    if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int hw = (H / ratio) * (W / ratio);
+    float *f = ws.at<float>(ws.L.f);
+    launch_combine_f(d_lrms, d_omega, N, hw, f, st);
+    launch_ete_lags(d_pan, H, W, ratio, R, ws.at<double>(ws.L.lags), st);
+    launch_ete_assemble(ws.at<double>(ws.L.lags), ratio, R, d_EtE, st);
+    launch_etf(d_pan, H, W, ratio, R, f, d_Etf, st);
+    return last_launch();
+}
+
+ps_status ps_op_admm(const double *d_EtE, const double *d_Etf, int R, const ps_kernel_params *p,
+                     float *d_kernel, ps_kernel_info *h_info, void *d_ws, size_t ws_bytes,
+                     void *stream) {
+    ps_status s;
+    if (R < 0 || R > kMaxR) return PS_ERR_INVALID_ARG;
+    if ((s = check_kernel_params(p)) != PS_OK) return s;
+    if (!d_EtE || !d_Etf || !d_kernel) return PS_ERR_INVALID_ARG;
+    const int n = 2 * R + 1, nt = n * n;
+    Ws ws;
+    if ((s = bind_ws(d_ws, ws_bytes, 1, n, n, 1, R, &ws)) != PS_OK) return s;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *ete = ws.at<double>(ws.L.ete);
+    if (cudaMemcpyAsync(ete, d_EtE, (size_t)nt * nt * 8, cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+        return PS_ERR_CUDA;
+    launch_cholesky(ete, nt, p->mu3, st);
+    launch_chol_solve(ete, d_Etf, nt, ws.at<double>(ws.L.zf), st);
+    launch_chol_inverse(ete, nt, p->mu3, ws.at<float>(ws.L.Q), nullptr, st);
+    int *ki = ws.at<int>(ws.L.kinfo);
+    launch_admm(ws.at<float>(ws.L.Q), ws.at<double>(ws.L.zf), R, *p, d_kernel, ki, ki + 1,
+                reinterpret_cast<double *>(ki + 2), st);
+    if ((s = last_launch()) != PS_OK) return s;
+    if (h_info) {
+        int hi[2];
+        double ch = 0.0;
+        if (cudaMemcpyAsync(hi, ki, sizeof(hi), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&ch, ki + 2, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return PS_ERR_CUDA;
+        h_info->iters = hi[0];
+        h_info->status = hi[1];
+        h_info->last_change = ch;
+    }
+    return PS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Shared device helpers of the F-BMP CUDA path (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ps.h"
+
+namespace ps {
+
+constexpr int kMaxR = 16;          // kernel radius: n = 2R + 1 <= 33
+constexpr int kMaxTaps = (2 * kMaxR + 1) * (2 * kMaxR + 1);
+constexpr int kMaxWinR = 4;        // LLP window radius r <= 4
+constexpr int kMaxBands = 64;
+constexpr int kMaxFFT = 8192;      // H, W <= 8192
+constexpr int kMaxRatio = 8;
+
+// Wrap an index that lies in [-n, 2n) onto [0, n).
+__host__ __device__ __forceinline__ int wrapi(int i, int n) {
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// Per-band CG scalars. FP64: the inner products of the solver are, with the
+// PAN statistics and the kernel normal equations, where double precision is
+// spent.
+struct CgBand {
+    double rr;       // r^T r of the current residual
+    double bb;       // b^T b
+    double pAp;      // accumulator of p^T A p (zeroed after use)
+    double rr_new;   // accumulator of the next r^T r (zeroed after use)
+    double alpha;
+    double beta;
+    int iters;
+    int status;      // ps_status
+    int done;
+    unsigned int cnt_apply;   // CTA arrival counters (last-block pattern)
+    unsigned int cnt_update;
+    unsigned int cnt_init;
+};
+
+struct CgGlobal {
+    double tol;               // relative residual target
+    unsigned int cnt_bands;
+    int active;               // bands not yet done
+    int max_iters;            // max over bands of iters
+    int stop;                 // set once the loop must end
+    int iter;                 // loop iterations run
+    int max_iter;             // hard cap
+};
+
+// Block-wide sum of a double over a 1-D block; the result is valid in
+// thread 0. `red` holds blockDim.x / 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum_d(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int tid = threadIdx.x;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid < 32) {
+        s = (tid < nw) ? red[tid] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
+}  // namespace ps

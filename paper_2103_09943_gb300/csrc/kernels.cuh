@@ -1,0 +1,89 @@
+// Internal launch interface between the kernels and the C-ABI layer.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ps {
+
+enum LlpMode { LLP_APPLY = 0, LLP_ZRHS = 1, LLP_GF = 2 };
+
+struct LlpArgs {
+    const float *in;    // p (APPLY), Z0 (ZRHS) or q (GF); N x H x W
+    const float *lr;    // D B p (APPLY) or X (ZRHS); N x h x w
+    const float *I, *mu, *s;
+    const float *u;
+    int R, c, H, W, N;
+    float lam;
+    float *out;         // N x H x W (APPLY, GF)
+    float2 *cout;       // packed complex images (ZRHS)
+    CgBand *bands;      // CG mode of APPLY: p^T A p and alpha
+    const CgGlobal *g;
+    int cg;
+};
+
+// operators.cu
+void launch_pan_stats(const float *Y, int H, int W, int r, float eps, float *I, float *mu,
+                      float *s, cudaStream_t st);
+void launch_db(const float *src, const float *rsrc, float *pdst, const CgBand *bands,
+               const CgGlobal *g, int cg, int N, int H, int W, int c, const float *u, int R,
+               float *v, cudaStream_t st);
+void launch_adj(const float *v, int N, int H, int W, int c, const float *u, int R, float *z,
+                cudaStream_t st);
+void launch_llp(const LlpArgs &a, int mode, int r, int N, cudaStream_t st);
+void launch_cg_reset(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter,
+                     cudaStream_t st);
+void launch_cg_init(const float *bvec, const float *ax0, const float *x0, float *x, float *r,
+                    int N, size_t HW, CgBand *bands, CgGlobal *g, cudaStream_t st);
+void launch_cg_update(float *x, float *r, const float *p, const float *ap, int N, size_t HW,
+                      CgBand *bands, const CgGlobal *g, cudaStream_t st);
+void launch_cg_control(CgBand *bands, CgGlobal *g, int N, int use_cond,
+                       cudaGraphConditionalHandle handle, cudaStream_t st);
+cudaError_t operators_set_attrs();
+size_t db_smem_bytes(int c, int R);
+size_t llp_smem_bytes(int r);
+
+// fft.cu
+struct FftPlan {
+    int L;
+    int npass;
+    int radix[16];
+};
+bool fft_make_plan(int L, FftPlan *plan);
+void launch_fft_twiddles(int L, float2 *tw, cudaStream_t st);
+void launch_fft_rows(float2 *data, const FftPlan &plan, int rows, const float2 *tw,
+                     int inverse, float scale, float *unpack, int N, size_t HW,
+                     cudaStream_t st);
+void launch_transpose(const float2 *in, float2 *out, int rows, int cols, int batch,
+                      cudaStream_t st);
+void launch_kernel_embed(const float *u, int R, int H, int W, float2 *out, cudaStream_t st);
+void launch_alias_solve(float2 *spec, const float2 *bspec, int nimg, int H, int W, int c,
+                        float lam, cudaStream_t st);
+cudaError_t fft_set_attrs();
+
+// kest.cu
+void launch_box_lr(const float *X, int N, int h, int w, int l, float *out, cudaStream_t st);
+void launch_box_hr_dec(const float *Y, int H, int W, int c, int half, float *out,
+                       cudaStream_t st);
+void launch_omega_normal(const float *A, const float *bv, int N, int hw, double *G,
+                         cudaStream_t st);
+void launch_omega_solve(double *G, int N, float lambda_omega, float *omega, cudaStream_t st);
+void launch_combine_f(const float *X, const float *omega, int N, int hw, float *f,
+                      cudaStream_t st);
+void launch_ete_lags(const float *Y, int H, int W, int c, int R, double *lags,
+                     cudaStream_t st);
+void launch_ete_assemble(const double *lags, int c, int R, double *EtE, cudaStream_t st);
+void launch_etf(const float *Y, int H, int W, int c, int R, const float *f, double *Etf,
+                cudaStream_t st);
+void launch_cholesky(double *A, int n, float mu3, cudaStream_t st);
+void launch_chol_solve(const double *L, const double *b, int n, double *x, cudaStream_t st);
+void launch_chol_inverse(const double *L, int n, float scale, float *Q, double *tmp,
+                         cudaStream_t st);
+void launch_admm(const float *Q, const double *zf, int R, const ps_kernel_params &p,
+                 float *kernel_out, int *info_iters, int *info_status, double *info_change,
+                 cudaStream_t st);
+size_t admm_smem_bytes(int R);
+cudaError_t kest_set_attrs();
+
+}  // namespace ps

@@ -1,0 +1,657 @@
+// Blur kernel estimation (Algorithm 1), sm_103a.
+//
+//   omega      Eq. objective3: box filters, FP64 normal equations, tiny solve
+//   E^T E      Eq. z_solution with E = D C(Y): E^T E[a, b] depends only on the
+//              phase of a modulo c and on the lag a - b, so it is assembled
+//              from c^2 (4R+1)^2 lag correlations of the PAN,
+//              C[phi][d] = sum_k Y(c k + phi) Y(c k + phi + d),
+//              accumulated in double-float (error-free products and sums in
+//              FP32, the FP64 rate of this part being 1/64 of FP32)
+//   Cholesky   of E^T E + mu3 I in FP64; z_f = (E^T E + mu3 I)^{-1} E^T f in
+//              FP64 and Q = mu3 (E^T E + mu3 I)^{-1} (FP32, column-parallel),
+//              so that the z step of Eq. z_solution is z_f + Q (u + Lambda3)
+//   ADMM       the loop of Eq. subproblems in one CTA: shrink, z step with
+//              simplex projection, {u, p} by n x n DFTs and Cramer's rule
+//              (Eq. u_p_solution), multiplier updates, stop test
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ps {
+
+__device__ __forceinline__ int wrapk(int i, int n) {
+    int m = i % n;
+    return m < 0 ? m + n : m;
+}
+
+// Error-free accumulation of a*b into (s, c): s + c carries ~48 bits.
+__device__ __forceinline__ void df_acc(float a, float b, float &s, float &c) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float t = s + p;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (p - bp);
+    s = t;
+    c += err + e;
+}
+
+// ---------------------------------------------------------------------------
+// omega (Eq. objective3)
+// ---------------------------------------------------------------------------
+__global__ void box_lr_kernel(const float *__restrict__ X, int h, int w, int l,
+                              float *__restrict__ out) {
+    const int b = blockIdx.z;
+    const int y = blockIdx.y * 8 + threadIdx.y, x = blockIdx.x * 32 + threadIdx.x;
+    if (y >= h || x >= w) return;
+    const float *Xb = X + (size_t)b * h * w;
+    float s = 0.f;
+    for (int dy = -l; dy <= l; ++dy)
+        for (int dx = -l; dx <= l; ++dx) s += Xb[(size_t)wrapk(y + dy, h) * w + wrapk(x + dx, w)];
+    out[(size_t)b * h * w + (size_t)y * w + x] = s / (float)((2 * l + 1) * (2 * l + 1));
+}
+
+void launch_box_lr(const float *X, int N, int h, int w, int l, float *out, cudaStream_t st) {
+    dim3 blk(32, 8), grd((w + 31) / 32, (h + 7) / 8, N);
+    box_lr_kernel<<<grd, blk, 0, st>>>(X, h, w, l, out);
+}
+
+// D B(u2) Y with u2 the (2 half + 1)^2 unit box: one thread per LR site.
+__global__ void box_hr_dec_kernel(const float *__restrict__ Y, int H, int W, int c, int half,
+                                  float *__restrict__ out) {
+    const int h = H / c, w = W / c;
+    const int k = blockIdx.y * 8 + threadIdx.y, l = blockIdx.x * 32 + threadIdx.x;
+    if (k >= h || l >= w) return;
+    float s = 0.f, cmp = 0.f;
+    for (int dy = -half; dy <= half; ++dy) {
+        const float *row = Y + (size_t)wrapk(c * k + dy, H) * W;
+        for (int dx = -half; dx <= half; ++dx) df_acc(row[wrapk(c * l + dx, W)], 1.0f, s, cmp);
+    }
+    const double nb = (double)((2 * half + 1) * (2 * half + 1));
+    out[(size_t)k * w + l] = (float)(((double)s + (double)cmp) / nb);
+}
+
+void launch_box_hr_dec(const float *Y, int H, int W, int c, int half, float *out,
+                       cudaStream_t st) {
+    const int h = H / c, w = W / c;
+    dim3 blk(32, 8), grd((w + 31) / 32, (h + 7) / 8);
+    box_hr_dec_kernel<<<grd, blk, 0, st>>>(Y, H, W, c, half, out);
+}
+
+// G[j][k] = sum_q A_j[q] A_k[q] (j <= k < N) and G[N][j] = sum_q A_j[q] bv[q];
+// one CTA per entry, double-float accumulation.
+__global__ void __launch_bounds__(256) omega_normal_kernel(const float *__restrict__ A,
+                                                           const float *__restrict__ bv, int N,
+                                                           int hw, double *G) {
+    __shared__ double red[8];
+    int e = blockIdx.x, j = 0, k = 0;
+    bool rhs = false;
+    const int npair = N * (N + 1) / 2;
+    if (e < npair) {
+        while (e >= N - j) { e -= N - j; ++j; }
+        k = j + e;
+    } else {
+        rhs = true;
+        j = e - npair;
+    }
+    const float *a = A + (size_t)j * hw;
+    const float *bb = rhs ? bv : A + (size_t)k * hw;
+    float s = 0.f, cmp = 0.f;
+    for (int q = threadIdx.x; q < hw; q += 256) df_acc(a[q], bb[q], s, cmp);
+    const double tot = block_sum_d((double)s + (double)cmp, red);
+    if (threadIdx.x == 0) {
+        if (rhs) {
+            G[(size_t)N * N + j] = tot;
+        } else {
+            G[(size_t)j * N + k] = tot;
+            G[(size_t)k * N + j] = tot;
+        }
+    }
+}
+
+void launch_omega_normal(const float *A, const float *bv, int N, int hw, double *G,
+                         cudaStream_t st) {
+    const int nblk = N * (N + 1) / 2 + N;
+    omega_normal_kernel<<<nblk, 256, 0, st>>>(A, bv, N, hw, G);
+}
+
+// (A^T A + lambda_omega G^T G) omega = A^T b by Cholesky, one thread (N <= 64).
+__global__ void omega_solve_kernel(double *G, int N, float lam, float *omega) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double *M = G;                 // N x N, overwritten
+    double *rhs = G + (size_t)N * N;
+    for (int i = 0; i < N; ++i) {
+        // G^T G of first differences: diag 1, 2, ..., 2, 1; off-diagonal -1
+        double d = (N == 1) ? 0.0 : ((i == 0 || i == N - 1) ? 1.0 : 2.0);
+        M[(size_t)i * N + i] += lam * d;
+        if (i + 1 < N) {
+            M[(size_t)i * N + i + 1] -= lam;
+            M[(size_t)(i + 1) * N + i] -= lam;
+        }
+    }
+    for (int k = 0; k < N; ++k) {
+        double dkk = M[(size_t)k * N + k];
+        for (int t = 0; t < k; ++t) dkk -= M[(size_t)k * N + t] * M[(size_t)k * N + t];
+        const double lkk = sqrt(dkk > 0.0 ? dkk : 1e-300);
+        M[(size_t)k * N + k] = lkk;
+        for (int i = k + 1; i < N; ++i) {
+            double v = M[(size_t)i * N + k];
+            for (int t = 0; t < k; ++t) v -= M[(size_t)i * N + t] * M[(size_t)k * N + t];
+            M[(size_t)i * N + k] = v / lkk;
+        }
+    }
+    for (int i = 0; i < N; ++i) {
+        double v = rhs[i];
+        for (int t = 0; t < i; ++t) v -= M[(size_t)i * N + t] * rhs[t];
+        rhs[i] = v / M[(size_t)i * N + i];
+    }
+    for (int i = N - 1; i >= 0; --i) {
+        double v = rhs[i];
+        for (int t = i + 1; t < N; ++t) v -= M[(size_t)t * N + i] * rhs[t];
+        rhs[i] = v / M[(size_t)i * N + i];
+    }
+    for (int i = 0; i < N; ++i) omega[i] = (float)rhs[i];
+}
+
+void launch_omega_solve(double *G, int N, float lambda_omega, float *omega, cudaStream_t st) {
+    omega_solve_kernel<<<1, 32, 0, st>>>(G, N, lambda_omega, omega);
+}
+
+__global__ void combine_f_kernel(const float *__restrict__ X, const float *__restrict__ om,
+                                 int N, int hw, float *__restrict__ f) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= hw) return;
+    float s = 0.f;
+    for (int b = 0; b < N; ++b) s = fmaf(om[b], X[(size_t)b * hw + q], s);
+    f[q] = s;
+}
+
+void launch_combine_f(const float *X, const float *omega, int N, int hw, float *f,
+                      cudaStream_t st) {
+    combine_f_kernel<<<(hw + 255) / 256, 256, 0, st>>>(X, omega, N, hw, f);
+}
+
+// ---------------------------------------------------------------------------
+// E^T E from lag correlations
+// ---------------------------------------------------------------------------
+constexpr int LAG_CHUNK = 17;
+
+// grid: (4R+1 dy, c*c phases, ceil((4R+1)/LAG_CHUNK) dx chunks)
+// lags[((py*c + px) * (4R+1) + (dy+2R)) * (4R+1) + (dx+2R)]
+__global__ void __launch_bounds__(256) ete_lag_kernel(const float *__restrict__ Y, int H, int W,
+                                                      int c, int R, double *lags) {
+    __shared__ double red[8];
+    const int nl = 4 * R + 1;
+    const int dy = (int)blockIdx.x - 2 * R;
+    const int py = blockIdx.y / c, px = blockIdx.y - (blockIdx.y / c) * c;
+    const int dx0 = (int)blockIdx.z * LAG_CHUNK - 2 * R;
+    const int ndx = min(LAG_CHUNK, 2 * R - dx0 + 1);
+    const int h = H / c, w = W / c;
+    float s[LAG_CHUNK], cm[LAG_CHUNK];
+#pragma unroll
+    for (int t = 0; t < LAG_CHUNK; ++t) { s[t] = 0.f; cm[t] = 0.f; }
+    for (int q = threadIdx.x; q < h * w; q += 256) {
+        const int ky = q / w, kx = q - (q / w) * w;
+        const int yy = c * ky + py, xx = c * kx + px;
+        const float a = Y[(size_t)yy * W + xx];
+        const float *row = Y + (size_t)wrapk(yy + dy, H) * W;
+#pragma unroll
+        for (int t = 0; t < LAG_CHUNK; ++t)
+            if (t < ndx) df_acc(a, row[wrapk(xx + dx0 + t, W)], s[t], cm[t]);
+    }
+    for (int t = 0; t < ndx; ++t) {
+        const double tot = block_sum_d((double)s[t] + (double)cm[t], red);
+        if (threadIdx.x == 0)
+            lags[((size_t)blockIdx.y * nl + (dy + 2 * R)) * nl + (dx0 + t + 2 * R)] = tot;
+    }
+}
+
+void launch_ete_lags(const float *Y, int H, int W, int c, int R, double *lags,
+                     cudaStream_t st) {
+    const int nl = 4 * R + 1;
+    dim3 grd(nl, c * c, (nl + LAG_CHUNK - 1) / LAG_CHUNK);
+    ete_lag_kernel<<<grd, 256, 0, st>>>(Y, H, W, c, R, lags);
+}
+
+// E^T E[a][b] = C[(-a) mod c][a - b], taps a = (ai, aj), b = (bi, bj).
+__global__ void ete_assemble_kernel(const double *__restrict__ lags, int c, int R,
+                                    double *EtE) {
+    const int n = 2 * R + 1, nt = n * n, nl = 4 * R + 1;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nt * nt) return;
+    const int ia = idx / nt, ib = idx - (idx / nt) * nt;
+    const int ai = ia / n - R, aj = ia % n - R, bi = ib / n - R, bj = ib % n - R;
+    const int py = wrapk(-ai, c), px = wrapk(-aj, c);
+    const int dy = ai - bi, dx = aj - bj;
+    EtE[idx] = lags[((size_t)(py * c + px) * nl + (dy + 2 * R)) * nl + (dx + 2 * R)];
+}
+
+void launch_ete_assemble(const double *lags, int c, int R, double *EtE, cudaStream_t st) {
+    const int nt = (2 * R + 1) * (2 * R + 1);
+    ete_assemble_kernel<<<(nt * nt + 255) / 256, 256, 0, st>>>(lags, c, R, EtE);
+}
+
+// E^T f[a] = sum_q Y(c q - a) f_q, one CTA per tap.
+__global__ void __launch_bounds__(256) etf_kernel(const float *__restrict__ Y, int H, int W,
+                                                  int c, int R, const float *__restrict__ f,
+                                                  double *Etf) {
+    __shared__ double red[8];
+    const int n = 2 * R + 1;
+    const int ai = (int)blockIdx.x / n - R, aj = (int)blockIdx.x % n - R;
+    const int h = H / c, w = W / c;
+    float s = 0.f, cm = 0.f;
+    for (int q = threadIdx.x; q < h * w; q += 256) {
+        const int ky = q / w, kx = q - (q / w) * w;
+        df_acc(Y[(size_t)wrapk(c * ky - ai, H) * W + wrapk(c * kx - aj, W)], f[q], s, cm);
+    }
+    const double tot = block_sum_d((double)s + (double)cm, red);
+    if (threadIdx.x == 0) Etf[blockIdx.x] = tot;
+}
+
+void launch_etf(const float *Y, int H, int W, int c, int R, const float *f, double *Etf,
+                cudaStream_t st) {
+    const int nt = (2 * R + 1) * (2 * R + 1);
+    etf_kernel<<<nt, 256, 0, st>>>(Y, H, W, c, R, f, Etf);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 Cholesky of A + mu3 I (lower triangle, in place), one CTA.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) cholesky_kernel(double *A, int n, float mu3) {
+    extern __shared__ double col[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    for (int i = tid; i < n; i += nthr) A[(size_t)i * n + i] += (double)mu3;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        const double d = A[(size_t)k * n + k];
+        const double lkk = sqrt(d > 0.0 ? d : 1e-300);
+        for (int i = k + 1 + tid; i < n; i += nthr) {
+            const double v = A[(size_t)i * n + k] / lkk;
+            col[i] = v;
+        }
+        __syncthreads();
+        for (int i = k + 1 + tid; i < n; i += nthr) A[(size_t)i * n + k] = col[i];
+        if (tid == 0) A[(size_t)k * n + k] = lkk;
+        for (int i = k + 1 + warp; i < n; i += nwarp) {
+            const double lik = col[i];
+            double *row = A + (size_t)i * n;
+            for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= lik * col[j];
+        }
+        __syncthreads();
+    }
+}
+
+void launch_cholesky(double *A, int n, float mu3, cudaStream_t st) {
+    cholesky_kernel<<<1, 1024, n * sizeof(double), st>>>(A, n, mu3);
+}
+
+// Solve (L L^T) x = b, one CTA.
+__global__ void __launch_bounds__(256) chol_solve_kernel(const double *L, const double *b,
+                                                         int n, double *x) {
+    extern __shared__ double yv[];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n; i += blockDim.x) yv[i] = b[i];
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        const double yk = yv[k] / L[(size_t)k * n + k];
+        __syncthreads();
+        if (tid == 0) yv[k] = yk;
+        for (int i = k + 1 + tid; i < n; i += blockDim.x) yv[i] -= L[(size_t)i * n + k] * yk;
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        const double xk = yv[k] / L[(size_t)k * n + k];
+        __syncthreads();
+        if (tid == 0) yv[k] = xk;
+        for (int i = tid; i < k; i += blockDim.x) yv[i] -= L[(size_t)k * n + i] * xk;
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += blockDim.x) x[i] = yv[i];
+}
+
+void launch_chol_solve(const double *L, const double *b, int n, double *x, cudaStream_t st) {
+    chol_solve_kernel<<<1, 256, n * sizeof(double), st>>>(L, b, n, x);
+}
+
+// Q[:, j] = scale (L L^T)^{-1} e_j, one CTA per column (Q is symmetric).
+__global__ void __launch_bounds__(256) chol_inverse_kernel(const double *L, int n, float scale,
+                                                           float *Q) {
+    extern __shared__ double yv[];
+    const int j = blockIdx.x, tid = threadIdx.x;
+    for (int i = tid; i < n; i += blockDim.x) yv[i] = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = j; k < n; ++k) {
+        const double yk = yv[k] / L[(size_t)k * n + k];
+        __syncthreads();
+        if (tid == 0) yv[k] = yk;
+        for (int i = k + 1 + tid; i < n; i += blockDim.x) yv[i] -= L[(size_t)i * n + k] * yk;
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        const double xk = yv[k] / L[(size_t)k * n + k];
+        __syncthreads();
+        if (tid == 0) yv[k] = xk;
+        for (int i = tid; i < k; i += blockDim.x) yv[i] -= L[(size_t)k * n + i] * xk;
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += blockDim.x) Q[(size_t)i * n + j] = (float)(scale * yv[i]);
+}
+
+void launch_chol_inverse(const double *L, int n, float scale, float *Q, double *,
+                         cudaStream_t st) {
+    chol_inverse_kernel<<<n, 256, n * sizeof(double), st>>>(L, n, scale, Q);
+}
+
+// ---------------------------------------------------------------------------
+// ADMM loop (Algorithm 1), one CTA of 1024 threads, state in shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 c_div(float2 a, float2 b) {
+    const float d = b.x * b.x + b.y * b.y;
+    return make_float2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ float2 det3c(float2 a11, float2 a12, float2 a13, float2 a21, float2 a22,
+                                        float2 a23, float2 a31, float2 a32, float2 a33) {
+    float2 r = c_mul(c_mul(a11, a22), a33);
+    r = c_add(r, c_mul(c_mul(a12, a23), a31));
+    r = c_add(r, c_mul(c_mul(a13, a21), a32));
+    r = c_sub(r, c_mul(c_mul(a13, a22), a31));
+    r = c_sub(r, c_mul(c_mul(a12, a21), a33));
+    r = c_sub(r, c_mul(c_mul(a11, a32), a23));
+    return r;
+}
+
+// Block sums (double) of two values; all threads receive the results.
+__device__ __forceinline__ void block_sum2(double a, double b, double *red, double &ra,
+                                           double &rb) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int tid = threadIdx.x, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((tid & 31) == 0) {
+        red[tid >> 5] = a;
+        red[32 + (tid >> 5)] = b;
+    }
+    __syncthreads();
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < nw; ++k) {
+        sa += red[k];
+        sb += red[32 + k];
+    }
+    ra = sa;
+    rb = sb;
+}
+
+// 2-D DFT of three real n x n arrays (sg = -1) or inverse of three complex
+// spectra to real arrays (sg = +1, scaled by 1/n^2).
+__device__ void dft3_forward(const float *a0, const float *a1, const float *a2, float2 *T0,
+                             float2 *T1, float2 *T2, float2 *F0, float2 *F1, float2 *F2,
+                             const float2 *tw, int n) {
+    const int nt = n * n;
+    for (int k = threadIdx.x; k < 3 * nt; k += blockDim.x) {
+        const int which = k / nt, e = k - which * nt;
+        const int i = e / n, kx = e - (e / n) * n;
+        const float *a = which == 0 ? a0 : (which == 1 ? a1 : a2);
+        float2 acc = make_float2(0.f, 0.f);
+        for (int j = 0; j < n; ++j) {
+            const float2 wv = tw[(j * kx) % n];
+            const float v = a[i * n + j];
+            acc.x += v * wv.x;
+            acc.y += v * wv.y;
+        }
+        (which == 0 ? T0 : (which == 1 ? T1 : T2))[e] = acc;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * nt; k += blockDim.x) {
+        const int which = k / nt, e = k - which * nt;
+        const int ky = e / n, kx = e - (e / n) * n;
+        const float2 *T = which == 0 ? T0 : (which == 1 ? T1 : T2);
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i = 0; i < n; ++i) acc = c_add(acc, c_mul(T[i * n + kx], tw[(i * ky) % n]));
+        (which == 0 ? F0 : (which == 1 ? F1 : F2))[e] = acc;
+    }
+    __syncthreads();
+}
+
+__device__ void dft3_inverse(const float2 *F0, const float2 *F1, const float2 *F2, float2 *T0,
+                             float2 *T1, float2 *T2, float *o0, float *o1, float *o2,
+                             const float2 *tw, int n) {
+    const int nt = n * n;
+    for (int k = threadIdx.x; k < 3 * nt; k += blockDim.x) {
+        const int which = k / nt, e = k - which * nt;
+        const int i = e / n, kx = e - (e / n) * n;
+        const float2 *F = which == 0 ? F0 : (which == 1 ? F1 : F2);
+        float2 acc = make_float2(0.f, 0.f);
+        for (int ky = 0; ky < n; ++ky) acc = c_add(acc, c_mul(F[ky * n + kx], c_conj(tw[(i * ky) % n])));
+        (which == 0 ? T0 : (which == 1 ? T1 : T2))[e] = acc;
+    }
+    __syncthreads();
+    const float inv = 1.0f / (float)nt;
+    for (int k = threadIdx.x; k < 3 * nt; k += blockDim.x) {
+        const int which = k / nt, e = k - which * nt;
+        const int i = e / n, j = e - (e / n) * n;
+        const float2 *T = which == 0 ? T0 : (which == 1 ? T1 : T2);
+        float acc = 0.f;
+        for (int kx = 0; kx < n; ++kx) {
+            const float2 wv = c_conj(tw[(j * kx) % n]);
+            const float2 tv = T[i * n + kx];
+            acc += tv.x * wv.x - tv.y * wv.y;
+        }
+        (which == 0 ? o0 : (which == 1 ? o1 : o2))[e] = acc * inv;
+    }
+    __syncthreads();
+}
+
+size_t admm_smem_bytes(int R) {
+    const int nt = (2 * R + 1) * (2 * R + 1);
+    const size_t ntp = (nt + 3) & ~3;
+    return 26 * ntp * sizeof(float) + (6 * ntp + 64) * sizeof(float2) + 64 * sizeof(double) +
+           16;
+}
+
+__global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
+                                                    const double *__restrict__ zf, int R,
+                                                    ps_kernel_params p, float *kernel_out,
+                                                    int *info_iters, int *info_status,
+                                                    double *info_change) {
+    extern __shared__ __align__(16) unsigned char admm_sm[];
+    const int n = 2 * R + 1, nt = n * n;
+    const int ntp = (nt + 3) & ~3;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    double *red = reinterpret_cast<double *>(admm_sm);
+    float2 *cbase = reinterpret_cast<float2 *>(admm_sm + 64 * sizeof(double));
+    float2 *F0 = cbase, *F1 = F0 + ntp, *F2 = F1 + ntp, *T0 = F2 + ntp, *T1 = T0 + ntp,
+           *T2 = T1 + ntp, *tw = T2 + ntp;
+    float *fb = reinterpret_cast<float *>(tw + 64);
+    float *u = fb, *un = u + ntp, *p1 = un + ntp, *p2 = p1 + ntp, *x0 = p2 + ntp, *x1 = x0 + ntp,
+          *y0 = x1 + ntp, *y1 = y0 + ntp, *y2 = y1 + ntp, *y3 = y2 + ntp, *l10 = y3 + ntp,
+          *l11 = l10 + ntp, *l20 = l11 + ntp, *l21 = l20 + ntp, *l22 = l21 + ntp,
+          *l23 = l22 + ntp, *l3 = l23 + ntp, *z = l3 + ntp, *zs = z + ntp, *wv = zs + ntp,
+          *t0 = wv + ntp, *t1 = t0 + ntp, *t2 = t1 + ntp, *t3 = t2 + ntp, *t4 = t3 + ntp,
+          *b3s = t4 + ntp;
+    int *flag = reinterpret_cast<int *>(b3s + ntp);
+
+    const float a1 = p.alpha1 * p.mu1, a2 = p.alpha2 * p.mu2;
+    for (int k = tid; k < nt; k += nthr) {
+        u[k] = 1.0f / (float)nt;
+        z[k] = 1.0f / (float)nt;
+        zs[k] = (float)zf[k];
+        p1[k] = p2[k] = x0[k] = x1[k] = y0[k] = y1[k] = y2[k] = y3[k] = 0.f;
+        l10[k] = l11[k] = l20[k] = l21[k] = l22[k] = l23[k] = l3[k] = 0.f;
+    }
+    for (int k = tid; k < n; k += nthr) {
+        double sn, cs;
+        sincospi(-2.0 * (double)k / (double)n, &sn, &cs);
+        tw[k] = make_float2((float)cs, (float)sn);
+    }
+    __syncthreads();
+
+    int it = 0, status = PS_ERR_NOT_CONVERGED;
+    double change = 0.0;
+    auto at = [n](const float *a, int i, int j) {
+        return a[((i + n) % n) * n + ((j + n) % n)];
+    };
+    for (int t = 0; t < p.t_max; ++t) {
+        // 1-2. x and y by row-wise shrinkage (Eq. x_update, Eq. y_update)
+        for (int k = tid; k < nt; k += nthr) {
+            const int i = k / n, j = k - (k / n) * n;
+            const float g0 = at(u, i, j + 1) - u[k] - p1[k] + l10[k];
+            const float g1 = at(u, i + 1, j) - u[k] - p2[k] + l11[k];
+            float nr = sqrtf(g0 * g0 + g1 * g1);
+            float sc = nr > 1.0f / p.mu1 ? (nr - 1.0f / p.mu1) / nr : 0.0f;
+            x0[k] = g0 * sc;
+            x1[k] = g1 * sc;
+            const float m = 0.5f * (at(p1, i + 1, j) - p1[k] + at(p2, i, j + 1) - p2[k]);
+            const float e0 = at(p1, i, j + 1) - p1[k] + l20[k];
+            const float e1 = m + l21[k];
+            const float e2 = m + l22[k];
+            const float e3 = at(p2, i + 1, j) - p2[k] + l23[k];
+            nr = sqrtf(e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3);
+            sc = nr > 1.0f / p.mu2 ? (nr - 1.0f / p.mu2) / nr : 0.0f;
+            y0[k] = e0 * sc;
+            y1[k] = e1 * sc;
+            y2[k] = e2 * sc;
+            y3[k] = e3 * sc;
+            wv[k] = u[k] + l3[k];
+        }
+        __syncthreads();
+        // 3. z = P_S(z_f + Q (u + Lambda3)) (Eq. z_solution, then projection)
+        for (int k = tid; k < nt; k += nthr) {
+            float acc = zs[k];
+            for (int m = 0; m < nt; ++m) acc = fmaf(__ldg(Q + (size_t)m * nt + k), wv[m], acc);
+            t0[k] = acc;
+            reinterpret_cast<int *>(t1)[k] = 1;
+        }
+        // Euclidean projection onto the simplex by Michelot's exact active-set
+        // iteration (same projection as the sort-based method).
+        float tau = 0.f;
+        for (int pass = 0; pass <= nt; ++pass) {
+            __syncthreads();
+            double s = 0.0, cnt = 0.0;
+            for (int k = tid; k < nt; k += nthr)
+                if (reinterpret_cast<int *>(t1)[k]) {
+                    s += t0[k];
+                    cnt += 1.0;
+                }
+            double S, C;
+            block_sum2(s, cnt, red, S, C);
+            tau = (float)((1.0 - S) / C);
+            __syncthreads();
+            if (tid == 0) *flag = 0;
+            __syncthreads();
+            for (int k = tid; k < nt; k += nthr) {
+                int *act = reinterpret_cast<int *>(t1);
+                if (act[k] && !(t0[k] + tau > 0.f)) {
+                    act[k] = 0;
+                    *flag = 1;
+                }
+            }
+            __syncthreads();
+            if (*flag == 0) break;
+        }
+        for (int k = tid; k < nt; k += nthr) z[k] = fmaxf(t0[k] + tau, 0.f);
+        __syncthreads();
+        // 4. {u, p} (Appendix A, with + mu3 (z - Lambda3) in B1 and + mu3 in d1)
+        for (int k = tid; k < nt; k += nthr) {
+            t0[k] = x0[k] - l10[k];
+            t1[k] = x1[k] - l11[k];
+            t2[k] = y0[k] - l20[k];
+            t3[k] = 0.5f * ((y1[k] - l21[k]) + (y2[k] - l22[k]));
+            t4[k] = y3[k] - l23[k];
+        }
+        __syncthreads();
+        for (int k = tid; k < nt; k += nthr) {
+            const int i = k / n, j = k - (k / n) * n;
+            // DhT f (i,j) = f(i, j-1) - f(i,j);  DvT f (i,j) = f(i-1, j) - f(i,j)
+            const float b1 = a1 * ((at(t0, i, j - 1) - t0[k]) + (at(t1, i - 1, j) - t1[k])) +
+                             p.mu3 * (z[k] - l3[k]);
+            const float b2 = -a1 * t0[k] + a2 * ((at(t2, i, j - 1) - t2[k]) + (at(t3, i - 1, j) - t3[k]));
+            const float b3 = -a1 * t1[k] + a2 * ((at(t4, i - 1, j) - t4[k]) + (at(t3, i, j - 1) - t3[k]));
+            un[k] = b1;
+            wv[k] = b2;
+            b3s[k] = b3;
+        }
+        __syncthreads();
+        dft3_forward(un, wv, b3s, T0, T1, T2, F0, F1, F2, tw, n);
+        for (int k = tid; k < nt; k += nthr) {
+            const int ky = k / n, kx = k - (k / n) * n;
+            const float2 dh = make_float2(tw[kx].x - 1.0f, -tw[kx].y);   // exp(+2 pi i kx/n) - 1
+            const float2 dv = make_float2(tw[ky].x - 1.0f, -tw[ky].y);
+            const float ah = dh.x * dh.x + dh.y * dh.y, av = dv.x * dv.x + dv.y * dv.y;
+            const float2 d1 = make_float2(a1 * (ah + av) + p.mu3, 0.f);
+            const float2 d2 = make_float2(a1 + a2 * ah + 0.5f * a2 * av, 0.f);
+            const float2 d3 = make_float2(a1 + a2 * av + 0.5f * a2 * ah, 0.f);
+            const float2 d4 = make_float2(-a1 * dh.x, -a1 * dh.y);
+            const float2 d5 = make_float2(-a1 * dv.x, -a1 * dv.y);
+            const float2 d6 = c_mul(make_float2(0.5f * a2 * dh.x, -0.5f * a2 * dh.y), dv);
+            const float2 c4 = c_conj(d4), c5 = c_conj(d5), c6 = c_conj(d6);
+            const float2 B1 = F0[k], B2 = F1[k], B3 = F2[k];
+            const float2 den = det3c(d1, c4, c5, d4, d2, c6, d5, d6, d3);
+            const float2 uu = c_div(det3c(B1, c4, c5, B2, d2, c6, B3, d6, d3), den);
+            const float2 q1 = c_div(det3c(d1, B1, c5, d4, B2, c6, d5, B3, d3), den);
+            const float2 q2 = c_div(det3c(d1, c4, B1, d4, d2, B2, d5, d6, B3), den);
+            F0[k] = uu;
+            F1[k] = q1;
+            F2[k] = q2;
+        }
+        __syncthreads();
+        dft3_inverse(F0, F1, F2, T0, T1, T2, un, p1, p2, tw, n);
+        // 5-7. multiplier updates (Eq. subproblems), stop test
+        double dn = 0.0, nn = 0.0;
+        for (int k = tid; k < nt; k += nthr) {
+            const int i = k / n, j = k - (k / n) * n;
+            const float gu0 = at(un, i, j + 1) - un[k];
+            const float gu1 = at(un, i + 1, j) - un[k];
+            l10[k] += p.rho * (gu0 - p1[k] - x0[k]);
+            l11[k] += p.rho * (gu1 - p2[k] - x1[k]);
+            const float m = 0.5f * (at(p1, i + 1, j) - p1[k] + at(p2, i, j + 1) - p2[k]);
+            l20[k] += p.rho * (at(p1, i, j + 1) - p1[k] - y0[k]);
+            l21[k] += p.rho * (m - y1[k]);
+            l22[k] += p.rho * (m - y2[k]);
+            l23[k] += p.rho * (at(p2, i + 1, j) - p2[k] - y3[k]);
+            l3[k] += p.rho * (un[k] - z[k]);
+            const double d = (double)u[k] - (double)un[k];
+            dn += d * d;
+            nn += (double)un[k] * (double)un[k];
+        }
+        double DN, NN;
+        block_sum2(dn, nn, red, DN, NN);
+        __syncthreads();
+        for (int k = tid; k < nt; k += nthr) u[k] = un[k];
+        __syncthreads();
+        it = t + 1;
+        change = sqrt(DN / NN);
+        if (change < (double)p.th) {
+            status = PS_OK;
+            break;
+        }
+    }
+    for (int k = tid; k < nt; k += nthr) kernel_out[k] = z[k];
+    if (tid == 0) {
+        if (info_iters) *info_iters = it;
+        if (info_status) *info_status = status;
+        if (info_change) *info_change = change;
+    }
+}
+
+void launch_admm(const float *Q, const double *zf, int R, const ps_kernel_params &p,
+                 float *kernel_out, int *info_iters, int *info_status, double *info_change,
+                 cudaStream_t st) {
+    admm_kernel<<<1, 1024, admm_smem_bytes(R), st>>>(Q, zf, R, p, kernel_out, info_iters,
+                                                     info_status, info_change);
+}
+
+cudaError_t kest_set_attrs() {
+    return cudaFuncSetAttribute(admm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)admm_smem_bytes(kMaxR));
+}
+
+}  // namespace ps

@@ -1,0 +1,117 @@
+"""The C-ABI library loads and exports every entry point declared in
+include/*.h; host-side parts (defaults, workspace sizes, argument checks that
+return before any launch) behave as documented. No GPU needed."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from tests.golden.load import paper_parameters
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import importlib
+    importlib.import_module("paper_2103_09943_gb300.build").build()
+    from paper_2103_09943_gb300 import _lib
+    return _lib.load()
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(ps_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2103_09943_gb300 import _lib
+    names = declared_functions()
+    assert len(names) >= 15
+    so = os.path.join(ROOT, "paper_2103_09943_gb300", "_build", "libps.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (ps_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    # and the Python binding declares exactly the header's entry points
+    assert sorted(_lib.SIGNATURES) == names
+
+
+def test_defaults_are_the_paper_values(lib):
+    from paper_2103_09943_gb300._lib import HrmsParams, KernelParams
+    p = paper_parameters()
+    kp = KernelParams()
+    lib.ps_default_kernel_params(ctypes.byref(kp))
+    for name in ("lambda_omega", "alpha1", "alpha2", "mu1", "mu2", "mu3", "rho", "t_max"):
+        assert getattr(kp, name) == pytest.approx(p[name], rel=1e-6), name
+    assert kp.th == pytest.approx(p["th"], rel=1e-6)
+    hp = HrmsParams()
+    lib.ps_default_hrms_params(ctypes.byref(hp))
+    assert hp.lambda_ == pytest.approx(p["lambda"], rel=1e-6)
+    assert hp.r == p["r"]
+
+
+def test_workspace_size(lib):
+    assert lib.ps_workspace_size(4, 256, 256, 4, 4, None) > 4 * 256 * 256 * 4 * 4
+    assert lib.ps_workspace_size(8, 1024, 1024, 4, 8, None) > 0
+    assert lib.ps_workspace_size(4, 256, 250, 4, 4, None) == 0      # W % c
+    assert lib.ps_workspace_size(4, 256, 256, 1, 4, None) == 0      # ratio < 2
+    assert lib.ps_workspace_size(0, 256, 256, 4, 4, None) == 0      # no bands
+    assert lib.ps_workspace_size(4, 16, 16, 4, 9, None) == 0       # kernel > image
+
+
+def test_status_strings(lib):
+    for s in range(9):
+        assert lib.ps_status_string(s)
+    assert lib.ps_status_string(0) == b"ok"
+
+
+def test_argument_errors_return_before_launch(lib):
+    from paper_2103_09943_gb300._lib import HrmsParams, KernelParams
+    hp = HrmsParams()
+    lib.ps_default_hrms_params(ctypes.byref(hp))
+    kp = KernelParams()
+    lib.ps_default_kernel_params(ctypes.byref(kp))
+    fake = ctypes.c_void_p(0x1000)
+    # shape: H not a multiple of the ratio
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 250, 256, 4, 4, ctypes.byref(hp), None, fake,
+                           None, None, fake, 1 << 30, None)
+    assert st == 2
+    # FFT sizes must be 2^a 3^b
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 260, 260, 4, 4, ctypes.byref(hp), None, fake,
+                           None, None, fake, 1 << 30, None)
+    assert st == 8
+    # bad parameter
+    bad = HrmsParams.from_buffer_copy(hp)
+    bad.eps = 0.0
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
+                           None, None, fake, 1 << 30, None)
+    assert st == 1
+    # null output
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(hp), None, None,
+                           None, None, fake, 1 << 30, None)
+    assert st == 1
+    # workspace too small / misaligned
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(hp), None, fake,
+                           None, None, fake, 1024, None)
+    assert st == 4
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(hp), None, fake,
+                           None, None, ctypes.c_void_p(0x1010), 1 << 30, None)
+    assert st == 4
+    bk = KernelParams.from_buffer_copy(kp)
+    bk.mu3 = -1.0
+    st = lib.ps_estimate_kernel(fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bk), None, fake,
+                                None, None, fake, 1 << 30, None)
+    assert st == 1
+    st = lib.ps_pansharpen(fake, fake, 4, 256, 256, 4, 17, ctypes.byref(kp), ctypes.byref(hp),
+                           fake, None, None, None, fake, 1 << 30, None)
+    assert st == 1                                                  # R > 16

@@ -1,0 +1,129 @@
+"""GPU parity of Algorithm 2 (the per-band HRMS solve) against the FP64
+oracle: the Z step alone, then Z0 and Z of ps_solve_hrms, on the 4-band
+256 x 256 scene and on smaller ragged and odd-band cases; warm start;
+device-side statuses."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2103_09943_gb300 import api, ops
+from tests.gpu_util import rel, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+# Plain FP32 form: FP32 vectors and operators, FP64 reductions. The CG stops
+# at a recursive relative residual of 1e-7; the bar against the oracle is
+# rel-L2 <= 1e-5 per band.
+PLAIN_TOL = 1e-5
+
+
+def _scene(cfg, **kw):
+    return synth.make_scene(replace(cfg, **kw) if kw else cfg)
+
+
+def test_zstep_given_oracle_z0(cuda):
+    sc = _scene(synth.CONFIGS["c0"])
+    cfg = sc["config"]
+    c, r, lam = cfg.ratio, 1, 2e-4
+    u = sc["kernel"].astype(np.float64)
+    hp = oracle.HrmsParams(tol=1e-11)
+    st = oracle.pan_stats(sc["pan"], r, hp.eps)
+    I, mu, s = (a.astype(np.float32) for a in (st.I, st.mu, st.s))
+    for exact in (False, True):
+        hp.exact_weight = exact
+        for b in (0, 3):
+            ob = oracle.solve_band(sc["lrms"][b], u, c, st, hp)
+            z0 = ob["Z0"].astype(np.float32)
+            gz = ops.zstep(to_dev(sc["lrms"][b:b + 1], cuda), to_dev(z0[None], cuda),
+                           to_dev(sc["kernel"], cuda), c, to_dev(I, cuda), to_dev(mu, cuda),
+                           to_dev(s, cuda), r, lam, exact_weight=exact)
+            assert rel(to_np(gz)[0], ob["Z"]) < PLAIN_TOL
+
+
+@pytest.fixture(scope="module")
+def c0_oracle():
+    sc = _scene(synth.CONFIGS["c0"])
+    cfg = sc["config"]
+    ref = oracle.solve_hrms(sc["lrms"], sc["pan"], sc["kernel"].astype(np.float64),
+                            cfg.ratio, oracle.HrmsParams(tol=1e-11), threads=4)
+    return sc, ref
+
+
+def test_solve_hrms_c0_plain_fp32(cuda, c0_oracle):
+    sc, ref = c0_oracle
+    cfg = sc["config"]
+    hp = api.default_hrms_params(tol=1e-7, max_iter=5000)
+    Z, Z0, info = api.solve_hrms(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                 to_dev(sc["kernel"], cuda), cfg.ratio, hp, want_z0=True)
+    Z, Z0 = to_np(Z), to_np(Z0)
+    assert all(s == 0 for s in info.status), info
+    for b in range(cfg.bands):
+        assert rel(Z0[b], ref["Z0"][b]) < PLAIN_TOL, (b, info)
+        assert rel(Z[b], ref["Z"][b]) < PLAIN_TOL, (b, info)
+
+
+def test_solve_hrms_default_tolerance_meets_1e3(cuda, c0_oracle):
+    sc, ref = c0_oracle
+    cfg = sc["config"]
+    Z, _, info = api.solve_hrms(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                to_dev(sc["kernel"], cuda), cfg.ratio)
+    Z = to_np(Z)
+    for b in range(cfg.bands):
+        assert rel(Z[b], ref["Z"][b]) < 1e-3
+
+
+def test_warm_start_from_solution(cuda, c0_oracle):
+    sc, ref = c0_oracle
+    cfg = sc["config"]
+    hp = api.default_hrms_params(tol=1e-7)
+    zi = to_dev(ref["Z0"], cuda)
+    Z, Z0, info = api.solve_hrms(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                 to_dev(sc["kernel"], cuda), cfg.ratio, hp, z_init=zi,
+                                 want_z0=True)
+    assert max(info.iters) < 60, info
+    assert max(rel(to_np(Z0)[b], ref["Z0"][b]) for b in range(cfg.bands)) < PLAIN_TOL
+
+
+@pytest.mark.parametrize("N,H,W,c,R,r", [(3, 144, 96, 4, 5, 1), (1, 96, 96, 2, 3, 2),
+                                         (2, 72, 108, 3, 4, 1)])
+def test_solve_hrms_ragged_and_odd(cuda, N, H, W, c, R, r):
+    base = synth.CONFIGS["c0"]
+    sc = _scene(base, bands=N, H=H, W=W, ratio=c, R=R, shapes=15, seed=40 + N)
+    u = sc["kernel"].astype(np.float64)
+    ref = oracle.solve_hrms(sc["lrms"], sc["pan"], u, c, oracle.HrmsParams(r=r, tol=1e-11),
+                            threads=3)
+    hp = api.default_hrms_params(tol=1e-7, r=r, max_iter=5000)
+    Z, Z0, info = api.solve_hrms(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                 to_dev(sc["kernel"], cuda), c, hp, want_z0=True)
+    Z, Z0 = to_np(Z), to_np(Z0)
+    for b in range(N):
+        assert rel(Z0[b], ref["Z0"][b]) < PLAIN_TOL, (b, info)
+        assert rel(Z[b], ref["Z"][b]) < PLAIN_TOL, (b, info)
+
+
+def test_status_not_converged_and_zero_band(cuda):
+    sc = _scene(synth.CONFIGS["c0"])
+    cfg = sc["config"]
+    X = sc["lrms"].copy()
+    X[1] = 0.0                                  # b = 0: done at once, Z = 0
+    hp = api.default_hrms_params(tol=1e-12, max_iter=3)
+    Z, _, info = api.solve_hrms(to_dev(X, cuda), to_dev(sc["pan"], cuda),
+                                to_dev(sc["kernel"], cuda), cfg.ratio, hp)
+    assert info.status[0] == 5 and info.iters[0] == 3
+    assert info.status[1] == 0 and info.iters[1] == 0
+    assert np.all(to_np(Z)[1] == 0.0)
+
+
+def test_status_nonfinite_input(cuda):
+    sc = _scene(synth.CONFIGS["c0"])
+    cfg = sc["config"]
+    X = sc["lrms"].copy()
+    X[2, 5, 7] = np.nan
+    Z, _, info = api.solve_hrms(to_dev(X, cuda), to_dev(sc["pan"], cuda),
+                                to_dev(sc["kernel"], cuda), cfg.ratio)
+    assert info.status[2] == 6
+    assert info.status[0] == 0
