@@ -268,7 +268,7 @@ def run_gpu(args):
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
     kp = api.default_kernel_params()
-    hp = api.default_hrms_params()
+    hp = api.default_hrms_params(host_loop=1 if args.cg_loop == "host" else 0)
     ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev)
     Z = torch.empty((cfg.bands, cfg.H, cfg.W), dtype=torch.float32, device=dev)
     K = torch.empty((cfg.n, cfg.n), dtype=torch.float32, device=dev)
@@ -363,7 +363,7 @@ def run_gpu(args):
             "config": {"workload": workload_name(cfg), "scenes_per_rank": 1,
                        "parallelism": f"replicas x{world} (independent scenes)",
                        "l2": "flushed between timed steps (256 MiB write)",
-                       "cg_tol": hp.tol, "cg_iters": binfo.iters,
+                       "cg_tol": hp.tol, "cg_iters": binfo.iters, "cg_loop": args.cg_loop,
                        "admm_iters": kinfo.iters},
             "wall_s_timed_region": wall,
             "e2e": {"value": throughput(units, world, e2e_ms * 1e-3), "unit": UNIT,
@@ -389,9 +389,12 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--r", type=int, default=1)
-    ap.add_argument("--cpu-crop", type=int, default=256)
-    ap.add_argument("--ref-crop", type=int, default=128)
+    ap.add_argument("--cpu-crop", type=int, default=128)
+    ap.add_argument("--ref-crop", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cg-loop", default="graph", choices=["graph", "host"],
+                    help="host: launch the CG iterations from the host (for profilers "
+                         "that cannot see inside conditional graphs)")
     return ap.parse_args(argv)
 
 

@@ -76,6 +76,12 @@ typedef struct ps_hrms_params {
     int exact_weight;   /* 0: the Z step of Eq. Z_solution uses lambda as
                            printed; 1: lambda (2r+1)^2, the exact minimiser of
                            Eq. pansharp for fixed A, C                         */
+    int host_loop;      /* 0: the CG loop runs on the device as one CUDA graph
+                           with a conditional while node (default); 1: the
+                           host launches the same iteration kernels itself and
+                           reads the stop flag every 8 iterations, for tools
+                           that cannot look inside conditional graphs
+                           (profilers). Results are identical.              */
 } ps_hrms_params;
 
 /* Per-band result of the Z0 conjugate-gradient solve. */

@@ -49,11 +49,12 @@ ps_status ps_op_apply_z0(const float *d_z, int N, int H, int W, int ratio,
 
 /* Guided filter of q_b with guide I (Eq. ac_h_compute): per window
  * a = (mean(I q) - mu mean(q)) s, c = mean(q) - a mu; out = mean(a) I +
- * mean(c), means over the windows containing each pixel. N x H x W. */
+ * mean(c), means over the windows containing each pixel. N x H x W.
+ * Workspace: at least 16 H W bytes, 256-byte aligned. */
 ps_status ps_op_guided_filter(const float *d_q, int N, int H, int W,
                               const float *d_I, const float *d_mu,
                               const float *d_s, int r, float *d_out,
-                              void *stream);
+                              void *d_ws, size_t ws_bytes, void *stream);
 
 /* Z step of Algorithm 2 (Eq. Z_solution) for every band, given Z0:
  * L-hat = guided filter of L Z0_b, then Z_b solves

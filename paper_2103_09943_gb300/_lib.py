@@ -23,7 +23,8 @@ class KernelParams(ctypes.Structure):
 class HrmsParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_float), ("r", ctypes.c_int),
                 ("eps", ctypes.c_float), ("tol", ctypes.c_float),
-                ("max_iter", ctypes.c_int), ("exact_weight", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("exact_weight", ctypes.c_int),
+                ("host_loop", ctypes.c_int)]
 
 
 class BandInfo(ctypes.Structure):
@@ -58,7 +59,7 @@ SIGNATURES = {
     "ps_op_blur_decimate_adj": (_I, [_P, _I, _I, _I, _I, _P, _I, _P, _P]),
     "ps_op_pan_stats": (_I, [_P, _I, _I, _I, _F, _P, _P, _P, _P]),
     "ps_op_apply_z0": (_I, [_P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _I, _F, _P, _P, _Z, _P]),
-    "ps_op_guided_filter": (_I, [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P]),
+    "ps_op_guided_filter": (_I, [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P, _Z, _P]),
     "ps_op_zstep": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _I, _F, _I, _P, _P, _Z,
                          _P]),
     "ps_op_omega": (_I, [_P, _P, _I, _I, _I, _I, _I, _F, _P, _P, _Z, _P]),

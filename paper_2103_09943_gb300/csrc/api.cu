@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -24,13 +25,13 @@ size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 // Workspace layout (offsets from the 256-byte aligned base).
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t stats_I, stats_mu, stats_s;  // 3 x HW f32
+    size_t st4;                         // HW float4: packed PAN statistics (I, mu, s)
     size_t xbuf;                        // N HW f32 (Z0 when the caller gives none)
     size_t r, pA, pB, ap;               // N HW f32 each; [r,pA] and [pB,ap] double as
                                         // the complex FFT buffers
     size_t v;                           // N hw f32
-    size_t bhat;                        // HW float2
-    size_t twW, twH;                    // twiddles
+    size_t bhat;                        // HW double2 (kernel spectrum)
+    size_t twW32, twH32, twW64, twH64;  // twiddles
     size_t bands, glob;                 // CG scalars
     size_t bvec, f, G, omega, lags, ete, etf, zf, Q, kern, kinfo;
     size_t total;
@@ -47,19 +48,21 @@ bool make_layout(int N, int H, int W, int c, int R, Layout *L) {
         o = align_up(o + bytes);
         return at;
     };
-    L->stats_I = take(HW * 4);
-    L->stats_mu = take(HW * 4);
-    L->stats_s = take(HW * 4);
+    L->st4 = take(HW * 16);
     L->xbuf = take((size_t)N * HW * 4);
-    // r and pA contiguous, pB and ap contiguous (complex work buffers)
-    L->r = take((size_t)N * HW * 4 * 2);
+    // r and pA contiguous, pB and ap contiguous: each pair doubles as one
+    // complex FFT buffer of ceil(N/2) FP64 images
+    const size_t pair = std::max((size_t)N * HW * 8, (size_t)((N + 1) / 2) * HW * 16);
+    L->r = take(pair);
     L->pA = L->r + (size_t)N * HW * 4;
-    L->pB = take((size_t)N * HW * 4 * 2);
+    L->pB = take(pair);
     L->ap = L->pB + (size_t)N * HW * 4;
     L->v = take((size_t)N * hw * 4);
-    L->bhat = take(HW * 8);
-    L->twW = take((size_t)W * 8);
-    L->twH = take((size_t)H * 8);
+    L->bhat = take(HW * 16);
+    L->twW32 = take((size_t)W * 8);
+    L->twH32 = take((size_t)H * 8);
+    L->twW64 = take((size_t)W * 16);
+    L->twH64 = take((size_t)H * 16);
     L->bands = take((size_t)N * sizeof(CgBand));
     L->glob = take(sizeof(CgGlobal));
     L->bvec = take(hw * 4);
@@ -181,7 +184,8 @@ struct CgLoopArgs {
     int dev;
     int N, H, W, c, R, r;
     float lam;
-    const float *u, *I, *mu, *s;
+    const float *u;
+    const float4 *st4;
     float *x, *rv, *pA, *pB, *ap, *v;
     CgBand *bands;
     CgGlobal *g;
@@ -196,14 +200,11 @@ std::vector<CgGraph> g_graphs;
 
 void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, int use_cond,
                        cudaGraphConditionalHandle h, cudaStream_t st) {
-    const size_t HW = (size_t)a.H * a.W;
     launch_db(p_old, a.rv, p_new, a.bands, a.g, 1, a.N, a.H, a.W, a.c, a.u, a.R, a.v, st);
     LlpArgs la = {};
     la.in = p_new;
     la.lr = a.v;
-    la.I = a.I;
-    la.mu = a.mu;
-    la.s = a.s;
+    la.st4 = a.st4;
     la.u = a.u;
     la.R = a.R;
     la.c = a.c;
@@ -215,8 +216,8 @@ void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, in
     la.bands = a.bands;
     la.g = a.g;
     la.cg = 1;
-    launch_llp(la, LLP_APPLY, a.r, a.N, st);
-    launch_cg_update(a.x, a.rv, p_new, a.ap, a.N, HW, a.bands, a.g, st);
+    launch_llp(la, LLP_CGQ, a.r, a.N, st);
+    launch_cg_update(a.x, a.rv, p_new, a.ap, a.v, a.u, a.R, a.c, a.N, a.H, a.W, a.bands, a.g, st);
     launch_cg_control(a.bands, a.g, a.N, use_cond, h, st);
 }
 
@@ -286,24 +287,25 @@ ps_status run_zstep(const Ws &ws, const float *lrms, const float *z0, const floa
     if (!fft_make_plan(W, &pw) || !fft_make_plan(H, &ph)) return PS_ERR_UNSUPPORTED;
     const size_t HW = (size_t)H * W;
     const int nimg = (N + 1) / 2;
-    float2 *cbuf = ws.at<float2>(ws.L.r);
-    float2 *ctmp = ws.at<float2>(ws.L.pB);
-    float2 *bhat = ws.at<float2>(ws.L.bhat);
-    float2 *twW = ws.at<float2>(ws.L.twW), *twH = ws.at<float2>(ws.L.twH);
-    launch_fft_twiddles(W, twW, st);
-    launch_fft_twiddles(H, twH, st);
-    // kernel spectrum, transposed layout [kx][ky]
-    launch_kernel_embed(u, R, H, W, cbuf, st);
-    launch_fft_rows(cbuf, pw, H, twW, 0, 1.0f, nullptr, N, HW, st);
-    launch_transpose(cbuf, bhat, H, W, 1, st);
-    launch_fft_rows(bhat, ph, W, twH, 0, 1.0f, nullptr, N, HW, st);
+    double2 *cbuf64 = ws.at<double2>(ws.L.r);
+    double2 *ctmp64 = ws.at<double2>(ws.L.pB);
+    float2 *sol32 = ws.at<float2>(ws.L.r);     // reuses cbuf64 once it is consumed
+    float2 *ctmp32 = ws.at<float2>(ws.L.pB);   // reuses ctmp64 once it is consumed
+    double2 *bhat = ws.at<double2>(ws.L.bhat);
+    float2 *twW32 = ws.at<float2>(ws.L.twW32), *twH32 = ws.at<float2>(ws.L.twH32);
+    double2 *twW64 = ws.at<double2>(ws.L.twW64), *twH64 = ws.at<double2>(ws.L.twH64);
+    launch_fft_twiddles(W, twW32, twW64, st);
+    launch_fft_twiddles(H, twH32, twH64, st);
+    // kernel spectrum (FP64), transposed layout [kx][ky]
+    launch_kernel_embed(u, R, H, W, cbuf64, st);
+    launch_fft_rows64(cbuf64, pw, H, twW64, st);
+    launch_transpose64(cbuf64, bhat, H, W, 1, st);
+    launch_fft_rows64(bhat, ph, W, twH64, st);
     // right-hand side B^T D^T X + lam' L L-hat, packed two bands per image
     LlpArgs la = {};
     la.in = z0;
     la.lr = lrms;
-    la.I = ws.at<float>(ws.L.stats_I);
-    la.mu = ws.at<float>(ws.L.stats_mu);
-    la.s = ws.at<float>(ws.L.stats_s);
+    la.st4 = ws.at<float4>(ws.L.st4);
     la.u = u;
     la.R = R;
     la.c = c;
@@ -311,15 +313,16 @@ ps_status run_zstep(const Ws &ws, const float *lrms, const float *z0, const floa
     la.W = W;
     la.N = N;
     la.lam = lam_z;
-    la.cout = cbuf;
+    la.cout = cbuf64;
     launch_llp(la, LLP_ZRHS, r, N, st);
-    launch_fft_rows(cbuf, pw, nimg * H, twW, 0, 1.0f, nullptr, N, HW, st);
-    launch_transpose(cbuf, ctmp, H, W, nimg, st);
-    launch_fft_rows(ctmp, ph, nimg * W, twH, 0, 1.0f, nullptr, N, HW, st);
-    launch_alias_solve(ctmp, bhat, nimg, H, W, c, lam_z, st);
-    launch_fft_rows(ctmp, ph, nimg * W, twH, 1, 1.0f, nullptr, N, HW, st);
-    launch_transpose(ctmp, cbuf, W, H, nimg, st);
-    launch_fft_rows(cbuf, pw, nimg * H, twW, 1, 1.0f, out, N, HW, st);
+    // forward 2-D FFT (FP64), group solve, inverse 2-D FFT (FP32)
+    launch_fft_rows64(cbuf64, pw, nimg * H, twW64, st);
+    launch_transpose64(cbuf64, ctmp64, H, W, nimg, st);
+    launch_fft_rows64(ctmp64, ph, nimg * W, twH64, st);
+    launch_alias_solve(ctmp64, bhat, sol32, nimg, H, W, c, lam_z, st);
+    launch_fft_rows32(sol32, ph, nimg * W, twH32, 1, nullptr, N, HW, st);
+    launch_transpose32(sol32, ctmp32, W, H, nimg, st);
+    launch_fft_rows32(ctmp32, pw, nimg * H, twW32, 1, out, N, HW, st);
     return last_launch();
 }
 
@@ -350,6 +353,7 @@ void ps_default_hrms_params(ps_hrms_params *p) {
     p->tol = 1e-6f;
     p->max_iter = 5000;
     p->exact_weight = 0;
+    p->host_loop = 0;
 }
 
 const char *ps_status_string(int s) {
@@ -452,15 +456,14 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
     cudaStream_t st = (cudaStream_t)stream;
     const int c = ratio;
     const size_t HW = (size_t)H * W;
-    float *I = ws.at<float>(ws.L.stats_I), *mu = ws.at<float>(ws.L.stats_mu),
-          *sv = ws.at<float>(ws.L.stats_s);
+    float4 *st4 = ws.at<float4>(ws.L.st4);
     float *x = d_z0 ? d_z0 : ws.at<float>(ws.L.xbuf);
     float *rv = ws.at<float>(ws.L.r), *pA = ws.at<float>(ws.L.pA), *pB = ws.at<float>(ws.L.pB),
           *ap = ws.at<float>(ws.L.ap), *v = ws.at<float>(ws.L.v);
     CgBand *bands = ws.at<CgBand>(ws.L.bands);
     CgGlobal *g = ws.at<CgGlobal>(ws.L.glob);
 
-    launch_pan_stats(d_pan, H, W, p->r, p->eps, I, mu, sv, st);
+    launch_pan_stats(d_pan, H, W, p->r, p->eps, nullptr, nullptr, nullptr, st4, st);
     launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
     if (d_z_init) {
         launch_db(d_z_init, nullptr, nullptr, nullptr, nullptr, 0, N, H, W, c, d_kernel, R, v,
@@ -468,9 +471,7 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
         LlpArgs la = {};
         la.in = d_z_init;
         la.lr = v;
-        la.I = I;
-        la.mu = mu;
-        la.s = sv;
+        la.st4 = st4;
         la.u = d_kernel;
         la.R = R;
         la.c = c;
@@ -489,12 +490,29 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
     memset(&a, 0, sizeof(a));
     cudaGetDevice(&a.dev);
     a.N = N; a.H = H; a.W = W; a.c = c; a.R = R; a.r = p->r; a.lam = p->lambda;
-    a.u = d_kernel; a.I = I; a.mu = mu; a.s = sv;
+    a.u = d_kernel; a.st4 = st4;
     a.x = x; a.rv = rv; a.pA = pA; a.pB = pB; a.ap = ap; a.v = v;
     a.bands = bands; a.g = g;
-    cudaGraphExec_t exec;
-    if ((s = get_cg_graph(a, capture, &exec)) != PS_OK) return s;
-    if (cudaGraphLaunch(exec, st) != cudaSuccess) return PS_ERR_CUDA;
+    if (p->host_loop) {
+        // same kernels, launched by the host; the stop flag is read every 8
+        // iterations, and the loop is bounded by max_iter whatever it says
+        int stop = 0;
+        for (int it = 0; it < p->max_iter + 2 && !stop; it += 2) {
+            enqueue_iteration(a, pA, pB, 0, 0, st);
+            enqueue_iteration(a, pB, pA, 0, 0, st);
+            if ((it & 7) == 6 || it + 2 >= p->max_iter + 2) {
+                if (cudaMemcpyAsync(&stop, &g->stop, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+                        cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess)
+                    return PS_ERR_CUDA;
+            }
+        }
+        if ((s = last_launch()) != PS_OK) return s;
+    } else {
+        cudaGraphExec_t exec;
+        if ((s = get_cg_graph(a, capture, &exec)) != PS_OK) return s;
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) return PS_ERR_CUDA;
+    }
 
     const float lam_z = p->lambda * (p->exact_weight ? (float)((2 * p->r + 1) * (2 * p->r + 1)) : 1.0f);
     if ((s = run_zstep(ws, d_lrms, x, d_kernel, N, H, W, c, R, p->r, lam_z, d_hrms, st)) != PS_OK)
@@ -563,7 +581,7 @@ ps_status ps_op_pan_stats(const float *d_pan, int H, int W, int r, float eps, fl
     if (!d_pan || !d_I || !d_mu || !d_s) return PS_ERR_INVALID_ARG;
     ps_status s;
     if ((s = ensure_device(nullptr)) != PS_OK) return s;
-    launch_pan_stats(d_pan, H, W, r, eps, d_I, d_mu, d_s, (cudaStream_t)stream);
+    launch_pan_stats(d_pan, H, W, r, eps, d_I, d_mu, d_s, nullptr, (cudaStream_t)stream);
     return last_launch();
 }
 
@@ -580,13 +598,13 @@ ps_status ps_op_apply_z0(const float *d_z, int N, int H, int W, int ratio,
     if ((s = ensure_device(nullptr)) != PS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     float *v = ws.at<float>(ws.L.v);
+    float4 *st4 = ws.at<float4>(ws.L.st4);
+    launch_pack_stats(d_I, d_mu, d_s, (size_t)H * W, st4, st);
     launch_db(d_z, nullptr, nullptr, nullptr, nullptr, 0, N, H, W, ratio, d_kernel, R, v, st);
     LlpArgs la = {};
     la.in = d_z;
     la.lr = v;
-    la.I = d_I;
-    la.mu = d_mu;
-    la.s = d_s;
+    la.st4 = st4;
     la.u = d_kernel;
     la.R = R;
     la.c = ratio;
@@ -601,17 +619,19 @@ ps_status ps_op_apply_z0(const float *d_z, int N, int H, int W, int ratio,
 
 ps_status ps_op_guided_filter(const float *d_q, int N, int H, int W, const float *d_I,
                               const float *d_mu, const float *d_s, int r, float *d_out,
-                              void *stream) {
+                              void *d_ws, size_t ws_bytes, void *stream) {
     if (N < 1 || N > kMaxBands || H < 1 || W < 1 || r < 1 || r > kMaxWinR)
         return PS_ERR_INVALID_ARG;
     if (!d_q || !d_I || !d_mu || !d_s || !d_out) return PS_ERR_INVALID_ARG;
     ps_status s;
+    if (!d_ws || ((uintptr_t)d_ws) % kAlign) return PS_ERR_WORKSPACE;
+    if (ws_bytes < (size_t)H * W * 16) return PS_ERR_WORKSPACE;
     if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    float4 *st4 = static_cast<float4 *>(d_ws);
+    launch_pack_stats(d_I, d_mu, d_s, (size_t)H * W, st4, (cudaStream_t)stream);
     LlpArgs la = {};
     la.in = d_q;
-    la.I = d_I;
-    la.mu = d_mu;
-    la.s = d_s;
+    la.st4 = st4;
     la.H = H;
     la.W = W;
     la.N = N;
@@ -636,14 +656,8 @@ ps_status ps_op_zstep(const float *d_lrms, const float *d_z0, int N, int H, int 
     if ((s = ensure_device(nullptr)) != PS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t HW = (size_t)H * W;
-    // the Z step reads the statistics from the workspace
-    if (cudaMemcpyAsync(ws.at<float>(ws.L.stats_I), d_I, HW * 4, cudaMemcpyDeviceToDevice, st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(ws.at<float>(ws.L.stats_mu), d_mu, HW * 4, cudaMemcpyDeviceToDevice,
-                        st) != cudaSuccess ||
-        cudaMemcpyAsync(ws.at<float>(ws.L.stats_s), d_s, HW * 4, cudaMemcpyDeviceToDevice, st) !=
-            cudaSuccess)
-        return PS_ERR_CUDA;
+    // the Z step reads the statistics, packed, from the workspace
+    launch_pack_stats(d_I, d_mu, d_s, HW, ws.at<float4>(ws.L.st4), st);
     const float lam_z = lambda * (exact_weight ? (float)((2 * r + 1) * (2 * r + 1)) : 1.0f);
     return run_zstep(ws, d_lrms, d_z0, d_kernel, N, H, W, ratio, R, r, lam_z, d_z, st);
 }

@@ -26,7 +26,8 @@ __host__ __device__ __forceinline__ int wrapi(int i, int n) {
 struct CgBand {
     double rr;       // r^T r of the current residual
     double bb;       // b^T b
-    double pAp;      // accumulator of p^T A p (zeroed after use)
+    double pAp;      // accumulator of p^T (lam L^T M L) p (zeroed after use)
+    double vv;       // accumulator of ||D B p||^2 = p^T B^T D^T D B p (zeroed after use)
     double rr_new;   // accumulator of the next r^T r (zeroed after use)
     double alpha;
     double beta;

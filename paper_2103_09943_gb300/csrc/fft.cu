@@ -11,6 +11,12 @@
 // between; the spectrum is kept in transposed layout [kx][ky]. Two real
 // bands are packed as the real and imaginary parts of one complex image:
 // the operator has a real kernel, so the two solves do not mix.
+//
+// Precision: the operator amplifies relative errors of its right-hand side
+// spectrum by roughly its condition number, so the forward transforms (of the
+// right-hand side and of the kernel) and the group solve run in FP64; the
+// solution spectrum is rounded to FP32 (harmless: the inverse transform does
+// not amplify) and the inverse transforms run in FP32.
 #include <math.h>
 
 #include "common.cuh"
@@ -30,117 +36,149 @@ bool fft_make_plan(int L, FftPlan *plan) {
     return true;
 }
 
-// tw[k] = exp(-2 pi i k / L), computed in FP64 and rounded once.
-__global__ void fft_twiddle_kernel(int L, float2 *tw) {
+// Twiddles tw[k] = exp(-2 pi i k / L), computed in FP64; the FP32 table is
+// the FP64 one rounded once.
+__global__ void fft_twiddle_kernel(int L, float2 *tw32, double2 *tw64) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L) return;
     double sn, cs;
     sincospi(-2.0 * (double)k / (double)L, &sn, &cs);
-    tw[k] = make_float2((float)cs, (float)sn);
+    tw64[k] = make_double2(cs, sn);
+    tw32[k] = make_float2((float)cs, (float)sn);
 }
 
-void launch_fft_twiddles(int L, float2 *tw, cudaStream_t st) {
-    fft_twiddle_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, tw);
+void launch_fft_twiddles(int L, float2 *tw32, double2 *tw64, cudaStream_t st) {
+    fft_twiddle_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, tw32, tw64);
 }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+template <class T2> struct Cplx;
+template <> struct Cplx<float2> {
+    using R = float;
+    static __device__ __forceinline__ float2 make(float x, float y) { return make_float2(x, y); }
+};
+template <> struct Cplx<double2> {
+    using R = double;
+    static __device__ __forceinline__ double2 make(double x, double y) { return make_double2(x, y); }
+};
+
+template <class T2>
+__device__ __forceinline__ T2 cmulT(T2 a, T2 b) {
+    return Cplx<T2>::make(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
 // In-place radix-R DFT of v with exponent sign `sg` (-1 forward, +1 inverse).
-template <int R>
-__device__ __forceinline__ void dft_small(float2 *v, float sg);
+template <int R, class T2>
+struct Dft;
 
-template <>
-__device__ __forceinline__ void dft_small<2>(float2 *v, float) {
-    const float2 a = v[0], b = v[1];
-    v[0] = make_float2(a.x + b.x, a.y + b.y);
-    v[1] = make_float2(a.x - b.x, a.y - b.y);
-}
+template <class T2>
+struct Dft<2, T2> {
+    static __device__ __forceinline__ void run(T2 *v, typename Cplx<T2>::R) {
+        const T2 a = v[0], b = v[1];
+        v[0] = Cplx<T2>::make(a.x + b.x, a.y + b.y);
+        v[1] = Cplx<T2>::make(a.x - b.x, a.y - b.y);
+    }
+};
 
-template <>
-__device__ __forceinline__ void dft_small<4>(float2 *v, float sg) {
-    // exp(sg * 2 pi i / 4) = (0, sg)
-    const float2 a0 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
-    const float2 a1 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
-    const float2 b0 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
-    const float2 b1 = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);
-    // (0, sg) * b1 = (-sg b1.y, sg b1.x)
-    const float2 jb1 = make_float2(-sg * b1.y, sg * b1.x);
-    v[0] = make_float2(a0.x + b0.x, a0.y + b0.y);
-    v[2] = make_float2(a0.x - b0.x, a0.y - b0.y);
-    v[1] = make_float2(a1.x + jb1.x, a1.y + jb1.y);
-    v[3] = make_float2(a1.x - jb1.x, a1.y - jb1.y);
-}
+template <class T2>
+struct Dft<4, T2> {
+    static __device__ __forceinline__ void run(T2 *v, typename Cplx<T2>::R sg) {
+        // exp(sg 2 pi i / 4) = (0, sg)
+        const T2 a0 = Cplx<T2>::make(v[0].x + v[2].x, v[0].y + v[2].y);
+        const T2 a1 = Cplx<T2>::make(v[0].x - v[2].x, v[0].y - v[2].y);
+        const T2 b0 = Cplx<T2>::make(v[1].x + v[3].x, v[1].y + v[3].y);
+        const T2 b1 = Cplx<T2>::make(v[1].x - v[3].x, v[1].y - v[3].y);
+        const T2 jb1 = Cplx<T2>::make(-sg * b1.y, sg * b1.x);
+        v[0] = Cplx<T2>::make(a0.x + b0.x, a0.y + b0.y);
+        v[2] = Cplx<T2>::make(a0.x - b0.x, a0.y - b0.y);
+        v[1] = Cplx<T2>::make(a1.x + jb1.x, a1.y + jb1.y);
+        v[3] = Cplx<T2>::make(a1.x - jb1.x, a1.y - jb1.y);
+    }
+};
 
-template <>
-__device__ __forceinline__ void dft_small<3>(float2 *v, float sg) {
-    // w = exp(sg * 2 pi i / 3) = (-1/2, sg sqrt(3)/2)
-    const float s3 = 0.86602540378443865f * sg;
-    const float2 a = v[0], b = v[1], c = v[2];
-    const float2 t = make_float2(b.x + c.x, b.y + c.y);
-    const float2 d = make_float2(b.x - c.x, b.y - c.y);
-    const float2 m = make_float2(a.x - 0.5f * t.x, a.y - 0.5f * t.y);
-    // w b + w^2 c = -t/2 + i s3 (b - c)
-    v[0] = make_float2(a.x + t.x, a.y + t.y);
-    v[1] = make_float2(m.x - s3 * d.y, m.y + s3 * d.x);
-    v[2] = make_float2(m.x + s3 * d.y, m.y - s3 * d.x);
-}
+template <class T2>
+struct Dft<3, T2> {
+    static __device__ __forceinline__ void run(T2 *v, typename Cplx<T2>::R sg) {
+        // w = exp(sg 2 pi i / 3) = (-1/2, sg sqrt(3)/2); w b + w^2 c = -t/2 + i s3 (b - c)
+        using Rl = typename Cplx<T2>::R;
+        const Rl s3 = (Rl)0.86602540378443864676 * sg;
+        const T2 a = v[0], b = v[1], c = v[2];
+        const T2 t = Cplx<T2>::make(b.x + c.x, b.y + c.y);
+        const T2 d = Cplx<T2>::make(b.x - c.x, b.y - c.y);
+        const T2 m = Cplx<T2>::make(a.x - (Rl)0.5 * t.x, a.y - (Rl)0.5 * t.y);
+        v[0] = Cplx<T2>::make(a.x + t.x, a.y + t.y);
+        v[1] = Cplx<T2>::make(m.x - s3 * d.y, m.y + s3 * d.x);
+        v[2] = Cplx<T2>::make(m.x + s3 * d.y, m.y - s3 * d.x);
+    }
+};
 
-template <int R>
-__device__ __forceinline__ void stockham_pass(const float2 *a, float2 *b, int L, int Ns,
-                                              const float2 *__restrict__ tw, float sg,
+// One Stockham pass of radix R, in place: every thread first reads the inputs
+// of its butterflies into registers, then (after a barrier) writes the
+// outputs, so a single buffer of L values suffices.
+template <int R, class T2>
+__device__ __forceinline__ void stockham_pass(T2 *a, int L, int Ns, const T2 *__restrict__ tw,
                                               bool inverse) {
+    constexpr int MAXB = (8 + R - 1) / R;
+    using Rl = typename Cplx<T2>::R;
+    const Rl sg = inverse ? (Rl)1 : (Rl)-1;
     const int m = L / R;
     const int stride = L / (Ns * R);
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        const int k = j % Ns;
-        float2 v[R];
+    T2 v[MAXB][R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
-            float2 x = a[j + t * m];
-            if (t > 0 && k > 0) {
-                float2 w = __ldg(tw + t * k * stride);
-                if (inverse) w.y = -w.y;
-                x = cmul(x, w);
+    for (int bi = 0; bi < MAXB; ++bi) {
+        const int j = threadIdx.x + bi * blockDim.x;
+        if (j < m) {
+            const int k = j % Ns;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                T2 x = a[j + t * m];
+                if (t > 0 && k > 0) {
+                    T2 w = tw[t * k * stride];
+                    if (inverse) w.y = -w.y;
+                    x = cmulT(x, w);
+                }
+                v[bi][t] = x;
             }
-            v[t] = x;
         }
-        dft_small<R>(v, sg);
-        const int idxD = (j / Ns) * Ns * R + k;
-#pragma unroll
-        for (int t = 0; t < R; ++t) b[idxD + t * Ns] = v[t];
     }
+    __syncthreads();
+#pragma unroll
+    for (int bi = 0; bi < MAXB; ++bi) {
+        const int j = threadIdx.x + bi * blockDim.x;
+        if (j < m) {
+            const int k = j % Ns;
+            Dft<R, T2>::run(v[bi], sg);
+            const int idxD = (j / Ns) * Ns * R + k;
+#pragma unroll
+            for (int t = 0; t < R; ++t) a[idxD + t * Ns] = v[bi][t];
+        }
+    }
+    __syncthreads();
 }
 
-// One CTA per row of length L. If `unpack` is given, the row is written back
-// as two real bands (real part -> band 2k, imaginary part -> band 2k+1 when
-// it exists) instead of in place.
-__global__ void __launch_bounds__(256) fft_rows_kernel(float2 *data, FftPlan plan,
-                                                       const float2 *__restrict__ tw,
-                                                       int inverse, float scale, float *unpack,
-                                                       int N, size_t HW) {
-    extern __shared__ float2 fsm[];
+// One CTA per row of length L (<= 8192), blockDim = L/8 rounded up to a
+// multiple of 32. If `unpack` is given (FP32 inverse only), the row is
+// written as two real bands (real part -> band 2k, imaginary part ->
+// band 2k+1 when it exists) instead of in place.
+template <class T2>
+__global__ void __launch_bounds__(1024) fft_rows_kernel(T2 *data, FftPlan plan,
+                                                        const T2 *__restrict__ tw, int inverse,
+                                                        float *unpack, int N, size_t HW) {
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
+    T2 *a = reinterpret_cast<T2 *>(fsm_raw);
     const int L = plan.L;
-    float2 *a = fsm, *b = fsm + L;
     const size_t row = blockIdx.x;
-    float2 *src = data + row * (size_t)L;
+    T2 *src = data + row * (size_t)L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) a[i] = src[i];
     __syncthreads();
-    const float sg = inverse ? 1.0f : -1.0f;
     int Ns = 1;
     for (int p = 0; p < plan.npass; ++p) {
         const int R = plan.radix[p];
         if (R == 4)
-            stockham_pass<4>(a, b, L, Ns, tw, sg, inverse != 0);
+            stockham_pass<4, T2>(a, L, Ns, tw, inverse != 0);
         else if (R == 2)
-            stockham_pass<2>(a, b, L, Ns, tw, sg, inverse != 0);
+            stockham_pass<2, T2>(a, L, Ns, tw, inverse != 0);
         else
-            stockham_pass<3>(a, b, L, Ns, tw, sg, inverse != 0);
-        __syncthreads();
-        float2 *t = a;
-        a = b;
-        b = t;
+            stockham_pass<3, T2>(a, L, Ns, tw, inverse != 0);
         Ns *= R;
     }
     if (unpack) {
@@ -151,28 +189,40 @@ __global__ void __launch_bounds__(256) fft_rows_kernel(float2 *data, FftPlan pla
         float *o0 = unpack + (size_t)b0 * HW + y * L;
         float *o1 = (b0 + 1 < N) ? unpack + (size_t)(b0 + 1) * HW + y * L : nullptr;
         for (int i = threadIdx.x; i < L; i += blockDim.x) {
-            o0[i] = a[i].x * scale;
-            if (o1) o1[i] = a[i].y * scale;
+            o0[i] = (float)a[i].x;
+            if (o1) o1[i] = (float)a[i].y;
         }
     } else {
-        for (int i = threadIdx.x; i < L; i += blockDim.x)
-            src[i] = make_float2(a[i].x * scale, a[i].y * scale);
+        for (int i = threadIdx.x; i < L; i += blockDim.x) src[i] = a[i];
     }
 }
 
-void launch_fft_rows(float2 *data, const FftPlan &plan, int rows, const float2 *tw,
-                     int inverse, float scale, float *unpack, int N, size_t HW,
-                     cudaStream_t st) {
-    const int thr = plan.L >= 1024 ? 256 : (plan.L >= 256 ? 128 : 64);
-    fft_rows_kernel<<<rows, thr, 2 * plan.L * sizeof(float2), st>>>(data, plan, tw, inverse,
-                                                                    scale, unpack, N, HW);
+static int fft_threads(int L) {
+    int t = (L + 7) / 8;
+    t = (t + 31) & ~31;
+    if (t < 32) t = 32;
+    if (t > 1024) t = 1024;
+    return t;
+}
+
+void launch_fft_rows32(float2 *data, const FftPlan &plan, int rows, const float2 *tw,
+                       int inverse, float *unpack, int N, size_t HW, cudaStream_t st) {
+    fft_rows_kernel<float2><<<rows, fft_threads(plan.L), plan.L * sizeof(float2), st>>>(
+        data, plan, tw, inverse, unpack, N, HW);
+}
+
+void launch_fft_rows64(double2 *data, const FftPlan &plan, int rows, const double2 *tw,
+                       cudaStream_t st) {
+    fft_rows_kernel<double2><<<rows, fft_threads(plan.L), plan.L * sizeof(double2), st>>>(
+        data, plan, tw, 0, nullptr, 0, 0);
 }
 
 // out[b][c][r] = in[b][r][c] for a batch of rows x cols complex matrices.
-__global__ void __launch_bounds__(256) transpose_kernel(const float2 *__restrict__ in,
-                                                        float2 *__restrict__ out, int rows,
+template <class T2>
+__global__ void __launch_bounds__(256) transpose_kernel(const T2 *__restrict__ in,
+                                                        T2 *__restrict__ out, int rows,
                                                         int cols) {
-    __shared__ float2 tile[32][33];
+    __shared__ T2 tile[32][33];
     const size_t bo = (size_t)blockIdx.z * rows * cols;
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     for (int k = threadIdx.y; k < 32; k += 8) {
@@ -186,15 +236,21 @@ __global__ void __launch_bounds__(256) transpose_kernel(const float2 *__restrict
     }
 }
 
-void launch_transpose(const float2 *in, float2 *out, int rows, int cols, int batch,
-                      cudaStream_t st) {
+void launch_transpose32(const float2 *in, float2 *out, int rows, int cols, int batch,
+                        cudaStream_t st) {
     dim3 blk(32, 8), grd((cols + 31) / 32, (rows + 31) / 32, batch);
-    transpose_kernel<<<grd, blk, 0, st>>>(in, out, rows, cols);
+    transpose_kernel<float2><<<grd, blk, 0, st>>>(in, out, rows, cols);
+}
+
+void launch_transpose64(const double2 *in, double2 *out, int rows, int cols, int batch,
+                        cudaStream_t st) {
+    dim3 blk(32, 8), grd((cols + 31) / 32, (rows + 31) / 32, batch);
+    transpose_kernel<double2><<<grd, blk, 0, st>>>(in, out, rows, cols);
 }
 
 // H x W complex image holding the kernel taps at (i mod H, j mod W).
 __global__ void kernel_embed_kernel(const float *__restrict__ u, int R, int H, int W,
-                                    float2 *out) {
+                                    double2 *out) {
     const size_t HW = (size_t)H * W;
     const int n = 2 * R + 1;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < HW;
@@ -203,13 +259,13 @@ __global__ void kernel_embed_kernel(const float *__restrict__ u, int R, int H, i
         int i = y, j = x;
         if (i > H / 2) i -= H;
         if (j > W / 2) j -= W;
-        float val = 0.0f;
-        if (i >= -R && i <= R && j >= -R && j <= R) val = u[(i + R) * n + (j + R)];
-        out[k] = make_float2(val, 0.0f);
+        double val = 0.0;
+        if (i >= -R && i <= R && j >= -R && j <= R) val = (double)u[(i + R) * n + (j + R)];
+        out[k] = make_double2(val, 0.0);
     }
 }
 
-void launch_kernel_embed(const float *u, int R, int H, int W, float2 *out, cudaStream_t st) {
+void launch_kernel_embed(const float *u, int R, int H, int W, double2 *out, cudaStream_t st) {
     const size_t HW = (size_t)H * W;
     int blocks = (int)((HW + 255) / 256);
     if (blocks > 4096) blocks = 4096;
@@ -225,101 +281,106 @@ void launch_kernel_embed(const float *u, int R, int H, int W, float2 *out, cudaS
 // DC group, where t_m = 0, needs no special case). When the data term
 // dominates member m (c^2 t_m < |v_m|^2), x_m is taken from
 // s = sum_j conj(v_j) x_j instead of dividing by the tiny t_m.
-// The result is scaled by 1/(H W) for the unnormalised inverse FFT.
-__global__ void __launch_bounds__(256) alias_solve_kernel(float2 *spec,
-                                                          const float2 *__restrict__ bspec,
-                                                          int H, int W, int c, float lam) {
+// The group algebra runs in FP64 (near-DC groups cancel strongly; there are
+// only H W / c^2 groups per image). The result is scaled by 1/(H W) for the
+// unnormalised inverse FFT.
+struct cd { double x, y; };
+__device__ __forceinline__ cd cd_mul(cd a, cd b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+
+__device__ __forceinline__ double symbol_t(int ky, int kx, int H, int W, double lam) {
+    const double sy = (double)sinpif((float)ky / (float)H);
+    const double sx = (double)sinpif((float)kx / (float)W);
+    const double sh = 4.0 * (sy * sy + sx * sx);
+    return lam * sh * sh;
+}
+
+__global__ void __launch_bounds__(256) alias_solve_kernel(const double2 *__restrict__ spec,
+                                                          const double2 *__restrict__ bspec,
+                                                          float2 *__restrict__ sol, int H,
+                                                          int W, int c, float lamf) {
     const int h = H / c, w = W / c;
     const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
     if (gidx >= h * w) return;
     const int kx0 = gidx / h, ky0 = gidx - (gidx / h) * h;
-    float2 *S = spec + (size_t)blockIdx.y * H * W;
-    const float cc = (float)(c * c);
-    // member with the smallest symbol
+    const double2 *S = spec + (size_t)blockIdx.y * H * W;
+    float2 *X = sol + (size_t)blockIdx.y * H * W;
+    const double cc = (double)(c * c), icc = 1.0 / cc, lam = (double)lamf;
     int pm = 0, qm = 0;
-    float tmin = 3.4e38f;
+    double tmin = 1e300;
     for (int p = 0; p < c; ++p)
         for (int q = 0; q < c; ++q) {
-            const float sy = sinpif((float)(ky0 + p * h) / (float)H);
-            const float sx = sinpif((float)(kx0 + q * w) / (float)W);
-            const float sh = 4.0f * (sy * sy + sx * sx);
-            const float t = lam * sh * sh;
+            const double t = symbol_t(ky0 + p * h, kx0 + q * w, H, W, lam);
             if (t < tmin) { tmin = t; pm = p; qm = q; }
         }
-    float2 num = make_float2(0.f, 0.f);
-    float dsum = 0.f;
-    float2 rm = make_float2(0.f, 0.f), vm = make_float2(0.f, 0.f);
+    cd num = {0.0, 0.0};
+    double dsum = 0.0;
+    cd rm = {0.0, 0.0}, vm = {0.0, 0.0};
     for (int p = 0; p < c; ++p)
         for (int q = 0; q < c; ++q) {
             const int ky = ky0 + p * h, kx = kx0 + q * w;
             const size_t o = (size_t)kx * H + ky;
-            const float2 r = S[o];
-            const float2 bh = bspec[o];
-            const float2 v = make_float2(bh.x, -bh.y);
+            const double2 rf = S[o], bh = bspec[o];
+            const cd r = {rf.x, rf.y};
+            const cd v = {bh.x, -bh.y};
             if (p == pm && q == qm) {
                 rm = r;
                 vm = v;
                 continue;
             }
-            const float sy = sinpif((float)ky / (float)H);
-            const float sx = sinpif((float)kx / (float)W);
-            const float sh = 4.0f * (sy * sy + sx * sx);
-            const float t = lam * sh * sh;
-            // conj(v) r / t
-            num.x += (v.x * r.x + v.y * r.y) / t;
-            num.y += (v.x * r.y - v.y * r.x) / t;
-            dsum += (v.x * v.x + v.y * v.y) / t;
+            const double it = 1.0 / symbol_t(ky, kx, H, W, lam);
+            num.x += (v.x * r.x + v.y * r.y) * it;
+            num.y += (v.x * r.y - v.y * r.x) * it;
+            dsum += (v.x * v.x + v.y * v.y) * it;
         }
-    const float vm2 = vm.x * vm.x + vm.y * vm.y;
-    // numerator: conj(vm) rm + tmin * num
-    float2 nn = make_float2(vm.x * rm.x + vm.y * rm.y + tmin * num.x,
-                            vm.x * rm.y - vm.y * rm.x + tmin * num.y);
-    const float den = tmin + (vm2 + tmin * dsum) / cc;
-    const float2 s = make_float2(nn.x / den, nn.y / den);
-    const float scale = 1.0f / ((float)H * (float)W);
-    float2 acc = make_float2(0.f, 0.f);  // sum_{j != m} conj(v_j) x_j
+    const double vm2 = vm.x * vm.x + vm.y * vm.y;
+    const cd nn = {vm.x * rm.x + vm.y * rm.y + tmin * num.x,
+                   vm.x * rm.y - vm.y * rm.x + tmin * num.y};
+    const double iden = 1.0 / (tmin + (vm2 + tmin * dsum) * icc);
+    const cd s = {nn.x * iden, nn.y * iden};
+    const double scale = 1.0 / ((double)H * (double)W);
+    cd acc = {0.0, 0.0};
     for (int p = 0; p < c; ++p)
         for (int q = 0; q < c; ++q) {
             if (p == pm && q == qm) continue;
             const int ky = ky0 + p * h, kx = kx0 + q * w;
             const size_t o = (size_t)kx * H + ky;
-            const float2 r = S[o];
-            const float2 bh = bspec[o];
-            const float2 v = make_float2(bh.x, -bh.y);
-            const float sy = sinpif((float)ky / (float)H);
-            const float sx = sinpif((float)kx / (float)W);
-            const float sh = 4.0f * (sy * sy + sx * sx);
-            const float t = lam * sh * sh;
-            const float2 vs = cmul(v, s);
-            const float2 x = make_float2((r.x - vs.x / cc) / t, (r.y - vs.y / cc) / t);
+            const double2 rf = S[o], bh = bspec[o];
+            const cd v = {bh.x, -bh.y};
+            const double it = 1.0 / symbol_t(ky, kx, H, W, lam);
+            const cd vs = cd_mul(v, s);
+            const cd x = {(rf.x - vs.x * icc) * it, (rf.y - vs.y * icc) * it};
             acc.x += v.x * x.x + v.y * x.y;
             acc.y += v.x * x.y - v.y * x.x;
-            S[o] = make_float2(x.x * scale, x.y * scale);
+            X[o] = make_float2((float)(x.x * scale), (float)(x.y * scale));
         }
-    float2 xm;
+    cd xm;
     if (cc * tmin < vm2) {
-        // x_m = (s - acc) / conj(v_m)
-        const float2 d = make_float2(s.x - acc.x, s.y - acc.y);
-        const float2 cv = make_float2(vm.x, -vm.y);
-        const float cv2 = vm2;
-        xm = make_float2((d.x * cv.x + d.y * cv.y) / cv2, (d.y * cv.x - d.x * cv.y) / cv2);
+        const cd d = {s.x - acc.x, s.y - acc.y};
+        const double iv = 1.0 / vm2;
+        xm = {(d.x * vm.x - d.y * vm.y) * iv, (d.y * vm.x + d.x * vm.y) * iv};
     } else {
-        const float2 vs = cmul(vm, s);
-        xm = make_float2((rm.x - vs.x / cc) / tmin, (rm.y - vs.y / cc) / tmin);
+        const cd vs = cd_mul(vm, s);
+        xm = {(rm.x - vs.x * icc) / tmin, (rm.y - vs.y * icc) / tmin};
     }
-    S[(size_t)(kx0 + qm * w) * H + (ky0 + pm * h)] = make_float2(xm.x * scale, xm.y * scale);
+    X[(size_t)(kx0 + qm * w) * H + (ky0 + pm * h)] =
+        make_float2((float)(xm.x * scale), (float)(xm.y * scale));
 }
 
-void launch_alias_solve(float2 *spec, const float2 *bspec, int nimg, int H, int W, int c,
-                        float lam, cudaStream_t st) {
+void launch_alias_solve(const double2 *spec, const double2 *bspec, float2 *sol, int nimg, int H,
+                        int W, int c, float lam, cudaStream_t st) {
     const int groups = (H / c) * (W / c);
     dim3 grd((groups + 255) / 256, nimg);
-    alias_solve_kernel<<<grd, 256, 0, st>>>(spec, bspec, H, W, c, lam);
+    alias_solve_kernel<<<grd, 256, 0, st>>>(spec, bspec, sol, H, W, c, lam);
 }
 
 cudaError_t fft_set_attrs() {
-    return cudaFuncSetAttribute(fft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(2 * kMaxFFT * sizeof(float2)));
+    cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<float2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kMaxFFT * sizeof(float2)));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fft_rows_kernel<double2>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(kMaxFFT * sizeof(double2)));
 }
 
 }  // namespace ps

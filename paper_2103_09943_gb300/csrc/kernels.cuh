@@ -7,17 +7,17 @@
 
 namespace ps {
 
-enum LlpMode { LLP_APPLY = 0, LLP_ZRHS = 1, LLP_GF = 2 };
+enum LlpMode { LLP_APPLY = 0, LLP_ZRHS = 1, LLP_GF = 2, LLP_CGQ = 3 };
 
 struct LlpArgs {
     const float *in;    // p (APPLY), Z0 (ZRHS) or q (GF); N x H x W
     const float *lr;    // D B p (APPLY) or X (ZRHS); N x h x w
-    const float *I, *mu, *s;
+    const float4 *st4;  // packed PAN statistics (I, mu, s, -) per pixel
     const float *u;
     int R, c, H, W, N;
     float lam;
     float *out;         // N x H x W (APPLY, GF)
-    float2 *cout;       // packed complex images (ZRHS)
+    double2 *cout;      // packed complex images (ZRHS), FP64 for the forward FFT
     CgBand *bands;      // CG mode of APPLY: p^T A p and alpha
     const CgGlobal *g;
     int cg;
@@ -25,7 +25,9 @@ struct LlpArgs {
 
 // operators.cu
 void launch_pan_stats(const float *Y, int H, int W, int r, float eps, float *I, float *mu,
-                      float *s, cudaStream_t st);
+                      float *s, float4 *st4, cudaStream_t st);
+void launch_pack_stats(const float *I, const float *mu, const float *s, size_t n, float4 *st4,
+                       cudaStream_t st);
 void launch_db(const float *src, const float *rsrc, float *pdst, const CgBand *bands,
                const CgGlobal *g, int cg, int N, int H, int W, int c, const float *u, int R,
                float *v, cudaStream_t st);
@@ -36,13 +38,24 @@ void launch_cg_reset(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter
                      cudaStream_t st);
 void launch_cg_init(const float *bvec, const float *ax0, const float *x0, float *x, float *r,
                     int N, size_t HW, CgBand *bands, CgGlobal *g, cudaStream_t st);
-void launch_cg_update(float *x, float *r, const float *p, const float *ap, int N, size_t HW,
-                      CgBand *bands, const CgGlobal *g, cudaStream_t st);
+void launch_cg_update(float *x, float *r, const float *p, const float *q, const float *v,
+                      const float *u, int R, int c, int N, int H, int W, CgBand *bands,
+                      const CgGlobal *g, cudaStream_t st);
 void launch_cg_control(CgBand *bands, CgGlobal *g, int N, int use_cond,
                        cudaGraphConditionalHandle handle, cudaStream_t st);
 cudaError_t operators_set_attrs();
 size_t db_smem_bytes(int c, int R);
 size_t llp_smem_bytes(int r);
+
+// cg_fast.cu: compile-time (ratio, radius) versions of db and cg_update;
+// return false when no specialisation covers (c, R)
+bool launch_db_fast(const float *src, const float *rsrc, float *pdst, CgBand *bands,
+                    const CgGlobal *g, int cg, int N, int H, int W, int c, const float *u, int R,
+                    float *v, cudaStream_t st);
+bool launch_cg_update_fast(float *x, float *r, const float *p, const float *q, const float *v,
+                           const float *u, int R, int c, int N, int H, int W, CgBand *bands,
+                           const CgGlobal *g, cudaStream_t st);
+cudaError_t cg_fast_set_attrs();
 
 // fft.cu
 struct FftPlan {
@@ -51,15 +64,18 @@ struct FftPlan {
     int radix[16];
 };
 bool fft_make_plan(int L, FftPlan *plan);
-void launch_fft_twiddles(int L, float2 *tw, cudaStream_t st);
-void launch_fft_rows(float2 *data, const FftPlan &plan, int rows, const float2 *tw,
-                     int inverse, float scale, float *unpack, int N, size_t HW,
-                     cudaStream_t st);
-void launch_transpose(const float2 *in, float2 *out, int rows, int cols, int batch,
-                      cudaStream_t st);
-void launch_kernel_embed(const float *u, int R, int H, int W, float2 *out, cudaStream_t st);
-void launch_alias_solve(float2 *spec, const float2 *bspec, int nimg, int H, int W, int c,
-                        float lam, cudaStream_t st);
+void launch_fft_twiddles(int L, float2 *tw32, double2 *tw64, cudaStream_t st);
+void launch_fft_rows32(float2 *data, const FftPlan &plan, int rows, const float2 *tw,
+                       int inverse, float *unpack, int N, size_t HW, cudaStream_t st);
+void launch_fft_rows64(double2 *data, const FftPlan &plan, int rows, const double2 *tw,
+                       cudaStream_t st);
+void launch_transpose32(const float2 *in, float2 *out, int rows, int cols, int batch,
+                        cudaStream_t st);
+void launch_transpose64(const double2 *in, double2 *out, int rows, int cols, int batch,
+                        cudaStream_t st);
+void launch_kernel_embed(const float *u, int R, int H, int W, double2 *out, cudaStream_t st);
+void launch_alias_solve(const double2 *spec, const double2 *bspec, float2 *sol, int nimg, int H,
+                        int W, int c, float lam, cudaStream_t st);
 cudaError_t fft_set_attrs();
 
 // kest.cu

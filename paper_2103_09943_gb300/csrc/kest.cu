@@ -190,19 +190,30 @@ __global__ void __launch_bounds__(256) ete_lag_kernel(const float *__restrict__ 
     float s[LAG_CHUNK], cm[LAG_CHUNK];
 #pragma unroll
     for (int t = 0; t < LAG_CHUNK; ++t) { s[t] = 0.f; cm[t] = 0.f; }
-    for (int q = threadIdx.x; q < h * w; q += 256) {
-        const int ky = q / w, kx = q - (q / w) * w;
+    int ky = 0, kx = threadIdx.x;
+    while (kx >= w) { kx -= w; ++ky; }
+    for (; ky < h;) {
         const int yy = c * ky + py, xx = c * kx + px;
         const float a = Y[(size_t)yy * W + xx];
         const float *row = Y + (size_t)wrapk(yy + dy, H) * W;
+        int cx = xx + dx0;
+        if (cx < 0) cx += W;
+        else if (cx >= W) cx -= W;
 #pragma unroll
-        for (int t = 0; t < LAG_CHUNK; ++t)
-            if (t < ndx) df_acc(a, row[wrapk(xx + dx0 + t, W)], s[t], cm[t]);
+        for (int t = 0; t < LAG_CHUNK; ++t) {
+            if (t < ndx) df_acc(a, row[cx], s[t], cm[t]);
+            cx = (cx + 1 == W) ? 0 : cx + 1;
+        }
+        kx += 256;
+        while (kx >= w) { kx -= w; ++ky; }
     }
-    for (int t = 0; t < ndx; ++t) {
-        const double tot = block_sum_d((double)s[t] + (double)cm[t], red);
-        if (threadIdx.x == 0)
-            lags[((size_t)blockIdx.y * nl + (dy + 2 * R)) * nl + (dx0 + t + 2 * R)] = tot;
+#pragma unroll
+    for (int t = 0; t < LAG_CHUNK; ++t) {
+        if (t < ndx) {
+            const double tot = block_sum_d((double)s[t] + (double)cm[t], red);
+            if (threadIdx.x == 0)
+                lags[((size_t)blockIdx.y * nl + (dy + 2 * R)) * nl + (dx0 + t + 2 * R)] = tot;
+        }
     }
 }
 
@@ -240,9 +251,13 @@ __global__ void __launch_bounds__(256) etf_kernel(const float *__restrict__ Y, i
     const int ai = (int)blockIdx.x / n - R, aj = (int)blockIdx.x % n - R;
     const int h = H / c, w = W / c;
     float s = 0.f, cm = 0.f;
-    for (int q = threadIdx.x; q < h * w; q += 256) {
-        const int ky = q / w, kx = q - (q / w) * w;
-        df_acc(Y[(size_t)wrapk(c * ky - ai, H) * W + wrapk(c * kx - aj, W)], f[q], s, cm);
+    int ky = 0, kx = threadIdx.x;
+    while (kx >= w) { kx -= w; ++ky; }
+    for (; ky < h;) {
+        df_acc(Y[(size_t)wrapk(c * ky - ai, H) * W + wrapk(c * kx - aj, W)],
+               f[(size_t)ky * w + kx], s, cm);
+        kx += 256;
+        while (kx >= w) { kx -= w; ++ky; }
     }
     const double tot = block_sum_d((double)s + (double)cm, red);
     if (threadIdx.x == 0) Etf[blockIdx.x] = tot;
@@ -255,92 +270,219 @@ void launch_etf(const float *Y, int H, int W, int c, int R, const float *f, doub
 }
 
 // ---------------------------------------------------------------------------
-// FP64 Cholesky of A + mu3 I (lower triangle, in place), one CTA.
+// FP64 Cholesky of A + mu3 I (lower triangle, in place), blocked right-looking
+// over 32-column panels: per panel one CTA factors the diagonal tile and
+// solves the rows below it, then one CTA per trailing tile applies the
+// rank-32 update. A is nt x nt row-major.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) cholesky_kernel(double *A, int n, float mu3) {
-    extern __shared__ double col[];
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-    for (int i = tid; i < n; i += nthr) A[(size_t)i * n + i] += (double)mu3;
+constexpr int CB = 32;
+
+__global__ void add_diag_kernel(double *A, int n, float mu3) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) A[(size_t)i * n + i] += (double)mu3;
+}
+
+// Factor the 32 x 32 diagonal tile of panel k0 in place (one CTA; one warp
+// does the factorisation, lane i owning row i).
+__global__ void __launch_bounds__(256) chol_diag_kernel(double *A, int nt, int k0) {
+    __shared__ double D[CB][CB + 1];
+    const int tid = threadIdx.x;
+    const int kb = min(CB, nt - k0);
+    for (int e = tid; e < CB * CB; e += blockDim.x) {
+        const int i = e / CB, j = e - (e / CB) * CB;
+        double v;
+        if (i < kb && j < kb) v = (j <= i) ? A[(size_t)(k0 + i) * nt + k0 + j] : 0.0;
+        else v = (i == j) ? 1.0 : 0.0;
+        D[i][j] = v;
+    }
     __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        const double d = A[(size_t)k * n + k];
-        const double lkk = sqrt(d > 0.0 ? d : 1e-300);
-        for (int i = k + 1 + tid; i < n; i += nthr) {
-            const double v = A[(size_t)i * n + k] / lkk;
-            col[i] = v;
+    if (tid < 32) {
+        const int i = tid;
+        for (int k = 0; k < CB; ++k) {
+            if (i == k) {
+                const double d = D[k][k];
+                D[k][k] = sqrt(d > 0.0 ? d : 1e-300);
+            }
+            __syncwarp();
+            if (i > k) D[i][k] /= D[k][k];
+            __syncwarp();
+            if (i > k)
+                for (int j = k + 1; j <= i; ++j) D[i][j] -= D[i][k] * D[j][k];
+            __syncwarp();
         }
-        __syncthreads();
-        for (int i = k + 1 + tid; i < n; i += nthr) A[(size_t)i * n + k] = col[i];
-        if (tid == 0) A[(size_t)k * n + k] = lkk;
-        for (int i = k + 1 + warp; i < n; i += nwarp) {
-            const double lik = col[i];
-            double *row = A + (size_t)i * n;
-            for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= lik * col[j];
-        }
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int e = tid; e < kb * kb; e += blockDim.x) {
+        const int i = e / kb, j = e - (e / kb) * kb;
+        if (j <= i) A[(size_t)(k0 + i) * nt + k0 + j] = D[i][j];
+    }
+}
+
+// Rows below the diagonal tile: L[i][k0 + k] = (A[i][k0+k] - sum_{m<k}
+// L[i][k0+m] D[k][m]) / D[k][k]; one warp per 32 rows, one row per lane.
+__global__ void __launch_bounds__(32) chol_panel_kernel(double *A, int nt, int k0) {
+    __shared__ double D[CB][CB + 1];
+    const int lane = threadIdx.x;
+    const int k1 = min(k0 + CB, nt), kb = k1 - k0;
+    for (int e = lane; e < CB * CB; e += 32) {
+        const int i = e / CB, j = e - (e / CB) * CB;
+        double v;
+        if (i < kb && j < kb) v = (j <= i) ? A[(size_t)(k0 + i) * nt + k0 + j] : 0.0;
+        else v = (i == j) ? 1.0 : 0.0;
+        D[i][j] = v;
+    }
+    __syncwarp();
+    const int i = k1 + blockIdx.x * 32 + lane;
+    if (i >= nt) return;
+    double x[CB];
+    double *row = A + (size_t)i * nt + k0;
+#pragma unroll
+    for (int k = 0; k < CB; ++k) x[k] = (k < kb) ? row[k] : 0.0;
+#pragma unroll
+    for (int k = 0; k < CB; ++k) {
+        double v = x[k];
+#pragma unroll
+        for (int m = 0; m < k; ++m) v -= x[m] * D[k][m];
+        x[k] = v / D[k][k];
+    }
+#pragma unroll
+    for (int k = 0; k < CB; ++k)
+        if (k < kb) row[k] = x[k];
+}
+
+// Trailing update A[I][J] -= L[I][K] L[J][K]^T over tiles I >= J of the
+// trailing matrix (one CTA per tile pair).
+__global__ void __launch_bounds__(256) chol_update_kernel(double *A, int nt, int k0) {
+    __shared__ double Li[CB][CB + 1], Lj[CB][CB + 1];
+    const int k1 = min(k0 + CB, nt), kb = k1 - k0;
+    int e = blockIdx.x, ti = 0;
+    while (e > ti) { e -= ti + 1; ++ti; }
+    const int tj = e;
+    const int i0 = k1 + ti * CB, j0 = k1 + tj * CB;
+    const int tid = threadIdx.x;
+    for (int q = tid; q < CB * CB; q += blockDim.x) {
+        const int r = q / CB, k = q - (q / CB) * CB;
+        Li[r][k] = (i0 + r < nt && k < kb) ? A[(size_t)(i0 + r) * nt + k0 + k] : 0.0;
+        Lj[r][k] = (j0 + r < nt && k < kb) ? A[(size_t)(j0 + r) * nt + k0 + k] : 0.0;
+    }
+    __syncthreads();
+    for (int q = tid; q < CB * CB; q += blockDim.x) {
+        const int r = q / CB, cc = q - (q / CB) * CB;
+        const int i = i0 + r, j = j0 + cc;
+        if (i >= nt || j >= nt || j > i) continue;
+        double acc = 0.0;
+#pragma unroll 8
+        for (int k = 0; k < CB; ++k) acc += Li[r][k] * Lj[cc][k];
+        A[(size_t)i * nt + j] -= acc;
     }
 }
 
 void launch_cholesky(double *A, int n, float mu3, cudaStream_t st) {
-    cholesky_kernel<<<1, 1024, n * sizeof(double), st>>>(A, n, mu3);
+    add_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(A, n, mu3);
+    for (int k0 = 0; k0 < n; k0 += CB) {
+        chol_diag_kernel<<<1, 256, 0, st>>>(A, n, k0);
+        const int rem = n - (k0 + CB);
+        if (rem > 0) {
+            chol_panel_kernel<<<(rem + 31) / 32, 32, 0, st>>>(A, n, k0);
+            const int nbt = (rem + CB - 1) / CB;
+            chol_update_kernel<<<nbt * (nbt + 1) / 2, 256, 0, st>>>(A, n, k0);
+        }
+    }
 }
 
-// Solve (L L^T) x = b, one CTA.
+// Solve (L L^T) x = b for `ncol` right-hand sides, one CTA per column; the
+// rhs of column j is b (ncol == 1) or e_j scaled (the inverse). Forward
+// substitution by 32-row tiles: the rows of a tile take their dot products
+// with the solved part in parallel (one warp per row, coalesced rows of L),
+// then one warp finishes the tile's triangle. Backward substitution on L^T by
+// tiles from the bottom: one warp solves the tile, then all threads update
+// the unknowns above from the tile's rows of L (coalesced).
+__device__ void chol_two_solves(const double *L, int nt, double *y, double *Dt) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    for (int t0 = 0; t0 < nt; t0 += CB) {
+        const int kb = min(CB, nt - t0);
+        for (int r = warp; r < kb; r += nwarp) {
+            const double *row = L + (size_t)(t0 + r) * nt;
+            double acc = 0.0;
+            for (int k = lane; k < t0; k += 32) acc += row[k] * y[k];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) y[t0 + r] -= acc;
+        }
+        for (int q = tid; q < kb * kb; q += blockDim.x) {
+            const int r = q / kb, k = q - (q / kb) * kb;
+            Dt[r * CB + k] = (k <= r) ? L[(size_t)(t0 + r) * nt + t0 + k] : 0.0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int r = 0; r < kb; ++r) {
+                double acc = 0.0;
+                if (lane < r) acc = Dt[r * CB + lane] * y[t0 + lane];
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) y[t0 + r] = (y[t0 + r] - acc) / Dt[r * CB + r];
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+    const int ntile = (nt + CB - 1) / CB;
+    for (int tt = ntile - 1; tt >= 0; --tt) {
+        const int t0 = tt * CB, kb = min(CB, nt - t0);
+        for (int q = tid; q < kb * kb; q += blockDim.x) {
+            const int r = q / kb, k = q - (q / kb) * kb;
+            Dt[r * CB + k] = (k <= r) ? L[(size_t)(t0 + r) * nt + t0 + k] : 0.0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int r = kb - 1; r >= 0; --r) {
+                // x_r = (y_r - sum_{k>r in tile} L[k][r] x_k) / L[r][r]
+                double acc = 0.0;
+                if (lane > r && lane < kb) acc = Dt[lane * CB + r] * y[t0 + lane];
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) y[t0 + r] = (y[t0 + r] - acc) / Dt[r * CB + r];
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < t0; i += blockDim.x) {
+            double acc = 0.0;
+            for (int k = 0; k < kb; ++k) acc += L[(size_t)(t0 + k) * nt + i] * y[t0 + k];
+            y[i] -= acc;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(256) chol_solve_kernel(const double *L, const double *b,
                                                          int n, double *x) {
-    extern __shared__ double yv[];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < n; i += blockDim.x) yv[i] = b[i];
+    extern __shared__ double ysm[];
+    double *y = ysm, *Dt = ysm + ((n + 1) & ~1);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = b[i];
     __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        const double yk = yv[k] / L[(size_t)k * n + k];
-        __syncthreads();
-        if (tid == 0) yv[k] = yk;
-        for (int i = k + 1 + tid; i < n; i += blockDim.x) yv[i] -= L[(size_t)i * n + k] * yk;
-        __syncthreads();
-    }
-    for (int k = n - 1; k >= 0; --k) {
-        const double xk = yv[k] / L[(size_t)k * n + k];
-        __syncthreads();
-        if (tid == 0) yv[k] = xk;
-        for (int i = tid; i < k; i += blockDim.x) yv[i] -= L[(size_t)k * n + i] * xk;
-        __syncthreads();
-    }
-    for (int i = tid; i < n; i += blockDim.x) x[i] = yv[i];
+    chol_two_solves(L, n, y, Dt);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = y[i];
 }
 
 void launch_chol_solve(const double *L, const double *b, int n, double *x, cudaStream_t st) {
-    chol_solve_kernel<<<1, 256, n * sizeof(double), st>>>(L, b, n, x);
+    const size_t sm = (((n + 1) & ~1) + CB * CB) * sizeof(double);
+    chol_solve_kernel<<<1, 256, sm, st>>>(L, b, n, x);
 }
 
 // Q[:, j] = scale (L L^T)^{-1} e_j, one CTA per column (Q is symmetric).
 __global__ void __launch_bounds__(256) chol_inverse_kernel(const double *L, int n, float scale,
                                                            float *Q) {
-    extern __shared__ double yv[];
-    const int j = blockIdx.x, tid = threadIdx.x;
-    for (int i = tid; i < n; i += blockDim.x) yv[i] = (i == j) ? 1.0 : 0.0;
+    extern __shared__ double ysm[];
+    double *y = ysm, *Dt = ysm + ((n + 1) & ~1);
+    const int j = blockIdx.x;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (i == j) ? 1.0 : 0.0;
     __syncthreads();
-    for (int k = j; k < n; ++k) {
-        const double yk = yv[k] / L[(size_t)k * n + k];
-        __syncthreads();
-        if (tid == 0) yv[k] = yk;
-        for (int i = k + 1 + tid; i < n; i += blockDim.x) yv[i] -= L[(size_t)i * n + k] * yk;
-        __syncthreads();
-    }
-    for (int k = n - 1; k >= 0; --k) {
-        const double xk = yv[k] / L[(size_t)k * n + k];
-        __syncthreads();
-        if (tid == 0) yv[k] = xk;
-        for (int i = tid; i < k; i += blockDim.x) yv[i] -= L[(size_t)k * n + i] * xk;
-        __syncthreads();
-    }
-    for (int i = tid; i < n; i += blockDim.x) Q[(size_t)i * n + j] = (float)(scale * yv[i]);
+    chol_two_solves(L, n, y, Dt);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Q[(size_t)i * n + j] = (float)(scale * y[i]);
 }
 
 void launch_chol_inverse(const double *L, int n, float scale, float *Q, double *,
                          cudaStream_t st) {
-    chol_inverse_kernel<<<n, 256, n * sizeof(double), st>>>(L, n, scale, Q);
+    const size_t sm = (((n + 1) & ~1) + CB * CB) * sizeof(double);
+    chol_inverse_kernel<<<n, 256, sm, st>>>(L, n, scale, Q);
 }
 
 // ---------------------------------------------------------------------------
@@ -381,13 +523,20 @@ __device__ __forceinline__ void block_sum2(double a, double b, double *red, doub
         red[32 + (tid >> 5)] = b;
     }
     __syncthreads();
-    double sa = 0.0, sb = 0.0;
-    for (int k = 0; k < nw; ++k) {
-        sa += red[k];
-        sb += red[32 + k];
+    if (tid < 32) {
+        double sa = (tid < nw) ? red[tid] : 0.0, sb = (tid < nw) ? red[32 + tid] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        }
+        if (tid == 0) {
+            red[64] = sa;
+            red[65] = sb;
+        }
     }
-    ra = sa;
-    rb = sb;
+    __syncthreads();
+    ra = red[64];
+    rb = red[65];
 }
 
 // 2-D DFT of three real n x n arrays (sg = -1) or inverse of three complex
@@ -401,11 +550,13 @@ __device__ void dft3_forward(const float *a0, const float *a1, const float *a2, 
         const int i = e / n, kx = e - (e / n) * n;
         const float *a = which == 0 ? a0 : (which == 1 ? a1 : a2);
         float2 acc = make_float2(0.f, 0.f);
-        for (int j = 0; j < n; ++j) {
-            const float2 wv = tw[(j * kx) % n];
+        for (int j = 0, ix = 0; j < n; ++j) {
+            const float2 wv = tw[ix];
             const float v = a[i * n + j];
             acc.x += v * wv.x;
             acc.y += v * wv.y;
+            ix += kx;
+            if (ix >= n) ix -= n;
         }
         (which == 0 ? T0 : (which == 1 ? T1 : T2))[e] = acc;
     }
@@ -415,7 +566,11 @@ __device__ void dft3_forward(const float *a0, const float *a1, const float *a2, 
         const int ky = e / n, kx = e - (e / n) * n;
         const float2 *T = which == 0 ? T0 : (which == 1 ? T1 : T2);
         float2 acc = make_float2(0.f, 0.f);
-        for (int i = 0; i < n; ++i) acc = c_add(acc, c_mul(T[i * n + kx], tw[(i * ky) % n]));
+        for (int i = 0, ix = 0; i < n; ++i) {
+            acc = c_add(acc, c_mul(T[i * n + kx], tw[ix]));
+            ix += ky;
+            if (ix >= n) ix -= n;
+        }
         (which == 0 ? F0 : (which == 1 ? F1 : F2))[e] = acc;
     }
     __syncthreads();
@@ -430,7 +585,11 @@ __device__ void dft3_inverse(const float2 *F0, const float2 *F1, const float2 *F
         const int i = e / n, kx = e - (e / n) * n;
         const float2 *F = which == 0 ? F0 : (which == 1 ? F1 : F2);
         float2 acc = make_float2(0.f, 0.f);
-        for (int ky = 0; ky < n; ++ky) acc = c_add(acc, c_mul(F[ky * n + kx], c_conj(tw[(i * ky) % n])));
+        for (int ky = 0, ix = 0; ky < n; ++ky) {
+            acc = c_add(acc, c_mul(F[ky * n + kx], c_conj(tw[ix])));
+            ix += i;
+            if (ix >= n) ix -= n;
+        }
         (which == 0 ? T0 : (which == 1 ? T1 : T2))[e] = acc;
     }
     __syncthreads();
@@ -440,10 +599,12 @@ __device__ void dft3_inverse(const float2 *F0, const float2 *F1, const float2 *F
         const int i = e / n, j = e - (e / n) * n;
         const float2 *T = which == 0 ? T0 : (which == 1 ? T1 : T2);
         float acc = 0.f;
-        for (int kx = 0; kx < n; ++kx) {
-            const float2 wv = c_conj(tw[(j * kx) % n]);
+        for (int kx = 0, ix = 0; kx < n; ++kx) {
+            const float2 wv = c_conj(tw[ix]);
             const float2 tv = T[i * n + kx];
             acc += tv.x * wv.x - tv.y * wv.y;
+            ix += j;
+            if (ix >= n) ix -= n;
         }
         (which == 0 ? o0 : (which == 1 ? o1 : o2))[e] = acc * inv;
     }
@@ -453,7 +614,7 @@ __device__ void dft3_inverse(const float2 *F0, const float2 *F1, const float2 *F
 size_t admm_smem_bytes(int R) {
     const int nt = (2 * R + 1) * (2 * R + 1);
     const size_t ntp = (nt + 3) & ~3;
-    return 26 * ntp * sizeof(float) + (6 * ntp + 64) * sizeof(float2) + 64 * sizeof(double) +
+    return 26 * ntp * sizeof(float) + (6 * ntp + 64) * sizeof(float2) + 80 * sizeof(double) +
            16;
 }
 
@@ -467,7 +628,7 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
     const int ntp = (nt + 3) & ~3;
     const int tid = threadIdx.x, nthr = blockDim.x;
     double *red = reinterpret_cast<double *>(admm_sm);
-    float2 *cbase = reinterpret_cast<float2 *>(admm_sm + 64 * sizeof(double));
+    float2 *cbase = reinterpret_cast<float2 *>(admm_sm + 80 * sizeof(double));
     float2 *F0 = cbase, *F1 = F0 + ntp, *F2 = F1 + ntp, *T0 = F2 + ntp, *T1 = T0 + ntp,
            *T2 = T1 + ntp, *tw = T2 + ntp;
     float *fb = reinterpret_cast<float *>(tw + 64);
@@ -497,7 +658,9 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
     int it = 0, status = PS_ERR_NOT_CONVERGED;
     double change = 0.0;
     auto at = [n](const float *a, int i, int j) {
-        return a[((i + n) % n) * n + ((j + n) % n)];
+        i = i < 0 ? i + n : (i >= n ? i - n : i);
+        j = j < 0 ? j + n : (j >= n ? j - n : j);
+        return a[i * n + j];
     };
     for (int t = 0; t < p.t_max; ++t) {
         // 1-2. x and y by row-wise shrinkage (Eq. x_update, Eq. y_update)
@@ -528,36 +691,58 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
             float acc = zs[k];
             for (int m = 0; m < nt; ++m) acc = fmaf(__ldg(Q + (size_t)m * nt + k), wv[m], acc);
             t0[k] = acc;
-            reinterpret_cast<int *>(t1)[k] = 1;
         }
-        // Euclidean projection onto the simplex by Michelot's exact active-set
-        // iteration (same projection as the sort-based method).
-        float tau = 0.f;
-        for (int pass = 0; pass <= nt; ++pass) {
-            __syncthreads();
-            double s = 0.0, cnt = 0.0;
-            for (int k = tid; k < nt; k += nthr)
-                if (reinterpret_cast<int *>(t1)[k]) {
-                    s += t0[k];
-                    cnt += 1.0;
-                }
-            double S, C;
-            block_sum2(s, cnt, red, S, C);
-            tau = (float)((1.0 - S) / C);
-            __syncthreads();
-            if (tid == 0) *flag = 0;
-            __syncthreads();
+        __syncthreads();
+        // Euclidean projection onto the simplex (the sort-based method): the
+        // position of each entry in descending order (ties by index) and the
+        // sum of the entries up to it give the largest position rho with
+        // v_rho + (1 - S_rho)/rho > 0 and tau = (1 - S_rho)/rho, without a sort.
+        {
+            int best = 0;
+            float btau = 0.f;
             for (int k = tid; k < nt; k += nthr) {
-                int *act = reinterpret_cast<int *>(t1);
-                if (act[k] && !(t0[k] + tau > 0.f)) {
-                    act[k] = 0;
-                    *flag = 1;
+                const float wk = t0[k];
+                int rk = 1;
+                float sk = wk;
+                for (int m = 0; m < nt; ++m) {
+                    const float wm = t0[m];
+                    if (wm > wk || (wm == wk && m < k)) {
+                        ++rk;
+                        sk += wm;
+                    }
+                }
+                const float tk = (1.0f - sk) / (float)rk;
+                if (wk + tk > 0.0f && rk > best) {
+                    best = rk;
+                    btau = tk;
                 }
             }
+            for (int o = 16; o > 0; o >>= 1) {
+                const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const float ot = __shfl_xor_sync(0xffffffffu, btau, o);
+                if (ob > best) {
+                    best = ob;
+                    btau = ot;
+                }
+            }
+            if ((tid & 31) == 0) {
+                red[tid >> 5] = (double)best;
+                red[32 + (tid >> 5)] = (double)btau;
+            }
             __syncthreads();
-            if (*flag == 0) break;
+            if (tid == 0) {
+                double bb = -1.0, bt = 0.0;
+                for (int k = 0; k < (nthr >> 5); ++k)
+                    if (red[k] > bb) {
+                        bb = red[k];
+                        bt = red[32 + k];
+                    }
+                red[0] = bt;
+            }
+            __syncthreads();
+            const float tau = (float)red[0];
+            for (int k = tid; k < nt; k += nthr) z[k] = fmaxf(t0[k] + tau, 0.f);
         }
-        for (int k = tid; k < nt; k += nthr) z[k] = fmaxf(t0[k] + tau, 0.f);
         __syncthreads();
         // 4. {u, p} (Appendix A, with + mu3 (z - Lambda3) in B1 and + mu3 in d1)
         for (int k = tid; k < nt; k += nthr) {

@@ -29,7 +29,7 @@ __device__ __forceinline__ int wrapm(int i, int n) {
 template <int RW>
 __global__ void __launch_bounds__(256) pan_stats_kernel(
     const float *__restrict__ Y, int H, int W, float eps, float *__restrict__ I,
-    float *__restrict__ mu, float *__restrict__ s) {
+    float *__restrict__ mu, float *__restrict__ s, float4 *__restrict__ st4) {
     constexpr int TX = 32, TY = 8;
     constexpr int GY = TY + 2 * RW + 2, GX = TX + 2 * RW + 2;
     constexpr int IY = TY + 2 * RW, IX = TX + 2 * RW;
@@ -64,37 +64,60 @@ __global__ void __launch_bounds__(256) pan_stats_kernel(
         const double m = s1 / nw;
         const double var = s2 / nw - m * m;
         const size_t o = (size_t)y * W + x;
-        I[o] = (float)sI[threadIdx.y + RW][threadIdx.x + RW];
-        mu[o] = (float)m;
-        s[o] = (float)(1.0 / (var + (double)eps));
+        const float iv = (float)sI[threadIdx.y + RW][threadIdx.x + RW];
+        const float mv = (float)m, sv = (float)(1.0 / (var + (double)eps));
+        if (I) {
+            I[o] = iv;
+            mu[o] = mv;
+            s[o] = sv;
+        }
+        if (st4) st4[o] = make_float4(iv, mv, sv, 0.0f);
     }
 }
 
+// (I, mu, s) -> one float4 per pixel, the layout the LLP kernel reads.
+__global__ void pack_stats_kernel(const float *__restrict__ I, const float *__restrict__ mu,
+                                  const float *__restrict__ s, size_t n, float4 *__restrict__ st4) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        st4[k] = make_float4(I[k], mu[k], s[k], 0.0f);
+}
+
+void launch_pack_stats(const float *I, const float *mu, const float *s, size_t n, float4 *st4,
+                       cudaStream_t st) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    pack_stats_kernel<<<blocks, 256, 0, st>>>(I, mu, s, n, st4);
+}
+
 void launch_pan_stats(const float *Y, int H, int W, int r, float eps, float *I,
-                      float *mu, float *s, cudaStream_t st) {
+                      float *mu, float *s, float4 *st4, cudaStream_t st) {
     dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
     switch (r) {
-        case 1: pan_stats_kernel<1><<<grd, blk, 0, st>>>(Y, H, W, eps, I, mu, s); break;
-        case 2: pan_stats_kernel<2><<<grd, blk, 0, st>>>(Y, H, W, eps, I, mu, s); break;
-        case 3: pan_stats_kernel<3><<<grd, blk, 0, st>>>(Y, H, W, eps, I, mu, s); break;
-        default: pan_stats_kernel<4><<<grd, blk, 0, st>>>(Y, H, W, eps, I, mu, s); break;
+        case 1: pan_stats_kernel<1><<<grd, blk, 0, st>>>(Y, H, W, eps, I, mu, s, st4); break;
+        case 2: pan_stats_kernel<2><<<grd, blk, 0, st>>>(Y, H, W, eps, I, mu, s, st4); break;
+        case 3: pan_stats_kernel<3><<<grd, blk, 0, st>>>(Y, H, W, eps, I, mu, s, st4); break;
+        default: pan_stats_kernel<4><<<grd, blk, 0, st>>>(Y, H, W, eps, I, mu, s, st4); break;
     }
 }
 
 // ----------------------------------------------------------------------------
 // v = D B(u) z on the LR grid. One thread per LR site over an 8 x 32 LR tile;
-// the HR footprint (c*8 + 2R) x (c*32 + 2R) is staged in shared memory.
+// the HR footprint (c*8 + 2R) x (c*32 + 2R) is staged in shared memory split
+// by column phase (column x stored in plane x mod c at x / c), so that the
+// 32 sites of a warp, c columns apart on the HR grid, read consecutive words.
 // In CG mode the staged value is p_new = r + beta p_old (beta = 0: p_new = r),
 // and every CTA also writes p_new for the HR block its LR sites own.
 // ----------------------------------------------------------------------------
-constexpr int DB_TLX = 32, DB_TLY = 8;
+constexpr int DB_TLX = 32, DB_TLY = 8, DB_TY = 4;   // 128 threads, 2 sites each
 
-__global__ void __launch_bounds__(256) db_kernel(
+__global__ void __launch_bounds__(128) db_kernel(
     const float *__restrict__ src, const float *__restrict__ rsrc,
-    float *__restrict__ pdst, const CgBand *bands, const CgGlobal *g, int cg,
+    float *__restrict__ pdst, CgBand *bands, const CgGlobal *g, int cg,
     int H, int W, int c, const float *__restrict__ u, int R,
     float *__restrict__ v) {
     extern __shared__ float sm[];
+    __shared__ float vred[4];
     const int b = blockIdx.z;
     float beta = 0.0f;
     bool use_old = false;
@@ -110,79 +133,143 @@ __global__ void __launch_bounds__(256) db_kernel(
     float *su = sm;
     float *sp = sm + ((nt + 3) & ~3);
     const int FY = c * DB_TLY + 2 * R, FX = c * DB_TLX + 2 * R;
+    const int FXp = (FX + c - 1) / c, plane = FY * FXp;
     const int ky0 = blockIdx.y * DB_TLY, kx0 = blockIdx.x * DB_TLX;
     const int oy = c * ky0 - R, ox = c * kx0 - R;
-    const int tid = threadIdx.y * DB_TLX + threadIdx.x;
-    for (int k = tid; k < nt; k += 256) su[k] = u[k];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * DB_TLX + tx;
+    for (int k = tid; k < nt; k += 128) su[k] = u[k];
     const float *S = src + (size_t)b * HW;
     const float *Rr = cg ? rsrc + (size_t)b * HW : nullptr;
     float *P = cg ? pdst + (size_t)b * HW : nullptr;
-    for (int k = tid; k < FY * FX; k += 256) {
-        const int yy = k / FX, xx = k - (k / FX) * FX;
-        const size_t gi = (size_t)wrapm(oy + yy, H) * W + wrapm(ox + xx, W);
-        float val;
-        if (cg) {
-            val = use_old ? fmaf(beta, S[gi], Rr[gi]) : Rr[gi];
-            if (yy >= R && yy < R + c * DB_TLY && xx >= R && xx < R + c * DB_TLX) {
-                const int hy = c * ky0 + (yy - R), hx = c * kx0 + (xx - R);
-                if (hy < H && hx < W) P[(size_t)hy * W + hx] = val;
+    // column walk of this thread: xx = tx + 32 m, phase and index within it
+    const int step_ph = 32 % c, step_q = 32 / c;
+    for (int yy = ty; yy < FY; yy += DB_TY) {
+        const size_t grow = (size_t)wrapm(oy + yy, H) * W;
+        const bool own_row = cg && yy >= R && yy < R + c * DB_TLY && c * ky0 + (yy - R) < H;
+        int ph = tx % c, q = tx / c;
+        int gx = wrapm(ox + tx, W);
+        for (int xx = tx; xx < FX; xx += 32) {
+            const size_t gi = grow + gx;
+            float val;
+            if (cg) {
+                val = use_old ? fmaf(beta, S[gi], Rr[gi]) : Rr[gi];
+                if (own_row && xx >= R && xx < R + c * DB_TLX) {
+                    const int hx = c * kx0 + (xx - R);
+                    if (hx < W) P[(size_t)(c * ky0 + (yy - R)) * W + hx] = val;
+                }
+            } else {
+                val = S[gi];
             }
-        } else {
-            val = S[gi];
+            sp[ph * plane + yy * FXp + q] = val;
+            ph += step_ph;
+            q += step_q;
+            if (ph >= c) {
+                ph -= c;
+                ++q;
+            }
+            gx += 32;
+            while (gx >= W) gx -= W;
         }
-        sp[k] = val;
     }
     __syncthreads();
-    const int ly = threadIdx.y, lx = threadIdx.x;
-    const int ky = ky0 + ly, kx = kx0 + lx;
-    if (ky < h && kx < w) {
-        float acc = 0.0f;
-        for (int i = -R; i <= R; ++i) {
-            const float *row = sp + (c * ly - i + R) * FX + c * lx + R;
-            const float *ur = su + (i + R) * n + R;
-            for (int j = -R; j <= R; ++j) acc = fmaf(ur[j], row[-j], acc);
+    // sites (ty, tx) and (ty + 4, tx). Sample (c ky - i, c kx - j): footprint
+    // row c ty - i + R, column c tx + t with t = R - j, i.e. plane t mod c,
+    // index tx + t / c.
+    float acc0 = 0.0f, acc1 = 0.0f;
+    const int rstep = c * DB_TY * FXp;
+    for (int i = -R; i <= R; ++i) {
+        const int row = c * ty - i + R;
+        const float *ur = su + (i + R) * n + 2 * R;   // tap j = R - t at ur[-t]
+        for (int ph = 0; ph < c; ++ph) {
+            const float *b0 = sp + ph * plane + row * FXp + tx;
+            const float *b1 = b0 + rstep;
+            const float *uu = ur - ph;
+            const int cnt = (ph <= 2 * R) ? (2 * R - ph) / c + 1 : 0;
+            for (int qq = 0; qq < cnt; ++qq) {
+                const float uv = uu[-c * qq];
+                acc0 = fmaf(uv, b0[qq], acc0);
+                acc1 = fmaf(uv, b1[qq], acc1);
+            }
         }
-        v[(size_t)b * h * w + (size_t)ky * w + kx] = acc;
+    }
+    const int kx = kx0 + tx;
+    const int ky_a = ky0 + ty, ky_b = ky0 + ty + DB_TY;
+    float vv = 0.0f;
+    if (kx < w) {
+        if (ky_a < h) {
+            v[(size_t)b * h * w + (size_t)ky_a * w + kx] = acc0;
+            vv = acc0 * acc0;
+        }
+        if (ky_b < h) {
+            v[(size_t)b * h * w + (size_t)ky_b * w + kx] = acc1;
+            vv = fmaf(acc1, acc1, vv);
+        }
+    }
+    if (cg) {
+        for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
+        if (tx == 0) vred[ty] = vv;
+        __syncthreads();
+        if (tid == 0)
+            atomicAdd(&bands[b].vv, (double)vred[0] + (double)vred[1] + (double)vred[2] +
+                                        (double)vred[3]);
     }
 }
 
 size_t db_smem_bytes(int c, int R) {
     const int n = 2 * R + 1;
-    return sizeof(float) * (((n * n + 3) & ~3) +
-                            (size_t)(c * DB_TLY + 2 * R) * (c * DB_TLX + 2 * R));
+    const int FY = c * DB_TLY + 2 * R, FX = c * DB_TLX + 2 * R;
+    const int FXp = (FX + c - 1) / c;
+    return sizeof(float) * (((n * n + 3) & ~3) + (size_t)c * FY * FXp);
 }
 
 void launch_db(const float *src, const float *rsrc, float *pdst, const CgBand *bands,
                const CgGlobal *g, int cg, int N, int H, int W, int c, const float *u,
                int R, float *v, cudaStream_t st) {
+    if (launch_db_fast(src, rsrc, pdst, const_cast<CgBand *>(bands), g, cg, N, H, W, c, u, R, v,
+                       st))
+        return;
     const int h = H / c, w = W / c;
-    dim3 blk(DB_TLX, DB_TLY), grd((w + DB_TLX - 1) / DB_TLX, (h + DB_TLY - 1) / DB_TLY, N);
-    db_kernel<<<grd, blk, db_smem_bytes(c, R), st>>>(src, rsrc, pdst, bands, g, cg, H, W,
-                                                     c, u, R, v);
+    dim3 blk(DB_TLX, DB_TY), grd((w + DB_TLX - 1) / DB_TLX, (h + DB_TLY - 1) / DB_TLY, N);
+    db_kernel<<<grd, blk, db_smem_bytes(c, R), st>>>(src, rsrc, pdst, const_cast<CgBand *>(bands),
+                                                     g, cg, H, W, c, u, R, v);
 }
 
 // ----------------------------------------------------------------------------
-// Data term B(u)^T D^T v at one HR pixel: the taps (i, j) with
+// Data term B(u)^T D^T v at HR pixel (y, x): the taps (i, j) with
 // (y + i) = 0 and (x + j) = 0 (mod c) pick the LR sample ((y+i)/c, (x+j)/c).
+// The taps of a pixel form a grid of step c; the first tap and its LR index
+// are found once per axis, the others follow by increments.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ float adj_at(const float *__restrict__ vb, int h, int w, int H,
-                                        int W, int c, const float *su, int n, int R,
-                                        int y, int x) {
-    const int my = ((y - R) % c + c) % c;
-    const int mx = ((x - R) % c + c) % c;
-    const int i0 = -R + (c - my) % c;
-    const int j0 = -R + (c - mx) % c;
+struct AdjAxis {
+    int t0;  // first tap + R
+    int k0;  // LR index of the first tap
+};
+
+__device__ __forceinline__ AdjAxis adj_axis(int y, int Hs, int c, int R) {
+    int m = (y - R) % c;
+    if (m < 0) m += c;
+    const int i0 = -R + (c - m) % c;
+    int yy = y + i0;
+    if (yy < 0) yy += Hs;
+    else if (yy >= Hs) yy -= Hs;
+    return {i0 + R, yy / c};
+}
+
+__device__ __forceinline__ float adj_sum(const float *__restrict__ vb, int h, int w, int c,
+                                         int n, const float *su, AdjAxis ay, AdjAxis ax) {
     float acc = 0.0f;
-    for (int i = i0; i <= R; i += c) {
-        const int ky = wrapm(y + i, H) / c;
+    int ky = ay.k0;
+    for (int ti = ay.t0; ti < n; ti += c) {
         const float *vr = vb + (size_t)ky * w;
-        const float *ur = su + (i + R) * n + R;
-        for (int j = j0; j <= R; j += c) {
-            const int kx = wrapm(x + j, W) / c;
-            acc = fmaf(ur[j], __ldg(vr + kx), acc);
+        const float *ur = su + ti * n;
+        int kx = ax.k0;
+        for (int tj = ax.t0; tj < n; tj += c) {
+            acc = fmaf(ur[tj], __ldg(vr + kx), acc);
+            kx = (kx + 1 == w) ? 0 : kx + 1;
         }
+        ky = (ky + 1 == h) ? 0 : ky + 1;
     }
-    (void)h;
     return acc;
 }
 
@@ -200,7 +287,7 @@ __global__ void __launch_bounds__(256) adj_kernel(const float *__restrict__ v, i
     const int y = blockIdx.y * 8 + threadIdx.y, x = blockIdx.x * 32 + threadIdx.x;
     if (y >= H || x >= W) return;
     z[(size_t)b * H * W + (size_t)y * W + x] =
-        adj_at(v + (size_t)b * h * w, h, w, H, W, c, su, n, R, y, x);
+        adj_sum(v + (size_t)b * h * w, h, w, c, n, su, adj_axis(y, H, c, R), adj_axis(x, W, c, R));
 }
 
 void launch_adj(const float *v, int N, int H, int W, int c, const float *u, int R,
@@ -210,7 +297,7 @@ void launch_adj(const float *v, int N, int H, int W, int c, const float *u, int 
 }
 
 // ----------------------------------------------------------------------------
-// Fused LLP tile kernel. Output tile 32 x 32, 256 threads.
+// Fused LLP kernel, register-streaming form.
 //
 // For the input field alpha (alpha = L p in modes APPLY / ZRHS, alpha = q in
 // mode GF) every window j gets the affine fit of Eq. ac_h_compute,
@@ -220,205 +307,208 @@ void launch_adj(const float *v, int N, int H, int W, int c, const float *u, int 
 //   matting matrix  M alpha   = |w| alpha - Sa I - Sb = |w| (alpha - GF(alpha)).
 // Modes:
 //   APPLY: out = B^T D^T v + lam L M L p            (Eq. Z_ini_matting operator)
-//          and, in CG, p^T out accumulated per band (FP64) with the last CTA
-//          of the band computing alpha = r^T r / p^T A p.
+//   CGQ:   out = q = lam L M L p, the prior part of A p inside the CG loop, and
+//          p^T q accumulated per band (FP64); the band's last CTA computes
+//          alpha = r^T r / (||D B p||^2 + p^T q), the data part of p^T A p
+//          being ||v||^2 from db_kernel. The data part of A p itself,
+//          B^T D^T v, is added in cg_update_kernel.
 //   ZRHS:  out = B^T D^T X + lam L GF(L z0)          (Eq. Z_solution rhs),
 //          written into the packed complex FFT buffer (band 2k -> real,
 //          band 2k+1 -> imaginary part of image k).
 //   GF:    out = GF(q).
-// Shared-memory regions (relative to the tile origin, G = 2r+2):
-//   P   = input on T+G          A, I, IA = alpha, I, I*alpha on T+(2r+1)
-//   HS  = row sums on rows T+(2r+1), cols T+(r+1)
-//   AB  = a, b on T+(r+1)      HAB = row sums of a, b on rows T+(r+1), cols T+1
-//   MM  = M alpha or GF(alpha) on T+1
+//
+// Each warp owns a strip of 32 columns and walks down LLP_TY output rows plus
+// a halo of G rows on each side. Every stage of the chain (Laplacian, row and
+// column window sums, affine fit, second window sums, final Laplacian) is
+// kept in registers as a short rolling buffer of rows; horizontal neighbours
+// come from warp shuffles, so lanes near the strip edges only feed their
+// neighbours and the 32 - 2G middle lanes produce outputs.
 // ----------------------------------------------------------------------------
-constexpr int LT = 32;
+constexpr int LLP_WARPS = 4;
+constexpr unsigned FULL = 0xffffffffu;
 
+// Output rows per warp: for r = 1 a multiple of 3, so that the 3-deep rolling
+// buffers cycle within the 3-way unrolled walk and need no register moves.
 template <int RW>
-struct LlpDims {
-    static constexpr int G = 2 * RW + 2;
-    static constexpr int AO = 2 * RW + 1, BO = RW + 1;
-    static constexpr int PY = LT + 2 * G, PX = PY;
-    static constexpr int AY = LT + 2 * AO, AX = AY;
-    static constexpr int BY = LT + 2 * BO, BX = BY;
-    static constexpr int CY = LT + 2, CX = CY;
-    static constexpr int szP = PY * PX, szA = AY * AX, szHS = AY * BX, szB = BY * BX,
-                         szHB = BY * CX, szC = CY * CX;
-    static constexpr int total = szP + 3 * szA + 2 * szHS + 2 * szB + 2 * szHB + szC;
+struct LlpRows {
+    static constexpr int TY = (RW == 1) ? 66 : 64;
+    static constexpr int UNR = (RW == 1) ? 3 : 1;
 };
 
-template <int RW>
-size_t llp_smem_bytes_t() {
-    return sizeof(float) * (LlpDims<RW>::total + ((kMaxTaps + 3) & ~3)) + 64 * sizeof(double);
-}
-
-size_t llp_smem_bytes(int r) {
-    switch (r) {
-        case 1: return llp_smem_bytes_t<1>();
-        case 2: return llp_smem_bytes_t<2>();
-        case 3: return llp_smem_bytes_t<3>();
-        default: return llp_smem_bytes_t<4>();
-    }
-}
-
 template <int RW, int MODE>
-__global__ void __launch_bounds__(256) llp_kernel(LlpArgs a) {
-    using D = LlpDims<RW>;
-    extern __shared__ float sm[];
+__global__ void __launch_bounds__(128) llp_kernel(LlpArgs a) {
+    constexpr int G = (MODE == LLP_GF) ? 2 * RW : 2 * RW + 2;
+    constexpr int VALID = 32 - 2 * G;
+    constexpr int NB = 2 * RW + 1;
+    constexpr int TY = LlpRows<RW>::TY;
+    constexpr float nw = (float)(NB * NB);
+    constexpr float inw = 1.0f / nw;
+    constexpr bool DATA = (MODE == LLP_APPLY || MODE == LLP_ZRHS);
+    constexpr bool MATT = (MODE == LLP_APPLY || MODE == LLP_CGQ);
+    __shared__ float su[kMaxTaps];
+    __shared__ double red[LLP_WARPS];
     const int b = blockIdx.z;
-    if (MODE == LLP_APPLY && a.cg) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (MODE == LLP_CGQ) {
         if (a.g->stop || a.bands[b].done) return;
     }
-    float *sP = sm;
-    float *sA = sP + D::szP;
-    float *sI = sA + D::szA;
-    float *sIA = sI + D::szA;
-    float *hS1 = sIA + D::szA;
-    float *hS2 = hS1 + D::szHS;
-    float *sa = hS2 + D::szHS;
-    float *sb = sa + D::szB;
-    float *ha = sb + D::szB;
-    float *hb = ha + D::szHB;
-    float *sM = hb + D::szHB;
-    float *su = sM + D::szC;
-    double *red = reinterpret_cast<double *>(su + ((kMaxTaps + 3) & ~3));
-
     const int H = a.H, W = a.W;
-    const size_t HW = (size_t)H * W;
-    const int y0 = blockIdx.y * LT, x0 = blockIdx.x * LT;
-    const int tid = threadIdx.x;
-    const float *in = a.in + (size_t)b * HW;
-    constexpr float nw = (float)((2 * RW + 1) * (2 * RW + 1));
+    const int HWi = H * W;
+    const size_t HW = (size_t)HWi;
     const int n = 2 * a.R + 1;
-
-    if (MODE != LLP_GF)
-        for (int k = tid; k < n * n; k += 256) su[k] = a.u[k];
-
-    // Phase 0/1: alpha, I, I*alpha on T + (2r+1).
-    if (MODE == LLP_GF) {
-        for (int k = tid; k < D::szA; k += 256) {
-            const int yy = k / D::AX, xx = k - (k / D::AX) * D::AX;
-            const size_t gi = (size_t)wrapm(y0 - D::AO + yy, H) * W + wrapm(x0 - D::AO + xx, W);
-            const float al = in[gi], iv = a.I[gi];
-            sA[k] = al;
-            sI[k] = iv;
-            sIA[k] = iv * al;
-        }
-    } else {
-        for (int k = tid; k < D::szP; k += 256) {
-            const int yy = k / D::PX, xx = k - (k / D::PX) * D::PX;
-            sP[k] = in[(size_t)wrapm(y0 - D::G + yy, H) * W + wrapm(x0 - D::G + xx, W)];
-        }
+    if (DATA) {
+        for (int k = tid; k < n * n; k += blockDim.x) su[k] = a.u[k];
         __syncthreads();
-        for (int k = tid; k < D::szA; k += 256) {
-            const int yy = k / D::AX, xx = k - (k / D::AX) * D::AX;
-            const float *pc = sP + (yy + 1) * D::PX + (xx + 1);
-            const float al = 4.0f * pc[0] - pc[-D::PX] - pc[D::PX] - pc[-1] - pc[1];
-            const float iv =
-                a.I[(size_t)wrapm(y0 - D::AO + yy, H) * W + wrapm(x0 - D::AO + xx, W)];
-            sA[k] = al;
-            sI[k] = iv;
-            sIA[k] = iv * al;
-        }
     }
-    __syncthreads();
-    // Phase 2: row sums over 2r+1 columns.
-    for (int k = tid; k < D::szHS; k += 256) {
-        const int yy = k / D::BX, xx = k - (k / D::BX) * D::BX;
-        const float *r1 = sA + yy * D::AX + xx;
-        const float *r2 = sIA + yy * D::AX + xx;
-        float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int d = 0; d <= 2 * RW; ++d) {
-            s1 += r1[d];
-            s2 += r2[d];
-        }
-        hS1[k] = s1;
-        hS2[k] = s2;
-    }
-    __syncthreads();
-    // Phase 3: column sums -> window means -> affine fit (a, b) on T + (r+1).
-    for (int k = tid; k < D::szB; k += 256) {
-        const int yy = k / D::BX, xx = k - (k / D::BX) * D::BX;
-        float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int d = 0; d <= 2 * RW; ++d) {
-            s1 += hS1[(yy + d) * D::BX + xx];
-            s2 += hS2[(yy + d) * D::BX + xx];
-        }
-        const size_t gi = (size_t)wrapm(y0 - D::BO + yy, H) * W + wrapm(x0 - D::BO + xx, W);
-        const float m = a.mu[gi], sv = a.s[gi];
-        const float ma = s1 * (1.0f / nw), mia = s2 * (1.0f / nw);
-        const float av = (mia - m * ma) * sv;
-        sa[k] = av;
-        sb[k] = ma - av * m;
-    }
-    __syncthreads();
-    // Phase 4: row sums of a, b.
-    for (int k = tid; k < D::szHB; k += 256) {
-        const int yy = k / D::CX, xx = k - (k / D::CX) * D::CX;
-        const float *r1 = sa + yy * D::BX + xx;
-        const float *r2 = sb + yy * D::BX + xx;
-        float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int d = 0; d <= 2 * RW; ++d) {
-            s1 += r1[d];
-            s2 += r2[d];
-        }
-        ha[k] = s1;
-        hb[k] = s2;
-    }
-    __syncthreads();
-    // Phase 5: column sums -> M alpha (APPLY) or GF(alpha) (ZRHS, GF) on T + 1.
-    for (int k = tid; k < D::szC; k += 256) {
-        const int yy = k / D::CX, xx = k - (k / D::CX) * D::CX;
-        float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int d = 0; d <= 2 * RW; ++d) {
-            s1 += ha[(yy + d) * D::CX + xx];
-            s2 += hb[(yy + d) * D::CX + xx];
-        }
-        const int ai = (yy + 2 * RW) * D::AX + (xx + 2 * RW);
-        const float iv = sI[ai];
-        if (MODE == LLP_APPLY)
-            sM[k] = nw * sA[ai] - s1 * iv - s2;
-        else
-            sM[k] = (s1 * iv + s2) * (1.0f / nw);
-    }
-    __syncthreads();
-    // Phase 6: outputs.
-    const int h = H / a.c, w = W / a.c;
+    const int x0 = blockIdx.x * VALID;
+    const int y0 = (blockIdx.y * LLP_WARPS + warp) * TY;
+    const int xl = x0 - G + lane;
+    const int gx = wrapm(xl, W);
+    const bool out_lane = lane >= G && lane < 32 - G && xl < W;
+    const float *in = a.in + (size_t)b * HW;
+    const float4 *st4 = a.st4;
+    const int c = a.c;
+    const int h = H / c, w = W / c;
     float part = 0.0f;
-    for (int k = tid; k < LT * LT; k += 256) {
-        const int ty = k >> 5, tx = k & 31;
-        const int y = y0 + ty, x = x0 + tx;
-        if (y >= H || x >= W) continue;
-        const float *mc = sM + (ty + 1) * D::CX + (tx + 1);
-        float val;
-        if (MODE == LLP_GF) {
-            val = mc[0];
-        } else {
-            const float lm = 4.0f * mc[0] - mc[-D::CX] - mc[D::CX] - mc[-1] - mc[1];
-            const float dat = adj_at(a.lr + (size_t)b * h * w, h, w, H, W, a.c, su, n, a.R, y, x);
-            val = fmaf(a.lam, lm, dat);
+
+    if (y0 < H) {
+        const AdjAxis ax = DATA ? adj_axis(gx, W, c, a.R) : AdjAxis{0, 0};
+        const float *lrb = DATA ? a.lr + (size_t)b * h * w : nullptr;
+        // row offsets (row * W) of the input row, the alpha row and the output row
+        int rowIn = wrapm(y0 - G, H) * W;
+        int rowA = ((MODE == LLP_GF) ? wrapm(y0 - G, H) : wrapm(y0 - G - 1, H)) * W;
+        int gyD = wrapm(y0, H);
+        int rowD = gyD * W;
+        float pm2 = 0.f, pm1 = 0.f, p0 = 0.f;
+        float hA[NB], hIA[NB], ab[NB], ib[NB], ha[NB], hb[NB], mub[RW + 1], sb[RW + 1];
+#pragma unroll
+        for (int d = 0; d < NB; ++d) hA[d] = hIA[d] = ab[d] = ib[d] = ha[d] = hb[d] = 0.f;
+#pragma unroll
+        for (int d = 0; d <= RW; ++d) mub[d] = sb[d] = 0.f;
+        float mm2 = 0.f, mm1 = 0.f, m0 = 0.f;
+
+        // one row of the chain; returns the chain output for the row 2G - G
+        // behind the input row (valid once the buffers are full)
+        auto advance = [&]() -> float {
+            const float pin = in[rowIn + gx];
+            float al;
+            if (MODE == LLP_GF) {
+                al = pin;
+            } else {
+                pm2 = pm1;
+                pm1 = p0;
+                p0 = pin;
+                al = 4.0f * pm1 - pm2 - p0 - __shfl_up_sync(FULL, pm1, 1) -
+                     __shfl_down_sync(FULL, pm1, 1);
+            }
+            const float4 stv = st4[rowA + gx];
+            const float iv = stv.x;
+            const float ia = iv * al;
+            float h1 = al, h2 = ia;
+#pragma unroll
+            for (int d = 1; d <= RW; ++d) {
+                h1 += __shfl_up_sync(FULL, al, d) + __shfl_down_sync(FULL, al, d);
+                h2 += __shfl_up_sync(FULL, ia, d) + __shfl_down_sync(FULL, ia, d);
+            }
+#pragma unroll
+            for (int d = 0; d < NB - 1; ++d) {
+                hA[d] = hA[d + 1];
+                hIA[d] = hIA[d + 1];
+                ab[d] = ab[d + 1];
+                ib[d] = ib[d + 1];
+            }
+            hA[NB - 1] = h1;
+            hIA[NB - 1] = h2;
+            ab[NB - 1] = al;
+            ib[NB - 1] = iv;
+#pragma unroll
+            for (int d = 0; d < RW; ++d) {
+                mub[d] = mub[d + 1];
+                sb[d] = sb[d + 1];
+            }
+            mub[RW] = stv.y;
+            sb[RW] = stv.z;
+            float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < NB; ++d) {
+                s1 += hA[d];
+                s2 += hIA[d];
+            }
+            const float mu = mub[0], sv = sb[0];
+            const float ma = s1 * inw, mia = s2 * inw;
+            const float av = (mia - mu * ma) * sv;
+            const float bv = ma - av * mu;
+            float g1 = av, g2 = bv;
+#pragma unroll
+            for (int d = 1; d <= RW; ++d) {
+                g1 += __shfl_up_sync(FULL, av, d) + __shfl_down_sync(FULL, av, d);
+                g2 += __shfl_up_sync(FULL, bv, d) + __shfl_down_sync(FULL, bv, d);
+            }
+#pragma unroll
+            for (int d = 0; d < NB - 1; ++d) {
+                ha[d] = ha[d + 1];
+                hb[d] = hb[d + 1];
+            }
+            ha[NB - 1] = g1;
+            hb[NB - 1] = g2;
+            float sa = 0.f, sbb = 0.f;
+#pragma unroll
+            for (int d = 0; d < NB; ++d) {
+                sa += ha[d];
+                sbb += hb[d];
+            }
+            rowIn += W;
+            if (rowIn == HWi) rowIn = 0;
+            rowA += W;
+            if (rowA == HWi) rowA = 0;
+            // alpha and I of the row whose window sums are complete: ab[0], ib[0]
+            if (MODE == LLP_GF) return (sa * ib[0] + sbb) * inw;
+            const float mv = MATT ? nw * ab[0] - sa * ib[0] - sbb : (sa * ib[0] + sbb) * inw;
+            mm2 = mm1;
+            mm1 = m0;
+            m0 = mv;
+            return 4.0f * mm1 - mm2 - m0 - __shfl_up_sync(FULL, mm1, 1) -
+                   __shfl_down_sync(FULL, mm1, 1);
+        };
+
+        for (int step = 0; step < 2 * G; ++step) (void)advance();
+#pragma unroll LlpRows<RW>::UNR
+        for (int yy = 0; yy < TY; ++yy) {
+            float val = advance();
+            if (out_lane && y0 + yy < H) {
+                const int o = rowD + gx;
+                if (DATA) {
+                    const float dat = adj_sum(lrb, h, w, c, n, su, adj_axis(gyD, H, c, a.R), ax);
+                    val = fmaf(a.lam, val, dat);
+                } else if (MODE == LLP_CGQ) {
+                    val *= a.lam;
+                }
+                if (MODE == LLP_ZRHS) {
+                    double2 *cimg = a.cout + (size_t)(b >> 1) * HW + o;
+                    if (b & 1)
+                        reinterpret_cast<double *>(cimg)[1] = (double)val;
+                    else if (b == a.N - 1)
+                        *cimg = make_double2((double)val, 0.0);
+                    else
+                        reinterpret_cast<double *>(cimg)[0] = (double)val;
+                } else {
+                    a.out[(size_t)b * HW + o] = val;
+                }
+                if (MODE == LLP_CGQ) part = fmaf(in[o], val, part);
+            }
+            rowD += W;
+            if (rowD == HWi) rowD = 0;
+            if (DATA) gyD = (gyD + 1 == H) ? 0 : gyD + 1;
         }
-        const size_t o = (size_t)y * W + x;
-        if (MODE == LLP_ZRHS) {
-            float2 *cimg = a.cout + (size_t)(b >> 1) * HW + o;
-            if (b & 1)
-                reinterpret_cast<float *>(cimg)[1] = val;
-            else if (b == a.N - 1)
-                *cimg = make_float2(val, 0.0f);
-            else
-                reinterpret_cast<float *>(cimg)[0] = val;
-        } else {
-            a.out[(size_t)b * HW + o] = val;
-        }
-        if (MODE == LLP_APPLY && a.cg) part = fmaf(sP[(ty + D::G) * D::PX + (tx + D::G)], val, part);
     }
-    if (MODE == LLP_APPLY && a.cg) {
-        const double tot = block_sum_d((double)part, red);
+    if (MODE == LLP_CGQ) {
+        double pd = (double)part;
+        for (int o = 16; o > 0; o >>= 1) pd += __shfl_xor_sync(FULL, pd, o);
+        if (lane == 0) red[warp] = pd;
+        __syncthreads();
         if (tid == 0) {
+            double tot = 0.0;
+            for (int k = 0; k < LLP_WARPS; ++k) tot += red[k];
             CgBand *bd = a.bands + b;
             atomicAdd(&bd->pAp, tot);
             __threadfence();
@@ -426,7 +516,8 @@ __global__ void __launch_bounds__(256) llp_kernel(LlpArgs a) {
             const unsigned int t = atomicAdd(&bd->cnt_apply, 1u);
             if (t == nblk - 1) {
                 __threadfence();
-                const double pAp = atomicAdd(&bd->pAp, 0.0);
+                // p^T A p = ||D B p||^2 + p^T (lam L^T M L) p
+                const double pAp = atomicAdd(&bd->pAp, 0.0) + bd->vv;
                 const double rr = bd->rr;
                 bd->cnt_apply = 0u;
                 if (!isfinite(pAp)) {
@@ -445,44 +536,35 @@ __global__ void __launch_bounds__(256) llp_kernel(LlpArgs a) {
     }
 }
 
+size_t llp_smem_bytes(int) { return 0; }
+
 template <int RW>
-static void launch_llp_r(const LlpArgs &a, int mode, dim3 grd, cudaStream_t st) {
-    const size_t sm = llp_smem_bytes_t<RW>();
+static void launch_llp_r(const LlpArgs &a, int mode, int N, cudaStream_t st) {
+    const int G = (mode == LLP_GF) ? 2 * RW : 2 * RW + 2;
+    const int valid = 32 - 2 * G;
+    const int rows = LlpRows<RW>::TY * LLP_WARPS;
+    dim3 grd((a.W + valid - 1) / valid, (a.H + rows - 1) / rows, N);
     switch (mode) {
-        case LLP_APPLY: llp_kernel<RW, LLP_APPLY><<<grd, 256, sm, st>>>(a); break;
-        case LLP_ZRHS: llp_kernel<RW, LLP_ZRHS><<<grd, 256, sm, st>>>(a); break;
-        default: llp_kernel<RW, LLP_GF><<<grd, 256, sm, st>>>(a); break;
+        case LLP_APPLY: llp_kernel<RW, LLP_APPLY><<<grd, 32 * LLP_WARPS, 0, st>>>(a); break;
+        case LLP_ZRHS: llp_kernel<RW, LLP_ZRHS><<<grd, 32 * LLP_WARPS, 0, st>>>(a); break;
+        case LLP_CGQ: llp_kernel<RW, LLP_CGQ><<<grd, 32 * LLP_WARPS, 0, st>>>(a); break;
+        default: llp_kernel<RW, LLP_GF><<<grd, 32 * LLP_WARPS, 0, st>>>(a); break;
     }
 }
 
-template <int RW>
-static cudaError_t llp_set_attrs_r() {
-    const int sm = (int)llp_smem_bytes_t<RW>();
-    cudaError_t e;
-    e = cudaFuncSetAttribute(llp_kernel<RW, LLP_APPLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(llp_kernel<RW, LLP_ZRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(llp_kernel<RW, LLP_GF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-}
-
 cudaError_t operators_set_attrs() {
-    cudaError_t e;
-    if ((e = llp_set_attrs_r<1>()) != cudaSuccess) return e;
-    if ((e = llp_set_attrs_r<2>()) != cudaSuccess) return e;
-    if ((e = llp_set_attrs_r<3>()) != cudaSuccess) return e;
-    if ((e = llp_set_attrs_r<4>()) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(db_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)db_smem_bytes(8, kMaxR));
+    cudaError_t e = cudaFuncSetAttribute(db_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)db_smem_bytes(8, kMaxR));
+    if (e != cudaSuccess) return e;
+    return cg_fast_set_attrs();
 }
 
 void launch_llp(const LlpArgs &a, int mode, int r, int N, cudaStream_t st) {
-    dim3 grd((a.W + LT - 1) / LT, (a.H + LT - 1) / LT, N);
     switch (r) {
-        case 1: launch_llp_r<1>(a, mode, grd, st); break;
-        case 2: launch_llp_r<2>(a, mode, grd, st); break;
-        case 3: launch_llp_r<3>(a, mode, grd, st); break;
-        default: launch_llp_r<4>(a, mode, grd, st); break;
+        case 1: launch_llp_r<1>(a, mode, N, st); break;
+        case 2: launch_llp_r<2>(a, mode, N, st); break;
+        case 3: launch_llp_r<3>(a, mode, N, st); break;
+        default: launch_llp_r<4>(a, mode, N, st); break;
     }
 }
 
@@ -550,6 +632,7 @@ __global__ void __launch_bounds__(256) cg_init_kernel(const float4 *__restrict__
             bd->bb = b2;
             bd->rr_new = 0.0;
             bd->pAp = 0.0;
+            bd->vv = 0.0;
             bd->beta = 0.0;
             bd->alpha = 0.0;
             bd->iters = 0;
@@ -564,44 +647,67 @@ __global__ void __launch_bounds__(256) cg_init_kernel(const float4 *__restrict__
     }
 }
 
-// x += alpha p; r -= alpha Ap; the next r^T r; the band's last CTA takes
-// beta, the convergence test and the iteration cap.
-__global__ void __launch_bounds__(256) cg_update_kernel(float4 *__restrict__ x,
+// x += alpha p; r -= alpha (B^T D^T v + q); the next r^T r. The data part of
+// A p is formed here from the LR samples v = D B p (held in L2) rather than in
+// the stencil kernel, where it would cost issue slots that this kernel, bound
+// by HBM, has to spare. One CTA covers 128 float4 of one row; the band's last
+// CTA takes beta, the convergence test and the iteration cap.
+__global__ void __launch_bounds__(128) cg_update_kernel(float4 *__restrict__ x,
                                                         float4 *__restrict__ r,
                                                         const float4 *__restrict__ p,
-                                                        const float4 *__restrict__ ap,
-                                                        size_t n4, CgBand *bands,
+                                                        const float4 *__restrict__ q,
+                                                        const float *__restrict__ v,
+                                                        const float *__restrict__ u, int R,
+                                                        int c, int H, int W, CgBand *bands,
                                                         const CgGlobal *g) {
-    __shared__ double red[8];
-    const int b = blockIdx.y;
+    __shared__ float su[kMaxTaps];
+    __shared__ double red[4];
+    const int b = blockIdx.z, y = blockIdx.y;
     if (g->stop || bands[b].done) return;
+    const int n = 2 * R + 1;
+    for (int k = threadIdx.x; k < n * n; k += 128) su[k] = u[k];
+    __syncthreads();
     const float al = (float)bands[b].alpha;
-    const size_t off = (size_t)b * n4;
-    double rr = 0.0;
-    for (size_t i = blockIdx.x * 256 + threadIdx.x; i < n4; i += (size_t)gridDim.x * 256) {
-        float4 xv = x[off + i], rv = r[off + i];
-        const float4 pv = p[off + i], av = ap[off + i];
+    const int W4 = W >> 2, h = H / c, w = W / c;
+    const int x4 = blockIdx.x * 128 + threadIdx.x;
+    float rrf = 0.0f;
+    if (x4 < W4) {
+        const size_t o = ((size_t)b * H + y) * W4 + x4;
+        const AdjAxis ay = adj_axis(y, H, c, R);
+        const float *vb = v + (size_t)b * h * w;
+        const int x0 = 4 * x4;
+        const float d0 = adj_sum(vb, h, w, c, n, su, ay, adj_axis(x0, W, c, R));
+        const float d1 = adj_sum(vb, h, w, c, n, su, ay, adj_axis(x0 + 1, W, c, R));
+        const float d2 = adj_sum(vb, h, w, c, n, su, ay, adj_axis(x0 + 2, W, c, R));
+        const float d3 = adj_sum(vb, h, w, c, n, su, ay, adj_axis(x0 + 3, W, c, R));
+        float4 xv = x[o], rv = r[o];
+        const float4 pv = p[o], qv = q[o];
         xv.x = fmaf(al, pv.x, xv.x); xv.y = fmaf(al, pv.y, xv.y);
         xv.z = fmaf(al, pv.z, xv.z); xv.w = fmaf(al, pv.w, xv.w);
-        rv.x = fmaf(-al, av.x, rv.x); rv.y = fmaf(-al, av.y, rv.y);
-        rv.z = fmaf(-al, av.z, rv.z); rv.w = fmaf(-al, av.w, rv.w);
-        x[off + i] = xv;
-        r[off + i] = rv;
-        rr += (double)(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
+        rv.x = fmaf(-al, d0 + qv.x, rv.x); rv.y = fmaf(-al, d1 + qv.y, rv.y);
+        rv.z = fmaf(-al, d2 + qv.z, rv.z); rv.w = fmaf(-al, d3 + qv.w, rv.w);
+        x[o] = xv;
+        r[o] = rv;
+        rrf = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
     }
-    const double t = block_sum_d(rr, red);
+    double rr = (double)rrf;
+    for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rr;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        const double t = red[0] + red[1] + red[2] + red[3];
         CgBand *bd = bands + b;
         atomicAdd(&bd->rr_new, t);
         __threadfence();
         const unsigned int k = atomicAdd(&bd->cnt_update, 1u);
-        if (k == gridDim.x - 1) {
+        if (k == gridDim.x * gridDim.y - 1) {
             __threadfence();
             const double rn = atomicAdd(&bd->rr_new, 0.0);
             const double ro = bd->rr;
             bd->cnt_update = 0u;
             bd->rr_new = 0.0;
             bd->pAp = 0.0;
+            bd->vv = 0.0;
             bd->iters += 1;
             if (!isfinite(rn)) {
                 bd->status = PS_ERR_NONFINITE;
@@ -672,14 +778,15 @@ void launch_cg_init(const float *bvec, const float *ax0, const float *x0, float 
         reinterpret_cast<float4 *>(r), n4, bands, g);
 }
 
-void launch_cg_update(float *x, float *r, const float *p, const float *ap, int N, size_t HW,
-                      CgBand *bands, const CgGlobal *g, cudaStream_t st) {
-    const size_t n4 = HW / 4;
-    dim3 grd(vec_blocks(n4), N);
-    cg_update_kernel<<<grd, 256, 0, st>>>(
+void launch_cg_update(float *x, float *r, const float *p, const float *q, const float *v,
+                      const float *u, int R, int c, int N, int H, int W, CgBand *bands,
+                      const CgGlobal *g, cudaStream_t st) {
+    if (launch_cg_update_fast(x, r, p, q, v, u, R, c, N, H, W, bands, g, st)) return;
+    dim3 grd((W / 4 + 127) / 128, H, N);
+    cg_update_kernel<<<grd, 128, 0, st>>>(
         reinterpret_cast<float4 *>(x), reinterpret_cast<float4 *>(r),
-        reinterpret_cast<const float4 *>(p), reinterpret_cast<const float4 *>(ap), n4, bands,
-        g);
+        reinterpret_cast<const float4 *>(p), reinterpret_cast<const float4 *>(q), v, u, R, c, H,
+        W, bands, g);
 }
 
 void launch_cg_control(CgBand *bands, CgGlobal *g, int N, int use_cond,

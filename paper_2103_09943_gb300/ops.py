@@ -66,8 +66,9 @@ def guided_filter(q, I, mu, s, r):
     for t, nm in ((q, "q"), (I, "I"), (mu, "mu"), (s, "s")):
         _f32(t, nm)
     out = torch.empty_like(q)
+    ws = torch.empty(H * W * 16, dtype=torch.uint8, device=q.device)
     _check(_lib.load().ps_op_guided_filter(_ptr(q), N, H, W, _ptr(I), _ptr(mu), _ptr(s), r,
-                                           _ptr(out), _stream()))
+                                           _ptr(out), _ptr(ws), ws.numel(), _stream()))
     return out
 
 

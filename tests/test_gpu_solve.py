@@ -15,10 +15,11 @@ from tests.gpu_util import rel, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
-# Plain FP32 form: FP32 vectors and operators, FP64 reductions. The CG stops
-# at a recursive relative residual of 1e-7; the bar against the oracle is
-# rel-L2 <= 1e-5 per band.
+# Plain FP32 form: FP32 vectors and operators, FP64 reductions (and the FP64
+# forward FFT of the Z step). The CG stops at a recursive relative residual of
+# 1e-8; the bar against the oracle is rel-L2 <= 1e-5 per band.
 PLAIN_TOL = 1e-5
+CG_TOL = 1e-8
 
 
 def _scene(cfg, **kw):
@@ -56,7 +57,7 @@ def c0_oracle():
 def test_solve_hrms_c0_plain_fp32(cuda, c0_oracle):
     sc, ref = c0_oracle
     cfg = sc["config"]
-    hp = api.default_hrms_params(tol=1e-7, max_iter=5000)
+    hp = api.default_hrms_params(tol=CG_TOL, max_iter=5000)
     Z, Z0, info = api.solve_hrms(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
                                  to_dev(sc["kernel"], cuda), cfg.ratio, hp, want_z0=True)
     Z, Z0 = to_np(Z), to_np(Z0)
@@ -79,12 +80,12 @@ def test_solve_hrms_default_tolerance_meets_1e3(cuda, c0_oracle):
 def test_warm_start_from_solution(cuda, c0_oracle):
     sc, ref = c0_oracle
     cfg = sc["config"]
-    hp = api.default_hrms_params(tol=1e-7)
+    hp = api.default_hrms_params(tol=CG_TOL)
     zi = to_dev(ref["Z0"], cuda)
     Z, Z0, info = api.solve_hrms(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
                                  to_dev(sc["kernel"], cuda), cfg.ratio, hp, z_init=zi,
                                  want_z0=True)
-    assert max(info.iters) < 60, info
+    assert max(info.iters) < 150, info
     assert max(rel(to_np(Z0)[b], ref["Z0"][b]) for b in range(cfg.bands)) < PLAIN_TOL
 
 
@@ -96,7 +97,7 @@ def test_solve_hrms_ragged_and_odd(cuda, N, H, W, c, R, r):
     u = sc["kernel"].astype(np.float64)
     ref = oracle.solve_hrms(sc["lrms"], sc["pan"], u, c, oracle.HrmsParams(r=r, tol=1e-11),
                             threads=3)
-    hp = api.default_hrms_params(tol=1e-7, r=r, max_iter=5000)
+    hp = api.default_hrms_params(tol=CG_TOL, r=r, max_iter=5000)
     Z, Z0, info = api.solve_hrms(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
                                  to_dev(sc["kernel"], cuda), c, hp, want_z0=True)
     Z, Z0 = to_np(Z), to_np(Z0)
@@ -115,7 +116,10 @@ def test_status_not_converged_and_zero_band(cuda):
                                 to_dev(sc["kernel"], cuda), cfg.ratio, hp)
     assert info.status[0] == 5 and info.iters[0] == 3
     assert info.status[1] == 0 and info.iters[1] == 0
-    assert np.all(to_np(Z)[1] == 0.0)
+    # band 1 shares its complex FFT image with band 0: only FP32 round-off of
+    # band 0 can reach it
+    Zn = to_np(Z)
+    assert np.max(np.abs(Zn[1])) < 1e-5 * np.max(np.abs(Zn[0]))
 
 
 def test_status_nonfinite_input(cuda):
@@ -127,3 +131,14 @@ def test_status_nonfinite_input(cuda):
                                 to_dev(sc["kernel"], cuda), cfg.ratio)
     assert info.status[2] == 6
     assert info.status[0] == 0
+
+
+def test_host_loop_matches_device_loop(cuda, c0_oracle):
+    sc, ref = c0_oracle
+    cfg = sc["config"]
+    args = (to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda), to_dev(sc["kernel"], cuda),
+            cfg.ratio)
+    Zg, _, ig = api.solve_hrms(*args, api.default_hrms_params(tol=1e-7))
+    Zh, _, ih = api.solve_hrms(*args, api.default_hrms_params(tol=1e-7, host_loop=1))
+    assert ig.iters == ih.iters
+    assert rel(to_np(Zh), to_np(Zg)) < 1e-6
