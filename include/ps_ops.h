@@ -96,6 +96,33 @@ ps_status ps_op_admm(const double *d_EtE, const double *d_Etf, int R,
  * (the largest any of them needs). */
 size_t ps_op_workspace_size(int N, int H, int W, int ratio, int R);
 
+/* Size of the scratch array the library defines for
+ * ps_op_kernel_normal_eq_noalloc (on every GPU that loads the library). */
+#define PS_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/* ps_op_kernel_normal_eq without a workspace. The paper has no counterpart:
+ * this entry point is for callers that cannot allocate device memory on
+ * their call path, such as plugins whose host application owns all device
+ * memory and passes in only inputs and outputs, or real-time code that cannot
+ * accept cudaMalloc's possible implicit synchronisation or failure. Inputs,
+ * outputs and results are those of ps_op_kernel_normal_eq.
+ * Scratch: a fixed array of PS_NOALLOC_SCRATCH_BYTES defined by the library
+ * on every GPU that loads it, kept until the process exits. A call uses
+ * (h w 4 bytes, rounded up to 256) + c^2 (4R+1)^2 8 bytes of it, with
+ * h w = (H/ratio)(W/ratio); when that exceeds the array the call returns
+ * PS_ERR_UNSUPPORTED before launching anything.
+ * All calls share the one array: calls that overlap on the GPU (on different
+ * streams, or from different host threads) race on it and must be serialised
+ * by the caller. The first call on a device looks up the array's device
+ * address, once per device, with that device current; make that first call
+ * before any stream capture. */
+ps_status ps_op_kernel_normal_eq_noalloc(const float *d_lrms,
+                                         const float *d_pan,
+                                         const float *d_omega, int N, int H,
+                                         int W, int ratio, int R,
+                                         double *d_EtE, double *d_Etf,
+                                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

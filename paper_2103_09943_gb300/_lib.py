@@ -67,6 +67,7 @@ SIGNATURES = {
     "ps_op_admm": (_I, [_P, _P, _I, ctypes.POINTER(KernelParams), _P,
                         ctypes.POINTER(KernelInfo), _P, _Z, _P]),
     "ps_op_workspace_size": (_Z, [_I, _I, _I, _I, _I]),
+    "ps_op_kernel_normal_eq_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
 }
 
 _lib = None

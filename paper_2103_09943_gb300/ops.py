@@ -128,3 +128,18 @@ def admm(ete, etf, R, params=None):
                                   ctypes.byref(p), _ptr(kern), ctypes.byref(ki), _ptr(ws),
                                   ws.numel(), _stream()))
     return kern, ki
+
+
+def kernel_normal_eq_noalloc(lrms, pan, omega_, ratio, R):
+    """(E^T E, E^T f) like kernel_normal_eq, through the entry point that takes
+    no workspace (its scratch is a fixed array owned by the library)."""
+    N = lrms.shape[0]
+    H, W = pan.shape
+    _f32(lrms, "lrms"), _f32(pan, "pan"), _f32(omega_, "omega")
+    nt = (2 * R + 1) ** 2
+    ete = torch.empty((nt, nt), dtype=torch.float64, device=pan.device)
+    etf = torch.empty(nt, dtype=torch.float64, device=pan.device)
+    _check(_lib.load().ps_op_kernel_normal_eq_noalloc(_ptr(lrms), _ptr(pan), _ptr(omega_), N, H,
+                                                      W, ratio, R, _ptr(ete), _ptr(etf),
+                                                      _stream()))
+    return ete, etf
