@@ -70,27 +70,42 @@ __global__ void __launch_bounds__(128) db_site_kernel(const float *__restrict__ 
     const float *S = src + (size_t)b * HW;
     const float *Rr = cg ? rsrc + (size_t)b * HW : nullptr;
     float *P = cg ? pdst + (size_t)b * HW : nullptr;
-    int gx0 = wrap_mod(ox + tx, W);
+    // Fill: every footprint row's loads are issued before any is used, so a
+    // thread keeps 2 * ceil(FX / 32) loads in flight.
+    constexpr int NXW = (D::FX + 31) / 32;
+    const int gx0 = wrap_mod(ox + tx, W);
+#pragma unroll 2
     for (int yy = ty; yy < D::FY; yy += SITE_TYT) {
         const size_t grow = (size_t)wrap_mod(oy + yy, H) * W;
         const bool own_row = cg && yy >= R && yy < R + C * SITE_TY && C * ky0 + (yy - R) < H;
+        float rv[NXW], pv[NXW];
         int gx = gx0;
-#pragma unroll 4
-        for (int xx = tx; xx < D::FX; xx += 32) {
-            const size_t gi = grow + gx;
-            float val;
-            if (cg) {
-                val = use_old ? fmaf(beta, S[gi], Rr[gi]) : Rr[gi];
+#pragma unroll
+        for (int m = 0; m < NXW; ++m) {
+            if (tx + 32 * m < D::FX) {
+                const size_t gi = grow + gx;
+                if (cg) {
+                    rv[m] = Rr[gi];
+                    pv[m] = use_old ? S[gi] : 0.0f;
+                } else {
+                    rv[m] = S[gi];
+                    pv[m] = 0.0f;
+                }
+            }
+            gx += 32;
+            while (gx >= W) gx -= W;
+        }
+#pragma unroll
+        for (int m = 0; m < NXW; ++m) {
+            const int xx = tx + 32 * m;
+            if (xx < D::FX) {
+                const float val = (cg && use_old) ? fmaf(beta, pv[m], rv[m]) : rv[m];
                 if (own_row && xx >= R && xx < R + C * SITE_TX) {
                     const int hx = C * kx0 + (xx - R);
                     if (hx < W) P[(size_t)(C * ky0 + (yy - R)) * W + hx] = val;
                 }
-            } else {
-                val = S[gi];
+                sp[(xx % C) * D::plane + yy * D::FXp + xx / C] = val;
             }
-            sp[(xx % C) * D::plane + yy * D::FXp + xx / C] = val;
-            gx += 32;
-            while (gx >= W) gx -= W;
         }
     }
     __syncthreads();

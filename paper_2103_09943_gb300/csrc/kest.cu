@@ -176,13 +176,15 @@ void launch_combine_f(const float *X, const float *omega, int N, int hw, float *
 // ---------------------------------------------------------------------------
 constexpr int LAG_CHUNK = 17;
 
-// grid: (4R+1 dy, c*c phases, ceil((4R+1)/LAG_CHUNK) dx chunks)
-// lags[((py*c + px) * (4R+1) + (dy+2R)) * (4R+1) + (dx+2R)]
+// grid: (2R+1 dy >= 0, c*c phases, ceil((4R+1)/LAG_CHUNK) dx chunks)
+// lags[((py*c + px) * (4R+1) + (dy+2R)) * (4R+1) + (dx+2R)]; the rows dy < 0
+// follow from C[phi][d] = C[(phi + d) mod c][-d] (E^T E is symmetric) and are
+// read through that identity by ete_assemble_kernel.
 __global__ void __launch_bounds__(256) ete_lag_kernel(const float *__restrict__ Y, int H, int W,
                                                       int c, int R, double *lags) {
     __shared__ double red[8];
     const int nl = 4 * R + 1;
-    const int dy = (int)blockIdx.x - 2 * R;
+    const int dy = (int)blockIdx.x;                      // 0 .. 2R
     const int py = blockIdx.y / c, px = blockIdx.y - (blockIdx.y / c) * c;
     const int dx0 = (int)blockIdx.z * LAG_CHUNK - 2 * R;
     const int ndx = min(LAG_CHUNK, 2 * R - dx0 + 1);
@@ -196,13 +198,18 @@ __global__ void __launch_bounds__(256) ete_lag_kernel(const float *__restrict__ 
         const int yy = c * ky + py, xx = c * kx + px;
         const float a = Y[(size_t)yy * W + xx];
         const float *row = Y + (size_t)wrapk(yy + dy, H) * W;
-        int cx = xx + dx0;
-        if (cx < 0) cx += W;
-        else if (cx >= W) cx -= W;
+        const int cx0 = xx + dx0;
+        if (cx0 >= 0 && cx0 + LAG_CHUNK <= W) {
+            const float *seg = row + cx0;
 #pragma unroll
-        for (int t = 0; t < LAG_CHUNK; ++t) {
-            if (t < ndx) df_acc(a, row[cx], s[t], cm[t]);
-            cx = (cx + 1 == W) ? 0 : cx + 1;
+            for (int t = 0; t < LAG_CHUNK; ++t) df_acc(a, seg[t], s[t], cm[t]);
+        } else {
+            int cx = cx0 < 0 ? cx0 + W : (cx0 >= W ? cx0 - W : cx0);
+#pragma unroll
+            for (int t = 0; t < LAG_CHUNK; ++t) {
+                df_acc(a, row[cx], s[t], cm[t]);
+                cx = (cx + 1 == W) ? 0 : cx + 1;
+            }
         }
         kx += 256;
         while (kx >= w) { kx -= w; ++ky; }
@@ -220,7 +227,7 @@ __global__ void __launch_bounds__(256) ete_lag_kernel(const float *__restrict__ 
 void launch_ete_lags(const float *Y, int H, int W, int c, int R, double *lags,
                      cudaStream_t st) {
     const int nl = 4 * R + 1;
-    dim3 grd(nl, c * c, (nl + LAG_CHUNK - 1) / LAG_CHUNK);
+    dim3 grd(2 * R + 1, c * c, (nl + LAG_CHUNK - 1) / LAG_CHUNK);
     ete_lag_kernel<<<grd, 256, 0, st>>>(Y, H, W, c, R, lags);
 }
 
@@ -232,8 +239,14 @@ __global__ void ete_assemble_kernel(const double *__restrict__ lags, int c, int 
     if (idx >= nt * nt) return;
     const int ia = idx / nt, ib = idx - (idx / nt) * nt;
     const int ai = ia / n - R, aj = ia % n - R, bi = ib / n - R, bj = ib % n - R;
-    const int py = wrapk(-ai, c), px = wrapk(-aj, c);
-    const int dy = ai - bi, dx = aj - bj;
+    int py = wrapk(-ai, c), px = wrapk(-aj, c);
+    int dy = ai - bi, dx = aj - bj;
+    if (dy < 0) {  // C[phi][d] = C[(phi + d) mod c][-d]
+        py = wrapk(py + dy, c);
+        px = wrapk(px + dx, c);
+        dy = -dy;
+        dx = -dx;
+    }
     EtE[idx] = lags[((size_t)(py * c + px) * nl + (dy + 2 * R)) * nl + (dx + 2 * R)];
 }
 
@@ -282,39 +295,37 @@ __global__ void add_diag_kernel(double *A, int n, float mu3) {
     if (i < n) A[(size_t)i * n + i] += (double)mu3;
 }
 
-// Factor the 32 x 32 diagonal tile of panel k0 in place (one CTA; one warp
-// does the factorisation, lane i owning row i).
-__global__ void __launch_bounds__(256) chol_diag_kernel(double *A, int nt, int k0) {
-    __shared__ double D[CB][CB + 1];
-    const int tid = threadIdx.x;
+// Factor the 32 x 32 diagonal tile of panel k0 in place: one warp, lane i
+// holding row i in registers. Right-looking: per column k the pivot is
+// broadcast from lane k, the rows below scale their entry k, and entry (i, j)
+// takes -= l_ik l_jk with l_jk shuffled from lane j.
+__global__ void __launch_bounds__(32) chol_diag_kernel(double *A, int nt, int k0) {
+    const int lane = threadIdx.x;
     const int kb = min(CB, nt - k0);
-    for (int e = tid; e < CB * CB; e += blockDim.x) {
-        const int i = e / CB, j = e - (e / CB) * CB;
-        double v;
-        if (i < kb && j < kb) v = (j <= i) ? A[(size_t)(k0 + i) * nt + k0 + j] : 0.0;
-        else v = (i == j) ? 1.0 : 0.0;
-        D[i][j] = v;
-    }
-    __syncthreads();
-    if (tid < 32) {
-        const int i = tid;
-        for (int k = 0; k < CB; ++k) {
-            if (i == k) {
-                const double d = D[k][k];
-                D[k][k] = sqrt(d > 0.0 ? d : 1e-300);
-            }
-            __syncwarp();
-            if (i > k) D[i][k] /= D[k][k];
-            __syncwarp();
-            if (i > k)
-                for (int j = k + 1; j <= i; ++j) D[i][j] -= D[i][k] * D[j][k];
-            __syncwarp();
+    double x[CB];
+    const double *row = A + (size_t)(k0 + lane) * nt + k0;
+#pragma unroll
+    for (int j = 0; j < CB; ++j)
+        x[j] = (lane < kb && j < kb) ? ((j <= lane) ? row[j] : 0.0) : (lane == j ? 1.0 : 0.0);
+#pragma unroll
+    for (int k = 0; k < CB; ++k) {
+        const double dkk = __shfl_sync(0xffffffffu, x[k], k);
+        const double lkk = sqrt(dkk > 0.0 ? dkk : 1e-300);
+        const double inv = 1.0 / lkk;
+        if (lane == k) x[k] = lkk;
+        else if (lane > k) x[k] *= inv;
+        const double lik = x[k];
+#pragma unroll
+        for (int j = k + 1; j < CB; ++j) {
+            const double ljk = __shfl_sync(0xffffffffu, lik, j);
+            if (lane >= j) x[j] -= lik * ljk;
         }
     }
-    __syncthreads();
-    for (int e = tid; e < kb * kb; e += blockDim.x) {
-        const int i = e / kb, j = e - (e / kb) * kb;
-        if (j <= i) A[(size_t)(k0 + i) * nt + k0 + j] = D[i][j];
+    if (lane < kb) {
+        double *out = A + (size_t)(k0 + lane) * nt + k0;
+#pragma unroll
+        for (int j = 0; j < CB; ++j)
+            if (j < kb && j <= lane) out[j] = x[j];
     }
 }
 
@@ -331,6 +342,9 @@ __global__ void __launch_bounds__(32) chol_panel_kernel(double *A, int nt, int k
         else v = (i == j) ? 1.0 : 0.0;
         D[i][j] = v;
     }
+    __shared__ double rdiag[CB];
+    __syncwarp();
+    rdiag[lane] = 1.0 / D[lane][lane];
     __syncwarp();
     const int i = k1 + blockIdx.x * 32 + lane;
     if (i >= nt) return;
@@ -343,7 +357,7 @@ __global__ void __launch_bounds__(32) chol_panel_kernel(double *A, int nt, int k
         double v = x[k];
 #pragma unroll
         for (int m = 0; m < k; ++m) v -= x[m] * D[k][m];
-        x[k] = v / D[k][k];
+        x[k] = v * rdiag[k];
     }
 #pragma unroll
     for (int k = 0; k < CB; ++k)
@@ -380,7 +394,7 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double *A, int nt, int
 void launch_cholesky(double *A, int n, float mu3, cudaStream_t st) {
     add_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(A, n, mu3);
     for (int k0 = 0; k0 < n; k0 += CB) {
-        chol_diag_kernel<<<1, 256, 0, st>>>(A, n, k0);
+        chol_diag_kernel<<<1, 32, 0, st>>>(A, n, k0);
         const int rem = n - (k0 + CB);
         if (rem > 0) {
             chol_panel_kernel<<<(rem + 31) / 32, 32, 0, st>>>(A, n, k0);

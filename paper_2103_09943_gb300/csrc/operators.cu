@@ -386,11 +386,45 @@ __global__ void __launch_bounds__(128) llp_kernel(LlpArgs a) {
 #pragma unroll
         for (int d = 0; d <= RW; ++d) mub[d] = sb[d] = 0.f;
         float mm2 = 0.f, mm1 = 0.f, m0 = 0.f;
+        // Loads run PF rows ahead of their use (a small register queue), so
+        // that each warp keeps several rows of global loads in flight.
+        constexpr int PF = 3;
+        float qp[PF];
+        float4 qs[PF];
+        // history of the input, to multiply the output row by its p (CG mode)
+        constexpr int PH = ((G + 1 + 2) / 3) * 3;
+        float ph[PH];
+#pragma unroll
+        for (int d = 0; d < PH; ++d) ph[d] = 0.f;
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            qp[k] = in[rowIn + gx];
+            qs[k] = st4[rowA + gx];
+            rowIn += W;
+            if (rowIn == HWi) rowIn = 0;
+            rowA += W;
+            if (rowA == HWi) rowA = 0;
+        }
 
-        // one row of the chain; returns the chain output for the row 2G - G
-        // behind the input row (valid once the buffers are full)
+        // one row of the chain; returns the chain output for the row G behind
+        // the input row (valid once the buffers are full)
         auto advance = [&]() -> float {
-            const float pin = in[rowIn + gx];
+            const float pin = qp[0];
+            const float4 stv = qs[0];
+#pragma unroll
+            for (int k = 0; k < PF - 1; ++k) {
+                qp[k] = qp[k + 1];
+                qs[k] = qs[k + 1];
+            }
+            qp[PF - 1] = in[rowIn + gx];
+            qs[PF - 1] = st4[rowA + gx];
+            rowIn += W;
+            if (rowIn == HWi) rowIn = 0;
+            rowA += W;
+            if (rowA == HWi) rowA = 0;
+#pragma unroll
+            for (int d = 0; d < PH - 1; ++d) ph[d] = ph[d + 1];
+            ph[PH - 1] = pin;
             float al;
             if (MODE == LLP_GF) {
                 al = pin;
@@ -401,7 +435,6 @@ __global__ void __launch_bounds__(128) llp_kernel(LlpArgs a) {
                 al = 4.0f * pm1 - pm2 - p0 - __shfl_up_sync(FULL, pm1, 1) -
                      __shfl_down_sync(FULL, pm1, 1);
             }
-            const float4 stv = st4[rowA + gx];
             const float iv = stv.x;
             const float ia = iv * al;
             float h1 = al, h2 = ia;
@@ -457,10 +490,6 @@ __global__ void __launch_bounds__(128) llp_kernel(LlpArgs a) {
                 sa += ha[d];
                 sbb += hb[d];
             }
-            rowIn += W;
-            if (rowIn == HWi) rowIn = 0;
-            rowA += W;
-            if (rowA == HWi) rowA = 0;
             // alpha and I of the row whose window sums are complete: ab[0], ib[0]
             if (MODE == LLP_GF) return (sa * ib[0] + sbb) * inw;
             const float mv = MATT ? nw * ab[0] - sa * ib[0] - sbb : (sa * ib[0] + sbb) * inw;
@@ -494,7 +523,8 @@ __global__ void __launch_bounds__(128) llp_kernel(LlpArgs a) {
                 } else {
                     a.out[(size_t)b * HW + o] = val;
                 }
-                if (MODE == LLP_CGQ) part = fmaf(in[o], val, part);
+                // the output row is the input row of G steps ago
+                if (MODE == LLP_CGQ) part = fmaf(ph[PH - 1 - G], val, part);
             }
             rowD += W;
             if (rowD == HWi) rowD = 0;
