@@ -203,10 +203,15 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 def cg_iteration_roofline(api, X, Y, kern, cfg, hp, peak_gbs, dev):
-    """Average duration of one CG iteration (db + llp + cg_update + control),
-    from two solves that run a fixed number of iterations (tolerance out of
-    reach), timed with CUDA events on the launching stream."""
-    import ctypes
+    """Average duration of one CG iteration of the Z0 solve, from two solves
+    that run a fixed number of iterations (tolerance out of reach), timed with
+    CUDA events on the launching stream. One iteration is db + llp +
+    cg_update (+ the three preconditioner kernels) + control; its algorithmic
+    bytes per px.band are 40 + 12/N for the CG (fused A-matvec 16, vector
+    update 24, PAN statistics 12 shared by the N bands) plus, preconditioned,
+    32: row FFT in 8 (r in, half a complex value out), column pass 8 + 8
+    ceil(N/2)/N (spectrum in and out, B^ once per band pair), inverse row FFT
+    12 (spectrum in, z out, r in for r^T z)."""
     import torch
     from paper_2103_09943_gb300._lib import HrmsParams
     ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev)
@@ -227,19 +232,44 @@ def cg_iteration_roofline(api, X, Y, kern, cfg, hp, peak_gbs, dev):
             ts.append(e0.elapsed_time(e1))
         return min(ts)
 
-    lo, hi = 20, 220
+    # below the iteration counts the solves need at their tolerance, so that
+    # the forced iterations stay well above the FP32 floor of the residual
+    lo, hi = (10, 60) if hp.precond else (20, 220)
     t_lo, t_hi = timed(lo), timed(hi)
     per_iter_ms = (t_hi - t_lo) / (hi - lo)
-    per_unit = 40.0 + 12.0 / cfg.bands          # algorithmic bytes per px.band per iteration
+    nimg = (cfg.bands + 1) // 2
+    per_unit = 40.0 + 12.0 / cfg.bands
+    kernels = "db_kernel + llp_kernel + cg_update_kernel + cg_control_kernel"
+    if hp.precond:
+        per_unit += 8.0 + (8.0 + 8.0 * nimg / cfg.bands) + 12.0
+        kernels = ("db_kernel + llp_kernel + cg_update_kernel + prec_rows_fwd_kernel + "
+                   "prec_cols_kernel + prec_rows_inv_kernel + cg_control_kernel")
     units = cfg.bands * cfg.H * cfg.W
     achieved = per_unit * units / (per_iter_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
             "frac": achieved / peak_gbs, "traffic": None,
-            "kernel": "CG iteration of Eq. Z_ini_matting (db_kernel + llp_kernel + "
-                      "cg_update_kernel + cg_control_kernel)",
+            "kernel": ("preconditioned " if hp.precond else "") +
+                      f"CG iteration of Eq. Z_ini_matting ({kernels})",
             "bytes_per_unit": per_unit, "units_per_launch": units,
             "ms_per_iteration": per_iter_ms, "peak_note": "of measured (MEASURED_PEAKS.json "
                                                           "hbm_gbs)"}
+
+
+def launches_per_step(cfg, hp, cg_iters) -> int:
+    """Kernels of this library launched by one ps_pansharpen call.
+    Kernel estimate: 4 (omega) + 4 (E^T E, E^T f) + Cholesky (1 + per 32-column
+    panel: diagonal, and below it panel and trailing update) + 3 (solve,
+    inverse, ADMM). HRMS solve: PAN statistics, 7 for the kernel spectrum,
+    right-hand side, reset, init (+3 for z0 = P^{-1} r0), then the loop body of
+    two iterations (4 or 7 kernels each) per two iterations, then 8 for the
+    Z step."""
+    nt = cfg.n * cfg.n
+    panels = (nt + 31) // 32
+    kest = 4 + 4 + (1 + panels + 2 * (panels - 1)) + 3
+    per_iter = 7 if hp.precond else 4
+    body_runs = max(1, math.ceil(max(cg_iters) / 2))
+    solve = 1 + 7 + 1 + 2 + (3 if hp.precond else 0) + 2 * per_iter * body_runs + 8
+    return kest + solve
 
 
 def read_peaks():
@@ -268,7 +298,8 @@ def run_gpu(args):
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
     kp = api.default_kernel_params()
-    hp = api.default_hrms_params(host_loop=1 if args.cg_loop == "host" else 0)
+    hp = api.default_hrms_params(host_loop=1 if args.cg_loop == "host" else 0,
+                                 precond=1 if args.precond == "fft" else 0)
     ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev)
     Z = torch.empty((cfg.bands, cfg.H, cfg.W), dtype=torch.float32, device=dev)
     K = torch.empty((cfg.n, cfg.n), dtype=torch.float32, device=dev)
@@ -325,8 +356,7 @@ def run_gpu(args):
     e2e_ms = reduce_max(float(np.mean(e2e)), world, dev)
 
     # launches of our kernels per step
-    body_runs = max(1, math.ceil(max(binfo.iters) / 2))
-    launches_per_step = 12 + 4 + 8 * body_runs + 14
+    n_launch = launches_per_step(cfg, hp, binfo.iters)
 
     peak, peak_kind = read_peaks()
     roof = cg_iteration_roofline(api, X, Y, K, cfg, hp, peak, dev)
@@ -364,12 +394,14 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world} (independent scenes)",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "cg_tol": hp.tol, "cg_iters": binfo.iters, "cg_loop": args.cg_loop,
+                       "cg_precond": ("FFT alias-group, gamma %g" % hp.precond_gamma)
+                       if hp.precond else "none",
                        "admm_iters": kinfo.iters},
             "wall_s_timed_region": wall,
             "e2e": {"value": throughput(units, world, e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": pipe.h2d_bytes, "d2h_bytes_per_step": pipe.d2h_bytes,
                     "ms_per_step": e2e_ms},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": n_launch * args.steps,
             "roofline": roof,
             "cpu_baseline": cpu,
             "accuracy": acc,
@@ -392,6 +424,9 @@ def parse(argv=None):
     ap.add_argument("--cpu-crop", type=int, default=128)
     ap.add_argument("--ref-crop", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precond", default="fft", choices=["fft", "none"],
+                    help="preconditioner of the Z0 CG (fft: alias-group FFT solve; none: "
+                         "plain CG as in the paper)")
     ap.add_argument("--cg-loop", default="graph", choices=["graph", "host"],
                     help="host: launch the CG iterations from the host (for profilers "
                          "that cannot see inside conditional graphs)")

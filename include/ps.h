@@ -82,6 +82,19 @@ typedef struct ps_hrms_params {
                            reads the stop flag every 8 iterations, for tools
                            that cannot look inside conditional graphs
                            (profilers). Results are identical.              */
+    int precond;        /* preconditioner of the Z0 CG. 0: none, plain CG as in
+                           the paper. 1 (default): P = B^T D^T D B
+                           + lambda gamma L^T L, the Z-step operator of
+                           Eq. Z_solution with M of Eq. Z_ini_matting replaced
+                           by gamma I, applied exactly by FFT and a per-alias-
+                           group solve (FP32). The solution and the stop rule
+                           are unchanged; the iteration count drops.          */
+    float precond_gamma; /* gamma of P (default 4; any value in [1, 8] gives
+                           about the same iteration counts)                   */
+    int warm;           /* start point of the Z0 CG when d_z_init is NULL.
+                           0 (default): zeros, as in the paper. 1: bicubic
+                           x ratio upsampling of the LRMS band (Keys, a = -1/2,
+                           phase 0, circular). The stop rule is the same. */
 } ps_hrms_params;
 
 /* Per-band result of the Z0 conjugate-gradient solve. */

@@ -67,6 +67,24 @@ ps_status ps_op_zstep(const float *d_lrms, const float *d_z0, int N, int H,
                       int r, float lambda, int exact_weight, float *d_z,
                       void *d_ws, size_t ws_bytes, void *stream);
 
+/* Preconditioner of the Z0 CG (an extension: the paper runs plain CG):
+ * z_b = P^{-1} r_b with P = B^T D^T D B + lambda_gamma L^T L, the operator of
+ * Eq. Z_solution at weight lambda_gamma, solved exactly in the Fourier domain
+ * per alias group of ratio^2 frequencies, FP32. N x H x W in and out (device,
+ * caller-owned, not aliased). H, W of the form 2^a 3^b.
+ * Workspace: ps_op_workspace_size. */
+ps_status ps_op_precond(const float *d_r, int N, int H, int W, int ratio,
+                        const float *d_kernel, int R, float lambda_gamma,
+                        float *d_z, void *d_ws, size_t ws_bytes, void *stream);
+
+/* Bicubic x ratio upsampling of N LR bands (h = H / ratio, w = W / ratio),
+ * the warm start of the Z0 solve: Keys' cubic convolution (a = -1/2), HR
+ * pixel ratio k + phi on LR coordinate k + phi / ratio, circular boundary.
+ * d_lrms N x h x w in, d_out N x H x W out (device, caller-owned, 16-byte
+ * aligned). No workspace. */
+ps_status ps_op_bicubic_up(const float *d_lrms, int N, int H, int W, int ratio,
+                           float *d_out, void *stream);
+
 /* Spectral weights of Eq. objective3 in closed form: the normal equations
  * of || B(u1) X omega - D B(u2) Y ||^2 + lambda_omega ||G omega||^2,
  * accumulated in FP64; u1 the (2l+1)^2 unit box on the LR grid, u2 the

@@ -14,17 +14,19 @@ the paper's datasets, which are not available.
 from . import fbmp
 from ._clib import build
 from .fbmp import (HrmsParams, KernelParams, PanStats, admm, apply_z0_system,
-                   apply_zstep_system, blur_decimate, blur_decimate_adj,
+                   apply_zstep_system, bicubic_up, blur_decimate, blur_decimate_adj,
                    box_filter, cg_solve, estimate_kernel, estimate_omega,
                    guided_filter, kernel_error_pct, kernel_normal_eq,
-                   laplacian, matting_apply, pan_stats, pansharpen, psnr,
-                   rel_l2, simplex_project, solve_band, solve_hrms, up_solve)
+                   laplacian, matting_apply, pan_stats, pansharpen, pcg_solve,
+                   precond_apply, psnr, rel_l2, simplex_project, solve_band,
+                   solve_hrms, up_solve)
 
 __all__ = [
     "fbmp", "build", "HrmsParams", "KernelParams", "PanStats", "admm",
-    "apply_z0_system", "apply_zstep_system", "blur_decimate",
+    "apply_z0_system", "apply_zstep_system", "bicubic_up", "blur_decimate",
     "blur_decimate_adj", "box_filter", "cg_solve", "estimate_kernel",
     "estimate_omega", "guided_filter", "kernel_error_pct", "kernel_normal_eq",
-    "laplacian", "matting_apply", "pan_stats", "pansharpen", "psnr", "rel_l2",
+    "laplacian", "matting_apply", "pan_stats", "pansharpen", "pcg_solve",
+    "precond_apply", "psnr", "rel_l2",
     "simplex_project", "solve_band", "solve_hrms", "up_solve",
 ]

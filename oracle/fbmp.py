@@ -169,6 +169,81 @@ def cg_solve(op: int, b, u, c: int, lam: float, st: PanStats | None,
     return x, it, rel.value
 
 
+def keys_cubic(x, a: float = -0.5):
+    """Keys' cubic convolution kernel W(x) (Keys 1981, a = -0.5)."""
+    x = np.abs(np.asarray(x, dtype=np.float64))
+    return np.where(x <= 1.0, (a + 2) * x ** 3 - (a + 3) * x ** 2 + 1,
+                    np.where(x < 2.0, a * x ** 3 - 5 * a * x ** 2 + 8 * a * x - 4 * a, 0.0))
+
+
+def bicubic_up(X, c: int) -> np.ndarray:
+    """Bicubic x c upsampling of the LR bands X (N x h x w, or h x w): the
+    warm start of the Z0 solve. READING: HR pixel c k + phi lies on LR
+    coordinate k + phi / c (phase 0, the samples D keeps), circular
+    boundary; out(y, x) = sum_{i,j} W(t_y - i) W(t_x - j) X(k_y + i, k_x + j)
+    over i, j in {-1, 0, 1, 2}, t = phi / c."""
+    X = f64(X)
+    if X.ndim == 2:
+        return bicubic_up(X[None], c)[0]
+    N, h, w = X.shape
+    out = np.zeros((N, h * c, w * c))
+    for py in range(c):
+        wy = keys_cubic(py / c - np.arange(-1, 3))
+        for px in range(c):
+            wx = keys_cubic(px / c - np.arange(-1, 3))
+            acc = np.zeros((N, h, w))
+            for i in range(4):
+                for j in range(4):
+                    acc += wy[i] * wx[j] * np.roll(X, (-(i - 1), -(j - 1)), axis=(1, 2))
+            out[:, py::c, px::c] = acc
+    return out
+
+
+def precond_apply(r, u, c: int, lam_gamma: float, tol: float = 1e-13) -> np.ndarray:
+    """z = P^{-1} r with P = B^T D^T D B + lam_gamma L^T L, the operator of
+    Eq. Z_solution at weight lam_gamma (L^T L from Eq. reg2 with M of
+    Eq. Z_ini_matting replaced by gamma I). This is the preconditioner of
+    the Z0 CG, an extension: the paper runs plain CG. Defined as the exact
+    solve of P z = r, here the oracle's CG on that system to `tol`."""
+    z, _, _ = cg_solve(1, r, u, c, lam_gamma, None, None, tol, 100000)
+    return z
+
+
+def pcg_solve(b, u, c: int, lam: float, st: PanStats, gamma: float, x0=None,
+              tol: float = 1e-12, max_iter: int = 100000):
+    """Preconditioned CG on the Z0 system of Eq. Z_ini_matting with the fixed
+    SPD preconditioner P of precond_apply (P at weight lam * gamma): the
+    textbook recurrence (Hestenes-Stiefel with z = P^{-1} r; e.g. Saad,
+    Iterative Methods for Sparse Linear Systems, Alg. 9.1). It stops when the
+    recursive residual ||r|| / ||b|| <= tol, the rule of the GPU solver.
+    Returns (x, iterations, recursive relative residual)."""
+    b, u = f64(b), f64(u)
+    x = np.zeros_like(b) if x0 is None else f64(x0).copy()
+    r = b - apply_z0_system(x, u, c, st, lam)
+    bb = float(np.sum(b * b))
+    if bb == 0.0:
+        return x, 0, 0.0
+    rel = float(np.sqrt(np.sum(r * r) / bb))
+    if rel <= tol:
+        return x, 0, rel
+    z = precond_apply(r, u, c, lam * gamma)
+    p = z.copy()
+    rz = float(np.sum(r * z))
+    for k in range(1, max_iter + 1):
+        Ap = apply_z0_system(p, u, c, st, lam)
+        alpha = rz / float(np.sum(p * Ap))
+        x += alpha * p
+        r -= alpha * Ap
+        rel = float(np.sqrt(np.sum(r * r) / bb))
+        if rel <= tol:
+            return x, k, rel
+        z = precond_apply(r, u, c, lam * gamma)
+        rz_new = float(np.sum(r * z))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, max_iter, rel
+
+
 def kernel_normal_eq(Y, f, c: int, R: int):
     """E^T E and E^T f with E = D C(Y) (Eq. z_update, Eq. z_solution)."""
     Y, f = f64(Y), f64(f)

@@ -24,7 +24,8 @@ class HrmsParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_float), ("r", ctypes.c_int),
                 ("eps", ctypes.c_float), ("tol", ctypes.c_float),
                 ("max_iter", ctypes.c_int), ("exact_weight", ctypes.c_int),
-                ("host_loop", ctypes.c_int)]
+                ("host_loop", ctypes.c_int), ("precond", ctypes.c_int),
+                ("precond_gamma", ctypes.c_float), ("warm", ctypes.c_int)]
 
 
 class BandInfo(ctypes.Structure):
@@ -62,6 +63,8 @@ SIGNATURES = {
     "ps_op_guided_filter": (_I, [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P, _Z, _P]),
     "ps_op_zstep": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _I, _F, _I, _P, _P, _Z,
                          _P]),
+    "ps_op_bicubic_up": (_I, [_P, _I, _I, _I, _I, _P, _P]),
+    "ps_op_precond": (_I, [_P, _I, _I, _I, _I, _P, _I, _F, _P, _P, _Z, _P]),
     "ps_op_omega": (_I, [_P, _P, _I, _I, _I, _I, _I, _F, _P, _P, _Z, _P]),
     "ps_op_kernel_normal_eq": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _Z, _P]),
     "ps_op_admm": (_I, [_P, _P, _I, ctypes.POINTER(KernelParams), _P,

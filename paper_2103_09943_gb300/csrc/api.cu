@@ -30,7 +30,10 @@ struct Layout {
     size_t r, pA, pB, ap;               // N HW f32 each; [r,pA] and [pB,ap] double as
                                         // the complex FFT buffers
     size_t v;                           // N hw f32
+    size_t z;                           // N HW f32: preconditioned residual
+    size_t spec;                        // ceil(N/2) HW float2: preconditioner spectrum
     size_t bhat;                        // HW double2 (kernel spectrum)
+    size_t bh32;                        // HW float2 (the same, rounded)
     size_t twW32, twH32, twW64, twH64;  // twiddles
     size_t bands, glob;                 // CG scalars
     size_t bvec, f, G, omega, lags, ete, etf, zf, Q, kern, kinfo;
@@ -58,7 +61,10 @@ bool make_layout(int N, int H, int W, int c, int R, Layout *L) {
     L->pB = take(pair);
     L->ap = L->pB + (size_t)N * HW * 4;
     L->v = take((size_t)N * hw * 4);
+    L->z = take((size_t)N * HW * 4);
+    L->spec = take((size_t)((N + 1) / 2) * HW * 8);
     L->bhat = take(HW * 16);
+    L->bh32 = take(HW * 8);
     L->twW32 = take((size_t)W * 8);
     L->twH32 = take((size_t)H * 8);
     L->twW64 = take((size_t)W * 16);
@@ -127,6 +133,10 @@ ps_status check_hrms(const ps_hrms_params *p) {
         return PS_ERR_INVALID_ARG;
     if (!isfinite(p->lambda) || !isfinite(p->eps) || !isfinite(p->tol))
         return PS_ERR_INVALID_ARG;
+    if (p->precond != 0 && p->precond != 1) return PS_ERR_INVALID_ARG;
+    if (p->precond && (!(p->precond_gamma > 0.f) || !isfinite(p->precond_gamma)))
+        return PS_ERR_INVALID_ARG;
+    if (p->warm != 0 && p->warm != 1) return PS_ERR_INVALID_ARG;
     return PS_OK;
 }
 
@@ -164,6 +174,7 @@ ps_status ensure_device(cudaStream_t *capture) {
         if (operators_set_attrs() != cudaSuccess) return PS_ERR_CUDA;
         if (fft_set_attrs() != cudaSuccess) return PS_ERR_CUDA;
         if (kest_set_attrs() != cudaSuccess) return PS_ERR_CUDA;
+        if (precond_set_attrs() != cudaSuccess) return PS_ERR_CUDA;
         d.attrs_done = 1;
     }
     if (capture) {
@@ -189,6 +200,8 @@ struct CgLoopArgs {
     float *x, *rv, *pA, *pB, *ap, *v;
     CgBand *bands;
     CgGlobal *g;
+    int precond;
+    PrecArgs pa;  // z = P^{-1} r (valid when precond)
     bool operator==(const CgLoopArgs &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
 };
 
@@ -200,7 +213,9 @@ std::vector<CgGraph> g_graphs;
 
 void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, int use_cond,
                        cudaGraphConditionalHandle h, cudaStream_t st) {
-    launch_db(p_old, a.rv, p_new, a.bands, a.g, 1, a.N, a.H, a.W, a.c, a.u, a.R, a.v, st);
+    // p_new = (z or r) + beta p_old, formed inside the blur-decimate load
+    launch_db(p_old, a.precond ? a.pa.z : a.rv, p_new, a.bands, a.g, 1, a.N, a.H, a.W, a.c, a.u,
+              a.R, a.v, st);
     LlpArgs la = {};
     la.in = p_new;
     la.lr = a.v;
@@ -218,6 +233,7 @@ void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, in
     la.cg = 1;
     launch_llp(la, LLP_CGQ, a.r, a.N, st);
     launch_cg_update(a.x, a.rv, p_new, a.ap, a.v, a.u, a.R, a.c, a.N, a.H, a.W, a.bands, a.g, st);
+    if (a.precond) launch_precond(a.pa, st);
     launch_cg_control(a.bands, a.g, a.N, use_cond, h, st);
 }
 
@@ -280,6 +296,51 @@ ps_status get_cg_graph(const CgLoopArgs &a, cudaStream_t capture, cudaGraphExec_
 // ---------------------------------------------------------------------------
 // Z step (Eq. Z_solution) on the FFT path, given Z0 in `z0`.
 // ---------------------------------------------------------------------------
+// Twiddles and the kernel spectrum B^ (FP64, transposed layout [kx][ky], and
+// its FP32 rounding for the preconditioner), once per solve.
+ps_status prepare_spectrum(const Ws &ws, const float *u, int H, int W, int R, cudaStream_t st) {
+    FftPlan pw, ph;
+    if (!fft_make_plan(W, &pw) || !fft_make_plan(H, &ph)) return PS_ERR_UNSUPPORTED;
+    double2 *cbuf64 = ws.at<double2>(ws.L.r);
+    double2 *bhat = ws.at<double2>(ws.L.bhat);
+    float2 *twW32 = ws.at<float2>(ws.L.twW32), *twH32 = ws.at<float2>(ws.L.twH32);
+    double2 *twW64 = ws.at<double2>(ws.L.twW64), *twH64 = ws.at<double2>(ws.L.twH64);
+    launch_fft_twiddles(W, twW32, twW64, st);
+    launch_fft_twiddles(H, twH32, twH64, st);
+    launch_kernel_embed(u, R, H, W, cbuf64, st);
+    launch_fft_rows64(cbuf64, pw, H, twW64, st);
+    launch_transpose64(cbuf64, bhat, H, W, 1, st);
+    launch_fft_rows64(bhat, ph, W, twH64, st);
+    launch_spectrum_to_f32(bhat, ws.at<float2>(ws.L.bh32), (size_t)H * W, st);
+    return last_launch();
+}
+
+PrecArgs make_prec_args(const Ws &ws, const float *r, float *z, int N, int H, int W, int c,
+                        float lam, CgBand *bands, const CgGlobal *g) {
+    PrecArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.r = r;
+    pa.z = z;
+    pa.spec = ws.at<float2>(ws.L.spec);
+    pa.bh = ws.at<float2>(ws.L.bh32);
+    pa.twW = ws.at<float2>(ws.L.twW32);
+    pa.twH = ws.at<float2>(ws.L.twH32);
+    fft_make_plan(W, &pa.pw);
+    fft_make_plan(H, &pa.ph);
+    pa.N = N;
+    pa.H = H;
+    pa.W = W;
+    pa.c = c;
+    pa.lam = lam;
+    pa.bands = bands;
+    pa.g = g;
+    return pa;
+}
+
+// ---------------------------------------------------------------------------
+// Z step (Eq. Z_solution) on the FFT path, given Z0 in `z0` and the spectrum
+// from prepare_spectrum.
+// ---------------------------------------------------------------------------
 ps_status run_zstep(const Ws &ws, const float *lrms, const float *z0, const float *u, int N,
                     int H, int W, int c, int R, int r, float lam_z, float *out,
                     cudaStream_t st) {
@@ -294,13 +355,6 @@ ps_status run_zstep(const Ws &ws, const float *lrms, const float *z0, const floa
     double2 *bhat = ws.at<double2>(ws.L.bhat);
     float2 *twW32 = ws.at<float2>(ws.L.twW32), *twH32 = ws.at<float2>(ws.L.twH32);
     double2 *twW64 = ws.at<double2>(ws.L.twW64), *twH64 = ws.at<double2>(ws.L.twH64);
-    launch_fft_twiddles(W, twW32, twW64, st);
-    launch_fft_twiddles(H, twH32, twH64, st);
-    // kernel spectrum (FP64), transposed layout [kx][ky]
-    launch_kernel_embed(u, R, H, W, cbuf64, st);
-    launch_fft_rows64(cbuf64, pw, H, twW64, st);
-    launch_transpose64(cbuf64, bhat, H, W, 1, st);
-    launch_fft_rows64(bhat, ph, W, twH64, st);
     // right-hand side B^T D^T X + lam' L L-hat, packed two bands per image
     LlpArgs la = {};
     la.in = z0;
@@ -354,6 +408,9 @@ void ps_default_hrms_params(ps_hrms_params *p) {
     p->max_iter = 5000;
     p->exact_weight = 0;
     p->host_loop = 0;
+    p->precond = 1;
+    p->precond_gamma = 4.0f;
+    p->warm = 0;
 }
 
 const char *ps_status_string(int s) {
@@ -446,6 +503,7 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
     if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
     if ((s = check_fft_dims(H, W)) != PS_OK) return s;
     if ((s = check_hrms(p)) != PS_OK) return s;
+    if (p->precond && !precond_supported(H, W, ratio)) return PS_ERR_UNSUPPORTED;
     if (!d_lrms || !d_pan || !d_kernel || !d_hrms) return PS_ERR_INVALID_ARG;
     if ((d_z0 && !aligned16(d_z0)) || (d_z_init && !aligned16(d_z_init)))
         return PS_ERR_INVALID_ARG;
@@ -464,7 +522,14 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
     CgGlobal *g = ws.at<CgGlobal>(ws.L.glob);
 
     launch_pan_stats(d_pan, H, W, p->r, p->eps, nullptr, nullptr, nullptr, st4, st);
+    // the spectrum uses the r buffer as scratch: before b is written there
+    if ((s = prepare_spectrum(ws, d_kernel, H, W, R, st)) != PS_OK) return s;
     launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
+    if (!d_z_init && p->warm == 1) {
+        // bicubic start point, written where the iterate lives
+        launch_bicubic_up(d_lrms, N, H / c, W / c, c, x, st);
+        d_z_init = x;
+    }
     if (d_z_init) {
         launch_db(d_z_init, nullptr, nullptr, nullptr, nullptr, 0, N, H, W, c, d_kernel, R, v,
                   st);
@@ -482,8 +547,16 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
         la.out = ap;
         launch_llp(la, LLP_APPLY, p->r, N, st);
     }
-    launch_cg_reset(bands, g, N, (double)p->tol, p->max_iter, st);
+    launch_cg_reset(bands, g, N, (double)p->tol, p->max_iter, p->precond, st);
     launch_cg_init(rv, d_z_init ? ap : nullptr, d_z_init, x, rv, N, HW, bands, g, st);
+    PrecArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    if (p->precond) {
+        // z0 = P^{-1} r0, rho = r0^T z0 (the first direction is p = z0)
+        pa = make_prec_args(ws, rv, ws.at<float>(ws.L.z), N, H, W, c,
+                            p->lambda * p->precond_gamma, bands, g);
+        launch_precond(pa, st);
+    }
     if ((s = last_launch()) != PS_OK) return s;
 
     CgLoopArgs a;
@@ -493,6 +566,8 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
     a.u = d_kernel; a.st4 = st4;
     a.x = x; a.rv = rv; a.pA = pA; a.pB = pB; a.ap = ap; a.v = v;
     a.bands = bands; a.g = g;
+    a.precond = p->precond;
+    a.pa = pa;
     if (p->host_loop) {
         // same kernels, launched by the host; the stop flag is read every 8
         // iterations, and the loop is bounded by max_iter whatever it says
@@ -659,7 +734,37 @@ ps_status ps_op_zstep(const float *d_lrms, const float *d_z0, int N, int H, int 
     // the Z step reads the statistics, packed, from the workspace
     launch_pack_stats(d_I, d_mu, d_s, HW, ws.at<float4>(ws.L.st4), st);
     const float lam_z = lambda * (exact_weight ? (float)((2 * r + 1) * (2 * r + 1)) : 1.0f);
+    if ((s = prepare_spectrum(ws, d_kernel, H, W, R, st)) != PS_OK) return s;
     return run_zstep(ws, d_lrms, d_z0, d_kernel, N, H, W, ratio, R, r, lam_z, d_z, st);
+}
+
+ps_status ps_op_bicubic_up(const float *d_lrms, int N, int H, int W, int ratio, float *d_out,
+                           void *stream) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, 0)) != PS_OK) return s;
+    if (!d_lrms || !d_out || !aligned16(d_out)) return PS_ERR_INVALID_ARG;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    launch_bicubic_up(d_lrms, N, H / ratio, W / ratio, ratio, d_out, (cudaStream_t)stream);
+    return last_launch();
+}
+
+ps_status ps_op_precond(const float *d_r, int N, int H, int W, int ratio, const float *d_kernel,
+                        int R, float lambda_gamma, float *d_z, void *d_ws, size_t ws_bytes,
+                        void *stream) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
+    if ((s = check_fft_dims(H, W)) != PS_OK) return s;
+    if (!(lambda_gamma > 0.f) || !isfinite(lambda_gamma)) return PS_ERR_INVALID_ARG;
+    if (!d_r || !d_kernel || !d_z) return PS_ERR_INVALID_ARG;
+    if (!precond_supported(H, W, ratio)) return PS_ERR_UNSUPPORTED;
+    Ws ws;
+    if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = prepare_spectrum(ws, d_kernel, H, W, R, st)) != PS_OK) return s;
+    launch_precond(make_prec_args(ws, d_r, d_z, N, H, W, ratio, lambda_gamma, nullptr, nullptr),
+                   st);
+    return last_launch();
 }
 
 ps_status ps_op_omega(const float *d_lrms, const float *d_pan, int N, int H, int W, int ratio,

@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(128) cg_update_site_kernel(
         if (k == gridDim.x * gridDim.y - 1) {
             __threadfence();
             const double rn = atomicAdd(&bd->rr_new, 0.0);
-            const double ro = bd->rr;
+            const double ro = bd->rho;
             bd->cnt_update = 0u;
             bd->rr_new = 0.0;
             bd->pAp = 0.0;
@@ -264,7 +264,10 @@ __global__ void __launch_bounds__(128) cg_update_site_kernel(
                 bd->done = 1;
                 bd->beta = 0.0;
             } else {
-                bd->beta = rn / ro;
+                if (!g->precond) {
+                    bd->beta = rn / ro;
+                    bd->rho = rn;
+                }
                 bd->rr = rn;
                 if (sqrt(rn / bd->bb) <= g->tol) {
                     bd->done = 1;

@@ -29,6 +29,8 @@ struct CgBand {
     double pAp;      // accumulator of p^T (lam L^T M L) p (zeroed after use)
     double vv;       // accumulator of ||D B p||^2 = p^T B^T D^T D B p (zeroed after use)
     double rr_new;   // accumulator of the next r^T r (zeroed after use)
+    double rho;      // numerator of alpha: r^T r (plain CG) or r^T z (preconditioned)
+    double rz_new;   // accumulator of the next r^T z (zeroed after use)
     double alpha;
     double beta;
     int iters;
@@ -37,6 +39,7 @@ struct CgBand {
     unsigned int cnt_apply;   // CTA arrival counters (last-block pattern)
     unsigned int cnt_update;
     unsigned int cnt_init;
+    unsigned int cnt_prec;    // CTAs of the preconditioner's last kernel (per band pair)
 };
 
 struct CgGlobal {
@@ -47,6 +50,7 @@ struct CgGlobal {
     int stop;                 // set once the loop must end
     int iter;                 // loop iterations run
     int max_iter;             // hard cap
+    int precond;              // 1: z = P^{-1} r feeds p and beta (preconditioned CG)
 };
 
 // Block-wide sum of a double over a 1-D block; the result is valid in

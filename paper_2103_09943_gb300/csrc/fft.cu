@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "fft_dev.cuh"
 #include "kernels.cuh"
 
 namespace ps {
@@ -51,110 +52,6 @@ void launch_fft_twiddles(int L, float2 *tw32, double2 *tw64, cudaStream_t st) {
     fft_twiddle_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, tw32, tw64);
 }
 
-template <class T2> struct Cplx;
-template <> struct Cplx<float2> {
-    using R = float;
-    static __device__ __forceinline__ float2 make(float x, float y) { return make_float2(x, y); }
-};
-template <> struct Cplx<double2> {
-    using R = double;
-    static __device__ __forceinline__ double2 make(double x, double y) { return make_double2(x, y); }
-};
-
-template <class T2>
-__device__ __forceinline__ T2 cmulT(T2 a, T2 b) {
-    return Cplx<T2>::make(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// In-place radix-R DFT of v with exponent sign `sg` (-1 forward, +1 inverse).
-template <int R, class T2>
-struct Dft;
-
-template <class T2>
-struct Dft<2, T2> {
-    static __device__ __forceinline__ void run(T2 *v, typename Cplx<T2>::R) {
-        const T2 a = v[0], b = v[1];
-        v[0] = Cplx<T2>::make(a.x + b.x, a.y + b.y);
-        v[1] = Cplx<T2>::make(a.x - b.x, a.y - b.y);
-    }
-};
-
-template <class T2>
-struct Dft<4, T2> {
-    static __device__ __forceinline__ void run(T2 *v, typename Cplx<T2>::R sg) {
-        // exp(sg 2 pi i / 4) = (0, sg)
-        const T2 a0 = Cplx<T2>::make(v[0].x + v[2].x, v[0].y + v[2].y);
-        const T2 a1 = Cplx<T2>::make(v[0].x - v[2].x, v[0].y - v[2].y);
-        const T2 b0 = Cplx<T2>::make(v[1].x + v[3].x, v[1].y + v[3].y);
-        const T2 b1 = Cplx<T2>::make(v[1].x - v[3].x, v[1].y - v[3].y);
-        const T2 jb1 = Cplx<T2>::make(-sg * b1.y, sg * b1.x);
-        v[0] = Cplx<T2>::make(a0.x + b0.x, a0.y + b0.y);
-        v[2] = Cplx<T2>::make(a0.x - b0.x, a0.y - b0.y);
-        v[1] = Cplx<T2>::make(a1.x + jb1.x, a1.y + jb1.y);
-        v[3] = Cplx<T2>::make(a1.x - jb1.x, a1.y - jb1.y);
-    }
-};
-
-template <class T2>
-struct Dft<3, T2> {
-    static __device__ __forceinline__ void run(T2 *v, typename Cplx<T2>::R sg) {
-        // w = exp(sg 2 pi i / 3) = (-1/2, sg sqrt(3)/2); w b + w^2 c = -t/2 + i s3 (b - c)
-        using Rl = typename Cplx<T2>::R;
-        const Rl s3 = (Rl)0.86602540378443864676 * sg;
-        const T2 a = v[0], b = v[1], c = v[2];
-        const T2 t = Cplx<T2>::make(b.x + c.x, b.y + c.y);
-        const T2 d = Cplx<T2>::make(b.x - c.x, b.y - c.y);
-        const T2 m = Cplx<T2>::make(a.x - (Rl)0.5 * t.x, a.y - (Rl)0.5 * t.y);
-        v[0] = Cplx<T2>::make(a.x + t.x, a.y + t.y);
-        v[1] = Cplx<T2>::make(m.x - s3 * d.y, m.y + s3 * d.x);
-        v[2] = Cplx<T2>::make(m.x + s3 * d.y, m.y - s3 * d.x);
-    }
-};
-
-// One Stockham pass of radix R, in place: every thread first reads the inputs
-// of its butterflies into registers, then (after a barrier) writes the
-// outputs, so a single buffer of L values suffices.
-template <int R, class T2>
-__device__ __forceinline__ void stockham_pass(T2 *a, int L, int Ns, const T2 *__restrict__ tw,
-                                              bool inverse) {
-    constexpr int MAXB = (8 + R - 1) / R;
-    using Rl = typename Cplx<T2>::R;
-    const Rl sg = inverse ? (Rl)1 : (Rl)-1;
-    const int m = L / R;
-    const int stride = L / (Ns * R);
-    T2 v[MAXB][R];
-#pragma unroll
-    for (int bi = 0; bi < MAXB; ++bi) {
-        const int j = threadIdx.x + bi * blockDim.x;
-        if (j < m) {
-            const int k = j % Ns;
-#pragma unroll
-            for (int t = 0; t < R; ++t) {
-                T2 x = a[j + t * m];
-                if (t > 0 && k > 0) {
-                    T2 w = tw[t * k * stride];
-                    if (inverse) w.y = -w.y;
-                    x = cmulT(x, w);
-                }
-                v[bi][t] = x;
-            }
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int bi = 0; bi < MAXB; ++bi) {
-        const int j = threadIdx.x + bi * blockDim.x;
-        if (j < m) {
-            const int k = j % Ns;
-            Dft<R, T2>::run(v[bi], sg);
-            const int idxD = (j / Ns) * Ns * R + k;
-#pragma unroll
-            for (int t = 0; t < R; ++t) a[idxD + t * Ns] = v[bi][t];
-        }
-    }
-    __syncthreads();
-}
-
 // One CTA per row of length L (<= 8192), blockDim = L/8 rounded up to a
 // multiple of 32. If `unpack` is given (FP32 inverse only), the row is
 // written as two real bands (real part -> band 2k, imaginary part ->
@@ -170,17 +67,7 @@ __global__ void __launch_bounds__(1024) fft_rows_kernel(T2 *data, FftPlan plan,
     T2 *src = data + row * (size_t)L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) a[i] = src[i];
     __syncthreads();
-    int Ns = 1;
-    for (int p = 0; p < plan.npass; ++p) {
-        const int R = plan.radix[p];
-        if (R == 4)
-            stockham_pass<4, T2>(a, L, Ns, tw, inverse != 0);
-        else if (R == 2)
-            stockham_pass<2, T2>(a, L, Ns, tw, inverse != 0);
-        else
-            stockham_pass<3, T2>(a, L, Ns, tw, inverse != 0);
-        Ns *= R;
-    }
+    fft_row<8, T2>(a, plan, tw, inverse != 0, threadIdx.x, blockDim.x);
     if (unpack) {
         // rows are ordered (image, y); image k holds bands 2k, 2k+1
         const size_t rows_per_img = HW / (size_t)L;

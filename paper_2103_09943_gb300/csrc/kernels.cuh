@@ -34,7 +34,7 @@ void launch_db(const float *src, const float *rsrc, float *pdst, const CgBand *b
 void launch_adj(const float *v, int N, int H, int W, int c, const float *u, int R, float *z,
                 cudaStream_t st);
 void launch_llp(const LlpArgs &a, int mode, int r, int N, cudaStream_t st);
-void launch_cg_reset(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter,
+void launch_cg_reset(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter, int precond,
                      cudaStream_t st);
 void launch_cg_init(const float *bvec, const float *ax0, const float *x0, float *x, float *r,
                     int N, size_t HW, CgBand *bands, CgGlobal *g, cudaStream_t st);
@@ -77,6 +77,28 @@ void launch_kernel_embed(const float *u, int R, int H, int W, double2 *out, cuda
 void launch_alias_solve(const double2 *spec, const double2 *bspec, float2 *sol, int nimg, int H,
                         int W, int c, float lam, cudaStream_t st);
 cudaError_t fft_set_attrs();
+
+// precond.cu: z = P^{-1} r, P = B^T D^T D B + lam L^T L (lam = lambda gamma)
+struct PrecArgs {
+    const float *r;       // N x H x W
+    float *z;             // N x H x W
+    float2 *spec;         // ceil(N/2) x W x H complex scratch
+    const float2 *bh;     // kernel spectrum B^, layout [kx][ky]
+    const float2 *twW, *twH;
+    FftPlan pw, ph;
+    int N, H, W, c;
+    float lam;
+    CgBand *bands;        // NULL: plain operator (no r^T z, no skipping)
+    const CgGlobal *g;
+};
+bool precond_supported(int H, int W, int c);
+void launch_precond(const PrecArgs &a, cudaStream_t st);
+void launch_spectrum_to_f32(const double2 *in, float2 *out, size_t n, cudaStream_t st);
+cudaError_t precond_set_attrs();
+
+// warm.cu
+void launch_bicubic_up(const float *X, int N, int h, int w, int c, float *out,
+                       cudaStream_t st);
 
 // kest.cu
 void launch_box_lr(const float *X, int N, int h, int w, int l, float *out, cudaStream_t st);

@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(128) llp_kernel(LlpArgs a) {
                 __threadfence();
                 // p^T A p = ||D B p||^2 + p^T (lam L^T M L) p
                 const double pAp = atomicAdd(&bd->pAp, 0.0) + bd->vv;
-                const double rr = bd->rr;
+                const double rr = bd->rho;
                 bd->cnt_apply = 0u;
                 if (!isfinite(pAp)) {
                     bd->status = PS_ERR_NONFINITE;
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(128) llp_kernel(LlpArgs a) {
                     bd->done = 1;
                     bd->alpha = 0.0;
                 } else {
-                    bd->alpha = rr / pAp;
+                    bd->alpha = rr / pAp;  // rho / p^T A p
                 }
             }
         }
@@ -604,7 +604,8 @@ void launch_llp(const LlpArgs &a, int mode, int r, int N, cudaStream_t st) {
 // a one-warp control kernel that always runs, so the device loop ends after
 // at most max_iter iterations whatever the band states.
 // ----------------------------------------------------------------------------
-__global__ void cg_reset_kernel(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter) {
+__global__ void cg_reset_kernel(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter,
+                                int precond) {
     const int t = threadIdx.x;
     for (int b = t; b < N; b += blockDim.x) {
         CgBand z = {};
@@ -618,6 +619,7 @@ __global__ void cg_reset_kernel(CgBand *bands, CgGlobal *g, int N, double tol, i
         g->iter = 0;
         g->max_iter = max_iter;
         g->tol = tol;
+        g->precond = precond;
     }
 }
 
@@ -659,6 +661,7 @@ __global__ void __launch_bounds__(256) cg_init_kernel(const float4 *__restrict__
             const double r2 = atomicAdd(&bd->rr_new, 0.0);
             const double b2 = atomicAdd(&bd->pAp, 0.0);
             bd->rr = r2;
+            bd->rho = r2;  // replaced by r^T z when a preconditioner follows
             bd->bb = b2;
             bd->rr_new = 0.0;
             bd->pAp = 0.0;
@@ -733,7 +736,7 @@ __global__ void __launch_bounds__(128) cg_update_kernel(float4 *__restrict__ x,
         if (k == gridDim.x * gridDim.y - 1) {
             __threadfence();
             const double rn = atomicAdd(&bd->rr_new, 0.0);
-            const double ro = bd->rr;
+            const double ro = bd->rho;
             bd->cnt_update = 0u;
             bd->rr_new = 0.0;
             bd->pAp = 0.0;
@@ -744,7 +747,10 @@ __global__ void __launch_bounds__(128) cg_update_kernel(float4 *__restrict__ x,
                 bd->done = 1;
                 bd->beta = 0.0;
             } else {
-                bd->beta = rn / ro;
+                if (!g->precond) {
+                    bd->beta = rn / ro;
+                    bd->rho = rn;
+                }
                 bd->rr = rn;
                 if (sqrt(rn / bd->bb) <= g->tol) {
                     bd->done = 1;
@@ -786,9 +792,9 @@ __global__ void cg_control_kernel(CgBand *bands, CgGlobal *g, int N, int use_con
     }
 }
 
-void launch_cg_reset(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter,
+void launch_cg_reset(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter, int precond,
                      cudaStream_t st) {
-    cg_reset_kernel<<<1, 64, 0, st>>>(bands, g, N, tol, max_iter);
+    cg_reset_kernel<<<1, 64, 0, st>>>(bands, g, N, tol, max_iter, precond);
 }
 
 static int vec_blocks(size_t n4) {

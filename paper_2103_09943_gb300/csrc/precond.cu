@@ -1,0 +1,513 @@
+// Preconditioner of the Z0 solve (Eq. Z_ini_matting), sm_103a.
+//
+// The Z0 system A = B^T D^T D B + lam L^T M L differs from the Z-step
+// operator of Eq. Z_solution only in the matting matrix M. With M replaced by
+// gamma I the operator
+//     P = B^T D^T D B + lam gamma L^T L
+// is SPD and, in Fourier space, block diagonal over alias groups of c^2 HR
+// frequencies (the same structure the Z step is solved with), so z = P^{-1} r
+// is applied exactly: one forward 2-D FFT, one small solve per group, one
+// inverse 2-D FFT. This is an extension beyond the paper (which runs plain
+// CG): it changes the iterates, not the solution the CG converges to.
+//
+// Three kernels per application, all FP32 (a preconditioner needs no more:
+// its rounding only perturbs the search directions):
+//   prec_rows_fwd   TR rows of two bands packed as one complex image (band
+//                   2k real, 2k+1 imaginary; P has a real kernel so the two do
+//                   not mix), row FFTs in shared memory, stored transposed
+//                   ([kx][ky]) in runs of TR values
+//   prec_cols<C>    one CTA per LR column index kx0 and image: the C columns
+//                   kx0 + q w are exactly the HR columns of the alias groups
+//                   (ky0 + p h, kx0 + q w); column FFTs, the group solves and
+//                   the inverse column FFTs all stay in shared memory
+//   prec_rows_inv   transposed load, inverse row FFTs, unpack to z, and the
+//                   per-band r^T z whose last CTA sets beta and the next alpha
+//                   numerator (preconditioned CG)
+// Sizes whose C columns do not fit one CTA take a fallback: column FFTs and
+// the group solve as separate passes over global memory.
+#include <math.h>
+
+#include "common.cuh"
+#include "fft_dev.cuh"
+#include "kernels.cuh"
+
+namespace ps {
+
+namespace {
+
+constexpr int kPrecPad = 4;  // float2 padding of shared rows (spreads banks)
+constexpr int kPrecMaxSmem = 192 * 1024;
+constexpr int kPrecColThreads = 512;  // CTA size bound of the fused column pass
+
+__device__ __forceinline__ bool image_idle(const PrecArgs &a, int k) {
+    if (!a.bands) return false;
+    if (a.g->stop) return true;
+    const bool d0 = a.bands[2 * k].done != 0;
+    const bool d1 = (2 * k + 1 >= a.N) || a.bands[2 * k + 1].done != 0;
+    return d0 && d1;
+}
+
+// Solve ((1/C^2) v v^H + diag(t)) x = s over the alias group (ky0, kx0),
+// in place; v_j = conj(B^_j), t_j = lam S^_j^2 with the Laplacian symbol
+// S^ = 4 sin^2(pi ky / H) + 4 sin^2(pi kx / W). The algebra is that of the
+// Z-step solve: m the member with the smallest t, both sides multiplied by
+// t_m (the DC group, t_m = 0, needs no special case), x_m by substitution
+// when c^2 t_m < |v_m|^2. `scale` folds in 1/(H W) of the inverse FFT.
+template <int C, class At>
+__device__ __forceinline__ void group_solve_f(At at, const float2 *__restrict__ bh, int ky0,
+                                              int kx0, int H, int W, float lam, float scale) {
+    const int h = H / C, w = W / C;
+    float sy2[C], sx2[C];
+#pragma unroll
+    for (int p = 0; p < C; ++p) {
+        const float s = sinpif((float)(ky0 + p * h) / (float)H);
+        sy2[p] = s * s;
+    }
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+        const float s = sinpif((float)(kx0 + q * w) / (float)W);
+        sx2[q] = s * s;
+    }
+    auto tval = [&](int p, int q) {
+        const float S = 4.0f * (sy2[p] + sx2[q]);
+        return lam * S * S;
+    };
+    auto vval = [&](int p, int q) {
+        const float2 b = bh[(size_t)(kx0 + q * w) * H + ky0 + p * h];
+        return make_float2(b.x, -b.y);
+    };
+    float tmin = INFINITY;
+    int jm = 0;
+#pragma unroll(C <= 4 ? C : 1)
+    for (int p = 0; p < C; ++p)
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            const float tj = tval(p, q);
+            if (tj < tmin) {
+                tmin = tj;
+                jm = p * C + q;
+            }
+        }
+    constexpr float icc = 1.0f / (float)(C * C);
+    float2 num = make_float2(0.f, 0.f), vm = make_float2(0.f, 0.f), rm = make_float2(0.f, 0.f);
+    float dsum = 0.f;
+#pragma unroll(C <= 4 ? C : 1)
+    for (int p = 0; p < C; ++p)
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            const float2 vj = vval(p, q), rj = at(p, q);
+            if (p * C + q == jm) {
+                vm = vj;
+                rm = rj;
+            } else {
+                const float it = __frcp_rn(tval(p, q));
+                num.x = fmaf(vj.x * rj.x + vj.y * rj.y, it, num.x);
+                num.y = fmaf(vj.x * rj.y - vj.y * rj.x, it, num.y);
+                dsum = fmaf(vj.x * vj.x + vj.y * vj.y, it, dsum);
+            }
+        }
+    const float vm2 = vm.x * vm.x + vm.y * vm.y;
+    const float iden = 1.0f / (tmin + (vm2 + tmin * dsum) * icc);
+    const float2 s = make_float2((vm.x * rm.x + vm.y * rm.y + tmin * num.x) * iden,
+                                 (vm.x * rm.y - vm.y * rm.x + tmin * num.y) * iden);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll(C <= 4 ? C : 1)
+    for (int p = 0; p < C; ++p)
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            if (p * C + q == jm) continue;
+            const float2 vj = vval(p, q), rj = at(p, q);
+            const float it = __frcp_rn(tval(p, q));
+            const float2 vs = make_float2(vj.x * s.x - vj.y * s.y, vj.x * s.y + vj.y * s.x);
+            const float2 x = make_float2((rj.x - vs.x * icc) * it, (rj.y - vs.y * icc) * it);
+            acc.x += vj.x * x.x + vj.y * x.y;
+            acc.y += vj.x * x.y - vj.y * x.x;
+            at(p, q) = make_float2(x.x * scale, x.y * scale);
+        }
+    float2 xm;
+    if ((float)(C * C) * tmin < vm2) {
+        const float2 d = make_float2(s.x - acc.x, s.y - acc.y);
+        const float iv = 1.0f / vm2;
+        xm = make_float2((d.x * vm.x - d.y * vm.y) * iv, (d.y * vm.x + d.x * vm.y) * iv);
+    } else {
+        const float2 vs = make_float2(vm.x * s.x - vm.y * s.y, vm.x * s.y + vm.y * s.x);
+        xm = make_float2((rm.x - vs.x * icc) / tmin, (rm.y - vs.y * icc) / tmin);
+    }
+    const int pm = jm / C, qm = jm - (jm / C) * C;
+    at(pm, qm) = make_float2(xm.x * scale, xm.y * scale);
+}
+
+// Row transform of one row in shared memory: the register FFT on padded rows
+// for powers of two (P2), the shared-memory Stockham passes otherwise.
+template <bool P2>
+__device__ __forceinline__ int ix(int i) {
+    return P2 ? prow(i) : i;
+}
+
+template <bool P2>
+__device__ __forceinline__ void row_fft(float2 *row, int L, const FftPlan &plan,
+                                        const float2 *__restrict__ tw, bool inverse, int t,
+                                        int nt) {
+    if (P2)
+        fft_p2_row(row, L, tw, inverse, t, nt);
+    else
+        fft_row<8, float2>(row, plan, tw, inverse, t, nt);
+}
+
+// ---------------------------------------------------------------------------
+// Row pass, forward: rows y0 .. y0 + TR - 1 of image k (bands 2k, 2k+1).
+// g.ld = padded row stride in float2, congruent to TR mod 16, so that the
+// transposed store (row index fastest) reads shared memory without conflicts.
+// ---------------------------------------------------------------------------
+struct RowGeom {
+    int TR;   // rows per CTA
+    int tpr;  // threads per row
+    int ld;   // shared-memory row stride (float2)
+};
+
+template <bool P2>
+__global__ void __launch_bounds__(1024) prec_rows_fwd_kernel(PrecArgs a, RowGeom g) {
+    extern __shared__ __align__(16) float2 psm[];
+    const int k = blockIdx.y;
+    if (image_idle(a, k)) return;
+    const int H = a.H, W = a.W, TR = g.TR, ld = g.ld;
+    const size_t HW = (size_t)H * W;
+    const int y0 = blockIdx.x * TR;
+    // a finished band (converged, or stopped on a non-finite value) enters as
+    // zeros, so that it cannot disturb the band it shares the image with
+    const float *r0 = a.r + (size_t)(2 * k) * HW + (size_t)y0 * W;
+    const float *r1 = (2 * k + 1 < a.N) ? r0 + HW : nullptr;
+    if (a.bands && a.bands[2 * k].done) r0 = nullptr;
+    if (a.bands && r1 && a.bands[2 * k + 1].done) r1 = nullptr;
+    for (int i = threadIdx.x; i < TR * W; i += blockDim.x) {
+        const int rr = i / W, x = i - rr * W;
+        psm[rr * ld + ix<P2>(x)] =
+            make_float2(r0 ? __ldg(r0 + i) : 0.0f, r1 ? __ldg(r1 + i) : 0.0f);
+    }
+    __syncthreads();
+    const int row = threadIdx.x / g.tpr, t = threadIdx.x - row * g.tpr;
+    row_fft<P2>(psm + row * ld, W, a.pw, a.twW, false, t, g.tpr);
+    float2 *S = a.spec + (size_t)k * HW;
+    for (int i = threadIdx.x; i < TR * W; i += blockDim.x) {
+        const int rr = i % TR, kx = i / TR;
+        S[(size_t)kx * H + y0 + rr] = psm[rr * ld + ix<P2>(kx)];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass with the group solves: columns kx0 + q w, q < C, of image k.
+// ---------------------------------------------------------------------------
+template <int C, int PER, bool P2>
+__global__ void __launch_bounds__(kPrecColThreads) prec_cols_kernel(PrecArgs a, int tpr, int ld,
+                                                                     float scale) {
+    extern __shared__ __align__(16) float2 psm[];
+    const int k = blockIdx.y, kx0 = blockIdx.x;
+    if (image_idle(a, k)) return;
+    const int H = a.H, W = a.W, h = H / C, w = W / C;
+    float2 *S = a.spec + (size_t)k * H * W;
+    for (int i = threadIdx.x; i < C * H; i += blockDim.x) {
+        const int q = i / H, y = i - q * H;
+        psm[q * ld + ix<P2>(y)] = S[(size_t)(kx0 + q * w) * H + y];
+    }
+    __syncthreads();
+    const int row = threadIdx.x / tpr, t = threadIdx.x - row * tpr;
+    if (P2)
+        fft_p2_row(psm + row * ld, H, a.twH, false, t, tpr);
+    else
+        fft_row<PER, float2>(psm + row * ld, a.ph, a.twH, false, t, tpr);
+    for (int ky0 = threadIdx.x; ky0 < h; ky0 += blockDim.x) {
+        auto at = [&](int p, int q) -> float2 & { return psm[q * ld + ix<P2>(ky0 + p * h)]; };
+        group_solve_f<C>(at, a.bh, ky0, kx0, H, W, a.lam, scale);
+    }
+    __syncthreads();
+    if (P2)
+        fft_p2_row(psm + row * ld, H, a.twH, true, t, tpr);
+    else
+        fft_row<PER, float2>(psm + row * ld, a.ph, a.twH, true, t, tpr);
+    for (int i = threadIdx.x; i < C * H; i += blockDim.x) {
+        const int q = i / H, y = i - q * H;
+        S[(size_t)(kx0 + q * w) * H + y] = psm[q * ld + ix<P2>(y)];
+    }
+}
+
+// Fallback column passes: FFTs of whole columns (one per CTA) and the group
+// solves over global memory.
+template <bool P2>
+__global__ void __launch_bounds__(1024) prec_col_fft_kernel(PrecArgs a, int inverse) {
+    extern __shared__ __align__(16) float2 psm[];
+    const int k = blockIdx.y;
+    if (image_idle(a, k)) return;
+    const int H = a.H;
+    float2 *col = a.spec + ((size_t)k * a.W + blockIdx.x) * H;
+    for (int i = threadIdx.x; i < H; i += blockDim.x) psm[ix<P2>(i)] = col[i];
+    __syncthreads();
+    row_fft<P2>(psm, H, a.ph, a.twH, inverse != 0, threadIdx.x, blockDim.x);
+    for (int i = threadIdx.x; i < H; i += blockDim.x) col[i] = psm[ix<P2>(i)];
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) prec_group_kernel(PrecArgs a, float scale) {
+    const int k = blockIdx.y;
+    if (image_idle(a, k)) return;
+    const int H = a.H, W = a.W, h = H / C, w = W / C;
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= h * w) return;
+    const int kx0 = gi / h, ky0 = gi - (gi / h) * h;
+    float2 *S = a.spec + (size_t)k * H * W;
+    auto at = [&](int p, int q) -> float2 & { return S[(size_t)(kx0 + q * w) * H + ky0 + p * h]; };
+    group_solve_f<C>(at, a.bh, ky0, kx0, H, W, a.lam, scale);
+}
+
+// ---------------------------------------------------------------------------
+// Row pass, inverse: transposed load, inverse row FFTs, z and r^T z.
+// ---------------------------------------------------------------------------
+template <bool P2>
+__global__ void __launch_bounds__(1024) prec_rows_inv_kernel(PrecArgs a, RowGeom g) {
+    extern __shared__ __align__(16) float2 psm[];
+    __shared__ double red[2][32];
+    const int k = blockIdx.y;
+    if (image_idle(a, k)) return;
+    const int H = a.H, W = a.W, TR = g.TR, ld = g.ld;
+    const size_t HW = (size_t)H * W;
+    const int y0 = blockIdx.x * TR;
+    const float2 *S = a.spec + (size_t)k * HW;
+    for (int i = threadIdx.x; i < TR * W; i += blockDim.x) {
+        const int rr = i % TR, kx = i / TR;
+        psm[rr * ld + ix<P2>(kx)] = S[(size_t)kx * H + y0 + rr];
+    }
+    __syncthreads();
+    const int row = threadIdx.x / g.tpr, t = threadIdx.x - row * g.tpr;
+    row_fft<P2>(psm + row * ld, W, a.pw, a.twW, true, t, g.tpr);
+    const size_t o0 = (size_t)(2 * k) * HW + (size_t)y0 * W;
+    const bool two = 2 * k + 1 < a.N;
+    float d0 = 0.f, d1 = 0.f;
+    for (int i = threadIdx.x; i < TR * W; i += blockDim.x) {
+        const int rr = i / W, x = i - rr * W;
+        const float2 zv = psm[rr * ld + ix<P2>(x)];
+        a.z[o0 + i] = zv.x;
+        if (two) a.z[o0 + HW + i] = zv.y;
+        if (a.bands) {
+            d0 = fmaf(__ldg(a.r + o0 + i), zv.x, d0);
+            if (two) d1 = fmaf(__ldg(a.r + o0 + HW + i), zv.y, d1);
+        }
+    }
+    if (!a.bands) return;
+    double s0 = d0, s1 = d1;
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = s0;
+        red[1][warp] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double t0 = 0.0, t1 = 0.0;
+    for (int j = 0; j < nw; ++j) {
+        t0 += red[0][j];
+        t1 += red[1][j];
+    }
+    CgBand *b0 = a.bands + 2 * k;
+    CgBand *b1 = two ? b0 + 1 : nullptr;
+    atomicAdd(&b0->rz_new, t0);
+    if (b1) atomicAdd(&b1->rz_new, t1);
+    __threadfence();
+    const unsigned int cnt = atomicAdd(&b0->cnt_prec, 1u);
+    if (cnt != gridDim.x - 1) return;
+    __threadfence();
+    b0->cnt_prec = 0u;
+    for (int j = 0; j < (two ? 2 : 1); ++j) {
+        CgBand *bd = b0 + j;
+        const double rz = atomicAdd(&bd->rz_new, 0.0);
+        bd->rz_new = 0.0;
+        if (bd->done) continue;
+        if (!isfinite(rz)) {
+            bd->status = PS_ERR_NONFINITE;
+            bd->done = 1;
+        } else if (!(rz > 0.0)) {
+            bd->status = PS_ERR_BREAKDOWN;
+            bd->done = 1;
+        } else {
+            // first application (before any iteration): p = z
+            bd->beta = bd->iters > 0 ? rz / bd->rho : 0.0;
+            bd->rho = rz;
+        }
+    }
+}
+
+int fft_threads_row(int L, int per = 8) {
+    int t = (L + per - 1) / per;
+    t = (t + 31) & ~31;
+    return t < 32 ? 32 : t;
+}
+
+bool is_pow2(int L) { return L >= 16 && (L & (L - 1)) == 0; }
+
+int round16(int x) { return (x + 15) & ~15; }
+
+// Launch geometry of the three passes for one size.
+struct PrecPlan {
+    bool p2;            // H and W powers of two: register FFT on padded rows
+    RowGeom rg;         // row passes
+    size_t row_smem;
+    int col_per;        // fused column pass: values per thread (generic FFT)
+    int col_tpr, col_ld;
+    size_t col_smem;    // 0: fallback column passes
+    int fb_tpr;         // fallback column FFT
+    size_t fb_smem;
+};
+
+bool make_prec_plan(int H, int W, int C, PrecPlan *pl) {
+    if (C != 2 && C != 3 && C != 4 && C != 6 && C != 8) return false;
+    pl->p2 = is_pow2(H) && is_pow2(W);
+    // rows: TR rows per CTA, a power of two dividing H, within 1024 threads
+    // and the shared-memory budget; row stride congruent to TR mod 16
+    const int tpr = pl->p2 ? W / 16 : fft_threads_row(W);
+    if (tpr > 1024) return false;
+    const int row_len = pl->p2 ? prow_len(W) : W;
+    int TR = 8;
+    auto row_bytes = [&](int tr) { return (size_t)tr * (round16(row_len) + tr) * sizeof(float2); };
+    while (TR > 1 && (H % TR || TR * tpr > 1024 || row_bytes(TR) > (size_t)kPrecMaxSmem)) TR >>= 1;
+    if (row_bytes(TR) > (size_t)kPrecMaxSmem) return false;
+    pl->rg.TR = TR;
+    pl->rg.tpr = tpr;
+    pl->rg.ld = round16(row_len) + TR;
+    pl->row_smem = row_bytes(TR);
+    // columns: the C columns of one alias-group set in one CTA when they fit
+    pl->col_smem = 0;
+    pl->col_per = 0;
+    if (pl->p2) {
+        const int ct = H / 16;
+        const size_t bytes = (size_t)C * prow_len(H) * sizeof(float2);
+        if (C * ct <= kPrecColThreads && bytes <= (size_t)kPrecMaxSmem) {
+            pl->col_tpr = ct;
+            pl->col_ld = prow_len(H);
+            pl->col_smem = bytes;
+        }
+        pl->fb_tpr = H / 16;
+        pl->fb_smem = (size_t)prow_len(H) * sizeof(float2);
+    } else {
+        const size_t bytes = (size_t)C * (H + kPrecPad) * sizeof(float2);
+        for (int per = 8; per <= 32 && bytes <= (size_t)kPrecMaxSmem; per *= 2)
+            if (C * fft_threads_row(H, per) <= kPrecColThreads) {
+                pl->col_per = per;
+                pl->col_tpr = fft_threads_row(H, per);
+                pl->col_ld = H + kPrecPad;
+                pl->col_smem = bytes;
+                break;
+            }
+        pl->fb_tpr = fft_threads_row(H);
+        pl->fb_smem = (size_t)H * sizeof(float2);
+    }
+    return pl->fb_tpr <= 1024 && pl->fb_smem <= (size_t)kPrecMaxSmem;
+}
+
+template <int C>
+void launch_cols(const PrecArgs &a, const PrecPlan &pl, float scale, cudaStream_t st) {
+    const int w = a.W / C, nimg = (a.N + 1) / 2;
+    if (pl.col_smem) {
+        const dim3 grd(w, nimg), blk(C * pl.col_tpr);
+        if (pl.p2)
+            prec_cols_kernel<C, 16, true><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr, pl.col_ld,
+                                                                         scale);
+        else if (pl.col_per == 8)
+            prec_cols_kernel<C, 8, false><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
+                                                                         pl.col_ld, scale);
+        else if (pl.col_per == 16)
+            prec_cols_kernel<C, 16, false><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
+                                                                          pl.col_ld, scale);
+        else
+            prec_cols_kernel<C, 32, false><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
+                                                                          pl.col_ld, scale);
+    } else {
+        const dim3 grd(a.W, nimg);
+        const int groups = (a.H / C) * w;
+        if (pl.p2) {
+            prec_col_fft_kernel<true><<<grd, pl.fb_tpr, pl.fb_smem, st>>>(a, 0);
+            prec_group_kernel<C><<<dim3((groups + 255) / 256, nimg), 256, 0, st>>>(a, scale);
+            prec_col_fft_kernel<true><<<grd, pl.fb_tpr, pl.fb_smem, st>>>(a, 1);
+        } else {
+            prec_col_fft_kernel<false><<<grd, pl.fb_tpr, pl.fb_smem, st>>>(a, 0);
+            prec_group_kernel<C><<<dim3((groups + 255) / 256, nimg), 256, 0, st>>>(a, scale);
+            prec_col_fft_kernel<false><<<grd, pl.fb_tpr, pl.fb_smem, st>>>(a, 1);
+        }
+    }
+}
+
+template <class F>
+cudaError_t smem_attr(F *f) {
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kPrecMaxSmem);
+}
+
+template <int C>
+cudaError_t set_attrs_c() {
+    cudaError_t e = smem_attr(prec_cols_kernel<C, 8, false>);
+    if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 16, false>);
+    if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 32, false>);
+    if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 16, true>);
+    return e;
+}
+
+}  // namespace
+
+bool precond_supported(int H, int W, int c) {
+    PrecPlan pl;
+    return make_prec_plan(H, W, c, &pl);
+}
+
+void launch_precond(const PrecArgs &a, cudaStream_t st) {
+    PrecPlan pl;
+    if (!make_prec_plan(a.H, a.W, a.c, &pl)) return;  // callers check precond_supported
+    const int nimg = (a.N + 1) / 2;
+    const float scale = 1.0f / ((float)a.H * (float)a.W);
+    const dim3 rgrd(a.H / pl.rg.TR, nimg), rblk(pl.rg.TR * pl.rg.tpr);
+    if (pl.p2)
+        prec_rows_fwd_kernel<true><<<rgrd, rblk, pl.row_smem, st>>>(a, pl.rg);
+    else
+        prec_rows_fwd_kernel<false><<<rgrd, rblk, pl.row_smem, st>>>(a, pl.rg);
+    switch (a.c) {
+        case 2: launch_cols<2>(a, pl, scale, st); break;
+        case 3: launch_cols<3>(a, pl, scale, st); break;
+        case 4: launch_cols<4>(a, pl, scale, st); break;
+        case 6: launch_cols<6>(a, pl, scale, st); break;
+        case 8: launch_cols<8>(a, pl, scale, st); break;
+        default: break;
+    }
+    if (pl.p2)
+        prec_rows_inv_kernel<true><<<rgrd, rblk, pl.row_smem, st>>>(a, pl.rg);
+    else
+        prec_rows_inv_kernel<false><<<rgrd, rblk, pl.row_smem, st>>>(a, pl.rg);
+}
+
+// B^ in FP32, same [kx][ky] layout as the FP64 spectrum it is rounded from.
+__global__ void spectrum_to_f32_kernel(const double2 *__restrict__ in, float2 *__restrict__ out,
+                                       size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+void launch_spectrum_to_f32(const double2 *in, float2 *out, size_t n, cudaStream_t st) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    spectrum_to_f32_kernel<<<blocks, 256, 0, st>>>(in, out, n);
+}
+
+cudaError_t precond_set_attrs() {
+    cudaError_t e = smem_attr(prec_rows_fwd_kernel<true>);
+    if (e == cudaSuccess) e = smem_attr(prec_rows_fwd_kernel<false>);
+    if (e == cudaSuccess) e = smem_attr(prec_rows_inv_kernel<true>);
+    if (e == cudaSuccess) e = smem_attr(prec_rows_inv_kernel<false>);
+    if (e == cudaSuccess) e = smem_attr(prec_col_fft_kernel<true>);
+    if (e == cudaSuccess) e = smem_attr(prec_col_fft_kernel<false>);
+    if (e == cudaSuccess) e = set_attrs_c<2>();
+    if (e == cudaSuccess) e = set_attrs_c<3>();
+    if (e == cudaSuccess) e = set_attrs_c<4>();
+    if (e == cudaSuccess) e = set_attrs_c<6>();
+    if (e == cudaSuccess) e = set_attrs_c<8>();
+    return e;
+}
+
+}  // namespace ps

@@ -88,6 +88,29 @@ def zstep(lrms, z0, kernel, ratio, I, mu, s, r, lam, exact_weight=False):
     return out
 
 
+def bicubic_up(lrms, ratio):
+    """Bicubic x ratio upsampling (Keys, a = -1/2) of (N, h, w) LR bands."""
+    N, h, w = lrms.shape
+    _f32(lrms, "lrms")
+    out = torch.empty((N, h * ratio, w * ratio), dtype=torch.float32, device=lrms.device)
+    _check(_lib.load().ps_op_bicubic_up(_ptr(lrms), N, h * ratio, w * ratio, ratio, _ptr(out),
+                                        _stream()))
+    return out
+
+
+def precond(r, kernel, ratio, lambda_gamma):
+    """z = P^{-1} r per band, P = B^T D^T D B + lambda_gamma L^T L (N, H, W)."""
+    N, H, W = r.shape
+    _f32(r, "r"), _f32(kernel, "kernel")
+    R = kernel.shape[0] // 2
+    out = torch.empty_like(r)
+    ws = _ws(N, H, W, ratio, R, r.device)
+    _check(_lib.load().ps_op_precond(_ptr(r), N, H, W, ratio, _ptr(kernel), R,
+                                     ctypes.c_float(lambda_gamma), _ptr(out), _ptr(ws),
+                                     ws.numel(), _stream()))
+    return out
+
+
 def omega(lrms, pan, ratio, l, lambda_omega):
     N = lrms.shape[0]
     H, W = pan.shape

@@ -58,6 +58,8 @@ def test_defaults_are_the_paper_values(lib):
     lib.ps_default_hrms_params(ctypes.byref(hp))
     assert hp.lambda_ == pytest.approx(p["lambda"], rel=1e-6)
     assert hp.r == p["r"]
+    # the preconditioned CG (an extension) is on by default, gamma = 4
+    assert hp.precond == 1 and hp.precond_gamma == pytest.approx(4.0)
 
 
 def test_workspace_size(lib):
@@ -107,6 +109,23 @@ def test_argument_errors_return_before_launch(lib):
     st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(hp), None, fake,
                            None, None, ctypes.c_void_p(0x1010), 1 << 30, None)
     assert st == 4
+    # preconditioner selector and weight
+    bad = HrmsParams.from_buffer_copy(hp)
+    bad.precond = 2
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
+                           None, None, fake, 1 << 30, None)
+    assert st == 1
+    bad = HrmsParams.from_buffer_copy(hp)
+    bad.precond_gamma = 0.0
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
+                           None, None, fake, 1 << 30, None)
+    assert st == 1
+    st = lib.ps_op_precond(fake, 2, 96, 96, 4, fake, 3, ctypes.c_float(-1.0), fake, fake,
+                           1 << 30, None)
+    assert st == 1
+    st = lib.ps_op_precond(fake, 2, 100, 100, 4, fake, 3, ctypes.c_float(1e-3), fake, fake,
+                           1 << 30, None)
+    assert st == 8                                                  # not 2^a 3^b
     bk = KernelParams.from_buffer_copy(kp)
     bk.mu3 = -1.0
     st = lib.ps_estimate_kernel(fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bk), None, fake,
