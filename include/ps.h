@@ -46,7 +46,8 @@ typedef enum ps_status {
     PS_ERR_NOT_CONVERGED = 5, /* iteration cap reached; result still written */
     PS_ERR_NONFINITE = 6,     /* NaN or Inf met in a reduction               */
     PS_ERR_BREAKDOWN = 7,     /* CG met p^T A p <= 0                         */
-    PS_ERR_UNSUPPORTED = 8    /* size outside what the kernels support       */
+    PS_ERR_UNSUPPORTED = 8,   /* size outside what the kernels support       */
+    PS_ERR_TIMEOUT = 9        /* a bounded device-side wait gave up          */
 } ps_status;
 
 /* Parameters of Algorithm 1 (blur kernel estimation). Defaults
@@ -94,7 +95,11 @@ typedef struct ps_hrms_params {
     int warm;           /* start point of the Z0 CG when d_z_init is NULL.
                            0 (default): zeros, as in the paper. 1: bicubic
                            x ratio upsampling of the LRMS band (Keys, a = -1/2,
-                           phase 0, circular). The stop rule is the same. */
+                           phase 0, circular). 2: the learned warm start of
+                           include/ps_cnn.h on (bicubic, PAN), parameters
+                           cnn_params. The stop rule is the same for all. */
+    const float *cnn_params; /* device, ps_cnn_param_count() FP32 values;
+                           read only when warm == 2                        */
 } ps_hrms_params;
 
 /* Per-band result of the Z0 conjugate-gradient solve. */
@@ -116,7 +121,8 @@ void ps_default_hrms_params(ps_hrms_params *h_params);
 const char *ps_status_string(int status);
 
 /* Workspace bytes needed by ps_pansharpen (covers ps_estimate_kernel and
- * ps_solve_hrms for the same sizes). 0 when a size is invalid. */
+ * ps_solve_hrms for the same sizes; h_hrms may be NULL, and with warm == 2
+ * the network's workspace is included). 0 when a size is invalid. */
 size_t ps_workspace_size(int N, int H, int W, int ratio, int R,
                          const ps_hrms_params *h_hrms);
 

@@ -85,6 +85,20 @@ ps_status ps_op_precond(const float *d_r, int N, int H, int W, int ratio,
 ps_status ps_op_bicubic_up(const float *d_lrms, int N, int H, int W, int ratio,
                            float *d_out, void *stream);
 
+/* One 3 x 3 convolution of the warm-start network with 32 input and 32
+ * output channels on the tensor cores (BF16 operands, FP32 accumulation),
+ * circular boundary. d_in and d_out: N x H x W x 32 BF16 (NHWC, device,
+ * 16-byte aligned, not aliased). d_weight: 32 x 32 x 3 x 3 FP32 as
+ * (out, in, dy + 1, dx + 1); d_bias: 32 FP32 or NULL. mode 0: out =
+ * ReLU(conv(in) + bias); 1: out = conv(in) + bias; 2: the adjoint in the
+ * input (backward data), out = conv^T(in), times (d_mask > 0) elementwise
+ * when d_mask (N x H x W x 32 BF16) is given. Workspace: 18688 bytes.
+ * Synchronises the stream; PS_ERR_TIMEOUT if a bounded wait gave up. */
+ps_status ps_op_cnn_conv32(const void *d_in, int N, int H, int W,
+                           const float *d_weight, const float *d_bias,
+                           const void *d_mask, int mode, void *d_out,
+                           void *d_ws, size_t ws_bytes, void *stream);
+
 /* Spectral weights of Eq. objective3 in closed form: the normal equations
  * of || B(u1) X omega - D B(u2) Y ||^2 + lambda_omega ||G omega||^2,
  * accumulated in FP64; u1 the (2l+1)^2 unit box on the LR grid, u2 the

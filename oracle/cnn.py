@@ -79,9 +79,11 @@ def make_input(up, pan):
     return np.stack([np.asarray(up, np.float64), np.asarray(pan, np.float64)]) / SCALE
 
 
-def forward(params, x):
+def forward(params, x, round_act=None):
     """Returns (z, cache): z (H, W) on the intensity scale, cache of the
-    pre-activations and activations for the backward pass."""
+    pre-activations and activations for the backward pass. round_act, if
+    given, is applied to every hidden activation (to model a storage
+    precision); None keeps plain FP64."""
     acts = [np.asarray(x, np.float64)]
     pre = []
     a = acts[0]
@@ -89,6 +91,8 @@ def forward(params, x):
         p = conv3x3(a, w, b)
         pre.append(p)
         a = np.maximum(p, 0.0) if l < len(params) - 1 else p
+        if round_act is not None and l < len(params) - 1:
+            a = round_act(a)
         acts.append(a)
     z = SCALE * (acts[0][0] + acts[-1][0])
     return z, {"acts": acts, "pre": pre}
@@ -99,8 +103,9 @@ def loss(z, target) -> float:
     return float(np.mean(d * d))
 
 
-def backward(params, cache, z, target):
-    """Gradients of loss(z, target) with respect to every (w, b)."""
+def backward(params, cache, z, target, round_grad=None):
+    """Gradients of loss(z, target) with respect to every (w, b). round_grad,
+    if given, is applied to the gradient passed between hidden layers."""
     acts, pre = cache["acts"], cache["pre"]
     H, W = z.shape
     d = (np.asarray(z, np.float64) - np.asarray(target, np.float64)) / SCALE
@@ -110,7 +115,9 @@ def backward(params, cache, z, target):
     for l in range(len(params) - 1, -1, -1):
         w, _ = params[l]
         if l < len(params) - 1:
-            g = g * (pre[l] > 0.0)                 # ReLU
+            g = g * (acts[l + 1] > 0.0)            # ReLU (its output is > 0 where it passes)
+            if round_grad is not None:
+                g = round_grad(g)
         grads[l] = (conv3x3_weight_grad(acts[l], g), g.sum(axis=(1, 2)))
         if l > 0:
             g = conv3x3_adjoint(g, w)

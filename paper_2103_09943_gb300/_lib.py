@@ -1,4 +1,5 @@
-"""ctypes declarations of the C-ABI in include/ps.h and include/ps_ops.h.
+"""ctypes declarations of the C-ABI in include/ps.h, include/ps_ops.h and
+include/ps_cnn.h.
 
 Loading fails loudly when libps.so has not been built: there is no CPU
 fallback anywhere in this package.
@@ -25,7 +26,8 @@ class HrmsParams(ctypes.Structure):
                 ("eps", ctypes.c_float), ("tol", ctypes.c_float),
                 ("max_iter", ctypes.c_int), ("exact_weight", ctypes.c_int),
                 ("host_loop", ctypes.c_int), ("precond", ctypes.c_int),
-                ("precond_gamma", ctypes.c_float), ("warm", ctypes.c_int)]
+                ("precond_gamma", ctypes.c_float), ("warm", ctypes.c_int),
+                ("cnn_params", ctypes.c_void_p)]
 
 
 class BandInfo(ctypes.Structure):
@@ -64,6 +66,13 @@ SIGNATURES = {
     "ps_op_zstep": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _I, _F, _I, _P, _P, _Z,
                          _P]),
     "ps_op_bicubic_up": (_I, [_P, _I, _I, _I, _I, _P, _P]),
+    "ps_cnn_param_count": (_I, []),
+    "ps_cnn_workspace_size": (_Z, [_I, _I, _I, _I]),
+    "ps_cnn_forward": (_I, [_P, _P, _P, _Z, _I, _I, _I, _P, _P, _Z, _P]),
+    "ps_cnn_loss_grad": (_I, [_P, _P, _P, _Z, _P, _I, _I, _I, _P, _P, _P, _Z, _P]),
+    "ps_cnn_adam": (_I, [_P, _P, _P, _P, _I, _F, _F, _F, _F, _P]),
+    "ps_cnn_sync_status": (_I, [_P, _I, _I, _I, _I, _P]),
+    "ps_op_cnn_conv32": (_I, [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P, _Z, _P]),
     "ps_op_precond": (_I, [_P, _I, _I, _I, _I, _P, _I, _F, _P, _P, _Z, _P]),
     "ps_op_omega": (_I, [_P, _P, _I, _I, _I, _I, _I, _F, _P, _P, _Z, _P]),
     "ps_op_kernel_normal_eq": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _Z, _P]),

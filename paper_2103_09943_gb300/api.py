@@ -57,12 +57,13 @@ def default_hrms_params(**kw) -> HrmsParams:
     return p
 
 
-def workspace_size(N, H, W, ratio, R) -> int:
-    return int(_lib.load().ps_workspace_size(N, H, W, ratio, R, None))
+def workspace_size(N, H, W, ratio, R, hparams: HrmsParams | None = None) -> int:
+    return int(_lib.load().ps_workspace_size(
+        N, H, W, ratio, R, ctypes.byref(hparams) if hparams is not None else None))
 
 
-def workspace(N, H, W, ratio, R, device=None) -> torch.Tensor:
-    n = workspace_size(N, H, W, ratio, R)
+def workspace(N, H, W, ratio, R, device=None, hparams: HrmsParams | None = None) -> torch.Tensor:
+    n = workspace_size(N, H, W, ratio, R, hparams)
     if n == 0:
         raise PsError("invalid sizes for a workspace")
     return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
@@ -105,7 +106,7 @@ def solve_hrms(lrms, pan, kernel, ratio: int, params: HrmsParams | None = None,
     hr = out if out is not None else torch.empty((N, H, W), dtype=torch.float32,
                                                  device=lrms.device)
     z0 = torch.empty_like(hr) if want_z0 else None
-    ws = ws if ws is not None else workspace(N, H, W, ratio, R, lrms.device)
+    ws = ws if ws is not None else workspace(N, H, W, ratio, R, lrms.device, p)
     bi = (BandInfo * N)()
     _check(_lib.load().ps_solve_hrms(
         _ptr(lrms), _ptr(pan), _ptr(kernel), N, H, W, ratio, R, ctypes.byref(p),
@@ -133,7 +134,7 @@ def pansharpen(lrms, pan, ratio: int, R: int, kparams: KernelParams | None = Non
                                                  device=lrms.device)
     kern = kernel_out if kernel_out is not None else torch.empty(
         (n, n), dtype=torch.float32, device=lrms.device)
-    ws = ws if ws is not None else workspace(N, H, W, ratio, R, lrms.device)
+    ws = ws if ws is not None else workspace(N, H, W, ratio, R, lrms.device, hp)
     ki = KernelInfo()
     bi = (BandInfo * N)()
     _check(_lib.load().ps_pansharpen(
@@ -162,7 +163,7 @@ class HostPipeline:
         self.d_hrms = torch.empty((N, H, W), dtype=torch.float32, device=device)
         self.d_kern = torch.empty((2 * R + 1, 2 * R + 1), dtype=torch.float32, device=device)
         self.h_hrms = torch.empty((N, H, W), dtype=torch.float32).pin_memory()
-        self.ws = workspace(N, H, W, ratio, R, device)
+        self.ws = workspace(N, H, W, ratio, R, device, self.hp)
 
     @property
     def h2d_bytes(self) -> int:

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <utility>
 #include <mutex>
 #include <vector>
 
@@ -12,6 +13,7 @@
 #include "kernels.cuh"
 #include "ps.h"
 #include "ps_ops.h"
+#include "ps_cnn.h"
 
 using namespace ps;
 
@@ -37,6 +39,7 @@ struct Layout {
     size_t twW32, twH32, twW64, twH64;  // twiddles
     size_t bands, glob;                 // CG scalars
     size_t bvec, f, G, omega, lags, ete, etf, zf, Q, kern, kinfo;
+    size_t cnn;
     size_t total;
 };
 
@@ -82,6 +85,7 @@ bool make_layout(int N, int H, int W, int c, int R, Layout *L) {
     L->Q = take(nt * nt * 4);
     L->kern = take(nt * 4);
     L->kinfo = take(64);
+    L->cnn = o;  // the warm-start network's workspace, when it is used
     L->total = o + kAlign;  // slack for aligning the caller's pointer
     return true;
 }
@@ -136,7 +140,8 @@ ps_status check_hrms(const ps_hrms_params *p) {
     if (p->precond != 0 && p->precond != 1) return PS_ERR_INVALID_ARG;
     if (p->precond && (!(p->precond_gamma > 0.f) || !isfinite(p->precond_gamma)))
         return PS_ERR_INVALID_ARG;
-    if (p->warm != 0 && p->warm != 1) return PS_ERR_INVALID_ARG;
+    if (p->warm < 0 || p->warm > 2) return PS_ERR_INVALID_ARG;
+    if (p->warm == 2 && !p->cnn_params) return PS_ERR_INVALID_ARG;
     return PS_OK;
 }
 
@@ -159,12 +164,13 @@ ps_status last_launch() { return cuda_status(cudaGetLastError()); }
 // One-time (per device) kernel attributes and the private capture stream.
 struct DevState {
     int attrs_done = 0;
+    int num_sms = 0;
     cudaStream_t capture = nullptr;
 };
 std::mutex g_mu;
 std::vector<DevState> g_dev;
 
-ps_status ensure_device(cudaStream_t *capture) {
+ps_status ensure_device(cudaStream_t *capture, int *num_sms = nullptr) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PS_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -175,8 +181,13 @@ ps_status ensure_device(cudaStream_t *capture) {
         if (fft_set_attrs() != cudaSuccess) return PS_ERR_CUDA;
         if (kest_set_attrs() != cudaSuccess) return PS_ERR_CUDA;
         if (precond_set_attrs() != cudaSuccess) return PS_ERR_CUDA;
+        if (cnn_set_attrs() != cudaSuccess) return PS_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev) !=
+            cudaSuccess)
+            return PS_ERR_CUDA;
         d.attrs_done = 1;
     }
+    if (num_sms) *num_sms = d.num_sms;
     if (capture) {
         if (!d.capture &&
             cudaStreamCreateWithFlags(&d.capture, cudaStreamNonBlocking) != cudaSuccess)
@@ -411,6 +422,7 @@ void ps_default_hrms_params(ps_hrms_params *p) {
     p->precond = 1;
     p->precond_gamma = 4.0f;
     p->warm = 0;
+    p->cnn_params = nullptr;
 }
 
 const char *ps_status_string(int s) {
@@ -424,14 +436,16 @@ const char *ps_status_string(int s) {
         case PS_ERR_NONFINITE: return "non-finite value in a reduction";
         case PS_ERR_BREAKDOWN: return "CG breakdown (p^T A p <= 0)";
         case PS_ERR_UNSUPPORTED: return "size not supported";
+        case PS_ERR_TIMEOUT: return "a bounded device-side wait gave up";
         default: return "unknown status";
     }
 }
 
-size_t ps_workspace_size(int N, int H, int W, int ratio, int R, const ps_hrms_params *) {
+size_t ps_workspace_size(int N, int H, int W, int ratio, int R, const ps_hrms_params *hp) {
     if (check_dims(N, H, W, ratio, R) != PS_OK) return 0;
     Layout L;
     if (!make_layout(N, H, W, ratio, R, &L)) return 0;
+    if (hp && hp->warm == 2) return L.total + ps_cnn_workspace_size(N, H, W, 0);
     return L.total;
 }
 
@@ -525,9 +539,18 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
     // the spectrum uses the r buffer as scratch: before b is written there
     if ((s = prepare_spectrum(ws, d_kernel, H, W, R, st)) != PS_OK) return s;
     launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
-    if (!d_z_init && p->warm == 1) {
+    if (!d_z_init && p->warm >= 1) {
         // bicubic start point, written where the iterate lives
         launch_bicubic_up(d_lrms, N, H / c, W / c, c, x, st);
+        if (p->warm == 2) {
+            // the network on (bicubic, PAN), in place: its last layer reads
+            // the bicubic value of a pixel and writes the result there
+            const size_t need = ws.L.cnn + ps_cnn_workspace_size(N, H, W, 0);
+            if (ws_bytes < need) return PS_ERR_WORKSPACE;
+            if ((s = ps_cnn_forward(p->cnn_params, x, d_pan, 0, N, H, W, x,
+                                    ws.base + ws.L.cnn, ws_bytes - ws.L.cnn, stream)) != PS_OK)
+                return s;
+        }
         d_z_init = x;
     }
     if (d_z_init) {
@@ -746,6 +769,233 @@ ps_status ps_op_bicubic_up(const float *d_lrms, int N, int H, int W, int ratio, 
     if ((s = ensure_device(nullptr)) != PS_OK) return s;
     launch_bicubic_up(d_lrms, N, H / ratio, W / ratio, ratio, d_out, (cudaStream_t)stream);
     return last_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Warm-start network (include/ps_cnn.h)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+constexpr size_t kWPack = 18432;
+
+struct CnnLayout {
+    size_t act[6];    // act[1..5]: hidden activations (training); act[1], act[2] ping-pong
+    size_t D[2];      // gradients between hidden layers (training)
+    size_t d5;        // gradient of the output (training)
+    size_t wf, wb;    // packed B operands, 4 layers each (forward, adjoint)
+    size_t err;
+    size_t total;
+};
+
+bool cnn_make_layout(int B, int H, int W, int training, CnnLayout *L) {
+    if (B < 1 || H < 1 || W < 1) return false;
+    const size_t P = (size_t)B * H * W;
+    size_t o = 0;
+    auto take = [&o](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    memset(L, 0, sizeof(*L));
+    const int nact = training ? 5 : 2;
+    for (int l = 1; l <= nact; ++l) L->act[l] = take(P * 64);
+    if (training) {
+        L->D[0] = take(P * 64);
+        L->D[1] = take(P * 64);
+        L->d5 = take(P * 4);
+    }
+    L->wf = take(4 * kWPack);
+    L->wb = take(4 * kWPack);
+    L->err = take(256);
+    L->total = o + kAlign;
+    return true;
+}
+
+struct CnnCall {
+    char *base;
+    CnnLayout L;
+    int w_off[7], b_off[6];
+    int sms;
+    template <class T>
+    T *at(size_t off) const { return reinterpret_cast<T *>(base + off); }
+};
+
+ps_status cnn_bind(void *d_ws, size_t ws_bytes, int B, int H, int W, int training, CnnCall *c) {
+    if (!d_ws || ((uintptr_t)d_ws) % kAlign) return PS_ERR_WORKSPACE;
+    if (!cnn_make_layout(B, H, W, training, &c->L)) return PS_ERR_INVALID_ARG;
+    if (ws_bytes < c->L.total - kAlign) return PS_ERR_WORKSPACE;
+    c->base = static_cast<char *>(d_ws);
+    cnn_layout(c->w_off, c->b_off);
+    ps_status s = ensure_device(nullptr, &c->sms);
+    return s;
+}
+
+void cnn_conv(const CnnCall &c, const __nv_bfloat16 *in, __nv_bfloat16 *out, int layer,
+              int adjoint, const __nv_bfloat16 *mask, const float *params, int B, int H, int W,
+              cudaStream_t st) {
+    Conv32Args a;
+    a.in = in;
+    a.out = out;
+    a.wpack = c.base + (adjoint ? c.L.wb : c.L.wf) + (size_t)(layer - 1) * kWPack;
+    a.bias = adjoint ? nullptr : params + c.b_off[layer];
+    a.mask = mask;
+    a.N = B;
+    a.H = H;
+    a.W = W;
+    a.relu = adjoint ? 0 : 1;
+    a.rpi = 32;
+    a.err = c.at<int>(c.L.err);
+    launch_conv32(a, c.sms, st);
+}
+
+ps_status cnn_check_inputs(const float *params, const float *up, const float *pan, int B, int H,
+                           int W) {
+    if (!params || !up || !pan || B < 1 || H < 3 || W < 3) return PS_ERR_INVALID_ARG;
+    if (W % 4) return PS_ERR_UNSUPPORTED;
+    return PS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ps_cnn_param_count(void) {
+    int w[7], b[6];
+    cnn_layout(w, b);
+    return w[6];
+}
+
+size_t ps_cnn_workspace_size(int B, int H, int W, int training) {
+    CnnLayout L;
+    if (!cnn_make_layout(B, H, W, training, &L)) return 0;
+    return L.total;
+}
+
+ps_status ps_cnn_forward(const float *d_params, const float *d_up, const float *d_pan,
+                         size_t pan_stride, int B, int H, int W, float *d_z, void *d_ws,
+                         size_t ws_bytes, void *stream) {
+    ps_status s;
+    if ((s = cnn_check_inputs(d_params, d_up, d_pan, B, H, W)) != PS_OK) return s;
+    if (!d_z) return PS_ERR_INVALID_ARG;
+    CnnCall c;
+    if ((s = cnn_bind(d_ws, ws_bytes, B, H, W, 0, &c)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(c.at<int>(c.L.err), 0, sizeof(int), st) != cudaSuccess) return PS_ERR_CUDA;
+    for (int l = 1; l <= 4; ++l)
+        launch_pack_w32(d_params + c.w_off[l], c.base + c.L.wf + (l - 1) * kWPack, 0, st);
+    __nv_bfloat16 *A = c.at<__nv_bfloat16>(c.L.act[1]), *Bf = c.at<__nv_bfloat16>(c.L.act[2]);
+    launch_cnn_first(d_up, d_pan, pan_stride, d_params + c.w_off[0], B, H, W, A, st);
+    for (int l = 1; l <= 4; ++l) {
+        cnn_conv(c, A, Bf, l, 0, nullptr, d_params, B, H, W, st);
+        std::swap(A, Bf);
+    }
+    launch_cnn_last(A, d_up, d_params + c.w_off[5], B, H, W, d_z, nullptr, nullptr, nullptr, st);
+    return last_launch();
+}
+
+ps_status ps_cnn_loss_grad(const float *d_params, const float *d_up, const float *d_pan,
+                           size_t pan_stride, const float *d_target, int B, int H, int W,
+                           float *d_grad, double *d_loss, void *d_ws, size_t ws_bytes,
+                           void *stream) {
+    ps_status s;
+    if ((s = cnn_check_inputs(d_params, d_up, d_pan, B, H, W)) != PS_OK) return s;
+    if (!d_target || !d_grad || !d_loss) return PS_ERR_INVALID_ARG;
+    CnnCall c;
+    if ((s = cnn_bind(d_ws, ws_bytes, B, H, W, 1, &c)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(c.at<int>(c.L.err), 0, sizeof(int), st) != cudaSuccess) return PS_ERR_CUDA;
+    if (cudaMemsetAsync(d_grad, 0, (size_t)c.w_off[6] * sizeof(float), st) != cudaSuccess ||
+        cudaMemsetAsync(d_loss, 0, sizeof(double), st) != cudaSuccess)
+        return PS_ERR_CUDA;
+    for (int l = 1; l <= 4; ++l) {
+        launch_pack_w32(d_params + c.w_off[l], c.base + c.L.wf + (l - 1) * kWPack, 0, st);
+        launch_pack_w32(d_params + c.w_off[l], c.base + c.L.wb + (l - 1) * kWPack, 1, st);
+    }
+    __nv_bfloat16 *act[6];
+    for (int l = 1; l <= 5; ++l) act[l] = c.at<__nv_bfloat16>(c.L.act[l]);
+    __nv_bfloat16 *D[2] = {c.at<__nv_bfloat16>(c.L.D[0]), c.at<__nv_bfloat16>(c.L.D[1])};
+    float *d5 = c.at<float>(c.L.d5);
+    // forward, keeping every activation
+    launch_cnn_first(d_up, d_pan, pan_stride, d_params + c.w_off[0], B, H, W, act[1], st);
+    for (int l = 1; l <= 4; ++l) cnn_conv(c, act[l], act[l + 1], l, 0, nullptr, d_params, B, H, W, st);
+    launch_cnn_last(act[5], d_up, d_params + c.w_off[5], B, H, W, nullptr, d_target, d5, d_loss,
+                    st);
+    // backward: D_l = dL / d(conv_l output before its ReLU)
+    launch_cnn_last_bwd(act[5], d5, d_params + c.w_off[5], B, H, W, D[0], d_grad + c.w_off[5],
+                        st);
+    int cur = 0;
+    for (int l = 4; l >= 1; --l) {
+        launch_cnn_wgrad32(act[l], D[cur], B, H, W, d_grad + c.w_off[l], d_grad + c.b_off[l],
+                           c.sms, st);
+        cnn_conv(c, D[cur], D[cur ^ 1], l, 1, act[l], d_params, B, H, W, st);
+        cur ^= 1;
+    }
+    launch_cnn_wgrad_first(d_up, d_pan, pan_stride, D[cur], B, H, W, d_grad + c.w_off[0], st);
+    return last_launch();
+}
+
+ps_status ps_cnn_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int step,
+                      float lr, float beta1, float beta2, float eps, void *stream) {
+    if (!d_params || !d_grad || !d_m || !d_v || step < 1) return PS_ERR_INVALID_ARG;
+    if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
+        !(eps > 0.f))
+        return PS_ERR_INVALID_ARG;
+    launch_cnn_adam(d_params, d_grad, d_m, d_v, ps_cnn_param_count(), step, lr, beta1, beta2, eps,
+                    (cudaStream_t)stream);
+    return last_launch();
+}
+
+ps_status ps_cnn_sync_status(void *d_ws, int B, int H, int W, int training, void *stream) {
+    CnnLayout L;
+    if (!d_ws || !cnn_make_layout(B, H, W, training, &L)) return PS_ERR_INVALID_ARG;
+    int *err = reinterpret_cast<int *>(static_cast<char *>(d_ws) + L.err);
+    int h = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return PS_ERR_CUDA;
+    if (h && cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return PS_ERR_CUDA;
+    return h ? PS_ERR_TIMEOUT : PS_OK;
+}
+
+ps_status ps_op_cnn_conv32(const void *d_in, int N, int H, int W, const float *d_weight,
+                           const float *d_bias, const void *d_mask, int mode, void *d_out,
+                           void *d_ws, size_t ws_bytes, void *stream) {
+    if (N < 1 || H < 1 || W < 1 || mode < 0 || mode > 2) return PS_ERR_INVALID_ARG;
+    if (!d_in || !d_weight || !d_out || d_in == d_out) return PS_ERR_INVALID_ARG;
+    if (!aligned16(d_in) || !aligned16(d_out) || (d_mask && !aligned16(d_mask)))
+        return PS_ERR_INVALID_ARG;
+    if (!d_ws || ((uintptr_t)d_ws) % kAlign) return PS_ERR_WORKSPACE;
+    if (ws_bytes < 18432 + 256) return PS_ERR_WORKSPACE;
+    ps_status s;
+    int sms = 0;
+    if ((s = ensure_device(nullptr, &sms)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = static_cast<char *>(d_ws);
+    int *err = reinterpret_cast<int *>(ws + 18432);
+    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return PS_ERR_CUDA;
+    launch_pack_w32(d_weight, ws, mode == 2 ? 1 : 0, st);
+    Conv32Args a;
+    a.in = static_cast<const __nv_bfloat16 *>(d_in);
+    a.out = static_cast<__nv_bfloat16 *>(d_out);
+    a.wpack = ws;
+    a.bias = mode == 2 ? nullptr : d_bias;
+    a.mask = mode == 2 ? static_cast<const __nv_bfloat16 *>(d_mask) : nullptr;
+    a.N = N;
+    a.H = H;
+    a.W = W;
+    a.relu = mode == 0 ? 1 : 0;
+    a.rpi = 32;
+    a.err = err;
+    launch_conv32(a, sms, st);
+    if ((s = last_launch()) != PS_OK) return s;
+    int h_err = 0;
+    if (cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return PS_ERR_CUDA;
+    return h_err ? PS_ERR_TIMEOUT : PS_OK;
 }
 
 ps_status ps_op_precond(const float *d_r, int N, int H, int W, int ratio, const float *d_kernel,

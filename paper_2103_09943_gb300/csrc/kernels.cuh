@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 
@@ -95,6 +96,40 @@ bool precond_supported(int H, int W, int c);
 void launch_precond(const PrecArgs &a, cudaStream_t st);
 void launch_spectrum_to_f32(const double2 *in, float2 *out, size_t n, cudaStream_t st);
 cudaError_t precond_set_attrs();
+
+// cnn.cu: 3 x 3 convolutions with 32 in / 32 out channels on tcgen05
+struct Conv32Args {
+    const __nv_bfloat16 *in;    // N x H x W x 32, NHWC
+    __nv_bfloat16 *out;         // N x H x W x 32
+    const void *wpack;          // B operand from launch_pack_w32 (18432 bytes)
+    const float *bias;          // 32, or NULL
+    const __nv_bfloat16 *mask;  // NULL, or out = conv * (mask > 0) (before the bias)
+    int N, H, W;
+    int relu;                   // bias then ReLU
+    int rpi;                    // output rows per work item
+    int *err;                   // set to 1 when a bounded wait gives up
+};
+size_t conv32_smem_bytes();
+void launch_pack_w32(const float *w, void *out, int adjoint, cudaStream_t st);
+void launch_conv32(const Conv32Args &a, int num_sms, cudaStream_t st);
+cudaError_t cnn_set_attrs();
+
+// cnn_core.cu: the network's CUDA-core parts
+void cnn_layout(int *w_off, int *b_off);  // w_off[6] = parameter count
+void launch_cnn_first(const float *up, const float *pan, size_t pan_stride, const float *prm,
+                      int B, int H, int W, __nv_bfloat16 *a1, cudaStream_t st);
+void launch_cnn_last(const __nv_bfloat16 *a5, const float *up, const float *prm5, int B, int H,
+                     int W, float *z, const float *target, float *d5, double *loss,
+                     cudaStream_t st);
+void launch_cnn_last_bwd(const __nv_bfloat16 *a5, const float *d5, const float *prm5, int B,
+                         int H, int W, __nv_bfloat16 *D4, float *g5, cudaStream_t st);
+void launch_cnn_wgrad32(const __nv_bfloat16 *act, const __nv_bfloat16 *D, int B, int H, int W,
+                        float *gw, float *gb, int num_sms, cudaStream_t st);
+void launch_cnn_wgrad_first(const float *up, const float *pan, size_t pan_stride,
+                            const __nv_bfloat16 *D0, int B, int H, int W, float *g0,
+                            cudaStream_t st);
+void launch_cnn_adam(float *p, const float *g, float *m, float *v, int n, int step, float lr,
+                     float b1, float b2, float eps, cudaStream_t st);
 
 // warm.cu
 void launch_bicubic_up(const float *X, int N, int h, int w, int c, float *out,

@@ -37,7 +37,7 @@ namespace {
 
 constexpr int kPrecPad = 4;  // float2 padding of shared rows (spreads banks)
 constexpr int kPrecMaxSmem = 192 * 1024;
-constexpr int kPrecColThreads = 512;  // CTA size bound of the fused column pass
+constexpr int kPrecColThreads = 256;  // CTA size bound of the fused column pass
 
 __device__ __forceinline__ bool image_idle(const PrecArgs &a, int k) {
     if (!a.bands) return false;
@@ -179,18 +179,40 @@ __global__ void __launch_bounds__(1024) prec_rows_fwd_kernel(PrecArgs a, RowGeom
     const float *r1 = (2 * k + 1 < a.N) ? r0 + HW : nullptr;
     if (a.bands && a.bands[2 * k].done) r0 = nullptr;
     if (a.bands && r1 && a.bands[2 * k + 1].done) r1 = nullptr;
-    for (int i = threadIdx.x; i < TR * W; i += blockDim.x) {
-        const int rr = i / W, x = i - rr * W;
-        psm[rr * ld + ix<P2>(x)] =
-            make_float2(r0 ? __ldg(r0 + i) : 0.0f, r1 ? __ldg(r1 + i) : 0.0f);
+    // four pixels of both bands per thread and step (W % 4 == 0), four steps
+    // in flight
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int n4 = TR * W / 4;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+        const float4 u = r0 ? __ldg(reinterpret_cast<const float4 *>(r0) + i) : z4;
+        const float4 v = r1 ? __ldg(reinterpret_cast<const float4 *>(r1) + i) : z4;
+        const int rr = (4 * i) / W, x = 4 * i - rr * W;
+        float2 *d = psm + rr * ld;
+        d[ix<P2>(x)] = make_float2(u.x, v.x);
+        d[ix<P2>(x + 1)] = make_float2(u.y, v.y);
+        d[ix<P2>(x + 2)] = make_float2(u.z, v.z);
+        d[ix<P2>(x + 3)] = make_float2(u.w, v.w);
     }
     __syncthreads();
     const int row = threadIdx.x / g.tpr, t = threadIdx.x - row * g.tpr;
     row_fft<P2>(psm + row * ld, W, a.pw, a.twW, false, t, g.tpr);
     float2 *S = a.spec + (size_t)k * HW;
-    for (int i = threadIdx.x; i < TR * W; i += blockDim.x) {
-        const int rr = i % TR, kx = i / TR;
-        S[(size_t)kx * H + y0 + rr] = psm[rr * ld + ix<P2>(kx)];
+    if (TR % 2 == 0) {
+        // two rows per 16-byte store
+        const int hp = TR / 2;
+        for (int i = threadIdx.x; i < hp * W; i += blockDim.x) {
+            const int r2 = i % hp, kx = i / hp;
+            const float2 e0 = psm[(2 * r2) * ld + ix<P2>(kx)];
+            const float2 e1 = psm[(2 * r2 + 1) * ld + ix<P2>(kx)];
+            *reinterpret_cast<float4 *>(S + (size_t)kx * H + y0 + 2 * r2) =
+                make_float4(e0.x, e0.y, e1.x, e1.y);
+        }
+    } else {
+        for (int i = threadIdx.x; i < TR * W; i += blockDim.x) {
+            const int rr = i % TR, kx = i / TR;
+            S[(size_t)kx * H + y0 + rr] = psm[rr * ld + ix<P2>(kx)];
+        }
     }
 }
 
@@ -198,16 +220,20 @@ __global__ void __launch_bounds__(1024) prec_rows_fwd_kernel(PrecArgs a, RowGeom
 // Column pass with the group solves: columns kx0 + q w, q < C, of image k.
 // ---------------------------------------------------------------------------
 template <int C, int PER, bool P2>
-__global__ void __launch_bounds__(kPrecColThreads) prec_cols_kernel(PrecArgs a, int tpr, int ld,
+__global__ void __launch_bounds__(kPrecColThreads, 3) prec_cols_kernel(PrecArgs a, int tpr, int ld,
                                                                      float scale) {
     extern __shared__ __align__(16) float2 psm[];
     const int k = blockIdx.y, kx0 = blockIdx.x;
     if (image_idle(a, k)) return;
     const int H = a.H, W = a.W, h = H / C, w = W / C;
     float2 *S = a.spec + (size_t)k * H * W;
-    for (int i = threadIdx.x; i < C * H; i += blockDim.x) {
-        const int q = i / H, y = i - q * H;
-        psm[q * ld + ix<P2>(y)] = S[(size_t)(kx0 + q * w) * H + y];
+    // two complex values per 16-byte access (H even), four accesses in flight
+#pragma unroll 4
+    for (int i = threadIdx.x; i < C * H / 2; i += blockDim.x) {
+        const int q = (2 * i) / H, y = 2 * i - q * H;
+        const float4 v = *reinterpret_cast<const float4 *>(S + (size_t)(kx0 + q * w) * H + y);
+        psm[q * ld + ix<P2>(y)] = make_float2(v.x, v.y);
+        psm[q * ld + ix<P2>(y + 1)] = make_float2(v.z, v.w);
     }
     __syncthreads();
     const int row = threadIdx.x / tpr, t = threadIdx.x - row * tpr;
@@ -224,9 +250,11 @@ __global__ void __launch_bounds__(kPrecColThreads) prec_cols_kernel(PrecArgs a, 
         fft_p2_row(psm + row * ld, H, a.twH, true, t, tpr);
     else
         fft_row<PER, float2>(psm + row * ld, a.ph, a.twH, true, t, tpr);
-    for (int i = threadIdx.x; i < C * H; i += blockDim.x) {
-        const int q = i / H, y = i - q * H;
-        S[(size_t)(kx0 + q * w) * H + y] = psm[q * ld + ix<P2>(y)];
+    for (int i = threadIdx.x; i < C * H / 2; i += blockDim.x) {
+        const int q = (2 * i) / H, y = 2 * i - q * H;
+        const float2 e0 = psm[q * ld + ix<P2>(y)], e1 = psm[q * ld + ix<P2>(y + 1)];
+        *reinterpret_cast<float4 *>(S + (size_t)(kx0 + q * w) * H + y) =
+            make_float4(e0.x, e0.y, e1.x, e1.y);
     }
 }
 
@@ -271,9 +299,22 @@ __global__ void __launch_bounds__(1024) prec_rows_inv_kernel(PrecArgs a, RowGeom
     const size_t HW = (size_t)H * W;
     const int y0 = blockIdx.x * TR;
     const float2 *S = a.spec + (size_t)k * HW;
-    for (int i = threadIdx.x; i < TR * W; i += blockDim.x) {
-        const int rr = i % TR, kx = i / TR;
-        psm[rr * ld + ix<P2>(kx)] = S[(size_t)kx * H + y0 + rr];
+    if (TR % 2 == 0) {
+        // two rows per 16-byte load, four loads in flight
+        const int hp = TR / 2;
+#pragma unroll 4
+        for (int i = threadIdx.x; i < hp * W; i += blockDim.x) {
+            const int r2 = i % hp, kx = i / hp;
+            const float4 v =
+                *reinterpret_cast<const float4 *>(S + (size_t)kx * H + y0 + 2 * r2);
+            psm[(2 * r2) * ld + ix<P2>(kx)] = make_float2(v.x, v.y);
+            psm[(2 * r2 + 1) * ld + ix<P2>(kx)] = make_float2(v.z, v.w);
+        }
+    } else {
+        for (int i = threadIdx.x; i < TR * W; i += blockDim.x) {
+            const int rr = i % TR, kx = i / TR;
+            psm[rr * ld + ix<P2>(kx)] = S[(size_t)kx * H + y0 + rr];
+        }
     }
     __syncthreads();
     const int row = threadIdx.x / g.tpr, t = threadIdx.x - row * g.tpr;
@@ -281,14 +322,26 @@ __global__ void __launch_bounds__(1024) prec_rows_inv_kernel(PrecArgs a, RowGeom
     const size_t o0 = (size_t)(2 * k) * HW + (size_t)y0 * W;
     const bool two = 2 * k + 1 < a.N;
     float d0 = 0.f, d1 = 0.f;
-    for (int i = threadIdx.x; i < TR * W; i += blockDim.x) {
-        const int rr = i / W, x = i - rr * W;
-        const float2 zv = psm[rr * ld + ix<P2>(x)];
-        a.z[o0 + i] = zv.x;
-        if (two) a.z[o0 + HW + i] = zv.y;
+    const int n4 = TR * W / 4;
+    float4 *z0 = reinterpret_cast<float4 *>(a.z + o0);
+    float4 *z1 = reinterpret_cast<float4 *>(a.z + o0 + HW);
+    const float4 *q0 = reinterpret_cast<const float4 *>(a.r + o0);
+    const float4 *q1 = reinterpret_cast<const float4 *>(a.r + o0 + HW);
+#pragma unroll 2
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+        const int rr = (4 * i) / W, x = 4 * i - rr * W;
+        const float2 *sr = psm + rr * ld;
+        const float2 e0 = sr[ix<P2>(x)], e1 = sr[ix<P2>(x + 1)], e2 = sr[ix<P2>(x + 2)],
+                     e3 = sr[ix<P2>(x + 3)];
+        z0[i] = make_float4(e0.x, e1.x, e2.x, e3.x);
+        if (two) z1[i] = make_float4(e0.y, e1.y, e2.y, e3.y);
         if (a.bands) {
-            d0 = fmaf(__ldg(a.r + o0 + i), zv.x, d0);
-            if (two) d1 = fmaf(__ldg(a.r + o0 + HW + i), zv.y, d1);
+            const float4 u = __ldg(q0 + i);
+            d0 = fmaf(u.x, e0.x, fmaf(u.y, e1.x, fmaf(u.z, e2.x, fmaf(u.w, e3.x, d0))));
+            if (two) {
+                const float4 v = __ldg(q1 + i);
+                d1 = fmaf(v.x, e0.y, fmaf(v.y, e1.y, fmaf(v.z, e2.y, fmaf(v.w, e3.y, d1))));
+            }
         }
     }
     if (!a.bands) return;

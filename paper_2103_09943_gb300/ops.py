@@ -98,6 +98,25 @@ def bicubic_up(lrms, ratio):
     return out
 
 
+def cnn_conv32(x, weight, bias=None, mode=0, mask=None):
+    """One 32 -> 32 3 x 3 convolution on the tensor cores: x (N, H, W, 32)
+    BF16 NHWC, weight (32, 32, 3, 3) FP32. mode 0: ReLU(conv + bias), 1:
+    conv + bias, 2: adjoint (backward data), masked by mask > 0 if given."""
+    N, H, W, C = x.shape
+    if C != 32 or x.dtype != torch.bfloat16 or not x.is_contiguous():
+        raise ValueError("x must be contiguous (N, H, W, 32) bfloat16")
+    _f32(weight, "weight")
+    if bias is not None:
+        _f32(bias, "bias")
+    out = torch.empty_like(x)
+    ws = torch.empty(18688, dtype=torch.uint8, device=x.device)
+    _check(_lib.load().ps_op_cnn_conv32(_ptr(x), N, H, W, _ptr(weight),
+                                        _ptr(bias) if bias is not None else None,
+                                        _ptr(mask) if mask is not None else None, mode,
+                                        _ptr(out), _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
 def precond(r, kernel, ratio, lambda_gamma):
     """z = P^{-1} r per band, P = B^T D^T D B + lambda_gamma L^T L (N, H, W)."""
     N, H, W = r.shape
