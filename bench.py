@@ -282,6 +282,31 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
+def run_profile_solve(args):
+    """One solve of the workload scene with host-launched CG iterations and a
+    fixed iteration count (the tolerance out of reach), after one untimed
+    solve, so that a profiler sees every kernel of the loop."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2103_09943_gb300 import api
+    cfg = workload_config(args.r)
+    scene = synth.make_scene(cfg)
+    X = torch.from_numpy(scene["lrms"]).to(dev)
+    Y = torch.from_numpy(scene["pan"]).to(dev)
+    K = torch.from_numpy(scene["kernel"]).to(dev)
+    hp = api.default_hrms_params(host_loop=1, tol=1e-30, max_iter=args.profile_solve,
+                                 precond=1 if args.precond == "fft" else 0)
+    for _ in range(2):
+        api.solve_hrms(X, Y, K, cfg.ratio, hp, info=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solve": args.profile_solve, "workload": workload_name(cfg)}))
+    return 0
+
+
 def run_gpu(args):
     import torch
     rank, local_rank, world = dist_env()
@@ -424,6 +449,9 @@ def parse(argv=None):
     ap.add_argument("--cpu-crop", type=int, default=128)
     ap.add_argument("--ref-crop", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-solve", type=int, default=0, metavar="ITERS",
+                    help="no timing: run one HRMS solve of the workload with the CG loop "
+                         "launched from the host, ITERS iterations (for profiler captures)")
     ap.add_argument("--precond", default="fft", choices=["fft", "none"],
                     help="preconditioner of the Z0 CG (fft: alias-group FFT solve; none: "
                          "plain CG as in the paper)")
@@ -437,6 +465,8 @@ def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_solve:
+        return run_profile_solve(args)
     return run_gpu(args)
 
 

@@ -242,7 +242,7 @@ void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, in
     la.bands = a.bands;
     la.g = a.g;
     la.cg = 1;
-    launch_llp(la, LLP_CGQ, a.r, a.N, st);
+    launch_llp_cgq2(la, a.r, a.N, st);
     launch_cg_update(a.x, a.rv, p_new, a.ap, a.v, a.u, a.R, a.c, a.N, a.H, a.W, a.bands, a.g, st);
     if (a.precond) launch_precond(a.pa, st);
     launch_cg_control(a.bands, a.g, a.N, use_cond, h, st);
@@ -310,18 +310,12 @@ ps_status get_cg_graph(const CgLoopArgs &a, cudaStream_t capture, cudaGraphExec_
 // Twiddles and the kernel spectrum B^ (FP64, transposed layout [kx][ky], and
 // its FP32 rounding for the preconditioner), once per solve.
 ps_status prepare_spectrum(const Ws &ws, const float *u, int H, int W, int R, cudaStream_t st) {
-    FftPlan pw, ph;
-    if (!fft_make_plan(W, &pw) || !fft_make_plan(H, &ph)) return PS_ERR_UNSUPPORTED;
-    double2 *cbuf64 = ws.at<double2>(ws.L.r);
     double2 *bhat = ws.at<double2>(ws.L.bhat);
     float2 *twW32 = ws.at<float2>(ws.L.twW32), *twH32 = ws.at<float2>(ws.L.twH32);
     double2 *twW64 = ws.at<double2>(ws.L.twW64), *twH64 = ws.at<double2>(ws.L.twH64);
     launch_fft_twiddles(W, twW32, twW64, st);
     launch_fft_twiddles(H, twH32, twH64, st);
-    launch_kernel_embed(u, R, H, W, cbuf64, st);
-    launch_fft_rows64(cbuf64, pw, H, twW64, st);
-    launch_transpose64(cbuf64, bhat, H, W, 1, st);
-    launch_fft_rows64(bhat, ph, W, twH64, st);
+    launch_kernel_spectrum(u, R, H, W, twW64, twH64, bhat, st);
     launch_spectrum_to_f32(bhat, ws.at<float2>(ws.L.bh32), (size_t)H * W, st);
     return last_launch();
 }
@@ -536,7 +530,6 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
     CgGlobal *g = ws.at<CgGlobal>(ws.L.glob);
 
     launch_pan_stats(d_pan, H, W, p->r, p->eps, nullptr, nullptr, nullptr, st4, st);
-    // the spectrum uses the r buffer as scratch: before b is written there
     if ((s = prepare_spectrum(ws, d_kernel, H, W, R, st)) != PS_OK) return s;
     launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
     if (!d_z_init && p->warm >= 1) {
@@ -834,8 +827,17 @@ ps_status cnn_bind(void *d_ws, size_t ws_bytes, int B, int H, int W, int trainin
 
 void cnn_conv(const CnnCall &c, const __nv_bfloat16 *in, __nv_bfloat16 *out, int layer,
               int adjoint, const __nv_bfloat16 *mask, const float *params, int B, int H, int W,
-              cudaStream_t st) {
+              cudaStream_t st, int mode = CONV_PLAIN, const float *up = nullptr,
+              const float *pan = nullptr, size_t pan_stride = 0, float *z = nullptr) {
     Conv32Args a;
+    memset(&a, 0, sizeof(a));
+    a.mode = mode;
+    a.up = up;
+    a.pan = pan;
+    a.pan_stride = pan_stride;
+    a.w0 = params + c.w_off[0];
+    a.w5 = params + c.w_off[5];
+    a.z = z;
     a.in = in;
     a.out = out;
     a.wpack = c.base + (adjoint ? c.L.wb : c.L.wf) + (size_t)(layer - 1) * kWPack;
@@ -886,12 +888,14 @@ ps_status ps_cnn_forward(const float *d_params, const float *d_up, const float *
     for (int l = 1; l <= 4; ++l)
         launch_pack_w32(d_params + c.w_off[l], c.base + c.L.wf + (l - 1) * kWPack, 0, st);
     __nv_bfloat16 *A = c.at<__nv_bfloat16>(c.L.act[1]), *Bf = c.at<__nv_bfloat16>(c.L.act[2]);
-    launch_cnn_first(d_up, d_pan, pan_stride, d_params + c.w_off[0], B, H, W, A, st);
-    for (int l = 1; l <= 4; ++l) {
-        cnn_conv(c, A, Bf, l, 0, nullptr, d_params, B, H, W, st);
-        std::swap(A, Bf);
-    }
-    launch_cnn_last(A, d_up, d_params + c.w_off[5], B, H, W, d_z, nullptr, nullptr, nullptr, st);
+    // layer 1 computes its input rows (the first layer) itself, layer 4
+    // applies the last layer in its epilogue: a1 and a5 never reach memory
+    cnn_conv(c, nullptr, A, 1, 0, nullptr, d_params, B, H, W, st, CONV_FIRST, d_up, d_pan,
+             pan_stride);
+    cnn_conv(c, A, Bf, 2, 0, nullptr, d_params, B, H, W, st);
+    cnn_conv(c, Bf, A, 3, 0, nullptr, d_params, B, H, W, st);
+    cnn_conv(c, A, nullptr, 4, 0, nullptr, d_params, B, H, W, st, CONV_LAST, d_up, d_pan,
+             pan_stride, d_z);
     return last_launch();
 }
 
@@ -978,6 +982,8 @@ ps_status ps_op_cnn_conv32(const void *d_in, int N, int H, int W, const float *d
     if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return PS_ERR_CUDA;
     launch_pack_w32(d_weight, ws, mode == 2 ? 1 : 0, st);
     Conv32Args a;
+    memset(&a, 0, sizeof(a));
+    a.mode = CONV_PLAIN;
     a.in = static_cast<const __nv_bfloat16 *>(d_in);
     a.out = static_cast<__nv_bfloat16 *>(d_out);
     a.wpack = ws;

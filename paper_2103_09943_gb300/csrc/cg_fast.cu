@@ -25,7 +25,7 @@ __device__ __forceinline__ int wrap_mod(int i, int n) {
     return m < 0 ? m + n : m;
 }
 
-constexpr int SITE_TX = 32, SITE_TY = 8, SITE_TYT = 4;
+constexpr int SITE_TX = 32, SITE_TYT = 4, SITE_K = 2, SITE_TY = SITE_TYT * SITE_K;
 
 template <int C, int R>
 struct SiteDims {
@@ -109,9 +109,12 @@ __global__ void __launch_bounds__(128) db_site_kernel(const float *__restrict__ 
         }
     }
     __syncthreads();
-    // sites (ty, tx) and (ty + 4, tx); sample (C ky - i, C kx - j) lives at
-    // footprint row C ty - i + R, column C tx + t with t = R - j.
-    float acc0 = 0.0f, acc1 = 0.0f;
+    // sites (ty + 4 k, tx), k < SITE_K; sample (C ky - i, C kx - j) lives at
+    // footprint row C ty - i + R, column C tx + t with t = R - j. Each tap's
+    // weight is one broadcast load shared by the thread's SITE_K sites.
+    float acc[SITE_K];
+#pragma unroll
+    for (int k = 0; k < SITE_K; ++k) acc[k] = 0.0f;
     const float *base = sp + (C * ty + R) * D::FXp + tx;
     constexpr int rstep = C * SITE_TYT * D::FXp;
 #pragma unroll
@@ -120,21 +123,20 @@ __global__ void __launch_bounds__(128) db_site_kernel(const float *__restrict__ 
         for (int t = 0; t <= 2 * R; ++t) {
             const float uv = su[(i + R) * D::n + (2 * R - t)];
             const float *bp = base + (t % C) * D::plane - i * D::FXp + t / C;
-            acc0 = fmaf(uv, bp[0], acc0);
-            acc1 = fmaf(uv, bp[rstep], acc1);
+#pragma unroll
+            for (int k = 0; k < SITE_K; ++k) acc[k] = fmaf(uv, bp[k * rstep], acc[k]);
         }
     }
     const int kx = kx0 + tx;
-    const int ky_a = ky0 + ty, ky_b = ky0 + ty + SITE_TYT;
     float vv = 0.0f;
     if (kx < w) {
-        if (ky_a < h) {
-            v[(size_t)b * h * w + (size_t)ky_a * w + kx] = acc0;
-            vv = acc0 * acc0;
-        }
-        if (ky_b < h) {
-            v[(size_t)b * h * w + (size_t)ky_b * w + kx] = acc1;
-            vv = fmaf(acc1, acc1, vv);
+#pragma unroll
+        for (int k = 0; k < SITE_K; ++k) {
+            const int ky = ky0 + ty + k * SITE_TYT;
+            if (ky < h) {
+                v[(size_t)b * h * w + (size_t)ky * w + kx] = acc[k];
+                vv = fmaf(acc[k], acc[k], vv);
+            }
         }
     }
     if (cg) {

@@ -63,6 +63,15 @@ __global__ void pack_w32_kernel(const float *__restrict__ w, __nv_bfloat16 *__re
     out[i] = __float2bfloat16_rn(v);
 }
 
+// Extra shared memory of the fused modes: first-layer parameters (608
+// floats), last-layer parameters (289 floats, padded) and the exchange of
+// the last layer's per-tap partial sums (128 pixels x 9).
+constexpr int kExtraW0 = 608 * 4;
+constexpr int kExtraW5 = 304 * 4;
+constexpr int kExtraX = kTileM * 9 * 4;
+constexpr int kConvSmemFused = kConvSmem + kExtraW0 + kExtraW5 + kExtraX;
+
+template <int MODE>
 __global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
     extern __shared__ __align__(1024) uint8_t csm[];
     uint8_t *wsm = csm;
@@ -70,12 +79,30 @@ __global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
     float *sbias = reinterpret_cast<float *>(ring + kRing * kRowB);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sbias + kCh);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    float *sw0 = reinterpret_cast<float *>(csm + kConvSmem);
+    float *sw5 = reinterpret_cast<float *>(csm + kConvSmem + kExtraW0);
+    float *sxc = reinterpret_cast<float *>(csm + kConvSmem + kExtraW0 + kExtraW5);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int H = a.H, W = a.W;
 
     for (int i = tid; i < kWBytes / 16; i += 128)
         reinterpret_cast<uint4 *>(wsm)[i] = __ldg(reinterpret_cast<const uint4 *>(a.wpack) + i);
     if (tid < kCh) sbias[tid] = a.bias ? a.bias[tid] : 0.0f;
+    // fused layers' weights transposed so that four output channels (first
+    // layer) or four input channels (last layer) are one 16-byte load:
+    // sw0[(t * 2 + i) * 32 + o] = w0[o][i][t], biases at 576;
+    // sw5[t * 32 + c] = w5[c][t], bias at 288
+    if (MODE == CONV_FIRST) {
+        for (int i = tid; i < 576; i += 128) {
+            const int o = i / 18, ci = (i / 9) % 2, t = i % 9;
+            sw0[(t * 2 + ci) * 32 + o] = a.w0[i];
+        }
+        if (tid < kCh) sw0[576 + tid] = a.w0[576 + tid];
+    }
+    if (MODE == CONV_LAST) {
+        for (int i = tid; i < 288; i += 128) sw5[(i % 9) * 32 + i / 9] = a.w5[i];
+        if (tid == 0) sw5[288] = a.w5[288];
+    }
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
         mbar_init(smem_u32(&mbar[1]), 1);
@@ -92,30 +119,130 @@ __global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
     uint32_t parity[2] = {0u, 0u};
     bool ok = true;
 
-    const int strips = (W + kTileM - 1) / kTileM;
+    // tiles of 128 pixels; the fused last layer keeps the 126 whose 3 x 3
+    // neighbourhood lies in the tile, so its tiles start one pixel early and
+    // advance by 126
+    constexpr int TS = (MODE == CONV_LAST) ? kTileM - 2 : kTileM;
+    const int strips = (W + TS - 1) / TS;
     const int chunks = (H + a.rpi - 1) / a.rpi;
     const int items = a.N * strips * chunks;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
         const int b = item / (strips * chunks);
         const int rem = item - b * strips * chunks;
         const int sx = rem / chunks, ch = rem - (rem / chunks) * chunks;
-        const int x0 = sx * kTileM, ya = ch * a.rpi, yb = min(H, ya + a.rpi);
-        const __nv_bfloat16 *inb = a.in + (size_t)b * H * W * kCh;
+        const int x0 = sx * TS - (MODE == CONV_LAST ? 1 : 0);
+        const int ya = ch * a.rpi, yb = min(H, ya + a.rpi);
+        // rows of this layer's output computed by the item
+        const int ys = ya - (MODE == CONV_LAST ? 1 : 0), ye = yb + (MODE == CONV_LAST ? 1 : 0);
+        const __nv_bfloat16 *inb = (MODE == CONV_FIRST) ? nullptr : a.in + (size_t)b * H * W * kCh;
+        float racc[3] = {0.f, 0.f, 0.f};  // last layer: output rows y - 1, y, y + 1
 
         auto load_row = [&](int yabs) {
             const int yy = wrapm(yabs, H);
             const uint32_t dst = ring_u32 + ring_slot(yabs) * kRowB;
-            const __nv_bfloat16 *src = inb + (size_t)yy * W * kCh;
-            for (int idx = tid; idx < kHalo * 4; idx += 128) {
-                const int p = idx >> 2, j = idx & 3;
-                const int x = wrapm(x0 - 1 + p, W);
-                cp_async16(dst + j * kPlane + p * 16, src + (size_t)x * kCh + j * 8);
+            if (MODE == CONV_FIRST) {
+                // the first layer (2 -> 32, CUDA cores) on the 130 pixels of the row
+                uint8_t *drow = ring + ring_slot(yabs) * kRowB;
+                const float *ub = a.up + (size_t)b * H * W;
+                const float *pb = a.pan + (size_t)b * a.pan_stride;
+                for (int px = tid; px < kHalo; px += 128) {
+                    const int x = wrapm(x0 - 1 + px, W);
+                    float in0[9], in1[9];
+#pragma unroll
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        const int ry = wrapm(yy + dy, H);
+#pragma unroll
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int rx = wrapm(x + dx, W);
+                            const size_t o = (size_t)ry * W + rx;
+                            in0[(dy + 1) * 3 + dx + 1] = __ldg(ub + o) * (1.0f / 255.0f);
+                            in1[(dy + 1) * 3 + dx + 1] = __ldg(pb + o) * (1.0f / 255.0f);
+                        }
+                    }
+                    float acc[kCh];
+#pragma unroll
+                    for (int o = 0; o < kCh; ++o) acc[o] = sw0[576 + o];
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) {
+#pragma unroll
+                        for (int ci = 0; ci < 2; ++ci) {
+                            const float xv = ci ? in1[t] : in0[t];
+                            const float4 *w4 = reinterpret_cast<const float4 *>(sw0 + (t * 2 + ci) * 32);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const float4 wv = w4[q];
+                                acc[4 * q] = fmaf(wv.x, xv, acc[4 * q]);
+                                acc[4 * q + 1] = fmaf(wv.y, xv, acc[4 * q + 1]);
+                                acc[4 * q + 2] = fmaf(wv.z, xv, acc[4 * q + 2]);
+                                acc[4 * q + 3] = fmaf(wv.w, xv, acc[4 * q + 3]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        uint4 pk;
+                        __nv_bfloat162 *ph = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            ph[e] = __floats2bfloat162_rn(fmaxf(acc[8 * j + 2 * e], 0.0f),
+                                                          fmaxf(acc[8 * j + 2 * e + 1], 0.0f));
+                        *reinterpret_cast<uint4 *>(drow + j * kPlane + px * 16) = pk;
+                    }
+                }
+            } else {
+                const __nv_bfloat16 *src = inb + (size_t)yy * W * kCh;
+                for (int idx = tid; idx < kHalo * 4; idx += 128) {
+                    const int p = idx >> 2, j = idx & 3;
+                    const int x = wrapm(x0 - 1 + p, W);
+                    cp_async16(dst + j * kPlane + p * 16, src + (size_t)x * kCh + j * 8);
+                }
             }
         };
         auto epilogue = [&](int y, int buf) {
             float v[32];
             tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * 32), v);
             const int x = x0 + tid;
+            if (MODE == CONV_LAST) {
+                // act5 = ReLU(conv + bias) at this pixel, then its 9 per-tap
+                // partial sums of the last layer, exchanged through shared
+                // memory: output (y - dy, x - dx) takes tap (dy, dx) of (y, x)
+#pragma unroll
+                for (int c = 0; c < kCh; ++c) v[c] = fmaxf(v[c] + sbias[c], 0.0f);
+#pragma unroll
+                for (int t = 0; t < 9; ++t) {
+                    const float4 *w4 = reinterpret_cast<const float4 *>(sw5 + t * 32);
+                    float s = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 wv = w4[q];
+                        s = fmaf(wv.x, v[4 * q], s);
+                        s = fmaf(wv.y, v[4 * q + 1], s);
+                        s = fmaf(wv.z, v[4 * q + 2], s);
+                        s = fmaf(wv.w, v[4 * q + 3], s);
+                    }
+                    sxc[t * kTileM + tid] = s;
+                }
+                __syncthreads();
+                if (tid >= 1 && tid <= kTileM - 2) {
+#pragma unroll
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        // tap (dy, dx) of pixel tid + dx feeds output row y - dy
+                        racc[0] += sxc[(2 * 3 + dx + 1) * kTileM + tid + dx];  // dy = +1
+                        racc[1] += sxc[(1 * 3 + dx + 1) * kTileM + tid + dx];  // dy = 0
+                        racc[2] += sxc[(0 * 3 + dx + 1) * kTileM + tid + dx];  // dy = -1
+                    }
+                    const int yo = y - 1;
+                    if (yo >= ya && yo < yb && x < W) {
+                        const size_t o = ((size_t)b * H + yo) * W + x;
+                        a.z[o] = __ldg(a.up + o) + 255.0f * (racc[0] + sw5[288]);
+                    }
+                }
+                racc[0] = racc[1];
+                racc[1] = racc[2];
+                racc[2] = 0.0f;
+                __syncthreads();
+                return;
+            }
             if (x >= W) return;
             const size_t o = (((size_t)b * H + y) * W + x) * kCh;
             if (a.mask) {
@@ -143,14 +270,14 @@ __global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
             for (int q = 0; q < 4; ++q) op[q] = pk[q];
         };
 
-        load_row(ya - 1);
-        load_row(ya);
-        load_row(ya + 1);
+        load_row(ys - 1);
+        load_row(ys);
+        load_row(ys + 1);
         cp_async_commit();
-        load_row(ya + 2);
+        load_row(ys + 2);
         cp_async_commit();
-        for (int y = ya; y < yb; ++y) {
-            const int buf = (y - ya) & 1;
+        for (int y = ys; y < ye; ++y) {
+            const int buf = (y - ys) & 1;
             cp_async_wait<1>();  // rows y - 1 .. y + 1 are in
             fence_async_smem();
             ok = __syncthreads_and(ok) != 0;
@@ -178,7 +305,7 @@ __global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
                 }
                 umma_commit(mb[buf]);
             }
-            if (y > ya) {
+            if (y > ys) {
                 // MMAs of row y - 1 done: its accumulator is readable and the
                 // ring slot of row y - 2 is free
                 const int pb = buf ^ 1;
@@ -190,13 +317,16 @@ __global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
                 parity[pb] ^= 1u;
                 tc_fence_after();
             }
+            // the fused last layer's epilogue holds CTA barriers: its
+            // condition must be uniform across the CTA
+            if (MODE == CONV_LAST) ok = __syncthreads_and(ok) != 0;
             load_row(y + 3);
             cp_async_commit();
-            if (y > ya && ok) epilogue(y - 1, buf ^ 1);
+            if (y > ys && ok) epilogue(y - 1, buf ^ 1);
             tc_fence_before();
         }
         if (ok) {
-            const int lb = (yb - 1 - ya) & 1;
+            const int lb = (ye - 1 - ys) & 1;
             if (!mbar_wait_bounded(mb[lb], parity[lb])) {
                 ok = false;
                 if (a.err) atomicExch(a.err, 1);
@@ -204,7 +334,8 @@ __global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
             ok = __all_sync(0xffffffffu, ok);
             parity[lb] ^= 1u;
             tc_fence_after();
-            if (ok) epilogue(yb - 1, lb);
+            if (MODE == CONV_LAST) ok = __syncthreads_and(ok) != 0;
+            if (ok) epilogue(ye - 1, lb);
             tc_fence_before();
         }
         cp_async_wait<0>();
@@ -219,7 +350,7 @@ __global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
 
 }  // namespace
 
-size_t conv32_smem_bytes() { return (size_t)kConvSmem; }
+size_t conv32_smem_bytes() { return (size_t)kConvSmemFused; }
 
 void launch_pack_w32(const float *w, void *out, int adjoint, cudaStream_t st) {
     pack_w32_kernel<<<(9 * kCh * kCh + 255) / 256, 256, 0, st>>>(
@@ -227,17 +358,29 @@ void launch_pack_w32(const float *w, void *out, int adjoint, cudaStream_t st) {
 }
 
 void launch_conv32(const Conv32Args &a, int num_sms, cudaStream_t st) {
-    const int strips = (a.W + kTileM - 1) / kTileM;
+    const int ts = a.mode == CONV_LAST ? kTileM - 2 : kTileM;
+    const int strips = (a.W + ts - 1) / ts;
     const int chunks = (a.H + a.rpi - 1) / a.rpi;
     const int items = a.N * strips * chunks;
     int grid = 3 * num_sms;
     if (grid > items) grid = items;
-    conv32_tc_kernel<<<grid, 128, kConvSmem, st>>>(a);
+    switch (a.mode) {
+        case CONV_FIRST: conv32_tc_kernel<CONV_FIRST><<<grid, 128, kConvSmemFused, st>>>(a); break;
+        case CONV_LAST: conv32_tc_kernel<CONV_LAST><<<grid, 128, kConvSmemFused, st>>>(a); break;
+        default: conv32_tc_kernel<CONV_PLAIN><<<grid, 128, kConvSmem, st>>>(a); break;
+    }
 }
 
 cudaError_t cnn_set_attrs() {
-    return cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kConvSmem);
+    cudaError_t e = cudaFuncSetAttribute(conv32_tc_kernel<CONV_PLAIN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(conv32_tc_kernel<CONV_FIRST>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmemFused);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(conv32_tc_kernel<CONV_LAST>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmemFused);
+    return e;
 }
 
 }  // namespace ps

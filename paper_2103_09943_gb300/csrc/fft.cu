@@ -159,6 +159,66 @@ void launch_kernel_embed(const float *u, int R, int H, int W, double2 *out, cuda
     kernel_embed_kernel<<<blocks, 256, 0, st>>>(u, R, H, W, out);
 }
 
+// Spectrum of the kernel embedded on the H x W torus, straight from its
+// (2R+1)^2 taps, layout [kx][ky] (FP64):
+//   B^(kx, ky) = sum_i exp(-2 pi i ky i / H) T_i(kx),
+//   T_i(kx) = sum_j u(i, j) exp(-2 pi i kx j / W),  i, j in [-R, R].
+// One CTA per 32 values of kx: the T_i of its columns in shared memory,
+// then one output per thread along ky (coalesced), twiddles from the FP64
+// tables tw[k] = exp(-2 pi i k / L).
+constexpr int kSpecCols = 32;
+__global__ void __launch_bounds__(256) kernel_spectrum_kernel(const float *__restrict__ u, int R,
+                                                              int H, int W,
+                                                              const double2 *__restrict__ twW,
+                                                              const double2 *__restrict__ twH,
+                                                              double2 *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char ksm[];
+    double2 *T = reinterpret_cast<double2 *>(ksm);  // [2R+1][kSpecCols]
+    const int n = 2 * R + 1;
+    const int kx0 = blockIdx.x * kSpecCols;
+    for (int e = threadIdx.x; e < n * kSpecCols; e += blockDim.x) {
+        const int ii = e / kSpecCols, c = e - ii * kSpecCols;
+        const int kx = kx0 + c;
+        double re = 0.0, im = 0.0;
+        if (kx < W) {
+            for (int jj = 0; jj < n; ++jj) {
+                const int j = jj - R;
+                int idx = (int)(((long long)kx * j) % W);
+                if (idx < 0) idx += W;
+                const double2 w = twW[idx];
+                const double uv = (double)u[ii * n + jj];
+                re = fma(uv, w.x, re);
+                im = fma(uv, w.y, im);
+            }
+        }
+        T[ii * kSpecCols + c] = make_double2(re, im);
+    }
+    __syncthreads();
+    const int cols = min(kSpecCols, W - kx0);
+    for (int e = threadIdx.x; e < cols * H; e += blockDim.x) {
+        const int c = e / H, ky = e - (e / H) * H;
+        double re = 0.0, im = 0.0;
+        for (int ii = 0; ii < n; ++ii) {
+            const int i = ii - R;
+            int idx = (int)(((long long)ky * i) % H);
+            if (idx < 0) idx += H;
+            const double2 w = twH[idx];
+            const double2 t = T[ii * kSpecCols + c];
+            re = fma(t.x, w.x, fma(-t.y, w.y, re));
+            im = fma(t.x, w.y, fma(t.y, w.x, im));
+        }
+        out[(size_t)(kx0 + c) * H + ky] = make_double2(re, im);
+    }
+}
+
+void launch_kernel_spectrum(const float *u, int R, int H, int W, const double2 *twW,
+                            const double2 *twH, double2 *out, cudaStream_t st) {
+    const int n = 2 * R + 1;
+    const size_t smem = (size_t)n * kSpecCols * sizeof(double2);
+    kernel_spectrum_kernel<<<(W + kSpecCols - 1) / kSpecCols, 256, smem, st>>>(u, R, H, W, twW,
+                                                                                twH, out);
+}
+
 // Per alias group (ky0 + p h, kx0 + q w), p, q in [0, c): solve
 //   ((1/c^2) v v^H + diag(t)) x = r,  v_j = conj(B^_j), t_j = lam S^_j^2.
 // With s = v^H x:  x_j = (r_j - v_j s / c^2) / t_j, and s from

@@ -75,6 +75,8 @@ void launch_transpose32(const float2 *in, float2 *out, int rows, int cols, int b
 void launch_transpose64(const double2 *in, double2 *out, int rows, int cols, int batch,
                         cudaStream_t st);
 void launch_kernel_embed(const float *u, int R, int H, int W, double2 *out, cudaStream_t st);
+void launch_kernel_spectrum(const float *u, int R, int H, int W, const double2 *twW,
+                            const double2 *twH, double2 *out, cudaStream_t st);
 void launch_alias_solve(const double2 *spec, const double2 *bspec, float2 *sol, int nimg, int H,
                         int W, int c, float lam, cudaStream_t st);
 cudaError_t fft_set_attrs();
@@ -98,9 +100,10 @@ void launch_spectrum_to_f32(const double2 *in, float2 *out, size_t n, cudaStream
 cudaError_t precond_set_attrs();
 
 // cnn.cu: 3 x 3 convolutions with 32 in / 32 out channels on tcgen05
+enum { CONV_PLAIN = 0, CONV_FIRST = 1, CONV_LAST = 2 };
 struct Conv32Args {
-    const __nv_bfloat16 *in;    // N x H x W x 32, NHWC
-    __nv_bfloat16 *out;         // N x H x W x 32
+    const __nv_bfloat16 *in;    // N x H x W x 32, NHWC (CONV_PLAIN, CONV_LAST)
+    __nv_bfloat16 *out;         // N x H x W x 32 (CONV_PLAIN, CONV_FIRST)
     const void *wpack;          // B operand from launch_pack_w32 (18432 bytes)
     const float *bias;          // 32, or NULL
     const __nv_bfloat16 *mask;  // NULL, or out = conv * (mask > 0) (before the bias)
@@ -108,6 +111,15 @@ struct Conv32Args {
     int relu;                   // bias then ReLU
     int rpi;                    // output rows per work item
     int *err;                   // set to 1 when a bounded wait gives up
+    int mode;                   // CONV_*
+    // CONV_FIRST: the input rows are the network's first layer evaluated on
+    // (up / 255, pan / 255) with w0 (32 x 2 x 9 weights, then 32 biases)
+    // CONV_LAST: the output is z = up + 255 (conv5(ReLU(conv + bias)) + b5)
+    // with w5 (32 x 9 weights, then the bias); z is N x H x W FP32
+    const float *up, *pan;
+    size_t pan_stride;
+    const float *w0, *w5;
+    float *z;
 };
 size_t conv32_smem_bytes();
 void launch_pack_w32(const float *w, void *out, int adjoint, cudaStream_t st);
@@ -130,6 +142,9 @@ void launch_cnn_wgrad_first(const float *up, const float *pan, size_t pan_stride
                             cudaStream_t st);
 void launch_cnn_adam(float *p, const float *g, float *m, float *v, int n, int step, float lr,
                      float b1, float b2, float eps, cudaStream_t st);
+
+// llp2.cu: q = lam L M L p and p^T q inside the CG loop, two pixels per lane
+void launch_llp_cgq2(const LlpArgs &a, int r, int N, cudaStream_t st);
 
 // warm.cu
 void launch_bicubic_up(const float *X, int N, int h, int w, int c, float *out,

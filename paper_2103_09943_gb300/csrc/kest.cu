@@ -413,13 +413,14 @@ void launch_cholesky(double *A, int n, float mu3, cudaStream_t st) {
 // the unknowns above from the tile's rows of L (coalesced).
 __device__ void chol_two_solves(const double *L, int nt, double *y, double *Dt) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    constexpr unsigned FULLM = 0xffffffffu;
     for (int t0 = 0; t0 < nt; t0 += CB) {
         const int kb = min(CB, nt - t0);
         for (int r = warp; r < kb; r += nwarp) {
             const double *row = L + (size_t)(t0 + r) * nt;
             double acc = 0.0;
             for (int k = lane; k < t0; k += 32) acc += row[k] * y[k];
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULLM, acc, o);
             if (lane == 0) y[t0 + r] -= acc;
         }
         for (int q = tid; q < kb * kb; q += blockDim.x) {
@@ -428,13 +429,16 @@ __device__ void chol_two_solves(const double *L, int nt, double *y, double *Dt) 
         }
         __syncthreads();
         if (warp == 0) {
+            // column-oriented: lane k holds y_k; x_r = y_r / L_rr, then every
+            // later row subtracts its L[k][r] x_r
+            const double rinv = lane < kb ? 1.0 / Dt[lane * CB + lane] : 0.0;
+            double yk = lane < kb ? y[t0 + lane] : 0.0;
             for (int r = 0; r < kb; ++r) {
-                double acc = 0.0;
-                if (lane < r) acc = Dt[r * CB + lane] * y[t0 + lane];
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) y[t0 + r] = (y[t0 + r] - acc) / Dt[r * CB + r];
-                __syncwarp();
+                const double xr = __shfl_sync(FULLM, yk * rinv, r);
+                if (lane == r) yk = xr;
+                else if (lane > r && lane < kb) yk = fma(-Dt[lane * CB + r], xr, yk);
             }
+            if (lane < kb) y[t0 + lane] = yk;
         }
         __syncthreads();
     }
@@ -447,14 +451,16 @@ __device__ void chol_two_solves(const double *L, int nt, double *y, double *Dt) 
         }
         __syncthreads();
         if (warp == 0) {
+            // L^T x = y on the tile, from its last row up: x_r = y_r / L_rr,
+            // then rows k < r subtract L[r][k] x_r
+            const double rinv = lane < kb ? 1.0 / Dt[lane * CB + lane] : 0.0;
+            double yk = lane < kb ? y[t0 + lane] : 0.0;
             for (int r = kb - 1; r >= 0; --r) {
-                // x_r = (y_r - sum_{k>r in tile} L[k][r] x_k) / L[r][r]
-                double acc = 0.0;
-                if (lane > r && lane < kb) acc = Dt[lane * CB + r] * y[t0 + lane];
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) y[t0 + r] = (y[t0 + r] - acc) / Dt[r * CB + r];
-                __syncwarp();
+                const double xr = __shfl_sync(FULLM, yk * rinv, r);
+                if (lane == r) yk = xr;
+                else if (lane < r) yk = fma(-Dt[r * CB + lane], xr, yk);
             }
+            if (lane < kb) y[t0 + lane] = yk;
         }
         __syncthreads();
         for (int i = tid; i < t0; i += blockDim.x) {
@@ -653,6 +659,13 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
           *t0 = wv + ntp, *t1 = t0 + ntp, *t2 = t1 + ntp, *t3 = t2 + ntp, *t4 = t3 + ntp,
           *b3s = t4 + ntp;
     int *flag = reinterpret_cast<int *>(b3s + ntp);
+    // split of the O(nt^2) phases: `parts` groups of threads per entry, their
+    // partial results in the DFT scratch T0..T2 (free at that point: 6 ntp
+    // floats), ranks after them
+    const int parts = max(1, min(3, nthr / nt));
+    const int chunk = (nt + parts - 1) / parts;
+    float *pbuf = reinterpret_cast<float *>(T0);
+    int *pcnt = reinterpret_cast<int *>(T0) + 3 * ntp;
 
     const float a1 = p.alpha1 * p.mu1, a2 = p.alpha2 * p.mu2;
     for (int k = tid; k < nt; k += nthr) {
@@ -700,10 +713,27 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
             wv[k] = u[k] + l3[k];
         }
         __syncthreads();
-        // 3. z = P_S(z_f + Q (u + Lambda3)) (Eq. z_solution, then projection)
+        // 3. z = P_S(z_f + Q (u + Lambda3)) (Eq. z_solution, then projection).
+        // The matvec's inner index is split over `parts` thread groups (the
+        // CTA has several threads per entry), partial sums in the DFT scratch.
+        for (int job = tid; job < parts * nt; job += nthr) {
+            const int part = job / nt, k = job - (job / nt) * nt;
+            const int m0 = part * chunk, m1 = min(nt, m0 + chunk);
+            float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+            int m = m0;
+            for (; m + 3 < m1; m += 4) {
+                c0 = fmaf(__ldg(Q + (size_t)m * nt + k), wv[m], c0);
+                c1 = fmaf(__ldg(Q + (size_t)(m + 1) * nt + k), wv[m + 1], c1);
+                c2 = fmaf(__ldg(Q + (size_t)(m + 2) * nt + k), wv[m + 2], c2);
+                c3 = fmaf(__ldg(Q + (size_t)(m + 3) * nt + k), wv[m + 3], c3);
+            }
+            for (; m < m1; ++m) c0 = fmaf(__ldg(Q + (size_t)m * nt + k), wv[m], c0);
+            pbuf[part * nt + k] = (c0 + c1) + (c2 + c3);
+        }
+        __syncthreads();
         for (int k = tid; k < nt; k += nthr) {
             float acc = zs[k];
-            for (int m = 0; m < nt; ++m) acc = fmaf(__ldg(Q + (size_t)m * nt + k), wv[m], acc);
+            for (int q = 0; q < parts; ++q) acc += pbuf[q * nt + k];
             t0[k] = acc;
         }
         __syncthreads();
@@ -712,18 +742,33 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
         // sum of the entries up to it give the largest position rho with
         // v_rho + (1 - S_rho)/rho > 0 and tau = (1 - S_rho)/rho, without a sort.
         {
+            // ranks and sums over the entries ahead, split like the matvec
+            for (int job = tid; job < parts * nt; job += nthr) {
+                const int part = job / nt, k = job - (job / nt) * nt;
+                const int m0 = part * chunk, m1 = min(nt, m0 + chunk);
+                const float wk = t0[k];
+                int rk = 0;
+                float sk = 0.f;
+                for (int m = m0; m < m1; ++m) {
+                    const float wm = t0[m];
+                    if (wm > wk || (wm == wk && m < k)) {
+                        ++rk;
+                        sk += wm;
+                    }
+                }
+                pbuf[part * nt + k] = sk;
+                pcnt[part * nt + k] = rk;
+            }
+            __syncthreads();
             int best = 0;
             float btau = 0.f;
             for (int k = tid; k < nt; k += nthr) {
                 const float wk = t0[k];
                 int rk = 1;
                 float sk = wk;
-                for (int m = 0; m < nt; ++m) {
-                    const float wm = t0[m];
-                    if (wm > wk || (wm == wk && m < k)) {
-                        ++rk;
-                        sk += wm;
-                    }
+                for (int q = 0; q < parts; ++q) {
+                    rk += pcnt[q * nt + k];
+                    sk += pbuf[q * nt + k];
                 }
                 const float tk = (1.0f - sk) / (float)rk;
                 if (wk + tk > 0.0f && rk > best) {

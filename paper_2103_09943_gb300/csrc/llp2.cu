@@ -1,0 +1,282 @@
+// The prior part of the Z0 operator inside the CG loop, q = lam L M L p with
+// p^T q per band (Eq. Z_ini_matting, matrix-free M of Eq. matting_matrix),
+// two pixels per lane (sm_103a).
+//
+// Same register-streaming scheme as the general LLP kernel (a warp walks
+// down a strip of columns keeping every stage of the chain -- Laplacian,
+// window sums, affine fit, window sums, Laplacian -- as short rolling
+// buffers of rows), but lane l owns the two adjacent columns 2l and 2l + 1
+// of a 64-column strip. A horizontal neighbour at offset d of column 2l + e
+// lives in lane l + floor((e + d) / 2): the shuffles per row stay those of
+// one pixel per lane while each warp row yields 64 - 2G outputs instead of
+// 32 - 2G, and the loads become one float2 of p and two float4 of
+// statistics per lane.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ps {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = 4;
+
+__device__ __forceinline__ int wrap2(int i, int n) {
+    int m = i % n;
+    return m < 0 ? m + n : m;
+}
+
+// Value at column 2 lane + E + D of the pair (v0, v1) held at columns
+// 2 lane, 2 lane + 1.
+template <int E, int D>
+__device__ __forceinline__ float nbr(float v0, float v1) {
+    constexpr int c = E + D;
+    constexpr int o = (c >= 0) ? c / 2 : -((1 - c) / 2);  // floor(c / 2)
+    constexpr int el = c - 2 * o;
+    const float src = el ? v1 : v0;
+    if (o == 0) return src;
+    if (o < 0) return __shfl_up_sync(kFull, src, -o);
+    return __shfl_down_sync(kFull, src, o);
+}
+
+// Horizontal window sum over [-RW, RW] at both columns of the pair.
+template <int RW, int E, int D = -RW>
+__device__ __forceinline__ float hsum(float v0, float v1) {
+    if constexpr (D > RW) {
+        return 0.0f;
+    } else {
+        return nbr<E, D>(v0, v1) + hsum<RW, E, D + 1>(v0, v1);
+    }
+}
+
+template <int RW>
+struct Llp2Rows {
+    static constexpr int TY = (RW == 1) ? 66 : 64;
+    static constexpr int UNR = (RW == 1) ? 3 : 1;
+};
+
+template <int RW>
+__global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
+    constexpr int G = 2 * RW + 2;
+    constexpr int VALID = 64 - 2 * G;
+    constexpr int NB = 2 * RW + 1;
+    constexpr int TY = Llp2Rows<RW>::TY;
+    constexpr float nw = (float)(NB * NB);
+    constexpr float inw = 1.0f / nw;
+    __shared__ double red[kWarps];
+    const int b = blockIdx.z;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (a.g->stop || a.bands[b].done) return;
+    const int H = a.H, W = a.W;
+    const int HWi = H * W;
+    const size_t HW = (size_t)HWi;
+    const int x0 = blockIdx.x * VALID;
+    const int y0 = (blockIdx.y * kWarps + warp) * TY;
+    const int xl = x0 - G + 2 * lane;  // even; W is even, so xl + 1 wraps with xl
+    const int gx = wrap2(xl, W);
+    const bool out_lane = lane >= G / 2 && lane < 32 - G / 2 && xl < W;
+    const float *in = a.in + (size_t)b * HW;
+    const float4 *st4 = a.st4;
+    float part = 0.0f;
+
+    if (y0 < H) {
+        int rowIn = wrap2(y0 - G, H) * W;
+        int rowA = wrap2(y0 - G - 1, H) * W;
+        int rowD = wrap2(y0, H) * W;
+        float pm2[2] = {0.f, 0.f}, pm1[2] = {0.f, 0.f}, p0[2] = {0.f, 0.f};
+        float hA[2][NB], hIA[2][NB], ab[2][NB], ib[2][NB], ha[2][NB], hb[2][NB];
+        float mub[2][RW + 1], sb[2][RW + 1];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+#pragma unroll
+            for (int d = 0; d < NB; ++d) hA[e][d] = hIA[e][d] = ab[e][d] = ib[e][d] = ha[e][d] = hb[e][d] = 0.f;
+#pragma unroll
+            for (int d = 0; d <= RW; ++d) mub[e][d] = sb[e][d] = 0.f;
+        }
+        float mm2[2] = {0.f, 0.f}, mm1[2] = {0.f, 0.f}, m0[2] = {0.f, 0.f};
+        constexpr int PF = 2;
+        float2 qp[PF];
+        float4 qs0[PF], qs1[PF];
+        constexpr int PH = ((G + 1 + 2) / 3) * 3;
+        float2 ph[PH];
+#pragma unroll
+        for (int d = 0; d < PH; ++d) ph[d] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            qp[k] = *reinterpret_cast<const float2 *>(in + rowIn + gx);
+            qs0[k] = st4[rowA + gx];
+            qs1[k] = st4[rowA + gx + 1];
+            rowIn += W;
+            if (rowIn == HWi) rowIn = 0;
+            rowA += W;
+            if (rowA == HWi) rowA = 0;
+        }
+
+        auto advance = [&]() -> float2 {
+            const float2 pin = qp[0];
+            const float4 s0 = qs0[0], s1 = qs1[0];
+#pragma unroll
+            for (int k = 0; k < PF - 1; ++k) {
+                qp[k] = qp[k + 1];
+                qs0[k] = qs0[k + 1];
+                qs1[k] = qs1[k + 1];
+            }
+            qp[PF - 1] = *reinterpret_cast<const float2 *>(in + rowIn + gx);
+            qs0[PF - 1] = st4[rowA + gx];
+            qs1[PF - 1] = st4[rowA + gx + 1];
+            rowIn += W;
+            if (rowIn == HWi) rowIn = 0;
+            rowA += W;
+            if (rowA == HWi) rowA = 0;
+#pragma unroll
+            for (int d = 0; d < PH - 1; ++d) ph[d] = ph[d + 1];
+            ph[PH - 1] = pin;
+            // alpha = L p on the row behind the input row
+            pm2[0] = pm1[0]; pm1[0] = p0[0]; p0[0] = pin.x;
+            pm2[1] = pm1[1]; pm1[1] = p0[1]; p0[1] = pin.y;
+            const float l0 = nbr<0, -1>(pm1[0], pm1[1]), r0 = pm1[1];
+            const float l1 = pm1[0], r1 = nbr<1, 1>(pm1[0], pm1[1]);
+            float al[2], iv[2], ia[2];
+            al[0] = 4.0f * pm1[0] - pm2[0] - p0[0] - l0 - r0;
+            al[1] = 4.0f * pm1[1] - pm2[1] - p0[1] - l1 - r1;
+            iv[0] = s0.x;
+            iv[1] = s1.x;
+            ia[0] = iv[0] * al[0];
+            ia[1] = iv[1] * al[1];
+            const float h10 = hsum<RW, 0>(al[0], al[1]), h11 = hsum<RW, 1>(al[0], al[1]);
+            const float h20 = hsum<RW, 0>(ia[0], ia[1]), h21 = hsum<RW, 1>(ia[0], ia[1]);
+            const float h1[2] = {h10, h11}, h2[2] = {h20, h21};
+            const float mu_in[2] = {s0.y, s1.y}, s_in[2] = {s0.z, s1.z};
+            float av[2], bv[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+#pragma unroll
+                for (int d = 0; d < NB - 1; ++d) {
+                    hA[e][d] = hA[e][d + 1];
+                    hIA[e][d] = hIA[e][d + 1];
+                    ab[e][d] = ab[e][d + 1];
+                    ib[e][d] = ib[e][d + 1];
+                }
+                hA[e][NB - 1] = h1[e];
+                hIA[e][NB - 1] = h2[e];
+                ab[e][NB - 1] = al[e];
+                ib[e][NB - 1] = iv[e];
+#pragma unroll
+                for (int d = 0; d < RW; ++d) {
+                    mub[e][d] = mub[e][d + 1];
+                    sb[e][d] = sb[e][d + 1];
+                }
+                mub[e][RW] = mu_in[e];
+                sb[e][RW] = s_in[e];
+                float v1 = 0.f, v2 = 0.f;
+#pragma unroll
+                for (int d = 0; d < NB; ++d) {
+                    v1 += hA[e][d];
+                    v2 += hIA[e][d];
+                }
+                const float mu = mub[e][0], sv = sb[e][0];
+                const float ma = v1 * inw, mia = v2 * inw;
+                av[e] = (mia - mu * ma) * sv;
+                bv[e] = ma - av[e] * mu;
+            }
+            const float g10 = hsum<RW, 0>(av[0], av[1]), g11 = hsum<RW, 1>(av[0], av[1]);
+            const float g20 = hsum<RW, 0>(bv[0], bv[1]), g21 = hsum<RW, 1>(bv[0], bv[1]);
+            const float g1[2] = {g10, g11}, g2[2] = {g20, g21};
+            float mv[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+#pragma unroll
+                for (int d = 0; d < NB - 1; ++d) {
+                    ha[e][d] = ha[e][d + 1];
+                    hb[e][d] = hb[e][d + 1];
+                }
+                ha[e][NB - 1] = g1[e];
+                hb[e][NB - 1] = g2[e];
+                float sa = 0.f, sbb = 0.f;
+#pragma unroll
+                for (int d = 0; d < NB; ++d) {
+                    sa += ha[e][d];
+                    sbb += hb[e][d];
+                }
+                // M alpha = |w| alpha - Sa I - Sb on the row of ab[0], ib[0]
+                mv[e] = nw * ab[e][0] - sa * ib[e][0] - sbb;
+                mm2[e] = mm1[e];
+                mm1[e] = m0[e];
+                m0[e] = mv[e];
+            }
+            const float ql0 = nbr<0, -1>(mm1[0], mm1[1]), qr0 = mm1[1];
+            const float ql1 = mm1[0], qr1 = nbr<1, 1>(mm1[0], mm1[1]);
+            return make_float2(4.0f * mm1[0] - mm2[0] - m0[0] - ql0 - qr0,
+                               4.0f * mm1[1] - mm2[1] - m0[1] - ql1 - qr1);
+        };
+
+        for (int step = 0; step < 2 * G; ++step) (void)advance();
+        float2 *outb = reinterpret_cast<float2 *>(a.out + (size_t)b * HW);
+#pragma unroll Llp2Rows<RW>::UNR
+        for (int yy = 0; yy < TY; ++yy) {
+            float2 val = advance();
+            if (out_lane && y0 + yy < H) {
+                val.x *= a.lam;
+                val.y *= a.lam;
+                outb[(rowD + gx) >> 1] = val;
+                // the output row is the input row of G steps ago
+                const float2 pv = ph[PH - 1 - G];
+                part = fmaf(pv.x, val.x, fmaf(pv.y, val.y, part));
+            }
+            rowD += W;
+            if (rowD == HWi) rowD = 0;
+        }
+    }
+    double pd = (double)part;
+    for (int o = 16; o > 0; o >>= 1) pd += __shfl_xor_sync(kFull, pd, o);
+    if (lane == 0) red[warp] = pd;
+    __syncthreads();
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < kWarps; ++k) tot += red[k];
+        CgBand *bd = a.bands + b;
+        atomicAdd(&bd->pAp, tot);
+        __threadfence();
+        const unsigned int nblk = gridDim.x * gridDim.y;
+        const unsigned int t = atomicAdd(&bd->cnt_apply, 1u);
+        if (t == nblk - 1) {
+            __threadfence();
+            // p^T A p = ||D B p||^2 + p^T (lam L^T M L) p
+            const double pAp = atomicAdd(&bd->pAp, 0.0) + bd->vv;
+            const double rho = bd->rho;
+            bd->cnt_apply = 0u;
+            if (!isfinite(pAp)) {
+                bd->status = PS_ERR_NONFINITE;
+                bd->done = 1;
+                bd->alpha = 0.0;
+            } else if (!(pAp > 0.0)) {
+                bd->status = PS_ERR_BREAKDOWN;
+                bd->done = 1;
+                bd->alpha = 0.0;
+            } else {
+                bd->alpha = rho / pAp;
+            }
+        }
+    }
+}
+
+template <int RW>
+void launch_r(const LlpArgs &a, int N, cudaStream_t st) {
+    constexpr int G = 2 * RW + 2, VALID = 64 - 2 * G;
+    const int rows = Llp2Rows<RW>::TY * kWarps;
+    dim3 grd((a.W + VALID - 1) / VALID, (a.H + rows - 1) / rows, N);
+    llp_cgq2_kernel<RW><<<grd, 32 * kWarps, 0, st>>>(a);
+}
+
+}  // namespace
+
+void launch_llp_cgq2(const LlpArgs &a, int r, int N, cudaStream_t st) {
+    switch (r) {
+        case 1: launch_r<1>(a, N, st); break;
+        case 2: launch_r<2>(a, N, st); break;
+        case 3: launch_r<3>(a, N, st); break;
+        default: launch_r<4>(a, N, st); break;
+    }
+}
+
+}  // namespace ps

@@ -133,3 +133,24 @@ def test_adam_steps_lower_the_loss(cuda):
         net.loss_grad(up, pan, target)
         net.adam(lr=2e-3)
     assert net.loss_grad(up, pan, target) < 0.5 * first
+
+
+@pytest.mark.parametrize("B,H,W,shared_pan", [(1, 70, 300, True), (2, 33, 132, False)])
+def test_fused_forward_matches_oracle(cuda, B, H, W, shared_pan):
+    # several 126-pixel strips (the last one partial) and row chunks: the
+    # first layer computed inside the first tensor-core layer, the last one
+    # in the epilogue of the fourth
+    from paper_2103_09943_gb300.cnn import WarmStartNet, init_params, split_params
+    rng = np.random.default_rng(B + H + W)
+    p = init_params(9)
+    parts = split_params(p)
+    parts[-1][0][...] *= 10.0
+    up = (rng.random((B, H, W)) * 255).astype(np.float32)
+    pan = (rng.random((H, W) if shared_pan else (B, H, W)) * 255).astype(np.float32)
+    net = WarmStartNet(params=p, device=cuda)
+    z = net.forward(torch.from_numpy(up).to(cuda), torch.from_numpy(pan).to(cuda),
+                    check=True).double().cpu().numpy()
+    pans = np.broadcast_to(pan, (B, H, W)) if shared_pan else pan
+    for bf16, tol in ((False, 5e-2), (True, 1e-2)):
+        zr, _, _ = _oracle_batch(p, up, pans, up, bf16)
+        assert np.linalg.norm((z - up) - (zr - up)) <= tol * np.linalg.norm(zr - up), bf16
