@@ -219,6 +219,7 @@ def cg_iteration_roofline(api, X, Y, kern, cfg, hp, peak_gbs, dev):
 
     def timed(iters, reps=3):
         p = HrmsParams.from_buffer_copy(hp)
+        p.warm = 0  # a fixed iteration count: the start point does not matter
         p.tol = 1e-30
         p.max_iter = iters
         api.solve_hrms(X, Y, kern, cfg.ratio, p, ws=ws, info=False, out=out)
@@ -259,17 +260,19 @@ def launches_per_step(cfg, hp, cg_iters) -> int:
     """Kernels of this library launched by one ps_pansharpen call.
     Kernel estimate: 4 (omega) + 4 (E^T E, E^T f) + Cholesky (1 + per 32-column
     panel: diagonal, and below it panel and trailing update) + 3 (solve,
-    inverse, ADMM). HRMS solve: PAN statistics, 7 for the kernel spectrum,
+    inverse, ADMM). HRMS solve: PAN statistics, 3 for the kernel spectrum,
     right-hand side, reset, init (+3 for z0 = P^{-1} r0), then the loop body of
     two iterations (4 or 7 kernels each) per two iterations, then 8 for the
-    Z step."""
+    Z step; plus the warm start's kernels."""
     nt = cfg.n * cfg.n
     panels = (nt + 31) // 32
     kest = 4 + 4 + (1 + panels + 2 * (panels - 1)) + 3
     per_iter = 7 if hp.precond else 4
     body_runs = max(1, math.ceil(max(cg_iters) / 2))
-    solve = 1 + 7 + 1 + 2 + (3 if hp.precond else 0) + 2 * per_iter * body_runs + 8
-    return kest + solve
+    solve = 1 + 3 + 1 + 2 + (3 if hp.precond else 0) + 2 * per_iter * body_runs + 8
+    # warm start: bicubic, (network: 4 weight packs + 4 convolutions), A z_init (2)
+    warm = {0: 0, 1: 1 + 2, 2: 1 + 8 + 2}[hp.warm]
+    return kest + solve + warm
 
 
 def read_peaks():
@@ -307,6 +310,75 @@ def run_profile_solve(args):
     return 0
 
 
+WARM_WEIGHTS = os.path.join(ROOT, "paper_2103_09943_gb300", "weights", "warm_cnn.npz")
+
+
+def load_warm_net(which, dev):
+    """The trained warm-start network when it is asked for and its weights
+    are present; else (None, reason)."""
+    if which != "cnn":
+        return None, which
+    if not os.path.exists(WARM_WEIGHTS):
+        return None, "cnn weights missing: cold start"
+    from paper_2103_09943_gb300.cnn import WarmStartNet
+    return WarmStartNet.load(WARM_WEIGHTS, device=dev), "cnn (" + os.path.relpath(
+        WARM_WEIGHTS, ROOT) + ")"
+
+
+def compare_variants(api, X, Y, cfg, kp, net, dev, steps=3):
+    """Whole-step time (CUDA events) of the same scene under three forms of
+    the solve: plain FP32 CG from zeros (the paper's solver, cold start), the
+    preconditioned CG from zeros, and the preconditioned CG from the network's
+    warm start. Every form stops at the same relative residual."""
+    import torch
+    out = {}
+    forms = [("plain_cg_cold", dict(precond=0, warm=0)), ("pcg_cold", dict(precond=1, warm=0))]
+    if net is not None:
+        forms.append(("pcg_cnn_warm", dict(precond=1, warm=2, cnn_params=net.params.data_ptr())))
+    for name, kw in forms:
+        hp = api.default_hrms_params(**kw)
+        ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev, hp)
+        _, _, _, bi = api.pansharpen(X, Y, cfg.ratio, cfg.R, kp, hp, ws=ws)
+        ts = []
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            api.pansharpen(X, Y, cfg.ratio, cfg.R, kp, hp, ws=ws, info=False)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        out[name] = {"ms_per_step": ms,
+                     "value": cfg.bands * cfg.H * cfg.W / 1e6 / (ms * 1e-3),
+                     "cg_iters_mean": float(np.mean(bi.iters))}
+    return out
+
+
+def run_profile_warm(args):
+    """The warm-start network's inference on the workload's 8 bands (trained
+    weights when present, else the seeded initial ones), three times."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2103_09943_gb300 import ops
+    from paper_2103_09943_gb300.cnn import WarmStartNet
+    cfg = workload_config(args.r)
+    scene = synth.make_scene(cfg)
+    X = torch.from_numpy(scene["lrms"]).to(dev)
+    Y = torch.from_numpy(scene["pan"]).to(dev)
+    net = WarmStartNet.load(WARM_WEIGHTS, device=dev) if os.path.exists(WARM_WEIGHTS) \
+        else WarmStartNet(device=dev)
+    up = ops.bicubic_up(X, cfg.ratio)
+    for _ in range(3):
+        net.forward(up, Y, check=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_warm": 3, "workload": workload_name(cfg)}))
+    return 0
+
+
 def run_gpu(args):
     import torch
     rank, local_rank, world = dist_env()
@@ -323,9 +395,15 @@ def run_gpu(args):
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
     kp = api.default_kernel_params()
+    net, warm_note = load_warm_net(args.warm, dev)
+    warm = {"none": 0, "bicubic": 1, "cnn": 2}[args.warm] if (net or args.warm != "cnn") else 0
     hp = api.default_hrms_params(host_loop=1 if args.cg_loop == "host" else 0,
-                                 precond=1 if args.precond == "fft" else 0)
-    ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev)
+                                 precond=1 if args.precond == "fft" else 0, warm=warm,
+                                 cnn_params=net.params.data_ptr() if net else None)
+    ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev, hp)
+    # launch shapes of the tunable kernels, picked on this GPU before timing
+    tuning = api.autotune(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, hp.r, ws=ws) \
+        if hp.precond else None
     Z = torch.empty((cfg.bands, cfg.H, cfg.W), dtype=torch.float32, device=dev)
     K = torch.empty((cfg.n, cfg.n), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -405,6 +483,10 @@ def run_gpu(args):
         acc = {"cg_tol": hp.tol, "z0_true_rel_residual_fp64": res,
                "parity": "tests/test_gpu_*.py: per-band rel-L2 vs the FP64 oracle"}
 
+    variants = None
+    if rank == 0 and not args.no_compare:
+        variants = compare_variants(api, X, Y, cfg, kp, net, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scene, args.cpu_crop)
@@ -421,6 +503,8 @@ def run_gpu(args):
                        "cg_tol": hp.tol, "cg_iters": binfo.iters, "cg_loop": args.cg_loop,
                        "cg_precond": ("FFT alias-group, gamma %g" % hp.precond_gamma)
                        if hp.precond else "none",
+                       "warm_start": warm_note,
+                       "autotuned": tuning,
                        "admm_iters": kinfo.iters},
             "wall_s_timed_region": wall,
             "e2e": {"value": throughput(units, world, e2e_ms * 1e-3), "unit": UNIT,
@@ -431,6 +515,7 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "accuracy": acc,
             "clocks": clk,
+            "variants": variants,
         }
         print(json.dumps(rec), flush=True)
     if world > 1:
@@ -452,6 +537,14 @@ def parse(argv=None):
     ap.add_argument("--profile-solve", type=int, default=0, metavar="ITERS",
                     help="no timing: run one HRMS solve of the workload with the CG loop "
                          "launched from the host, ITERS iterations (for profiler captures)")
+    ap.add_argument("--profile-warm", action="store_true",
+                    help="no timing: run the warm-start network on the workload's bicubic "
+                         "upsampling and PAN three times (for profiler captures)")
+    ap.add_argument("--warm", default="cnn", choices=["cnn", "bicubic", "none"],
+                    help="start point of the Z0 solve (cnn: the trained network when its "
+                         "weights are present, else zeros)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the timing of the plain-CG / PCG / warm-start forms")
     ap.add_argument("--precond", default="fft", choices=["fft", "none"],
                     help="preconditioner of the Z0 CG (fft: alias-group FFT solve; none: "
                          "plain CG as in the paper)")
@@ -467,6 +560,8 @@ def main(argv=None):
         return run_reference(args)
     if args.profile_solve:
         return run_profile_solve(args)
+    if args.profile_warm:
+        return run_profile_warm(args)
     return run_gpu(args)
 
 

@@ -120,6 +120,24 @@ void ps_default_kernel_params(ps_kernel_params *h_params);
 void ps_default_hrms_params(ps_hrms_params *h_params);
 const char *ps_status_string(int status);
 
+/* Launch choices of the tunable kernels of ps_solve_hrms for one size, and
+ * the times (microseconds, one launch on the workload's sizes) that picked
+ * them; 0 marks a candidate that was not valid. */
+typedef struct ps_tuning {
+    int prec_rows;       /* rows per CTA of the preconditioner's row FFTs   */
+    int llp_rows;        /* output rows per warp of the CG loop's LLP kernel */
+    float prec_us[4];    /* candidates 1, 2, 4, 8 rows                      */
+    float llp_us[2];     /* candidates: the long and the short walk         */
+} ps_tuning;
+
+/* Autotuner: times every candidate of each tunable kernel on N bands of
+ * H x W (CUDA events on `stream`, zeroed scratch in the caller's workspace
+ * of ps_workspace_size) and records the fastest for this device and sizes;
+ * later ps_solve_hrms / ps_pansharpen calls with the same sizes use it.
+ * Synchronises the stream. h_out may be NULL. */
+ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, void *d_ws,
+                      size_t ws_bytes, void *stream, ps_tuning *h_out);
+
 /* Workspace bytes needed by ps_pansharpen (covers ps_estimate_kernel and
  * ps_solve_hrms for the same sizes; h_hrms may be NULL, and with warm == 2
  * the network's workspace is included). 0 when a size is invalid. */

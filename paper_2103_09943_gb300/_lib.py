@@ -30,6 +30,11 @@ class HrmsParams(ctypes.Structure):
                 ("cnn_params", ctypes.c_void_p)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("prec_rows", ctypes.c_int), ("llp_rows", ctypes.c_int),
+                ("prec_us", ctypes.c_float * 4), ("llp_us", ctypes.c_float * 2)]
+
+
 class BandInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
                 ("rel_residual", ctypes.c_double)]
@@ -55,6 +60,7 @@ SIGNATURES = {
                                 _P, _P, _P, ctypes.POINTER(KernelInfo), _P, _Z, _P]),
     "ps_solve_hrms": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(HrmsParams),
                            _P, _P, _P, _P, _P, _Z, _P]),
+    "ps_autotune": (_I, [_I, _I, _I, _I, _I, _I, _P, _Z, _P, ctypes.POINTER(Tuning)]),
     "ps_pansharpen": (_I, [_P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(KernelParams),
                            ctypes.POINTER(HrmsParams), _P, _P, ctypes.POINTER(KernelInfo),
                            _P, _P, _Z, _P]),

@@ -13,7 +13,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib
-from ._lib import BandInfo, HrmsParams, KernelInfo, KernelParams
+from ._lib import BandInfo, HrmsParams, KernelInfo, KernelParams, Tuning
 
 
 class PsError(RuntimeError):
@@ -67,6 +67,18 @@ def workspace(N, H, W, ratio, R, device=None, hparams: HrmsParams | None = None)
     if n == 0:
         raise PsError("invalid sizes for a workspace")
     return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+
+
+def autotune(N, H, W, ratio, R, r=1, ws=None, device=None) -> dict:
+    """Times the candidate launch shapes of the tunable kernels on these sizes
+    and records the fastest for later solves (ps_autotune)."""
+    ws = ws if ws is not None else workspace(N, H, W, ratio, R, device)
+    t = Tuning()
+    _check(_lib.load().ps_autotune(N, H, W, ratio, R, r, _ptr(ws), ws.numel(), _stream(),
+                                   ctypes.byref(t)))
+    return {"prec_rows": t.prec_rows, "llp_rows": t.llp_rows,
+            "prec_us": {str(k): round(v, 2) for k, v in zip((1, 2, 4, 8), t.prec_us) if v},
+            "llp_us": {"long": round(t.llp_us[0], 2), "short": round(t.llp_us[1], 2)}}
 
 
 @dataclass

@@ -166,6 +166,10 @@ struct DevState {
     int attrs_done = 0;
     int num_sms = 0;
     cudaStream_t capture = nullptr;
+    // two branch streams and their fork / join events: the CG iteration runs
+    // the two halves of the bands as parallel branches
+    cudaStream_t branch[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
 };
 std::mutex g_mu;
 std::vector<DevState> g_dev;
@@ -193,8 +197,32 @@ ps_status ensure_device(cudaStream_t *capture, int *num_sms = nullptr) {
             cudaStreamCreateWithFlags(&d.capture, cudaStreamNonBlocking) != cudaSuccess)
             return PS_ERR_CUDA;
         *capture = d.capture;
+        for (int k = 0; k < 2; ++k) {
+            if (!d.branch[k] &&
+                cudaStreamCreateWithFlags(&d.branch[k], cudaStreamNonBlocking) != cudaSuccess)
+                return PS_ERR_CUDA;
+            if (!d.join[k] && cudaEventCreateWithFlags(&d.join[k], cudaEventDisableTiming) !=
+                                  cudaSuccess)
+                return PS_ERR_CUDA;
+        }
+        if (!d.fork && cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming) != cudaSuccess)
+            return PS_ERR_CUDA;
     }
     return PS_OK;
+}
+
+// Branch streams and events of the current device (after ensure_device with
+// a capture stream).
+struct Branches {
+    cudaStream_t s[2];
+    cudaEvent_t fork, join[2];
+};
+Branches device_branches() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    const DevState &d = g_dev[dev];
+    return {{d.branch[0], d.branch[1]}, d.fork, {d.join[0], d.join[1]}};
 }
 
 // ---------------------------------------------------------------------------
@@ -213,6 +241,9 @@ struct CgLoopArgs {
     CgGlobal *g;
     int precond;
     PrecArgs pa;  // z = P^{-1} r (valid when precond)
+    int split;    // 1, or 2: the two halves of the bands as parallel branches
+    Tuning tune;  // launch choices (part of the graph cache key)
+    int pad_;
     bool operator==(const CgLoopArgs &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
 };
 
@@ -222,29 +253,64 @@ struct CgGraph {
 };
 std::vector<CgGraph> g_graphs;
 
-void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, int use_cond,
-                       cudaGraphConditionalHandle h, cudaStream_t st) {
+// One iteration's kernels for the bands [b0, b0 + n) (b0 even).
+void enqueue_bands(const CgLoopArgs &a, int b0, int n, const float *p_old, float *p_new,
+                   cudaStream_t st) {
+    const size_t HW = (size_t)a.H * a.W, hw = HW / ((size_t)a.c * a.c);
+    const size_t o = (size_t)b0 * HW;
+    CgBand *bands = a.bands + b0;
+    float *v = a.v + (size_t)b0 * hw;
     // p_new = (z or r) + beta p_old, formed inside the blur-decimate load
-    launch_db(p_old, a.precond ? a.pa.z : a.rv, p_new, a.bands, a.g, 1, a.N, a.H, a.W, a.c, a.u,
-              a.R, a.v, st);
+    launch_db(p_old + o, (a.precond ? a.pa.z : a.rv) + o, p_new + o, bands, a.g, 1, n, a.H, a.W,
+              a.c, a.u, a.R, v, st);
     LlpArgs la = {};
-    la.in = p_new;
-    la.lr = a.v;
+    la.in = p_new + o;
+    la.lr = v;
     la.st4 = a.st4;
     la.u = a.u;
     la.R = a.R;
     la.c = a.c;
     la.H = a.H;
     la.W = a.W;
-    la.N = a.N;
+    la.N = n;
     la.lam = a.lam;
-    la.out = a.ap;
-    la.bands = a.bands;
+    la.out = a.ap + o;
+    la.bands = bands;
     la.g = a.g;
     la.cg = 1;
-    launch_llp_cgq2(la, a.r, a.N, st);
-    launch_cg_update(a.x, a.rv, p_new, a.ap, a.v, a.u, a.R, a.c, a.N, a.H, a.W, a.bands, a.g, st);
-    if (a.precond) launch_precond(a.pa, st);
+    la.ty = a.tune.llp_rows;
+    launch_llp_cgq2(la, a.r, n, st);
+    launch_cg_update(a.x + o, a.rv + o, p_new + o, a.ap + o, v, a.u, a.R, a.c, n, a.H, a.W, bands,
+                     a.g, st);
+    if (a.precond) {
+        PrecArgs pa = a.pa;
+        pa.r = a.rv + o;
+        pa.z = a.pa.z + o;
+        pa.spec = a.pa.spec + (size_t)(b0 / 2) * HW;
+        pa.N = n;
+        pa.bands = bands;
+        pa.rows = a.tune.prec_rows;
+        launch_precond(pa, st);
+    }
+}
+
+void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, int use_cond,
+                       cudaGraphConditionalHandle h, cudaStream_t st) {
+    if (a.split == 2) {
+        // the two halves of the bands as parallel branches, joined before the
+        // loop control
+        const Branches br = device_branches();
+        const int n0 = 2 * ((a.N / 2 + 1) / 2);
+        cudaEventRecord(br.fork, st);
+        for (int k = 0; k < 2; ++k) {
+            cudaStreamWaitEvent(br.s[k], br.fork, 0);
+            enqueue_bands(a, k ? n0 : 0, k ? a.N - n0 : n0, p_old, p_new, br.s[k]);
+            cudaEventRecord(br.join[k], br.s[k]);
+        }
+        for (int k = 0; k < 2; ++k) cudaStreamWaitEvent(st, br.join[k], 0);
+    } else {
+        enqueue_bands(a, 0, a.N, p_old, p_new, st);
+    }
     launch_cg_control(a.bands, a.g, a.N, use_cond, h, st);
 }
 
@@ -584,6 +650,8 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
     a.bands = bands; a.g = g;
     a.precond = p->precond;
     a.pa = pa;
+    a.split = (N >= 4) ? 2 : 1;
+    a.tune = tuning_get(a.dev, N, H, W, c, p->r);
     if (p->host_loop) {
         // same kernels, launched by the host; the stop flag is read every 8
         // iterations, and the loop is bounded by max_iter whatever it says
@@ -620,6 +688,95 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
             h_info[b].rel_residual = hb[b].bb > 0.0 ? sqrt(hb[b].rr / hb[b].bb) : 0.0;
         }
     }
+    return PS_OK;
+}
+
+ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, void *d_ws, size_t ws_bytes,
+                      void *stream, ps_tuning *h_out) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
+    if ((s = check_fft_dims(H, W)) != PS_OK) return s;
+    if (r < 1 || r > kMaxWinR) return PS_ERR_INVALID_ARG;
+    if (!precond_supported(H, W, ratio)) return PS_ERR_UNSUPPORTED;
+    Ws ws;
+    if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
+    cudaStream_t capture = nullptr;
+    if ((s = ensure_device(&capture)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t HW = (size_t)H * W;
+    // zeroed inputs: the kernels' times do not depend on the values
+    const size_t vec = (size_t)N * HW * sizeof(float);
+    if (cudaMemsetAsync(ws.base + ws.L.st4, 0, HW * 16, st) != cudaSuccess ||
+        cudaMemsetAsync(ws.base + ws.L.r, 0, vec, st) != cudaSuccess ||
+        cudaMemsetAsync(ws.base + ws.L.pA, 0, vec, st) != cudaSuccess ||
+        cudaMemsetAsync(ws.base + ws.L.bh32, 0, HW * 8, st) != cudaSuccess)
+        return PS_ERR_CUDA;
+    launch_fft_twiddles(W, ws.at<float2>(ws.L.twW32), ws.at<double2>(ws.L.twW64), st);
+    launch_fft_twiddles(H, ws.at<float2>(ws.L.twH32), ws.at<double2>(ws.L.twH64), st);
+    CgBand *bands = ws.at<CgBand>(ws.L.bands);
+    CgGlobal *g = ws.at<CgGlobal>(ws.L.glob);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return PS_ERR_CUDA;
+    // best of three single launches, the CG scalars reset before each
+    auto timed = [&](auto launch) -> float {
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaMemsetAsync(bands, 0, N * sizeof(CgBand), st);
+            cudaMemsetAsync(g, 0, sizeof(CgGlobal), st);
+            cudaEventRecord(e0, st);
+            launch();
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best) best = ms;  // the first launch warms up
+        }
+        return best * 1000.f;
+    };
+    ps_tuning out;
+    memset(&out, 0, sizeof(out));
+    PrecArgs pa = make_prec_args(ws, ws.at<float>(ws.L.r), ws.at<float>(ws.L.z), N, H, W, ratio,
+                                 2e-4f, nullptr, nullptr);
+    const int trs[4] = {1, 2, 4, 8};
+    float bestp = 1e30f;
+    for (int k = 0; k < 4; ++k) {
+        if (!precond_rows_ok(H, W, ratio, trs[k])) continue;
+        pa.rows = trs[k];
+        out.prec_us[k] = timed([&] { launch_precond(pa, st); });
+        if (out.prec_us[k] < bestp) {
+            bestp = out.prec_us[k];
+            out.prec_rows = trs[k];
+        }
+    }
+    LlpArgs la = {};
+    la.in = ws.at<float>(ws.L.pA);
+    la.st4 = ws.at<float4>(ws.L.st4);
+    la.H = H;
+    la.W = W;
+    la.N = N;
+    la.c = ratio;
+    la.lam = 2e-4f;
+    la.out = ws.at<float>(ws.L.ap);
+    la.bands = bands;
+    la.g = g;
+    la.cg = 1;
+    float bestl = 1e30f;
+    for (int k = 0; k < 2; ++k) {
+        la.ty = llp_cgq2_rows(r, k);
+        out.llp_us[k] = timed([&] { launch_llp_cgq2(la, r, N, st); });
+        if (out.llp_us[k] < bestl) {
+            bestl = out.llp_us[k];
+            out.llp_rows = la.ty;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if ((s = last_launch()) != PS_OK) return s;
+    tuning_set(dev, N, H, W, ratio, r, Tuning{out.prec_rows, out.llp_rows});
+    if (h_out) *h_out = out;
     return PS_OK;
 }
 
@@ -828,14 +985,11 @@ ps_status cnn_bind(void *d_ws, size_t ws_bytes, int B, int H, int W, int trainin
 void cnn_conv(const CnnCall &c, const __nv_bfloat16 *in, __nv_bfloat16 *out, int layer,
               int adjoint, const __nv_bfloat16 *mask, const float *params, int B, int H, int W,
               cudaStream_t st, int mode = CONV_PLAIN, const float *up = nullptr,
-              const float *pan = nullptr, size_t pan_stride = 0, float *z = nullptr) {
+              float *z = nullptr) {
     Conv32Args a;
     memset(&a, 0, sizeof(a));
     a.mode = mode;
     a.up = up;
-    a.pan = pan;
-    a.pan_stride = pan_stride;
-    a.w0 = params + c.w_off[0];
     a.w5 = params + c.w_off[5];
     a.z = z;
     a.in = in;
@@ -888,14 +1042,13 @@ ps_status ps_cnn_forward(const float *d_params, const float *d_up, const float *
     for (int l = 1; l <= 4; ++l)
         launch_pack_w32(d_params + c.w_off[l], c.base + c.L.wf + (l - 1) * kWPack, 0, st);
     __nv_bfloat16 *A = c.at<__nv_bfloat16>(c.L.act[1]), *Bf = c.at<__nv_bfloat16>(c.L.act[2]);
-    // layer 1 computes its input rows (the first layer) itself, layer 4
-    // applies the last layer in its epilogue: a1 and a5 never reach memory
-    cnn_conv(c, nullptr, A, 1, 0, nullptr, d_params, B, H, W, st, CONV_FIRST, d_up, d_pan,
-             pan_stride);
-    cnn_conv(c, A, Bf, 2, 0, nullptr, d_params, B, H, W, st);
-    cnn_conv(c, Bf, A, 3, 0, nullptr, d_params, B, H, W, st);
-    cnn_conv(c, A, nullptr, 4, 0, nullptr, d_params, B, H, W, st, CONV_LAST, d_up, d_pan,
-             pan_stride, d_z);
+    // the first layer on the CUDA cores; layer 4 applies the last layer in
+    // its epilogue, so a5 never reaches memory
+    launch_cnn_first(d_up, d_pan, pan_stride, d_params + c.w_off[0], B, H, W, A, st);
+    cnn_conv(c, A, Bf, 1, 0, nullptr, d_params, B, H, W, st);
+    cnn_conv(c, Bf, A, 2, 0, nullptr, d_params, B, H, W, st);
+    cnn_conv(c, A, Bf, 3, 0, nullptr, d_params, B, H, W, st);
+    cnn_conv(c, Bf, nullptr, 4, 0, nullptr, d_params, B, H, W, st, CONV_LAST, d_up, d_z);
     return last_launch();
 }
 

@@ -63,13 +63,11 @@ __global__ void pack_w32_kernel(const float *__restrict__ w, __nv_bfloat16 *__re
     out[i] = __float2bfloat16_rn(v);
 }
 
-// Extra shared memory of the fused modes: first-layer parameters (608
-// floats), last-layer parameters (289 floats, padded) and the exchange of
-// the last layer's per-tap partial sums (128 pixels x 9).
-constexpr int kExtraW0 = 608 * 4;
+// Extra shared memory of the fused last layer: its parameters (289 floats,
+// padded) and the exchange of its per-tap partial sums (128 pixels x 9).
 constexpr int kExtraW5 = 304 * 4;
 constexpr int kExtraX = kTileM * 9 * 4;
-constexpr int kConvSmemFused = kConvSmem + kExtraW0 + kExtraW5 + kExtraX;
+constexpr int kConvSmemFused = kConvSmem + kExtraW5 + kExtraX;
 
 template <int MODE>
 __global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
@@ -79,26 +77,16 @@ __global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
     float *sbias = reinterpret_cast<float *>(ring + kRing * kRowB);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sbias + kCh);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
-    float *sw0 = reinterpret_cast<float *>(csm + kConvSmem);
-    float *sw5 = reinterpret_cast<float *>(csm + kConvSmem + kExtraW0);
-    float *sxc = reinterpret_cast<float *>(csm + kConvSmem + kExtraW0 + kExtraW5);
+    float *sw5 = reinterpret_cast<float *>(csm + kConvSmem);
+    float *sxc = reinterpret_cast<float *>(csm + kConvSmem + kExtraW5);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int H = a.H, W = a.W;
 
     for (int i = tid; i < kWBytes / 16; i += 128)
         reinterpret_cast<uint4 *>(wsm)[i] = __ldg(reinterpret_cast<const uint4 *>(a.wpack) + i);
     if (tid < kCh) sbias[tid] = a.bias ? a.bias[tid] : 0.0f;
-    // fused layers' weights transposed so that four output channels (first
-    // layer) or four input channels (last layer) are one 16-byte load:
-    // sw0[(t * 2 + i) * 32 + o] = w0[o][i][t], biases at 576;
-    // sw5[t * 32 + c] = w5[c][t], bias at 288
-    if (MODE == CONV_FIRST) {
-        for (int i = tid; i < 576; i += 128) {
-            const int o = i / 18, ci = (i / 9) % 2, t = i % 9;
-            sw0[(t * 2 + ci) * 32 + o] = a.w0[i];
-        }
-        if (tid < kCh) sw0[576 + tid] = a.w0[576 + tid];
-    }
+    // the fused last layer's weights transposed so that four input channels
+    // are one 16-byte load: sw5[t * 32 + c] = w5[c][t], bias at 288
     if (MODE == CONV_LAST) {
         for (int i = tid; i < 288; i += 128) sw5[(i % 9) * 32 + i / 9] = a.w5[i];
         if (tid == 0) sw5[288] = a.w5[288];
@@ -134,62 +122,13 @@ __global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
         const int ya = ch * a.rpi, yb = min(H, ya + a.rpi);
         // rows of this layer's output computed by the item
         const int ys = ya - (MODE == CONV_LAST ? 1 : 0), ye = yb + (MODE == CONV_LAST ? 1 : 0);
-        const __nv_bfloat16 *inb = (MODE == CONV_FIRST) ? nullptr : a.in + (size_t)b * H * W * kCh;
+        const __nv_bfloat16 *inb = a.in + (size_t)b * H * W * kCh;
         float racc[3] = {0.f, 0.f, 0.f};  // last layer: output rows y - 1, y, y + 1
 
         auto load_row = [&](int yabs) {
             const int yy = wrapm(yabs, H);
             const uint32_t dst = ring_u32 + ring_slot(yabs) * kRowB;
-            if (MODE == CONV_FIRST) {
-                // the first layer (2 -> 32, CUDA cores) on the 130 pixels of the row
-                uint8_t *drow = ring + ring_slot(yabs) * kRowB;
-                const float *ub = a.up + (size_t)b * H * W;
-                const float *pb = a.pan + (size_t)b * a.pan_stride;
-                for (int px = tid; px < kHalo; px += 128) {
-                    const int x = wrapm(x0 - 1 + px, W);
-                    float in0[9], in1[9];
-#pragma unroll
-                    for (int dy = -1; dy <= 1; ++dy) {
-                        const int ry = wrapm(yy + dy, H);
-#pragma unroll
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            const int rx = wrapm(x + dx, W);
-                            const size_t o = (size_t)ry * W + rx;
-                            in0[(dy + 1) * 3 + dx + 1] = __ldg(ub + o) * (1.0f / 255.0f);
-                            in1[(dy + 1) * 3 + dx + 1] = __ldg(pb + o) * (1.0f / 255.0f);
-                        }
-                    }
-                    float acc[kCh];
-#pragma unroll
-                    for (int o = 0; o < kCh; ++o) acc[o] = sw0[576 + o];
-#pragma unroll
-                    for (int t = 0; t < 9; ++t) {
-#pragma unroll
-                        for (int ci = 0; ci < 2; ++ci) {
-                            const float xv = ci ? in1[t] : in0[t];
-                            const float4 *w4 = reinterpret_cast<const float4 *>(sw0 + (t * 2 + ci) * 32);
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) {
-                                const float4 wv = w4[q];
-                                acc[4 * q] = fmaf(wv.x, xv, acc[4 * q]);
-                                acc[4 * q + 1] = fmaf(wv.y, xv, acc[4 * q + 1]);
-                                acc[4 * q + 2] = fmaf(wv.z, xv, acc[4 * q + 2]);
-                                acc[4 * q + 3] = fmaf(wv.w, xv, acc[4 * q + 3]);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        uint4 pk;
-                        __nv_bfloat162 *ph = reinterpret_cast<__nv_bfloat162 *>(&pk);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            ph[e] = __floats2bfloat162_rn(fmaxf(acc[8 * j + 2 * e], 0.0f),
-                                                          fmaxf(acc[8 * j + 2 * e + 1], 0.0f));
-                        *reinterpret_cast<uint4 *>(drow + j * kPlane + px * 16) = pk;
-                    }
-                }
-            } else {
+            {
                 const __nv_bfloat16 *src = inb + (size_t)yy * W * kCh;
                 for (int idx = tid; idx < kHalo * 4; idx += 128) {
                     const int p = idx >> 2, j = idx & 3;
@@ -365,7 +304,6 @@ void launch_conv32(const Conv32Args &a, int num_sms, cudaStream_t st) {
     int grid = 3 * num_sms;
     if (grid > items) grid = items;
     switch (a.mode) {
-        case CONV_FIRST: conv32_tc_kernel<CONV_FIRST><<<grid, 128, kConvSmemFused, st>>>(a); break;
         case CONV_LAST: conv32_tc_kernel<CONV_LAST><<<grid, 128, kConvSmemFused, st>>>(a); break;
         default: conv32_tc_kernel<CONV_PLAIN><<<grid, 128, kConvSmem, st>>>(a); break;
     }
@@ -374,9 +312,6 @@ void launch_conv32(const Conv32Args &a, int num_sms, cudaStream_t st) {
 cudaError_t cnn_set_attrs() {
     cudaError_t e = cudaFuncSetAttribute(conv32_tc_kernel<CONV_PLAIN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(conv32_tc_kernel<CONV_FIRST>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmemFused);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(conv32_tc_kernel<CONV_LAST>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmemFused);

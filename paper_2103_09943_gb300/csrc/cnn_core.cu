@@ -48,15 +48,21 @@ __device__ __forceinline__ void store_px32(__nv_bfloat16 *p, const float *v) {
     for (int k = 0; k < 4; ++k) q[k] = pk[k];
 }
 
-// a1 = ReLU(conv0(x) + b0), x = (up / s, pan / s). One thread per pixel.
+// a1 = ReLU(conv0(x) + b0), x = (up / s, pan / s). One thread per pixel; the
+// weights sit transposed in shared memory, sw[(t * 2 + i) * 32 + o] =
+// w0[o][i][t], so that four output channels are one broadcast 16-byte load.
 __global__ void __launch_bounds__(256) cnn_first_kernel(const float *__restrict__ up,
                                                         const float *__restrict__ pan,
                                                         size_t pan_stride,
                                                         const float *__restrict__ prm, int B,
                                                         int H, int W,
                                                         __nv_bfloat16 *__restrict__ a1) {
-    __shared__ float sw[kCh * 2 * 9 + kCh];
-    for (int i = threadIdx.x; i < kCh * 2 * 9 + kCh; i += blockDim.x) sw[i] = prm[i];
+    __shared__ __align__(16) float sw[kCh * 2 * 9 + kCh];
+    for (int i = threadIdx.x; i < kCh * 18; i += blockDim.x) {
+        const int o = i / 18, ci = (i / 9) % 2, t = i % 9;
+        sw[(t * 2 + ci) * 32 + o] = prm[i];
+    }
+    if (threadIdx.x < kCh) sw[576 + threadIdx.x] = prm[576 + threadIdx.x];
     __syncthreads();
     const size_t HW = (size_t)H * W;
     const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -77,16 +83,26 @@ __global__ void __launch_bounds__(256) cnn_first_kernel(const float *__restrict_
         }
     }
     float v[kCh];
-#pragma unroll 4
-    for (int o = 0; o < kCh; ++o) {
-        float s = sw[kCh * 18 + o];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            s = fmaf(sw[(o * 2 + 0) * 9 + t], in[0][t], s);
-            s = fmaf(sw[(o * 2 + 1) * 9 + t], in[1][t], s);
+    for (int o = 0; o < kCh; ++o) v[o] = sw[576 + o];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+#pragma unroll
+        for (int ci = 0; ci < 2; ++ci) {
+            const float xv = in[ci][t];
+            const float4 *w4 = reinterpret_cast<const float4 *>(sw + (t * 2 + ci) * 32);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 wv = w4[q];
+                v[4 * q] = fmaf(wv.x, xv, v[4 * q]);
+                v[4 * q + 1] = fmaf(wv.y, xv, v[4 * q + 1]);
+                v[4 * q + 2] = fmaf(wv.z, xv, v[4 * q + 2]);
+                v[4 * q + 3] = fmaf(wv.w, xv, v[4 * q + 3]);
+            }
         }
-        v[o] = fmaxf(s, 0.0f);
     }
+#pragma unroll
+    for (int o = 0; o < kCh; ++o) v[o] = fmaxf(v[o], 0.0f);
     store_px32(a1 + idx * kCh, v);
 }
 

@@ -163,10 +163,10 @@ void launch_kernel_embed(const float *u, int R, int H, int W, double2 *out, cuda
 // (2R+1)^2 taps, layout [kx][ky] (FP64):
 //   B^(kx, ky) = sum_i exp(-2 pi i ky i / H) T_i(kx),
 //   T_i(kx) = sum_j u(i, j) exp(-2 pi i kx j / W),  i, j in [-R, R].
-// One CTA per 32 values of kx: the T_i of its columns in shared memory,
-// then one output per thread along ky (coalesced), twiddles from the FP64
-// tables tw[k] = exp(-2 pi i k / L).
-constexpr int kSpecCols = 32;
+// One CTA per 32 values of kx and 128 of ky: the T_i of its columns in
+// shared memory, then one output per thread along ky (coalesced), twiddles
+// from the FP64 tables tw[k] = exp(-2 pi i k / L).
+constexpr int kSpecCols = 32, kSpecRows = 128;
 __global__ void __launch_bounds__(256) kernel_spectrum_kernel(const float *__restrict__ u, int R,
                                                               int H, int W,
                                                               const double2 *__restrict__ twW,
@@ -181,28 +181,31 @@ __global__ void __launch_bounds__(256) kernel_spectrum_kernel(const float *__res
         const int kx = kx0 + c;
         double re = 0.0, im = 0.0;
         if (kx < W) {
+            // twiddle index kx j mod W, stepped by kx from j = -R
+            int idx = (int)(((long long)W * (R + 1) - (long long)kx * R) % W);
             for (int jj = 0; jj < n; ++jj) {
-                const int j = jj - R;
-                int idx = (int)(((long long)kx * j) % W);
-                if (idx < 0) idx += W;
                 const double2 w = twW[idx];
                 const double uv = (double)u[ii * n + jj];
                 re = fma(uv, w.x, re);
                 im = fma(uv, w.y, im);
+                idx += kx;
+                if (idx >= W) idx -= W;
             }
         }
         T[ii * kSpecCols + c] = make_double2(re, im);
     }
     __syncthreads();
     const int cols = min(kSpecCols, W - kx0);
-    for (int e = threadIdx.x; e < cols * H; e += blockDim.x) {
-        const int c = e / H, ky = e - (e / H) * H;
+    const int ky0 = blockIdx.y * kSpecRows, nky = min(kSpecRows, H - ky0);
+    for (int e = threadIdx.x; e < cols * nky; e += blockDim.x) {
+        const int c = e / nky, ky = ky0 + (e - (e / nky) * nky);
         double re = 0.0, im = 0.0;
+        // twiddle index ky i mod H, stepped by ky from i = -R
+        int idx = (int)(((long long)H * (R + 1) - (long long)ky * R) % H);
         for (int ii = 0; ii < n; ++ii) {
-            const int i = ii - R;
-            int idx = (int)(((long long)ky * i) % H);
-            if (idx < 0) idx += H;
             const double2 w = twH[idx];
+            idx += ky;
+            if (idx >= H) idx -= H;
             const double2 t = T[ii * kSpecCols + c];
             re = fma(t.x, w.x, fma(-t.y, w.y, re));
             im = fma(t.x, w.y, fma(t.y, w.x, im));
@@ -215,8 +218,8 @@ void launch_kernel_spectrum(const float *u, int R, int H, int W, const double2 *
                             const double2 *twH, double2 *out, cudaStream_t st) {
     const int n = 2 * R + 1;
     const size_t smem = (size_t)n * kSpecCols * sizeof(double2);
-    kernel_spectrum_kernel<<<(W + kSpecCols - 1) / kSpecCols, 256, smem, st>>>(u, R, H, W, twW,
-                                                                                twH, out);
+    const dim3 grd((W + kSpecCols - 1) / kSpecCols, (H + kSpecRows - 1) / kSpecRows);
+    kernel_spectrum_kernel<<<grd, 256, smem, st>>>(u, R, H, W, twW, twH, out);
 }
 
 // Per alias group (ky0 + p h, kx0 + q w), p, q in [0, c): solve

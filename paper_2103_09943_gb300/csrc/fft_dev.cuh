@@ -279,6 +279,32 @@ __device__ __forceinline__ void p2_stage(float2 *a, int L, int Ns, const float2 
     __syncthreads();
 }
 
+// Stages of the register FFT from span Ns0 up to span Ns1 (powers of two,
+// Ns0 < Ns1 <= L): the first log(Ns1 / Ns0) stages of a transform that starts
+// at Ns0. With Ns0 = 1 and Ns1 = L it is the whole transform.
+__device__ __forceinline__ void fft_p2_range(float2 *a, int L, int Ns0, int Ns1,
+                                             const float2 *__restrict__ tw, bool inverse, int t,
+                                             int T) {
+    const float sg = inverse ? 1.0f : -1.0f;
+    int Ns = Ns0;
+    while (Ns < Ns1) {
+        const int rem = Ns1 / Ns;
+        if (rem >= 16) {
+            p2_stage<16>(a, L, Ns, tw, sg, t, T);
+            Ns *= 16;
+        } else if (rem == 8) {
+            p2_stage<8>(a, L, Ns, tw, sg, t, T);
+            Ns *= 8;
+        } else if (rem == 4) {
+            p2_stage<4>(a, L, Ns, tw, sg, t, T);
+            Ns *= 4;
+        } else {
+            p2_stage<2>(a, L, Ns, tw, sg, t, T);
+            Ns *= 2;
+        }
+    }
+}
+
 // Whole transform of one padded row of power-of-two length L (16 <= L),
 // natural order in and out. Every thread of the CTA must call it with the
 // same L (the stages end on CTA barriers).

@@ -22,6 +22,7 @@ struct LlpArgs {
     CgBand *bands;      // CG mode of APPLY: p^T A p and alpha
     const CgGlobal *g;
     int cg;
+    int ty;             // CG mode: output rows per warp (0: default)
 };
 
 // operators.cu
@@ -93,17 +94,19 @@ struct PrecArgs {
     float lam;
     CgBand *bands;        // NULL: plain operator (no r^T z, no skipping)
     const CgGlobal *g;
+    int rows;             // rows per CTA of the row passes (0: the plan's choice)
 };
 bool precond_supported(int H, int W, int c);
+bool precond_rows_ok(int H, int W, int c, int tr);
 void launch_precond(const PrecArgs &a, cudaStream_t st);
 void launch_spectrum_to_f32(const double2 *in, float2 *out, size_t n, cudaStream_t st);
 cudaError_t precond_set_attrs();
 
 // cnn.cu: 3 x 3 convolutions with 32 in / 32 out channels on tcgen05
-enum { CONV_PLAIN = 0, CONV_FIRST = 1, CONV_LAST = 2 };
+enum { CONV_PLAIN = 0, CONV_LAST = 2 };
 struct Conv32Args {
-    const __nv_bfloat16 *in;    // N x H x W x 32, NHWC (CONV_PLAIN, CONV_LAST)
-    __nv_bfloat16 *out;         // N x H x W x 32 (CONV_PLAIN, CONV_FIRST)
+    const __nv_bfloat16 *in;    // N x H x W x 32, NHWC
+    __nv_bfloat16 *out;         // N x H x W x 32 (CONV_PLAIN)
     const void *wpack;          // B operand from launch_pack_w32 (18432 bytes)
     const float *bias;          // 32, or NULL
     const __nv_bfloat16 *mask;  // NULL, or out = conv * (mask > 0) (before the bias)
@@ -112,13 +115,10 @@ struct Conv32Args {
     int rpi;                    // output rows per work item
     int *err;                   // set to 1 when a bounded wait gives up
     int mode;                   // CONV_*
-    // CONV_FIRST: the input rows are the network's first layer evaluated on
-    // (up / 255, pan / 255) with w0 (32 x 2 x 9 weights, then 32 biases)
     // CONV_LAST: the output is z = up + 255 (conv5(ReLU(conv + bias)) + b5)
     // with w5 (32 x 9 weights, then the bias); z is N x H x W FP32
-    const float *up, *pan;
-    size_t pan_stride;
-    const float *w0, *w5;
+    const float *up;
+    const float *w5;
     float *z;
 };
 size_t conv32_smem_bytes();
@@ -143,8 +143,18 @@ void launch_cnn_wgrad_first(const float *up, const float *pan, size_t pan_stride
 void launch_cnn_adam(float *p, const float *g, float *m, float *v, int n, int step, float lr,
                      float b1, float b2, float eps, cudaStream_t st);
 
-// llp2.cu: q = lam L M L p and p^T q inside the CG loop, two pixels per lane
+// llp2.cu: q = lam L M L p and p^T q inside the CG loop, two pixels per lane;
+// rows per warp from LlpArgs::ty (llp_cgq2_rows(r, 0) long, (r, 1) short)
 void launch_llp_cgq2(const LlpArgs &a, int r, int N, cudaStream_t st);
+int llp_cgq2_rows(int r, int which);
+
+// tune.cu: launch choices of the tunable kernels per problem size
+struct Tuning {
+    int prec_rows;  // rows per CTA of the preconditioner's row passes (0: default)
+    int llp_rows;   // output rows per warp of the CG-loop LLP kernel (0: default)
+};
+Tuning tuning_get(int dev, int N, int H, int W, int c, int r);
+void tuning_set(int dev, int N, int H, int W, int c, int r, const Tuning &t);
 
 // warm.cu
 void launch_bicubic_up(const float *X, int N, int h, int w, int c, float *out,

@@ -15,6 +15,8 @@
 //              (Eq. u_p_solution), multiplier updates, stop test
 #include <math.h>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -530,6 +532,37 @@ __device__ __forceinline__ float2 det3c(float2 a11, float2 a12, float2 a13, floa
 }
 
 // Block sums (double) of two values; all threads receive the results.
+// Block-wide sums of two floats by a pairwise tree (warp shuffles, then one
+// warp over the warp sums): the result is valid in every thread.
+__device__ __forceinline__ void block_sum2f(float a, float b, double *red, float &ra, float &rb) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    float *rf = reinterpret_cast<float *>(red);
+    const int tid = threadIdx.x, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((tid & 31) == 0) {
+        rf[tid >> 5] = a;
+        rf[32 + (tid >> 5)] = b;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        float sa = (tid < nw) ? rf[tid] : 0.f, sb = (tid < nw) ? rf[32 + tid] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        }
+        if (tid == 0) {
+            rf[64] = sa;
+            rf[65] = sb;
+        }
+    }
+    __syncthreads();
+    ra = rf[64];
+    rb = rf[65];
+}
+
 __device__ __forceinline__ void block_sum2(double a, double b, double *red, double &ra,
                                            double &rb) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -631,11 +664,33 @@ __device__ void dft3_inverse(const float2 *F0, const float2 *F1, const float2 *F
     __syncthreads();
 }
 
-size_t admm_smem_bytes(int R) {
+size_t admm_state_bytes(int R) {
     const int nt = (2 * R + 1) * (2 * R + 1);
     const size_t ntp = (nt + 3) & ~3;
     return 26 * ntp * sizeof(float) + (6 * ntp + 64) * sizeof(float2) + 80 * sizeof(double) +
            16;
+}
+
+constexpr size_t kAdmmMaxSmem = 227 * 1024;
+
+// Q (nt x nt) as FP16 after the state, when the whole fits in shared memory.
+__host__ __device__ inline bool admm_q_fits(int R, size_t state) {
+    const size_t nt = (size_t)(2 * R + 1) * (2 * R + 1);
+    return state + nt * nt * 2 <= kAdmmMaxSmem;
+}
+
+size_t admm_smem_bytes(int R) {
+    const size_t st = admm_state_bytes(R);
+    const size_t nt = (size_t)(2 * R + 1) * (2 * R + 1);
+    return admm_q_fits(R, st) ? st + nt * nt * 2 : st;
+}
+
+__device__ __forceinline__ bool admm_q_in_smem(int R) {
+    const int nt = (2 * R + 1) * (2 * R + 1);
+    const size_t ntp = (nt + 3) & ~3;
+    const size_t state = 26 * ntp * sizeof(float) + (6 * ntp + 64) * sizeof(float2) +
+                         80 * sizeof(double) + 16;
+    return admm_q_fits(R, state);
 }
 
 __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
@@ -666,6 +721,12 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
     const int chunk = (nt + parts - 1) / parts;
     float *pbuf = reinterpret_cast<float *>(T0);
     int *pcnt = reinterpret_cast<int *>(T0) + 3 * ntp;
+    // Q in shared memory as FP16 when it fits: its product enters z at most
+    // ~2.5e-4 of z's size (mu3 dominated by E^T E), so FP16's 4.9e-4 relative
+    // rounding costs ~1e-7 of z; otherwise Q is read from global memory
+    __half *qh = admm_q_in_smem(R) ? reinterpret_cast<__half *>(flag + 4) : nullptr;
+    if (qh)
+        for (int i = tid; i < nt * nt; i += nthr) qh[i] = __float2half_rn(Q[i]);
 
     const float a1 = p.alpha1 * p.mu1, a2 = p.alpha2 * p.mu2;
     for (int k = tid; k < nt; k += nthr) {
@@ -721,13 +782,23 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
             const int m0 = part * chunk, m1 = min(nt, m0 + chunk);
             float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
             int m = m0;
-            for (; m + 3 < m1; m += 4) {
-                c0 = fmaf(__ldg(Q + (size_t)m * nt + k), wv[m], c0);
-                c1 = fmaf(__ldg(Q + (size_t)(m + 1) * nt + k), wv[m + 1], c1);
-                c2 = fmaf(__ldg(Q + (size_t)(m + 2) * nt + k), wv[m + 2], c2);
-                c3 = fmaf(__ldg(Q + (size_t)(m + 3) * nt + k), wv[m + 3], c3);
+            if (qh) {
+                for (; m + 3 < m1; m += 4) {
+                    c0 = fmaf(__half2float(qh[m * nt + k]), wv[m], c0);
+                    c1 = fmaf(__half2float(qh[(m + 1) * nt + k]), wv[m + 1], c1);
+                    c2 = fmaf(__half2float(qh[(m + 2) * nt + k]), wv[m + 2], c2);
+                    c3 = fmaf(__half2float(qh[(m + 3) * nt + k]), wv[m + 3], c3);
+                }
+                for (; m < m1; ++m) c0 = fmaf(__half2float(qh[m * nt + k]), wv[m], c0);
+            } else {
+                for (; m + 3 < m1; m += 4) {
+                    c0 = fmaf(__ldg(Q + (size_t)m * nt + k), wv[m], c0);
+                    c1 = fmaf(__ldg(Q + (size_t)(m + 1) * nt + k), wv[m + 1], c1);
+                    c2 = fmaf(__ldg(Q + (size_t)(m + 2) * nt + k), wv[m + 2], c2);
+                    c3 = fmaf(__ldg(Q + (size_t)(m + 3) * nt + k), wv[m + 3], c3);
+                }
+                for (; m < m1; ++m) c0 = fmaf(__ldg(Q + (size_t)m * nt + k), wv[m], c0);
             }
-            for (; m < m1; ++m) c0 = fmaf(__ldg(Q + (size_t)m * nt + k), wv[m], c0);
             pbuf[part * nt + k] = (c0 + c1) + (c2 + c3);
         }
         __syncthreads();
@@ -849,7 +920,7 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
         __syncthreads();
         dft3_inverse(F0, F1, F2, T0, T1, T2, un, p1, p2, tw, n);
         // 5-7. multiplier updates (Eq. subproblems), stop test
-        double dn = 0.0, nn = 0.0;
+        float dn = 0.f, nn = 0.f;
         for (int k = tid; k < nt; k += nthr) {
             const int i = k / n, j = k - (k / n) * n;
             const float gu0 = at(un, i, j + 1) - un[k];
@@ -862,17 +933,20 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
             l22[k] += p.rho * (m - y2[k]);
             l23[k] += p.rho * (at(p2, i + 1, j) - p2[k] - y3[k]);
             l3[k] += p.rho * (un[k] - z[k]);
-            const double d = (double)u[k] - (double)un[k];
-            dn += d * d;
-            nn += (double)un[k] * (double)un[k];
+            // stop-test norms: each thread holds at most a few entries, the
+            // rest is a pairwise tree, so FP32 sums are accurate to ~1e-6
+            // relative, far inside the threshold th
+            const float d = u[k] - un[k];
+            dn = fmaf(d, d, dn);
+            nn = fmaf(un[k], un[k], nn);
         }
-        double DN, NN;
-        block_sum2(dn, nn, red, DN, NN);
+        float DN, NN;
+        block_sum2f(dn, nn, red, DN, NN);
         __syncthreads();
         for (int k = tid; k < nt; k += nthr) u[k] = un[k];
         __syncthreads();
         it = t + 1;
-        change = sqrt(DN / NN);
+        change = (double)sqrtf(DN / NN);
         if (change < (double)p.th) {
             status = PS_OK;
             break;
@@ -895,7 +969,7 @@ void launch_admm(const float *Q, const double *zf, int R, const ps_kernel_params
 
 cudaError_t kest_set_attrs() {
     return cudaFuncSetAttribute(admm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)admm_smem_bytes(kMaxR));
+                                (int)kAdmmMaxSmem);
 }
 
 }  // namespace ps

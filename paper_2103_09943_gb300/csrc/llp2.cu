@@ -49,18 +49,22 @@ __device__ __forceinline__ float hsum(float v0, float v1) {
     }
 }
 
+// Output rows per warp: a multiple of 3 for r = 1, so that the 3-deep rolling
+// buffers cycle within the 3-way unrolled walk. Two lengths per radius (the
+// autotuner picks): longer walks spend less on the 2G halo rows, shorter
+// ones give more warps.
 template <int RW>
 struct Llp2Rows {
-    static constexpr int TY = (RW == 1) ? 66 : 64;
+    static constexpr int LONG = (RW == 1) ? 66 : 64;
+    static constexpr int SHORT = (RW == 1) ? 33 : 32;
     static constexpr int UNR = (RW == 1) ? 3 : 1;
 };
 
-template <int RW>
+template <int RW, int TY>
 __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
     constexpr int G = 2 * RW + 2;
     constexpr int VALID = 64 - 2 * G;
     constexpr int NB = 2 * RW + 1;
-    constexpr int TY = Llp2Rows<RW>::TY;
     constexpr float nw = (float)(NB * NB);
     constexpr float inw = 1.0f / nw;
     __shared__ double red[kWarps];
@@ -260,15 +264,32 @@ __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
     }
 }
 
+template <int RW, int TY>
+void launch_ty(const LlpArgs &a, int N, cudaStream_t st) {
+    constexpr int G = 2 * RW + 2, VALID = 64 - 2 * G;
+    const int rows = TY * kWarps;
+    dim3 grd((a.W + VALID - 1) / VALID, (a.H + rows - 1) / rows, N);
+    llp_cgq2_kernel<RW, TY><<<grd, 32 * kWarps, 0, st>>>(a);
+}
+
 template <int RW>
 void launch_r(const LlpArgs &a, int N, cudaStream_t st) {
-    constexpr int G = 2 * RW + 2, VALID = 64 - 2 * G;
-    const int rows = Llp2Rows<RW>::TY * kWarps;
-    dim3 grd((a.W + VALID - 1) / VALID, (a.H + rows - 1) / rows, N);
-    llp_cgq2_kernel<RW><<<grd, 32 * kWarps, 0, st>>>(a);
+    if (a.ty == Llp2Rows<RW>::SHORT)
+        launch_ty<RW, Llp2Rows<RW>::SHORT>(a, N, st);
+    else
+        launch_ty<RW, Llp2Rows<RW>::LONG>(a, N, st);
 }
 
 }  // namespace
+
+int llp_cgq2_rows(int r, int which) {
+    switch (r) {
+        case 1: return which ? Llp2Rows<1>::SHORT : Llp2Rows<1>::LONG;
+        case 2: return which ? Llp2Rows<2>::SHORT : Llp2Rows<2>::LONG;
+        case 3: return which ? Llp2Rows<3>::SHORT : Llp2Rows<3>::LONG;
+        default: return which ? Llp2Rows<4>::SHORT : Llp2Rows<4>::LONG;
+    }
+}
 
 void launch_llp_cgq2(const LlpArgs &a, int r, int N, cudaStream_t st) {
     switch (r) {

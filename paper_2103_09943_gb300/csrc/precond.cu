@@ -196,7 +196,11 @@ __global__ void __launch_bounds__(1024) prec_rows_fwd_kernel(PrecArgs a, RowGeom
     }
     __syncthreads();
     const int row = threadIdx.x / g.tpr, t = threadIdx.x - row * g.tpr;
-    row_fft<P2>(psm + row * ld, W, a.pw, a.twW, false, t, g.tpr);
+    if (P2)
+        fft_p2_range(psm + row * ld, W, 1, W, a.twW, false, t, g.tpr);
+    else
+        fft_row<8, float2>(psm + row * ld, a.pw, a.twW, false, t, g.tpr);
+    __syncthreads();
     float2 *S = a.spec + (size_t)k * HW;
     if (TR % 2 == 0) {
         // two rows per 16-byte store
@@ -318,7 +322,11 @@ __global__ void __launch_bounds__(1024) prec_rows_inv_kernel(PrecArgs a, RowGeom
     }
     __syncthreads();
     const int row = threadIdx.x / g.tpr, t = threadIdx.x - row * g.tpr;
-    row_fft<P2>(psm + row * ld, W, a.pw, a.twW, true, t, g.tpr);
+    if (P2)
+        fft_p2_range(psm + row * ld, W, 1, W, a.twW, true, t, g.tpr);
+    else
+        fft_row<8, float2>(psm + row * ld, a.pw, a.twW, true, t, g.tpr);
+    __syncthreads();
     const size_t o0 = (size_t)(2 * k) * HW + (size_t)y0 * W;
     const bool two = 2 * k + 1 < a.N;
     float d0 = 0.f, d1 = 0.f;
@@ -503,7 +511,20 @@ cudaError_t set_attrs_c() {
     return e;
 }
 
+// Rows per CTA `tr` for the row passes, if it is a valid choice.
+bool prec_rows_valid(const PrecPlan &pl, int H, int W, int tr) {
+    if (tr != 1 && tr != 2 && tr != 4 && tr != 8) return false;
+    if (H % tr || tr * pl.rg.tpr > 1024) return false;
+    const int row_len = pl.p2 ? prow_len(W) : W;
+    return (size_t)tr * (round16(row_len) + tr) * sizeof(float2) <= (size_t)kPrecMaxSmem;
+}
+
 }  // namespace
+
+bool precond_rows_ok(int H, int W, int c, int tr) {
+    PrecPlan pl;
+    return make_prec_plan(H, W, c, &pl) && prec_rows_valid(pl, H, W, tr);
+}
 
 bool precond_supported(int H, int W, int c) {
     PrecPlan pl;
@@ -513,6 +534,12 @@ bool precond_supported(int H, int W, int c) {
 void launch_precond(const PrecArgs &a, cudaStream_t st) {
     PrecPlan pl;
     if (!make_prec_plan(a.H, a.W, a.c, &pl)) return;  // callers check precond_supported
+    if (a.rows && a.rows != pl.rg.TR && prec_rows_valid(pl, a.H, a.W, a.rows)) {
+        const int row_len = pl.p2 ? prow_len(a.W) : a.W;
+        pl.rg.TR = a.rows;
+        pl.rg.ld = round16(row_len) + a.rows;
+        pl.row_smem = (size_t)a.rows * pl.rg.ld * sizeof(float2);
+    }
     const int nimg = (a.N + 1) / 2;
     const float scale = 1.0f / ((float)a.H * (float)a.W);
     const dim3 rgrd(a.H / pl.rg.TR, nimg), rblk(pl.rg.TR * pl.rg.tpr);

@@ -1,0 +1,41 @@
+// Table of launch choices picked by the autotuner (ps_autotune in api.cu):
+// per device and problem size, the rows per CTA of the preconditioner's row
+// passes and the rows per warp of the CG-loop LLP kernel. Launchers read it;
+// sizes never tuned get the static defaults.
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ps {
+
+namespace {
+
+struct Entry {
+    int dev, N, H, W, c, r;
+    Tuning t;
+};
+std::mutex g_tune_mu;
+std::vector<Entry> g_tune;
+
+}  // namespace
+
+Tuning tuning_get(int dev, int N, int H, int W, int c, int r) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const Entry &e : g_tune)
+        if (e.dev == dev && e.N == N && e.H == H && e.W == W && e.c == c && e.r == r) return e.t;
+    return Tuning{0, 0};
+}
+
+void tuning_set(int dev, int N, int H, int W, int c, int r, const Tuning &t) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (Entry &e : g_tune)
+        if (e.dev == dev && e.N == N && e.H == H && e.W == W && e.c == c && e.r == r) {
+            e.t = t;
+            return;
+        }
+    g_tune.push_back(Entry{dev, N, H, W, c, r, t});
+}
+
+}  // namespace ps

@@ -24,6 +24,10 @@ PREC_TOL = 5e-5
     (1, 64, 128, 2, 4, 1e-2),     # ratio 2, non-square
     (2, 96, 144, 6, 4, 8e-4),     # ratio 6
     (1, 3072, 64, 8, 3, 8e-4),    # 8 columns of 3072 exceed one CTA: fallback passes
+    (2, 256, 256, 4, 3, 8e-4),    # powers of two: radix-c stages merged into the column pass
+    (1, 128, 64, 8, 2, 8e-4),     # merged, ratio 8
+    (3, 512, 1024, 4, 5, 8e-4),   # merged, the workload's aspect
+    (1, 64, 256, 2, 4, 1e-2),     # merged, ratio 2, H / c = 32
 ])
 def test_precond_matches_oracle(cuda, N, H, W, c, R, lg):
     rng = np.random.default_rng(N * 1000 + H + W + c)
@@ -115,3 +119,18 @@ def test_pcg_nonfinite_band_leaves_its_partner_alone(cuda):
                                  api.default_hrms_params(precond=1), want_z0=True)
     assert info.status[2] == 6
     assert info.status[3] == 0 and np.isfinite(to_np(Z0)[3]).all()
+
+
+def test_autotune_picks_valid_shapes_and_keeps_parity(cuda, c0_ref):
+    sc, ref = c0_ref
+    cfg = sc["config"]
+    t = api.autotune(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, 1, device=cuda)
+    assert t["prec_rows"] in (1, 2, 4, 8) and str(t["prec_rows"]) in t["prec_us"]
+    assert t["llp_rows"] in (33, 66)
+    assert all(v > 0 for v in t["prec_us"].values())
+    Z, Z0, info = api.solve_hrms(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                 to_dev(sc["kernel"], cuda), cfg.ratio,
+                                 api.default_hrms_params(tol=1e-8), want_z0=True)
+    for b in range(cfg.bands):
+        assert rel(to_np(Z0)[b], ref["Z0"][b]) < 1e-5
+        assert rel(to_np(Z)[b], ref["Z"][b]) < 1e-5

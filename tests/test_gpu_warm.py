@@ -41,3 +41,33 @@ def test_warm_start_reaches_the_same_solution(cuda):
         iters[warm] = info.iters
     # the bicubic start is closer to Z0 than zeros: never more iterations
     assert sum(iters[1]) <= sum(iters[0]) + cfg.bands, iters
+
+
+def test_trained_network_saves_iterations(cuda):
+    # a held-out scene of the 8-band 1024 x 1024 workload (seed outside the
+    # training seeds 1000-1159): the committed network's start is closer to Z0
+    # than the bicubic one and cuts the preconditioned CG's iterations, and
+    # both starts reach the same Z0
+    import os
+    from dataclasses import replace
+    from paper_2103_09943_gb300 import cnn
+    wpath = os.path.join(os.path.dirname(cnn.__file__), "weights", "warm_cnn.npz")
+    if not os.path.exists(wpath):
+        pytest.skip("no trained weights")
+    net = cnn.WarmStartNet.load(wpath, device=cuda)
+    cfg = replace(synth.CONFIGS["c1"], seed=5005)
+    sc = synth.make_scene(cfg)
+    X, Y = to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda)
+    K, _, _ = api.estimate_kernel(X, Y, cfg.ratio, cfg.R, info=False)
+    out = {}
+    for warm in (0, 2):
+        hp = api.default_hrms_params(precond=1, warm=warm, cnn_params=net.params.data_ptr())
+        _, Z0, info = api.solve_hrms(X, Y, K, cfg.ratio, hp, want_z0=True)
+        assert all(s == 0 for s in info.status), info
+        out[warm] = (to_np(Z0), float(np.mean(info.iters)))
+    up = to_np(ops.bicubic_up(X, cfg.ratio))
+    z_cnn = to_np(net.forward(ops.bicubic_up(X, cfg.ratio), Y, check=True))
+    z0 = out[0][0]
+    assert rel(z_cnn, z0) < 0.8 * rel(up, z0)
+    assert out[2][1] < 0.85 * out[0][1], (out[0][1], out[2][1])
+    assert rel(out[2][0], z0) < 1e-3
