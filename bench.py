@@ -402,8 +402,11 @@ def run_gpu(args):
                                  cnn_params=net.params.data_ptr() if net else None)
     ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev, hp)
     # launch shapes of the tunable kernels, picked on this GPU before timing
-    tuning = api.autotune(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, hp.r, ws=ws) \
-        if hp.precond else None
+    tuning = None
+    if hp.precond:
+        K0, _, _ = api.estimate_kernel(X, Y, cfg.ratio, cfg.R, kp, ws=ws, info=False)
+        tuning = api.autotune(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, hp.r, ws=ws,
+                              lrms=X, pan=Y, kernel=K0)
     Z = torch.empty((cfg.bands, cfg.H, cfg.W), dtype=torch.float32, device=dev)
     K = torch.empty((cfg.n, cfg.n), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)

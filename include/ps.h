@@ -126,17 +126,24 @@ const char *ps_status_string(int status);
 typedef struct ps_tuning {
     int prec_rows;       /* rows per CTA of the preconditioner's row FFTs   */
     int llp_rows;        /* output rows per warp of the CG loop's LLP kernel */
+    int llp_pf;          /* rows its loads run ahead (2, 4, 6)              */
     float prec_us[4];    /* candidates 1, 2, 4, 8 rows                      */
-    float llp_us[2];     /* candidates: the long and the short walk         */
+    float llp_us[6];     /* candidates: long walk with 2, 4, 6 rows ahead,
+                            then the short walk                             */
+    int split;           /* parallel branches of a CG iteration (1, 2, 4)    */
+    float split_us[3];   /* two CG iterations, candidates 1, 2, 4 branches   */
 } ps_tuning;
 
 /* Autotuner: times every candidate of each tunable kernel on N bands of
  * H x W (CUDA events on `stream`, zeroed scratch in the caller's workspace
  * of ps_workspace_size) and records the fastest for this device and sizes;
  * later ps_solve_hrms / ps_pansharpen calls with the same sizes use it.
- * Synchronises the stream. h_out may be NULL. */
-ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, void *d_ws,
-                      size_t ws_bytes, void *stream, ps_tuning *h_out);
+ * With a scene (d_lrms, d_pan, d_kernel as for ps_solve_hrms; all NULL to
+ * skip) it also times whole solves of 20 CG iterations for each number of
+ * parallel branches. Synchronises the stream. h_out may be NULL. */
+ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r,
+                      const float *d_lrms, const float *d_pan, const float *d_kernel,
+                      void *d_ws, size_t ws_bytes, void *stream, ps_tuning *h_out);
 
 /* Workspace bytes needed by ps_pansharpen (covers ps_estimate_kernel and
  * ps_solve_hrms for the same sizes; h_hrms may be NULL, and with warm == 2

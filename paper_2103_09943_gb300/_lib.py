@@ -32,7 +32,9 @@ class HrmsParams(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("prec_rows", ctypes.c_int), ("llp_rows", ctypes.c_int),
-                ("prec_us", ctypes.c_float * 4), ("llp_us", ctypes.c_float * 2)]
+                ("llp_pf", ctypes.c_int), ("prec_us", ctypes.c_float * 4),
+                ("llp_us", ctypes.c_float * 6), ("split", ctypes.c_int),
+                ("split_us", ctypes.c_float * 3)]
 
 
 class BandInfo(ctypes.Structure):
@@ -60,7 +62,8 @@ SIGNATURES = {
                                 _P, _P, _P, ctypes.POINTER(KernelInfo), _P, _Z, _P]),
     "ps_solve_hrms": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(HrmsParams),
                            _P, _P, _P, _P, _P, _Z, _P]),
-    "ps_autotune": (_I, [_I, _I, _I, _I, _I, _I, _P, _Z, _P, ctypes.POINTER(Tuning)]),
+    "ps_autotune": (_I, [_I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _Z, _P,
+                         ctypes.POINTER(Tuning)]),
     "ps_pansharpen": (_I, [_P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(KernelParams),
                            ctypes.POINTER(HrmsParams), _P, _P, ctypes.POINTER(KernelInfo),
                            _P, _P, _Z, _P]),

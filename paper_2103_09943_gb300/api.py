@@ -69,16 +69,22 @@ def workspace(N, H, W, ratio, R, device=None, hparams: HrmsParams | None = None)
     return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
 
 
-def autotune(N, H, W, ratio, R, r=1, ws=None, device=None) -> dict:
+def autotune(N, H, W, ratio, R, r=1, ws=None, device=None, lrms=None, pan=None,
+             kernel=None) -> dict:
     """Times the candidate launch shapes of the tunable kernels on these sizes
-    and records the fastest for later solves (ps_autotune)."""
+    and records the fastest for later solves (ps_autotune); with a scene
+    (lrms, pan, kernel) also the number of parallel CG branches."""
     ws = ws if ws is not None else workspace(N, H, W, ratio, R, device)
     t = Tuning()
-    _check(_lib.load().ps_autotune(N, H, W, ratio, R, r, _ptr(ws), ws.numel(), _stream(),
-                                   ctypes.byref(t)))
+    _check(_lib.load().ps_autotune(N, H, W, ratio, R, r, _ptr(lrms), _ptr(pan), _ptr(kernel),
+                                   _ptr(ws), ws.numel(), _stream(), ctypes.byref(t)))
     return {"prec_rows": t.prec_rows, "llp_rows": t.llp_rows,
             "prec_us": {str(k): round(v, 2) for k, v in zip((1, 2, 4, 8), t.prec_us) if v},
-            "llp_us": {"long": round(t.llp_us[0], 2), "short": round(t.llp_us[1], 2)}}
+            "llp_pf": t.llp_pf,
+            "llp_us": {f"{w}/{pf}": round(t.llp_us[3 * i + j], 2)
+                       for i, w in enumerate(("long", "short")) for j, pf in enumerate((2, 4, 6))},
+            "split": t.split,
+            "split_us": {str(k): round(v, 2) for k, v in zip((1, 2, 4), t.split_us) if v}}
 
 
 @dataclass

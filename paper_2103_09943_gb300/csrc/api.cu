@@ -168,8 +168,8 @@ struct DevState {
     cudaStream_t capture = nullptr;
     // two branch streams and their fork / join events: the CG iteration runs
     // the two halves of the bands as parallel branches
-    cudaStream_t branch[2] = {nullptr, nullptr};
-    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    cudaStream_t branch[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 std::mutex g_mu;
 std::vector<DevState> g_dev;
@@ -197,7 +197,7 @@ ps_status ensure_device(cudaStream_t *capture, int *num_sms = nullptr) {
             cudaStreamCreateWithFlags(&d.capture, cudaStreamNonBlocking) != cudaSuccess)
             return PS_ERR_CUDA;
         *capture = d.capture;
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 4; ++k) {
             if (!d.branch[k] &&
                 cudaStreamCreateWithFlags(&d.branch[k], cudaStreamNonBlocking) != cudaSuccess)
                 return PS_ERR_CUDA;
@@ -214,15 +214,29 @@ ps_status ensure_device(cudaStream_t *capture, int *num_sms = nullptr) {
 // Branch streams and events of the current device (after ensure_device with
 // a capture stream).
 struct Branches {
-    cudaStream_t s[2];
-    cudaEvent_t fork, join[2];
+    cudaStream_t s[4];
+    cudaEvent_t fork, join[4];
 };
 Branches device_branches() {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_mu);
     const DevState &d = g_dev[dev];
-    return {{d.branch[0], d.branch[1]}, d.fork, {d.join[0], d.join[1]}};
+    Branches b;
+    for (int k = 0; k < 4; ++k) {
+        b.s[k] = d.branch[k];
+        b.join[k] = d.join[k];
+    }
+    b.fork = d.fork;
+    return b;
+}
+
+// Branch split of N bands into `split` parts on band-pair boundaries:
+// first band of part k (k <= split).
+int split_begin(int N, int split, int k) {
+    const int pairs = (N + 1) / 2;
+    const int pb = (pairs * k) / split;
+    return std::min(N, 2 * pb);
 }
 
 // ---------------------------------------------------------------------------
@@ -241,7 +255,7 @@ struct CgLoopArgs {
     CgGlobal *g;
     int precond;
     PrecArgs pa;  // z = P^{-1} r (valid when precond)
-    int split;    // 1, or 2: the two halves of the bands as parallel branches
+    int split;    // 1, 2 or 4: parts of the bands run as parallel branches
     Tuning tune;  // launch choices (part of the graph cache key)
     int pad_;
     bool operator==(const CgLoopArgs &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
@@ -279,6 +293,7 @@ void enqueue_bands(const CgLoopArgs &a, int b0, int n, const float *p_old, float
     la.g = a.g;
     la.cg = 1;
     la.ty = a.tune.llp_rows;
+    la.pf = a.tune.llp_pf;
     launch_llp_cgq2(la, a.r, n, st);
     launch_cg_update(a.x + o, a.rv + o, p_new + o, a.ap + o, v, a.u, a.R, a.c, n, a.H, a.W, bands,
                      a.g, st);
@@ -296,18 +311,18 @@ void enqueue_bands(const CgLoopArgs &a, int b0, int n, const float *p_old, float
 
 void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, int use_cond,
                        cudaGraphConditionalHandle h, cudaStream_t st) {
-    if (a.split == 2) {
-        // the two halves of the bands as parallel branches, joined before the
-        // loop control
+    if (a.split > 1) {
+        // parts of the bands as parallel branches, joined before the loop
+        // control
         const Branches br = device_branches();
-        const int n0 = 2 * ((a.N / 2 + 1) / 2);
         cudaEventRecord(br.fork, st);
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < a.split; ++k) {
+            const int b0 = split_begin(a.N, a.split, k), b1 = split_begin(a.N, a.split, k + 1);
             cudaStreamWaitEvent(br.s[k], br.fork, 0);
-            enqueue_bands(a, k ? n0 : 0, k ? a.N - n0 : n0, p_old, p_new, br.s[k]);
+            if (b1 > b0) enqueue_bands(a, b0, b1 - b0, p_old, p_new, br.s[k]);
             cudaEventRecord(br.join[k], br.s[k]);
         }
-        for (int k = 0; k < 2; ++k) cudaStreamWaitEvent(st, br.join[k], 0);
+        for (int k = 0; k < a.split; ++k) cudaStreamWaitEvent(st, br.join[k], 0);
     } else {
         enqueue_bands(a, 0, a.N, p_old, p_new, st);
     }
@@ -650,8 +665,8 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
     a.bands = bands; a.g = g;
     a.precond = p->precond;
     a.pa = pa;
-    a.split = (N >= 4) ? 2 : 1;
     a.tune = tuning_get(a.dev, N, H, W, c, p->r);
+    a.split = a.tune.split ? a.tune.split : ((N >= 4) ? 2 : 1);
     if (p->host_loop) {
         // same kernels, launched by the host; the stop flag is read every 8
         // iterations, and the loop is bounded by max_iter whatever it says
@@ -691,7 +706,8 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
     return PS_OK;
 }
 
-ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, void *d_ws, size_t ws_bytes,
+ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float *d_lrms,
+                      const float *d_pan, const float *d_kernel, void *d_ws, size_t ws_bytes,
                       void *stream, ps_tuning *h_out) {
     ps_status s;
     if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
@@ -710,9 +726,11 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, void *d_ws, 
     const size_t vec = (size_t)N * HW * sizeof(float);
     if (cudaMemsetAsync(ws.base + ws.L.st4, 0, HW * 16, st) != cudaSuccess ||
         cudaMemsetAsync(ws.base + ws.L.r, 0, vec, st) != cudaSuccess ||
-        cudaMemsetAsync(ws.base + ws.L.pA, 0, vec, st) != cudaSuccess ||
-        cudaMemsetAsync(ws.base + ws.L.bh32, 0, HW * 8, st) != cudaSuccess)
+        cudaMemsetAsync(ws.base + ws.L.pA, 0, vec, st) != cudaSuccess)
         return PS_ERR_CUDA;
+    // a kernel spectrum of ones: a zero one would make the DC group singular,
+    // and the NaN it spreads would end the timed CG iterations early
+    launch_fill(ws.at<float>(ws.L.bh32), 2 * HW, 1.0f, st);
     launch_fft_twiddles(W, ws.at<float2>(ws.L.twW32), ws.at<double2>(ws.L.twW64), st);
     launch_fft_twiddles(H, ws.at<float2>(ws.L.twH32), ws.at<double2>(ws.L.twH64), st);
     CgBand *bands = ws.at<CgBand>(ws.L.bands);
@@ -721,12 +739,14 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, void *d_ws, 
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return PS_ERR_CUDA;
     // best of three single launches, the CG scalars reset before each
-    auto timed = [&](auto launch) -> float {
+    auto timed = [&](auto launch, bool reset = true) -> float {
         float best = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
-            cudaMemsetAsync(bands, 0, N * sizeof(CgBand), st);
-            cudaMemsetAsync(g, 0, sizeof(CgGlobal), st);
-            cudaEventRecord(e0, st);
+            if (reset) {
+                cudaMemsetAsync(bands, 0, N * sizeof(CgBand), st);
+                cudaMemsetAsync(g, 0, sizeof(CgGlobal), st);
+                cudaEventRecord(e0, st);
+            }
             launch();
             cudaEventRecord(e1, st);
             cudaEventSynchronize(e1);
@@ -764,18 +784,58 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, void *d_ws, 
     la.g = g;
     la.cg = 1;
     float bestl = 1e30f;
+    const int pfs[3] = {2, 4, 6};
     for (int k = 0; k < 2; ++k) {
-        la.ty = llp_cgq2_rows(r, k);
-        out.llp_us[k] = timed([&] { launch_llp_cgq2(la, r, N, st); });
-        if (out.llp_us[k] < bestl) {
-            bestl = out.llp_us[k];
-            out.llp_rows = la.ty;
+        for (int q = 0; q < 3; ++q) {
+            la.ty = llp_cgq2_rows(r, k);
+            la.pf = pfs[q];
+            const float us = timed([&] { launch_llp_cgq2(la, r, N, st); });
+            out.llp_us[k * 3 + q] = us;
+            if (us < bestl) {
+                bestl = us;
+                out.llp_rows = la.ty;
+                out.llp_pf = la.pf;
+            }
+        }
+    }
+    // branches of the CG iteration, when the scene is given: whole solves of
+    // 20 iterations (tolerance out of reach) per candidate, on the caller's
+    // data; the solves' results go to scratch (the preconditioner's z buffer)
+    if (d_lrms && d_pan && d_kernel) {
+        ps_hrms_params hp;
+        ps_default_hrms_params(&hp);
+        hp.r = r;
+        hp.tol = 1e-30f;
+        hp.max_iter = 20;
+        const int splits[3] = {1, 2, 4};
+        float bests = 1e30f;
+        for (int k = 0; k < 3; ++k) {
+            if (splits[k] > 1 && N < 2 * splits[k]) continue;
+            tuning_set(dev, N, H, W, ratio, r,
+                       Tuning{out.prec_rows, out.llp_rows, splits[k], out.llp_pf});
+            float best = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, st);
+                s = ps_solve_hrms(d_lrms, d_pan, d_kernel, N, H, W, ratio, R, &hp, nullptr,
+                                  ws.at<float>(ws.L.z), nullptr, nullptr, d_ws, ws_bytes, stream);
+                if (s != PS_OK) return s;
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && ms < best) best = ms;  // the first run captures the graph
+            }
+            out.split_us[k] = best * 1000.f;
+            if (out.split_us[k] < bests) {
+                bests = out.split_us[k];
+                out.split = splits[k];
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if ((s = last_launch()) != PS_OK) return s;
-    tuning_set(dev, N, H, W, ratio, r, Tuning{out.prec_rows, out.llp_rows});
+    tuning_set(dev, N, H, W, ratio, r, Tuning{out.prec_rows, out.llp_rows, out.split, out.llp_pf});
     if (h_out) *h_out = out;
     return PS_OK;
 }

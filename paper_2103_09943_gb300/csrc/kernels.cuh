@@ -23,6 +23,7 @@ struct LlpArgs {
     const CgGlobal *g;
     int cg;
     int ty;             // CG mode: output rows per warp (0: default)
+    int pf;             // CG mode: rows the loads run ahead (2, 4 or 6; 0: 2)
 };
 
 // operators.cu
@@ -152,8 +153,11 @@ int llp_cgq2_rows(int r, int which);
 struct Tuning {
     int prec_rows;  // rows per CTA of the preconditioner's row passes (0: default)
     int llp_rows;   // output rows per warp of the CG-loop LLP kernel (0: default)
+    int split;      // parallel branches of the CG iteration (0: default)
+    int llp_pf;     // rows the LLP kernel's loads run ahead (0: default)
 };
 Tuning tuning_get(int dev, int N, int H, int W, int c, int r);
+void launch_fill(float *p, size_t n, float v, cudaStream_t st);
 void tuning_set(int dev, int N, int H, int W, int c, int r, const Tuning &t);
 
 // warm.cu

@@ -60,7 +60,7 @@ struct Llp2Rows {
     static constexpr int UNR = (RW == 1) ? 3 : 1;
 };
 
-template <int RW, int TY>
+template <int RW, int TY, int PF>
 __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
     constexpr int G = 2 * RW + 2;
     constexpr int VALID = 64 - 2 * G;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
             for (int d = 0; d <= RW; ++d) mub[e][d] = sb[e][d] = 0.f;
         }
         float mm2[2] = {0.f, 0.f}, mm1[2] = {0.f, 0.f}, m0[2] = {0.f, 0.f};
-        constexpr int PF = 2;
+        // loads run PF rows ahead of their use
         float2 qp[PF];
         float4 qs0[PF], qs1[PF];
         constexpr int PH = ((G + 1 + 2) / 3) * 3;
@@ -264,20 +264,30 @@ __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
     }
 }
 
-template <int RW, int TY>
+template <int RW, int TY, int PF>
 void launch_ty(const LlpArgs &a, int N, cudaStream_t st) {
     constexpr int G = 2 * RW + 2, VALID = 64 - 2 * G;
     const int rows = TY * kWarps;
     dim3 grd((a.W + VALID - 1) / VALID, (a.H + rows - 1) / rows, N);
-    llp_cgq2_kernel<RW, TY><<<grd, 32 * kWarps, 0, st>>>(a);
+    llp_cgq2_kernel<RW, TY, PF><<<grd, 32 * kWarps, 0, st>>>(a);
+}
+
+template <int RW, int TY>
+void launch_pf(const LlpArgs &a, int N, cudaStream_t st) {
+    if (a.pf == 6)
+        launch_ty<RW, TY, 6>(a, N, st);
+    else if (a.pf == 4)
+        launch_ty<RW, TY, 4>(a, N, st);
+    else
+        launch_ty<RW, TY, 2>(a, N, st);
 }
 
 template <int RW>
 void launch_r(const LlpArgs &a, int N, cudaStream_t st) {
     if (a.ty == Llp2Rows<RW>::SHORT)
-        launch_ty<RW, Llp2Rows<RW>::SHORT>(a, N, st);
+        launch_pf<RW, Llp2Rows<RW>::SHORT>(a, N, st);
     else
-        launch_ty<RW, Llp2Rows<RW>::LONG>(a, N, st);
+        launch_pf<RW, Llp2Rows<RW>::LONG>(a, N, st);
 }
 
 }  // namespace

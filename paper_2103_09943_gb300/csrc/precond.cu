@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(1024) prec_rows_fwd_kernel(PrecArgs a, RowGeom
 // Column pass with the group solves: columns kx0 + q w, q < C, of image k.
 // ---------------------------------------------------------------------------
 template <int C, int PER, bool P2>
-__global__ void __launch_bounds__(kPrecColThreads, 3) prec_cols_kernel(PrecArgs a, int tpr, int ld,
+__global__ void __launch_bounds__(kPrecColThreads, 4) prec_cols_kernel(PrecArgs a, int tpr, int ld,
                                                                      float scale) {
     extern __shared__ __align__(16) float2 psm[];
     const int k = blockIdx.y, kx0 = blockIdx.x;

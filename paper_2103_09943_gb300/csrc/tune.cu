@@ -25,7 +25,7 @@ Tuning tuning_get(int dev, int N, int H, int W, int c, int r) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (const Entry &e : g_tune)
         if (e.dev == dev && e.N == N && e.H == H && e.W == W && e.c == c && e.r == r) return e.t;
-    return Tuning{0, 0};
+    return Tuning{0, 0, 0, 0};
 }
 
 void tuning_set(int dev, int N, int H, int W, int c, int r, const Tuning &t) {
@@ -36,6 +36,24 @@ void tuning_set(int dev, int N, int H, int W, int c, int r, const Tuning &t) {
             return;
         }
     g_tune.push_back(Entry{dev, N, H, W, c, r, t});
+}
+
+}  // namespace ps
+
+namespace ps {
+
+namespace {
+__global__ void fill_kernel(float *p, size_t n, float v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+}  // namespace
+
+void launch_fill(float *p, size_t n, float v, cudaStream_t st) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    fill_kernel<<<blocks, 256, 0, st>>>(p, n, v);
 }
 
 }  // namespace ps
