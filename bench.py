@@ -527,6 +527,202 @@ def run_gpu(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# uneven batch: many scenes in one graph launch
+# ---------------------------------------------------------------------------
+def _scene_arrays(cfg):
+    import synth
+    sc = synth.make_scene(cfg)
+    return sc["lrms"], sc["pan"]
+
+
+def make_batch_scenes(count: int, seed0: int):
+    """The uneven batch (sides 512..2048, 4 or 8 bands, kernels 9x9..17x17),
+    generated on the host cores by spawned workers, before any CUDA call."""
+    import multiprocessing as mp
+    import synth
+    cfgs = synth.make_batch_configs(count, seed0)
+    workers = max(1, min(len(cfgs), os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        arrays = pool.map(_scene_arrays, cfgs, chunksize=1)
+    return cfgs, arrays
+
+
+def batch_name(cfgs) -> str:
+    sides = sorted({c.H for c in cfgs})
+    return (f"c3: {len(cfgs)} seeded synthetic scenes of uneven sizes in one graph launch, "
+            f"PAN sides {sides}, 4 or 8 bands, ratio 4, kernels {min(c.n for c in cfgs)}x"
+            f"{min(c.n for c in cfgs)} to {max(c.n for c in cfgs)}x{max(c.n for c in cfgs)} "
+            "estimated, LLP window radius 1; generated as the 8-band 1024x1024 workload")
+
+
+def _timed_steps(fn, steps, flush):
+    import torch
+    ev = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def run_batch(args):
+    rank, local_rank, world = dist_env()
+    t_gen = time.perf_counter()
+    cfgs, arrays = make_batch_scenes(args.batch, 3000 + 1000 * rank)
+    t_gen = time.perf_counter() - t_gen
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    init_dist(world, "nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2103_09943_gb300 import api
+
+    X = [torch.from_numpy(a[0]).to(dev) for a in arrays]
+    Y = [torch.from_numpy(a[1]).to(dev) for a in arrays]
+    units = sum(c.bands * c.H * c.W for c in cfgs)
+    kp = api.default_kernel_params()
+    net, warm_note = load_warm_net(args.warm, dev)
+    warm = {"none": 0, "bicubic": 1, "cnn": 2}[args.warm] if (net or args.warm != "cnn") else 0
+    hp = api.default_hrms_params(precond=1 if args.precond == "fft" else 0, warm=warm,
+                                 cnn_params=net.params.data_ptr() if net else None)
+    scenes = [(x, y, c.R) for x, y, c in zip(X, Y, cfgs)]
+    batch = api.Batch(scenes, cfgs[0].ratio, hparams=hp, kparams=kp, estimate=True)
+    kinfo, sinfo = batch.run(info=True)
+    for _ in range(max(args.warmup - 1, 0)):
+        batch.run()
+    torch.cuda.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    step_ms = _timed_steps(batch.run, args.steps, flush)
+    wall = time.perf_counter() - wall0
+    barrier(world)
+    clk = clocks.stop()
+    scene_ms = np.array(batch.scene_ms())
+    step_ms = reduce_max(step_ms, world, dev)
+    value = throughput(units, world, step_ms * 1e-3)
+
+    # end to end: pinned host inputs copied in and every HRMS copied out
+    # inside the timed region
+    hx = [torch.from_numpy(a[0]).pin_memory() for a in arrays]
+    hy = [torch.from_numpy(a[1]).pin_memory() for a in arrays]
+    ho = [torch.empty(t.shape, dtype=torch.float32).pin_memory() for t in batch.hrms]
+
+    def e2e_step():
+        for (x, y), a, b in zip(batch.inputs, hx, hy):
+            x.copy_(a, non_blocking=True)
+            y.copy_(b, non_blocking=True)
+        batch.run()
+        for o, t in zip(ho, batch.hrms):
+            o.copy_(t, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        e2e_step()
+        b.record()
+        b.synchronize()
+        e2e.append(a.elapsed_time(b))
+    e2e_ms = reduce_max(float(np.mean(e2e)), world, dev)
+    h2d = sum(t.numel() * 4 for t in hx + hy)
+    d2h = sum(t.numel() * 4 for t in ho)
+
+    # the same batch scene by scene (one ps_pansharpen call each), in this
+    # form and as the plain FP32 CG from zeros (the paper's solver)
+    variants = None
+    if rank == 0 and not args.no_compare:
+        variants = {}
+        forms = [("sequential_same_form", hp),
+                 ("sequential_plain_cg_cold", api.default_hrms_params(precond=0, warm=0))]
+        for name, p in forms:
+            wss = [api.workspace(c.bands, c.H, c.W, c.ratio, c.R, dev, p) for c in cfgs]
+
+            def seq(p=p, wss=wss):
+                for (x, y), c, w, o, k in zip(batch.inputs, cfgs, wss, batch.hrms,
+                                              batch.kernels):
+                    api.pansharpen(x, y, c.ratio, c.R, kp, p, ws=w, info=False, out=o,
+                                   kernel_out=k)
+
+            seq()
+            ms = _timed_steps(seq, max(1, min(args.steps, 2)), flush)
+            variants[name] = {"ms_per_step": ms, "value": throughput(units, 1, ms * 1e-3)}
+            del wss
+        pc = api.default_hrms_params(precond=0, warm=0)
+        bc = api.Batch(scenes, cfgs[0].ratio, hparams=pc, kparams=kp, estimate=True)
+        bc.run()
+        ms = _timed_steps(bc.run, max(1, min(args.steps, 2)), flush)
+        variants["batched_plain_cg_cold"] = {"ms_per_step": ms,
+                                             "value": throughput(units, 1, ms * 1e-3)}
+        del bc
+        variants["batched_same_form"] = {"ms_per_step": step_ms, "value": value}
+
+    # roofline of the CG iteration on the largest scene of the batch
+    big = max(range(len(cfgs)), key=lambda i: cfgs[i].bands * cfgs[i].H * cfgs[i].W)
+    peak, peak_kind = read_peaks()
+    roof = cg_iteration_roofline(api, X[big], Y[big], batch.kernels[big], cfgs[big], hp, peak,
+                                 dev)
+    roof["peak_note"] = f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)" \
+        if peak_kind == "measured" else "of fallback (6.8 TB/s)"
+    roof["scene"] = f"{cfgs[big].bands} x {cfgs[big].H}x{cfgs[big].W}, {cfgs[big].n}x{cfgs[big].n}"
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import synth
+        small = min(range(len(cfgs)), key=lambda i: cfgs[i].H)
+        cpu = cpu_baseline(synth.make_scene(cfgs[small]), args.cpu_crop)
+
+    iters = [n for si in sinfo for n in si.iters]
+    if rank == 0:
+        rec = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": batch_name(cfgs), "scenes_per_rank": len(cfgs),
+                       "px_band_per_rank": units,
+                       "parallelism": f"replicas x{world} (independent batches)",
+                       "l2": "inputs larger than L2 (and a 256 MiB write between steps)",
+                       "cg_tol": hp.tol, "cg_iters_mean": float(np.mean(iters)),
+                       "cg_iters_max": int(max(iters)),
+                       "cg_precond": ("FFT alias-group, gamma %g" % hp.precond_gamma)
+                       if hp.precond else "none",
+                       "warm_start": warm_note,
+                       "admm_iters_mean": float(np.mean([k.iters for k in kinfo])),
+                       "host_generation_s": t_gen},
+            "per_scene_finish_ms": {"p50": float(np.percentile(scene_ms, 50)),
+                                    "p99": float(np.percentile(scene_ms, 99)),
+                                    "max": float(scene_ms.max())},
+            "wall_s_timed_region": wall,
+            "e2e": {"value": throughput(units, world, e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_ms},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "variants": variants,
+        }
+        print(json.dumps(rec), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -551,6 +747,10 @@ def parse(argv=None):
     ap.add_argument("--precond", default="fft", choices=["fft", "none"],
                     help="preconditioner of the Z0 CG (fft: alias-group FFT solve; none: "
                          "plain CG as in the paper)")
+    ap.add_argument("--batch", type=int, default=0, metavar="SCENES",
+                    help="time the uneven batch of SCENES seeded scenes (sides 512..2048, "
+                         "4 or 8 bands, kernels 9x9..17x17) in one graph launch instead of "
+                         "the 8 x 1024^2 scene")
     ap.add_argument("--cg-loop", default="graph", choices=["graph", "host"],
                     help="host: launch the CG iterations from the host (for profilers "
                          "that cannot see inside conditional graphs)")
@@ -565,6 +765,8 @@ def main(argv=None):
         return run_profile_solve(args)
     if args.profile_warm:
         return run_profile_warm(args)
+    if args.batch:
+        return run_batch(args)
     return run_gpu(args)
 
 

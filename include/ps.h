@@ -207,6 +207,49 @@ ps_status ps_pansharpen(const float *d_lrms, const float *d_pan, int N, int H,
                         ps_band_info *h_binfo, void *d_ws, size_t ws_bytes,
                         void *stream);
 
+/* One scene of a batched call: device pointers and sizes as for
+ * ps_pansharpen / ps_solve_hrms. */
+typedef struct ps_scene {
+    const float *lrms;   /* N x h x w                                      */
+    const float *pan;    /* H x W                                          */
+    float *hrms;         /* out: N x H x W                                 */
+    float *kernel;       /* n x n, n = 2R + 1: written when the call
+                            estimates the kernel, read otherwise           */
+    int N, H, W, ratio, R;
+} ps_scene;
+
+/* Workspace bytes of ps_pansharpen_batched for these scenes: a header of
+ * (count + 1) timer stamps, then one ps_workspace_size slice per scene.
+ * 0 when a scene's sizes are invalid. */
+size_t ps_batch_workspace_size(const ps_scene *h_scenes, int count,
+                               const ps_hrms_params *h_hparams);
+
+/*
+ * Many scenes of uneven sizes (and band counts, and kernel supports) in one
+ * launch: Algorithm 1 for every scene when h_kparams is non-NULL (else each
+ * scene's kernel is given), then Algorithm 2 for all their bands, as
+ * ps_pansharpen / ps_solve_hrms would compute them one by one. The whole
+ * batch is one CUDA graph launched once: every scene is an independent
+ * branch whose CG loop is a device-side conditional node of its own, so
+ * small scenes run beside large ones and the GPU never waits on the host.
+ * The executable graph is built on the first call and reused while the
+ * scenes, parameters, workspace and tuning stay the same. host_loop must be
+ * 0. h_kinfo: count entries or NULL; h_binfo: sum of the scenes' N entries,
+ * in scene order, or NULL (either makes the call blocking). Scenes must not
+ * overlap in their outputs.
+ */
+ps_status ps_pansharpen_batched(const ps_scene *h_scenes, int count,
+                                const ps_kernel_params *h_kparams,
+                                const ps_hrms_params *h_hparams,
+                                ps_kernel_info *h_kinfo, ps_band_info *h_binfo,
+                                void *d_ws, size_t ws_bytes, void *stream);
+
+/* Finish time of every scene of the last batched call on this workspace,
+ * in milliseconds after the batch started on the device (the device's
+ * global timer). Synchronises the stream. h_ms: count entries. */
+ps_status ps_batch_scene_ms(const void *d_ws, int count, void *stream,
+                            double *h_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,13 @@ class KernelInfo(ctypes.Structure):
                 ("last_change", ctypes.c_double)]
 
 
+class Scene(ctypes.Structure):
+    _fields_ = [("lrms", ctypes.c_void_p), ("pan", ctypes.c_void_p),
+                ("hrms", ctypes.c_void_p), ("kernel", ctypes.c_void_p),
+                ("N", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("ratio", ctypes.c_int), ("R", ctypes.c_int)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _F = ctypes.c_float
@@ -67,6 +74,10 @@ SIGNATURES = {
     "ps_pansharpen": (_I, [_P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(KernelParams),
                            ctypes.POINTER(HrmsParams), _P, _P, ctypes.POINTER(KernelInfo),
                            _P, _P, _Z, _P]),
+    "ps_batch_workspace_size": (_Z, [ctypes.POINTER(Scene), _I, _P]),
+    "ps_pansharpen_batched": (_I, [ctypes.POINTER(Scene), _I, _P, ctypes.POINTER(HrmsParams),
+                                   _P, _P, _P, _Z, _P]),
+    "ps_batch_scene_ms": (_I, [_P, _I, _P, ctypes.POINTER(ctypes.c_double)]),
     "ps_op_blur_decimate": (_I, [_P, _I, _I, _I, _I, _P, _I, _P, _P]),
     "ps_op_blur_decimate_adj": (_I, [_P, _I, _I, _I, _I, _P, _I, _P, _P]),
     "ps_op_pan_stats": (_I, [_P, _I, _I, _I, _F, _P, _P, _P, _P]),

@@ -13,7 +13,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib
-from ._lib import BandInfo, HrmsParams, KernelInfo, KernelParams, Tuning
+from ._lib import BandInfo, HrmsParams, KernelInfo, KernelParams, Scene, Tuning
 
 
 class PsError(RuntimeError):
@@ -164,6 +164,65 @@ def pansharpen(lrms, pan, ratio: int, R: int, kparams: KernelParams | None = Non
         si = SolveInfo([b.status for b in bi], [b.iters for b in bi],
                        [b.rel_residual for b in bi])
     return hr, kern, (ki if info else None), si
+
+
+class Batch:
+    """Many scenes of uneven sizes in one graph launch (ps_pansharpen_batched).
+
+    scenes: list of (lrms (N,h,w), pan (H,W), R) on the device. Outputs
+    (hrms per scene, kernel per scene) and the workspace are allocated once;
+    run() launches the whole batch, estimating every kernel when
+    estimate=True, else using the kernels in self.kernels (fill them first).
+    """
+
+    def __init__(self, scenes, ratio: int, hparams: HrmsParams | None = None,
+                 kparams: KernelParams | None = None, estimate: bool = True):
+        self.hp = hparams or default_hrms_params()
+        self.kp = (kparams or default_kernel_params()) if estimate else None
+        self.inputs, self.hrms, self.kernels = [], [], []
+        arr = (Scene * len(scenes))()
+        for i, (lrms, pan, R) in enumerate(scenes):
+            _f32(lrms, "lrms"), _f32(pan, "pan")
+            N = lrms.shape[0]
+            H, W = pan.shape
+            hr = torch.empty((N, H, W), dtype=torch.float32, device=lrms.device)
+            kern = torch.zeros((2 * R + 1, 2 * R + 1), dtype=torch.float32, device=lrms.device)
+            self.inputs.append((lrms, pan))
+            self.hrms.append(hr)
+            self.kernels.append(kern)
+            arr[i] = Scene(lrms.data_ptr(), pan.data_ptr(), hr.data_ptr(), kern.data_ptr(),
+                           N, H, W, ratio, R)
+        self.scenes = arr
+        self.count = len(scenes)
+        self.bands = sum(t.shape[0] for t in self.hrms)
+        n = int(_lib.load().ps_batch_workspace_size(arr, self.count, ctypes.byref(self.hp)))
+        if n == 0:
+            raise PsError("invalid scene sizes for a batch")
+        self.ws = torch.empty(n, dtype=torch.uint8, device=scenes[0][0].device)
+
+    def run(self, info: bool = False):
+        """Launch the batch. With info, block and return (list of KernelInfo
+        or None, list of SolveInfo per scene)."""
+        ki = (KernelInfo * self.count)() if info and self.kp is not None else None
+        bi = (BandInfo * self.bands)() if info else None
+        _check(_lib.load().ps_pansharpen_batched(
+            self.scenes, self.count, ctypes.byref(self.kp) if self.kp is not None else None,
+            ctypes.byref(self.hp), ki, bi, _ptr(self.ws), self.ws.numel(), _stream()))
+        if not info:
+            return None
+        out, k = [], 0
+        for hr in self.hrms:
+            n = hr.shape[0]
+            out.append(SolveInfo([b.status for b in bi[k:k + n]], [b.iters for b in bi[k:k + n]],
+                                 [b.rel_residual for b in bi[k:k + n]]))
+            k += n
+        return (list(ki) if ki is not None else None), out
+
+    def scene_ms(self) -> list:
+        """Finish time of every scene of the last run, ms after it started."""
+        ms = (ctypes.c_double * self.count)()
+        _check(_lib.load().ps_batch_scene_ms(_ptr(self.ws), self.count, _stream(), ms))
+        return list(ms)
 
 
 class HostPipeline:

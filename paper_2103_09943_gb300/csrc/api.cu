@@ -329,6 +329,36 @@ void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, in
     launch_cg_control(a.bands, a.g, a.N, use_cond, h, st);
 }
 
+// Adds to `graph`, after `deps`, the CG loop of `a`: a conditional WHILE node
+// (its handle starts at 1, and cg_control clears it once every band has
+// stopped) whose body, captured on `capture`, holds two iterations.
+ps_status add_cg_loop_node(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t ndeps,
+                           const CgLoopArgs &a, cudaStream_t capture, cudaGraphNode_t *node) {
+    cudaGraphConditionalHandle handle;
+    if (cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault) !=
+        cudaSuccess)
+        return PS_ERR_CUDA;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(node, graph, deps, nullptr, ndeps, &cp) != cudaSuccess)
+        return PS_ERR_CUDA;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(capture, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return PS_ERR_CUDA;
+    enqueue_iteration(a, a.pA, a.pB, 1, handle, capture);
+    enqueue_iteration(a, a.pB, a.pA, 1, handle, capture);
+    cudaGraph_t captured = nullptr;
+    if (cudaStreamEndCapture(capture, &captured) != cudaSuccess) {
+        cudaGetLastError();
+        return PS_ERR_CUDA;
+    }
+    return PS_OK;
+}
+
 ps_status get_cg_graph(const CgLoopArgs &a, cudaStream_t capture, cudaGraphExec_t *out) {
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -340,39 +370,14 @@ ps_status get_cg_graph(const CgLoopArgs &a, cudaStream_t capture, cudaGraphExec_
     }
     cudaGraph_t graph = nullptr;
     if (cudaGraphCreate(&graph, 0) != cudaSuccess) return PS_ERR_CUDA;
-    cudaGraphConditionalHandle handle;
-    if (cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault) !=
-        cudaSuccess) {
-        cudaGraphDestroy(graph);
-        return PS_ERR_CUDA;
-    }
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = handle;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
     cudaGraphNode_t node;
-    if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+    ps_status s = add_cg_loop_node(graph, nullptr, 0, a, capture, &node);
+    if (s != PS_OK) {
         cudaGraphDestroy(graph);
-        return PS_ERR_CUDA;
-    }
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if (cudaStreamBeginCaptureToGraph(capture, body, nullptr, nullptr, 0,
-                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        return PS_ERR_CUDA;
-    }
-    enqueue_iteration(a, a.pA, a.pB, 1, handle, capture);
-    enqueue_iteration(a, a.pB, a.pA, 1, handle, capture);
-    cudaGraph_t captured = nullptr;
-    cudaError_t e = cudaStreamEndCapture(capture, &captured);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        cudaGraphDestroy(graph);
-        return PS_ERR_CUDA;
+        return s;
     }
     cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, graph, 0);
+    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return PS_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -464,6 +469,245 @@ ps_status run_zstep(const Ws &ws, const float *lrms, const float *z0, const floa
     launch_transpose32(sol32, ctmp32, W, H, nimg, st);
     launch_fft_rows32(ctmp32, pw, nimg * H, twW32, 1, out, N, HW, st);
     return last_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Stages of ps_solve_hrms, shared with the batched entry point: everything
+// before the CG loop (PAN statistics, spectra, right-hand side, start point,
+// CG state), and the Z step after it. Neither synchronises, so both can be
+// captured into a graph.
+// ---------------------------------------------------------------------------
+struct SolveCall {
+    Ws ws;
+    size_t ws_bytes;
+    const float *lrms, *pan, *u, *z_init;
+    float *hrms, *z0;
+    int N, H, W, c, R;
+    ps_hrms_params p;
+};
+
+ps_status make_solve_call(const float *d_lrms, const float *d_pan, const float *d_kernel, int N,
+                          int H, int W, int ratio, int R, const ps_hrms_params *p,
+                          const float *d_z_init, float *d_hrms, float *d_z0, void *d_ws,
+                          size_t ws_bytes, SolveCall *sc) {
+    ps_status s;
+    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
+    if ((s = check_fft_dims(H, W)) != PS_OK) return s;
+    if ((s = check_hrms(p)) != PS_OK) return s;
+    if (p->precond && !precond_supported(H, W, ratio)) return PS_ERR_UNSUPPORTED;
+    if (!d_lrms || !d_pan || !d_kernel || !d_hrms) return PS_ERR_INVALID_ARG;
+    if ((d_z0 && !aligned16(d_z0)) || (d_z_init && !aligned16(d_z_init)))
+        return PS_ERR_INVALID_ARG;
+    if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &sc->ws)) != PS_OK) return s;
+    if (p->warm == 2 && !d_z_init && ws_bytes < sc->ws.L.cnn + ps_cnn_workspace_size(N, H, W, 0))
+        return PS_ERR_WORKSPACE;
+    sc->ws_bytes = ws_bytes;
+    sc->lrms = d_lrms;
+    sc->pan = d_pan;
+    sc->u = d_kernel;
+    sc->z_init = d_z_init;
+    sc->hrms = d_hrms;
+    sc->z0 = d_z0;
+    sc->N = N;
+    sc->H = H;
+    sc->W = W;
+    sc->c = ratio;
+    sc->R = R;
+    sc->p = *p;
+    return PS_OK;
+}
+
+ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
+    ps_status s;
+    const Ws &ws = sc.ws;
+    const ps_hrms_params *p = &sc.p;
+    const int N = sc.N, H = sc.H, W = sc.W, c = sc.c, R = sc.R;
+    const float *d_kernel = sc.u, *d_lrms = sc.lrms, *d_z_init = sc.z_init;
+    const size_t HW = (size_t)H * W;
+    float4 *st4 = ws.at<float4>(ws.L.st4);
+    float *x = sc.z0 ? sc.z0 : ws.at<float>(ws.L.xbuf);
+    float *rv = ws.at<float>(ws.L.r), *ap = ws.at<float>(ws.L.ap), *v = ws.at<float>(ws.L.v);
+    CgBand *bands = ws.at<CgBand>(ws.L.bands);
+    CgGlobal *g = ws.at<CgGlobal>(ws.L.glob);
+
+    launch_pan_stats(sc.pan, H, W, p->r, p->eps, nullptr, nullptr, nullptr, st4, st);
+    if ((s = prepare_spectrum(ws, d_kernel, H, W, R, st)) != PS_OK) return s;
+    launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
+    if (!d_z_init && p->warm >= 1) {
+        // bicubic start point, written where the iterate lives
+        launch_bicubic_up(d_lrms, N, H / c, W / c, c, x, st);
+        if (p->warm == 2) {
+            // the network on (bicubic, PAN), in place: its last layer reads
+            // the bicubic value of a pixel and writes the result there
+            if ((s = ps_cnn_forward(p->cnn_params, x, sc.pan, 0, N, H, W, x,
+                                    ws.base + ws.L.cnn, sc.ws_bytes - ws.L.cnn, st)) != PS_OK)
+                return s;
+        }
+        d_z_init = x;
+    }
+    if (d_z_init) {
+        launch_db(d_z_init, nullptr, nullptr, nullptr, nullptr, 0, N, H, W, c, d_kernel, R, v,
+                  st);
+        LlpArgs la = {};
+        la.in = d_z_init;
+        la.lr = v;
+        la.st4 = st4;
+        la.u = d_kernel;
+        la.R = R;
+        la.c = c;
+        la.H = H;
+        la.W = W;
+        la.N = N;
+        la.lam = p->lambda;
+        la.out = ap;
+        launch_llp(la, LLP_APPLY, p->r, N, st);
+    }
+    launch_cg_reset(bands, g, N, (double)p->tol, p->max_iter, p->precond, st);
+    launch_cg_init(rv, d_z_init ? ap : nullptr, d_z_init, x, rv, N, HW, bands, g, st);
+    PrecArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    if (p->precond) {
+        // z0 = P^{-1} r0, rho = r0^T z0 (the first direction is p = z0)
+        pa = make_prec_args(ws, rv, ws.at<float>(ws.L.z), N, H, W, c,
+                            p->lambda * p->precond_gamma, bands, g);
+        launch_precond(pa, st);
+    }
+    if ((s = last_launch()) != PS_OK) return s;
+
+    memset(a, 0, sizeof(*a));
+    cudaGetDevice(&a->dev);
+    a->N = N; a->H = H; a->W = W; a->c = c; a->R = R; a->r = p->r; a->lam = p->lambda;
+    a->u = d_kernel; a->st4 = st4;
+    a->x = x; a->rv = rv; a->pA = ws.at<float>(ws.L.pA); a->pB = ws.at<float>(ws.L.pB);
+    a->ap = ap; a->v = v;
+    a->bands = bands; a->g = g;
+    a->precond = p->precond;
+    a->pa = pa;
+    a->tune = tuning_get(a->dev, N, H, W, c, p->r);
+    a->split = a->tune.split ? a->tune.split : ((N >= 4) ? 2 : 1);
+    return PS_OK;
+}
+
+ps_status solve_epilogue(const SolveCall &sc, const CgLoopArgs &a, cudaStream_t st) {
+    const ps_hrms_params *p = &sc.p;
+    const float lam_z =
+        p->lambda * (p->exact_weight ? (float)((2 * p->r + 1) * (2 * p->r + 1)) : 1.0f);
+    return run_zstep(sc.ws, sc.lrms, a.x, sc.u, sc.N, sc.H, sc.W, sc.c, sc.R, p->r, lam_z,
+                     sc.hrms, st);
+}
+
+// Per-band CG results (after the work that wrote them has finished).
+ps_status read_band_info(const CgBand *d_bands, int N, ps_band_info *h_info) {
+    std::vector<CgBand> hb(N);
+    if (cudaMemcpy(hb.data(), d_bands, N * sizeof(CgBand), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return PS_ERR_CUDA;
+    for (int b = 0; b < N; ++b) {
+        h_info[b].status = hb[b].status;
+        h_info[b].iters = hb[b].iters;
+        h_info[b].rel_residual = hb[b].bb > 0.0 ? sqrt(hb[b].rr / hb[b].bb) : 0.0;
+    }
+    return PS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched scenes: one executable graph holds every scene of the batch. Each
+// scene is an independent branch: its prelude (kernel estimate when asked,
+// then the stages before the CG loop), its CG loop as a conditional WHILE
+// node of its own, and its Z step. The branches are added largest scene
+// first. A timer stamp opens the graph and closes every scene.
+// ---------------------------------------------------------------------------
+constexpr int kMaxBatch = 4096;
+
+size_t batch_header_bytes(int count) { return align_up((size_t)(count + 1) * 8); }
+
+size_t scene_ws_bytes(const ps_scene &q, const ps_hrms_params *hp) {
+    return align_up(ps_workspace_size(q.N, q.H, q.W, q.ratio, q.R, hp));
+}
+
+struct BatchGraph {
+    std::vector<char> key;
+    cudaGraphExec_t exec;
+};
+std::vector<BatchGraph> g_batch;
+
+template <class T>
+void key_put(std::vector<char> &k, const T &v) {
+    const char *b = reinterpret_cast<const char *>(&v);
+    k.insert(k.end(), b, b + sizeof(T));
+}
+
+// Captures what `enqueue` launches on `capture` and adds it to `graph` as a
+// child-graph node after `deps`.
+template <class F>
+ps_status capture_child(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t ndeps,
+                        cudaStream_t capture, F &&enqueue, cudaGraphNode_t *node) {
+    if (cudaStreamBeginCapture(capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return PS_ERR_CUDA;
+    ps_status s = enqueue(capture);
+    cudaGraph_t child = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(capture, &child);
+    if (s == PS_OK && e != cudaSuccess) s = PS_ERR_CUDA;
+    if (s == PS_OK && cudaGraphAddChildGraphNode(node, graph, deps, ndeps, child) != cudaSuccess)
+        s = PS_ERR_CUDA;
+    if (child) cudaGraphDestroy(child);
+    if (s != PS_OK) cudaGetLastError();
+    return s;
+}
+
+ps_status build_batch_graph(const ps_scene *scenes, int count, const ps_kernel_params *kp,
+                            const std::vector<SolveCall> &calls, unsigned long long *stamps,
+                            cudaStream_t capture, cudaGraphExec_t *out) {
+    cudaGraph_t graph = nullptr;
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) return PS_ERR_CUDA;
+    ps_status s;
+    cudaGraphNode_t root;
+    s = capture_child(graph, nullptr, 0, capture,
+                      [&](cudaStream_t st) {
+                          launch_stamp(stamps, st);
+                          return last_launch();
+                      },
+                      &root);
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const ps_scene &a = scenes[x], &b = scenes[y];
+        return (double)a.N * a.H * a.W > (double)b.N * b.H * b.W;
+    });
+    for (int k = 0; k < count && s == PS_OK; ++k) {
+        const int i = order[k];
+        const ps_scene &q = scenes[i];
+        const SolveCall &sc = calls[i];
+        CgLoopArgs a;
+        cudaGraphNode_t pre, loop, post;
+        s = capture_child(graph, &root, 1, capture,
+                          [&](cudaStream_t st) {
+                              ps_status e = PS_OK;
+                              if (kp)
+                                  e = ps_estimate_kernel(q.lrms, q.pan, q.N, q.H, q.W, q.ratio,
+                                                         q.R, kp, nullptr, q.kernel, nullptr,
+                                                         nullptr, sc.ws.base, sc.ws_bytes, st);
+                              if (e == PS_OK) e = solve_prelude(sc, st, &a);
+                              return e;
+                          },
+                          &pre);
+        if (s == PS_OK) {
+            // concurrency comes from the scenes: one branch per iteration
+            a.split = 1;
+            s = add_cg_loop_node(graph, &pre, 1, a, capture, &loop);
+        }
+        if (s == PS_OK)
+            s = capture_child(graph, &loop, 1, capture,
+                              [&](cudaStream_t st) {
+                                  ps_status e = solve_epilogue(sc, a, st);
+                                  launch_stamp(stamps + 1 + i, st);
+                                  return e == PS_OK ? last_launch() : e;
+                              },
+                              &post);
+    }
+    if (s == PS_OK && cudaGraphInstantiate(out, graph, 0) != cudaSuccess) s = PS_ERR_CUDA;
+    cudaGraphDestroy(graph);
+    return s;
 }
 
 }  // namespace
@@ -589,94 +833,25 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
                         const float *d_z_init, float *d_hrms, float *d_z0,
                         ps_band_info *h_info, void *d_ws, size_t ws_bytes, void *stream) {
     ps_status s;
-    if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
-    if ((s = check_fft_dims(H, W)) != PS_OK) return s;
-    if ((s = check_hrms(p)) != PS_OK) return s;
-    if (p->precond && !precond_supported(H, W, ratio)) return PS_ERR_UNSUPPORTED;
-    if (!d_lrms || !d_pan || !d_kernel || !d_hrms) return PS_ERR_INVALID_ARG;
-    if ((d_z0 && !aligned16(d_z0)) || (d_z_init && !aligned16(d_z_init)))
-        return PS_ERR_INVALID_ARG;
-    Ws ws;
-    if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
+    SolveCall sc;
+    if ((s = make_solve_call(d_lrms, d_pan, d_kernel, N, H, W, ratio, R, p, d_z_init, d_hrms,
+                             d_z0, d_ws, ws_bytes, &sc)) != PS_OK)
+        return s;
     cudaStream_t capture = nullptr;
     if ((s = ensure_device(&capture)) != PS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    const int c = ratio;
-    const size_t HW = (size_t)H * W;
-    float4 *st4 = ws.at<float4>(ws.L.st4);
-    float *x = d_z0 ? d_z0 : ws.at<float>(ws.L.xbuf);
-    float *rv = ws.at<float>(ws.L.r), *pA = ws.at<float>(ws.L.pA), *pB = ws.at<float>(ws.L.pB),
-          *ap = ws.at<float>(ws.L.ap), *v = ws.at<float>(ws.L.v);
-    CgBand *bands = ws.at<CgBand>(ws.L.bands);
-    CgGlobal *g = ws.at<CgGlobal>(ws.L.glob);
-
-    launch_pan_stats(d_pan, H, W, p->r, p->eps, nullptr, nullptr, nullptr, st4, st);
-    if ((s = prepare_spectrum(ws, d_kernel, H, W, R, st)) != PS_OK) return s;
-    launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
-    if (!d_z_init && p->warm >= 1) {
-        // bicubic start point, written where the iterate lives
-        launch_bicubic_up(d_lrms, N, H / c, W / c, c, x, st);
-        if (p->warm == 2) {
-            // the network on (bicubic, PAN), in place: its last layer reads
-            // the bicubic value of a pixel and writes the result there
-            const size_t need = ws.L.cnn + ps_cnn_workspace_size(N, H, W, 0);
-            if (ws_bytes < need) return PS_ERR_WORKSPACE;
-            if ((s = ps_cnn_forward(p->cnn_params, x, d_pan, 0, N, H, W, x,
-                                    ws.base + ws.L.cnn, ws_bytes - ws.L.cnn, stream)) != PS_OK)
-                return s;
-        }
-        d_z_init = x;
-    }
-    if (d_z_init) {
-        launch_db(d_z_init, nullptr, nullptr, nullptr, nullptr, 0, N, H, W, c, d_kernel, R, v,
-                  st);
-        LlpArgs la = {};
-        la.in = d_z_init;
-        la.lr = v;
-        la.st4 = st4;
-        la.u = d_kernel;
-        la.R = R;
-        la.c = c;
-        la.H = H;
-        la.W = W;
-        la.N = N;
-        la.lam = p->lambda;
-        la.out = ap;
-        launch_llp(la, LLP_APPLY, p->r, N, st);
-    }
-    launch_cg_reset(bands, g, N, (double)p->tol, p->max_iter, p->precond, st);
-    launch_cg_init(rv, d_z_init ? ap : nullptr, d_z_init, x, rv, N, HW, bands, g, st);
-    PrecArgs pa;
-    memset(&pa, 0, sizeof(pa));
-    if (p->precond) {
-        // z0 = P^{-1} r0, rho = r0^T z0 (the first direction is p = z0)
-        pa = make_prec_args(ws, rv, ws.at<float>(ws.L.z), N, H, W, c,
-                            p->lambda * p->precond_gamma, bands, g);
-        launch_precond(pa, st);
-    }
-    if ((s = last_launch()) != PS_OK) return s;
-
     CgLoopArgs a;
-    memset(&a, 0, sizeof(a));
-    cudaGetDevice(&a.dev);
-    a.N = N; a.H = H; a.W = W; a.c = c; a.R = R; a.r = p->r; a.lam = p->lambda;
-    a.u = d_kernel; a.st4 = st4;
-    a.x = x; a.rv = rv; a.pA = pA; a.pB = pB; a.ap = ap; a.v = v;
-    a.bands = bands; a.g = g;
-    a.precond = p->precond;
-    a.pa = pa;
-    a.tune = tuning_get(a.dev, N, H, W, c, p->r);
-    a.split = a.tune.split ? a.tune.split : ((N >= 4) ? 2 : 1);
+    if ((s = solve_prelude(sc, st, &a)) != PS_OK) return s;
     if (p->host_loop) {
         // same kernels, launched by the host; the stop flag is read every 8
         // iterations, and the loop is bounded by max_iter whatever it says
         int stop = 0;
         for (int it = 0; it < p->max_iter + 2 && !stop; it += 2) {
-            enqueue_iteration(a, pA, pB, 0, 0, st);
-            enqueue_iteration(a, pB, pA, 0, 0, st);
+            enqueue_iteration(a, a.pA, a.pB, 0, 0, st);
+            enqueue_iteration(a, a.pB, a.pA, 0, 0, st);
             if ((it & 7) == 6 || it + 2 >= p->max_iter + 2) {
-                if (cudaMemcpyAsync(&stop, &g->stop, sizeof(int), cudaMemcpyDeviceToHost, st) !=
-                        cudaSuccess ||
+                if (cudaMemcpyAsync(&stop, &a.g->stop, sizeof(int), cudaMemcpyDeviceToHost,
+                                    st) != cudaSuccess ||
                     cudaStreamSynchronize(st) != cudaSuccess)
                     return PS_ERR_CUDA;
             }
@@ -687,21 +862,10 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
         if ((s = get_cg_graph(a, capture, &exec)) != PS_OK) return s;
         if (cudaGraphLaunch(exec, st) != cudaSuccess) return PS_ERR_CUDA;
     }
-
-    const float lam_z = p->lambda * (p->exact_weight ? (float)((2 * p->r + 1) * (2 * p->r + 1)) : 1.0f);
-    if ((s = run_zstep(ws, d_lrms, x, d_kernel, N, H, W, c, R, p->r, lam_z, d_hrms, st)) != PS_OK)
-        return s;
+    if ((s = solve_epilogue(sc, a, st)) != PS_OK) return s;
     if (h_info) {
-        std::vector<CgBand> hb(N);
-        if (cudaMemcpyAsync(hb.data(), bands, N * sizeof(CgBand), cudaMemcpyDeviceToHost, st) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return PS_ERR_CUDA;
-        for (int b = 0; b < N; ++b) {
-            h_info[b].status = hb[b].status;
-            h_info[b].iters = hb[b].iters;
-            h_info[b].rel_residual = hb[b].bb > 0.0 ? sqrt(hb[b].rr / hb[b].bb) : 0.0;
-        }
+        if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ERR_CUDA;
+        if ((s = read_band_info(a.bands, N, h_info)) != PS_OK) return s;
     }
     return PS_OK;
 }
@@ -857,6 +1021,149 @@ ps_status ps_pansharpen(const float *d_lrms, const float *d_pan, int N, int H, i
         return s;
     return ps_solve_hrms(d_lrms, d_pan, kern, N, H, W, ratio, R, hp, nullptr, d_hrms, nullptr,
                          h_binfo, d_ws, ws_bytes, stream);
+}
+
+size_t ps_batch_workspace_size(const ps_scene *scenes, int count, const ps_hrms_params *hp) {
+    if (!scenes || count < 1 || count > kMaxBatch) return 0;
+    size_t total = batch_header_bytes(count);
+    for (int i = 0; i < count; ++i) {
+        const size_t b = scene_ws_bytes(scenes[i], hp);
+        if (b == 0) return 0;
+        total += b;
+    }
+    return total;
+}
+
+ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kernel_params *kp,
+                                const ps_hrms_params *hp, ps_kernel_info *h_kinfo,
+                                ps_band_info *h_binfo, void *d_ws, size_t ws_bytes,
+                                void *stream) {
+    ps_status s;
+    if (!scenes || count < 1 || count > kMaxBatch) return PS_ERR_INVALID_ARG;
+    if ((s = check_hrms(hp)) != PS_OK) return s;
+    if (hp->host_loop) return PS_ERR_INVALID_ARG;
+    if (kp && (s = check_kernel_params(kp)) != PS_OK) return s;
+    if (!d_ws || ((uintptr_t)d_ws) % kAlign) return PS_ERR_WORKSPACE;
+    for (int i = 0; i < count; ++i) {
+        const ps_scene &q = scenes[i];
+        if ((s = check_dims(q.N, q.H, q.W, q.ratio, q.R)) != PS_OK) return s;
+        if (!q.kernel) return PS_ERR_INVALID_ARG;
+    }
+    if (ws_bytes < ps_batch_workspace_size(scenes, count, hp)) return PS_ERR_WORKSPACE;
+    char *base = static_cast<char *>(d_ws);
+    std::vector<SolveCall> calls(count);
+    size_t off = batch_header_bytes(count);
+    for (int i = 0; i < count; ++i) {
+        const ps_scene &q = scenes[i];
+        const size_t b = scene_ws_bytes(q, hp);
+        if ((s = make_solve_call(q.lrms, q.pan, q.kernel, q.N, q.H, q.W, q.ratio, q.R, hp,
+                                 nullptr, q.hrms, nullptr, base + off, b, &calls[i])) != PS_OK)
+            return s;
+        off += b;
+    }
+    cudaStream_t capture = nullptr;
+    if ((s = ensure_device(&capture)) != PS_OK) return s;
+    std::vector<char> key;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    key_put(key, dev);
+    key_put(key, count);
+    key_put(key, d_ws);
+    // field by field: the callers' structs may carry uninitialised padding
+    key_put(key, hp->lambda);
+    key_put(key, hp->r);
+    key_put(key, hp->eps);
+    key_put(key, hp->tol);
+    key_put(key, hp->max_iter);
+    key_put(key, hp->exact_weight);
+    key_put(key, hp->precond);
+    key_put(key, hp->precond_gamma);
+    key_put(key, hp->warm);
+    key_put(key, hp->cnn_params);
+    key_put(key, kp != nullptr);
+    if (kp) {
+        key_put(key, kp->lambda_omega);
+        key_put(key, kp->l);
+        key_put(key, kp->alpha1);
+        key_put(key, kp->alpha2);
+        key_put(key, kp->mu1);
+        key_put(key, kp->mu2);
+        key_put(key, kp->mu3);
+        key_put(key, kp->rho);
+        key_put(key, kp->t_max);
+        key_put(key, kp->th);
+    }
+    for (int i = 0; i < count; ++i) {
+        const ps_scene &q = scenes[i];
+        key_put(key, q.lrms);
+        key_put(key, q.pan);
+        key_put(key, q.hrms);
+        key_put(key, q.kernel);
+        const int dims[5] = {q.N, q.H, q.W, q.ratio, q.R};
+        key_put(key, dims);
+        const Tuning t = tuning_get(dev, q.N, q.H, q.W, q.ratio, hp->r);
+        const int tk[4] = {t.prec_rows, t.llp_rows, t.split, t.llp_pf};
+        key_put(key, tk);
+    }
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        for (auto &e : g_batch)
+            if (e.key == key) exec = e.exec;
+    }
+    if (!exec) {
+        unsigned long long *stamps = reinterpret_cast<unsigned long long *>(base);
+        if ((s = build_batch_graph(scenes, count, kp, calls, stamps, capture, &exec)) != PS_OK)
+            return s;
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_batch.size() >= 4) {
+            cudaGraphExecDestroy(g_batch.front().exec);
+            g_batch.erase(g_batch.begin());
+        }
+        g_batch.push_back({key, exec});
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaGraphLaunch(exec, st) != cudaSuccess) return PS_ERR_CUDA;
+    if (h_kinfo || h_binfo) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ERR_CUDA;
+        int nb = 0;
+        for (int i = 0; i < count; ++i) {
+            const Ws &ws = calls[i].ws;
+            if (h_binfo) {
+                if ((s = read_band_info(ws.at<CgBand>(ws.L.bands), scenes[i].N, h_binfo + nb)) !=
+                    PS_OK)
+                    return s;
+                nb += scenes[i].N;
+            }
+            if (h_kinfo) {
+                int hi[2] = {0, 0};
+                double ch = 0.0;
+                if (kp) {
+                    const int *ki = ws.at<int>(ws.L.kinfo);
+                    if (cudaMemcpy(hi, ki, sizeof(hi), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                        cudaMemcpy(&ch, ki + 2, sizeof(double), cudaMemcpyDeviceToHost) !=
+                            cudaSuccess)
+                        return PS_ERR_CUDA;
+                }
+                h_kinfo[i].iters = hi[0];
+                h_kinfo[i].status = hi[1];
+                h_kinfo[i].last_change = ch;
+            }
+        }
+    }
+    return PS_OK;
+}
+
+ps_status ps_batch_scene_ms(const void *d_ws, int count, void *stream, double *h_ms) {
+    if (!d_ws || !h_ms || count < 1 || count > kMaxBatch) return PS_ERR_INVALID_ARG;
+    std::vector<unsigned long long> t(count + 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(t.data(), d_ws, t.size() * 8, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return PS_ERR_CUDA;
+    for (int i = 0; i < count; ++i) h_ms[i] = (double)(long long)(t[1 + i] - t[0]) * 1e-6;
+    return PS_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -44,6 +44,7 @@ void launch_cg_init(const float *bvec, const float *ax0, const float *x0, float 
 void launch_cg_update(float *x, float *r, const float *p, const float *q, const float *v,
                       const float *u, int R, int c, int N, int H, int W, CgBand *bands,
                       const CgGlobal *g, cudaStream_t st);
+void launch_stamp(unsigned long long *t, cudaStream_t st);
 void launch_cg_control(CgBand *bands, CgGlobal *g, int N, int use_cond,
                        cudaGraphConditionalHandle handle, cudaStream_t st);
 cudaError_t operators_set_attrs();

@@ -830,4 +830,14 @@ void launch_cg_control(CgBand *bands, CgGlobal *g, int N, int use_cond,
     cg_control_kernel<<<1, 32, 0, st>>>(bands, g, N, use_cond, handle);
 }
 
+// The device's global nanosecond timer, written by one thread: marks where
+// a scene of a batched call starts and ends inside the one graph launch.
+__global__ void stamp_kernel(unsigned long long *t) {
+    unsigned long long v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    *t = v;
+}
+
+void launch_stamp(unsigned long long *t, cudaStream_t st) { stamp_kernel<<<1, 1, 0, st>>>(t); }
+
 }  // namespace ps

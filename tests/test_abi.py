@@ -134,3 +134,40 @@ def test_argument_errors_return_before_launch(lib):
     st = lib.ps_pansharpen(fake, fake, 4, 256, 256, 4, 17, ctypes.byref(kp), ctypes.byref(hp),
                            fake, None, None, None, fake, 1 << 30, None)
     assert st == 1                                                  # R > 16
+
+
+def test_batched_argument_errors_return_before_launch(lib):
+    from paper_2103_09943_gb300._lib import HrmsParams, KernelParams, Scene
+    hp = HrmsParams()
+    lib.ps_default_hrms_params(ctypes.byref(hp))
+    kp = KernelParams()
+    lib.ps_default_kernel_params(ctypes.byref(kp))
+    f = 0x1000
+    arr = (Scene * 3)(Scene(f, f, f, f, 4, 512, 512, 4, 4), Scene(f, f, f, f, 8, 768, 768, 4, 8),
+                      Scene(f, f, f, f, 4, 1536, 1536, 4, 6))
+    need = lib.ps_batch_workspace_size(arr, 3, ctypes.byref(hp))
+    singles = sum(lib.ps_workspace_size(s.N, s.H, s.W, s.ratio, s.R, ctypes.byref(hp))
+                  for s in arr)
+    assert need >= singles + 4 * 8
+    ws = ctypes.c_void_p(0x100000)
+    # workspace too small, misaligned
+    assert lib.ps_pansharpen_batched(arr, 3, ctypes.byref(kp), ctypes.byref(hp), None, None,
+                                     ws, need - 1, None) == 4
+    assert lib.ps_pansharpen_batched(arr, 3, ctypes.byref(kp), ctypes.byref(hp), None, None,
+                                     ctypes.c_void_p(0x100010), need, None) == 4
+    # the batch is one graph: no host-driven loop
+    bad = HrmsParams.from_buffer_copy(hp)
+    bad.host_loop = 1
+    assert lib.ps_pansharpen_batched(arr, 3, ctypes.byref(kp), ctypes.byref(bad), None, None,
+                                     ws, need, None) == 1
+    # empty batch, one bad scene among good ones
+    assert lib.ps_pansharpen_batched(arr, 0, ctypes.byref(kp), ctypes.byref(hp), None, None,
+                                     ws, need, None) == 1
+    arr[1].H = 770
+    assert lib.ps_batch_workspace_size(arr, 3, ctypes.byref(hp)) == 0
+    assert lib.ps_pansharpen_batched(arr, 3, ctypes.byref(kp), ctypes.byref(hp), None, None,
+                                     ws, need, None) == 2
+    arr[1].H = 768
+    arr[2].kernel = None
+    assert lib.ps_pansharpen_batched(arr, 3, ctypes.byref(kp), ctypes.byref(hp), None, None,
+                                     ws, need, None) == 1

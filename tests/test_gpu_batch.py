@@ -1,0 +1,128 @@
+"""GPU parity of the batched entry point (ps_pansharpen_batched): scenes of
+uneven sizes, band counts and kernel supports in one graph launch give, scene
+by scene, what the FP64 oracle gives (Algorithm 1 then Algorithm 2), and what
+the one-scene calls give; kernels given or estimated; the network's warm
+start inside the batch; per-scene finish times."""
+import os
+from dataclasses import replace
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2103_09943_gb300 import api
+from tests.gpu_util import rel, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+WEIGHTS = os.path.join(ROOT, "paper_2103_09943_gb300", "weights", "warm_cnn.npz")
+
+# (bands, side, R): sides 2^a 3^b, LR grids 24..48 pixels, kernels 9x9 .. 13x13;
+# the odd band count leaves half an image pair in the preconditioner's FFTs
+SHAPES = [(4, 128, 4), (3, 192, 6), (8, 96, 4), (5, 144, 5)]
+
+
+def _scenes():
+    base = synth.CONFIGS["c0"]
+    out = []
+    for k, (N, side, R) in enumerate(SHAPES):
+        cfg = replace(base, name=f"batch_{k}", bands=N, H=side, W=side, R=R, seed=4100 + k,
+                      shapes=max(8, side * side // 2048))
+        out.append(synth.make_scene(cfg))
+    return out
+
+
+@pytest.fixture(scope="module")
+def scenes():
+    return _scenes()
+
+
+@pytest.fixture(scope="module")
+def batch_estimated(cuda, scenes):
+    hp = api.default_hrms_params(tol=1e-7)
+    dev = [(to_dev(s["lrms"], cuda), to_dev(s["pan"], cuda), s["config"].R) for s in scenes]
+    b = api.Batch(dev, ratio=4, hparams=hp, estimate=True)
+    kinfo, sinfo = b.run(info=True)
+    return b, kinfo, sinfo, hp
+
+
+def test_batch_matches_oracle(scenes, batch_estimated):
+    b, kinfo, sinfo, hp = batch_estimated
+    for i, sc in enumerate(scenes):
+        cfg = sc["config"]
+        ref = oracle.pansharpen(sc["lrms"], sc["pan"], cfg.ratio, cfg.R,
+                                hp=oracle.HrmsParams(tol=1e-11), threads=4)
+        assert kinfo[i].status == 0, (i, kinfo[i].status)
+        assert all(s == 0 for s in sinfo[i].status), (i, sinfo[i])
+        assert rel(to_np(b.kernels[i]), ref["kernel"]) < 1e-4, i
+        Z = to_np(b.hrms[i])
+        for k in range(cfg.bands):
+            assert rel(Z[k], ref["Z"][k]) < 1e-4, (i, k)
+
+
+def test_batch_equals_single_scene_calls(cuda, scenes, batch_estimated):
+    b, kinfo, sinfo, hp = batch_estimated
+    for i, sc in enumerate(scenes):
+        cfg = sc["config"]
+        Z, k, ki, si = api.pansharpen(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                      cfg.ratio, cfg.R, hparams=hp)
+        assert ki.iters == kinfo[i].iters
+        assert rel(to_np(b.kernels[i]), to_np(k)) < 1e-6
+        for n in range(cfg.bands):
+            assert abs(si.iters[n] - sinfo[i].iters[n]) <= 1, (i, n)
+        assert rel(to_np(b.hrms[i]), to_np(Z)) < 1e-5, i
+
+
+def test_batch_rerun_reuses_graph_and_times_scenes(cuda, batch_estimated):
+    b, kinfo, sinfo, hp = batch_estimated
+    before = [t.clone() for t in b.hrms]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.run()
+    e1.record()
+    torch.cuda.synchronize()
+    for x, y in zip(before, b.hrms):
+        assert rel(to_np(y), to_np(x)) < 1e-6
+    ms = b.scene_ms()
+    assert len(ms) == b.count
+    assert all(0.0 < t <= e0.elapsed_time(e1) * 1.05 + 0.5 for t in ms), ms
+
+
+def test_batch_given_kernels_plain_fp32(cuda, scenes):
+    # kernels given (the generator's), plain CG from zeros at a tight
+    # tolerance: the plain FP32 bar against the oracle
+    hp = api.default_hrms_params(tol=1e-8, precond=0, max_iter=5000)
+    dev = [(to_dev(s["lrms"], cuda), to_dev(s["pan"], cuda), s["config"].R) for s in scenes]
+    b = api.Batch(dev, ratio=4, hparams=hp, estimate=False)
+    for i, s in enumerate(scenes):
+        b.kernels[i].copy_(to_dev(s["kernel"], cuda))
+    kinfo, sinfo = b.run(info=True)
+    assert kinfo is None
+    for i, sc in enumerate(scenes[:2]):
+        cfg = sc["config"]
+        ref = oracle.solve_hrms(sc["lrms"], sc["pan"], sc["kernel"].astype(np.float64),
+                                cfg.ratio, oracle.HrmsParams(tol=1e-11), threads=4)
+        Z = to_np(b.hrms[i])
+        assert all(s == 0 for s in sinfo[i].status), sinfo[i]
+        for k in range(cfg.bands):
+            assert rel(Z[k], ref["Z"][k]) < 1e-5, (i, k)
+
+
+def test_batch_network_warm_start(cuda, scenes):
+    from paper_2103_09943_gb300.cnn import WarmStartNet
+    net = WarmStartNet.load(WEIGHTS, device=cuda)
+    hp = api.default_hrms_params(tol=1e-7, warm=2, cnn_params=net.params.data_ptr())
+    dev = [(to_dev(s["lrms"], cuda), to_dev(s["pan"], cuda), s["config"].R) for s in scenes]
+    b = api.Batch(dev, ratio=4, hparams=hp, estimate=True)
+    kinfo, sinfo = b.run(info=True)
+    for i, sc in enumerate(scenes):
+        cfg = sc["config"]
+        Z, k, ki, si = api.pansharpen(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                      cfg.ratio, cfg.R, hparams=hp)
+        assert all(s == 0 for s in sinfo[i].status)
+        for n in range(cfg.bands):
+            assert abs(si.iters[n] - sinfo[i].iters[n]) <= 1, (i, n)
+        assert rel(to_np(b.hrms[i]), to_np(Z)) < 1e-5, i
