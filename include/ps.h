@@ -100,6 +100,13 @@ typedef struct ps_hrms_params {
                            cnn_params. The stop rule is the same for all. */
     const float *cnn_params; /* device, ps_cnn_param_count() FP32 values;
                            read only when warm == 2                        */
+    int stop_rule;      /* stop test of the Z0 CG. 0 (default): the recursive
+                           residual ||b - A z|| / ||b|| <= tol, independent of
+                           the start point. 1: the paper's rule (Sec. IV-F):
+                           the relative change of the iterate in the
+                           Frobenius norm, ||z_k+1 - z_k|| / ||z_k+1|| < tol
+                           (the paper's tol is 5e-5); it depends on the start
+                           point and on the preconditioner.              */
 } ps_hrms_params;
 
 /* Per-band result of the Z0 conjugate-gradient solve. */

@@ -13,7 +13,7 @@ the paper's datasets, which are not available.
 """
 from . import fbmp
 from ._clib import build
-from .fbmp import (HrmsParams, KernelParams, PanStats, admm, apply_z0_system,
+from .fbmp import (HrmsParams, KernelParams, PanStats, admm, apply_z0_system, cg_relchange,
                    apply_zstep_system, bicubic_up, blur_decimate, blur_decimate_adj,
                    box_filter, cg_solve, estimate_kernel, estimate_omega,
                    guided_filter, kernel_error_pct, kernel_normal_eq,
@@ -22,6 +22,7 @@ from .fbmp import (HrmsParams, KernelParams, PanStats, admm, apply_z0_system,
                    solve_hrms, up_solve)
 
 __all__ = [
+    "cg_relchange",
     "fbmp", "build", "HrmsParams", "KernelParams", "PanStats", "admm",
     "apply_z0_system", "apply_zstep_system", "bicubic_up", "blur_decimate",
     "blur_decimate_adj", "box_filter", "cg_solve", "estimate_kernel",

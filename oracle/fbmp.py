@@ -50,6 +50,8 @@ class HrmsParams:
     tol: float = 1e-12    # relative residual of each linear solve
     max_iter: int = 100000
     exact_weight: bool = False   # READING: Z-step weight lam (paper) or lam|w|
+    stop_rule: int = 0    # Z0 CG stop: 0 relative residual <= tol; 1 the
+                          # paper's relative change of the iterate < tol
 
 
 # ----------------------------------------------------------------------------
@@ -244,6 +246,36 @@ def pcg_solve(b, u, c: int, lam: float, st: PanStats, gamma: float, x0=None,
     return x, max_iter, rel
 
 
+def cg_relchange(b, u, c: int, lam: float, st: PanStats, x0=None, tol: float = 5e-5,
+                 max_iter: int = 100000):
+    """CG on the Z0 system of Eq. Z_ini_matting (textbook Hestenes-Stiefel)
+    with the stop rule of Sec. IV-F: stop after the first iteration k whose
+    relative change of the iterate in the Frobenius norm,
+    ||x_k - x_(k-1)|| / ||x_k|| = |alpha| ||p|| / ||x_k||, is below tol.
+    Before any iteration it stops only on an exact zero residual.
+    Returns (x, iterations, recursive relative residual)."""
+    b, u = f64(b), f64(u)
+    x = np.zeros_like(b) if x0 is None else f64(x0).copy()
+    r = b - apply_z0_system(x, u, c, st, lam)
+    bb = float(np.sum(b * b))
+    rr = float(np.sum(r * r))
+    if bb == 0.0 or rr == 0.0:
+        return x, 0, 0.0
+    p = r.copy()
+    for k in range(1, max_iter + 1):
+        Ap = apply_z0_system(p, u, c, st, lam)
+        alpha = rr / float(np.sum(p * Ap))
+        x += alpha * p
+        r -= alpha * Ap
+        rr_new = float(np.sum(r * r))
+        change = abs(alpha) * float(np.linalg.norm(p)) / float(np.linalg.norm(x))
+        if change < tol:
+            return x, k, float(np.sqrt(rr_new / bb))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x, max_iter, float(np.sqrt(rr / bb))
+
+
 def kernel_normal_eq(Y, f, c: int, R: int):
     """E^T E and E^T f with E = D C(Y) (Eq. z_update, Eq. z_solution)."""
     Y, f = f64(Y), f64(f)
@@ -259,15 +291,20 @@ def kernel_normal_eq(Y, f, c: int, R: int):
 # Algorithm 2: the per-band HRMS solve
 # ----------------------------------------------------------------------------
 def solve_band(x_lr, u, c: int, st: PanStats, p: HrmsParams, z_init=None):
-    """One band of Algorithm 2: Z0 (Eq. Z_ini_matting, by CG), then the
-    A, C step (Eq. ac_h_compute) as a guided filter, then the Z step
-    (Eq. Z_solution), solved exactly (CG to tolerance p.tol)."""
+    """One band of Algorithm 2: Z0 (Eq. Z_ini_matting, by CG, stopped by
+    p.stop_rule), then the A, C step (Eq. ac_h_compute) as a guided filter,
+    then the Z step (Eq. Z_solution), solved exactly (CG to relative residual
+    p.tol, or 1e-12 under the relative-change rule)."""
     b = blur_decimate_adj(x_lr, u, c)
-    z0, it0, rel0 = cg_solve(0, b, u, c, p.lam, st, z_init, p.tol, p.max_iter)
+    if p.stop_rule == 1:
+        z0, it0, rel0 = cg_relchange(b, u, c, p.lam, st, z_init, p.tol, p.max_iter)
+    else:
+        z0, it0, rel0 = cg_solve(0, b, u, c, p.lam, st, z_init, p.tol, p.max_iter)
     lhat = guided_filter(laplacian(z0), st)
     lam_z = p.lam * ((2 * p.r + 1) ** 2 if p.exact_weight else 1.0)
     rhs = b + lam_z * laplacian(lhat)
-    z, it1, rel1 = cg_solve(1, rhs, u, c, lam_z, None, z0, p.tol, p.max_iter)
+    ztol = p.tol if p.stop_rule == 0 else 1e-12
+    z, it1, rel1 = cg_solve(1, rhs, u, c, lam_z, None, z0, ztol, p.max_iter)
     return {"Z": z, "Z0": z0, "iters_z0": it0, "relres_z0": rel0,
             "iters_z": it1, "relres_z": rel1, "b": b, "lhat": lhat}
 

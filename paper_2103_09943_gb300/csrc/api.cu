@@ -141,6 +141,7 @@ ps_status check_hrms(const ps_hrms_params *p) {
     if (p->precond && (!(p->precond_gamma > 0.f) || !isfinite(p->precond_gamma)))
         return PS_ERR_INVALID_ARG;
     if (p->warm < 0 || p->warm > 2) return PS_ERR_INVALID_ARG;
+    if (p->stop_rule != 0 && p->stop_rule != 1) return PS_ERR_INVALID_ARG;
     if (p->warm == 2 && !p->cnn_params) return PS_ERR_INVALID_ARG;
     return PS_OK;
 }
@@ -562,7 +563,7 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
         la.out = ap;
         launch_llp(la, LLP_APPLY, p->r, N, st);
     }
-    launch_cg_reset(bands, g, N, (double)p->tol, p->max_iter, p->precond, st);
+    launch_cg_reset(bands, g, N, (double)p->tol, p->max_iter, p->precond, p->stop_rule, st);
     launch_cg_init(rv, d_z_init ? ap : nullptr, d_z_init, x, rv, N, HW, bands, g, st);
     PrecArgs pa;
     memset(&pa, 0, sizeof(pa));
@@ -742,6 +743,7 @@ void ps_default_hrms_params(ps_hrms_params *p) {
     p->precond_gamma = 4.0f;
     p->warm = 0;
     p->cnn_params = nullptr;
+    p->stop_rule = 0;
 }
 
 const char *ps_status_string(int s) {
@@ -1080,6 +1082,7 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
     key_put(key, hp->precond_gamma);
     key_put(key, hp->warm);
     key_put(key, hp->cnn_params);
+    key_put(key, hp->stop_rule);
     key_put(key, kp != nullptr);
     if (kp) {
         key_put(key, kp->lambda_omega);

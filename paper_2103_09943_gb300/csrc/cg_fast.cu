@@ -182,6 +182,11 @@ __device__ __forceinline__ void vupd(float4 &x, float4 &r, float4 p, float4 q, c
     rr = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, fmaf(r.w, r.w, rr))));
 }
 
+__device__ __forceinline__ float vsq(float2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float vsq(float4 a) {
+    return a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+}
+
 // B^T D^T v on the C x C block of LR site (ky, kx): pixel (C ky + a, C kx + b)
 // takes tap (i, j) exactly when i = -a and j = -b (mod C), with the sample
 // v(ky + (a + i)/C, kx + (b + j)/C).
@@ -196,14 +201,15 @@ __global__ void __launch_bounds__(128) cg_update_site_kernel(
     constexpr int KN = K1 - K0 + 1;
     using V = typename VecT<C>::T;
     __shared__ float su[n * n];
-    __shared__ double red[4];
+    __shared__ double red[3][4];
     const int b = blockIdx.z, ky = blockIdx.y;
     if (g->stop || bands[b].done) return;
     for (int k = threadIdx.x; k < n * n; k += 128) su[k] = u[k];
     __syncthreads();
     const int h = H / C, w = W / C;
     const int kx = blockIdx.x * 128 + threadIdx.x;
-    float rrf = 0.0f;
+    float rrf = 0.0f, xxf = 0.0f, ppf = 0.0f;
+    const bool rel = g->rule == 1;
     if (kx < w) {
         const float *vb = v + (size_t)b * h * w;
         float vw[KN][KN];
@@ -238,26 +244,47 @@ __global__ void __launch_bounds__(128) cg_update_site_kernel(
             const V pv = __ldg(reinterpret_cast<const V *>(p + o));
             const V qv = __ldg(reinterpret_cast<const V *>(q + o));
             vupd(xv, rv, pv, qv, acc[a], al, rrf);
+            if (rel) {
+                xxf += vsq(xv);
+                ppf += vsq(pv);
+            }
             *reinterpret_cast<V *>(x + o) = xv;
             *reinterpret_cast<V *>(r + o) = rv;
         }
     }
-    double rr = (double)rrf;
-    for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rr;
+    double rr = (double)rrf, xx = (double)xxf, pp = (double)ppf;
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        if (rel) {
+            xx += __shfl_xor_sync(0xffffffffu, xx, o);
+            pp += __shfl_xor_sync(0xffffffffu, pp, o);
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = rr;
+        red[1][threadIdx.x >> 5] = xx;
+        red[2][threadIdx.x >> 5] = pp;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const double t = red[0] + red[1] + red[2] + red[3];
+        const double t = red[0][0] + red[0][1] + red[0][2] + red[0][3];
         CgBand *bd = bands + b;
         atomicAdd(&bd->rr_new, t);
+        if (rel) {
+            atomicAdd(&bd->xx_new, red[1][0] + red[1][1] + red[1][2] + red[1][3]);
+            atomicAdd(&bd->pp_new, red[2][0] + red[2][1] + red[2][2] + red[2][3]);
+        }
         __threadfence();
         const unsigned int k = atomicAdd(&bd->cnt_update, 1u);
         if (k == gridDim.x * gridDim.y - 1) {
             __threadfence();
             const double rn = atomicAdd(&bd->rr_new, 0.0);
+            const double xn = atomicAdd(&bd->xx_new, 0.0), pn = atomicAdd(&bd->pp_new, 0.0);
             const double ro = bd->rho;
             bd->cnt_update = 0u;
             bd->rr_new = 0.0;
+            bd->xx_new = 0.0;
+            bd->pp_new = 0.0;
             bd->pAp = 0.0;
             bd->vv = 0.0;
             bd->iters += 1;
@@ -271,7 +298,7 @@ __global__ void __launch_bounds__(128) cg_update_site_kernel(
                     bd->rho = rn;
                 }
                 bd->rr = rn;
-                if (sqrt(rn / bd->bb) <= g->tol) {
+                if (cg_converged(g, bd, rn, xn, pn)) {
                     bd->done = 1;
                 } else if (bd->iters >= g->max_iter) {
                     bd->status = PS_ERR_NOT_CONVERGED;

@@ -31,6 +31,8 @@ struct CgBand {
     double rr_new;   // accumulator of the next r^T r (zeroed after use)
     double rho;      // numerator of alpha: r^T r (plain CG) or r^T z (preconditioned)
     double rz_new;   // accumulator of the next r^T z (zeroed after use)
+    double xx_new;   // accumulators of ||x_new||^2 and ||p||^2 for the relative-
+    double pp_new;   // change stop rule (zeroed after use)
     double alpha;
     double beta;
     int iters;
@@ -51,7 +53,17 @@ struct CgGlobal {
     int iter;                 // loop iterations run
     int max_iter;             // hard cap
     int precond;              // 1: z = P^{-1} r feeds p and beta (preconditioned CG)
+    int rule;                 // stop rule: 0 ||r|| / ||b|| <= tol; 1 ||x_new - x|| / ||x_new|| < tol
 };
+
+// The stop test of a band after an update with step alpha: the relative
+// residual, or the relative change ||alpha p|| / ||x_new|| of the iterate
+// in the Frobenius norm (the rule the paper states for the Z0 CG, Sec. IV-F).
+__device__ __forceinline__ bool cg_converged(const CgGlobal *g, const CgBand *bd, double rn,
+                                             double xx, double pp) {
+    if (g->rule == 1) return bd->alpha * bd->alpha * pp < g->tol * g->tol * xx;
+    return sqrt(rn / bd->bb) <= g->tol;
+}
 
 // Block-wide sum of a double over a 1-D block; the result is valid in
 // thread 0. `red` holds blockDim.x / 32 doubles of shared memory.

@@ -38,7 +38,7 @@ void launch_adj(const float *v, int N, int H, int W, int c, const float *u, int 
                 cudaStream_t st);
 void launch_llp(const LlpArgs &a, int mode, int r, int N, cudaStream_t st);
 void launch_cg_reset(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter, int precond,
-                     cudaStream_t st);
+                     int rule, cudaStream_t st);
 void launch_cg_init(const float *bvec, const float *ax0, const float *x0, float *x, float *r,
                     int N, size_t HW, CgBand *bands, CgGlobal *g, cudaStream_t st);
 void launch_cg_update(float *x, float *r, const float *p, const float *q, const float *v,

@@ -605,7 +605,7 @@ void launch_llp(const LlpArgs &a, int mode, int r, int N, cudaStream_t st) {
 // at most max_iter iterations whatever the band states.
 // ----------------------------------------------------------------------------
 __global__ void cg_reset_kernel(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter,
-                                int precond) {
+                                int precond, int rule) {
     const int t = threadIdx.x;
     for (int b = t; b < N; b += blockDim.x) {
         CgBand z = {};
@@ -620,6 +620,7 @@ __global__ void cg_reset_kernel(CgBand *bands, CgGlobal *g, int N, double tol, i
         g->max_iter = max_iter;
         g->tol = tol;
         g->precond = precond;
+        g->rule = rule;
     }
 }
 
@@ -673,7 +674,8 @@ __global__ void __launch_bounds__(256) cg_init_kernel(const float4 *__restrict__
             if (!isfinite(r2) || !isfinite(b2)) {
                 bd->status = PS_ERR_NONFINITE;
                 bd->done = 1;
-            } else if (b2 == 0.0 || sqrt(r2 / b2) <= g->tol) {
+            } else if (b2 == 0.0 || r2 == 0.0 || (g->rule == 0 && sqrt(r2 / b2) <= g->tol)) {
+                // the relative-change rule needs a step: only an exact start ends here
                 bd->done = 1;
             }
         }
@@ -694,7 +696,7 @@ __global__ void __launch_bounds__(128) cg_update_kernel(float4 *__restrict__ x,
                                                         int c, int H, int W, CgBand *bands,
                                                         const CgGlobal *g) {
     __shared__ float su[kMaxTaps];
-    __shared__ double red[4];
+    __shared__ double red[3][4];
     const int b = blockIdx.z, y = blockIdx.y;
     if (g->stop || bands[b].done) return;
     const int n = 2 * R + 1;
@@ -703,7 +705,7 @@ __global__ void __launch_bounds__(128) cg_update_kernel(float4 *__restrict__ x,
     const float al = (float)bands[b].alpha;
     const int W4 = W >> 2, h = H / c, w = W / c;
     const int x4 = blockIdx.x * 128 + threadIdx.x;
-    float rrf = 0.0f;
+    float rrf = 0.0f, xxf = 0.0f, ppf = 0.0f;
     if (x4 < W4) {
         const size_t o = ((size_t)b * H + y) * W4 + x4;
         const AdjAxis ay = adj_axis(y, H, c, R);
@@ -722,23 +724,43 @@ __global__ void __launch_bounds__(128) cg_update_kernel(float4 *__restrict__ x,
         x[o] = xv;
         r[o] = rv;
         rrf = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+        xxf = xv.x * xv.x + xv.y * xv.y + xv.z * xv.z + xv.w * xv.w;
+        ppf = pv.x * pv.x + pv.y * pv.y + pv.z * pv.z + pv.w * pv.w;
     }
-    double rr = (double)rrf;
-    for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rr;
+    const bool rel = g->rule == 1;
+    double rr = (double)rrf, xx = (double)xxf, pp = (double)ppf;
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        if (rel) {
+            xx += __shfl_xor_sync(0xffffffffu, xx, o);
+            pp += __shfl_xor_sync(0xffffffffu, pp, o);
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = rr;
+        red[1][threadIdx.x >> 5] = xx;
+        red[2][threadIdx.x >> 5] = pp;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const double t = red[0] + red[1] + red[2] + red[3];
+        const double t = red[0][0] + red[0][1] + red[0][2] + red[0][3];
         CgBand *bd = bands + b;
         atomicAdd(&bd->rr_new, t);
+        if (rel) {
+            atomicAdd(&bd->xx_new, red[1][0] + red[1][1] + red[1][2] + red[1][3]);
+            atomicAdd(&bd->pp_new, red[2][0] + red[2][1] + red[2][2] + red[2][3]);
+        }
         __threadfence();
         const unsigned int k = atomicAdd(&bd->cnt_update, 1u);
         if (k == gridDim.x * gridDim.y - 1) {
             __threadfence();
             const double rn = atomicAdd(&bd->rr_new, 0.0);
+            const double xn = atomicAdd(&bd->xx_new, 0.0), pn = atomicAdd(&bd->pp_new, 0.0);
             const double ro = bd->rho;
             bd->cnt_update = 0u;
             bd->rr_new = 0.0;
+            bd->xx_new = 0.0;
+            bd->pp_new = 0.0;
             bd->pAp = 0.0;
             bd->vv = 0.0;
             bd->iters += 1;
@@ -752,7 +774,7 @@ __global__ void __launch_bounds__(128) cg_update_kernel(float4 *__restrict__ x,
                     bd->rho = rn;
                 }
                 bd->rr = rn;
-                if (sqrt(rn / bd->bb) <= g->tol) {
+                if (cg_converged(g, bd, rn, xn, pn)) {
                     bd->done = 1;
                 } else if (bd->iters >= g->max_iter) {
                     bd->status = PS_ERR_NOT_CONVERGED;
@@ -793,8 +815,8 @@ __global__ void cg_control_kernel(CgBand *bands, CgGlobal *g, int N, int use_con
 }
 
 void launch_cg_reset(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter, int precond,
-                     cudaStream_t st) {
-    cg_reset_kernel<<<1, 64, 0, st>>>(bands, g, N, tol, max_iter, precond);
+                     int rule, cudaStream_t st) {
+    cg_reset_kernel<<<1, 64, 0, st>>>(bands, g, N, tol, max_iter, precond, rule);
 }
 
 static int vec_blocks(size_t n4) {

@@ -36,8 +36,21 @@ namespace ps {
 namespace {
 
 constexpr int kPrecPad = 4;  // float2 padding of shared rows (spreads banks)
+// Row stride of the row passes, in float2, is a multiple of 16 plus kRowPad.
+// Their transposed global accesses move two rows per 16 bytes: a warp covers
+// TR / 2 row pairs (rows 2 j, 2 j + 1) times 64 / TR consecutive columns. With
+// the stride 4 mod 16, row pair j starts 8 j float2 (mod 16) into the banks,
+// so for TR = 8 the four pairs land two on each half of the 16 bank pairs and
+// the 256-byte access takes the minimum two wavefronts; TR <= 4 is
+// conflict-free for any stride.
+constexpr int kRowPad = 4;
 constexpr int kPrecMaxSmem = 192 * 1024;
-constexpr int kPrecColThreads = 256;  // CTA size bound of the fused column pass
+// CTA size of the fused column pass: C columns of H / 16 (or H / PER) threads,
+// rounded up to one of three launch shapes, all at 64 registers a thread
+constexpr int kPrecColThreads = 1024;
+__host__ __device__ constexpr int col_shape(int threads) {
+    return threads <= 256 ? 256 : (threads <= 512 ? 512 : 1024);
+}
 
 __device__ __forceinline__ bool image_idle(const PrecArgs &a, int k) {
     if (!a.bands) return false;
@@ -156,13 +169,11 @@ __device__ __forceinline__ void row_fft(float2 *row, int L, const FftPlan &plan,
 
 // ---------------------------------------------------------------------------
 // Row pass, forward: rows y0 .. y0 + TR - 1 of image k (bands 2k, 2k+1).
-// g.ld = padded row stride in float2, congruent to TR mod 16, so that the
-// transposed store (row index fastest) reads shared memory without conflicts.
 // ---------------------------------------------------------------------------
 struct RowGeom {
     int TR;   // rows per CTA
     int tpr;  // threads per row
-    int ld;   // shared-memory row stride (float2)
+    int ld;   // shared-memory row stride (float2), 4 mod 16: see kRowPad
 };
 
 template <bool P2>
@@ -223,9 +234,9 @@ __global__ void __launch_bounds__(1024) prec_rows_fwd_kernel(PrecArgs a, RowGeom
 // ---------------------------------------------------------------------------
 // Column pass with the group solves: columns kx0 + q w, q < C, of image k.
 // ---------------------------------------------------------------------------
-template <int C, int PER, bool P2>
-__global__ void __launch_bounds__(kPrecColThreads, 4) prec_cols_kernel(PrecArgs a, int tpr, int ld,
-                                                                     float scale) {
+template <int C, int PER, bool P2, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1024 / MAXT) prec_cols_kernel(PrecArgs a, int tpr, int ld,
+                                                                      float scale) {
     extern __shared__ __align__(16) float2 psm[];
     const int k = blockIdx.y, kx0 = blockIdx.x;
     if (image_idle(a, k)) return;
@@ -424,17 +435,17 @@ bool make_prec_plan(int H, int W, int C, PrecPlan *pl) {
     if (C != 2 && C != 3 && C != 4 && C != 6 && C != 8) return false;
     pl->p2 = is_pow2(H) && is_pow2(W);
     // rows: TR rows per CTA, a power of two dividing H, within 1024 threads
-    // and the shared-memory budget; row stride congruent to TR mod 16
+    // and the shared-memory budget
     const int tpr = pl->p2 ? W / 16 : fft_threads_row(W);
     if (tpr > 1024) return false;
     const int row_len = pl->p2 ? prow_len(W) : W;
     int TR = 8;
-    auto row_bytes = [&](int tr) { return (size_t)tr * (round16(row_len) + tr) * sizeof(float2); };
+    auto row_bytes = [&](int tr) { return (size_t)tr * (round16(row_len) + kRowPad) * sizeof(float2); };
     while (TR > 1 && (H % TR || TR * tpr > 1024 || row_bytes(TR) > (size_t)kPrecMaxSmem)) TR >>= 1;
     if (row_bytes(TR) > (size_t)kPrecMaxSmem) return false;
     pl->rg.TR = TR;
     pl->rg.tpr = tpr;
-    pl->rg.ld = round16(row_len) + TR;
+    pl->rg.ld = round16(row_len) + kRowPad;
     pl->row_smem = row_bytes(TR);
     // columns: the C columns of one alias-group set in one CTA when they fit
     pl->col_smem = 0;
@@ -450,6 +461,8 @@ bool make_prec_plan(int H, int W, int C, PrecPlan *pl) {
         pl->fb_tpr = H / 16;
         pl->fb_smem = (size_t)prow_len(H) * sizeof(float2);
     } else {
+        // the fewest values per thread that fit one CTA: 16 and 32 values a
+        // thread spill at 64 registers, 8 do not
         const size_t bytes = (size_t)C * (H + kPrecPad) * sizeof(float2);
         for (int per = 8; per <= 32 && bytes <= (size_t)kPrecMaxSmem; per *= 2)
             if (C * fft_threads_row(H, per) <= kPrecColThreads) {
@@ -465,23 +478,33 @@ bool make_prec_plan(int H, int W, int C, PrecPlan *pl) {
     return pl->fb_tpr <= 1024 && pl->fb_smem <= (size_t)kPrecMaxSmem;
 }
 
+template <int C, int MAXT>
+void launch_cols_shape(const PrecArgs &a, const PrecPlan &pl, dim3 grd, dim3 blk, float scale,
+                       cudaStream_t st) {
+    if (pl.p2)
+        prec_cols_kernel<C, 16, true, MAXT><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
+                                                                           pl.col_ld, scale);
+    else if (pl.col_per == 8)
+        prec_cols_kernel<C, 8, false, MAXT><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
+                                                                           pl.col_ld, scale);
+    else if (pl.col_per == 16)
+        prec_cols_kernel<C, 16, false, MAXT><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
+                                                                            pl.col_ld, scale);
+    else
+        prec_cols_kernel<C, 32, false, MAXT><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
+                                                                            pl.col_ld, scale);
+}
+
 template <int C>
 void launch_cols(const PrecArgs &a, const PrecPlan &pl, float scale, cudaStream_t st) {
     const int w = a.W / C, nimg = (a.N + 1) / 2;
     if (pl.col_smem) {
         const dim3 grd(w, nimg), blk(C * pl.col_tpr);
-        if (pl.p2)
-            prec_cols_kernel<C, 16, true><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr, pl.col_ld,
-                                                                         scale);
-        else if (pl.col_per == 8)
-            prec_cols_kernel<C, 8, false><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
-                                                                         pl.col_ld, scale);
-        else if (pl.col_per == 16)
-            prec_cols_kernel<C, 16, false><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
-                                                                          pl.col_ld, scale);
-        else
-            prec_cols_kernel<C, 32, false><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
-                                                                          pl.col_ld, scale);
+        switch (col_shape(C * pl.col_tpr)) {
+            case 256: launch_cols_shape<C, 256>(a, pl, grd, blk, scale, st); break;
+            case 512: launch_cols_shape<C, 512>(a, pl, grd, blk, scale, st); break;
+            default: launch_cols_shape<C, 1024>(a, pl, grd, blk, scale, st); break;
+        }
     } else {
         const dim3 grd(a.W, nimg);
         const int groups = (a.H / C) * w;
@@ -502,12 +525,20 @@ cudaError_t smem_attr(F *f) {
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kPrecMaxSmem);
 }
 
+template <int C, int MAXT>
+cudaError_t set_attrs_cs() {
+    cudaError_t e = smem_attr(prec_cols_kernel<C, 8, false, MAXT>);
+    if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 16, false, MAXT>);
+    if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 32, false, MAXT>);
+    if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 16, true, MAXT>);
+    return e;
+}
+
 template <int C>
 cudaError_t set_attrs_c() {
-    cudaError_t e = smem_attr(prec_cols_kernel<C, 8, false>);
-    if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 16, false>);
-    if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 32, false>);
-    if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 16, true>);
+    cudaError_t e = set_attrs_cs<C, 256>();
+    if (e == cudaSuccess) e = set_attrs_cs<C, 512>();
+    if (e == cudaSuccess) e = set_attrs_cs<C, 1024>();
     return e;
 }
 
@@ -516,7 +547,7 @@ bool prec_rows_valid(const PrecPlan &pl, int H, int W, int tr) {
     if (tr != 1 && tr != 2 && tr != 4 && tr != 8) return false;
     if (H % tr || tr * pl.rg.tpr > 1024) return false;
     const int row_len = pl.p2 ? prow_len(W) : W;
-    return (size_t)tr * (round16(row_len) + tr) * sizeof(float2) <= (size_t)kPrecMaxSmem;
+    return (size_t)tr * (round16(row_len) + kRowPad) * sizeof(float2) <= (size_t)kPrecMaxSmem;
 }
 
 }  // namespace
@@ -537,7 +568,7 @@ void launch_precond(const PrecArgs &a, cudaStream_t st) {
     if (a.rows && a.rows != pl.rg.TR && prec_rows_valid(pl, a.H, a.W, a.rows)) {
         const int row_len = pl.p2 ? prow_len(a.W) : a.W;
         pl.rg.TR = a.rows;
-        pl.rg.ld = round16(row_len) + a.rows;
+        pl.rg.ld = round16(row_len) + kRowPad;
         pl.row_smem = (size_t)a.rows * pl.rg.ld * sizeof(float2);
     }
     const int nimg = (a.N + 1) / 2;

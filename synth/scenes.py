@@ -20,7 +20,11 @@ and 8-band, ratio-4 workloads, Sec. IV-A):
   sub-pixel shift, normalised to unit sum (Eq. gaussian_blur): isotropic with
   ``sigma ~ U[sigma_lo, sigma_hi]``, or anisotropic with covariance
   ``Rot(theta) diag(sx^2, sy^2) Rot(theta)^T``, ``sx, sy ~ U[sigma_lo,
-  sigma_hi]``, ``theta ~ U[0, pi)``.
+  sigma_hi]``, ``theta ~ U[0, pi)``; or ("motion") the Gaussian convolved
+  with a linear motion of length ``d ~ U[motion_lo, motion_hi]`` pixels
+  (Appendix B): along the motion axis the difference of two Gaussian CDFs
+  ``Phi(x' + d/2) - Phi(x' - d/2)``, across it a Gaussian, on coordinates
+  shifted by the centre and rotated by ``theta ~ U[0, pi)``.
 * LRMS ``X_b = D B(u) Z_b + N(0, noise^2)``: circular convolution
   ``(B(u) z)(y, x) = sum_{i,j} u(i, j) z(y - i, x - j)`` then keeping every
   ``ratio``-th sample at phase 0.
@@ -56,6 +60,8 @@ class SceneConfig:
     texture_amp: float = 0.05
     rho: float = 0.8
     seed: int = 0
+    motion_lo: float = 0.0      # motion length range ("motion" blur only)
+    motion_hi: float = 0.0
 
     @property
     def n(self) -> int:
@@ -80,6 +86,10 @@ CONFIGS = {
     # 8 bands, 8192^2, LR 2048^2, as c1 with seed 2
     "c2": SceneConfig("c2", 8, 8192, 8192, 4, 8, 200, 3.0, "aniso", 0.8, 2.5,
                       2.0, 0.005, r=1, seed=2),
+    # the paper's own setting (Sec. IV-F, Appendix B): a 29x29 support and a
+    # Gaussian-times-motion blur; 4 bands, 256^2, ratio 4
+    "p0": SceneConfig("p0", 4, 256, 256, 4, 14, 40, 2.0, "motion", 0.8, 1.5,
+                      3.0, 0.01, r=1, seed=10, motion_lo=3.0, motion_hi=9.0),
 }
 
 
@@ -87,6 +97,10 @@ def make_kernel(cfg: SceneConfig, rng: np.random.Generator) -> np.ndarray:
     """Sampled, shifted Gaussian on the (2R+1)^2 grid, unit sum (float64)."""
     R = cfg.R
     cy, cx = rng.uniform(-cfg.shift, cfg.shift, size=2)
+    if cfg.blur == "motion":
+        return _motion_kernel(R, cx, cy, rng.uniform(cfg.sigma_lo, cfg.sigma_hi),
+                              rng.uniform(cfg.motion_lo, cfg.motion_hi),
+                              rng.uniform(0.0, np.pi))
     if cfg.blur == "iso":
         s = rng.uniform(cfg.sigma_lo, cfg.sigma_hi)
         cov = np.diag([s * s, s * s])
@@ -100,6 +114,21 @@ def make_kernel(cfg: SceneConfig, rng: np.random.Generator) -> np.ndarray:
     d = np.stack([j - cx, i - cy], axis=-1)          # (x, y) offsets
     q = np.einsum("...a,ab,...b->...", d, icov, d)
     u = np.exp(-0.5 * q)
+    return u / u.sum()
+
+
+def _motion_kernel(R: int, cx: float, cy: float, sigma: float, d: float,
+                   theta: float) -> np.ndarray:
+    """Gaussian (sigma) convolved with a linear motion of length d, centred
+    at (cx, cy) and rotated by theta, sampled on the (2R+1)^2 grid (tap (i, j)
+    at x = j, y = i), unit sum."""
+    i, j = np.meshgrid(np.arange(-R, R + 1), np.arange(-R, R + 1), indexing="ij")
+    x, y = j - cx, i - cy
+    xr = x * np.cos(theta) + y * np.sin(theta)
+    yr = -x * np.sin(theta) + y * np.cos(theta)
+    s = sigma * np.sqrt(2.0)
+    along = ndtr((xr + 0.5 * d) / sigma) - ndtr((xr - 0.5 * d) / sigma)
+    u = along * np.exp(-(yr / s) ** 2)
     return u / u.sum()
 
 
