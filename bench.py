@@ -32,14 +32,14 @@ UNIT = "Mpix·band/s"
 L2_FLUSH_BYTES = 256 << 20
 
 
-def workload_config(r: int = 1):
+def workload_config(r: int = 1, scene: str = "c1"):
     import synth
     from dataclasses import replace
-    return replace(synth.CONFIGS["c1"], r=r)
+    return replace(synth.CONFIGS[scene], r=r)
 
 
 def workload_name(cfg) -> str:
-    return (f"c1: {cfg.bands} bands x {cfg.H}x{cfg.W} HRMS, LRMS {cfg.bands}x{cfg.h}x{cfg.w}, "
+    return (f"{cfg.name}: {cfg.bands} bands x {cfg.H}x{cfg.W} HRMS, LRMS {cfg.bands}x{cfg.h}x{cfg.w}, "
             f"ratio {cfg.ratio}, {cfg.n}x{cfg.n} kernel estimated, LLP window radius {cfg.r}; "
             "seeded synthetic scene (shapes + texture, Dirichlet PAN weights, anisotropic "
             "shifted Gaussian blur, noise 0.005)")
@@ -172,7 +172,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import synth
-    cfg = workload_config(args.r)
+    cfg = workload_config(args.r, args.scene)
     scene = synth.make_scene(cfg)
     crop = args.ref_crop
     sc = synth.crop_scene(scene, crop)
@@ -296,7 +296,7 @@ def run_profile_solve(args):
     __graft_entry__.build()
     import synth
     from paper_2103_09943_gb300 import api
-    cfg = workload_config(args.r)
+    cfg = workload_config(args.r, args.scene)
     scene = synth.make_scene(cfg)
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
@@ -374,7 +374,7 @@ def run_profile_warm(args):
     import synth
     from paper_2103_09943_gb300 import ops
     from paper_2103_09943_gb300.cnn import WarmStartNet
-    cfg = workload_config(args.r)
+    cfg = workload_config(args.r, args.scene)
     scene = synth.make_scene(cfg)
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
@@ -399,7 +399,7 @@ def run_gpu(args):
     import synth
     from paper_2103_09943_gb300 import api
 
-    cfg = workload_config(args.r)
+    cfg = workload_config(args.r, args.scene)
     scene = synth.make_scene(cfg, seed=cfg.seed + rank)   # one independent scene per rank
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
@@ -739,6 +739,9 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--r", type=int, default=1)
+    ap.add_argument("--scene", default="c1", choices=["c1", "c2"],
+                    help="c1: 8 x 1024^2 (the metric's workload); c2: one 8 x 8192^2 scene "
+                         "(LRMS 8 x 2048^2), generated as c1 with seed 2")
     ap.add_argument("--cpu-crop", type=int, default=128)
     ap.add_argument("--ref-crop", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")

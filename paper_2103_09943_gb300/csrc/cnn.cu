@@ -13,10 +13,9 @@
 // tap's pixel shift, so no im2col copy is made. The B operand (weights) is
 // packed once per launch in the same core-matrix form.
 //
-// Each CTA walks a vertical strip 128 pixels wide, row after row, with a
-// ring of five input rows: the load of row y + 3 (cp.async) and the
-// epilogue of row y - 1 (tcgen05.ld, bias + ReLU or the backward mask, BF16
-// store) overlap the MMAs of row y, which go to one of two TMEM accumulators.
+// Each CTA walks vertical strips 128 pixels wide, row after row, as a
+// warp-specialised pipeline (a cp.async producer warp, one MMA-issuing
+// thread, four epilogue warps) coupled by mbarriers; see conv32_tc_kernel.
 // Every wait is bounded: on a timeout the kernel sets an error flag and
 // stops.
 #include <cuda_bf16.h>
@@ -34,13 +33,9 @@ constexpr int kTileM = 128;
 constexpr int kHalo = kTileM + 2;
 constexpr int kPlane = kHalo * 16;      // bytes of one 8-channel plane of a halo row
 constexpr int kRowB = 4 * kPlane;       // bytes of one halo row
-constexpr int kRing = 5;
 constexpr int kWTap = 4 * kCh * 16;     // bytes of one tap's B operand
 constexpr int kWBytes = 9 * kWTap;
-constexpr int kConvSmem = kWBytes + kRing * kRowB + 256;
 constexpr uint32_t kIdesc = umma_idesc_bf16(128, 32);
-
-__device__ __forceinline__ int ring_slot(int y) { return ((y % kRing) + kRing) % kRing; }
 
 __device__ __forceinline__ int wrapm(int i, int n) {
     i %= n;
@@ -63,233 +58,332 @@ __global__ void pack_w32_kernel(const float *__restrict__ w, __nv_bfloat16 *__re
     out[i] = __float2bfloat16_rn(v);
 }
 
-// Extra shared memory of the fused last layer: its parameters (289 floats,
-// padded) and the exchange of its per-tap partial sums (128 pixels x 9).
+// ---------------------------------------------------------------------------
+// Warp-specialised pipeline. Each CTA (six warps) walks its work items, each
+// a vertical strip 128 pixels wide and a run of rows, with three roles that
+// only meet at mbarriers:
+//   warp 0     producer: cp.async of input rows (130 pixels with the halo)
+//              into a ring of kRingWs slots; kDepth rows in flight per lane;
+//              a row is announced on full[slot] (32 lane arrivals) once its
+//              copies have landed and been fenced for the async proxy
+//   warp 1     MMA issuer (one thread): per output row, 18 tcgen05.mma into
+//              one of kAcc TMEM accumulators, then commits to acc_full[acc]
+//              and to empty[slot] of the input row no longer needed
+//   warps 2-5  epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (one
+//              pixel per thread), releases the accumulator on acc_empty[acc]
+//              (4 warp arrivals), then bias + ReLU (or the backward mask) and
+//              the BF16 store, or the fused last layer
+// All three roles follow the same item and row sequence, so slot and
+// accumulator phases are counted, not exchanged. Every wait is bounded and
+// also ends when another role has set the CTA's abort flag.
+// ---------------------------------------------------------------------------
+constexpr int kRingWs = 8;
+constexpr int kDepth = 4;
+constexpr int kAcc = 4;
+constexpr int kWsThreads = 192;
 constexpr int kExtraW5 = 304 * 4;
 constexpr int kExtraX = kTileM * 9 * 4;
-constexpr int kConvSmemFused = kConvSmem + kExtraW5 + kExtraX;
+constexpr int kOffRing = kWBytes;
+constexpr int kOffBias = kOffRing + kRingWs * kRowB;
+constexpr int kOffW5 = kOffBias + kCh * 4;
+constexpr int kOffX = kOffW5 + kExtraW5;
+constexpr int kOffBar = kOffX + kExtraX;  // 8-byte aligned
+constexpr int kNumBar = 2 * kRingWs + 2 * kAcc + 1;
+constexpr int kConvSmemWs = kOffBar + kNumBar * 8 + 16;
+static_assert(kOffBar % 8 == 0, "mbarriers need 8-byte alignment");
+
+struct ConvItem {
+    int b, x0, ys, ye, ya, yb;
+};
 
 template <int MODE>
-__global__ void __launch_bounds__(128, 3) conv32_tc_kernel(Conv32Args a) {
+__device__ __forceinline__ ConvItem conv_item(const Conv32Args &a, int item, int strips,
+                                              int chunks) {
+    constexpr int TS = (MODE == CONV_LAST) ? kTileM - 2 : kTileM;
+    ConvItem it;
+    it.b = item / (strips * chunks);
+    const int rem = item - it.b * strips * chunks;
+    const int sx = rem / chunks, ch = rem - (rem / chunks) * chunks;
+    // the fused last layer keeps the 126 pixels whose 3 x 3 neighbourhood
+    // lies in the tile: its tiles start one pixel early and advance by 126,
+    // and it computes one extra layer-4 row above and below its rows
+    it.x0 = sx * TS - (MODE == CONV_LAST ? 1 : 0);
+    it.ya = ch * a.rpi;
+    it.yb = min(a.H, it.ya + a.rpi);
+    it.ys = it.ya - (MODE == CONV_LAST ? 1 : 0);
+    it.ye = it.yb + (MODE == CONV_LAST ? 1 : 0);
+    return it;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) {
     extern __shared__ __align__(1024) uint8_t csm[];
     uint8_t *wsm = csm;
-    uint8_t *ring = csm + kWBytes;
-    float *sbias = reinterpret_cast<float *>(ring + kRing * kRowB);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sbias + kCh);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
-    float *sw5 = reinterpret_cast<float *>(csm + kConvSmem);
-    float *sxc = reinterpret_cast<float *>(csm + kConvSmem + kExtraW5);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    float *sbias = reinterpret_cast<float *>(csm + kOffBias);
+    float *sw5 = reinterpret_cast<float *>(csm + kOffW5);
+    float *sxc = reinterpret_cast<float *>(csm + kOffX);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(csm + kOffBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + kNumBar);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int H = a.H, W = a.W;
 
-    for (int i = tid; i < kWBytes / 16; i += 128)
+    for (int i = tid; i < kWBytes / 16; i += kWsThreads)
         reinterpret_cast<uint4 *>(wsm)[i] = __ldg(reinterpret_cast<const uint4 *>(a.wpack) + i);
     if (tid < kCh) sbias[tid] = a.bias ? a.bias[tid] : 0.0f;
     // the fused last layer's weights transposed so that four input channels
     // are one 16-byte load: sw5[t * 32 + c] = w5[c][t], bias at 288
     if (MODE == CONV_LAST) {
-        for (int i = tid; i < 288; i += 128) sw5[(i % 9) * 32 + i / 9] = a.w5[i];
+        for (int i = tid; i < 288; i += kWsThreads) sw5[(i % 9) * 32 + i / 9] = a.w5[i];
         if (tid == 0) sw5[288] = a.w5[288];
     }
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (uint32_t)(kRingWs + s); };
+    auto accf_bar = [&](int k) { return bar0 + 8u * (uint32_t)(2 * kRingWs + k); };
+    auto acce_bar = [&](int k) { return bar0 + 8u * (uint32_t)(2 * kRingWs + kAcc + k); };
+    const uint32_t done_bar = bar0 + 8u * (uint32_t)(2 * kRingWs + 2 * kAcc);
     if (tid == 0) {
-        mbar_init(smem_u32(&mbar[0]), 1);
-        mbar_init(smem_u32(&mbar[1]), 1);
+        for (int s = 0; s < kRingWs; ++s) {
+            mbar_init(full_bar(s), 32);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int k = 0; k < kAcc; ++k) {
+            mbar_init(accf_bar(k), 1);
+            mbar_init(acce_bar(k), 4);
+        }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(smem_u32(tslot), 64);
+    if (warp == 1) tmem_alloc(smem_u32(tslot), 32 * kAcc);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t w_u32 = smem_u32(wsm), ring_u32 = smem_u32(ring);
-    const uint32_t mb[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
-    uint32_t parity[2] = {0u, 0u};
-    bool ok = true;
+    const uint32_t w_u32 = smem_u32(wsm), ring_u32 = smem_u32(csm + kOffRing);
 
-    // tiles of 128 pixels; the fused last layer keeps the 126 whose 3 x 3
-    // neighbourhood lies in the tile, so its tiles start one pixel early and
-    // advance by 126
     constexpr int TS = (MODE == CONV_LAST) ? kTileM - 2 : kTileM;
     const int strips = (W + TS - 1) / TS;
     const int chunks = (H + a.rpi - 1) / a.rpi;
     const int items = a.N * strips * chunks;
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-        const int b = item / (strips * chunks);
-        const int rem = item - b * strips * chunks;
-        const int sx = rem / chunks, ch = rem - (rem / chunks) * chunks;
-        const int x0 = sx * TS - (MODE == CONV_LAST ? 1 : 0);
-        const int ya = ch * a.rpi, yb = min(H, ya + a.rpi);
-        // rows of this layer's output computed by the item
-        const int ys = ya - (MODE == CONV_LAST ? 1 : 0), ye = yb + (MODE == CONV_LAST ? 1 : 0);
-        const __nv_bfloat16 *inb = a.in + (size_t)b * H * W * kCh;
-        float racc[3] = {0.f, 0.f, 0.f};  // last layer: output rows y - 1, y, y + 1
+    auto fail = [&]() {
+        *abort_flag = 1;
+        if (a.err) atomicExch(a.err, 1);
+    };
 
-        auto load_row = [&](int yabs) {
-            const int yy = wrapm(yabs, H);
-            const uint32_t dst = ring_u32 + ring_slot(yabs) * kRowB;
-            {
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        uint32_t q = 0;  // input rows issued by this CTA
+        int pend = 0;    // issued rows not yet announced
+        bool ok = true;
+        for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            const ConvItem it = conv_item<MODE>(a, item, strips, chunks);
+            const __nv_bfloat16 *inb = a.in + (size_t)it.b * H * W * kCh;
+            const int n_in = it.ye - it.ys + 2;
+            for (int i = 0; i < n_in; ++i, ++q) {
+                const int s = (int)(q % kRingWs);
+                const uint32_t u = q / kRingWs;
+                if (u >= 1)
+                    ok = __all_sync(0xffffffffu,
+                                    mbar_wait_or_abort(empty_bar(s), (u - 1) & 1u, abort_flag));
+                if (!ok) break;
+                const int yy = wrapm(it.ys - 1 + i, H);
                 const __nv_bfloat16 *src = inb + (size_t)yy * W * kCh;
-                for (int idx = tid; idx < kHalo * 4; idx += 128) {
+                const uint32_t dst = ring_u32 + s * kRowB;
+                for (int idx = lane; idx < kHalo * 4; idx += 32) {
                     const int p = idx >> 2, j = idx & 3;
-                    const int x = wrapm(x0 - 1 + p, W);
+                    const int x = wrapm(it.x0 - 1 + p, W);
                     cp_async16(dst + j * kPlane + p * 16, src + (size_t)x * kCh + j * 8);
                 }
-            }
-        };
-        auto epilogue = [&](int y, int buf) {
-            float v[32];
-            tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * 32), v);
-            const int x = x0 + tid;
-            if (MODE == CONV_LAST) {
-                // act5 = ReLU(conv + bias) at this pixel, then its 9 per-tap
-                // partial sums of the last layer, exchanged through shared
-                // memory: output (y - dy, x - dx) takes tap (dy, dx) of (y, x)
-#pragma unroll
-                for (int c = 0; c < kCh; ++c) v[c] = fmaxf(v[c] + sbias[c], 0.0f);
-#pragma unroll
-                for (int t = 0; t < 9; ++t) {
-                    const float4 *w4 = reinterpret_cast<const float4 *>(sw5 + t * 32);
-                    float s = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 wv = w4[q];
-                        s = fmaf(wv.x, v[4 * q], s);
-                        s = fmaf(wv.y, v[4 * q + 1], s);
-                        s = fmaf(wv.z, v[4 * q + 2], s);
-                        s = fmaf(wv.w, v[4 * q + 3], s);
-                    }
-                    sxc[t * kTileM + tid] = s;
-                }
-                __syncthreads();
-                if (tid >= 1 && tid <= kTileM - 2) {
-#pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        // tap (dy, dx) of pixel tid + dx feeds output row y - dy
-                        racc[0] += sxc[(2 * 3 + dx + 1) * kTileM + tid + dx];  // dy = +1
-                        racc[1] += sxc[(1 * 3 + dx + 1) * kTileM + tid + dx];  // dy = 0
-                        racc[2] += sxc[(0 * 3 + dx + 1) * kTileM + tid + dx];  // dy = -1
-                    }
-                    const int yo = y - 1;
-                    if (yo >= ya && yo < yb && x < W) {
-                        const size_t o = ((size_t)b * H + yo) * W + x;
-                        a.z[o] = __ldg(a.up + o) + 255.0f * (racc[0] + sw5[288]);
-                    }
-                }
-                racc[0] = racc[1];
-                racc[1] = racc[2];
-                racc[2] = 0.0f;
-                __syncthreads();
-                return;
-            }
-            if (x >= W) return;
-            const size_t o = (((size_t)b * H + y) * W + x) * kCh;
-            if (a.mask) {
-                const uint4 *mp = reinterpret_cast<const uint4 *>(a.mask + o);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint4 m = __ldg(mp + q);
-                    const __nv_bfloat16 *mh = reinterpret_cast<const __nv_bfloat16 *>(&m);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        if (!(__bfloat162float(mh[e]) > 0.0f)) v[8 * q + e] = 0.0f;
+                cp_async_commit();
+                if (pend == kDepth - 1) {
+                    // the row issued kDepth - 1 rows ago has landed
+                    cp_async_wait<kDepth - 1>();
+                    fence_async_smem();
+                    mbar_arrive(full_bar((int)((q - (kDepth - 1)) % kRingWs)));
+                } else {
+                    ++pend;
                 }
             }
-#pragma unroll
-            for (int c = 0; c < kCh; ++c) {
-                v[c] += sbias[c];
-                if (a.relu) v[c] = fmaxf(v[c], 0.0f);
-            }
-            uint4 pk[4];
-            __nv_bfloat162 *ph = reinterpret_cast<__nv_bfloat162 *>(pk);
-#pragma unroll
-            for (int c = 0; c < kCh / 2; ++c) ph[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
-            uint4 *op = reinterpret_cast<uint4 *>(a.out + o);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) op[q] = pk[q];
-        };
-
-        load_row(ys - 1);
-        load_row(ys);
-        load_row(ys + 1);
-        cp_async_commit();
-        load_row(ys + 2);
-        cp_async_commit();
-        for (int y = ys; y < ye; ++y) {
-            const int buf = (y - ys) & 1;
-            cp_async_wait<1>();  // rows y - 1 .. y + 1 are in
-            fence_async_smem();
-            ok = __syncthreads_and(ok) != 0;
-            if (!ok) break;
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t d = tbase + (uint32_t)(buf * 32);
-                int kk = 0;
-#pragma unroll
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const uint32_t rb = ring_u32 + ring_slot(y + dy) * kRowB;
-#pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int tap = (dy + 1) * 3 + (dx + 1);
-#pragma unroll
-                        for (int s = 0; s < 2; ++s) {
-                            const uint64_t ad = umma_desc(rb + 2 * s * kPlane + (dx + 1) * 16,
-                                                          kPlane, 128);
-                            const uint64_t bd = umma_desc(w_u32 + tap * kWTap + 2 * s * 512, 512,
-                                                          128);
-                            umma_bf16(d, ad, bd, kIdesc, kk > 0 ? 1u : 0u);
-                            ++kk;
-                        }
-                    }
-                }
-                umma_commit(mb[buf]);
-            }
-            if (y > ys) {
-                // MMAs of row y - 1 done: its accumulator is readable and the
-                // ring slot of row y - 2 is free
-                const int pb = buf ^ 1;
-                if (!mbar_wait_bounded(mb[pb], parity[pb])) {
-                    ok = false;
-                    if (a.err) atomicExch(a.err, 1);
-                }
-                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
-                parity[pb] ^= 1u;
-                tc_fence_after();
-            }
-            // the fused last layer's epilogue holds CTA barriers: its
-            // condition must be uniform across the CTA
-            if (MODE == CONV_LAST) ok = __syncthreads_and(ok) != 0;
-            load_row(y + 3);
-            cp_async_commit();
-            if (y > ys && ok) epilogue(y - 1, buf ^ 1);
-            tc_fence_before();
-        }
-        if (ok) {
-            const int lb = (ye - 1 - ys) & 1;
-            if (!mbar_wait_bounded(mb[lb], parity[lb])) {
-                ok = false;
-                if (a.err) atomicExch(a.err, 1);
-            }
-            ok = __all_sync(0xffffffffu, ok);
-            parity[lb] ^= 1u;
-            tc_fence_after();
-            if (MODE == CONV_LAST) ok = __syncthreads_and(ok) != 0;
-            if (ok) epilogue(ye - 1, lb);
-            tc_fence_before();
         }
         cp_async_wait<0>();
-        ok = __syncthreads_and(ok) != 0;
+        fence_async_smem();
+        if (ok) {
+            for (int k = pend; k >= 1; --k) mbar_arrive(full_bar((int)((q - k) % kRingWs)));
+        } else {
+            fail();
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t q = 0, o = 0;
+            bool ok = true;
+            auto wait_full = [&](uint32_t row) {
+                return mbar_wait_or_abort(full_bar((int)(row % kRingWs)), (row / kRingWs) & 1u,
+                                          abort_flag);
+            };
+            for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+                const ConvItem it = conv_item<MODE>(a, item, strips, chunks);
+                const int n_out = it.ye - it.ys;
+                ok = wait_full(q) && wait_full(q + 1);
+                for (int k = 0; k < n_out && ok; ++k, ++o) {
+                    const int acc = (int)(o % kAcc);
+                    const uint32_t v = o / kAcc;
+                    if (!wait_full(q + k + 2) ||
+                        (v >= 1 && !mbar_wait_or_abort(acce_bar(acc), (v - 1) & 1u, abort_flag))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tbase + (uint32_t)(acc * 32);
+                    int kk = 0;
+#pragma unroll
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        const uint32_t rb = ring_u32 + ((q + k + 1 + dy) % kRingWs) * kRowB;
+#pragma unroll
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int tap = (dy + 1) * 3 + (dx + 1);
+#pragma unroll
+                            for (int sk = 0; sk < 2; ++sk) {
+                                const uint64_t ad = umma_desc(
+                                    rb + 2 * sk * kPlane + (dx + 1) * 16, kPlane, 128);
+                                const uint64_t bd = umma_desc(
+                                    w_u32 + tap * kWTap + 2 * sk * 512, 512, 128);
+                                umma_bf16(d, ad, bd, kIdesc, kk > 0 ? 1u : 0u);
+                                ++kk;
+                            }
+                        }
+                    }
+                    umma_commit(accf_bar(acc));
+                    // the input row above this output row is not read again
+                    umma_commit(empty_bar((int)((q + k) % kRingWs)));
+                    if (k == n_out - 1) {
+                        umma_commit(empty_bar((int)((q + k + 1) % kRingWs)));
+                        umma_commit(empty_bar((int)((q + k + 2) % kRingWs)));
+                    }
+                }
+                q += (uint32_t)(n_out + 2);
+            }
+            if (!ok) fail();
+            // every MMA issued has completed before the CTA frees its TMEM
+            if (o > 0) {
+                umma_commit(done_bar);
+                mbar_wait_bounded(done_bar, 0);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue ----------------
+        const int eg = warp & 3;             // TMEM lane group of this warp
+        const int pix = 32 * eg + lane;      // pixel of the tile
+        uint32_t o = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            const ConvItem it = conv_item<MODE>(a, item, strips, chunks);
+            const int n_out = it.ye - it.ys;
+            const int x = it.x0 + pix;
+            float racc[3] = {0.f, 0.f, 0.f};  // last layer: output rows y - 1, y, y + 1
+            for (int k = 0; k < n_out; ++k, ++o) {
+                const int acc = (int)(o % kAcc);
+                const uint32_t v = o / kAcc;
+                ok = mbar_wait_or_abort(accf_bar(acc), v & 1u, abort_flag);
+                // the fused last layer exchanges partial sums among the four
+                // epilogue warps: they must agree to go on
+                if (MODE == CONV_LAST) ok = named_and(1, 128, ok);
+                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+                if (!ok) break;
+                tc_fence_after();
+                float vals[32];
+                tmem_ld32(tbase + ((uint32_t)(32 * eg) << 16) + (uint32_t)(acc * 32), vals);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce_bar(acc));
+                const int y = it.ys + k;
+                if (MODE == CONV_LAST) {
+                    // act5 = ReLU(conv + bias) at this pixel, then its 9
+                    // per-tap partial sums of the last layer: output
+                    // (y - dy, x - dx) takes tap (dy, dx) of (y, x)
+#pragma unroll
+                    for (int c = 0; c < kCh; ++c) vals[c] = fmaxf(vals[c] + sbias[c], 0.0f);
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) {
+                        const float4 *w4 = reinterpret_cast<const float4 *>(sw5 + t * 32);
+                        float sacc = 0.0f;
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq) {
+                            const float4 wv = w4[qq];
+                            sacc = fmaf(wv.x, vals[4 * qq], sacc);
+                            sacc = fmaf(wv.y, vals[4 * qq + 1], sacc);
+                            sacc = fmaf(wv.z, vals[4 * qq + 2], sacc);
+                            sacc = fmaf(wv.w, vals[4 * qq + 3], sacc);
+                        }
+                        sxc[t * kTileM + pix] = sacc;
+                    }
+                    named_sync(1, 128);
+                    if (pix >= 1 && pix <= kTileM - 2) {
+#pragma unroll
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            // tap (dy, dx) of pixel pix + dx feeds output row y - dy
+                            racc[0] += sxc[(2 * 3 + dx + 1) * kTileM + pix + dx];  // dy = +1
+                            racc[1] += sxc[(1 * 3 + dx + 1) * kTileM + pix + dx];  // dy = 0
+                            racc[2] += sxc[(0 * 3 + dx + 1) * kTileM + pix + dx];  // dy = -1
+                        }
+                        const int yo = y - 1;
+                        if (yo >= it.ya && yo < it.yb && x < W) {
+                            const size_t oo = ((size_t)it.b * H + yo) * W + x;
+                            a.z[oo] = __ldg(a.up + oo) + 255.0f * (racc[0] + sw5[288]);
+                        }
+                    }
+                    racc[0] = racc[1];
+                    racc[1] = racc[2];
+                    racc[2] = 0.0f;
+                    named_sync(1, 128);
+                    continue;
+                }
+                if (x >= W) continue;
+                const size_t oo = (((size_t)it.b * H + y) * W + x) * kCh;
+                if (a.mask) {
+                    const uint4 *mp = reinterpret_cast<const uint4 *>(a.mask + oo);
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        const uint4 m = __ldg(mp + qq);
+                        const __nv_bfloat16 *mh = reinterpret_cast<const __nv_bfloat16 *>(&m);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (!(__bfloat162float(mh[e]) > 0.0f)) vals[8 * qq + e] = 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < kCh; ++c) {
+                    vals[c] += sbias[c];
+                    if (a.relu) vals[c] = fmaxf(vals[c], 0.0f);
+                }
+                uint4 pk[4];
+                __nv_bfloat162 *ph = reinterpret_cast<__nv_bfloat162 *>(pk);
+#pragma unroll
+                for (int c = 0; c < kCh / 2; ++c)
+                    ph[c] = __floats2bfloat162_rn(vals[2 * c], vals[2 * c + 1]);
+                uint4 *op = reinterpret_cast<uint4 *>(a.out + oo);
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) op[qq] = pk[qq];
+            }
+        }
+        if (!ok) fail();
     }
+    // every role is done: its MMAs were committed and waited on by the
+    // epilogue, its copies waited for by the producer
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tbase, 64);
+        tmem_dealloc(tbase, 32 * kAcc);
     }
 }
 
 }  // namespace
 
-size_t conv32_smem_bytes() { return (size_t)kConvSmemFused; }
+size_t conv32_smem_bytes() { return (size_t)kConvSmemWs; }
 
 void launch_pack_w32(const float *w, void *out, int adjoint, cudaStream_t st) {
     pack_w32_kernel<<<(9 * kCh * kCh + 255) / 256, 256, 0, st>>>(
@@ -301,20 +395,22 @@ void launch_conv32(const Conv32Args &a, int num_sms, cudaStream_t st) {
     const int strips = (a.W + ts - 1) / ts;
     const int chunks = (a.H + a.rpi - 1) / a.rpi;
     const int items = a.N * strips * chunks;
-    int grid = 3 * num_sms;
+    int grid = 2 * num_sms;
     if (grid > items) grid = items;
     switch (a.mode) {
-        case CONV_LAST: conv32_tc_kernel<CONV_LAST><<<grid, 128, kConvSmemFused, st>>>(a); break;
-        default: conv32_tc_kernel<CONV_PLAIN><<<grid, 128, kConvSmem, st>>>(a); break;
+        case CONV_LAST:
+            conv32_tc_kernel<CONV_LAST><<<grid, kWsThreads, kConvSmemWs, st>>>(a);
+            break;
+        default: conv32_tc_kernel<CONV_PLAIN><<<grid, kWsThreads, kConvSmemWs, st>>>(a); break;
     }
 }
 
 cudaError_t cnn_set_attrs() {
     cudaError_t e = cudaFuncSetAttribute(conv32_tc_kernel<CONV_PLAIN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmemWs);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(conv32_tc_kernel<CONV_LAST>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmemFused);
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmemWs);
     return e;
 }
 

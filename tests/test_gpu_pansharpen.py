@@ -106,3 +106,24 @@ def test_host_pipeline_matches_device_call(cuda):
                                 cfg.R)
     # FP64 atomics make the reduction order, hence the last bits, vary run to run
     assert rel(out.numpy(), to_np(Z)) < 1e-6
+
+
+def test_paper_setting_29x29_motion_blur(cuda):
+    # Sec. IV-F and Appendix B: a 29 x 29 kernel support, a Gaussian-times-
+    # motion blur, plain CG from zeros with the relative-change stop rule.
+    sc = synth.make_scene("p0")
+    cfg = sc["config"]
+    hp = api.default_hrms_params(tol=5e-5, stop_rule=1, precond=0, max_iter=5000)
+    Z, k, kinfo, binfo = api.pansharpen(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                        cfg.ratio, cfg.R, hparams=hp)
+    Z, k = to_np(Z), to_np(k)
+    ref_k, _, res = oracle.estimate_kernel(sc["lrms"], sc["pan"], cfg.ratio, cfg.R)
+    assert kinfo.status == 0
+    assert k.shape == (29, 29)
+    assert rel(k, ref_k) < 1e-4
+    assert kinfo.iters == pytest.approx(res.iters, abs=3)
+    ref = oracle.solve_hrms(sc["lrms"], sc["pan"], ref_k, cfg.ratio,
+                            oracle.HrmsParams(tol=5e-5, stop_rule=1), threads=4)
+    for b in range(cfg.bands):
+        assert abs(binfo.iters[b] - ref["bands"][b]["iters_z0"]) <= 2, (b, binfo.iters)
+        assert rel(Z[b], ref["Z"][b]) < 1e-4, b

@@ -142,3 +142,39 @@ def test_host_loop_matches_device_loop(cuda, c0_oracle):
     Zh, _, ih = api.solve_hrms(*args, api.default_hrms_params(tol=1e-7, host_loop=1))
     assert ig.iters == ih.iters
     assert rel(to_np(Zh), to_np(Zg)) < 1e-6
+
+
+def test_paper_stop_rule_matches_oracle(cuda):
+    # Sec. IV-F: the paper's CG for Z0 runs from zeros and stops when the
+    # relative change of the iterate (Frobenius norm) falls below 5e-5. The
+    # GPU stops at the oracle's iteration and lands on its iterate (measured:
+    # equal counts, rel-L2 6e-6).
+    sc = _scene(synth.CONFIGS["c0"])
+    cfg = sc["config"]
+    ref = oracle.solve_hrms(sc["lrms"], sc["pan"], sc["kernel"].astype(np.float64), cfg.ratio,
+                            oracle.HrmsParams(tol=5e-5, stop_rule=1), threads=4)
+    hp = api.default_hrms_params(tol=5e-5, stop_rule=1, precond=0, max_iter=5000)
+    Z, Z0, info = api.solve_hrms(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                 to_dev(sc["kernel"], cuda), cfg.ratio, hp, want_z0=True)
+    Z, Z0 = to_np(Z), to_np(Z0)
+    assert all(s == 0 for s in info.status), info
+    for b in range(cfg.bands):
+        assert abs(info.iters[b] - ref["bands"][b]["iters_z0"]) <= 2, (b, info.iters)
+        assert rel(Z0[b], ref["Z0"][b]) < 1e-4, b
+        assert rel(Z[b], ref["Z"][b]) < 1e-4, b
+
+
+def test_paper_stop_rule_with_preconditioner_stops_earlier(cuda):
+    # the rule is the same with the preconditioner; it stops much sooner and
+    # (measured) closer to the exact solution
+    sc = _scene(synth.CONFIGS["c0"])
+    cfg = sc["config"]
+    args = (to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda), to_dev(sc["kernel"], cuda),
+            cfg.ratio)
+    it = {}
+    for pc in (0, 1):
+        hp = api.default_hrms_params(tol=5e-5, stop_rule=1, precond=pc, max_iter=5000)
+        _, _, info = api.solve_hrms(*args, hp)
+        assert all(s == 0 for s in info.status), info
+        it[pc] = info.iters
+    assert max(it[1]) * 2 < min(it[0]), it
