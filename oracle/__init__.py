@@ -13,7 +13,9 @@ the paper's datasets, which are not available.
 """
 from . import fbmp
 from ._clib import build
-from .fbmp import (HrmsParams, KernelParams, PanStats, admm, apply_z0_system, cg_relchange,
+from .fbmp import (PRIORS, apply_z0_prior, apply_zstep_prior, cg_op, filt, filt_adj,
+                   guide_stats, prior_filters, prior_stats, solve_band_prior, solve_hrms_prior,
+                   HrmsParams, KernelParams, PanStats, admm, apply_z0_system, cg_relchange,
                    apply_zstep_system, bicubic_up, blur_decimate, blur_decimate_adj,
                    box_filter, cg_solve, estimate_kernel, estimate_omega,
                    guided_filter, kernel_error_pct, kernel_normal_eq,
@@ -22,7 +24,9 @@ from .fbmp import (HrmsParams, KernelParams, PanStats, admm, apply_z0_system, cg
                    solve_hrms, up_solve)
 
 __all__ = [
-    "cg_relchange",
+    "cg_relchange", "PRIORS", "apply_z0_prior", "apply_zstep_prior", "cg_op", "filt",
+    "filt_adj", "guide_stats", "prior_filters", "prior_stats", "solve_band_prior",
+    "solve_hrms_prior",
     "fbmp", "build", "HrmsParams", "KernelParams", "PanStats", "admm",
     "apply_z0_system", "apply_zstep_system", "bicubic_up", "blur_decimate",
     "blur_decimate_adj", "box_filter", "cg_solve", "estimate_kernel",

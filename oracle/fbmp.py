@@ -276,6 +276,143 @@ def cg_relchange(b, u, c: int, lam: float, st: PanStats, x0=None, tol: float = 5
     return x, max_iter, float(np.sqrt(rr / bb))
 
 
+# ----------------------------------------------------------------------------
+# Alternative cross-channel priors (Sec. IV-D, Table III): the LLP's Laplacian
+# replaced by other filters F_d; each keeps its own local affine model of
+# F_d Z_i against the guide F_d Y, so the Z0 operator becomes
+# B^T D^T D B + lam sum_d F_d^T M_d F_d and the Z step
+# (B^T D^T D B + lam' sum_d F_d^T F_d) Z = B^T D^T X + lam' sum_d F_d^T L-hat_d.
+# ----------------------------------------------------------------------------
+PRIORS = ("llp", "lpf", "hpf", "lpp", "lgc")
+
+
+def prior_filters(prior: str, u) -> list:
+    """The filters F_d of a prior, on (2R+1)^2 grids with the convention of
+    B(u) (tap (i, j) weighs z(y - i, x - j)). llp: the 5-point Laplacian;
+    lpf: the blur kernel u (low-pass); hpf: delta - u (its complement); lpp:
+    delta (the pixels); lgc: the horizontal and vertical differences
+    z(y, x) - z(y, x - 1) and z(y, x) - z(y - 1, x) (Eq. reg2_lgc)."""
+    u = f64(u)
+    R = u.shape[0] // 2
+    if prior == "llp":
+        return [np.array([[0.0, -1.0, 0.0], [-1.0, 4.0, -1.0], [0.0, -1.0, 0.0]])]
+    if prior == "lpf":
+        return [u.copy()]
+    if prior == "hpf":
+        d = -u.copy()
+        d[R, R] += 1.0
+        return [d]
+    if prior == "lpp":
+        return [np.ones((1, 1))]
+    if prior == "lgc":
+        h = np.zeros((3, 3))
+        h[1, 1], h[1, 2] = 1.0, -1.0
+        v = np.zeros((3, 3))
+        v[1, 1], v[2, 1] = 1.0, -1.0
+        return [h, v]
+    raise ValueError(prior)
+
+
+def filt(z, F) -> np.ndarray:
+    """F z, circular (B(F) of Sec. II-A without decimation)."""
+    return blur_decimate(z, F, 1)
+
+
+def filt_adj(z, F) -> np.ndarray:
+    """F^T z."""
+    return blur_decimate_adj(z, F, 1)
+
+
+def guide_stats(I, r: int, eps: float) -> PanStats:
+    """Window mean, population variance and s = 1/(var + eps) of a given
+    guide image I over (2r+1)^2 circular windows."""
+    I = f64(I)
+    mu = box_filter(I, r)
+    var = box_filter(I * I, r) - mu * mu
+    return PanStats(I, mu, var, 1.0 / (var + eps), r, eps)
+
+
+def prior_stats(Y, prior: str, u, r: int, eps: float) -> list:
+    return [guide_stats(filt(Y, F), r, eps) for F in prior_filters(prior, u)]
+
+
+def apply_z0_prior(z, u, c: int, filters, stats, lam: float) -> np.ndarray:
+    """(B^T D^T D B + lam sum_d F_d^T M_d F_d) z."""
+    out = blur_decimate_adj(blur_decimate(z, u, c), u, c)
+    for F, st in zip(filters, stats):
+        out += lam * filt_adj(matting_apply(filt(z, F), st), F)
+    return out
+
+
+def apply_zstep_prior(z, u, c: int, filters, lam: float) -> np.ndarray:
+    """(B^T D^T D B + lam sum_d F_d^T F_d) z."""
+    out = blur_decimate_adj(blur_decimate(z, u, c), u, c)
+    for F in filters:
+        out += lam * filt_adj(filt(z, F), F)
+    return out
+
+
+def cg_op(apply, b, x0=None, tol: float = 1e-12, max_iter: int = 100000):
+    """Textbook CG (Hestenes-Stiefel) for an SPD operator given as a
+    function; stops on the recursive relative residual. Returns (x, iters)."""
+    b = f64(b)
+    x = np.zeros_like(b) if x0 is None else f64(x0).copy()
+    r = b - apply(x)
+    bb = float(np.sum(b * b))
+    rr = float(np.sum(r * r))
+    if bb == 0.0 or np.sqrt(rr / bb) <= tol:
+        return x, 0
+    p = r.copy()
+    for k in range(1, max_iter + 1):
+        Ap = apply(p)
+        alpha = rr / float(np.sum(p * Ap))
+        x += alpha * p
+        r -= alpha * Ap
+        rr_new = float(np.sum(r * r))
+        if np.sqrt(rr_new / bb) <= tol:
+            return x, k
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x, max_iter
+
+
+def solve_band_prior(x_lr, u, c: int, prior: str, stats, p: HrmsParams, z_init=None):
+    """One band of Algorithm 2 under an alternative prior: Z0 by CG on
+    apply_z0_prior, the per-filter guided filters L-hat_d of F_d Z0, then
+    the Z step by CG."""
+    filters = prior_filters(prior, u)
+    b = blur_decimate_adj(x_lr, u, c)
+    z0, it0 = cg_op(lambda z: apply_z0_prior(z, u, c, filters, stats, p.lam), b, z_init,
+                    p.tol, p.max_iter)
+    lam_z = p.lam * ((2 * p.r + 1) ** 2 if p.exact_weight else 1.0)
+    rhs = b.copy()
+    for F, st in zip(filters, stats):
+        rhs += lam_z * filt_adj(guided_filter(filt(z0, F), st), F)
+    z, it1 = cg_op(lambda v: apply_zstep_prior(v, u, c, filters, lam_z), rhs, z0, p.tol,
+                   p.max_iter)
+    return {"Z": z, "Z0": z0, "iters_z0": it0, "iters_z": it1}
+
+
+def solve_hrms_prior(X, Y, u, c: int, prior: str, p: HrmsParams | None = None,
+                     threads: int = 1):
+    """Algorithm 2 over all bands under an alternative prior."""
+    p = p or HrmsParams()
+    X = f64(X)
+    stats = prior_stats(Y, prior, u, p.r, p.eps)
+    N = X.shape[0]
+
+    def one(bd):
+        return solve_band_prior(X[bd], u, c, prior, stats, p)
+
+    if threads > 1:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            out = list(ex.map(one, range(N)))
+    else:
+        out = [one(bd) for bd in range(N)]
+    return {"Z": np.stack([o["Z"] for o in out]), "Z0": np.stack([o["Z0"] for o in out]),
+            "bands": out}
+
+
 def kernel_normal_eq(Y, f, c: int, R: int):
     """E^T E and E^T f with E = D C(Y) (Eq. z_update, Eq. z_solution)."""
     Y, f = f64(Y), f64(f)

@@ -69,18 +69,23 @@ __global__ void pack_w32_kernel(const float *__restrict__ w, __nv_bfloat16 *__re
 //   warp 1     MMA issuer (one thread): per output row, 18 tcgen05.mma into
 //              one of kAcc TMEM accumulators, then commits to acc_full[acc]
 //              and to empty[slot] of the input row no longer needed
-//   warps 2-5  epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (one
-//              pixel per thread), releases the accumulator on acc_empty[acc]
-//              (4 warp arrivals), then bias + ReLU (or the backward mask) and
-//              the BF16 store, or the fused last layer
+//   warps 2-9  epilogue, two groups of four warps taking alternate output
+//              rows (the fused last layer, whose rows chain, uses group 0
+//              only): warp w reads TMEM lanes 32 (w mod 4) .. + 31 (one pixel
+//              per thread), releases the accumulator on acc_empty[acc] (4 warp
+//              arrivals), then bias + ReLU (or the backward mask) and the BF16
+//              store, or the fused last layer
 // All three roles follow the same item and row sequence, so slot and
 // accumulator phases are counted, not exchanged. Every wait is bounded and
 // also ends when another role has set the CTA's abort flag.
 // ---------------------------------------------------------------------------
 constexpr int kRingWs = 8;
 constexpr int kDepth = 4;
+// the producer waits for a slot that output row q - kRingWs + 2 frees while
+// it holds kDepth - 1 rows unannounced: the ring must exceed kDepth + 1
+static_assert(kRingWs > kDepth + 1, "ring too short for the prefetch depth");
 constexpr int kAcc = 4;
-constexpr int kWsThreads = 192;
+constexpr int kWsThreads = 320;
 constexpr int kExtraW5 = 304 * 4;
 constexpr int kExtraX = kTileM * 9 * 4;
 constexpr int kOffRing = kWBytes;
@@ -178,10 +183,22 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
         uint32_t q = 0;  // input rows issued by this CTA
         int pend = 0;    // issued rows not yet announced
         bool ok = true;
+        // a lane's 16-byte chunks of a halo row: chunk idx = lane + 32 m is
+        // plane j = idx & 3 of pixel p = idx >> 2; the same columns for every
+        // row of an item, so their offsets are computed once per item
+        constexpr int kChunks = (kHalo * 4 + 31) / 32;
+        uint32_t soff[kChunks], doff[kChunks];
         for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
             const ConvItem it = conv_item<MODE>(a, item, strips, chunks);
             const __nv_bfloat16 *inb = a.in + (size_t)it.b * H * W * kCh;
             const int n_in = it.ye - it.ys + 2;
+#pragma unroll
+            for (int m = 0; m < kChunks; ++m) {
+                const int idx = lane + 32 * m;
+                const int p = idx >> 2, j = idx & 3;
+                soff[m] = (uint32_t)(wrapm(it.x0 - 1 + p, W) * kCh + j * 8);
+                doff[m] = (uint32_t)(j * kPlane + p * 16);
+            }
             for (int i = 0; i < n_in; ++i, ++q) {
                 const int s = (int)(q % kRingWs);
                 const uint32_t u = q / kRingWs;
@@ -192,11 +209,9 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
                 const int yy = wrapm(it.ys - 1 + i, H);
                 const __nv_bfloat16 *src = inb + (size_t)yy * W * kCh;
                 const uint32_t dst = ring_u32 + s * kRowB;
-                for (int idx = lane; idx < kHalo * 4; idx += 32) {
-                    const int p = idx >> 2, j = idx & 3;
-                    const int x = wrapm(it.x0 - 1 + p, W);
-                    cp_async16(dst + j * kPlane + p * 16, src + (size_t)x * kCh + j * 8);
-                }
+#pragma unroll
+                for (int m = 0; m < kChunks; ++m)
+                    if (lane + 32 * m < kHalo * 4) cp_async16(dst + doff[m], src + soff[m]);
                 cp_async_commit();
                 if (pend == kDepth - 1) {
                     // the row issued kDepth - 1 rows ago has landed
@@ -224,6 +239,15 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
                 return mbar_wait_or_abort(full_bar((int)(row % kRingWs)), (row / kRingWs) & 1u,
                                           abort_flag);
             };
+            // descriptors: B per (tap, K half) fixed; A is the ring base
+            // descriptor plus the 16-byte-unit offset of slot, K half and dx
+            uint64_t bdesc[18];
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+                for (int sk = 0; sk < 2; ++sk)
+                    bdesc[2 * tap + sk] = umma_desc(w_u32 + tap * kWTap + 2 * sk * 512, 512, 128);
+            const uint64_t adesc0 = umma_desc(ring_u32, kPlane, 128);
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
                 const ConvItem it = conv_item<MODE>(a, item, strips, chunks);
                 const int n_out = it.ye - it.ys;
@@ -241,17 +265,16 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
                     int kk = 0;
 #pragma unroll
                     for (int dy = -1; dy <= 1; ++dy) {
-                        const uint32_t rb = ring_u32 + ((q + k + 1 + dy) % kRingWs) * kRowB;
+                        const uint64_t ar =
+                            adesc0 + (uint64_t)(((q + k + 1 + dy) % kRingWs) * (kRowB >> 4));
 #pragma unroll
                         for (int dx = -1; dx <= 1; ++dx) {
                             const int tap = (dy + 1) * 3 + (dx + 1);
 #pragma unroll
                             for (int sk = 0; sk < 2; ++sk) {
-                                const uint64_t ad = umma_desc(
-                                    rb + 2 * sk * kPlane + (dx + 1) * 16, kPlane, 128);
-                                const uint64_t bd = umma_desc(
-                                    w_u32 + tap * kWTap + 2 * sk * 512, 512, 128);
-                                umma_bf16(d, ad, bd, kIdesc, kk > 0 ? 1u : 0u);
+                                const uint64_t ad =
+                                    ar + (uint64_t)((2 * sk * kPlane + (dx + 1) * 16) >> 4);
+                                umma_bf16(d, ad, bdesc[2 * tap + sk], kIdesc, kk > 0 ? 1u : 0u);
                                 ++kk;
                             }
                         }
@@ -278,14 +301,17 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
         // ---------------- epilogue ----------------
         const int eg = warp & 3;             // TMEM lane group of this warp
         const int pix = 32 * eg + lane;      // pixel of the tile
+        const int grp = (warp - 2) >> 2;     // rows with o % 2 == grp
         uint32_t o = 0;
         bool ok = true;
-        for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        for (int item = blockIdx.x; item < items && ok && (MODE != CONV_LAST || grp == 0);
+             item += gridDim.x) {
             const ConvItem it = conv_item<MODE>(a, item, strips, chunks);
             const int n_out = it.ye - it.ys;
             const int x = it.x0 + pix;
             float racc[3] = {0.f, 0.f, 0.f};  // last layer: output rows y - 1, y, y + 1
             for (int k = 0; k < n_out; ++k, ++o) {
+                if (MODE != CONV_LAST && (int)(o & 1u) != grp) continue;
                 const int acc = (int)(o % kAcc);
                 const uint32_t v = o / kAcc;
                 ok = mbar_wait_or_abort(accf_bar(acc), v & 1u, abort_flag);

@@ -48,10 +48,12 @@ __device__ __forceinline__ void store_px32(__nv_bfloat16 *p, const float *v) {
     for (int k = 0; k < 4; ++k) q[k] = pk[k];
 }
 
-// a1 = ReLU(conv0(x) + b0), x = (up / s, pan / s). One thread per pixel; the
+// a1 = ReLU(conv0(x) + b0), x = (up / s, pan / s). One thread per pair of
+// horizontally adjacent pixels (W is even): every weight load feeds both
+// pixels, and the two 3 x 3 neighbourhoods share a 3 x 4 input patch. The
 // weights sit transposed in shared memory, sw[(t * 2 + i) * 32 + o] =
 // w0[o][i][t], so that four output channels are one broadcast 16-byte load.
-__global__ void __launch_bounds__(256) cnn_first_kernel(const float *__restrict__ up,
+__global__ void __launch_bounds__(256, 2) cnn_first_kernel(const float *__restrict__ up,
                                                         const float *__restrict__ pan,
                                                         size_t pan_stride,
                                                         const float *__restrict__ prm, int B,
@@ -65,45 +67,57 @@ __global__ void __launch_bounds__(256) cnn_first_kernel(const float *__restrict_
     if (threadIdx.x < kCh) sw[576 + threadIdx.x] = prm[576 + threadIdx.x];
     __syncthreads();
     const size_t HW = (size_t)H * W;
+    const int W2 = W >> 1;
     const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (idx >= (size_t)B * HW) return;
-    const int b = (int)(idx / HW);
-    const int rem = (int)(idx - (size_t)b * HW), y = rem / W, x = rem - (rem / W) * W;
+    if (idx >= (size_t)B * H * W2) return;
+    const size_t HW2 = (size_t)H * W2;
+    const int b = (int)(idx / HW2);
+    const int rem = (int)(idx - (size_t)b * HW2), y = rem / W2, x = 2 * (rem - (rem / W2) * W2);
     const float *u = up + (size_t)b * HW;
     const float *p = pan + (size_t)b * pan_stride;
-    float in[2][9];
+    float in[2][3][4];  // channel, row y - 1 .. y + 1, columns x - 1 .. x + 2
 #pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = wrapi2(y + dy, H);
+    for (int dy = 0; dy < 3; ++dy) {
+        const size_t ro = (size_t)wrapi2(y + dy - 1, H) * W;
 #pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int xx = wrapi2(x + dx, W);
-            in[0][(dy + 1) * 3 + dx + 1] = __ldg(u + (size_t)yy * W + xx) * (1.0f / kScale);
-            in[1][(dy + 1) * 3 + dx + 1] = __ldg(p + (size_t)yy * W + xx) * (1.0f / kScale);
+        for (int c = 0; c < 4; ++c) {
+            const int xx = wrapi2(x - 1 + c, W);
+            in[0][dy][c] = __ldg(u + ro + xx) * (1.0f / kScale);
+            in[1][dy][c] = __ldg(p + ro + xx) * (1.0f / kScale);
         }
     }
-    float v[kCh];
+    float v0[kCh], v1[kCh];
 #pragma unroll
-    for (int o = 0; o < kCh; ++o) v[o] = sw[576 + o];
+    for (int o = 0; o < kCh; ++o) v0[o] = v1[o] = sw[576 + o];
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
+        const int dy = t / 3, dx = t % 3;
 #pragma unroll
         for (int ci = 0; ci < 2; ++ci) {
-            const float xv = in[ci][t];
+            const float xa = in[ci][dy][dx], xb = in[ci][dy][dx + 1];
             const float4 *w4 = reinterpret_cast<const float4 *>(sw + (t * 2 + ci) * 32);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const float4 wv = w4[q];
-                v[4 * q] = fmaf(wv.x, xv, v[4 * q]);
-                v[4 * q + 1] = fmaf(wv.y, xv, v[4 * q + 1]);
-                v[4 * q + 2] = fmaf(wv.z, xv, v[4 * q + 2]);
-                v[4 * q + 3] = fmaf(wv.w, xv, v[4 * q + 3]);
+                v0[4 * q] = fmaf(wv.x, xa, v0[4 * q]);
+                v0[4 * q + 1] = fmaf(wv.y, xa, v0[4 * q + 1]);
+                v0[4 * q + 2] = fmaf(wv.z, xa, v0[4 * q + 2]);
+                v0[4 * q + 3] = fmaf(wv.w, xa, v0[4 * q + 3]);
+                v1[4 * q] = fmaf(wv.x, xb, v1[4 * q]);
+                v1[4 * q + 1] = fmaf(wv.y, xb, v1[4 * q + 1]);
+                v1[4 * q + 2] = fmaf(wv.z, xb, v1[4 * q + 2]);
+                v1[4 * q + 3] = fmaf(wv.w, xb, v1[4 * q + 3]);
             }
         }
     }
 #pragma unroll
-    for (int o = 0; o < kCh; ++o) v[o] = fmaxf(v[o], 0.0f);
-    store_px32(a1 + idx * kCh, v);
+    for (int o = 0; o < kCh; ++o) {
+        v0[o] = fmaxf(v0[o], 0.0f);
+        v1[o] = fmaxf(v1[o], 0.0f);
+    }
+    __nv_bfloat16 *dst = a1 + ((size_t)b * HW + (size_t)y * W + x) * kCh;
+    store_px32(dst, v0);
+    store_px32(dst + kCh, v1);
 }
 
 // z = s (up / s + conv5(a5) + b5). With a target: also the loss sum
@@ -409,7 +423,7 @@ void cnn_layout(int *w_off, int *b_off) {
 
 void launch_cnn_first(const float *up, const float *pan, size_t pan_stride, const float *prm,
                       int B, int H, int W, __nv_bfloat16 *a1, cudaStream_t st) {
-    const size_t P = (size_t)B * H * W;
+    const size_t P = (size_t)B * H * (W / 2);
     cnn_first_kernel<<<blocks_for(P, 256), 256, 0, st>>>(up, pan, pan_stride, prm, B, H, W, a1);
 }
 
