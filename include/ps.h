@@ -65,6 +65,17 @@ typedef struct ps_kernel_params {
     float th;           /* stop when ||u^t - u^{t+1}|| / ||u^{t+1}|| < th (1e-5) */
 } ps_kernel_params;
 
+/* Cross-channel prior of Algorithm 2 (Sec. IV-D, Table III): the filter F_d
+ * whose local affine relation to F_d Y is regularised. */
+typedef enum ps_prior {
+    PS_PRIOR_LLP = 0, /* the 5-point Laplacian (the paper's method)        */
+    PS_PRIOR_LPF = 1, /* the blur kernel u (low-pass)                      */
+    PS_PRIOR_HPF = 2, /* delta - u (high-pass)                             */
+    PS_PRIOR_LPP = 3, /* delta (the pixels)                                */
+    PS_PRIOR_LGC = 4  /* horizontal and vertical first differences, each
+                         with its own affine model (Eq. reg2_lgc)          */
+} ps_prior;
+
 /* Parameters of Algorithm 2 (per-band HRMS solve). */
 typedef struct ps_hrms_params {
     float lambda;       /* LLP weight of Eq. pansharp (2e-4, Sec. IV-F)        */
@@ -107,6 +118,11 @@ typedef struct ps_hrms_params {
                            Frobenius norm, ||z_k+1 - z_k|| / ||z_k+1|| < tol
                            (the paper's tol is 5e-5); it depends on the start
                            point and on the preconditioner.              */
+    int prior;          /* ps_prior (default PS_PRIOR_LLP). The alternatives
+                           replace L by their filters in Eq. Z_ini_matting,
+                           the guided filter and Eq. Z_solution; they take
+                           the plain CG (precond must be 0) and one branch
+                           per iteration.                                */
 } ps_hrms_params;
 
 /* Per-band result of the Z0 conjugate-gradient solve. */

@@ -27,7 +27,8 @@ class HrmsParams(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("exact_weight", ctypes.c_int),
                 ("host_loop", ctypes.c_int), ("precond", ctypes.c_int),
                 ("precond_gamma", ctypes.c_float), ("warm", ctypes.c_int),
-                ("cnn_params", ctypes.c_void_p), ("stop_rule", ctypes.c_int)]
+                ("cnn_params", ctypes.c_void_p), ("stop_rule", ctypes.c_int),
+                ("prior", ctypes.c_int)]
 
 
 class Tuning(ctypes.Structure):

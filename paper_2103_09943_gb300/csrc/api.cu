@@ -142,6 +142,8 @@ ps_status check_hrms(const ps_hrms_params *p) {
         return PS_ERR_INVALID_ARG;
     if (p->warm < 0 || p->warm > 2) return PS_ERR_INVALID_ARG;
     if (p->stop_rule != 0 && p->stop_rule != 1) return PS_ERR_INVALID_ARG;
+    if (p->prior < PS_PRIOR_LLP || p->prior > PS_PRIOR_LGC) return PS_ERR_INVALID_ARG;
+    if (p->prior != PS_PRIOR_LLP && p->precond) return PS_ERR_INVALID_ARG;
     if (p->warm == 2 && !p->cnn_params) return PS_ERR_INVALID_ARG;
     return PS_OK;
 }
@@ -245,6 +247,18 @@ int split_begin(int N, int split, int k) {
 // iterations (the direction p alternates between two buffers). Executable
 // graphs are cached per argument set.
 // ---------------------------------------------------------------------------
+// The alternative priors' operator pieces: filters F_d (radius fR), the
+// statistics of their guides F_d Y, four N x H x W scratch images, the FP64
+// symbol sum_d |F_d^|^2 of the Z step.
+struct PriorOps {
+    int prior, nf, fR, r;
+    int N, H, W, pad_;
+    const float *filt[2];
+    const float4 *gst4[2];
+    float *t[4];
+    double *tsym;
+};
+
 struct CgLoopArgs {
     int dev;
     int N, H, W, c, R, r;
@@ -259,8 +273,36 @@ struct CgLoopArgs {
     int split;    // 1, 2 or 4: parts of the bands run as parallel branches
     Tuning tune;  // launch choices (part of the graph cache key)
     int pad_;
+    PriorOps po;  // po.prior != PS_PRIOR_LLP: the generic-filter loop
     bool operator==(const CgLoopArgs &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
 };
+
+// sum_d F_d^T W_d(F_d z) with W_d the matting matrix of guide d (gf = 0) or
+// its guided filter (gf = 1): into t[3] (d = 0) and t[1] (d = 1).
+void prior_terms(const PriorOps &o, const float *z, int gf, const CgBand *bands,
+                 const CgGlobal *g, cudaStream_t st) {
+    for (int d = 0; d < o.nf; ++d) {
+        launch_db(z, nullptr, nullptr, nullptr, nullptr, 0, o.N, o.H, o.W, 1, o.filt[d], o.fR,
+                  o.t[0], st);
+        launch_prior_window(o.t[0], o.gst4[d], o.N, o.H, o.W, o.r, gf, o.t[1], o.t[2], o.t[0],
+                            bands, g, st);
+        launch_adj(o.t[0], o.N, o.H, o.W, 1, o.filt[d], o.fR, d == 0 ? o.t[3] : o.t[1], st);
+    }
+}
+
+// One CG iteration under an alternative prior (all bands, one branch):
+// p = r + beta p and v = D B p; q = lam sum_d F_d^T M_d F_d p with p^T q and
+// alpha; x, r, beta and the stop test.
+void enqueue_prior_iteration(const CgLoopArgs &a, const float *p_old, float *p_new,
+                             cudaStream_t st) {
+    const size_t HW = (size_t)a.H * a.W;
+    launch_db(p_old, a.rv, p_new, a.bands, a.g, 1, a.N, a.H, a.W, a.c, a.u, a.R, a.v, st);
+    prior_terms(a.po, p_new, 0, a.bands, a.g, st);
+    launch_prior_combine(a.po.t[3], a.po.nf == 2 ? a.po.t[1] : nullptr, p_new, a.ap, a.N, HW,
+                         a.lam, a.bands, a.g, st);
+    launch_cg_update(a.x, a.rv, p_new, a.ap, a.v, a.u, a.R, a.c, a.N, a.H, a.W, a.bands, a.g,
+                     st);
+}
 
 struct CgGraph {
     CgLoopArgs key;
@@ -312,7 +354,9 @@ void enqueue_bands(const CgLoopArgs &a, int b0, int n, const float *p_old, float
 
 void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, int use_cond,
                        cudaGraphConditionalHandle h, cudaStream_t st) {
-    if (a.split > 1) {
+    if (a.po.prior != PS_PRIOR_LLP) {
+        enqueue_prior_iteration(a, p_old, p_new, st);
+    } else if (a.split > 1) {
         // parts of the bands as parallel branches, joined before the loop
         // control
         const Branches br = device_branches();
@@ -435,7 +479,7 @@ PrecArgs make_prec_args(const Ws &ws, const float *r, float *z, int N, int H, in
 // ---------------------------------------------------------------------------
 ps_status run_zstep(const Ws &ws, const float *lrms, const float *z0, const float *u, int N,
                     int H, int W, int c, int R, int r, float lam_z, float *out,
-                    cudaStream_t st) {
+                    cudaStream_t st, const PriorOps *po = nullptr) {
     FftPlan pw, ph;
     if (!fft_make_plan(W, &pw) || !fft_make_plan(H, &ph)) return PS_ERR_UNSUPPORTED;
     const size_t HW = (size_t)H * W;
@@ -447,25 +491,38 @@ ps_status run_zstep(const Ws &ws, const float *lrms, const float *z0, const floa
     double2 *bhat = ws.at<double2>(ws.L.bhat);
     float2 *twW32 = ws.at<float2>(ws.L.twW32), *twH32 = ws.at<float2>(ws.L.twH32);
     double2 *twW64 = ws.at<double2>(ws.L.twW64), *twH64 = ws.at<double2>(ws.L.twH64);
-    // right-hand side B^T D^T X + lam' L L-hat, packed two bands per image
-    LlpArgs la = {};
-    la.in = z0;
-    la.lr = lrms;
-    la.st4 = ws.at<float4>(ws.L.st4);
-    la.u = u;
-    la.R = R;
-    la.c = c;
-    la.H = H;
-    la.W = W;
-    la.N = N;
-    la.lam = lam_z;
-    la.cout = cbuf64;
-    launch_llp(la, LLP_ZRHS, r, N, st);
+    const double *tsym = nullptr;
+    if (po && po->prior != PS_PRIOR_LLP) {
+        // B^T D^T X + lam' sum_d F_d^T L-hat_d, L-hat_d the guided filter of
+        // F_d Z0 with guide F_d Y; the symbol sum_d |F_d^|^2 replaces S^2
+        prior_terms(*po, z0, 1, nullptr, nullptr, st);
+        if (po->nf == 2)
+            launch_prior_combine(po->t[3], po->t[1], nullptr, po->t[3], N, HW, 1.0f, nullptr,
+                                 nullptr, st);
+        launch_adj(lrms, N, H, W, c, u, R, po->t[0], st);
+        launch_prior_pack(po->t[0], po->t[3], lam_z, N, HW, cbuf64, st);
+        tsym = po->tsym;
+    } else {
+        // right-hand side B^T D^T X + lam' L L-hat, packed two bands per image
+        LlpArgs la = {};
+        la.in = z0;
+        la.lr = lrms;
+        la.st4 = ws.at<float4>(ws.L.st4);
+        la.u = u;
+        la.R = R;
+        la.c = c;
+        la.H = H;
+        la.W = W;
+        la.N = N;
+        la.lam = lam_z;
+        la.cout = cbuf64;
+        launch_llp(la, LLP_ZRHS, r, N, st);
+    }
     // forward 2-D FFT (FP64), group solve, inverse 2-D FFT (FP32)
     launch_fft_rows64(cbuf64, pw, nimg * H, twW64, st);
     launch_transpose64(cbuf64, ctmp64, H, W, nimg, st);
     launch_fft_rows64(ctmp64, ph, nimg * W, twH64, st);
-    launch_alias_solve(ctmp64, bhat, sol32, nimg, H, W, c, lam_z, st);
+    launch_alias_solve(ctmp64, bhat, sol32, nimg, H, W, c, lam_z, st, tsym);
     launch_fft_rows32(sol32, ph, nimg * W, twH32, 1, nullptr, N, HW, st);
     launch_transpose32(sol32, ctmp32, W, H, nimg, st);
     launch_fft_rows32(ctmp32, pw, nimg * H, twW32, 1, out, N, HW, st);
@@ -481,11 +538,62 @@ ps_status run_zstep(const Ws &ws, const float *lrms, const float *z0, const floa
 struct SolveCall {
     Ws ws;
     size_t ws_bytes;
+    size_t prior_off;  // start of the alternative prior's scratch (prior != LLP)
     const float *lrms, *pan, *u, *z_init;
     float *hrms, *z0;
     int N, H, W, c, R;
     ps_hrms_params p;
 };
+
+// Scratch of an alternative prior, after the base layout (and after the
+// network's workspace when that is used): four N x H x W images, the
+// statistics of two guides, one FP64 spectrum, the FP64 symbol, two filters.
+size_t prior_bytes(int N, int H, int W) {
+    const size_t HW = (size_t)H * W;
+    return 4 * align_up((size_t)N * HW * 4) + 3 * align_up(HW * 16) + align_up(HW * 8) +
+           2 * align_up((size_t)kMaxTaps * 4);
+}
+
+size_t prior_offset(const Layout &L, int N, int H, int W, const ps_hrms_params *p) {
+    return align_up(L.cnn + (p && p->warm == 2 ? ps_cnn_workspace_size(N, H, W, 0) : 0));
+}
+
+// The prior's operator pieces over the scratch at `off` (pointers only).
+PriorOps prior_ops(const Ws &ws, size_t off, int prior, int N, int H, int W, int R, int r) {
+    PriorOps o;
+    memset(&o, 0, sizeof(o));
+    o.prior = prior;
+    o.nf = prior_filter_count(prior);
+    o.fR = prior_filter_radius(prior, R);
+    o.r = r;
+    o.N = N;
+    o.H = H;
+    o.W = W;
+    const size_t HW = (size_t)H * W;
+    size_t at = off;
+    for (int k = 0; k < 4; ++k) {
+        o.t[k] = ws.at<float>(at);
+        at += align_up((size_t)N * HW * 4);
+    }
+    float4 *g0 = ws.at<float4>(at);
+    at += align_up(HW * 16);
+    float4 *g1 = ws.at<float4>(at);
+    at += align_up(HW * 16);
+    o.gst4[0] = g0;
+    o.gst4[1] = g1;
+    at += align_up(HW * 16);  // FP64 filter spectrum (prior_fhat)
+    o.tsym = ws.at<double>(at);
+    at += align_up(HW * 8);
+    o.filt[0] = ws.at<float>(at);
+    at += align_up((size_t)kMaxTaps * 4);
+    o.filt[1] = ws.at<float>(at);
+    return o;
+}
+
+double2 *prior_fhat(const Ws &ws, size_t off, int N, int H, int W) {
+    const size_t HW = (size_t)H * W;
+    return ws.at<double2>(off + 4 * align_up((size_t)N * HW * 4) + 2 * align_up(HW * 16));
+}
 
 ps_status make_solve_call(const float *d_lrms, const float *d_pan, const float *d_kernel, int N,
                           int H, int W, int ratio, int R, const ps_hrms_params *p,
@@ -502,6 +610,11 @@ ps_status make_solve_call(const float *d_lrms, const float *d_pan, const float *
     if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &sc->ws)) != PS_OK) return s;
     if (p->warm == 2 && !d_z_init && ws_bytes < sc->ws.L.cnn + ps_cnn_workspace_size(N, H, W, 0))
         return PS_ERR_WORKSPACE;
+    sc->prior_off = 0;
+    if (p->prior != PS_PRIOR_LLP) {
+        sc->prior_off = prior_offset(sc->ws.L, N, H, W, p);
+        if (ws_bytes < sc->prior_off + prior_bytes(N, H, W)) return PS_ERR_WORKSPACE;
+    }
     sc->ws_bytes = ws_bytes;
     sc->lrms = d_lrms;
     sc->pan = d_pan;
@@ -531,8 +644,32 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
     CgBand *bands = ws.at<CgBand>(ws.L.bands);
     CgGlobal *g = ws.at<CgGlobal>(ws.L.glob);
 
-    launch_pan_stats(sc.pan, H, W, p->r, p->eps, nullptr, nullptr, nullptr, st4, st);
+    PriorOps po;
+    memset(&po, 0, sizeof(po));
+    if (p->prior == PS_PRIOR_LLP) {
+        launch_pan_stats(sc.pan, H, W, p->r, p->eps, nullptr, nullptr, nullptr, st4, st);
+    } else {
+        po = prior_ops(ws, sc.prior_off, p->prior, N, H, W, R, p->r);
+        launch_prior_filters(d_kernel, R, p->prior, const_cast<float *>(po.filt[0]),
+                             const_cast<float *>(po.filt[1]), st);
+        // the guides F_d Y and their window statistics
+        for (int d = 0; d < po.nf; ++d) {
+            launch_db(sc.pan, nullptr, nullptr, nullptr, nullptr, 0, 1, H, W, 1, po.filt[d],
+                      po.fR, po.t[0], st);
+            launch_guide_stats(po.t[0], H, W, p->r, p->eps, const_cast<float4 *>(po.gst4[d]),
+                               st);
+        }
+    }
     if ((s = prepare_spectrum(ws, d_kernel, H, W, R, st)) != PS_OK) return s;
+    if (p->prior != PS_PRIOR_LLP) {
+        // the Z step's symbol sum_d |F_d^|^2
+        double2 *fh = prior_fhat(ws, sc.prior_off, N, H, W);
+        for (int d = 0; d < po.nf; ++d) {
+            launch_kernel_spectrum(po.filt[d], po.fR, H, W, ws.at<double2>(ws.L.twW64),
+                                   ws.at<double2>(ws.L.twH64), fh, st);
+            launch_symbol_add(fh, po.tsym, HW, d == 0, st);
+        }
+    }
     launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
     if (!d_z_init && p->warm >= 1) {
         // bicubic start point, written where the iterate lives
@@ -546,7 +683,16 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
         }
         d_z_init = x;
     }
-    if (d_z_init) {
+    if (d_z_init && p->prior != PS_PRIOR_LLP) {
+        // A z_init = B^T D^T D B z_init + lam sum_d F_d^T M_d F_d z_init
+        launch_db(d_z_init, nullptr, nullptr, nullptr, nullptr, 0, N, H, W, c, d_kernel, R, v,
+                  st);
+        prior_terms(po, d_z_init, 0, nullptr, nullptr, st);
+        launch_prior_combine(po.t[3], po.nf == 2 ? po.t[1] : nullptr, nullptr, ap, N, HW,
+                             p->lambda, nullptr, nullptr, st);
+        launch_adj(v, N, H, W, c, d_kernel, R, po.t[0], st);
+        launch_prior_combine(ap, po.t[0], nullptr, ap, N, HW, 1.0f, nullptr, nullptr, st);
+    } else if (d_z_init) {
         launch_db(d_z_init, nullptr, nullptr, nullptr, nullptr, 0, N, H, W, c, d_kernel, R, v,
                   st);
         LlpArgs la = {};
@@ -586,6 +732,7 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
     a->pa = pa;
     a->tune = tuning_get(a->dev, N, H, W, c, p->r);
     a->split = a->tune.split ? a->tune.split : ((N >= 4) ? 2 : 1);
+    a->po = po;
     return PS_OK;
 }
 
@@ -594,7 +741,7 @@ ps_status solve_epilogue(const SolveCall &sc, const CgLoopArgs &a, cudaStream_t 
     const float lam_z =
         p->lambda * (p->exact_weight ? (float)((2 * p->r + 1) * (2 * p->r + 1)) : 1.0f);
     return run_zstep(sc.ws, sc.lrms, a.x, sc.u, sc.N, sc.H, sc.W, sc.c, sc.R, p->r, lam_z,
-                     sc.hrms, st);
+                     sc.hrms, st, &a.po);
 }
 
 // Per-band CG results (after the work that wrote them has finished).
@@ -744,6 +891,7 @@ void ps_default_hrms_params(ps_hrms_params *p) {
     p->warm = 0;
     p->cnn_params = nullptr;
     p->stop_rule = 0;
+    p->prior = PS_PRIOR_LLP;
 }
 
 const char *ps_status_string(int s) {
@@ -766,6 +914,8 @@ size_t ps_workspace_size(int N, int H, int W, int ratio, int R, const ps_hrms_pa
     if (check_dims(N, H, W, ratio, R) != PS_OK) return 0;
     Layout L;
     if (!make_layout(N, H, W, ratio, R, &L)) return 0;
+    if (hp && hp->prior != PS_PRIOR_LLP)
+        return prior_offset(L, N, H, W, hp) + prior_bytes(N, H, W) + kAlign;
     if (hp && hp->warm == 2) return L.total + ps_cnn_workspace_size(N, H, W, 0);
     return L.total;
 }
@@ -1083,6 +1233,7 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
     key_put(key, hp->warm);
     key_put(key, hp->cnn_params);
     key_put(key, hp->stop_rule);
+    key_put(key, hp->prior);
     key_put(key, kp != nullptr);
     if (kp) {
         key_put(key, kp->lambda_omega);

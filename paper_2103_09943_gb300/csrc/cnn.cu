@@ -4,14 +4,16 @@
 //
 // Implicit GEMM per tile of 128 consecutive pixels of one row:
 //   D[128 px][32 out] = sum over 9 taps of A_tap[128 px][32 in] B_tap[32 in][32 out]
-// i.e. 18 MMAs of M = 128, N = 32, K = 16. Activations are NHWC BF16 (64 B
+// i.e. 18 MMAs of M = 128, N = 32, K = 16 per row, issued as 24 MMAs (N = 32
+// and 64) per pair of rows. Activations are NHWC BF16 (64 B
 // per pixel). Three input rows of 130 pixels (the tile and its halo) sit in
 // shared memory as four planes of 8-channel chunks, plane[j][p] = channels
 // 8j .. 8j+7 of pixel p (16 B): in this layout the A operand of every tap is
 // a canonical no-swizzle K-major matrix (core matrices of 8 pixels x 16 B,
 // 128 B apart along M, one plane apart along K) whose start address is the
 // tap's pixel shift, so no im2col copy is made. The B operand (weights) is
-// packed once per launch in the same core-matrix form.
+// packed once per launch in the same core-matrix form, the three vertical
+// taps of each dx stacked along N.
 //
 // Each CTA walks vertical strips 128 pixels wide, row after row, as a
 // warp-specialised pipeline (a cp.async producer warp, one MMA-issuing
@@ -33,26 +35,35 @@ constexpr int kTileM = 128;
 constexpr int kHalo = kTileM + 2;
 constexpr int kPlane = kHalo * 16;      // bytes of one 8-channel plane of a halo row
 constexpr int kRowB = 4 * kPlane;       // bytes of one halo row
-constexpr int kWTap = 4 * kCh * 16;     // bytes of one tap's B operand
-constexpr int kWBytes = 9 * kWTap;
-constexpr uint32_t kIdesc = umma_idesc_bf16(128, 32);
+constexpr int kWStack = 3 * kCh;         // B rows of one dx: W(dy = 1), W(0), W(-1)
+constexpr int kWChunk = kWStack * 16;    // bytes of one 8-channel K chunk of a dx block
+constexpr int kWdx = 4 * kWChunk;        // bytes of one dx block
+constexpr int kWBytes = 3 * kWdx;
+constexpr uint32_t kIdesc32 = umma_idesc_bf16(128, 32);
+constexpr uint32_t kIdesc64 = umma_idesc_bf16(128, 64);
 
 __device__ __forceinline__ int wrapm(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
 }
 
-// The B operand of one layer: element (tap, k, n) at byte
-// tap * kWTap + (k / 8) * 512 + n * 16 + (k % 8) * 2, k the input and n the
-// output channel of the GEMM. Forward: n = out, k = in, the tap as is.
-// Backward data (the adjoint): n = in, k = out and the tap mirrored.
+// The B operand of one layer, K-major: for each horizontal tap offset dx the
+// three vertical taps are stacked along N, rows 32 (1 - dy) + n, so that
+// W(dy = 1) | W(0) and W(0) | W(-1) are each one N = 64 operand. Element
+// (dx, dy, k, n) sits at byte (dx + 1) * kWdx + (k / 8) * kWChunk
+// + (32 (1 - dy) + n) * 16 + (k % 8) * 2, k the input and n the output
+// channel of the GEMM. Forward: n = out, k = in, the tap as is. Backward data
+// (the adjoint): n = in, k = out and the tap mirrored.
 __global__ void pack_w32_kernel(const float *__restrict__ w, __nv_bfloat16 *__restrict__ out,
                                 int adjoint) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 9 * kCh * kCh) return;
-    const int tap = i / 1024, r = i - tap * 1024;
-    const int j = r / 256, n = (r - j * 256) / 8, e = r & 7;
+    const int dxi = i / (kWdx / 2), r = i - dxi * (kWdx / 2);
+    const int j = r / (kWChunk / 2), r2 = r - j * (kWChunk / 2);
+    const int ns = r2 / 8, e = r2 & 7;
+    const int dy = 1 - ns / kCh, n = ns % kCh;
     const int k = 8 * j + e;
+    const int tap = (dy + 1) * 3 + dxi;
     const float v = adjoint ? w[((size_t)k * kCh + n) * 9 + (8 - tap)]
                             : w[((size_t)n * kCh + k) * 9 + tap];
     out[i] = __float2bfloat16_rn(v);
@@ -66,9 +77,13 @@ __global__ void pack_w32_kernel(const float *__restrict__ w, __nv_bfloat16 *__re
 //              into a ring of kRingWs slots; kDepth rows in flight per lane;
 //              a row is announced on full[slot] (32 lane arrivals) once its
 //              copies have landed and been fenced for the async proxy
-//   warp 1     MMA issuer (one thread): per output row, 18 tcgen05.mma into
-//              one of kAcc TMEM accumulators, then commits to acc_full[acc]
-//              and to empty[slot] of the input row no longer needed
+//   warp 1     MMA issuer (one thread): per pair of output rows k, k + 1,
+//              one of kAcc TMEM accumulators of 64 columns (row k in 0..31,
+//              k + 1 in 32..63). Input row k - 1 feeds only row k and row k + 2
+//              only row k + 1 (N = 32, each starts its half); rows k and k + 1
+//              feed both (N = 64 with the weights stacked along N): 24 MMAs
+//              of K = 16 for two rows instead of 36. Then commits to
+//              acc_full[acc] and to empty[slot] of input rows no longer needed
 //   warps 2-9  epilogue, two groups of four warps taking alternate output
 //              rows (the fused last layer, whose rows chain, uses group 0
 //              only): warp w reads TMEM lanes 32 (w mod 4) .. + 31 (one pixel
@@ -81,9 +96,9 @@ __global__ void pack_w32_kernel(const float *__restrict__ w, __nv_bfloat16 *__re
 // ---------------------------------------------------------------------------
 constexpr int kRingWs = 8;
 constexpr int kDepth = 4;
-// the producer waits for a slot that output row q - kRingWs + 2 frees while
-// it holds kDepth - 1 rows unannounced: the ring must exceed kDepth + 1
-static_assert(kRingWs > kDepth + 1, "ring too short for the prefetch depth");
+// an MMA group reads four input rows and frees two; the producer holds
+// kDepth - 1 issued rows unannounced: the ring must hold kDepth + 3 rows
+static_assert(kRingWs >= kDepth + 3, "ring too short for the prefetch depth");
 constexpr int kAcc = 4;
 constexpr int kWsThreads = 320;
 constexpr int kExtraW5 = 304 * 4;
@@ -155,13 +170,15 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
         }
         for (int k = 0; k < kAcc; ++k) {
             mbar_init(accf_bar(k), 1);
-            mbar_init(acce_bar(k), 4);
+            // the epilogue warps that read an accumulator: both groups in the
+            // plain form, group 0 alone in the fused last layer
+            mbar_init(acce_bar(k), MODE == CONV_LAST ? 4 : 8);
         }
         mbar_init(done_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(smem_u32(tslot), 32 * kAcc);
+    if (warp == 1) tmem_alloc(smem_u32(tslot), 64 * kAcc);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -239,55 +256,72 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
                 return mbar_wait_or_abort(full_bar((int)(row % kRingWs)), (row / kRingWs) & 1u,
                                           abort_flag);
             };
-            // descriptors: B per (tap, K half) fixed; A is the ring base
-            // descriptor plus the 16-byte-unit offset of slot, K half and dx
-            uint64_t bdesc[18];
+            // descriptors: B per (dx, K half, stacked slice) fixed, slice 0 at
+            // W(1) (N = 64: W(1) | W(0)), 1 at W(0) (W(0) | W(-1)), 2 at W(-1);
+            // A is the ring base descriptor plus the 16-byte-unit offset of
+            // slot, K half and dx
+            uint64_t bdesc[3][2][3];
 #pragma unroll
-            for (int tap = 0; tap < 9; ++tap)
+            for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                 for (int sk = 0; sk < 2; ++sk)
-                    bdesc[2 * tap + sk] = umma_desc(w_u32 + tap * kWTap + 2 * sk * 512, 512, 128);
+#pragma unroll
+                    for (int sl = 0; sl < 3; ++sl)
+                        bdesc[dx][sk][sl] =
+                            umma_desc(w_u32 + dx * kWdx + 2 * sk * kWChunk + sl * kCh * 16,
+                                      kWChunk, 128);
             const uint64_t adesc0 = umma_desc(ring_u32, kPlane, 128);
+            // one input row times one stacked slice into D columns dcol ..
+            auto mma_row = [&](uint32_t in_seq, uint32_t d, int sl, uint32_t idesc, bool &first) {
+                const uint64_t ar = adesc0 + (uint64_t)((in_seq % kRingWs) * (kRowB >> 4));
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                    for (int sk = 0; sk < 2; ++sk) {
+                        const uint64_t ad = ar + (uint64_t)((2 * sk * kPlane + dx * 16) >> 4);
+                        umma_bf16(d, ad, bdesc[dx][sk][sl], idesc, first ? 0u : 1u);
+                        first = false;
+                    }
+            };
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
                 const ConvItem it = conv_item<MODE>(a, item, strips, chunks);
-                const int n_out = it.ye - it.ys;
-                ok = wait_full(q) && wait_full(q + 1);
-                for (int k = 0; k < n_out && ok; ++k, ++o) {
+                const int n_out = it.ye - it.ys, n_in = n_out + 2;
+                int waited = 0, freed = 0;  // input rows of the item waited for, released
+                // output rows k, k + 1 (one MMA group, one accumulator of 64
+                // columns: row k in columns 0..31, row k + 1 in 32..63) read
+                // input rows k .. k + 3
+                for (int k = 0; k < n_out && ok; k += 2, ++o) {
+                    const int cnt = min(2, n_out - k);
+                    for (; waited < k + cnt + 2 && ok; ++waited) ok = wait_full(q + waited);
                     const int acc = (int)(o % kAcc);
                     const uint32_t v = o / kAcc;
-                    if (!wait_full(q + k + 2) ||
-                        (v >= 1 && !mbar_wait_or_abort(acce_bar(acc), (v - 1) & 1u, abort_flag))) {
-                        ok = false;
-                        break;
-                    }
+                    if (ok && v >= 1)
+                        ok = mbar_wait_or_abort(acce_bar(acc), (v - 1) & 1u, abort_flag);
+                    if (!ok) break;
                     tc_fence_after();
-                    const uint32_t d = tbase + (uint32_t)(acc * 32);
-                    int kk = 0;
-#pragma unroll
-                    for (int dy = -1; dy <= 1; ++dy) {
-                        const uint64_t ar =
-                            adesc0 + (uint64_t)(((q + k + 1 + dy) % kRingWs) * (kRowB >> 4));
-#pragma unroll
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            const int tap = (dy + 1) * 3 + (dx + 1);
-#pragma unroll
-                            for (int sk = 0; sk < 2; ++sk) {
-                                const uint64_t ad =
-                                    ar + (uint64_t)((2 * sk * kPlane + (dx + 1) * 16) >> 4);
-                                umma_bf16(d, ad, bdesc[2 * tap + sk], kIdesc, kk > 0 ? 1u : 0u);
-                                ++kk;
-                            }
-                        }
+                    const uint32_t d = tbase + (uint32_t)(acc * 64);
+                    const uint32_t r0 = q + (uint32_t)k;
+                    if (cnt == 2) {
+                        // each D half starts fresh with its one-tap input row,
+                        // then the two shared rows add to both halves at once
+                        bool f0 = true, f1 = true, f2 = false;
+                        mma_row(r0, d, 2, kIdesc32, f0);            // row k - 1: W(-1) -> k
+                        mma_row(r0 + 3, d + 32, 0, kIdesc32, f1);   // row k + 2: W(1) -> k + 1
+                        mma_row(r0 + 1, d, 1, kIdesc64, f2);        // row k: W(0) | W(-1)
+                        mma_row(r0 + 2, d, 0, kIdesc64, f2);        // row k + 1: W(1) | W(0)
+                    } else {
+                        bool f0 = true;
+                        mma_row(r0, d, 2, kIdesc32, f0);
+                        mma_row(r0 + 1, d, 1, kIdesc32, f0);
+                        mma_row(r0 + 2, d, 0, kIdesc32, f0);
                     }
                     umma_commit(accf_bar(acc));
-                    // the input row above this output row is not read again
-                    umma_commit(empty_bar((int)((q + k) % kRingWs)));
-                    if (k == n_out - 1) {
-                        umma_commit(empty_bar((int)((q + k + 1) % kRingWs)));
-                        umma_commit(empty_bar((int)((q + k + 2) % kRingWs)));
-                    }
+                    // input rows below the next group's first are not read again
+                    const int keep = (k + cnt < n_out) ? k + cnt : n_in;
+                    for (; freed < keep; ++freed)
+                        umma_commit(empty_bar((int)((q + freed) % kRingWs)));
                 }
-                q += (uint32_t)(n_out + 2);
+                q += (uint32_t)n_in;
             }
             if (!ok) fail();
             // every MMA issued has completed before the CTA frees its TMEM
@@ -301,7 +335,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
         // ---------------- epilogue ----------------
         const int eg = warp & 3;             // TMEM lane group of this warp
         const int pix = 32 * eg + lane;      // pixel of the tile
-        const int grp = (warp - 2) >> 2;     // rows with o % 2 == grp
+        const int grp = (warp - 2) >> 2;     // row k + grp of each MMA group
         uint32_t o = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < items && ok && (MODE != CONV_LAST || grp == 0);
@@ -310,23 +344,9 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
             const int n_out = it.ye - it.ys;
             const int x = it.x0 + pix;
             float racc[3] = {0.f, 0.f, 0.f};  // last layer: output rows y - 1, y, y + 1
-            for (int k = 0; k < n_out; ++k, ++o) {
-                if (MODE != CONV_LAST && (int)(o & 1u) != grp) continue;
-                const int acc = (int)(o % kAcc);
-                const uint32_t v = o / kAcc;
-                ok = mbar_wait_or_abort(accf_bar(acc), v & 1u, abort_flag);
-                // the fused last layer exchanges partial sums among the four
-                // epilogue warps: they must agree to go on
-                if (MODE == CONV_LAST) ok = named_and(1, 128, ok);
-                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
-                if (!ok) break;
-                tc_fence_after();
-                float vals[32];
-                tmem_ld32(tbase + ((uint32_t)(32 * eg) << 16) + (uint32_t)(acc * 32), vals);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(acce_bar(acc));
-                const int y = it.ys + k;
+            // the fused last layer's row (exchange with the neighbours of the
+            // row, 3 running output rows) or the plain store of one row
+            auto process_row = [&](int y, float *vals) {
                 if (MODE == CONV_LAST) {
                     // act5 = ReLU(conv + bias) at this pixel, then its 9
                     // per-tap partial sums of the last layer: output
@@ -366,9 +386,9 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
                     racc[1] = racc[2];
                     racc[2] = 0.0f;
                     named_sync(1, 128);
-                    continue;
+                    return;
                 }
-                if (x >= W) continue;
+                if (x >= W) return;
                 const size_t oo = (((size_t)it.b * H + y) * W + x) * kCh;
                 if (a.mask) {
                     const uint4 *mp = reinterpret_cast<const uint4 *>(a.mask + oo);
@@ -394,6 +414,39 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
                 uint4 *op = reinterpret_cast<uint4 *>(a.out + oo);
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) op[qq] = pk[qq];
+            };
+            // one accumulator per pair of output rows (k in columns 0..31,
+            // k + 1 in 32..63): group g of the plain epilogue takes row
+            // k + g; the fused last layer takes both rows in order
+            for (int k = 0; k < n_out; k += 2, ++o) {
+                const int cnt = min(2, n_out - k);
+                const int acc = (int)(o % kAcc);
+                const uint32_t v = o / kAcc;
+                ok = mbar_wait_or_abort(accf_bar(acc), v & 1u, abort_flag);
+                // the fused last layer exchanges partial sums among the four
+                // epilogue warps: they must agree to go on
+                if (MODE == CONV_LAST) ok = named_and(1, 128, ok);
+                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t tl = tbase + ((uint32_t)(32 * eg) << 16) + (uint32_t)(acc * 64);
+                float vals[32];
+                if (MODE == CONV_LAST) {
+                    for (int h = 0; h < cnt; ++h) {
+                        tmem_ld32(tl + (uint32_t)(32 * h), vals);
+                        process_row(it.ys + k + h, vals);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(acce_bar(acc));
+                } else {
+                    const bool mine = grp < cnt;
+                    if (mine) tmem_ld32(tl + (uint32_t)(32 * grp), vals);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(acce_bar(acc));
+                    if (mine) process_row(it.ys + k + grp, vals);
+                }
             }
         }
         if (!ok) fail();
@@ -403,7 +456,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv32_tc_kernel(Conv32Args a) 
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tbase, 32 * kAcc);
+        tmem_dealloc(tbase, 64 * kAcc);
     }
 }
 

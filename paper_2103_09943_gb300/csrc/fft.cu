@@ -247,7 +247,8 @@ __device__ __forceinline__ double symbol_t(int ky, int kx, int H, int W, double 
 __global__ void __launch_bounds__(256) alias_solve_kernel(const double2 *__restrict__ spec,
                                                           const double2 *__restrict__ bspec,
                                                           float2 *__restrict__ sol, int H,
-                                                          int W, int c, float lamf) {
+                                                          int W, int c, float lamf,
+                                                          const double *__restrict__ tsym) {
     const int h = H / c, w = W / c;
     const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
     if (gidx >= h * w) return;
@@ -259,7 +260,8 @@ __global__ void __launch_bounds__(256) alias_solve_kernel(const double2 *__restr
     double tmin = 1e300;
     for (int p = 0; p < c; ++p)
         for (int q = 0; q < c; ++q) {
-            const double t = symbol_t(ky0 + p * h, kx0 + q * w, H, W, lam);
+            const int ky = ky0 + p * h, kx = kx0 + q * w;
+            const double t = tsym ? lam * tsym[(size_t)kx * H + ky] : symbol_t(ky, kx, H, W, lam);
             if (t < tmin) { tmin = t; pm = p; qm = q; }
         }
     cd num = {0.0, 0.0};
@@ -277,7 +279,8 @@ __global__ void __launch_bounds__(256) alias_solve_kernel(const double2 *__restr
                 vm = v;
                 continue;
             }
-            const double it = 1.0 / symbol_t(ky, kx, H, W, lam);
+            const double it =
+                1.0 / (tsym ? lam * tsym[(size_t)kx * H + ky] : symbol_t(ky, kx, H, W, lam));
             num.x += (v.x * r.x + v.y * r.y) * it;
             num.y += (v.x * r.y - v.y * r.x) * it;
             dsum += (v.x * v.x + v.y * v.y) * it;
@@ -296,7 +299,8 @@ __global__ void __launch_bounds__(256) alias_solve_kernel(const double2 *__restr
             const size_t o = (size_t)kx * H + ky;
             const double2 rf = S[o], bh = bspec[o];
             const cd v = {bh.x, -bh.y};
-            const double it = 1.0 / symbol_t(ky, kx, H, W, lam);
+            const double it =
+                1.0 / (tsym ? lam * tsym[(size_t)kx * H + ky] : symbol_t(ky, kx, H, W, lam));
             const cd vs = cd_mul(v, s);
             const cd x = {(rf.x - vs.x * icc) * it, (rf.y - vs.y * icc) * it};
             acc.x += v.x * x.x + v.y * x.y;
@@ -317,10 +321,10 @@ __global__ void __launch_bounds__(256) alias_solve_kernel(const double2 *__restr
 }
 
 void launch_alias_solve(const double2 *spec, const double2 *bspec, float2 *sol, int nimg, int H,
-                        int W, int c, float lam, cudaStream_t st) {
+                        int W, int c, float lam, cudaStream_t st, const double *tsym) {
     const int groups = (H / c) * (W / c);
     dim3 grd((groups + 255) / 256, nimg);
-    alias_solve_kernel<<<grd, 256, 0, st>>>(spec, bspec, sol, H, W, c, lam);
+    alias_solve_kernel<<<grd, 256, 0, st>>>(spec, bspec, sol, H, W, c, lam, tsym);
 }
 
 cudaError_t fft_set_attrs() {

@@ -81,8 +81,25 @@ void launch_kernel_embed(const float *u, int R, int H, int W, double2 *out, cuda
 void launch_kernel_spectrum(const float *u, int R, int H, int W, const double2 *twW,
                             const double2 *twH, double2 *out, cudaStream_t st);
 void launch_alias_solve(const double2 *spec, const double2 *bspec, float2 *sol, int nimg, int H,
-                        int W, int c, float lam, cudaStream_t st);
+                        int W, int c, float lam, cudaStream_t st, const double *tsym = nullptr);
 cudaError_t fft_set_attrs();
+
+// prior.cu: the alternative cross-channel priors
+int prior_filter_radius(int prior, int R);
+int prior_filter_count(int prior);
+void launch_prior_filters(const float *u, int R, int prior, float *f0, float *f1,
+                          cudaStream_t st);
+void launch_guide_stats(const float *G, int H, int W, int r, float eps, float4 *st4,
+                        cudaStream_t st);
+void launch_prior_window(const float *alpha, const float4 *st4, int N, int H, int W, int r,
+                         int gf, float *ta, float *tb, float *out, const CgBand *bands,
+                         const CgGlobal *g, cudaStream_t st);
+void launch_prior_combine(const float *t0, const float *t1, const float *p, float *q, int N,
+                          size_t HW, float lam, CgBand *bands, const CgGlobal *g,
+                          cudaStream_t st);
+void launch_symbol_add(const double2 *fh, double *T, size_t n, int first, cudaStream_t st);
+void launch_prior_pack(const float *b, const float *acc, float lam, int N, size_t HW,
+                       double2 *out, cudaStream_t st);
 
 // precond.cu: z = P^{-1} r, P = B^T D^T D B + lam L^T L (lam = lambda gamma)
 struct PrecArgs {
