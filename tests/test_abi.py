@@ -123,6 +123,22 @@ def test_argument_errors_return_before_launch(lib):
     st = lib.ps_op_precond(fake, 2, 96, 96, 4, fake, 3, ctypes.c_float(-1.0), fake, fake,
                            1 << 30, None)
     assert st == 1
+    # alternative priors: a valid id, and the plain CG
+    bad = HrmsParams.from_buffer_copy(hp)
+    bad.prior = 5
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
+                           None, None, fake, 1 << 30, None)
+    assert st == 1
+    bad.prior = 4
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
+                           None, None, fake, 1 << 30, None)
+    assert st == 1                                                  # precond with a prior
+    bad.precond = 0
+    need = lib.ps_workspace_size(4, 256, 256, 4, 4, ctypes.byref(bad))
+    assert need > lib.ps_workspace_size(4, 256, 256, 4, 4, ctypes.byref(hp))
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
+                           None, None, fake, need - 1024, None)
+    assert st == 4                                                  # its scratch is missing
     st = lib.ps_op_precond(fake, 2, 100, 100, 4, fake, 3, ctypes.c_float(1e-3), fake, fake,
                            1 << 30, None)
     assert st == 8                                                  # not 2^a 3^b
