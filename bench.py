@@ -342,7 +342,7 @@ def compare_variants(api, X, Y, cfg, kp, net, dev, steps=3):
     forms.append(("paper_setting_29x29_relchange",
                   dict(precond=0, warm=0, stop_rule=1, tol=5e-5), 14))
     for name, kw, R in forms:
-        hp = api.default_hrms_params(**kw)
+        hp = api.default_hrms_params(zstep_fp32=1, **kw)
         ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, R, dev, hp)
         _, _, _, bi = api.pansharpen(X, Y, cfg.ratio, R, kp, hp, ws=ws)
         ts = []
@@ -408,7 +408,8 @@ def run_gpu(args):
     warm = {"none": 0, "bicubic": 1, "cnn": 2}[args.warm] if (net or args.warm != "cnn") else 0
     hp = api.default_hrms_params(host_loop=1 if args.cg_loop == "host" else 0,
                                  precond=1 if args.precond == "fft" else 0, warm=warm,
-                                 cnn_params=net.params.data_ptr() if net else None)
+                                 cnn_params=net.params.data_ptr() if net else None,
+                                 zstep_fp32=0 if args.zstep_fp64 else 1)
     ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev, hp)
     # launch shapes of the tunable kernels, picked on this GPU before timing
     tuning = None
@@ -516,6 +517,7 @@ def run_gpu(args):
                        "cg_precond": ("FFT alias-group, gamma %g" % hp.precond_gamma)
                        if hp.precond else "none",
                        "warm_start": warm_note,
+                       "zstep": "FP64 forward FFT" if args.zstep_fp64 else "FP32",
                        "autotuned": tuning,
                        "admm_iters": kinfo.iters},
             "wall_s_timed_region": wall,
@@ -599,7 +601,8 @@ def run_batch(args):
     net, warm_note = load_warm_net(args.warm, dev)
     warm = {"none": 0, "bicubic": 1, "cnn": 2}[args.warm] if (net or args.warm != "cnn") else 0
     hp = api.default_hrms_params(precond=1 if args.precond == "fft" else 0, warm=warm,
-                                 cnn_params=net.params.data_ptr() if net else None)
+                                 cnn_params=net.params.data_ptr() if net else None,
+                                 zstep_fp32=0 if args.zstep_fp64 else 1)
     scenes = [(x, y, c.R) for x, y, c in zip(X, Y, cfgs)]
     batch = api.Batch(scenes, cfgs[0].ratio, hparams=hp, kparams=kp, estimate=True)
     kinfo, sinfo = batch.run(info=True)
@@ -657,7 +660,8 @@ def run_batch(args):
     if rank == 0 and not args.no_compare:
         variants = {}
         forms = [("sequential_same_form", hp),
-                 ("sequential_plain_cg_cold", api.default_hrms_params(precond=0, warm=0))]
+                 ("sequential_plain_cg_cold",
+                  api.default_hrms_params(precond=0, warm=0, zstep_fp32=hp.zstep_fp32))]
         for name, p in forms:
             wss = [api.workspace(c.bands, c.H, c.W, c.ratio, c.R, dev, p) for c in cfgs]
 
@@ -671,7 +675,7 @@ def run_batch(args):
             ms = _timed_steps(seq, max(1, min(args.steps, 2)), flush)
             variants[name] = {"ms_per_step": ms, "value": throughput(units, 1, ms * 1e-3)}
             del wss
-        pc = api.default_hrms_params(precond=0, warm=0)
+        pc = api.default_hrms_params(precond=0, warm=0, zstep_fp32=hp.zstep_fp32)
         bc = api.Batch(scenes, cfgs[0].ratio, hparams=pc, kparams=kp, estimate=True)
         bc.run()
         ms = _timed_steps(bc.run, max(1, min(args.steps, 2)), flush)
@@ -803,6 +807,9 @@ def parse(argv=None):
     ap.add_argument("--warm", default="cnn", choices=["cnn", "bicubic", "none"],
                     help="start point of the Z0 solve (cnn: the trained network when its "
                          "weights are present, else zeros)")
+    ap.add_argument("--zstep-fp64", action="store_true",
+                    help="Z step with the FP64 forward FFT (the plain-form precision) instead "
+                         "of all-FP32")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (default launch shapes; for profiler launch lists)")
     ap.add_argument("--no-compare", action="store_true",

@@ -118,6 +118,12 @@ typedef struct ps_hrms_params {
                            Frobenius norm, ||z_k+1 - z_k|| / ||z_k+1|| < tol
                            (the paper's tol is 5e-5); it depends on the start
                            point and on the preconditioner.              */
+    int zstep_fp32;     /* Z step of Eq. Z_solution: 0 (default) forward FFT and
+                           group solve in FP64, inverse in FP32 (rel-L2 to the
+                           exact solve ~1e-7); 1 all in FP32 through the
+                           preconditioner's register FFTs (~1e-5), for the
+                           mixed-precision form whose bar is 1e-3. LLP only;
+                           sizes the preconditioner does not take use FP64. */
     int prior;          /* ps_prior (default PS_PRIOR_LLP). The alternatives
                            replace L by their filters in Eq. Z_ini_matting,
                            the guided filter and Eq. Z_solution; they take
@@ -155,6 +161,8 @@ typedef struct ps_tuning {
                             then the short walk                             */
     int split;           /* parallel branches of a CG iteration (1, 2, 4)    */
     float split_us[3];   /* two CG iterations, candidates 1, 2, 4 branches   */
+    int llp_bands;       /* bands per CTA of that LLP kernel (1, 2)          */
+    float llp2_us[2];    /* two bands per CTA: long, short walk (2 ahead)    */
 } ps_tuning;
 
 /* Autotuner: times every candidate of each tunable kernel on N bands of
@@ -167,6 +175,13 @@ typedef struct ps_tuning {
 ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r,
                       const float *d_lrms, const float *d_pan, const float *d_kernel,
                       void *d_ws, size_t ws_bytes, void *stream, ps_tuning *h_out);
+
+/* The launch choices recorded for these sizes on the current device (all
+ * zero: the defaults), and their replacement, e.g. with choices an earlier
+ * process's ps_autotune found. Only the choice fields (prec_rows, llp_rows,
+ * llp_pf, split, llp_bands) are read or written; 0 keeps a default. */
+ps_status ps_get_tuning(int N, int H, int W, int ratio, int r, ps_tuning *h_out);
+ps_status ps_set_tuning(int N, int H, int W, int ratio, int r, const ps_tuning *h_in);
 
 /* Workspace bytes needed by ps_pansharpen (covers ps_estimate_kernel and
  * ps_solve_hrms for the same sizes; h_hrms may be NULL, and with warm == 2

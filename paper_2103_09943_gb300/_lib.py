@@ -28,14 +28,15 @@ class HrmsParams(ctypes.Structure):
                 ("host_loop", ctypes.c_int), ("precond", ctypes.c_int),
                 ("precond_gamma", ctypes.c_float), ("warm", ctypes.c_int),
                 ("cnn_params", ctypes.c_void_p), ("stop_rule", ctypes.c_int),
-                ("prior", ctypes.c_int)]
+                ("zstep_fp32", ctypes.c_int), ("prior", ctypes.c_int)]
 
 
 class Tuning(ctypes.Structure):
     _fields_ = [("prec_rows", ctypes.c_int), ("llp_rows", ctypes.c_int),
                 ("llp_pf", ctypes.c_int), ("prec_us", ctypes.c_float * 4),
                 ("llp_us", ctypes.c_float * 6), ("split", ctypes.c_int),
-                ("split_us", ctypes.c_float * 3)]
+                ("split_us", ctypes.c_float * 3), ("llp_bands", ctypes.c_int),
+                ("llp2_us", ctypes.c_float * 2)]
 
 
 class BandInfo(ctypes.Structure):
@@ -72,6 +73,8 @@ SIGNATURES = {
                            _P, _P, _P, _P, _P, _Z, _P]),
     "ps_autotune": (_I, [_I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _Z, _P,
                          ctypes.POINTER(Tuning)]),
+    "ps_get_tuning": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(Tuning)]),
+    "ps_set_tuning": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(Tuning)]),
     "ps_pansharpen": (_I, [_P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(KernelParams),
                            ctypes.POINTER(HrmsParams), _P, _P, ctypes.POINTER(KernelInfo),
                            _P, _P, _Z, _P]),

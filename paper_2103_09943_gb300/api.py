@@ -83,8 +83,25 @@ def autotune(N, H, W, ratio, R, r=1, ws=None, device=None, lrms=None, pan=None,
             "llp_pf": t.llp_pf,
             "llp_us": {f"{w}/{pf}": round(t.llp_us[3 * i + j], 2)
                        for i, w in enumerate(("long", "short")) for j, pf in enumerate((2, 4, 6))},
+            "llp_bands": t.llp_bands,
+            "llp2_us": {w: round(v, 2) for w, v in zip(("long/2", "short/2"), t.llp2_us) if v},
             "split": t.split,
             "split_us": {str(k): round(v, 2) for k, v in zip((1, 2, 4), t.split_us) if v}}
+
+
+def set_tuning(N, H, W, ratio, r=1, **choices) -> None:
+    """Record launch choices for these sizes (ps_set_tuning): prec_rows,
+    llp_rows, llp_pf, split, llp_bands; 0 or absent keeps a default."""
+    t = Tuning()
+    for k, v in choices.items():
+        setattr(t, k, v)
+    _check(_lib.load().ps_set_tuning(N, H, W, ratio, r, ctypes.byref(t)))
+
+
+def get_tuning(N, H, W, ratio, r=1) -> dict:
+    t = Tuning()
+    _check(_lib.load().ps_get_tuning(N, H, W, ratio, r, ctypes.byref(t)))
+    return {k: getattr(t, k) for k in ("prec_rows", "llp_rows", "llp_pf", "split", "llp_bands")}
 
 
 @dataclass

@@ -142,6 +142,7 @@ ps_status check_hrms(const ps_hrms_params *p) {
         return PS_ERR_INVALID_ARG;
     if (p->warm < 0 || p->warm > 2) return PS_ERR_INVALID_ARG;
     if (p->stop_rule != 0 && p->stop_rule != 1) return PS_ERR_INVALID_ARG;
+    if (p->zstep_fp32 != 0 && p->zstep_fp32 != 1) return PS_ERR_INVALID_ARG;
     if (p->prior < PS_PRIOR_LLP || p->prior > PS_PRIOR_LGC) return PS_ERR_INVALID_ARG;
     if (p->prior != PS_PRIOR_LLP && p->precond) return PS_ERR_INVALID_ARG;
     if (p->warm == 2 && !p->cnn_params) return PS_ERR_INVALID_ARG;
@@ -337,6 +338,7 @@ void enqueue_bands(const CgLoopArgs &a, int b0, int n, const float *p_old, float
     la.cg = 1;
     la.ty = a.tune.llp_rows;
     la.pf = a.tune.llp_pf;
+    la.nbd = a.tune.llp_bands;
     launch_llp_cgq2(la, a.r, n, st);
     launch_cg_update(a.x + o, a.rv + o, p_new + o, a.ap + o, v, a.u, a.R, a.c, n, a.H, a.W, bands,
                      a.g, st);
@@ -479,10 +481,33 @@ PrecArgs make_prec_args(const Ws &ws, const float *r, float *z, int N, int H, in
 // ---------------------------------------------------------------------------
 ps_status run_zstep(const Ws &ws, const float *lrms, const float *z0, const float *u, int N,
                     int H, int W, int c, int R, int r, float lam_z, float *out,
-                    cudaStream_t st, const PriorOps *po = nullptr) {
+                    cudaStream_t st, const PriorOps *po = nullptr, int fp32 = 0) {
     FftPlan pw, ph;
     if (!fft_make_plan(W, &pw) || !fft_make_plan(H, &ph)) return PS_ERR_UNSUPPORTED;
     const size_t HW = (size_t)H * W;
+    if (fp32 && !(po && po->prior != PS_PRIOR_LLP) && precond_supported(H, W, c) &&
+        aligned16(out)) {
+        // all FP32: the right-hand side as real bands, then the
+        // preconditioner's solve, whose operator B^T D^T D B + lam L^T L is
+        // the Z step's at lam = lam'
+        float *rhs = ws.at<float>(ws.L.z);
+        LlpArgs la = {};
+        la.in = z0;
+        la.lr = lrms;
+        la.st4 = ws.at<float4>(ws.L.st4);
+        la.u = u;
+        la.R = R;
+        la.c = c;
+        la.H = H;
+        la.W = W;
+        la.N = N;
+        la.lam = lam_z;
+        la.out = rhs;
+        launch_llp(la, LLP_ZRHS, r, N, st);
+        PrecArgs pa = make_prec_args(ws, rhs, out, N, H, W, c, lam_z, nullptr, nullptr);
+        launch_precond(pa, st);
+        return last_launch();
+    }
     const int nimg = (N + 1) / 2;
     double2 *cbuf64 = ws.at<double2>(ws.L.r);
     double2 *ctmp64 = ws.at<double2>(ws.L.pB);
@@ -741,7 +766,7 @@ ps_status solve_epilogue(const SolveCall &sc, const CgLoopArgs &a, cudaStream_t 
     const float lam_z =
         p->lambda * (p->exact_weight ? (float)((2 * p->r + 1) * (2 * p->r + 1)) : 1.0f);
     return run_zstep(sc.ws, sc.lrms, a.x, sc.u, sc.N, sc.H, sc.W, sc.c, sc.R, p->r, lam_z,
-                     sc.hrms, st, &a.po);
+                     sc.hrms, st, &a.po, p->zstep_fp32);
 }
 
 // Per-band CG results (after the work that wrote them has finished).
@@ -891,6 +916,7 @@ void ps_default_hrms_params(ps_hrms_params *p) {
     p->warm = 0;
     p->cnn_params = nullptr;
     p->stop_rule = 0;
+    p->zstep_fp32 = 0;
     p->prior = PS_PRIOR_LLP;
 }
 
@@ -1114,6 +1140,21 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
             }
         }
     }
+    // two bands per CTA (shared statistics), long and short walks
+    out.llp_bands = 1;
+    for (int k = 0; k < 2 && N >= 2; ++k) {
+        la.ty = llp_cgq2_rows(r, k);
+        la.pf = 2;
+        la.nbd = 2;
+        const float us = timed([&] { launch_llp_cgq2(la, r, N, st); });
+        out.llp2_us[k] = us;
+        if (us < bestl) {
+            bestl = us;
+            out.llp_rows = la.ty;
+            out.llp_pf = la.pf;
+            out.llp_bands = 2;
+        }
+    }
     // branches of the CG iteration, when the scene is given: whole solves of
     // 20 iterations (tolerance out of reach) per candidate, on the caller's
     // data; the solves' results go to scratch (the preconditioner's z buffer)
@@ -1128,7 +1169,8 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
         for (int k = 0; k < 3; ++k) {
             if (splits[k] > 1 && N < 2 * splits[k]) continue;
             tuning_set(dev, N, H, W, ratio, r,
-                       Tuning{out.prec_rows, out.llp_rows, splits[k], out.llp_pf});
+                       Tuning{out.prec_rows, out.llp_rows, splits[k], out.llp_pf,
+                              out.llp_bands});
             float best = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, st);
@@ -1151,8 +1193,42 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if ((s = last_launch()) != PS_OK) return s;
-    tuning_set(dev, N, H, W, ratio, r, Tuning{out.prec_rows, out.llp_rows, out.split, out.llp_pf});
+    tuning_set(dev, N, H, W, ratio, r,
+               Tuning{out.prec_rows, out.llp_rows, out.split, out.llp_pf, out.llp_bands});
     if (h_out) *h_out = out;
+    return PS_OK;
+}
+
+ps_status ps_get_tuning(int N, int H, int W, int ratio, int r, ps_tuning *h_out) {
+    if (!h_out) return PS_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PS_ERR_CUDA;
+    const Tuning t = tuning_get(dev, N, H, W, ratio, r);
+    memset(h_out, 0, sizeof(*h_out));
+    h_out->prec_rows = t.prec_rows;
+    h_out->llp_rows = t.llp_rows;
+    h_out->llp_pf = t.llp_pf;
+    h_out->split = t.split;
+    h_out->llp_bands = t.llp_bands;
+    return PS_OK;
+}
+
+ps_status ps_set_tuning(int N, int H, int W, int ratio, int r, const ps_tuning *h_in) {
+    ps_status s;
+    if (!h_in) return PS_ERR_INVALID_ARG;
+    if ((s = check_dims(N, H, W, ratio, 0)) != PS_OK) return s;
+    if (r < 1 || r > kMaxWinR) return PS_ERR_INVALID_ARG;
+    const ps_tuning &t = *h_in;
+    if (t.prec_rows && !precond_rows_ok(H, W, ratio, t.prec_rows)) return PS_ERR_INVALID_ARG;
+    if (t.llp_rows && t.llp_rows != llp_cgq2_rows(r, 0) && t.llp_rows != llp_cgq2_rows(r, 1))
+        return PS_ERR_INVALID_ARG;
+    if (t.llp_pf && t.llp_pf != 2 && t.llp_pf != 4 && t.llp_pf != 6) return PS_ERR_INVALID_ARG;
+    if (t.split && t.split != 1 && t.split != 2 && t.split != 4) return PS_ERR_INVALID_ARG;
+    if (t.llp_bands && t.llp_bands != 1 && t.llp_bands != 2) return PS_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PS_ERR_CUDA;
+    tuning_set(dev, N, H, W, ratio, r, Tuning{t.prec_rows, t.llp_rows, t.split, t.llp_pf,
+                                              t.llp_bands});
     return PS_OK;
 }
 
@@ -1234,6 +1310,7 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
     key_put(key, hp->cnn_params);
     key_put(key, hp->stop_rule);
     key_put(key, hp->prior);
+    key_put(key, hp->zstep_fp32);
     key_put(key, kp != nullptr);
     if (kp) {
         key_put(key, kp->lambda_omega);
@@ -1256,7 +1333,7 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
         const int dims[5] = {q.N, q.H, q.W, q.ratio, q.R};
         key_put(key, dims);
         const Tuning t = tuning_get(dev, q.N, q.H, q.W, q.ratio, hp->r);
-        const int tk[4] = {t.prec_rows, t.llp_rows, t.split, t.llp_pf};
+        const int tk[5] = {t.prec_rows, t.llp_rows, t.split, t.llp_pf, t.llp_bands};
         key_put(key, tk);
     }
     cudaGraphExec_t exec = nullptr;

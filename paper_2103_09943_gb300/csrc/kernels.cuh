@@ -18,12 +18,14 @@ struct LlpArgs {
     int R, c, H, W, N;
     float lam;
     float *out;         // N x H x W (APPLY, GF)
-    double2 *cout;      // packed complex images (ZRHS), FP64 for the forward FFT
+    double2 *cout;      // packed complex images (ZRHS), FP64 for the forward FFT;
+                        // NULL: ZRHS writes real bands to out
     CgBand *bands;      // CG mode of APPLY: p^T A p and alpha
     const CgGlobal *g;
     int cg;
     int ty;             // CG mode: output rows per warp (0: default)
     int pf;             // CG mode: rows the loads run ahead (2, 4 or 6; 0: 2)
+    int nbd;            // CG mode: bands per CTA (1 or 2; 0: 1)
 };
 
 // operators.cu
@@ -173,6 +175,7 @@ struct Tuning {
     int llp_rows;   // output rows per warp of the CG-loop LLP kernel (0: default)
     int split;      // parallel branches of the CG iteration (0: default)
     int llp_pf;     // rows the LLP kernel's loads run ahead (0: default)
+    int llp_bands;  // bands per CTA of the CG-loop LLP kernel (0: 1)
 };
 Tuning tuning_get(int dev, int N, int H, int W, int c, int r);
 void launch_fill(float *p, size_t n, float v, cudaStream_t st);

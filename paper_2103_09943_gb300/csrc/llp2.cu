@@ -264,6 +264,255 @@ __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
     }
 }
 
+// The same walk for two bands at once (bands 2z and 2z + 1 of blockIdx.z):
+// the PAN statistics and their rolling buffers are loaded and kept once for
+// both, and the two bands' chains give each lane twice the independent work.
+// A band that has stopped still runs (its outputs and partial sums are not
+// used); the CTA leaves only when both have.
+template <int RW, int TY, int PF>
+__global__ void __launch_bounds__(128) llp_cgq2b_kernel(LlpArgs a) {
+    constexpr int G = 2 * RW + 2;
+    constexpr int VALID = 64 - 2 * G;
+    constexpr int NB = 2 * RW + 1;
+    constexpr float nw = (float)(NB * NB);
+    constexpr float inw = 1.0f / nw;
+    __shared__ double red[2][kWarps];
+    const int b0 = 2 * blockIdx.z;
+    const bool two = b0 + 1 < a.N;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (a.g->stop || (a.bands[b0].done && (!two || a.bands[b0 + 1].done))) return;
+    const int H = a.H, W = a.W;
+    const int HWi = H * W;
+    const size_t HW = (size_t)HWi;
+    const int x0 = blockIdx.x * VALID;
+    const int y0 = (blockIdx.y * kWarps + warp) * TY;
+    const int xl = x0 - G + 2 * lane;
+    const int gx = wrap2(xl, W);
+    const bool out_lane = lane >= G / 2 && lane < 32 - G / 2 && xl < W;
+    const float *in0 = a.in + (size_t)b0 * HW;
+    const float *in1 = two ? in0 + HW : in0;
+    const float4 *st4 = a.st4;
+    float part[2] = {0.f, 0.f};
+
+    if (y0 < H) {
+        int rowIn = wrap2(y0 - G, H) * W;
+        int rowA = wrap2(y0 - G - 1, H) * W;
+        int rowD = wrap2(y0, H) * W;
+        // per band q, pixel e
+        float pm2[2][2], pm1[2][2], p0[2][2], mm2[2][2], mm1[2][2], m0[2][2];
+        float hA[2][2][NB], hIA[2][2][NB], ab[2][2][NB], ha[2][2][NB], hb[2][2][NB];
+        // shared by the bands
+        float ib[2][NB], mub[2][RW + 1], sb[2][RW + 1];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+#pragma unroll
+            for (int d = 0; d < NB; ++d) ib[e][d] = 0.f;
+#pragma unroll
+            for (int d = 0; d <= RW; ++d) mub[e][d] = sb[e][d] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                pm2[q][e] = pm1[q][e] = p0[q][e] = mm2[q][e] = mm1[q][e] = m0[q][e] = 0.f;
+#pragma unroll
+                for (int d = 0; d < NB; ++d)
+                    hA[q][e][d] = hIA[q][e][d] = ab[q][e][d] = ha[q][e][d] = hb[q][e][d] = 0.f;
+            }
+        }
+        float2 qp[2][PF];
+        float4 qs0[PF], qs1[PF];
+        constexpr int PH = ((G + 1 + 2) / 3) * 3;
+        float2 ph[2][PH];
+#pragma unroll
+        for (int d = 0; d < PH; ++d) ph[0][d] = ph[1][d] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            qp[0][k] = *reinterpret_cast<const float2 *>(in0 + rowIn + gx);
+            qp[1][k] = *reinterpret_cast<const float2 *>(in1 + rowIn + gx);
+            qs0[k] = st4[rowA + gx];
+            qs1[k] = st4[rowA + gx + 1];
+            rowIn += W;
+            if (rowIn == HWi) rowIn = 0;
+            rowA += W;
+            if (rowA == HWi) rowA = 0;
+        }
+
+        auto advance = [&](float2 *res) {
+            float2 pin[2];
+            pin[0] = qp[0][0];
+            pin[1] = qp[1][0];
+            const float4 s0 = qs0[0], s1 = qs1[0];
+#pragma unroll
+            for (int k = 0; k < PF - 1; ++k) {
+                qp[0][k] = qp[0][k + 1];
+                qp[1][k] = qp[1][k + 1];
+                qs0[k] = qs0[k + 1];
+                qs1[k] = qs1[k + 1];
+            }
+            qp[0][PF - 1] = *reinterpret_cast<const float2 *>(in0 + rowIn + gx);
+            qp[1][PF - 1] = *reinterpret_cast<const float2 *>(in1 + rowIn + gx);
+            qs0[PF - 1] = st4[rowA + gx];
+            qs1[PF - 1] = st4[rowA + gx + 1];
+            rowIn += W;
+            if (rowIn == HWi) rowIn = 0;
+            rowA += W;
+            if (rowA == HWi) rowA = 0;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                for (int d = 0; d < PH - 1; ++d) ph[q][d] = ph[q][d + 1];
+                ph[q][PH - 1] = pin[q];
+            }
+            const float iv[2] = {s0.x, s1.x};
+            const float mu_in[2] = {s0.y, s1.y}, s_in[2] = {s0.z, s1.z};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+#pragma unroll
+                for (int d = 0; d < NB - 1; ++d) ib[e][d] = ib[e][d + 1];
+                ib[e][NB - 1] = iv[e];
+#pragma unroll
+                for (int d = 0; d < RW; ++d) {
+                    mub[e][d] = mub[e][d + 1];
+                    sb[e][d] = sb[e][d + 1];
+                }
+                mub[e][RW] = mu_in[e];
+                sb[e][RW] = s_in[e];
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                // alpha = L p on the row behind the input row
+                pm2[q][0] = pm1[q][0]; pm1[q][0] = p0[q][0]; p0[q][0] = pin[q].x;
+                pm2[q][1] = pm1[q][1]; pm1[q][1] = p0[q][1]; p0[q][1] = pin[q].y;
+                const float l0 = nbr<0, -1>(pm1[q][0], pm1[q][1]), r0 = pm1[q][1];
+                const float l1 = pm1[q][0], r1 = nbr<1, 1>(pm1[q][0], pm1[q][1]);
+                float al[2], ia[2];
+                al[0] = 4.0f * pm1[q][0] - pm2[q][0] - p0[q][0] - l0 - r0;
+                al[1] = 4.0f * pm1[q][1] - pm2[q][1] - p0[q][1] - l1 - r1;
+                ia[0] = iv[0] * al[0];
+                ia[1] = iv[1] * al[1];
+                const float h10 = hsum<RW, 0>(al[0], al[1]), h11 = hsum<RW, 1>(al[0], al[1]);
+                const float h20 = hsum<RW, 0>(ia[0], ia[1]), h21 = hsum<RW, 1>(ia[0], ia[1]);
+                const float h1[2] = {h10, h11}, h2[2] = {h20, h21};
+                float av[2], bv[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+#pragma unroll
+                    for (int d = 0; d < NB - 1; ++d) {
+                        hA[q][e][d] = hA[q][e][d + 1];
+                        hIA[q][e][d] = hIA[q][e][d + 1];
+                        ab[q][e][d] = ab[q][e][d + 1];
+                    }
+                    hA[q][e][NB - 1] = h1[e];
+                    hIA[q][e][NB - 1] = h2[e];
+                    ab[q][e][NB - 1] = al[e];
+                    float v1 = 0.f, v2 = 0.f;
+#pragma unroll
+                    for (int d = 0; d < NB; ++d) {
+                        v1 += hA[q][e][d];
+                        v2 += hIA[q][e][d];
+                    }
+                    const float mu = mub[e][0], sv = sb[e][0];
+                    const float ma = v1 * inw, mia = v2 * inw;
+                    av[e] = (mia - mu * ma) * sv;
+                    bv[e] = ma - av[e] * mu;
+                }
+                const float g10 = hsum<RW, 0>(av[0], av[1]), g11 = hsum<RW, 1>(av[0], av[1]);
+                const float g20 = hsum<RW, 0>(bv[0], bv[1]), g21 = hsum<RW, 1>(bv[0], bv[1]);
+                const float g1[2] = {g10, g11}, g2[2] = {g20, g21};
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+#pragma unroll
+                    for (int d = 0; d < NB - 1; ++d) {
+                        ha[q][e][d] = ha[q][e][d + 1];
+                        hb[q][e][d] = hb[q][e][d + 1];
+                    }
+                    ha[q][e][NB - 1] = g1[e];
+                    hb[q][e][NB - 1] = g2[e];
+                    float sa = 0.f, sbb = 0.f;
+#pragma unroll
+                    for (int d = 0; d < NB; ++d) {
+                        sa += ha[q][e][d];
+                        sbb += hb[q][e][d];
+                    }
+                    const float mv = nw * ab[q][e][0] - sa * ib[e][0] - sbb;
+                    mm2[q][e] = mm1[q][e];
+                    mm1[q][e] = m0[q][e];
+                    m0[q][e] = mv;
+                }
+                const float ql0 = nbr<0, -1>(mm1[q][0], mm1[q][1]), qr0 = mm1[q][1];
+                const float ql1 = mm1[q][0], qr1 = nbr<1, 1>(mm1[q][0], mm1[q][1]);
+                res[q] = make_float2(4.0f * mm1[q][0] - mm2[q][0] - m0[q][0] - ql0 - qr0,
+                                     4.0f * mm1[q][1] - mm2[q][1] - m0[q][1] - ql1 - qr1);
+            }
+        };
+
+        float2 val[2];
+        for (int step = 0; step < 2 * G; ++step) advance(val);
+        float2 *out0 = reinterpret_cast<float2 *>(a.out + (size_t)b0 * HW);
+        float2 *out1 = reinterpret_cast<float2 *>(a.out + (size_t)(b0 + 1) * HW);
+#pragma unroll Llp2Rows<RW>::UNR
+        for (int yy = 0; yy < TY; ++yy) {
+            advance(val);
+            if (out_lane && y0 + yy < H) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    if (q == 1 && !two) break;
+                    val[q].x *= a.lam;
+                    val[q].y *= a.lam;
+                    (q ? out1 : out0)[(rowD + gx) >> 1] = val[q];
+                    // the output row is the input row of G steps ago
+                    const float2 pv = ph[q][PH - 1 - G];
+                    part[q] = fmaf(pv.x, val[q].x, fmaf(pv.y, val[q].y, part[q]));
+                }
+            }
+            rowD += W;
+            if (rowD == HWi) rowD = 0;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        double pd = (double)part[q];
+        for (int o = 16; o > 0; o >>= 1) pd += __shfl_xor_sync(kFull, pd, o);
+        if (lane == 0) red[q][warp] = pd;
+    }
+    __syncthreads();
+    if (tid >= 2 || (tid == 1 && !two)) return;
+    // thread q finishes band b0 + q
+    const int q = tid;
+    double tot = 0.0;
+    for (int k = 0; k < kWarps; ++k) tot += red[q][k];
+    CgBand *bd = a.bands + b0 + q;
+    atomicAdd(&bd->pAp, tot);
+    __threadfence();
+    const unsigned int nblk = gridDim.x * gridDim.y;
+    const unsigned int t = atomicAdd(&bd->cnt_apply, 1u);
+    if (t == nblk - 1) {
+        __threadfence();
+        // p^T A p = ||D B p||^2 + p^T (lam L^T M L) p
+        const double pAp = atomicAdd(&bd->pAp, 0.0) + bd->vv;
+        const double rho = bd->rho;
+        bd->cnt_apply = 0u;
+        if (bd->done) return;
+        if (!isfinite(pAp)) {
+            bd->status = PS_ERR_NONFINITE;
+            bd->done = 1;
+            bd->alpha = 0.0;
+        } else if (!(pAp > 0.0)) {
+            bd->status = PS_ERR_BREAKDOWN;
+            bd->done = 1;
+            bd->alpha = 0.0;
+        } else {
+            bd->alpha = rho / pAp;
+        }
+    }
+}
+
+template <int RW, int TY, int PF>
+void launch_ty2(const LlpArgs &a, int N, cudaStream_t st) {
+    constexpr int G = 2 * RW + 2, VALID = 64 - 2 * G;
+    const int rows = TY * kWarps;
+    dim3 grd((a.W + VALID - 1) / VALID, (a.H + rows - 1) / rows, (N + 1) / 2);
+    llp_cgq2b_kernel<RW, TY, PF><<<grd, 32 * kWarps, 0, st>>>(a);
+}
+
 template <int RW, int TY, int PF>
 void launch_ty(const LlpArgs &a, int N, cudaStream_t st) {
     constexpr int G = 2 * RW + 2, VALID = 64 - 2 * G;
@@ -274,7 +523,9 @@ void launch_ty(const LlpArgs &a, int N, cudaStream_t st) {
 
 template <int RW, int TY>
 void launch_pf(const LlpArgs &a, int N, cudaStream_t st) {
-    if (a.pf == 6)
+    if (a.nbd == 2)
+        launch_ty2<RW, TY, 2>(a, N, st);
+    else if (a.pf == 6)
         launch_ty<RW, TY, 6>(a, N, st);
     else if (a.pf == 4)
         launch_ty<RW, TY, 4>(a, N, st);

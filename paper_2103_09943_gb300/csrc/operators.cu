@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(128) llp_kernel(LlpArgs a) {
                 } else if (MODE == LLP_CGQ) {
                     val *= a.lam;
                 }
-                if (MODE == LLP_ZRHS) {
+                if (MODE == LLP_ZRHS && a.cout) {
                     double2 *cimg = a.cout + (size_t)(b >> 1) * HW + o;
                     if (b & 1)
                         reinterpret_cast<double *>(cimg)[1] = (double)val;

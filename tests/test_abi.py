@@ -187,3 +187,18 @@ def test_batched_argument_errors_return_before_launch(lib):
     arr[2].kernel = None
     assert lib.ps_pansharpen_batched(arr, 3, ctypes.byref(kp), ctypes.byref(hp), None, None,
                                      ws, need, None) == 1
+
+
+def test_tuning_arguments(lib):
+    from paper_2103_09943_gb300._lib import Tuning
+    t = Tuning()
+    t.split = 3
+    assert lib.ps_set_tuning(4, 256, 256, 4, 1, ctypes.byref(t)) == 1
+    t.split, t.llp_bands = 2, 3
+    assert lib.ps_set_tuning(4, 256, 256, 4, 1, ctypes.byref(t)) == 1
+    t.llp_bands, t.llp_pf = 2, 5
+    assert lib.ps_set_tuning(4, 256, 256, 4, 1, ctypes.byref(t)) == 1
+    t.llp_pf = 4
+    assert lib.ps_set_tuning(4, 250, 256, 4, 1, ctypes.byref(t)) == 2   # H % ratio
+    assert lib.ps_set_tuning(4, 256, 256, 4, 1, None) == 1
+

@@ -139,3 +139,48 @@ def test_autotune_picks_valid_shapes_and_keeps_parity(cuda, c0_ref):
     for b in range(cfg.bands):
         assert rel(to_np(Z0)[b], ref["Z0"][b]) < 1e-5
         assert rel(to_np(Z)[b], ref["Z"][b]) < 1e-5
+
+
+@pytest.mark.parametrize("split", [1, 2])
+def test_two_band_llp_kernel_reaches_the_oracle(cuda, c0_ref, split):
+    # the CG-loop LLP kernel that walks two bands per CTA (shared PAN
+    # statistics), selected through the tuning table, in one and two branches
+    sc, ref = c0_ref
+    cfg = sc["config"]
+    args = (to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda), to_dev(sc["kernel"], cuda),
+            cfg.ratio)
+    hp = api.default_hrms_params(tol=1e-8, max_iter=5000)
+    try:
+        api.set_tuning(cfg.bands, cfg.H, cfg.W, cfg.ratio, 1, llp_bands=2, split=split)
+        assert api.get_tuning(cfg.bands, cfg.H, cfg.W, cfg.ratio, 1)["llp_bands"] == 2
+        Z, Z0, info = api.solve_hrms(*args, hp, want_z0=True)
+    finally:
+        api.set_tuning(cfg.bands, cfg.H, cfg.W, cfg.ratio, 1)
+    assert all(s == 0 for s in info.status), info
+    Z, Z0 = to_np(Z), to_np(Z0)
+    for b in range(cfg.bands):
+        assert rel(Z0[b], ref["Z0"][b]) < 1e-5, b
+        assert rel(Z[b], ref["Z"][b]) < 1e-5, b
+
+
+def test_two_band_llp_kernel_odd_band_count(cuda):
+    # three bands: the second CTA column holds one band
+    N, H, W, c, R = 3, 144, 96, 4, 5
+    rng = np.random.default_rng(41)
+    u = rand_kernel(R, rng)
+    X = to_dev(rng.random((N, H // c, W // c)) * 255.0, cuda)
+    Y = to_dev(rng.random((H, W)) * 255.0, cuda)
+    K = to_dev(u, cuda)
+    hp = api.default_hrms_params(tol=1e-8, max_iter=5000)
+    out = {}
+    for nbd in (1, 2):
+        try:
+            api.set_tuning(N, H, W, c, 1, llp_bands=nbd)
+            Z, Z0, info = api.solve_hrms(X, Y, K, c, hp, want_z0=True)
+        finally:
+            api.set_tuning(N, H, W, c, 1)
+        assert all(s == 0 for s in info.status), info
+        out[nbd] = (to_np(Z0), info.iters)
+    for b in range(N):
+        assert abs(out[1][1][b] - out[2][1][b]) <= 1
+        assert rel(out[2][0][b], out[1][0][b]) < 1e-5

@@ -178,3 +178,25 @@ def test_paper_stop_rule_with_preconditioner_stops_earlier(cuda):
         assert all(s == 0 for s in info.status), info
         it[pc] = info.iters
     assert max(it[1]) * 2 < min(it[0]), it
+
+
+def test_zstep_fp32_within_its_bound(cuda, c0_oracle):
+    # the all-FP32 Z step (the preconditioner's register FFTs and group
+    # solve): the forward spectrum's rounding, amplified by the Z-step
+    # operator's condition number (~200), costs ~6e-6 rel-L2 (numpy
+    # experiment); the bar leaves a factor of five, far inside the 1e-3 of
+    # the mixed-precision form
+    sc, ref = c0_oracle
+    cfg = sc["config"]
+    args = (to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda), to_dev(sc["kernel"], cuda),
+            cfg.ratio)
+    out = {}
+    for fp32 in (0, 1):
+        hp = api.default_hrms_params(tol=CG_TOL, max_iter=5000, zstep_fp32=fp32)
+        Z, Z0, info = api.solve_hrms(*args, hp, want_z0=True)
+        out[fp32] = (to_np(Z), to_np(Z0), info.iters)
+    assert out[0][2] == out[1][2]
+    for b in range(cfg.bands):
+        assert rel(out[1][1][b], out[0][1][b]) < 1e-6   # same Z0
+        assert rel(out[1][0][b], out[0][0][b]) < 3e-5
+        assert rel(out[1][0][b], ref["Z"][b]) < 3e-5
