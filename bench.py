@@ -32,10 +32,11 @@ UNIT = "Mpix·band/s"
 L2_FLUSH_BYTES = 256 << 20
 
 
-def workload_config(r: int = 1, scene: str = "c1"):
+def workload_config(r: int = 1, scene: str = "c1", ratio: int = 0):
     import synth
     from dataclasses import replace
-    return replace(synth.CONFIGS[scene], r=r)
+    cfg = replace(synth.CONFIGS[scene], r=r)
+    return replace(cfg, ratio=ratio) if ratio else cfg
 
 
 def workload_name(cfg) -> str:
@@ -172,7 +173,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import synth
-    cfg = workload_config(args.r, args.scene)
+    cfg = workload_config(args.r, args.scene, args.ratio)
     scene = synth.make_scene(cfg)
     crop = args.ref_crop
     sc = synth.crop_scene(scene, crop)
@@ -296,7 +297,7 @@ def run_profile_solve(args):
     __graft_entry__.build()
     import synth
     from paper_2103_09943_gb300 import api
-    cfg = workload_config(args.r, args.scene)
+    cfg = workload_config(args.r, args.scene, args.ratio)
     scene = synth.make_scene(cfg)
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
@@ -374,7 +375,7 @@ def run_profile_warm(args):
     import synth
     from paper_2103_09943_gb300 import ops
     from paper_2103_09943_gb300.cnn import WarmStartNet
-    cfg = workload_config(args.r, args.scene)
+    cfg = workload_config(args.r, args.scene, args.ratio)
     scene = synth.make_scene(cfg)
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
@@ -399,7 +400,7 @@ def run_gpu(args):
     import synth
     from paper_2103_09943_gb300 import api
 
-    cfg = workload_config(args.r, args.scene)
+    cfg = workload_config(args.r, args.scene, args.ratio)
     scene = synth.make_scene(cfg, seed=cfg.seed + rank)   # one independent scene per rank
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
@@ -792,6 +793,9 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--r", type=int, default=1)
+    ap.add_argument("--ratio", type=int, default=0,
+                    help="resolution ratio of the scene (default: the config's, 4); 2 gives the "
+                         "paper's other setting")
     ap.add_argument("--scene", default="c1", choices=["c1", "c2"],
                     help="c1: 8 x 1024^2 (the metric's workload); c2: one 8 x 8192^2 scene "
                          "(LRMS 8 x 2048^2), generated as c1 with seed 2")

@@ -11,10 +11,18 @@
 //                              v), then x += alpha p, r -= alpha (B^T D^T v + q)
 //                              and the next r^T r
 //
-// Instantiated for C in {2, 4} and R in [1, 8]; other sizes use the generic
-// kernels of operators.cu.
+// Instantiated for C in {2, 4} and R in [1, 8]; compiled a second time with
+// PS_SITE_WIDE (cg_fast_wide.cu, a translation unit of its own so that the two
+// build in parallel) for C = 4 and R in {12, 14, 16}, the paper's 29 x 29
+// support among them. Other sizes use the generic kernels of operators.cu.
 #include "common.cuh"
 #include "kernels.cuh"
+
+#ifdef PS_SITE_WIDE
+#define PS_SITE_FN(name) name##_wide
+#else
+#define PS_SITE_FN(name) name
+#endif
 
 namespace ps {
 
@@ -335,7 +343,11 @@ bool dispatch_r(int R, int which, const float *a0, const float *a1, float *a2, C
     case RR:                                                                                 \
         return launch_pair<C, RR>(which, a0, a1, a2, bands, g, cg, N, H, W, u, v, x, r, q, \
                                   st);
+#ifdef PS_SITE_WIDE
+        PS_CASE(12) PS_CASE(14) PS_CASE(16)
+#else
         PS_CASE(1) PS_CASE(2) PS_CASE(3) PS_CASE(4) PS_CASE(5) PS_CASE(6) PS_CASE(7) PS_CASE(8)
+#endif
 #undef PS_CASE
         default: return false;
     }
@@ -345,7 +357,9 @@ bool dispatch(int C, int R, int which, const float *a0, const float *a1, float *
               CgBand *bands, const CgGlobal *g, int cg, int N, int H, int W, const float *u,
               float *v, float *x, float *r, const float *q, cudaStream_t st) {
     if (C == 4) return dispatch_r<4>(R, which, a0, a1, a2, bands, g, cg, N, H, W, u, v, x, r, q, st);
+#ifndef PS_SITE_WIDE
     if (C == 2) return dispatch_r<2>(R, which, a0, a1, a2, bands, g, cg, N, H, W, u, v, x, r, q, st);
+#endif
     return false;
 }
 
@@ -360,31 +374,47 @@ cudaError_t set_attrs_c() {
     cudaError_t e = cudaSuccess;
 #define PS_ATTR(RR) \
     if (e == cudaSuccess) e = set_attr_one<C, RR>();
+#ifdef PS_SITE_WIDE
+    PS_ATTR(12) PS_ATTR(14) PS_ATTR(16)
+#else
     PS_ATTR(1) PS_ATTR(2) PS_ATTR(3) PS_ATTR(4) PS_ATTR(5) PS_ATTR(6) PS_ATTR(7) PS_ATTR(8)
+#endif
 #undef PS_ATTR
     return e;
 }
 
 }  // namespace
 
-bool launch_db_fast(const float *src, const float *rsrc, float *pdst, CgBand *bands,
-                    const CgGlobal *g, int cg, int N, int H, int W, int c, const float *u, int R,
-                    float *v, cudaStream_t st) {
+bool PS_SITE_FN(launch_db_fast)(const float *src, const float *rsrc, float *pdst,
+                                CgBand *bands, const CgGlobal *g, int cg, int N, int H, int W,
+                                int c, const float *u, int R, float *v, cudaStream_t st) {
+#ifndef PS_SITE_WIDE
+    if (R > 8)
+        return launch_db_fast_wide(src, rsrc, pdst, bands, g, cg, N, H, W, c, u, R, v, st);
+#endif
     return dispatch(c, R, 0, src, rsrc, pdst, bands, g, cg, N, H, W, u, v, nullptr, nullptr,
                     nullptr, st);
 }
 
-bool launch_cg_update_fast(float *x, float *r, const float *p, const float *q, const float *v,
-                           const float *u, int R, int c, int N, int H, int W, CgBand *bands,
-                           const CgGlobal *g, cudaStream_t st) {
+bool PS_SITE_FN(launch_cg_update_fast)(float *x, float *r, const float *p, const float *q,
+                                       const float *v, const float *u, int R, int c, int N,
+                                       int H, int W, CgBand *bands, const CgGlobal *g,
+                                       cudaStream_t st) {
+#ifndef PS_SITE_WIDE
+    if (R > 8)
+        return launch_cg_update_fast_wide(x, r, p, q, v, u, R, c, N, H, W, bands, g, st);
+#endif
     return dispatch(c, R, 1, p, nullptr, nullptr, bands, g, 1, N, H, W, u,
                     const_cast<float *>(v), x, r, q, st);
 }
 
-cudaError_t cg_fast_set_attrs() {
+cudaError_t PS_SITE_FN(cg_fast_set_attrs)() {
     cudaError_t e = set_attrs_c<4>();
-    if (e != cudaSuccess) return e;
-    return set_attrs_c<2>();
+#ifndef PS_SITE_WIDE
+    if (e == cudaSuccess) e = set_attrs_c<2>();
+    if (e == cudaSuccess) e = cg_fast_set_attrs_wide();
+#endif
+    return e;
 }
 
 }  // namespace ps

@@ -62,6 +62,14 @@ bool launch_cg_update_fast(float *x, float *r, const float *p, const float *q, c
                            const float *u, int R, int c, int N, int H, int W, CgBand *bands,
                            const CgGlobal *g, cudaStream_t st);
 cudaError_t cg_fast_set_attrs();
+// the same for ratio 4 and radii 12, 14, 16 (cg_fast_wide.cu)
+bool launch_db_fast_wide(const float *src, const float *rsrc, float *pdst, CgBand *bands,
+                         const CgGlobal *g, int cg, int N, int H, int W, int c, const float *u,
+                         int R, float *v, cudaStream_t st);
+bool launch_cg_update_fast_wide(float *x, float *r, const float *p, const float *q,
+                                const float *v, const float *u, int R, int c, int N, int H,
+                                int W, CgBand *bands, const CgGlobal *g, cudaStream_t st);
+cudaError_t cg_fast_set_attrs_wide();
 
 // fft.cu
 struct FftPlan {
@@ -122,6 +130,10 @@ bool precond_rows_ok(int H, int W, int c, int tr);
 void launch_precond(const PrecArgs &a, cudaStream_t st);
 void launch_spectrum_to_f32(const double2 *in, float2 *out, size_t n, cudaStream_t st);
 cudaError_t precond_set_attrs();
+// precond_wide.cu: the column pass's 512- and 1024-thread shapes (C = 2, 4)
+void launch_prec_cols_wide(int C, int shape, const PrecArgs &a, bool p2, int col_per, int col_tpr,
+                           int col_ld, size_t col_smem, float scale, cudaStream_t st);
+cudaError_t precond_set_attrs_wide();
 
 // cnn.cu: 3 x 3 convolutions with 32 in / 32 out channels on tcgen05
 enum { CONV_PLAIN = 0, CONV_LAST = 2 };

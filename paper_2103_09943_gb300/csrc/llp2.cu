@@ -34,9 +34,9 @@ __device__ __forceinline__ float nbr(float v0, float v1) {
     constexpr int o = (c >= 0) ? c / 2 : -((1 - c) / 2);  // floor(c / 2)
     constexpr int el = c - 2 * o;
     const float src = el ? v1 : v0;
-    if (o == 0) return src;
-    if (o < 0) return __shfl_up_sync(kFull, src, -o);
-    return __shfl_down_sync(kFull, src, o);
+    if constexpr (o == 0) return src;
+    else if constexpr (o < 0) return __shfl_up_sync(kFull, src, (unsigned)(-o));
+    else return __shfl_down_sync(kFull, src, (unsigned)o);
 }
 
 // Horizontal window sum over [-RW, RW] at both columns of the pair.

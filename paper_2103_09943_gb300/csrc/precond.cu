@@ -26,6 +26,7 @@
 // Sizes whose C columns do not fit one CTA take a fallback: column FFTs and
 // the group solve as separate passes over global memory.
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 #include "fft_dev.cuh"
@@ -51,6 +52,8 @@ constexpr int kPrecColThreads = 1024;
 __host__ __device__ constexpr int col_shape(int threads) {
     return threads <= 256 ? 256 : (threads <= 512 ? 512 : 1024);
 }
+// the 512- and 1024-thread shapes are built for ratios 2 and 4 only
+constexpr int col_threads_max(int C) { return (C == 2 || C == 4) ? kPrecColThreads : 256; }
 
 __device__ __forceinline__ bool image_idle(const PrecArgs &a, int k) {
     if (!a.bands) return false;
@@ -453,7 +456,7 @@ bool make_prec_plan(int H, int W, int C, PrecPlan *pl) {
     if (pl->p2) {
         const int ct = H / 16;
         const size_t bytes = (size_t)C * prow_len(H) * sizeof(float2);
-        if (C * ct <= kPrecColThreads && bytes <= (size_t)kPrecMaxSmem) {
+        if (C * ct <= col_threads_max(C) && bytes <= (size_t)kPrecMaxSmem) {
             pl->col_tpr = ct;
             pl->col_ld = prow_len(H);
             pl->col_smem = bytes;
@@ -465,7 +468,7 @@ bool make_prec_plan(int H, int W, int C, PrecPlan *pl) {
         // thread spill at 64 registers, 8 do not
         const size_t bytes = (size_t)C * (H + kPrecPad) * sizeof(float2);
         for (int per = 8; per <= 32 && bytes <= (size_t)kPrecMaxSmem; per *= 2)
-            if (C * fft_threads_row(H, per) <= kPrecColThreads) {
+            if (C * fft_threads_row(H, per) <= (per == 32 ? 256 : col_threads_max(C))) {
                 pl->col_per = per;
                 pl->col_tpr = fft_threads_row(H, per);
                 pl->col_ld = H + kPrecPad;
@@ -487,12 +490,12 @@ void launch_cols_shape(const PrecArgs &a, const PrecPlan &pl, dim3 grd, dim3 blk
     else if (pl.col_per == 8)
         prec_cols_kernel<C, 8, false, MAXT><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
                                                                            pl.col_ld, scale);
-    else if (pl.col_per == 16)
+    else if (pl.col_per == 16 || MAXT > 256)
         prec_cols_kernel<C, 16, false, MAXT><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
                                                                             pl.col_ld, scale);
     else
-        prec_cols_kernel<C, 32, false, MAXT><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
-                                                                            pl.col_ld, scale);
+        prec_cols_kernel<C, 32, false, 256><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr,
+                                                                           pl.col_ld, scale);
 }
 
 template <int C>
@@ -500,11 +503,12 @@ void launch_cols(const PrecArgs &a, const PrecPlan &pl, float scale, cudaStream_
     const int w = a.W / C, nimg = (a.N + 1) / 2;
     if (pl.col_smem) {
         const dim3 grd(w, nimg), blk(C * pl.col_tpr);
-        switch (col_shape(C * pl.col_tpr)) {
-            case 256: launch_cols_shape<C, 256>(a, pl, grd, blk, scale, st); break;
-            case 512: launch_cols_shape<C, 512>(a, pl, grd, blk, scale, st); break;
-            default: launch_cols_shape<C, 1024>(a, pl, grd, blk, scale, st); break;
-        }
+        const int shape = col_shape(C * pl.col_tpr);
+        if (shape == 256)
+            launch_cols_shape<C, 256>(a, pl, grd, blk, scale, st);
+        else
+            launch_prec_cols_wide(C, shape, a, pl.p2, pl.col_per, pl.col_tpr, pl.col_ld,
+                                  pl.col_smem, scale, st);
     } else {
         const dim3 grd(a.W, nimg);
         const int groups = (a.H / C) * w;
@@ -529,17 +533,14 @@ template <int C, int MAXT>
 cudaError_t set_attrs_cs() {
     cudaError_t e = smem_attr(prec_cols_kernel<C, 8, false, MAXT>);
     if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 16, false, MAXT>);
-    if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 32, false, MAXT>);
+    if (MAXT == 256 && e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 32, false, 256>);
     if (e == cudaSuccess) e = smem_attr(prec_cols_kernel<C, 16, true, MAXT>);
     return e;
 }
 
 template <int C>
 cudaError_t set_attrs_c() {
-    cudaError_t e = set_attrs_cs<C, 256>();
-    if (e == cudaSuccess) e = set_attrs_cs<C, 512>();
-    if (e == cudaSuccess) e = set_attrs_cs<C, 1024>();
-    return e;
+    return set_attrs_cs<C, 256>();
 }
 
 // Rows per CTA `tr` for the row passes, if it is a valid choice.
@@ -551,6 +552,34 @@ bool prec_rows_valid(const PrecPlan &pl, int H, int W, int tr) {
 }
 
 }  // namespace
+
+#ifdef PS_PREC_WIDE
+// The 512- and 1024-thread column shapes (ratios 2 and 4), built in a
+// translation unit of their own.
+void launch_prec_cols_wide(int C, int shape, const PrecArgs &a, bool p2, int col_per, int col_tpr,
+                           int col_ld, size_t col_smem, float scale, cudaStream_t st) {
+    PrecPlan pl;
+    memset(&pl, 0, sizeof(pl));
+    pl.p2 = p2;
+    pl.col_per = col_per;
+    pl.col_tpr = col_tpr;
+    pl.col_ld = col_ld;
+    pl.col_smem = col_smem;
+    const dim3 grd(a.W / C, (a.N + 1) / 2), blk(C * col_tpr);
+    if (C == 4 && shape == 512) launch_cols_shape<4, 512>(a, pl, grd, blk, scale, st);
+    if (C == 4 && shape == 1024) launch_cols_shape<4, 1024>(a, pl, grd, blk, scale, st);
+    if (C == 2 && shape == 512) launch_cols_shape<2, 512>(a, pl, grd, blk, scale, st);
+    if (C == 2 && shape == 1024) launch_cols_shape<2, 1024>(a, pl, grd, blk, scale, st);
+}
+
+cudaError_t precond_set_attrs_wide() {
+    cudaError_t e = set_attrs_cs<4, 512>();
+    if (e == cudaSuccess) e = set_attrs_cs<4, 1024>();
+    if (e == cudaSuccess) e = set_attrs_cs<2, 512>();
+    if (e == cudaSuccess) e = set_attrs_cs<2, 1024>();
+    return e;
+}
+#else
 
 bool precond_rows_ok(int H, int W, int c, int tr) {
     PrecPlan pl;
@@ -618,7 +647,9 @@ cudaError_t precond_set_attrs() {
     if (e == cudaSuccess) e = set_attrs_c<4>();
     if (e == cudaSuccess) e = set_attrs_c<6>();
     if (e == cudaSuccess) e = set_attrs_c<8>();
+    if (e == cudaSuccess) e = precond_set_attrs_wide();
     return e;
 }
+#endif  // PS_PREC_WIDE
 
 }  // namespace ps
