@@ -30,12 +30,12 @@ def make_dataset(n_scenes: int, size: int, seed0: int, device, tol: float = 1e-8
     import synth
     base = synth.CONFIGS["c1"]
     shapes = max(8, int(round(base.shapes * (size * size) / (base.H * base.W))))
+    cfgs = [replace(base, H=size, W=size, shapes=shapes, seed=seed0 + k) for k in range(n_scenes)]
+    arrays = synth.make_scenes_parallel(cfgs)   # host cores, spawned workers
     data = []
-    for k in range(n_scenes):
-        cfg = replace(base, H=size, W=size, shapes=shapes, seed=seed0 + k)
-        sc = synth.make_scene(cfg)
-        X = torch.from_numpy(sc["lrms"]).to(device)
-        Y = torch.from_numpy(sc["pan"]).to(device)
+    for cfg, (lrms, pan) in zip(cfgs, arrays):
+        X = torch.from_numpy(lrms).to(device)
+        Y = torch.from_numpy(pan).to(device)
         kern, _, _ = api.estimate_kernel(X, Y, cfg.ratio, cfg.R, info=False)
         hp = api.default_hrms_params(tol=tol, max_iter=20000)
         _, z0, _ = api.solve_hrms(X, Y, kern, cfg.ratio, hp, want_z0=True, info=False)

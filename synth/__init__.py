@@ -7,7 +7,7 @@ decimation, Sec. II-A, Eq. objective0) is simulated here with numpy's FFT, an
 implementation independent of both the CUDA path and the oracle.
 """
 from .scenes import (SceneConfig, CONFIGS, make_scene, make_kernel,
-                     make_batch_configs, crop_scene)
+                     make_batch_configs, crop_scene, make_scenes_parallel)
 
 __all__ = ["SceneConfig", "CONFIGS", "make_scene", "make_kernel",
-           "make_batch_configs", "crop_scene"]
+           "make_batch_configs", "crop_scene", "make_scenes_parallel"]

@@ -253,3 +253,21 @@ def make_batch_configs(count: int = 64, seed0: int = 3000) -> list[SceneConfig]:
         out.append(replace(base, name=f"c3_{k}", bands=bands, H=side, W=side,
                            R=R, seed=seed0 + k))
     return out
+
+
+def _lrms_pan(cfg: SceneConfig):
+    sc = make_scene(cfg)
+    return sc["lrms"], sc["pan"]
+
+
+def make_scenes_parallel(cfgs, workers: int | None = None) -> list:
+    """(lrms, pan) of every config, generated by spawned worker processes
+    (the same arrays as make_scene, in the order of cfgs)."""
+    import multiprocessing as mp
+    import os
+    workers = max(1, min(len(cfgs), workers or os.cpu_count() or 1))
+    if workers == 1:
+        return [_lrms_pan(c) for c in cfgs]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_lrms_pan, cfgs, chunksize=1)
+
