@@ -226,11 +226,74 @@ __global__ void __launch_bounds__(256) ete_lag_kernel(const float *__restrict__ 
     }
 }
 
+// The same sums for a compile-time ratio C, LAG_SITES horizontally adjacent LR
+// sites per thread: their row segments overlap in all but C (LAG_SITES - 1)
+// samples, so one register copy of the union (LAG_CHUNK + C (LAG_SITES - 1)
+// values) feeds LAG_SITES x LAG_CHUNK products, about half the loads of the
+// one-site walk.
+constexpr int LAG_SITES = 4;
+
+template <int C>
+__global__ void __launch_bounds__(256) ete_lag_sites_kernel(const float *__restrict__ Y, int H,
+                                                            int W, int R, double *lags) {
+    __shared__ double red[8];
+    constexpr int SEG = LAG_CHUNK + C * (LAG_SITES - 1);
+    const int nl = 4 * R + 1;
+    const int dy = (int)blockIdx.x;
+    const int py = blockIdx.y / C, px = blockIdx.y - (blockIdx.y / C) * C;
+    const int dx0 = (int)blockIdx.z * LAG_CHUNK - 2 * R;
+    const int ndx = min(LAG_CHUNK, 2 * R - dx0 + 1);
+    const int h = H / C, w = W / C;
+    const int gw = (w + LAG_SITES - 1) / LAG_SITES;   // site groups per LR row
+    float s[LAG_CHUNK], cm[LAG_CHUNK];
+#pragma unroll
+    for (int t = 0; t < LAG_CHUNK; ++t) { s[t] = 0.f; cm[t] = 0.f; }
+    for (int gi = threadIdx.x; gi < h * gw; gi += 256) {
+        const int ky = gi / gw, kx0 = (gi - ky * gw) * LAG_SITES;
+        const int yy = C * ky + py;
+        const float *arow = Y + (size_t)yy * W;
+        const float *row = Y + (size_t)wrapk(yy + dy, H) * W;
+        const int cx0 = C * kx0 + px + dx0;
+        float seg[SEG];
+        if (cx0 >= 0 && cx0 + SEG <= W) {
+#pragma unroll
+            for (int t = 0; t < SEG; ++t) seg[t] = row[cx0 + t];
+        } else {
+            int cx = wrapk(cx0, W);
+#pragma unroll
+            for (int t = 0; t < SEG; ++t) {
+                seg[t] = row[cx];
+                cx = (cx + 1 == W) ? 0 : cx + 1;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < LAG_SITES; ++q) {
+            if (kx0 + q >= w) break;
+            const float a = arow[C * (kx0 + q) + px];
+#pragma unroll
+            for (int t = 0; t < LAG_CHUNK; ++t) df_acc(a, seg[C * q + t], s[t], cm[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < LAG_CHUNK; ++t) {
+        if (t < ndx) {
+            const double tot = block_sum_d((double)s[t] + (double)cm[t], red);
+            if (threadIdx.x == 0)
+                lags[((size_t)blockIdx.y * nl + (dy + 2 * R)) * nl + (dx0 + t + 2 * R)] = tot;
+        }
+    }
+}
+
 void launch_ete_lags(const float *Y, int H, int W, int c, int R, double *lags,
                      cudaStream_t st) {
     const int nl = 4 * R + 1;
     dim3 grd(2 * R + 1, c * c, (nl + LAG_CHUNK - 1) / LAG_CHUNK);
-    ete_lag_kernel<<<grd, 256, 0, st>>>(Y, H, W, c, R, lags);
+    if (c == 4)
+        ete_lag_sites_kernel<4><<<grd, 256, 0, st>>>(Y, H, W, R, lags);
+    else if (c == 2)
+        ete_lag_sites_kernel<2><<<grd, 256, 0, st>>>(Y, H, W, R, lags);
+    else
+        ete_lag_kernel<<<grd, 256, 0, st>>>(Y, H, W, c, R, lags);
 }
 
 // E^T E[a][b] = C[(-a) mod c][a - b], taps a = (ai, aj), b = (bi, bj).
