@@ -126,3 +126,20 @@ def test_batch_network_warm_start(cuda, scenes):
         for n in range(cfg.bands):
             assert abs(si.iters[n] - sinfo[i].iters[n]) <= 1, (i, n)
         assert rel(to_np(b.hrms[i]), to_np(Z)) < 1e-5, i
+
+
+def test_batch_with_an_alternative_prior_and_the_paper_rule(cuda, scenes):
+    # the batch runs whatever loop the parameters select: here the LGC prior
+    # (plain CG) stopped by the paper's relative-change rule
+    hp = api.default_hrms_params(precond=0, prior=4, stop_rule=1, tol=5e-5, max_iter=5000)
+    dev = [(to_dev(s["lrms"], cuda), to_dev(s["pan"], cuda), s["config"].R) for s in scenes[:3]]
+    b = api.Batch(dev, ratio=4, hparams=hp, estimate=True)
+    kinfo, sinfo = b.run(info=True)
+    for i, sc in enumerate(scenes[:3]):
+        cfg = sc["config"]
+        Z, k, ki, si = api.pansharpen(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                      cfg.ratio, cfg.R, hparams=hp)
+        assert all(s == 0 for s in sinfo[i].status)
+        for n in range(cfg.bands):
+            assert abs(si.iters[n] - sinfo[i].iters[n]) <= 1, (i, n)
+        assert rel(to_np(b.hrms[i]), to_np(Z)) < 1e-5, i
