@@ -19,7 +19,7 @@ from .fbmp import (PRIORS, apply_z0_prior, apply_zstep_prior, cg_op, filt, filt_
                    apply_zstep_system, bicubic_up, blur_decimate, blur_decimate_adj,
                    box_filter, cg_solve, estimate_kernel, estimate_omega,
                    guided_filter, kernel_error_pct, kernel_normal_eq,
-                   laplacian, matting_apply, pan_stats, pansharpen, pcg_solve,
+                   laplacian, matting_apply, pan_stats, pansharpen, pcg_diag_solve, pcg_solve,
                    precond_apply, psnr, rel_l2, simplex_project, solve_band,
                    solve_hrms, up_solve)
 
@@ -31,7 +31,7 @@ __all__ = [
     "apply_z0_system", "apply_zstep_system", "bicubic_up", "blur_decimate",
     "blur_decimate_adj", "box_filter", "cg_solve", "estimate_kernel",
     "estimate_omega", "guided_filter", "kernel_error_pct", "kernel_normal_eq",
-    "laplacian", "matting_apply", "pan_stats", "pansharpen", "pcg_solve",
+    "laplacian", "matting_apply", "pan_stats", "pansharpen", "pcg_diag_solve", "pcg_solve",
     "precond_apply", "psnr", "rel_l2",
     "simplex_project", "solve_band", "solve_hrms", "up_solve",
 ]

@@ -98,18 +98,23 @@ def forward(params, x, round_act=None):
     return z, {"acts": acts, "pre": pre}
 
 
-def loss(z, target) -> float:
+def loss(z, target, weight=None) -> float:
+    """Mean over pixels of weight * ((z - target) / s)^2 (weight 1 if None)."""
     d = (np.asarray(z, np.float64) - np.asarray(target, np.float64)) / SCALE
-    return float(np.mean(d * d))
+    w = 1.0 if weight is None else np.asarray(weight, np.float64)
+    return float(np.mean(w * d * d))
 
 
-def backward(params, cache, z, target, round_grad=None):
-    """Gradients of loss(z, target) with respect to every (w, b). round_grad,
-    if given, is applied to the gradient passed between hidden layers."""
+def backward(params, cache, z, target, round_grad=None, weight=None):
+    """Gradients of loss(z, target, weight) with respect to every (w, b).
+    round_grad, if given, is applied to the gradient passed between hidden
+    layers."""
     acts, pre = cache["acts"], cache["pre"]
     H, W = z.shape
     d = (np.asarray(z, np.float64) - np.asarray(target, np.float64)) / SCALE
-    # dL/dz_scaled = 2 d / (H W), z_scaled = x_0 + f(x): dL/df = that
+    if weight is not None:
+        d = d * np.asarray(weight, np.float64)
+    # dL/dz_scaled = 2 w d / (H W), z_scaled = x_0 + f(x): dL/df = that
     g = (2.0 / (H * W)) * d[None]
     grads = [None] * len(params)
     for l in range(len(params) - 1, -1, -1):
@@ -144,3 +149,41 @@ def adam_step(params, grads, state, lr: float, beta1: float = 0.9, beta2: float 
         vh = state["v"][i] / (1 - beta2 ** t)
         out.append(p - lr * mh / (np.sqrt(vh) + eps))
     return [(out[2 * l], out[2 * l + 1]) for l in range(len(params))]
+
+
+# ----------------------------------------------------------------------------
+# Learned diagonal preconditioner (an extension of the Z0 CG; the paper runs
+# plain CG). A second network of the same architecture, with its own
+# parameters, reads (bicubic, PAN); its learned part c = f(x) = z / s - x_0
+# gives the diagonal s_d = max(c, floor) > 0 of P^{-1} = diag(s_d).
+# Training fits one preconditioned correction step from the warm start z_w,
+# z_w + kappa c r_0 ~ z*, with r_0 = b - A z_w and e = z* - z_w: the squared
+# error sum (kappa c r_0 - e)^2 equals, pixel by pixel,
+# kappa^2 r_0^2 (c - e / (kappa r_0))^2, i.e. the weighted loss above with
+# target z_t = s (x_0 + e / (kappa r_0)) and weight kappa^2 r_0^2. kappa is
+# a fixed scale (the least-squares constant step over the training pixels)
+# so that c is of order one; PCG is invariant under a constant scaling of
+# s_d, so kappa does not reach the solver.
+# ----------------------------------------------------------------------------
+DIAG_FLOOR = 1.0 / 64.0
+
+
+def diag_head(z, up, floor: float = DIAG_FLOOR):
+    """s_d = max(z / s - up / s, floor): the learned part of the diagonal
+    network's output, kept positive (a non-finite value gives the floor)."""
+    c = (np.asarray(z, np.float64) - np.asarray(up, np.float64)) / SCALE
+    return np.fmax(c, floor)
+
+
+def diag_fit(up, z_w, z_star, r0, kappa: float):
+    """(target, weight) of the weighted loss whose minimiser over the network's
+    learned part c is the one-step fit kappa c r_0 ~ z* - z_w (pixels with
+    r_0 = 0 get weight 0)."""
+    up, z_w, z_star, r0 = (np.asarray(a, np.float64) for a in (up, z_w, z_star, r0))
+    e = z_star - z_w
+    live = r0 != 0.0
+    q = np.where(live, e / np.where(live, kappa * r0, 1.0), 0.0)
+    target = up + SCALE * q
+    weight = (kappa * r0) ** 2
+    return target, weight
+

@@ -246,6 +246,42 @@ def pcg_solve(b, u, c: int, lam: float, st: PanStats, gamma: float, x0=None,
     return x, max_iter, rel
 
 
+def pcg_diag_solve(b, u, c: int, lam: float, st: PanStats, s, x0=None, tol: float = 1e-12,
+                   max_iter: int = 100000):
+    """Preconditioned CG on the Z0 system of Eq. Z_ini_matting with a diagonal
+    preconditioner, P^{-1} = diag(s), s > 0 per pixel (an extension: the
+    paper runs plain CG). The same textbook recurrence as pcg_solve with
+    z = s * r. The stop rule is the recursive residual ||r|| / ||b|| <= tol.
+    Returns (x, iterations, recursive relative residual)."""
+    b, u, s = f64(b), f64(u), f64(s)
+    if s.shape != b.shape or not np.all(s > 0.0):
+        raise ValueError("s must be positive and shaped like b")
+    x = np.zeros_like(b) if x0 is None else f64(x0).copy()
+    r = b - apply_z0_system(x, u, c, st, lam)
+    bb = float(np.sum(b * b))
+    if bb == 0.0:
+        return x, 0, 0.0
+    rel = float(np.sqrt(np.sum(r * r) / bb))
+    if rel <= tol:
+        return x, 0, rel
+    z = s * r
+    p = z.copy()
+    rz = float(np.sum(r * z))
+    for k in range(1, max_iter + 1):
+        Ap = apply_z0_system(p, u, c, st, lam)
+        alpha = rz / float(np.sum(p * Ap))
+        x += alpha * p
+        r -= alpha * Ap
+        rel = float(np.sqrt(np.sum(r * r) / bb))
+        if rel <= tol:
+            return x, k, rel
+        z = s * r
+        rz_new = float(np.sum(r * z))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, max_iter, rel
+
+
 def cg_relchange(b, u, c: int, lam: float, st: PanStats, x0=None, tol: float = 5e-5,
                  max_iter: int = 100000):
     """CG on the Z0 system of Eq. Z_ini_matting (textbook Hestenes-Stiefel)
