@@ -312,6 +312,7 @@ def run_profile_solve(args):
 
 
 WARM_WEIGHTS = os.path.join(ROOT, "paper_2103_09943_gb300", "weights", "warm_cnn.npz")
+DIAG_WEIGHTS = os.path.join(ROOT, "paper_2103_09943_gb300", "weights", "diag_cnn.npz")
 
 
 def load_warm_net(which, dev):
@@ -332,14 +333,22 @@ def compare_variants(api, X, Y, cfg, kp, net, dev, steps=3):
     from zeros, and the preconditioned CG from the network's warm start, all
     stopping at the same relative residual; and the paper's own setting
     (Sec. IV-F): a 29 x 29 kernel support, plain CG from zeros stopped when
-    the relative change of the iterate falls below 5e-5."""
+    the relative change of the iterate falls below 5e-5. With the network:
+    plain CG and the learned diagonal preconditioner from its warm start."""
     import torch
     out = {}
     forms = [("plain_cg_cold", dict(precond=0, warm=0), cfg.R),
              ("pcg_cold", dict(precond=1, warm=0), cfg.R)]
     if net is not None:
-        forms.append(("pcg_cnn_warm", dict(precond=1, warm=2, cnn_params=net.params.data_ptr()),
-                      cfg.R))
+        wp = net.params.data_ptr()
+        forms.append(("pcg_cnn_warm", dict(precond=1, warm=2, cnn_params=wp), cfg.R))
+        forms.append(("plain_cg_cnn_warm", dict(precond=0, warm=2, cnn_params=wp), cfg.R))
+        if os.path.exists(DIAG_WEIGHTS):
+            from paper_2103_09943_gb300.cnn import WarmStartNet
+            dnet = WarmStartNet.load(DIAG_WEIGHTS, device=dev)
+            forms.append(("diag_learned_cnn_warm",
+                          dict(precond=2, warm=2, cnn_params=wp,
+                               diag_params=dnet.params.data_ptr()), cfg.R))
     forms.append(("paper_setting_29x29_relchange",
                   dict(precond=0, warm=0, stop_rule=1, tol=5e-5), 14))
     for name, kw, R in forms:

@@ -100,7 +100,10 @@ typedef struct ps_hrms_params {
                            Eq. Z_solution with M of Eq. Z_ini_matting replaced
                            by gamma I, applied exactly by FFT and a per-alias-
                            group solve (FP32). The solution and the stop rule
-                           are unchanged; the iteration count drops.          */
+                           are unchanged; the iteration count drops.
+                           2: diagonal, P^{-1} = diag(s) with s > 0 per pixel
+                           and band, from precond_diag or from the learned
+                           diagonal network diag_params.                   */
     float precond_gamma; /* gamma of P (default 4; any value in [1, 8] gives
                            about the same iteration counts)                   */
     int warm;           /* start point of the Z0 CG when d_z_init is NULL.
@@ -129,6 +132,19 @@ typedef struct ps_hrms_params {
                            the guided filter and Eq. Z_solution; they take
                            the plain CG (precond must be 0) and one branch
                            per iteration.                                */
+    const float *precond_diag; /* precond == 2: the diagonal s of P^{-1}
+                           (device, N x H x W FP32, every value > 0 and
+                           finite, caller-owned, read during the solve).
+                           NULL: s comes from diag_params. Not accepted by
+                           ps_pansharpen_batched (one diagonal per scene). */
+    const float *diag_params; /* precond == 2 without precond_diag: device,
+                           ps_cnn_param_count() FP32 values of the diagonal
+                           network, the architecture of include/ps_cnn.h on
+                           (bicubic, PAN); s = max((net - bicubic) / 255,
+                           1/64). It is trained (ps_cnn_loss_grad_weighted)
+                           so that z_w + kappa s r_0 fits the solution from
+                           a warm start z_w with residual r_0; PCG does not
+                           depend on the scale kappa.                      */
 } ps_hrms_params;
 
 /* Per-band result of the Z0 conjugate-gradient solve. */

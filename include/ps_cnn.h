@@ -48,6 +48,15 @@ ps_status ps_cnn_loss_grad(const float *d_params, const float *d_up, const float
                            float *d_grad, double *d_loss, void *d_ws, size_t ws_bytes,
                            void *stream);
 
+/* The same with a per-pixel weight w >= 0 (B x H x W FP32, device; NULL:
+ * w = 1): loss sum_p w_p ((z - target) / 255)^2 / (B H W). This trains the
+ * diagonal network of ps_hrms_params.diag_params, whose target and weight
+ * turn the one-step fit of the diagonal into this form. */
+ps_status ps_cnn_loss_grad_weighted(const float *d_params, const float *d_up,
+                                    const float *d_pan, size_t pan_stride, const float *d_target,
+                                    const float *d_weight, int B, int H, int W, float *d_grad,
+                                    double *d_loss, void *d_ws, size_t ws_bytes, void *stream);
+
 /* One Adam step (t = step >= 1) on d_params with moments d_m, d_v (FP32,
  * ps_cnn_param_count() each, zero before the first step). */
 ps_status ps_cnn_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int step,

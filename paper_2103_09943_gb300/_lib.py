@@ -28,7 +28,8 @@ class HrmsParams(ctypes.Structure):
                 ("host_loop", ctypes.c_int), ("precond", ctypes.c_int),
                 ("precond_gamma", ctypes.c_float), ("warm", ctypes.c_int),
                 ("cnn_params", ctypes.c_void_p), ("stop_rule", ctypes.c_int),
-                ("zstep_fp32", ctypes.c_int), ("prior", ctypes.c_int)]
+                ("zstep_fp32", ctypes.c_int), ("prior", ctypes.c_int),
+                ("precond_diag", ctypes.c_void_p), ("diag_params", ctypes.c_void_p)]
 
 
 class Tuning(ctypes.Structure):
@@ -94,6 +95,7 @@ SIGNATURES = {
     "ps_cnn_workspace_size": (_Z, [_I, _I, _I, _I]),
     "ps_cnn_forward": (_I, [_P, _P, _P, _Z, _I, _I, _I, _P, _P, _Z, _P]),
     "ps_cnn_loss_grad": (_I, [_P, _P, _P, _Z, _P, _I, _I, _I, _P, _P, _P, _Z, _P]),
+    "ps_cnn_loss_grad_weighted": (_I, [_P, _P, _P, _Z, _P, _P, _I, _I, _I, _P, _P, _P, _Z, _P]),
     "ps_cnn_adam": (_I, [_P, _P, _P, _P, _I, _F, _F, _F, _F, _P]),
     "ps_cnn_sync_status": (_I, [_P, _I, _I, _I, _I, _P]),
     "ps_op_cnn_conv32": (_I, [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P, _Z, _P]),

@@ -93,17 +93,28 @@ class WarmStartNet:
             _check(lib.ps_cnn_sync_status(_ptr(ws), B, H, W, 0, _stream()))
         return z
 
-    def loss_grad(self, up, pan, target):
-        """Mean squared error of z / 255 against target / 255 and its gradient
-        (into self.grad). Returns the loss as a float (synchronises)."""
+    def loss_grad(self, up, pan, target, weight=None):
+        """Mean squared error of z / 255 against target / 255 (per-pixel
+        weighted when `weight` (B, H, W) is given) and its gradient (into
+        self.grad). Returns the loss as a float (synchronises)."""
         B, H, W = up.shape
         _f32(up, "up"), _f32(pan, "pan"), _f32(target, "target")
         ws = self._workspace(B, H, W, 1)
         lib = _lib.load()
-        _check(lib.ps_cnn_loss_grad(_ptr(self.params), _ptr(up), _ptr(pan),
-                                    self._pan_stride(pan, B, H, W), _ptr(target), B, H, W,
-                                    _ptr(self.grad), _ptr(self.loss), _ptr(ws), ws.numel(),
-                                    _stream()))
+        if weight is None:
+            _check(lib.ps_cnn_loss_grad(_ptr(self.params), _ptr(up), _ptr(pan),
+                                        self._pan_stride(pan, B, H, W), _ptr(target), B, H, W,
+                                        _ptr(self.grad), _ptr(self.loss), _ptr(ws), ws.numel(),
+                                        _stream()))
+        else:
+            _f32(weight, "weight")
+            if tuple(weight.shape) != (B, H, W):
+                raise ValueError("weight must be shaped like up")
+            _check(lib.ps_cnn_loss_grad_weighted(_ptr(self.params), _ptr(up), _ptr(pan),
+                                                 self._pan_stride(pan, B, H, W), _ptr(target),
+                                                 _ptr(weight), B, H, W, _ptr(self.grad),
+                                                 _ptr(self.loss), _ptr(ws), ws.numel(),
+                                                 _stream()))
         _check(lib.ps_cnn_sync_status(_ptr(ws), B, H, W, 1, _stream()))
         return float(self.loss.item()) / (B * H * W)
 

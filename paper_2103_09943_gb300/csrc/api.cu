@@ -137,9 +137,10 @@ ps_status check_hrms(const ps_hrms_params *p) {
         return PS_ERR_INVALID_ARG;
     if (!isfinite(p->lambda) || !isfinite(p->eps) || !isfinite(p->tol))
         return PS_ERR_INVALID_ARG;
-    if (p->precond != 0 && p->precond != 1) return PS_ERR_INVALID_ARG;
-    if (p->precond && (!(p->precond_gamma > 0.f) || !isfinite(p->precond_gamma)))
+    if (p->precond < 0 || p->precond > 2) return PS_ERR_INVALID_ARG;
+    if (p->precond == 1 && (!(p->precond_gamma > 0.f) || !isfinite(p->precond_gamma)))
         return PS_ERR_INVALID_ARG;
+    if (p->precond == 2 && !p->precond_diag && !p->diag_params) return PS_ERR_INVALID_ARG;
     if (p->warm < 0 || p->warm > 2) return PS_ERR_INVALID_ARG;
     if (p->stop_rule != 0 && p->stop_rule != 1) return PS_ERR_INVALID_ARG;
     if (p->zstep_fp32 != 0 && p->zstep_fp32 != 1) return PS_ERR_INVALID_ARG;
@@ -269,8 +270,9 @@ struct CgLoopArgs {
     float *x, *rv, *pA, *pB, *ap, *v;
     CgBand *bands;
     CgGlobal *g;
-    int precond;
-    PrecArgs pa;  // z = P^{-1} r (valid when precond)
+    int precond;  // 0 none, 1 the FFT preconditioner, 2 diagonal
+    PrecArgs pa;  // z = P^{-1} r (pa.z and pa.r valid when precond)
+    const float *sd;  // the diagonal s of P^{-1} (precond == 2)
     int split;    // 1, 2 or 4: parts of the bands run as parallel branches
     Tuning tune;  // launch choices (part of the graph cache key)
     int pad_;
@@ -342,7 +344,9 @@ void enqueue_bands(const CgLoopArgs &a, int b0, int n, const float *p_old, float
     launch_llp_cgq2(la, a.r, n, st);
     launch_cg_update(a.x + o, a.rv + o, p_new + o, a.ap + o, v, a.u, a.R, a.c, n, a.H, a.W, bands,
                      a.g, st);
-    if (a.precond) {
+    if (a.precond == 2) {
+        launch_diag_precond(a.rv + o, a.sd + o, a.pa.z + o, n, HW, bands, st);
+    } else if (a.precond) {
         PrecArgs pa = a.pa;
         pa.r = a.rv + o;
         pa.z = a.pa.z + o;
@@ -579,8 +583,14 @@ size_t prior_bytes(int N, int H, int W) {
            2 * align_up((size_t)kMaxTaps * 4);
 }
 
+// Whether a solve with parameters p may run a network (the warm start or the
+// diagonal), which then takes its workspace at Layout::cnn.
+bool runs_network(const ps_hrms_params *p) {
+    return p && (p->warm == 2 || (p->precond == 2 && !p->precond_diag));
+}
+
 size_t prior_offset(const Layout &L, int N, int H, int W, const ps_hrms_params *p) {
-    return align_up(L.cnn + (p && p->warm == 2 ? ps_cnn_workspace_size(N, H, W, 0) : 0));
+    return align_up(L.cnn + (runs_network(p) ? ps_cnn_workspace_size(N, H, W, 0) : 0));
 }
 
 // The prior's operator pieces over the scratch at `off` (pointers only).
@@ -628,12 +638,15 @@ ps_status make_solve_call(const float *d_lrms, const float *d_pan, const float *
     if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
     if ((s = check_fft_dims(H, W)) != PS_OK) return s;
     if ((s = check_hrms(p)) != PS_OK) return s;
-    if (p->precond && !precond_supported(H, W, ratio)) return PS_ERR_UNSUPPORTED;
+    if (p->precond == 1 && !precond_supported(H, W, ratio)) return PS_ERR_UNSUPPORTED;
     if (!d_lrms || !d_pan || !d_kernel || !d_hrms) return PS_ERR_INVALID_ARG;
     if ((d_z0 && !aligned16(d_z0)) || (d_z_init && !aligned16(d_z_init)))
         return PS_ERR_INVALID_ARG;
+    if (p->precond == 2 && p->precond_diag && !aligned16(p->precond_diag))
+        return PS_ERR_INVALID_ARG;
     if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &sc->ws)) != PS_OK) return s;
-    if (p->warm == 2 && !d_z_init && ws_bytes < sc->ws.L.cnn + ps_cnn_workspace_size(N, H, W, 0))
+    const bool net = (p->warm == 2 && !d_z_init) || (p->precond == 2 && !p->precond_diag);
+    if (net && ws_bytes < sc->ws.L.cnn + ps_cnn_workspace_size(N, H, W, 0))
         return PS_ERR_WORKSPACE;
     sc->prior_off = 0;
     if (p->prior != PS_PRIOR_LLP) {
@@ -695,6 +708,22 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
             launch_symbol_add(fh, po.tsym, HW, d == 0, st);
         }
     }
+    const float *sd = nullptr;
+    if (p->precond == 2 && p->precond_diag) {
+        sd = p->precond_diag;
+    } else if (p->precond == 2) {
+        // the diagonal network on (bicubic, PAN): its output in z (free
+        // until the first preconditioner application), the bicubic and then
+        // s = max((net - bicubic) / 255, 1/64) in the unused spectrum buffer
+        float *s_buf = ws.at<float>(ws.L.spec);
+        float *net_out = ws.at<float>(ws.L.z);
+        launch_bicubic_up(d_lrms, N, H / c, W / c, c, s_buf, st);
+        if ((s = ps_cnn_forward(p->diag_params, s_buf, sc.pan, 0, N, H, W, net_out,
+                                ws.base + ws.L.cnn, sc.ws_bytes - ws.L.cnn, st)) != PS_OK)
+            return s;
+        launch_diag_head(net_out, s_buf, (size_t)N * HW, 1.0f / 64.0f, st);
+        sd = s_buf;
+    }
     launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
     if (!d_z_init && p->warm >= 1) {
         // bicubic start point, written where the iterate lives
@@ -738,7 +767,12 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
     launch_cg_init(rv, d_z_init ? ap : nullptr, d_z_init, x, rv, N, HW, bands, g, st);
     PrecArgs pa;
     memset(&pa, 0, sizeof(pa));
-    if (p->precond) {
+    if (p->precond == 2) {
+        // z0 = s r0, rho = r0^T z0
+        pa.r = rv;
+        pa.z = ws.at<float>(ws.L.z);
+        launch_diag_precond(rv, sd, pa.z, N, HW, bands, st);
+    } else if (p->precond) {
         // z0 = P^{-1} r0, rho = r0^T z0 (the first direction is p = z0)
         pa = make_prec_args(ws, rv, ws.at<float>(ws.L.z), N, H, W, c,
                             p->lambda * p->precond_gamma, bands, g);
@@ -755,6 +789,7 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
     a->bands = bands; a->g = g;
     a->precond = p->precond;
     a->pa = pa;
+    a->sd = sd;
     a->tune = tuning_get(a->dev, N, H, W, c, p->r);
     a->split = a->tune.split ? a->tune.split : ((N >= 4) ? 2 : 1);
     a->po = po;
@@ -918,6 +953,8 @@ void ps_default_hrms_params(ps_hrms_params *p) {
     p->stop_rule = 0;
     p->zstep_fp32 = 0;
     p->prior = PS_PRIOR_LLP;
+    p->precond_diag = nullptr;
+    p->diag_params = nullptr;
 }
 
 const char *ps_status_string(int s) {
@@ -942,7 +979,7 @@ size_t ps_workspace_size(int N, int H, int W, int ratio, int R, const ps_hrms_pa
     if (!make_layout(N, H, W, ratio, R, &L)) return 0;
     if (hp && hp->prior != PS_PRIOR_LLP)
         return prior_offset(L, N, H, W, hp) + prior_bytes(N, H, W) + kAlign;
-    if (hp && hp->warm == 2) return L.total + ps_cnn_workspace_size(N, H, W, 0);
+    if (runs_network(hp)) return L.total + ps_cnn_workspace_size(N, H, W, 0);
     return L.total;
 }
 
@@ -1269,7 +1306,7 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
     ps_status s;
     if (!scenes || count < 1 || count > kMaxBatch) return PS_ERR_INVALID_ARG;
     if ((s = check_hrms(hp)) != PS_OK) return s;
-    if (hp->host_loop) return PS_ERR_INVALID_ARG;
+    if (hp->host_loop || hp->precond_diag) return PS_ERR_INVALID_ARG;
     if (kp && (s = check_kernel_params(kp)) != PS_OK) return s;
     if (!d_ws || ((uintptr_t)d_ws) % kAlign) return PS_ERR_WORKSPACE;
     for (int i = 0; i < count; ++i) {
@@ -1311,6 +1348,7 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
     key_put(key, hp->stop_rule);
     key_put(key, hp->prior);
     key_put(key, hp->zstep_fp32);
+    key_put(key, hp->diag_params);
     key_put(key, kp != nullptr);
     if (kp) {
         key_put(key, kp->lambda_omega);
@@ -1654,6 +1692,14 @@ ps_status ps_cnn_loss_grad(const float *d_params, const float *d_up, const float
                            size_t pan_stride, const float *d_target, int B, int H, int W,
                            float *d_grad, double *d_loss, void *d_ws, size_t ws_bytes,
                            void *stream) {
+    return ps_cnn_loss_grad_weighted(d_params, d_up, d_pan, pan_stride, d_target, nullptr, B, H,
+                                     W, d_grad, d_loss, d_ws, ws_bytes, stream);
+}
+
+ps_status ps_cnn_loss_grad_weighted(const float *d_params, const float *d_up,
+                                    const float *d_pan, size_t pan_stride, const float *d_target,
+                                    const float *d_weight, int B, int H, int W, float *d_grad,
+                                    double *d_loss, void *d_ws, size_t ws_bytes, void *stream) {
     ps_status s;
     if ((s = cnn_check_inputs(d_params, d_up, d_pan, B, H, W)) != PS_OK) return s;
     if (!d_target || !d_grad || !d_loss) return PS_ERR_INVALID_ARG;
@@ -1675,8 +1721,8 @@ ps_status ps_cnn_loss_grad(const float *d_params, const float *d_up, const float
     // forward, keeping every activation
     launch_cnn_first(d_up, d_pan, pan_stride, d_params + c.w_off[0], B, H, W, act[1], st);
     for (int l = 1; l <= 4; ++l) cnn_conv(c, act[l], act[l + 1], l, 0, nullptr, d_params, B, H, W, st);
-    launch_cnn_last(act[5], d_up, d_params + c.w_off[5], B, H, W, nullptr, d_target, d5, d_loss,
-                    st);
+    launch_cnn_last(act[5], d_up, d_params + c.w_off[5], B, H, W, nullptr, d_target, d_weight, d5,
+                    d_loss, st);
     // backward: D_l = dL / d(conv_l output before its ReLU)
     launch_cnn_last_bwd(act[5], d5, d_params + c.w_off[5], B, H, W, D[0], d_grad + c.w_off[5],
                         st);

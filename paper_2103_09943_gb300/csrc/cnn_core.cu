@@ -121,12 +121,14 @@ __global__ void __launch_bounds__(256, 2) cnn_first_kernel(const float *__restri
 }
 
 // z = s (up / s + conv5(a5) + b5). With a target: also the loss sum
-// sum ((z - t) / s)^2 (FP64, per launch) and d5 = 2 (z - t) / s / count.
+// sum w ((z - t) / s)^2 (FP64, per launch) and d5 = 2 w (z - t) / s / count,
+// w the per-pixel weight (1 without one).
 __global__ void __launch_bounds__(256) cnn_last_kernel(const __nv_bfloat16 *__restrict__ a5,
                                                        const float *__restrict__ up,
                                                        const float *__restrict__ prm5, int B,
                                                        int H, int W, float *__restrict__ z,
                                                        const float *__restrict__ target,
+                                                       const float *__restrict__ weight,
                                                        float inv_count, float *__restrict__ d5,
                                                        double *loss) {
     __shared__ float sw[kCh * 9 + 1];
@@ -157,8 +159,9 @@ __global__ void __launch_bounds__(256) cnn_last_kernel(const __nv_bfloat16 *__re
         if (z) z[idx] = zv;
         if (target) {
             const float d = (zv - __ldg(target + idx)) * (1.0f / kScale);
-            d5[idx] = 2.0f * d * inv_count;
-            l2 = (double)d * (double)d;
+            const float w = weight ? __ldg(weight + idx) : 1.0f;
+            d5[idx] = 2.0f * w * d * inv_count;
+            l2 = (double)w * (double)d * (double)d;
         }
     }
     if (!target) return;
@@ -428,10 +431,10 @@ void launch_cnn_first(const float *up, const float *pan, size_t pan_stride, cons
 }
 
 void launch_cnn_last(const __nv_bfloat16 *a5, const float *up, const float *prm5, int B, int H,
-                     int W, float *z, const float *target, float *d5, double *loss,
-                     cudaStream_t st) {
+                     int W, float *z, const float *target, const float *weight, float *d5,
+                     double *loss, cudaStream_t st) {
     const size_t P = (size_t)B * H * W;
-    cnn_last_kernel<<<blocks_for(P, 256), 256, 0, st>>>(a5, up, prm5, B, H, W, z, target,
+    cnn_last_kernel<<<blocks_for(P, 256), 256, 0, st>>>(a5, up, prm5, B, H, W, z, target, weight,
                                                         1.0f / (float)P, d5, loss);
 }
 

@@ -94,6 +94,12 @@ void launch_alias_solve(const double2 *spec, const double2 *bspec, float2 *sol, 
                         int W, int c, float lam, cudaStream_t st, const double *tsym = nullptr);
 cudaError_t fft_set_attrs();
 
+// diag.cu: the diagonal preconditioner z = s r (per-band r^T z, beta) and the
+// head s = max((zd - up) / 255, floor) of the diagonal network
+void launch_diag_precond(const float *r, const float *s, float *z, int N, size_t HW,
+                         CgBand *bands, cudaStream_t st);
+void launch_diag_head(const float *zd, float *s, size_t n, float floor_, cudaStream_t st);
+
 // prior.cu: the alternative cross-channel priors
 int prior_filter_radius(int prior, int R);
 int prior_filter_count(int prior);
@@ -164,8 +170,8 @@ void cnn_layout(int *w_off, int *b_off);  // w_off[6] = parameter count
 void launch_cnn_first(const float *up, const float *pan, size_t pan_stride, const float *prm,
                       int B, int H, int W, __nv_bfloat16 *a1, cudaStream_t st);
 void launch_cnn_last(const __nv_bfloat16 *a5, const float *up, const float *prm5, int B, int H,
-                     int W, float *z, const float *target, float *d5, double *loss,
-                     cudaStream_t st);
+                     int W, float *z, const float *target, const float *weight, float *d5,
+                     double *loss, cudaStream_t st);
 void launch_cnn_last_bwd(const __nv_bfloat16 *a5, const float *d5, const float *prm5, int B,
                          int H, int W, __nv_bfloat16 *D4, float *g5, cudaStream_t st);
 void launch_cnn_wgrad32(const __nv_bfloat16 *act, const __nv_bfloat16 *D, int B, int H, int W,

@@ -120,6 +120,26 @@ def test_argument_errors_return_before_launch(lib):
     st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
                            None, None, fake, 1 << 30, None)
     assert st == 1
+    # the diagonal preconditioner: a selector in 0..2, a 16-byte aligned
+    # diagonal, and room for the diagonal network when it supplies s
+    bad = HrmsParams.from_buffer_copy(hp)
+    bad.precond = 3
+    bad.precond_diag = 0x1000
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
+                           None, None, fake, 1 << 30, None)
+    assert st == 1
+    bad.precond = 2
+    bad.precond_diag = 0x1004
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
+                           None, None, fake, 1 << 30, None)
+    assert st == 1
+    bad.precond_diag = None
+    bad.diag_params = 0x1000
+    need = lib.ps_workspace_size(4, 256, 256, 4, 4, ctypes.byref(bad))
+    assert need > lib.ps_workspace_size(4, 256, 256, 4, 4, ctypes.byref(hp))
+    st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
+                           None, None, fake, lib.ps_workspace_size(4, 256, 256, 4, 4, None), None)
+    assert st == 4                                                  # no room for the network
     st = lib.ps_op_precond(fake, 2, 96, 96, 4, fake, 3, ctypes.c_float(-1.0), fake, fake,
                            1 << 30, None)
     assert st == 1
@@ -174,6 +194,12 @@ def test_batched_argument_errors_return_before_launch(lib):
     # the batch is one graph: no host-driven loop
     bad = HrmsParams.from_buffer_copy(hp)
     bad.host_loop = 1
+    assert lib.ps_pansharpen_batched(arr, 3, ctypes.byref(kp), ctypes.byref(bad), None, None,
+                                     ws, need, None) == 1
+    # one diagonal array cannot serve every scene
+    bad = HrmsParams.from_buffer_copy(hp)
+    bad.precond = 2
+    bad.precond_diag = 0x1000
     assert lib.ps_pansharpen_batched(arr, 3, ctypes.byref(kp), ctypes.byref(bad), None, None,
                                      ws, need, None) == 1
     # empty batch, one bad scene among good ones
