@@ -298,6 +298,12 @@ def run_profile_solve(args):
     import synth
     from paper_2103_09943_gb300 import api
     cfg = workload_config(args.r, args.scene, args.ratio)
+    if args.profile_shape:
+        from dataclasses import replace
+        b, side = (int(v) for v in args.profile_shape.lower().split("x"))
+        # the workload's shape count: the scene's content does not change the
+        # loop kernels' memory traffic, and the generator's time grows with it
+        cfg = replace(cfg, name=f"{cfg.name}-{b}x{side}", bands=b, H=side, W=side)
     scene = synth.make_scene(cfg)
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
@@ -814,6 +820,10 @@ def parse(argv=None):
     ap.add_argument("--profile-solve", type=int, default=0, metavar="ITERS",
                     help="no timing: run one HRMS solve of the workload with the CG loop "
                          "launched from the host, ITERS iterations (for profiler captures)")
+    ap.add_argument("--profile-shape", default="", metavar="BxS",
+                    help="with --profile-solve: B bands of S x S instead of the workload's "
+                         "size (the same scene recipe), e.g. 2x4096 for a case whose vectors "
+                         "exceed the L2 cache")
     ap.add_argument("--profile-warm", action="store_true",
                     help="no timing: run the warm-start network on the workload's bicubic "
                          "upsampling and PAN three times (for profiler captures)")
