@@ -37,7 +37,7 @@ struct Layout {
     size_t bhat;                        // HW double2 (kernel spectrum)
     size_t bh32;                        // HW float2 (the same, rounded)
     size_t twW32, twH32, twW64, twH64;  // twiddles
-    size_t bands, glob;                 // CG scalars
+    size_t bands, glob;                 // CG scalars; kMaxSplit loop-control records
     size_t bvec, f, G, omega, lags, ete, etf, zf, Q, kern, kinfo;
     size_t cnn;
     size_t total;
@@ -73,7 +73,7 @@ bool make_layout(int N, int H, int W, int c, int R, Layout *L) {
     L->twW64 = take((size_t)W * 16);
     L->twH64 = take((size_t)H * 16);
     L->bands = take((size_t)N * sizeof(CgBand));
-    L->glob = take(sizeof(CgGlobal));
+    L->glob = take(kMaxSplit * sizeof(CgGlobal));  // one per branch loop
     L->bvec = take(hw * 4);
     L->f = take(hw * 4);
     L->G = take(((size_t)N * N + N) * 8);
@@ -380,11 +380,66 @@ void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, in
     launch_cg_control(a.bands, a.g, a.N, use_cond, h, st);
 }
 
-// Adds to `graph`, after `deps`, the CG loop of `a`: a conditional WHILE node
-// (its handle starts at 1, and cg_control clears it once every band has
-// stopped) whose body, captured on `capture`, holds two iterations.
+// One conditional WHILE node (its handle starts at 1; cg_control clears it
+// once every band of [b0, b0 + n) has stopped) whose body, captured on
+// `capture`, holds two iterations of those bands' kernels, with `g` as the
+// loop's control record.
+ps_status add_branch_loop(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t ndeps,
+                          const CgLoopArgs &a, int b0, int n, CgGlobal *g, cudaStream_t capture,
+                          cudaGraphNode_t *node) {
+    cudaGraphConditionalHandle handle;
+    if (cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault) !=
+        cudaSuccess)
+        return PS_ERR_CUDA;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(node, graph, deps, nullptr, ndeps, &cp) != cudaSuccess)
+        return PS_ERR_CUDA;
+    if (cudaStreamBeginCaptureToGraph(capture, cp.conditional.phGraph_out[0], nullptr, nullptr,
+                                      0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return PS_ERR_CUDA;
+    CgLoopArgs ak = a;
+    ak.g = g;
+    ak.pa.g = g;
+    enqueue_bands(ak, b0, n, a.pA, a.pB, capture);
+    launch_cg_control(a.bands + b0, g, n, 1, handle, capture);
+    enqueue_bands(ak, b0, n, a.pB, a.pA, capture);
+    launch_cg_control(a.bands + b0, g, n, 1, handle, capture);
+    cudaGraph_t captured = nullptr;
+    if (cudaStreamEndCapture(capture, &captured) != cudaSuccess) {
+        cudaGetLastError();
+        return PS_ERR_CUDA;
+    }
+    return PS_OK;
+}
+
+// Adds to `graph`, after `deps`, the CG loop of `a`. With the bands split
+// into branches, each branch is a loop of its own (its own WHILE node and
+// control record a.g + k, all copies of a.g made by the prelude), so that
+// no branch waits for the others between iterations and a branch whose
+// bands have stopped launches nothing more; an empty node joins them.
+// Otherwise one WHILE node whose body, captured on `capture`, holds two
+// iterations (its handle starts at 1, and cg_control clears it once every
+// band has stopped).
 ps_status add_cg_loop_node(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t ndeps,
                            const CgLoopArgs &a, cudaStream_t capture, cudaGraphNode_t *node) {
+    if (a.po.prior == PS_PRIOR_LLP && a.split > 1) {
+        cudaGraphNode_t loops[kMaxSplit];
+        int nl = 0;
+        for (int k = 0; k < a.split; ++k) {
+            const int b0 = split_begin(a.N, a.split, k), b1 = split_begin(a.N, a.split, k + 1);
+            if (b1 <= b0) continue;
+            const ps_status s =
+                add_branch_loop(graph, deps, ndeps, a, b0, b1 - b0, a.g + k, capture, &loops[nl]);
+            if (s != PS_OK) return s;
+            ++nl;
+        }
+        if (cudaGraphAddEmptyNode(node, graph, loops, nl) != cudaSuccess) return PS_ERR_CUDA;
+        return PS_OK;
+    }
     cudaGraphConditionalHandle handle;
     if (cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault) !=
         cudaSuccess)

@@ -14,6 +14,7 @@ constexpr int kMaxWinR = 4;        // LLP window radius r <= 4
 constexpr int kMaxBands = 64;
 constexpr int kMaxFFT = 8192;      // H, W <= 8192
 constexpr int kMaxRatio = 8;
+constexpr int kMaxSplit = 4;       // parallel branches (own loops) of the CG iteration
 
 // Wrap an index that lies in [-n, 2n) onto [0, n).
 __host__ __device__ __forceinline__ int wrapi(int i, int n) {

@@ -611,16 +611,18 @@ __global__ void cg_reset_kernel(CgBand *bands, CgGlobal *g, int N, double tol, i
         CgBand z = {};
         bands[b] = z;
     }
-    if (t == 0) {
-        g->cnt_bands = 0u;
-        g->active = N;
-        g->max_iters = 0;
-        g->stop = 0;
-        g->iter = 0;
-        g->max_iter = max_iter;
-        g->tol = tol;
-        g->precond = precond;
-        g->rule = rule;
+    // every loop-control record of the solve (one per branch loop), alike
+    if (t < kMaxSplit) {
+        CgGlobal *gk = g + t;
+        gk->cnt_bands = 0u;
+        gk->active = N;
+        gk->max_iters = 0;
+        gk->stop = 0;
+        gk->iter = 0;
+        gk->max_iter = max_iter;
+        gk->tol = tol;
+        gk->precond = precond;
+        gk->rule = rule;
     }
 }
 
