@@ -236,7 +236,8 @@ def cg_iteration_roofline(api, X, Y, kern, cfg, hp, peak_gbs, dev):
 
     # below the iteration counts the solves need at their tolerance, so that
     # the forced iterations stay well above the FP32 floor of the residual
-    lo, hi = (10, 60) if hp.precond else (20, 220)
+    # (multiples of four: the graph's branch loops run four iterations a body)
+    lo, hi = (12, 60) if hp.precond else (20, 220)
     t_lo, t_hi = timed(lo), timed(hi)
     per_iter_ms = (t_hi - t_lo) / (hi - lo)
     nimg = (cfg.bands + 1) // 2

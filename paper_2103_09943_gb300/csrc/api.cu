@@ -380,10 +380,15 @@ void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, in
     launch_cg_control(a.bands, a.g, a.N, use_cond, h, st);
 }
 
+// Iterations per body of a branch loop (even: the direction alternates
+// between two buffers). Iterations after the stop inside a body launch and
+// return at once.
+constexpr int kBranchBodyIters = 4;
+
 // One conditional WHILE node (its handle starts at 1; cg_control clears it
 // once every band of [b0, b0 + n) has stopped) whose body, captured on
-// `capture`, holds two iterations of those bands' kernels, with `g` as the
-// loop's control record.
+// `capture`, holds kBranchBodyIters iterations of those bands' kernels, with
+// `g` as the loop's control record.
 ps_status add_branch_loop(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t ndeps,
                           const CgLoopArgs &a, int b0, int n, CgGlobal *g, cudaStream_t capture,
                           cudaGraphNode_t *node) {
@@ -404,10 +409,12 @@ ps_status add_branch_loop(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t
     CgLoopArgs ak = a;
     ak.g = g;
     ak.pa.g = g;
-    enqueue_bands(ak, b0, n, a.pA, a.pB, capture);
-    launch_cg_control(a.bands + b0, g, n, 1, handle, capture);
-    enqueue_bands(ak, b0, n, a.pB, a.pA, capture);
-    launch_cg_control(a.bands + b0, g, n, 1, handle, capture);
+    for (int i = 0; i < kBranchBodyIters; i += 2) {
+        enqueue_bands(ak, b0, n, a.pA, a.pB, capture);
+        launch_cg_control(a.bands + b0, g, n, 1, handle, capture);
+        enqueue_bands(ak, b0, n, a.pB, a.pA, capture);
+        launch_cg_control(a.bands + b0, g, n, 1, handle, capture);
+    }
     cudaGraph_t captured = nullptr;
     if (cudaStreamEndCapture(capture, &captured) != cudaSuccess) {
         cudaGetLastError();
