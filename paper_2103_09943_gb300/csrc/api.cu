@@ -245,9 +245,9 @@ int split_begin(int N, int split, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// CG loop as a CUDA graph: a conditional WHILE node whose body holds two
-// iterations (the direction p alternates between two buffers). Executable
-// graphs are cached per argument set.
+// CG loop as a CUDA graph: conditional WHILE nodes whose bodies hold a few
+// iterations each (the direction p alternates between two buffers).
+// Executable graphs are cached per argument set.
 // ---------------------------------------------------------------------------
 // The alternative priors' operator pieces: filters F_d (radius fR), the
 // statistics of their guides F_d Y, four N x H x W scratch images, the FP64
@@ -380,9 +380,9 @@ void enqueue_iteration(const CgLoopArgs &a, const float *p_old, float *p_new, in
     launch_cg_control(a.bands, a.g, a.N, use_cond, h, st);
 }
 
-// Iterations per body of a branch loop (even: the direction alternates
-// between two buffers). Iterations after the stop inside a body launch and
-// return at once.
+// Iterations per body of a CG loop (even: the direction alternates between
+// two buffers). Iterations after the stop inside a body launch and return at
+// once.
 constexpr int kBranchBodyIters = 4;
 
 // One conditional WHILE node (its handle starts at 1; cg_control clears it
@@ -428,9 +428,9 @@ ps_status add_branch_loop(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t
 // control record a.g + k, all copies of a.g made by the prelude), so that
 // no branch waits for the others between iterations and a branch whose
 // bands have stopped launches nothing more; an empty node joins them.
-// Otherwise one WHILE node whose body, captured on `capture`, holds two
-// iterations (its handle starts at 1, and cg_control clears it once every
-// band has stopped).
+// Otherwise one WHILE node whose body, captured on `capture`, holds
+// kBranchBodyIters iterations (its handle starts at 1, and cg_control clears
+// it once every band has stopped).
 ps_status add_cg_loop_node(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t ndeps,
                            const CgLoopArgs &a, cudaStream_t capture, cudaGraphNode_t *node) {
     if (a.po.prior == PS_PRIOR_LLP && a.split > 1) {
@@ -462,8 +462,10 @@ ps_status add_cg_loop_node(cudaGraph_t graph, const cudaGraphNode_t *deps, size_
     if (cudaStreamBeginCaptureToGraph(capture, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return PS_ERR_CUDA;
-    enqueue_iteration(a, a.pA, a.pB, 1, handle, capture);
-    enqueue_iteration(a, a.pB, a.pA, 1, handle, capture);
+    for (int i = 0; i < kBranchBodyIters; i += 2) {
+        enqueue_iteration(a, a.pA, a.pB, 1, handle, capture);
+        enqueue_iteration(a, a.pB, a.pA, 1, handle, capture);
+    }
     cudaGraph_t captured = nullptr;
     if (cudaStreamEndCapture(capture, &captured) != cudaSuccess) {
         cudaGetLastError();
