@@ -657,9 +657,14 @@ __device__ __forceinline__ void block_sum2(double a, double b, double *red, doub
 
 // 2-D DFT of three real n x n arrays (sg = -1) or inverse of three complex
 // spectra to real arrays (sg = +1, scaled by 1/n^2).
-__device__ void dft3_forward(const float *a0, const float *a1, const float *a2, float2 *T0,
-                             float2 *T1, float2 *T2, float2 *F0, float2 *F1, float2 *F2,
-                             const float2 *tw, int n) {
+// NC > 0: n = NC known at compile time (divisions by n become multiplies,
+// the tap loops unroll); NC = 0: n = n_rt.
+template <int NC>
+__device__ __forceinline__ void dft3_forward(const float *a0, const float *a1, const float *a2,
+                                             float2 *T0, float2 *T1, float2 *T2, float2 *F0,
+                                             float2 *F1, float2 *F2, const float2 *tw,
+                                             int n_rt) {
+    const int n = NC ? NC : n_rt;
     const int nt = n * n;
     for (int k = threadIdx.x; k < 3 * nt; k += blockDim.x) {
         const int which = k / nt, e = k - which * nt;
@@ -692,9 +697,12 @@ __device__ void dft3_forward(const float *a0, const float *a1, const float *a2, 
     __syncthreads();
 }
 
-__device__ void dft3_inverse(const float2 *F0, const float2 *F1, const float2 *F2, float2 *T0,
-                             float2 *T1, float2 *T2, float *o0, float *o1, float *o2,
-                             const float2 *tw, int n) {
+template <int NC>
+__device__ __forceinline__ void dft3_inverse(const float2 *F0, const float2 *F1,
+                                             const float2 *F2, float2 *T0, float2 *T1,
+                                             float2 *T2, float *o0, float *o1, float *o2,
+                                             const float2 *tw, int n_rt) {
+    const int n = NC ? NC : n_rt;
     const int nt = n * n;
     for (int k = threadIdx.x; k < 3 * nt; k += blockDim.x) {
         const int which = k / nt, e = k - which * nt;
@@ -756,13 +764,16 @@ __device__ __forceinline__ bool admm_q_in_smem(int R) {
     return admm_q_fits(R, state);
 }
 
+// NC > 0: compiled for the kernel side n = 2R + 1 = NC (every index
+// division by n or n^2 becomes a multiply); NC = 0: any R.
+template <int NC>
 __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
                                                     const double *__restrict__ zf, int R,
                                                     ps_kernel_params p, float *kernel_out,
                                                     int *info_iters, int *info_status,
                                                     double *info_change) {
     extern __shared__ __align__(16) unsigned char admm_sm[];
-    const int n = 2 * R + 1, nt = n * n;
+    const int n = NC ? NC : 2 * R + 1, nt = n * n;
     const int ntp = (nt + 3) & ~3;
     const int tid = threadIdx.x, nthr = blockDim.x;
     double *red = reinterpret_cast<double *>(admm_sm);
@@ -958,7 +969,7 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
             b3s[k] = b3;
         }
         __syncthreads();
-        dft3_forward(un, wv, b3s, T0, T1, T2, F0, F1, F2, tw, n);
+        dft3_forward<NC>(un, wv, b3s, T0, T1, T2, F0, F1, F2, tw, n);
         for (int k = tid; k < nt; k += nthr) {
             const int ky = k / n, kx = k - (k / n) * n;
             const float2 dh = make_float2(tw[kx].x - 1.0f, -tw[kx].y);   // exp(+2 pi i kx/n) - 1
@@ -981,7 +992,7 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
             F2[k] = q2;
         }
         __syncthreads();
-        dft3_inverse(F0, F1, F2, T0, T1, T2, un, p1, p2, tw, n);
+        dft3_inverse<NC>(F0, F1, F2, T0, T1, T2, un, p1, p2, tw, n);
         // 5-7. multiplier updates (Eq. subproblems), stop test
         float dn = 0.f, nn = 0.f;
         for (int k = tid; k < nt; k += nthr) {
@@ -1026,13 +1037,30 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
 void launch_admm(const float *Q, const double *zf, int R, const ps_kernel_params &p,
                  float *kernel_out, int *info_iters, int *info_status, double *info_change,
                  cudaStream_t st) {
-    admm_kernel<<<1, 1024, admm_smem_bytes(R), st>>>(Q, zf, R, p, kernel_out, info_iters,
-                                                     info_status, info_change);
+    const size_t smem = admm_smem_bytes(R);
+    switch (R) {
+#define PS_ADMM(RR)                                                                      \
+    case RR:                                                                             \
+        admm_kernel<2 * RR + 1><<<1, 1024, smem, st>>>(Q, zf, R, p, kernel_out, info_iters, \
+                                                       info_status, info_change);         \
+        return;
+        PS_ADMM(4) PS_ADMM(6) PS_ADMM(8) PS_ADMM(14)
+#undef PS_ADMM
+        default:
+            admm_kernel<0><<<1, 1024, smem, st>>>(Q, zf, R, p, kernel_out, info_iters,
+                                                  info_status, info_change);
+    }
 }
 
 cudaError_t kest_set_attrs() {
-    return cudaFuncSetAttribute(admm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kAdmmMaxSmem);
+    cudaError_t e = cudaSuccess;
+#define PS_ADMM_ATTR(NC)                                                                   \
+    if (e == cudaSuccess)                                                                  \
+        e = cudaFuncSetAttribute(admm_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)kAdmmMaxSmem);
+    PS_ADMM_ATTR(0) PS_ADMM_ATTR(9) PS_ADMM_ATTR(13) PS_ADMM_ATTR(17) PS_ADMM_ATTR(29)
+#undef PS_ADMM_ATTR
+    return e;
 }
 
 }  // namespace ps
