@@ -175,9 +175,15 @@ struct DevState {
     // the two halves of the bands as parallel branches
     cudaStream_t branch[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
+    // ps_pansharpen's high-priority side stream (the kernel estimate)
+    cudaStream_t early = nullptr;
+    cudaEvent_t early_fork = nullptr, early_join = nullptr;
 };
 std::mutex g_mu;
 std::vector<DevState> g_dev;
+// SMs that the warm-start network leaves free while it overlaps the kernel
+// estimate (whose ADMM takes one whole SM, its Cholesky panels a few)
+constexpr int kEarlyReserveSms = 2;
 
 ps_status ensure_device(cudaStream_t *capture, int *num_sms = nullptr) {
     int dev = 0;
@@ -212,8 +218,33 @@ ps_status ensure_device(cudaStream_t *capture, int *num_sms = nullptr) {
         }
         if (!d.fork && cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming) != cudaSuccess)
             return PS_ERR_CUDA;
+        int lo = 0, hi = 0;
+        if (!d.early && (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+                         cudaStreamCreateWithPriority(&d.early, cudaStreamNonBlocking, hi) !=
+                             cudaSuccess))
+            return PS_ERR_CUDA;
+        if (!d.early_fork &&
+            cudaEventCreateWithFlags(&d.early_fork, cudaEventDisableTiming) != cudaSuccess)
+            return PS_ERR_CUDA;
+        if (!d.early_join &&
+            cudaEventCreateWithFlags(&d.early_join, cudaEventDisableTiming) != cudaSuccess)
+            return PS_ERR_CUDA;
     }
     return PS_OK;
+}
+
+// The high-priority side stream and events of ps_pansharpen (after
+// ensure_device with a capture stream).
+struct Early {
+    cudaStream_t s;
+    cudaEvent_t fork, join;
+};
+Early device_early() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    const DevState &d = g_dev[dev];
+    return Early{d.early, d.early_fork, d.early_join};
 }
 
 // Branch streams and events of the current device (after ensure_device with
@@ -636,7 +667,15 @@ struct SolveCall {
     float *hrms, *z0;
     int N, H, W, c, R;
     ps_hrms_params p;
+    int early;  // 1: solve_early has run (PAN statistics, warm start)
 };
+
+// The network's forward pass with `reserve` SMs left out of its persistent
+// convolution grids (so that latency-bound work on another stream finds
+// whole SMs free); defined with the network's other entry points.
+ps_status cnn_forward_reserve(const float *d_params, const float *d_up, const float *d_pan,
+                              size_t pan_stride, int B, int H, int W, float *d_z, void *d_ws,
+                              size_t ws_bytes, int reserve, void *stream);
 
 // Scratch of an alternative prior, after the base layout (and after the
 // network's workspace when that is used): four N x H x W images, the
@@ -718,6 +757,7 @@ ps_status make_solve_call(const float *d_lrms, const float *d_pan, const float *
         if (ws_bytes < sc->prior_off + prior_bytes(N, H, W)) return PS_ERR_WORKSPACE;
     }
     sc->ws_bytes = ws_bytes;
+    sc->early = 0;
     sc->lrms = d_lrms;
     sc->pan = d_pan;
     sc->u = d_kernel;
@@ -731,6 +771,30 @@ ps_status make_solve_call(const float *d_lrms, const float *d_pan, const float *
     sc->R = R;
     sc->p = *p;
     return PS_OK;
+}
+
+// The steps of the solve that do not read the blur kernel: the PAN window
+// statistics of the LLP prior and the warm start (bicubic, and the network on
+// it). ps_pansharpen runs them while the kernel is estimated on another
+// stream, leaving `reserve` SMs out of the network's persistent grids.
+ps_status solve_early(const SolveCall &sc, cudaStream_t st, int reserve) {
+    const Ws &ws = sc.ws;
+    const ps_hrms_params *p = &sc.p;
+    const int N = sc.N, H = sc.H, W = sc.W, c = sc.c;
+    float *x = sc.z0 ? sc.z0 : ws.at<float>(ws.L.xbuf);
+    if (p->prior == PS_PRIOR_LLP)
+        launch_pan_stats(sc.pan, H, W, p->r, p->eps, nullptr, nullptr, nullptr,
+                         ws.at<float4>(ws.L.st4), st);
+    if (!sc.z_init && p->warm >= 1) {
+        launch_bicubic_up(sc.lrms, N, H / c, W / c, c, x, st);
+        if (p->warm == 2) {
+            ps_status s = cnn_forward_reserve(p->cnn_params, x, sc.pan, 0, N, H, W, x,
+                                              ws.base + ws.L.cnn, sc.ws_bytes - ws.L.cnn,
+                                              reserve, st);
+            if (s != PS_OK) return s;
+        }
+    }
+    return last_launch();
 }
 
 ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
@@ -749,7 +813,8 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
     PriorOps po;
     memset(&po, 0, sizeof(po));
     if (p->prior == PS_PRIOR_LLP) {
-        launch_pan_stats(sc.pan, H, W, p->r, p->eps, nullptr, nullptr, nullptr, st4, st);
+        if (!sc.early) launch_pan_stats(sc.pan, H, W, p->r, p->eps, nullptr, nullptr, nullptr,
+                                        st4, st);
     } else {
         po = prior_ops(ws, sc.prior_off, p->prior, N, H, W, R, p->r);
         launch_prior_filters(d_kernel, R, p->prior, const_cast<float *>(po.filt[0]),
@@ -789,7 +854,7 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
         sd = s_buf;
     }
     launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
-    if (!d_z_init && p->warm >= 1) {
+    if (!d_z_init && p->warm >= 1 && !sc.early) {
         // bicubic start point, written where the iterate lives
         launch_bicubic_up(d_lrms, N, H / c, W / c, c, x, st);
         if (p->warm == 2) {
@@ -799,6 +864,8 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
                                     ws.base + ws.L.cnn, sc.ws_bytes - ws.L.cnn, st)) != PS_OK)
                 return s;
         }
+    }
+    if (!d_z_init && p->warm >= 1) {
         d_z_init = x;
     }
     if (d_z_init && p->prior != PS_PRIOR_LLP) {
@@ -982,6 +1049,43 @@ ps_status build_batch_graph(const ps_scene *scenes, int count, const ps_kernel_p
     return s;
 }
 
+// Algorithm 2 on a prepared call: prelude, the CG loop (graph or host
+// launched), the guided filter and Z step; per-band results into h_info.
+ps_status run_solve(const SolveCall &sc, cudaStream_t st, ps_band_info *h_info) {
+    ps_status s;
+    const ps_hrms_params *p = &sc.p;
+    cudaStream_t capture = nullptr;
+    if ((s = ensure_device(&capture)) != PS_OK) return s;
+    CgLoopArgs a;
+    if ((s = solve_prelude(sc, st, &a)) != PS_OK) return s;
+    if (p->host_loop) {
+        // same kernels, launched by the host; the stop flag is read every 8
+        // iterations, and the loop is bounded by max_iter whatever it says
+        int stop = 0;
+        for (int it = 0; it < p->max_iter + 2 && !stop; it += 2) {
+            enqueue_iteration(a, a.pA, a.pB, 0, 0, st);
+            enqueue_iteration(a, a.pB, a.pA, 0, 0, st);
+            if ((it & 7) == 6 || it + 2 >= p->max_iter + 2) {
+                if (cudaMemcpyAsync(&stop, &a.g->stop, sizeof(int), cudaMemcpyDeviceToHost,
+                                    st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess)
+                    return PS_ERR_CUDA;
+            }
+        }
+        if ((s = last_launch()) != PS_OK) return s;
+    } else {
+        cudaGraphExec_t exec;
+        if ((s = get_cg_graph(a, capture, &exec)) != PS_OK) return s;
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) return PS_ERR_CUDA;
+    }
+    if ((s = solve_epilogue(sc, a, st)) != PS_OK) return s;
+    if (h_info) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ERR_CUDA;
+        if ((s = read_band_info(a.bands, sc.N, h_info)) != PS_OK) return s;
+    }
+    return PS_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1116,37 +1220,7 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_
     if ((s = make_solve_call(d_lrms, d_pan, d_kernel, N, H, W, ratio, R, p, d_z_init, d_hrms,
                              d_z0, d_ws, ws_bytes, &sc)) != PS_OK)
         return s;
-    cudaStream_t capture = nullptr;
-    if ((s = ensure_device(&capture)) != PS_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    CgLoopArgs a;
-    if ((s = solve_prelude(sc, st, &a)) != PS_OK) return s;
-    if (p->host_loop) {
-        // same kernels, launched by the host; the stop flag is read every 8
-        // iterations, and the loop is bounded by max_iter whatever it says
-        int stop = 0;
-        for (int it = 0; it < p->max_iter + 2 && !stop; it += 2) {
-            enqueue_iteration(a, a.pA, a.pB, 0, 0, st);
-            enqueue_iteration(a, a.pB, a.pA, 0, 0, st);
-            if ((it & 7) == 6 || it + 2 >= p->max_iter + 2) {
-                if (cudaMemcpyAsync(&stop, &a.g->stop, sizeof(int), cudaMemcpyDeviceToHost,
-                                    st) != cudaSuccess ||
-                    cudaStreamSynchronize(st) != cudaSuccess)
-                    return PS_ERR_CUDA;
-            }
-        }
-        if ((s = last_launch()) != PS_OK) return s;
-    } else {
-        cudaGraphExec_t exec;
-        if ((s = get_cg_graph(a, capture, &exec)) != PS_OK) return s;
-        if (cudaGraphLaunch(exec, st) != cudaSuccess) return PS_ERR_CUDA;
-    }
-    if ((s = solve_epilogue(sc, a, st)) != PS_OK) return s;
-    if (h_info) {
-        if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ERR_CUDA;
-        if ((s = read_band_info(a.bands, N, h_info)) != PS_OK) return s;
-    }
-    return PS_OK;
+    return run_solve(sc, (cudaStream_t)stream, h_info);
 }
 
 ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float *d_lrms,
@@ -1345,11 +1419,33 @@ ps_status ps_pansharpen(const float *d_lrms, const float *d_pan, int N, int H, i
     Ws ws;
     if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
     float *kern = d_kernel_out ? d_kernel_out : ws.at<float>(ws.L.kern);
-    if ((s = ps_estimate_kernel(d_lrms, d_pan, N, H, W, ratio, R, kp, nullptr, kern, nullptr,
-                                h_kinfo, d_ws, ws_bytes, stream)) != PS_OK)
+    SolveCall sc;
+    if ((s = make_solve_call(d_lrms, d_pan, kern, N, H, W, ratio, R, hp, nullptr, d_hrms, nullptr,
+                             d_ws, ws_bytes, &sc)) != PS_OK)
         return s;
-    return ps_solve_hrms(d_lrms, d_pan, kern, N, H, W, ratio, R, hp, nullptr, d_hrms, nullptr,
-                         h_binfo, d_ws, ws_bytes, stream);
+    if (!d_lrms || !d_pan) return PS_ERR_INVALID_ARG;
+    cudaStream_t capture = nullptr;
+    if ((s = ensure_device(&capture)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    // The kernel estimate, mostly latency-bound kernels on a few SMs, runs
+    // on a high-priority side stream while the solve's kernel-independent
+    // steps (PAN statistics, warm start) run on the caller's stream. They
+    // touch disjoint parts of the workspace; the solve proper waits for both.
+    // The early steps are queued first, so that a kernel estimate that
+    // synchronises for h_kinfo still overlaps them.
+    const Early e = device_early();
+    if (cudaEventRecord(e.fork, st) != cudaSuccess ||
+        cudaStreamWaitEvent(e.s, e.fork, 0) != cudaSuccess)
+        return PS_ERR_CUDA;
+    if ((s = solve_early(sc, st, kEarlyReserveSms)) != PS_OK) return s;
+    s = ps_estimate_kernel(d_lrms, d_pan, N, H, W, ratio, R, kp, nullptr, kern, nullptr, h_kinfo,
+                           d_ws, ws_bytes, e.s);
+    if (cudaEventRecord(e.join, e.s) != cudaSuccess ||
+        cudaStreamWaitEvent(st, e.join, 0) != cudaSuccess)
+        return PS_ERR_CUDA;
+    if (s != PS_OK) return s;
+    sc.early = 1;
+    return run_solve(sc, st, h_binfo);
 }
 
 size_t ps_batch_workspace_size(const ps_scene *scenes, int count, const ps_hrms_params *hp) {
@@ -1732,11 +1828,23 @@ size_t ps_cnn_workspace_size(int B, int H, int W, int training) {
 ps_status ps_cnn_forward(const float *d_params, const float *d_up, const float *d_pan,
                          size_t pan_stride, int B, int H, int W, float *d_z, void *d_ws,
                          size_t ws_bytes, void *stream) {
+    return cnn_forward_reserve(d_params, d_up, d_pan, pan_stride, B, H, W, d_z, d_ws, ws_bytes,
+                               0, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+ps_status cnn_forward_reserve(const float *d_params, const float *d_up, const float *d_pan,
+                              size_t pan_stride, int B, int H, int W, float *d_z, void *d_ws,
+                              size_t ws_bytes, int reserve, void *stream) {
     ps_status s;
     if ((s = cnn_check_inputs(d_params, d_up, d_pan, B, H, W)) != PS_OK) return s;
     if (!d_z) return PS_ERR_INVALID_ARG;
     CnnCall c;
     if ((s = cnn_bind(d_ws, ws_bytes, B, H, W, 0, &c)) != PS_OK) return s;
+    if (reserve > 0 && c.sms > 2 * reserve) c.sms -= reserve;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(c.at<int>(c.L.err), 0, sizeof(int), st) != cudaSuccess) return PS_ERR_CUDA;
     for (int l = 1; l <= 4; ++l)
@@ -1751,6 +1859,10 @@ ps_status ps_cnn_forward(const float *d_params, const float *d_up, const float *
     cnn_conv(c, Bf, nullptr, 4, 0, nullptr, d_params, B, H, W, st, CONV_LAST, d_up, d_z);
     return last_launch();
 }
+
+}  // namespace
+
+extern "C" {
 
 ps_status ps_cnn_loss_grad(const float *d_params, const float *d_up, const float *d_pan,
                            size_t pan_stride, const float *d_target, int B, int H, int W,
