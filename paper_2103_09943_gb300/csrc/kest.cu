@@ -360,37 +360,59 @@ __global__ void add_diag_kernel(double *A, int n, float mu3) {
     if (i < n) A[(size_t)i * n + i] += (double)mu3;
 }
 
-// Factor the 32 x 32 diagonal tile of panel k0 in place: one warp, lane i
-// holding row i in registers. Right-looking: per column k the pivot is
-// broadcast from lane k, the rows below scale their entry k, and entry (i, j)
-// takes -= l_ik l_jk with l_jk shuffled from lane j.
-__global__ void __launch_bounds__(32) chol_diag_kernel(double *A, int nt, int k0) {
-    const int lane = threadIdx.x;
+// Factor the 32 x 32 diagonal tile of panel k0 in place. Four warps, lane i
+// of each holding row i; warp w holds the columns j = w (mod 4) in
+// registers, so that the FP64 work of the rank-1 updates (the pipe is 1/64
+// of the FP32 rate on this part) spreads over four schedulers. Right-looking:
+// per column k the owning warp takes the pivot from lane k,
+// l_kk = d_kk rsqrt(d_kk), scales the rows below by rsqrt(d_kk) and
+// publishes the column in shared memory; then every warp updates its own
+// columns j > k by -= l_ik l_jk.
+constexpr int kDiagWarps = 4;
+
+__global__ void __launch_bounds__(32 * kDiagWarps) chol_diag_kernel(double *A, int nt, int k0) {
+    constexpr int CPW = CB / kDiagWarps;
+    __shared__ double col[CB];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int kb = min(CB, nt - k0);
-    double x[CB];
+    double x[CPW];
     const double *row = A + (size_t)(k0 + lane) * nt + k0;
 #pragma unroll
-    for (int j = 0; j < CB; ++j)
-        x[j] = (lane < kb && j < kb) ? ((j <= lane) ? row[j] : 0.0) : (lane == j ? 1.0 : 0.0);
+    for (int m = 0; m < CPW; ++m) {
+        const int j = w + kDiagWarps * m;
+        x[m] = (lane < kb && j < kb) ? ((j <= lane) ? row[j] : 0.0) : (lane == j ? 1.0 : 0.0);
+    }
 #pragma unroll
     for (int k = 0; k < CB; ++k) {
-        const double dkk = __shfl_sync(0xffffffffu, x[k], k);
-        const double lkk = sqrt(dkk > 0.0 ? dkk : 1e-300);
-        const double inv = 1.0 / lkk;
-        if (lane == k) x[k] = lkk;
-        else if (lane > k) x[k] *= inv;
-        const double lik = x[k];
-#pragma unroll
-        for (int j = k + 1; j < CB; ++j) {
-            const double ljk = __shfl_sync(0xffffffffu, lik, j);
-            if (lane >= j) x[j] -= lik * ljk;
+        const int mk = k / kDiagWarps;
+        if (w == k % kDiagWarps) {
+            const double dkk = __shfl_sync(0xffffffffu, x[mk], k);
+            const double rs = rsqrt(dkk > 0.0 ? dkk : 1e-300);
+            double v = x[mk];
+            if (lane == k) v = dkk * rs;
+            else if (lane > k) v *= rs;
+            x[mk] = v;
+            col[lane] = v;
         }
+        __syncthreads();
+        const double lik = col[lane];
+#pragma unroll
+        for (int m = 0; m < CPW; ++m) {
+            const int j = w + kDiagWarps * m;
+            if (j > k) {
+                const double ljk = col[j];
+                if (lane >= j) x[m] -= lik * ljk;
+            }
+        }
+        __syncthreads();
     }
     if (lane < kb) {
         double *out = A + (size_t)(k0 + lane) * nt + k0;
 #pragma unroll
-        for (int j = 0; j < CB; ++j)
-            if (j < kb && j <= lane) out[j] = x[j];
+        for (int m = 0; m < CPW; ++m) {
+            const int j = w + kDiagWarps * m;
+            if (j < kb && j <= lane) out[j] = x[m];
+        }
     }
 }
 
@@ -459,7 +481,7 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double *A, int nt, int
 void launch_cholesky(double *A, int n, float mu3, cudaStream_t st) {
     add_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(A, n, mu3);
     for (int k0 = 0; k0 < n; k0 += CB) {
-        chol_diag_kernel<<<1, 32, 0, st>>>(A, n, k0);
+        chol_diag_kernel<<<1, 32 * kDiagWarps, 0, st>>>(A, n, k0);
         const int rem = n - (k0 + CB);
         if (rem > 0) {
             chol_panel_kernel<<<(rem + 31) / 32, 32, 0, st>>>(A, n, k0);
