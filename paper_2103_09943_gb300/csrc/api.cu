@@ -178,6 +178,9 @@ struct DevState {
     // ps_pansharpen's high-priority side stream (the kernel estimate)
     cudaStream_t early = nullptr;
     cudaEvent_t early_fork = nullptr, early_join = nullptr;
+    // the kernel estimate's second branch (omega, E^T f, the z_f solve)
+    cudaStream_t kside = nullptr;
+    cudaEvent_t k_fork = nullptr, k_chol = nullptr, k_zf = nullptr;
 };
 std::mutex g_mu;
 std::vector<DevState> g_dev;
@@ -218,11 +221,19 @@ ps_status ensure_device(cudaStream_t *capture, int *num_sms = nullptr) {
         }
         if (!d.fork && cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming) != cudaSuccess)
             return PS_ERR_CUDA;
-        int lo = 0, hi = 0;
-        if (!d.early && (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
-                         cudaStreamCreateWithPriority(&d.early, cudaStreamNonBlocking, hi) !=
-                             cudaSuccess))
-            return PS_ERR_CUDA;
+        if (!d.early || !d.kside) {
+            int lo = 0, hi = 0;
+            if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return PS_ERR_CUDA;
+            if (!d.early &&
+                cudaStreamCreateWithPriority(&d.early, cudaStreamNonBlocking, hi) != cudaSuccess)
+                return PS_ERR_CUDA;
+            if (!d.kside &&
+                cudaStreamCreateWithPriority(&d.kside, cudaStreamNonBlocking, hi) != cudaSuccess)
+                return PS_ERR_CUDA;
+        }
+        for (cudaEvent_t *ev : {&d.k_fork, &d.k_chol, &d.k_zf})
+            if (!*ev && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess)
+                return PS_ERR_CUDA;
         if (!d.early_fork &&
             cudaEventCreateWithFlags(&d.early_fork, cudaEventDisableTiming) != cudaSuccess)
             return PS_ERR_CUDA;
@@ -245,6 +256,20 @@ Early device_early() {
     std::lock_guard<std::mutex> lk(g_mu);
     const DevState &d = g_dev[dev];
     return Early{d.early, d.early_fork, d.early_join};
+}
+
+// The kernel estimate's second branch: its stream and events (after
+// ensure_device with a capture stream).
+struct KSide {
+    cudaStream_t s;
+    cudaEvent_t fork, chol, zf;
+};
+KSide device_kside() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    const DevState &d = g_dev[dev];
+    return KSide{d.kside, d.k_fork, d.k_chol, d.k_zf};
 }
 
 // Branch streams and events of the current device (after ensure_device with
@@ -1166,32 +1191,46 @@ ps_status ps_estimate_kernel(const float *d_lrms, const float *d_pan, int N, int
     if (!d_lrms || !d_pan || !d_kernel) return PS_ERR_INVALID_ARG;
     Ws ws;
     if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
-    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    cudaStream_t capture = nullptr;
+    if ((s = ensure_device(&capture)) != PS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int c = ratio, h = H / c, w = W / c, hw = h * w;
     const int nt = (2 * R + 1) * (2 * R + 1);
     float *omega = d_omega_out ? d_omega_out : ws.at<float>(ws.L.omega);
+    double *ete = ws.at<double>(ws.L.ete);
+    // Two branches, on disjoint parts of the workspace: E^T E and its
+    // factor, then Q = mu3 (E^T E + mu3 I)^-1, on `st`; omega, f and E^T f,
+    // then z_f (once the factor exists), on the side stream. ADMM waits for
+    // both.
+    const KSide k2 = device_kside();
+    if (cudaEventRecord(k2.fork, st) != cudaSuccess ||
+        cudaStreamWaitEvent(k2.s, k2.fork, 0) != cudaSuccess)
+        return PS_ERR_CUDA;
     if (d_omega_in) {
         if (omega != d_omega_in &&
             cudaMemcpyAsync(omega, d_omega_in, N * sizeof(float), cudaMemcpyDeviceToDevice,
-                            st) != cudaSuccess)
+                            k2.s) != cudaSuccess)
             return PS_ERR_CUDA;
     } else {
         float *Aw = ws.at<float>(ws.L.v);
-        launch_box_lr(d_lrms, N, h, w, p->l, Aw, st);
-        launch_box_hr_dec(d_pan, H, W, c, c * p->l, ws.at<float>(ws.L.bvec), st);
-        launch_omega_normal(Aw, ws.at<float>(ws.L.bvec), N, hw, ws.at<double>(ws.L.G), st);
-        launch_omega_solve(ws.at<double>(ws.L.G), N, p->lambda_omega, omega, st);
+        launch_box_lr(d_lrms, N, h, w, p->l, Aw, k2.s);
+        launch_box_hr_dec(d_pan, H, W, c, c * p->l, ws.at<float>(ws.L.bvec), k2.s);
+        launch_omega_normal(Aw, ws.at<float>(ws.L.bvec), N, hw, ws.at<double>(ws.L.G), k2.s);
+        launch_omega_solve(ws.at<double>(ws.L.G), N, p->lambda_omega, omega, k2.s);
     }
     float *f = ws.at<float>(ws.L.f);
-    launch_combine_f(d_lrms, omega, N, hw, f, st);
-    double *ete = ws.at<double>(ws.L.ete);
+    launch_combine_f(d_lrms, omega, N, hw, f, k2.s);
+    launch_etf(d_pan, H, W, c, R, f, ws.at<double>(ws.L.etf), k2.s);
     launch_ete_lags(d_pan, H, W, c, R, ws.at<double>(ws.L.lags), st);
     launch_ete_assemble(ws.at<double>(ws.L.lags), c, R, ete, st);
-    launch_etf(d_pan, H, W, c, R, f, ws.at<double>(ws.L.etf), st);
     launch_cholesky(ete, nt, p->mu3, st);
-    launch_chol_solve(ete, ws.at<double>(ws.L.etf), nt, ws.at<double>(ws.L.zf), st);
+    if (cudaEventRecord(k2.chol, st) != cudaSuccess ||
+        cudaStreamWaitEvent(k2.s, k2.chol, 0) != cudaSuccess)
+        return PS_ERR_CUDA;
+    launch_chol_solve(ete, ws.at<double>(ws.L.etf), nt, ws.at<double>(ws.L.zf), k2.s);
+    if (cudaEventRecord(k2.zf, k2.s) != cudaSuccess) return PS_ERR_CUDA;
     launch_chol_inverse(ete, nt, p->mu3, ws.at<float>(ws.L.Q), nullptr, st);
+    if (cudaStreamWaitEvent(st, k2.zf, 0) != cudaSuccess) return PS_ERR_CUDA;
     int *ki = ws.at<int>(ws.L.kinfo);
     launch_admm(ws.at<float>(ws.L.Q), ws.at<double>(ws.L.zf), R, *p, d_kernel, ki, ki + 1,
                 reinterpret_cast<double *>(ki + 2), st);
