@@ -177,7 +177,7 @@ struct DevState {
     cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
     // ps_pansharpen's high-priority side stream (the kernel estimate)
     cudaStream_t early = nullptr;
-    cudaEvent_t early_fork = nullptr, early_join = nullptr;
+    cudaEvent_t early_fork = nullptr, early_join = nullptr, early_lags = nullptr;
     // the kernel estimate's second branch (omega, E^T f, the z_f solve)
     cudaStream_t kside = nullptr;
     cudaEvent_t k_fork = nullptr, k_chol = nullptr, k_zf = nullptr;
@@ -240,6 +240,9 @@ ps_status ensure_device(cudaStream_t *capture, int *num_sms = nullptr) {
         if (!d.early_join &&
             cudaEventCreateWithFlags(&d.early_join, cudaEventDisableTiming) != cudaSuccess)
             return PS_ERR_CUDA;
+        if (!d.early_lags &&
+            cudaEventCreateWithFlags(&d.early_lags, cudaEventDisableTiming) != cudaSuccess)
+            return PS_ERR_CUDA;
     }
     return PS_OK;
 }
@@ -248,14 +251,14 @@ ps_status ensure_device(cudaStream_t *capture, int *num_sms = nullptr) {
 // ensure_device with a capture stream).
 struct Early {
     cudaStream_t s;
-    cudaEvent_t fork, join;
+    cudaEvent_t fork, join, lags;
 };
 Early device_early() {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_mu);
     const DevState &d = g_dev[dev];
-    return Early{d.early, d.early_fork, d.early_join};
+    return Early{d.early, d.early_fork, d.early_join, d.early_lags};
 }
 
 // The kernel estimate's second branch: its stream and events (after
@@ -701,6 +704,12 @@ struct SolveCall {
 ps_status cnn_forward_reserve(const float *d_params, const float *d_up, const float *d_pan,
                               size_t pan_stride, int B, int H, int W, float *d_z, void *d_ws,
                               size_t ws_bytes, int reserve, void *stream);
+
+ps_status estimate_kernel_impl(const float *d_lrms, const float *d_pan, int N, int H, int W,
+                               int ratio, int R, const ps_kernel_params *p,
+                               const float *d_omega_in, float *d_kernel, float *d_omega_out,
+                               ps_kernel_info *h_info, void *d_ws, size_t ws_bytes,
+                               cudaStream_t st, cudaEvent_t lags_done);
 
 // Scratch of an alternative prior, after the base layout (and after the
 // network's workspace when that is used): four N x H x W images, the
@@ -1185,6 +1194,39 @@ ps_status ps_estimate_kernel(const float *d_lrms, const float *d_pan, int N, int
                              const float *d_omega_in, float *d_kernel, float *d_omega_out,
                              ps_kernel_info *h_info, void *d_ws, size_t ws_bytes,
                              void *stream) {
+    return estimate_kernel_impl(d_lrms, d_pan, N, H, W, ratio, R, p, d_omega_in, d_kernel,
+                                d_omega_out, h_info, d_ws, ws_bytes, (cudaStream_t)stream,
+                                nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The ADMM's iteration count, status and last relative change, after the
+// work queued on `st` (synchronises it).
+ps_status read_kernel_info(const Ws &ws, cudaStream_t st, ps_kernel_info *h_info) {
+    const int *ki = ws.at<int>(ws.L.kinfo);
+    int hi[2];
+    double ch = 0.0;
+    if (cudaMemcpyAsync(hi, ki, sizeof(hi), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&ch, ki + 2, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return PS_ERR_CUDA;
+    h_info->iters = hi[0];
+    h_info->status = hi[1];
+    h_info->last_change = ch;
+    return PS_OK;
+}
+
+// Algorithm 1. `lags_done`, when given, is recorded on `st` once the lag
+// correlations behind E^T E (the estimate's one kernel that fills the GPU)
+// are queued.
+ps_status estimate_kernel_impl(const float *d_lrms, const float *d_pan, int N, int H, int W,
+                               int ratio, int R, const ps_kernel_params *p,
+                               const float *d_omega_in, float *d_kernel, float *d_omega_out,
+                               ps_kernel_info *h_info, void *d_ws, size_t ws_bytes,
+                               cudaStream_t st, cudaEvent_t lags_done) {
     ps_status s;
     if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
     if ((s = check_kernel_params(p)) != PS_OK) return s;
@@ -1193,7 +1235,6 @@ ps_status ps_estimate_kernel(const float *d_lrms, const float *d_pan, int N, int
     if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
     cudaStream_t capture = nullptr;
     if ((s = ensure_device(&capture)) != PS_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
     const int c = ratio, h = H / c, w = W / c, hw = h * w;
     const int nt = (2 * R + 1) * (2 * R + 1);
     float *omega = d_omega_out ? d_omega_out : ws.at<float>(ws.L.omega);
@@ -1222,6 +1263,7 @@ ps_status ps_estimate_kernel(const float *d_lrms, const float *d_pan, int N, int
     launch_combine_f(d_lrms, omega, N, hw, f, k2.s);
     launch_etf(d_pan, H, W, c, R, f, ws.at<double>(ws.L.etf), k2.s);
     launch_ete_lags(d_pan, H, W, c, R, ws.at<double>(ws.L.lags), st);
+    if (lags_done && cudaEventRecord(lags_done, st) != cudaSuccess) return PS_ERR_CUDA;
     launch_ete_assemble(ws.at<double>(ws.L.lags), c, R, ete, st);
     launch_cholesky(ete, nt, p->mu3, st);
     if (cudaEventRecord(k2.chol, st) != cudaSuccess ||
@@ -1235,20 +1277,13 @@ ps_status ps_estimate_kernel(const float *d_lrms, const float *d_pan, int N, int
     launch_admm(ws.at<float>(ws.L.Q), ws.at<double>(ws.L.zf), R, *p, d_kernel, ki, ki + 1,
                 reinterpret_cast<double *>(ki + 2), st);
     if ((s = last_launch()) != PS_OK) return s;
-    if (h_info) {
-        int hi[2];
-        double ch = 0.0;
-        if (cudaMemcpyAsync(hi, ki, sizeof(hi), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaMemcpyAsync(&ch, ki + 2, sizeof(double), cudaMemcpyDeviceToHost, st) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return PS_ERR_CUDA;
-        h_info->iters = hi[0];
-        h_info->status = hi[1];
-        h_info->last_change = ch;
-    }
+    if (h_info) return read_kernel_info(ws, st, h_info);
     return PS_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan, const float *d_kernel, int N,
                         int H, int W, int ratio, int R, const ps_hrms_params *p,
@@ -1470,19 +1505,23 @@ ps_status ps_pansharpen(const float *d_lrms, const float *d_pan, int N, int H, i
     // on a high-priority side stream while the solve's kernel-independent
     // steps (PAN statistics, warm start) run on the caller's stream. They
     // touch disjoint parts of the workspace; the solve proper waits for both.
-    // The early steps are queued first, so that a kernel estimate that
-    // synchronises for h_kinfo still overlaps them.
+    // The early steps start once the estimate's lag correlations (its one
+    // kernel that fills the GPU) are done, so that the network's persistent
+    // grids meet only the estimate's latency-bound kernels. Both are queued
+    // before h_kinfo is read back.
     const Early e = device_early();
     if (cudaEventRecord(e.fork, st) != cudaSuccess ||
         cudaStreamWaitEvent(e.s, e.fork, 0) != cudaSuccess)
         return PS_ERR_CUDA;
+    s = estimate_kernel_impl(d_lrms, d_pan, N, H, W, ratio, R, kp, nullptr, kern, nullptr,
+                             nullptr, d_ws, ws_bytes, e.s, e.lags);
+    if (s != PS_OK) return s;
+    if (cudaStreamWaitEvent(st, e.lags, 0) != cudaSuccess) return PS_ERR_CUDA;
     if ((s = solve_early(sc, st, kEarlyReserveSms)) != PS_OK) return s;
-    s = ps_estimate_kernel(d_lrms, d_pan, N, H, W, ratio, R, kp, nullptr, kern, nullptr, h_kinfo,
-                           d_ws, ws_bytes, e.s);
     if (cudaEventRecord(e.join, e.s) != cudaSuccess ||
         cudaStreamWaitEvent(st, e.join, 0) != cudaSuccess)
         return PS_ERR_CUDA;
-    if (s != PS_OK) return s;
+    if (h_kinfo && (s = read_kernel_info(ws, e.s, h_kinfo)) != PS_OK) return s;
     sc.early = 1;
     return run_solve(sc, st, h_binfo);
 }
@@ -2097,18 +2136,7 @@ ps_status ps_op_admm(const double *d_EtE, const double *d_Etf, int R, const ps_k
     launch_admm(ws.at<float>(ws.L.Q), ws.at<double>(ws.L.zf), R, *p, d_kernel, ki, ki + 1,
                 reinterpret_cast<double *>(ki + 2), st);
     if ((s = last_launch()) != PS_OK) return s;
-    if (h_info) {
-        int hi[2];
-        double ch = 0.0;
-        if (cudaMemcpyAsync(hi, ki, sizeof(hi), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaMemcpyAsync(&ch, ki + 2, sizeof(double), cudaMemcpyDeviceToHost, st) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return PS_ERR_CUDA;
-        h_info->iters = hi[0];
-        h_info->status = hi[1];
-        h_info->last_change = ch;
-    }
+    if (h_info) return read_kernel_info(ws, st, h_info);
     return PS_OK;
 }
 
