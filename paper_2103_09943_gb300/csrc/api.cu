@@ -861,7 +861,21 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
                                st);
         }
     }
-    if ((s = prepare_spectrum(ws, d_kernel, H, W, R, st)) != PS_OK) return s;
+    // With the LLP prior, the kernel spectrum and b = B^T D^T X (disjoint
+    // buffers) go on a side stream while A z_init is formed here; cg_init
+    // waits for both.
+    const bool side = p->prior == PS_PRIOR_LLP;
+    const KSide k2 = device_kside();
+    if (side) {
+        if (cudaEventRecord(k2.fork, st) != cudaSuccess ||
+            cudaStreamWaitEvent(k2.s, k2.fork, 0) != cudaSuccess)
+            return PS_ERR_CUDA;
+        if ((s = prepare_spectrum(ws, d_kernel, H, W, R, k2.s)) != PS_OK) return s;
+        launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, k2.s);  // b = B^T D^T X
+        if (cudaEventRecord(k2.zf, k2.s) != cudaSuccess) return PS_ERR_CUDA;
+    } else if ((s = prepare_spectrum(ws, d_kernel, H, W, R, st)) != PS_OK) {
+        return s;
+    }
     if (p->prior != PS_PRIOR_LLP) {
         // the Z step's symbol sum_d |F_d^|^2
         double2 *fh = prior_fhat(ws, sc.prior_off, N, H, W);
@@ -887,7 +901,7 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
         launch_diag_head(net_out, s_buf, (size_t)N * HW, 1.0f / 64.0f, st);
         sd = s_buf;
     }
-    launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
+    if (!side) launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
     if (!d_z_init && p->warm >= 1 && !sc.early) {
         // bicubic start point, written where the iterate lives
         launch_bicubic_up(d_lrms, N, H / c, W / c, c, x, st);
@@ -928,6 +942,7 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
         la.out = ap;
         launch_llp(la, LLP_APPLY, p->r, N, st);
     }
+    if (side && cudaStreamWaitEvent(st, k2.zf, 0) != cudaSuccess) return PS_ERR_CUDA;
     launch_cg_reset(bands, g, N, (double)p->tol, p->max_iter, p->precond, p->stop_rule, st);
     launch_cg_init(rv, d_z_init ? ap : nullptr, d_z_init, x, rv, N, HW, bands, g, st);
     PrecArgs pa;
