@@ -258,22 +258,32 @@ def cg_iteration_roofline(api, X, Y, kern, cfg, hp, peak_gbs, dev):
                                                           "hbm_gbs)"}
 
 
-def launches_per_step(cfg, hp, cg_iters) -> int:
+def launches_per_step(cfg, hp, cg_iters, split=1) -> int:
     """Kernels of this library launched by one ps_pansharpen call.
-    Kernel estimate: 4 (omega) + 4 (E^T E, E^T f) + Cholesky (1 + per 32-column
-    panel: diagonal, and below it panel and trailing update) + 3 (solve,
-    inverse, ADMM). HRMS solve: PAN statistics, 3 for the kernel spectrum,
-    right-hand side, reset, init (+3 for z0 = P^{-1} r0), then the loop body of
-    two iterations (4 or 7 kernels each) per two iterations, then 8 for the
-    Z step; plus the warm start's kernels."""
+    Kernel estimate: 4 (omega) + 4 (f, E^T E lags and assembly, E^T f) +
+    Cholesky (1 + per 32-column panel: diagonal, and below it panel and
+    trailing update) + 3 (solve, inverse, ADMM). HRMS solve: PAN statistics,
+    4 for the kernel spectrum (two twiddle tables, spectrum, FP32 copy),
+    right-hand side, reset, init (+3 for z0 = P^{-1} r0), then the CG loop:
+    per branch of bands (split on band pairs), bodies of four iterations of
+    4 (plain) or 7 (preconditioned) kernels until its bands stop; then the Z
+    step (4 in FP32: fused right-hand side, 3 preconditioner passes; 8 in
+    FP64). Warm start: bicubic, the network (4 weight packs, first layer,
+    4 convolutions) and A z_init (2)."""
     nt = cfg.n * cfg.n
     panels = (nt + 31) // 32
     kest = 4 + 4 + (1 + panels + 2 * (panels - 1)) + 3
     per_iter = 7 if hp.precond else 4
-    body_runs = max(1, math.ceil(max(cg_iters) / 2))
-    solve = 1 + 3 + 1 + 2 + (3 if hp.precond else 0) + 2 * per_iter * body_runs + 8
-    # warm start: bicubic, (network: 4 weight packs + 4 convolutions), A z_init (2)
-    warm = {0: 0, 1: 1 + 2, 2: 1 + 8 + 2}[hp.warm]
+    pairs = (cfg.bands + 1) // 2
+    bounds = [min(cfg.bands, 2 * ((pairs * k) // split)) for k in range(split + 1)]
+    loop = 0
+    for k in range(split):
+        its = cg_iters[bounds[k]:bounds[k + 1]]
+        if its:
+            loop += per_iter * 4 * max(1, math.ceil(max(its) / 4))
+    zstep = 4 if hp.zstep_fp32 else 8
+    solve = 1 + 4 + 1 + 2 + (3 if hp.precond else 0) + loop + zstep
+    warm = {0: 0, 1: 1 + 2, 2: 1 + 9 + 2}[hp.warm]
     return kest + solve + warm
 
 
@@ -489,7 +499,8 @@ def run_gpu(args):
     e2e_ms = reduce_max(float(np.mean(e2e)), world, dev)
 
     # launches of our kernels per step
-    n_launch = launches_per_step(cfg, hp, binfo.iters)
+    split = (tuning or {}).get("split") or (2 if cfg.bands >= 4 else 1)
+    n_launch = launches_per_step(cfg, hp, list(binfo.iters), split)
 
     peak, peak_kind = read_peaks()
     roof = cg_iteration_roofline(api, X, Y, K, cfg, hp, peak, dev)
