@@ -252,6 +252,11 @@ ps_status ps_solve_hrms(const float *d_lrms, const float *d_pan,
  * The two-stage scheme of Sec. III-C: ps_estimate_kernel, then
  * ps_solve_hrms with the estimated kernel, no outer loop.
  * d_kernel_out (n x n, may be NULL) receives the estimated kernel.
+ * The result is the same as the two calls in sequence. The solve's steps
+ * that do not read the kernel (PAN statistics, warm start) run while the
+ * kernel is estimated: the estimate goes on the library's own
+ * high-priority streams, forked from and joined back to `stream` with
+ * events, so the call stays ordered on `stream` like any other.
  */
 ps_status ps_pansharpen(const float *d_lrms, const float *d_pan, int N, int H,
                         int W, int ratio, int R,
