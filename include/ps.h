@@ -25,8 +25,10 @@
  *   its work is enqueued.
  * - Intensities are expected on the [0, 255] scale: the paper states its
  *   images on that scale (Sec. IV-C) and its parameter values assume it.
- * - No C++ exception crosses this interface. Not thread-safe for concurrent
- *   calls that share one workspace.
+ * - No C++ exception crosses this interface. Calls from several host
+ *   threads at once are not supported: besides the workspace, the library
+ *   keeps per-device side streams, events and cached CUDA graphs that its
+ *   calls share.
  */
 #ifndef PS_H
 #define PS_H
