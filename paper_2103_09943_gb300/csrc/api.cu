@@ -810,8 +810,11 @@ ps_status make_solve_call(const float *d_lrms, const float *d_pan, const float *
 // The steps of the solve that do not read the blur kernel: the PAN window
 // statistics of the LLP prior and the warm start (bicubic, and the network on
 // it). ps_pansharpen runs them while the kernel is estimated on another
-// stream, leaving `reserve` SMs out of the network's persistent grids.
-ps_status solve_early(const SolveCall &sc, cudaStream_t st, int reserve) {
+// stream, leaving `reserve` SMs out of the network's persistent grids; the
+// network waits for `before_net` (when given), the statistics and bicubic
+// do not.
+ps_status solve_early(const SolveCall &sc, cudaStream_t st, int reserve,
+                      cudaEvent_t before_net = nullptr) {
     const Ws &ws = sc.ws;
     const ps_hrms_params *p = &sc.p;
     const int N = sc.N, H = sc.H, W = sc.W, c = sc.c;
@@ -822,6 +825,8 @@ ps_status solve_early(const SolveCall &sc, cudaStream_t st, int reserve) {
     if (!sc.z_init && p->warm >= 1) {
         launch_bicubic_up(sc.lrms, N, H / c, W / c, c, x, st);
         if (p->warm == 2) {
+            if (before_net && cudaStreamWaitEvent(st, before_net, 0) != cudaSuccess)
+                return PS_ERR_CUDA;
             ps_status s = cnn_forward_reserve(p->cnn_params, x, sc.pan, 0, N, H, W, x,
                                               ws.base + ws.L.cnn, sc.ws_bytes - ws.L.cnn,
                                               reserve, st);
@@ -1520,10 +1525,11 @@ ps_status ps_pansharpen(const float *d_lrms, const float *d_pan, int N, int H, i
     // on a high-priority side stream while the solve's kernel-independent
     // steps (PAN statistics, warm start) run on the caller's stream. They
     // touch disjoint parts of the workspace; the solve proper waits for both.
-    // The early steps start once the estimate's lag correlations (its one
-    // kernel that fills the GPU) are done, so that the network's persistent
-    // grids meet only the estimate's latency-bound kernels. Both are queued
-    // before h_kinfo is read back.
+    // The network starts once the estimate's lag correlations (its one
+    // kernel that fills the GPU) are done, so that its persistent grids meet
+    // only the estimate's latency-bound kernels; the PAN statistics and the
+    // bicubic, memory-bound, run beside the lag correlations. Everything is
+    // queued before h_kinfo is read back.
     const Early e = device_early();
     if (cudaEventRecord(e.fork, st) != cudaSuccess ||
         cudaStreamWaitEvent(e.s, e.fork, 0) != cudaSuccess)
@@ -1531,8 +1537,7 @@ ps_status ps_pansharpen(const float *d_lrms, const float *d_pan, int N, int H, i
     s = estimate_kernel_impl(d_lrms, d_pan, N, H, W, ratio, R, kp, nullptr, kern, nullptr,
                              nullptr, d_ws, ws_bytes, e.s, e.lags);
     if (s != PS_OK) return s;
-    if (cudaStreamWaitEvent(st, e.lags, 0) != cudaSuccess) return PS_ERR_CUDA;
-    if ((s = solve_early(sc, st, kEarlyReserveSms)) != PS_OK) return s;
+    if ((s = solve_early(sc, st, kEarlyReserveSms, e.lags)) != PS_OK) return s;
     if (cudaEventRecord(e.join, e.s) != cudaSuccess ||
         cudaStreamWaitEvent(st, e.join, 0) != cudaSuccess)
         return PS_ERR_CUDA;
