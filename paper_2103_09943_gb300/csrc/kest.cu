@@ -233,29 +233,40 @@ __global__ void __launch_bounds__(256) ete_lag_kernel(const float *__restrict__ 
 // one-site walk.
 constexpr int LAG_SITES = 4;
 
-template <int C>
-__global__ void __launch_bounds__(256) ete_lag_sites_kernel(const float *__restrict__ Y, int H,
-                                                            int W, int R, double *lags) {
-    __shared__ double red[8];
+// The walk over the CTA's LR sites. OFF = (px + dx0) mod 4 is the same for
+// every site group of a CTA (C kx0 is a multiple of 4), so with a 16-byte
+// aligned PAN a group's row segment is NV aligned float4 loads shifted by
+// OFF: a warp's load instruction touches the same 16 cache lines for four
+// values as a scalar load does for one.
+template <int C, int OFF>
+__device__ __forceinline__ void lag_sites_walk(const float *__restrict__ Y, int H, int W, int py,
+                                               int px, int dy, int dx0, int h, int w, int gw,
+                                               bool vec, float (&s)[LAG_CHUNK],
+                                               float (&cm)[LAG_CHUNK]) {
     constexpr int SEG = LAG_CHUNK + C * (LAG_SITES - 1);
-    const int nl = 4 * R + 1;
-    const int dy = (int)blockIdx.x;
-    const int py = blockIdx.y / C, px = blockIdx.y - (blockIdx.y / C) * C;
-    const int dx0 = (int)blockIdx.z * LAG_CHUNK - 2 * R;
-    const int ndx = min(LAG_CHUNK, 2 * R - dx0 + 1);
-    const int h = H / C, w = W / C;
-    const int gw = (w + LAG_SITES - 1) / LAG_SITES;   // site groups per LR row
-    float s[LAG_CHUNK], cm[LAG_CHUNK];
-#pragma unroll
-    for (int t = 0; t < LAG_CHUNK; ++t) { s[t] = 0.f; cm[t] = 0.f; }
+    constexpr int NV = (SEG + OFF + 3) / 4;
     for (int gi = threadIdx.x; gi < h * gw; gi += 256) {
         const int ky = gi / gw, kx0 = (gi - ky * gw) * LAG_SITES;
         const int yy = C * ky + py;
         const float *arow = Y + (size_t)yy * W;
         const float *row = Y + (size_t)wrapk(yy + dy, H) * W;
         const int cx0 = C * kx0 + px + dx0;
+        const int base = cx0 - OFF;
         float seg[SEG];
-        if (cx0 >= 0 && cx0 + SEG <= W) {
+        if (vec && base >= 0 && base + 4 * NV <= W) {
+            float v[4 * NV];
+            const float4 *rv = reinterpret_cast<const float4 *>(row + base);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const float4 q = __ldg(rv + k);
+                v[4 * k] = q.x;
+                v[4 * k + 1] = q.y;
+                v[4 * k + 2] = q.z;
+                v[4 * k + 3] = q.w;
+            }
+#pragma unroll
+            for (int t = 0; t < SEG; ++t) seg[t] = v[t + OFF];
+        } else if (cx0 >= 0 && cx0 + SEG <= W) {
 #pragma unroll
             for (int t = 0; t < SEG; ++t) seg[t] = row[cx0 + t];
         } else {
@@ -274,6 +285,30 @@ __global__ void __launch_bounds__(256) ete_lag_sites_kernel(const float *__restr
             for (int t = 0; t < LAG_CHUNK; ++t) df_acc(a, seg[C * q + t], s[t], cm[t]);
         }
     }
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) ete_lag_sites_kernel(const float *__restrict__ Y, int H,
+                                                            int W, int R, int vec,
+                                                            double *lags) {
+    __shared__ double red[8];
+    const int nl = 4 * R + 1;
+    const int dy = (int)blockIdx.x;
+    const int py = blockIdx.y / C, px = blockIdx.y - (blockIdx.y / C) * C;
+    const int dx0 = (int)blockIdx.z * LAG_CHUNK - 2 * R;
+    const int ndx = min(LAG_CHUNK, 2 * R - dx0 + 1);
+    const int h = H / C, w = W / C;
+    const int gw = (w + LAG_SITES - 1) / LAG_SITES;   // site groups per LR row
+    float s[LAG_CHUNK], cm[LAG_CHUNK];
+#pragma unroll
+    for (int t = 0; t < LAG_CHUNK; ++t) { s[t] = 0.f; cm[t] = 0.f; }
+    const bool v = vec != 0;
+    switch (((px + dx0) % 4 + 4) % 4) {
+        case 0: lag_sites_walk<C, 0>(Y, H, W, py, px, dy, dx0, h, w, gw, v, s, cm); break;
+        case 1: lag_sites_walk<C, 1>(Y, H, W, py, px, dy, dx0, h, w, gw, v, s, cm); break;
+        case 2: lag_sites_walk<C, 2>(Y, H, W, py, px, dy, dx0, h, w, gw, v, s, cm); break;
+        default: lag_sites_walk<C, 3>(Y, H, W, py, px, dy, dx0, h, w, gw, v, s, cm); break;
+    }
 #pragma unroll
     for (int t = 0; t < LAG_CHUNK; ++t) {
         if (t < ndx) {
@@ -288,10 +323,11 @@ void launch_ete_lags(const float *Y, int H, int W, int c, int R, double *lags,
                      cudaStream_t st) {
     const int nl = 4 * R + 1;
     dim3 grd(2 * R + 1, c * c, (nl + LAG_CHUNK - 1) / LAG_CHUNK);
+    const int vec = ((uintptr_t)Y % 16) == 0 && W % 4 == 0;
     if (c == 4)
-        ete_lag_sites_kernel<4><<<grd, 256, 0, st>>>(Y, H, W, R, lags);
+        ete_lag_sites_kernel<4><<<grd, 256, 0, st>>>(Y, H, W, R, vec, lags);
     else if (c == 2)
-        ete_lag_sites_kernel<2><<<grd, 256, 0, st>>>(Y, H, W, R, lags);
+        ete_lag_sites_kernel<2><<<grd, 256, 0, st>>>(Y, H, W, R, vec, lags);
     else
         ete_lag_kernel<<<grd, 256, 0, st>>>(Y, H, W, c, R, lags);
 }
