@@ -127,3 +127,27 @@ def test_paper_setting_29x29_motion_blur(cuda):
     for b in range(cfg.bands):
         assert abs(binfo.iters[b] - ref["bands"][b]["iters_z0"]) <= 2, (b, binfo.iters)
         assert rel(Z[b], ref["Z"][b]) < 1e-4, b
+
+
+def test_overlapped_call_equals_the_two_stages_in_sequence(cuda):
+    # ps_pansharpen runs the kernel estimate on its own streams beside the
+    # solve's PAN statistics and warm start; the result must be that of
+    # ps_estimate_kernel followed by ps_solve_hrms on the caller's stream
+    import os
+    from paper_2103_09943_gb300.cnn import WarmStartNet
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    net = WarmStartNet.load(os.path.join(root, "paper_2103_09943_gb300", "weights",
+                                         "warm_cnn.npz"), device=cuda)
+    sc = synth.make_scene(synth.CONFIGS["c0"])
+    cfg = sc["config"]
+    X, Y = to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda)
+    hp = api.default_hrms_params(tol=1e-7, warm=2, cnn_params=net.params.data_ptr())
+    for _ in range(2):                      # the second call reuses the cached graphs
+        Z, k, ki, si = api.pansharpen(X, Y, cfg.ratio, cfg.R, hparams=hp)
+        k2, _, ki2 = api.estimate_kernel(X, Y, cfg.ratio, cfg.R)
+        Z2, _, si2 = api.solve_hrms(X, Y, k2, cfg.ratio, hp)
+        assert ki.iters == ki2.iters and ki.status == ki2.status == 0
+        assert rel(to_np(k), to_np(k2)) < 1e-6
+        for n in range(cfg.bands):
+            assert abs(si.iters[n] - si2.iters[n]) <= 1, (si.iters, si2.iters)
+        assert rel(to_np(Z), to_np(Z2)) < 1e-5
