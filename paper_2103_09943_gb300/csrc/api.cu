@@ -1517,7 +1517,6 @@ ps_status ps_pansharpen(const float *d_lrms, const float *d_pan, int N, int H, i
     if ((s = make_solve_call(d_lrms, d_pan, kern, N, H, W, ratio, R, hp, nullptr, d_hrms, nullptr,
                              d_ws, ws_bytes, &sc)) != PS_OK)
         return s;
-    if (!d_lrms || !d_pan) return PS_ERR_INVALID_ARG;
     cudaStream_t capture = nullptr;
     if ((s = ensure_device(&capture)) != PS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
