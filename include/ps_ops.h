@@ -143,11 +143,15 @@ size_t ps_op_workspace_size(int N, int H, int W, int ratio, int R);
  * (h w 4 bytes, rounded up to 256) + c^2 (4R+1)^2 8 bytes of it, with
  * h w = (H/ratio)(W/ratio); when that exceeds the array the call returns
  * PS_ERR_UNSUPPORTED before launching anything.
+ * Sizes: the limits of ps_op_kernel_normal_eq (same status codes), then the
+ * array's.
  * All calls share the one array: calls that overlap on the GPU (on different
  * streams, or from different host threads) race on it and must be serialised
- * by the caller. The first call on a device looks up the array's device
- * address, once per device, with that device current; make that first call
- * before any stream capture. */
+ * by the caller. The array has one device address per CUDA context; the
+ * first call in a context (the device's primary context, or a context the
+ * caller made current through the driver API) looks that address up and
+ * caches it under the context's ID. Make that first call before any stream
+ * capture. */
 ps_status ps_op_kernel_normal_eq_noalloc(const float *d_lrms,
                                          const float *d_pan,
                                          const float *d_omega, int N, int H,

@@ -17,6 +17,19 @@
 
 using namespace ps;
 
+// Sizes every image entry point accepts (declared in kernels.cuh; the
+// allocation-free entry point applies the same limits).
+ps_status ps::check_dims(int N, int H, int W, int c, int R) {
+    if (N < 1 || N > kMaxBands) return PS_ERR_INVALID_ARG;
+    if (c < 2 || c > kMaxRatio) return PS_ERR_INVALID_ARG;
+    if (R < 0 || R > kMaxR) return PS_ERR_INVALID_ARG;
+    if (H < 1 || W < 1 || H % c || W % c) return PS_ERR_SHAPE;
+    if (H > kMaxFFT || W > kMaxFFT) return PS_ERR_UNSUPPORTED;
+    if (2 * R + 1 > H || 2 * R + 1 > W) return PS_ERR_SHAPE;
+    if (W % 4) return PS_ERR_UNSUPPORTED;
+    return PS_OK;
+}
+
 namespace {
 
 constexpr size_t kAlign = 256;
@@ -111,17 +124,6 @@ bool is_pow23(int L) {
     while (L % 2 == 0) L /= 2;
     while (L % 3 == 0) L /= 3;
     return L == 1;
-}
-
-ps_status check_dims(int N, int H, int W, int c, int R) {
-    if (N < 1 || N > kMaxBands) return PS_ERR_INVALID_ARG;
-    if (c < 2 || c > kMaxRatio) return PS_ERR_INVALID_ARG;
-    if (R < 0 || R > kMaxR) return PS_ERR_INVALID_ARG;
-    if (H < 1 || W < 1 || H % c || W % c) return PS_ERR_SHAPE;
-    if (H > kMaxFFT || W > kMaxFFT) return PS_ERR_UNSUPPORTED;
-    if (2 * R + 1 > H || 2 * R + 1 > W) return PS_ERR_SHAPE;
-    if (W % 4) return PS_ERR_UNSUPPORTED;
-    return PS_OK;
 }
 
 ps_status check_fft_dims(int H, int W) {

@@ -8,6 +8,10 @@
 
 namespace ps {
 
+// api.cu: the band count, sizes, ratio and kernel radius every image entry
+// point accepts (PS_ERR_INVALID_ARG, PS_ERR_SHAPE or PS_ERR_UNSUPPORTED).
+ps_status check_dims(int N, int H, int W, int c, int R);
+
 enum LlpMode { LLP_APPLY = 0, LLP_ZRHS = 1, LLP_GF = 2, LLP_CGQ = 3 };
 
 struct LlpArgs {

@@ -172,6 +172,23 @@ def test_argument_errors_return_before_launch(lib):
     assert st == 1                                                  # R > 16
 
 
+def test_noalloc_shape_limits_are_its_twins(lib):
+    # The allocation-free entry point applies the workspace entry point's
+    # size limits (same status codes) before its own scratch limit.
+    fake = ctypes.c_void_p(0x1000)
+    cases = [((4, 96, 98, 2, 4), 8),      # W % 4: the lag kernels' float4 rows
+             ((4, 98, 96, 4, 4), 2),      # H % ratio
+             ((4, 16384, 96, 4, 4), 8),   # beyond the largest image side
+             ((4, 96, 96, 4, 17), 1),     # R > 16
+             ((0, 96, 96, 4, 4), 1)]      # no bands
+    for (N, H, W, c, R), want in cases:
+        twin = lib.ps_op_kernel_normal_eq(fake, fake, fake, N, H, W, c, R, fake, fake, fake,
+                                          1 << 30, None)
+        st = lib.ps_op_kernel_normal_eq_noalloc(fake, fake, fake, N, H, W, c, R, fake, fake,
+                                                None)
+        assert st == twin == want, ((N, H, W, c, R), st, twin)
+
+
 def test_batched_argument_errors_return_before_launch(lib):
     from paper_2103_09943_gb300._lib import HrmsParams, KernelParams, Scene
     hp = HrmsParams()

@@ -36,6 +36,27 @@ def test_noalloc_matches_workspace_entry_point(cuda, N, H, c, R):
         assert rel(to_np(f), to_np(ref_f)) < 1e-12
 
 
+def test_noalloc_matches_the_oracle_on_a_non_square_grid(cuda):
+    # E^T E and E^T f by their plain definition (the FP64 oracle), on a
+    # 96 x 160 PAN at ratio 2: rows and columns of the LR grid differ, so a
+    # transposed index would show.
+    import oracle
+    from paper_2103_09943_gb300 import ops
+    N, H, W, c, R = 3, 96, 160, 2, 5
+    rng = np.random.default_rng(7)
+    Y = (rng.random((H, W)) * 255).astype(np.float32)
+    X = (rng.random((N, H // c, W // c)) * 255).astype(np.float32)
+    om = rng.dirichlet(np.ones(N)).astype(np.float32)
+    f = np.tensordot(om.astype(np.float64), X.astype(np.float64), axes=1)
+    ref_e, ref_f = oracle.kernel_normal_eq(Y, f, c, R)
+    gx, gy, go = to_dev(X, cuda), to_dev(Y, cuda), to_dev(om, cuda)
+    for _ in range(2):
+        e, g = ops.kernel_normal_eq_noalloc(gx, gy, go, c, R)
+        # double-float accumulation of exact FP32 products; f formed in FP32
+        assert rel(to_np(e), ref_e) < 1e-12
+        assert rel(to_np(g), ref_f) < 1e-6
+
+
 def test_noalloc_rejects_sizes_beyond_its_array(cuda):
     from paper_2103_09943_gb300 import _lib
     lib = _lib.load()
