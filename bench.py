@@ -1,13 +1,19 @@
 """Benchmark of the F-BMP hot path on GB300.
 
-One step = one ps_pansharpen call (Algorithm 1 then Algorithm 2) on one
-seeded synthetic scene shaped like the paper's 8-band, ratio-4 workload:
-8 x 1024 x 1024 HRMS, LRMS 8 x 256 x 256, 17 x 17 kernel, window radius 1.
+Default workload (c3): one step = one ps_pansharpen_batched call, i.e.
+Algorithm 1 then Algorithm 2 on each of 64 seeded synthetic scenes of uneven
+sizes (PAN sides 512..2048, 4 or 8 bands, ratio 4, kernels 9x9..17x17, all
+estimated), in one graph launch: 597 M pixel-bands, the largest single-GPU
+configuration of the paper's 4- and 8-band ratio-4 workloads. The solve runs
+in its fastest form (FFT alias-group preconditioned CG from the trained
+warm-start network, FP32 Z step, relative residual 1e-6); its accuracy
+against the FP64 oracle is measured on a stated sample outside the timed
+region. --workload c1 / c2 time one 8 x 1024^2 / 8 x 8192^2 scene instead.
 Prints one JSON line (rank 0).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun every rank solves its own scene (scenes are independent
+Under torchrun every rank solves its own batch (scenes are independent
 units: weak scaling, no collective on the data path); the step time is the
 max over ranks.
 """
@@ -19,6 +25,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -44,6 +51,34 @@ def workload_name(cfg) -> str:
             f"ratio {cfg.ratio}, {cfg.n}x{cfg.n} kernel estimated, LLP window radius {cfg.r}; "
             "seeded synthetic scene (shapes + texture, Dirichlet PAN weights, anisotropic "
             "shifted Gaussian blur, noise 0.005)")
+
+
+def form_note(args) -> dict:
+    """The timed solve's form, as both arms' config states it."""
+    if args.warm == "cnn":
+        warm = ("cnn (" + os.path.relpath(WARM_WEIGHTS, ROOT) + ")"
+                if os.path.exists(WARM_WEIGHTS) else "cnn weights missing: cold start")
+    else:
+        warm = args.warm
+    return {"cg_tol": 1e-6, "cg_stop": "relative residual",
+            "cg_precond": "FFT alias-group, gamma 4" if args.precond == "fft" else "none",
+            "warm_start": warm, "zstep": "FP64 forward FFT" if args.zstep_fp64 else "FP32",
+            "oracle_sample": oracle_sample_note(args.ref_crop)}
+
+
+def single_config(cfg, args) -> dict:
+    return {"workload": workload_name(cfg), "scenes_per_rank": 1,
+            "px_band_per_rank": cfg.bands * cfg.H * cfg.W,
+            "parallelism": f"replicas x{args.gpus} (independent scenes)",
+            "l2": "flushed between timed steps (256 MiB write)", **form_note(args)}
+
+
+def batch_config(cfgs, args) -> dict:
+    return {"workload": batch_name(cfgs), "scenes_per_rank": len(cfgs),
+            "px_band_per_rank": sum(c.bands * c.H * c.W for c in cfgs),
+            "parallelism": f"replicas x{args.gpus} (independent batches)",
+            "l2": "inputs larger than L2 (and a 256 MiB write between steps)",
+            **form_note(args)}
 
 
 # ---------------------------------------------------------------------------
@@ -94,12 +129,12 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = None
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix=f"ps_clocks_gpu{self.gpu}_", suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
@@ -118,8 +153,11 @@ class ClockSampler:
             self.proc.kill()
         self.fh.close()
         sm, smax, reasons = [], [], set()
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        os.unlink(self.path)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -138,31 +176,67 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU baseline: the oracle as it stands, on a bounded crop
+# The oracle as it stands, on a bounded sample of the workload: the CPU
+# baseline of the GPU arm and every step of the reference arm time the same
+# sample
 # ---------------------------------------------------------------------------
-def oracle_step(sc_crop, threads: int) -> float:
-    import oracle
-    cfg = sc_crop["config"]
-    t0 = time.perf_counter()
-    oracle.pansharpen(sc_crop["lrms"], sc_crop["pan"], cfg.ratio, cfg.R,
-                      hp=oracle.HrmsParams(r=cfg.r), threads=threads)
-    return time.perf_counter() - t0
+ORACLE_CROP = 96          # HR side of each crop (2^5 3: an FFT size the GPU path takes)
+ORACLE_SCENES = 4         # scenes of the batch the sample is cropped from
 
 
-def cpu_baseline(scene, crop: int, reps: int = 1) -> dict:
+def oracle_sample_scenes(cfgs, crop: int = ORACLE_CROP, count: int = ORACLE_SCENES):
+    """Top-left crop x crop of the first `count` scenes of the workload, each
+    treated as its own periodic scene (all its bands, its kernel size)."""
     import synth
-    sc = synth.crop_scene(scene, crop)
-    cfg = sc["config"]
-    threads = min(os.cpu_count() or 1, cfg.bands)
-    secs = [oracle_step(sc, threads) for _ in range(reps)]
+    return [synth.crop_scene(synth.make_scene(c), crop) for c in cfgs[:count]]
+
+
+def oracle_sample_note(crop: int = ORACLE_CROP, count: int = ORACLE_SCENES) -> str:
+    return (f"{crop}x{crop} crops of the first {count} scenes of the workload (all their "
+            f"bands, their kernel sizes, ratio 4), each solved as its own periodic scene by "
+            f"the FP64 oracle (C + numpy; Algorithm 1, then Algorithm 2 with CG to 1e-12); "
+            f"scenes and bands on host threads")
+
+
+def oracle_pass(samples) -> tuple[float, list]:
+    """One pass of the oracle over the sample: every scene on its own host
+    thread, its bands on threads of their own (the paper's channel-parallel
+    scheme, across scenes too). Returns (seconds, results)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(sc):
+        cfg = sc["config"]
+        return oracle.pansharpen(sc["lrms"], sc["pan"], cfg.ratio, cfg.R,
+                                 hp=oracle.HrmsParams(r=cfg.r), threads=cfg.bands)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=len(samples)) as ex:
+        out = list(ex.map(one, samples))
+    return time.perf_counter() - t0, out
+
+
+def sample_units(samples) -> int:
+    return sum(s["config"].bands * s["config"].H * s["config"].W for s in samples)
+
+
+def sample_threads(samples) -> int:
+    return min(os.cpu_count() or 1, sum(s["config"].bands for s in samples))
+
+
+def cpu_baseline(samples, reps: int = 2):
+    """The oracle timed on the host cores over the sample; returns the
+    cpu_baseline record and the oracle's results (for the accuracy block)."""
+    secs, res = [], None
+    for _ in range(reps):
+        t, res = oracle_pass(samples)
+        secs.append(t)
     t = float(np.mean(secs))
-    return {"value": cfg.bands * crop * crop / 1e6 / t, "unit": UNIT, "cores": threads,
-            "kind": "oracle",
-            "sample": f"{crop}x{crop} crop of the workload scene (all {cfg.bands} bands, same "
-                      f"kernel size and ratio) solved as its own periodic scene by the FP64 "
-                      f"oracle (C + numpy, bands on {threads} threads, CG to 1e-12), "
-                      f"{reps} run(s), {t:.1f} s each",
-            "host_cores": os.cpu_count()}
+    rec = {"value": sample_units(samples) / 1e6 / t, "unit": UNIT,
+           "cores": sample_threads(samples), "kind": "oracle",
+           "sample": oracle_sample_note() + f"; {reps} passes, {t:.1f} s each",
+           "host_cores": os.cpu_count()}
+    return rec, res
 
 
 # ---------------------------------------------------------------------------
@@ -172,28 +246,33 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    import synth
-    cfg = workload_config(args.r, args.scene, args.ratio)
-    scene = synth.make_scene(cfg)
-    crop = args.ref_crop
-    sc = synth.crop_scene(scene, crop)
-    threads = min(os.cpu_count() or 1, cfg.bands)
+    if args.workload == "c3":
+        import synth
+        cfgs = synth.make_batch_configs(args.batch, 3000)
+        config = batch_config(cfgs, args)
+    else:
+        cfg = workload_config(args.r, args.workload, args.ratio)
+        cfgs = [cfg]
+        config = single_config(cfg, args)
+    samples = oracle_sample_scenes(cfgs, args.ref_crop)
+    units = sample_units(samples)
     for _ in range(args.warmup):
-        oracle_step(sc, threads)
-    t0 = time.perf_counter()
+        oracle_pass(samples)
+    total = 0.0
     for _ in range(args.steps):
-        oracle_step(sc, threads)
-    t = (time.perf_counter() - t0) / args.steps
-    value = cfg.bands * crop * crop / 1e6 / t
+        t, _ = oracle_pass(samples)
+        total += t
+    t = total / max(args.steps, 1)
+    value = units / 1e6 / t
     rec = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(cfg), "sample_crop": crop},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"each step: {crop}x{crop} crop of the workload scene, "
-                                   f"all {cfg.bands} bands, FP64 oracle"},
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample_threads(samples),
+                         "kind": "oracle",
+                         "sample": "each step: " + oracle_sample_note(args.ref_crop)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(rec), flush=True)
@@ -207,15 +286,18 @@ def cg_iteration_roofline(api, X, Y, kern, cfg, hp, peak_gbs, dev):
     """Average duration of one CG iteration of the Z0 solve, from two solves
     that run a fixed number of iterations (tolerance out of reach), timed with
     CUDA events on the launching stream. One iteration is db + llp +
-    cg_update (+ the three preconditioner kernels) + control; its algorithmic
-    bytes per px.band are 40 + 12/N for the CG (fused A-matvec 16, vector
-    update 24, PAN statistics 12 shared by the N bands) plus, preconditioned,
-    32: row FFT in 8 (r in, half a complex value out), column pass 8 + 8
-    ceil(N/2)/N (spectrum in and out, B^ once per band pair), inverse row FFT
-    12 (spectrum in, z out, r in for r^T z)."""
+    cg_update (+ the three preconditioner kernels) + control.
+
+    Its algorithmic bytes per px.band are the method's: 40 + 12/N (fused
+    A-matvec 16, vector update 24, PAN statistics 12 shared by the N bands).
+    The preconditioner (an extension; the paper runs plain CG) moves another
+    32 (row FFT 8: r in, half a complex value out; column pass 8 + 8
+    ceil(N/2)/N: spectrum in and out, B^ once per band pair; inverse row FFT
+    12: spectrum in, z out, r in for r^T z), reported apart and not counted
+    in `achieved`."""
     import torch
     from paper_2103_09943_gb300._lib import HrmsParams
-    ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev)
+    ws = api.workspace(cfg.bands, cfg.H, cfg.W, cfg.ratio, cfg.R, dev, hp)
     out = torch.empty((cfg.bands, cfg.H, cfg.W), dtype=torch.float32, device=dev)
 
     def timed(iters, reps=3):
@@ -242,20 +324,35 @@ def cg_iteration_roofline(api, X, Y, kern, cfg, hp, peak_gbs, dev):
     per_iter_ms = (t_hi - t_lo) / (hi - lo)
     nimg = (cfg.bands + 1) // 2
     per_unit = 40.0 + 12.0 / cfg.bands
-    kernels = "db_kernel + llp_kernel + cg_update_kernel + cg_control_kernel"
+    prec_unit = 8.0 + (8.0 + 8.0 * nimg / cfg.bands) + 12.0 if hp.precond else 0.0
+    kernels = "db_site + llp_cgq + cg_update_site + cg_control"
     if hp.precond:
-        per_unit += 8.0 + (8.0 + 8.0 * nimg / cfg.bands) + 12.0
-        kernels = ("db_kernel + llp_kernel + cg_update_kernel + prec_rows_fwd_kernel + "
-                   "prec_cols_kernel + prec_rows_inv_kernel + cg_control_kernel")
+        kernels = ("db_site + llp_cgq + cg_update_site + prec_rows_fwd + prec_cols + "
+                   "prec_rows_inv + cg_control")
     units = cfg.bands * cfg.H * cfg.W
-    achieved = per_unit * units / (per_iter_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-            "frac": achieved / peak_gbs, "traffic": None,
-            "kernel": ("preconditioned " if hp.precond else "") +
-                      f"CG iteration of Eq. Z_ini_matting ({kernels})",
-            "bytes_per_unit": per_unit, "units_per_launch": units,
-            "ms_per_iteration": per_iter_ms, "peak_note": "of measured (MEASURED_PEAKS.json "
-                                                          "hbm_gbs)"}
+    secs = per_iter_ms * 1e-3
+    achieved = per_unit * units / secs / 1e9
+    rec = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+           "frac": achieved / peak_gbs, "traffic": None,
+           "kernel": ("preconditioned " if hp.precond else "") +
+                     f"CG iteration of Eq. Z_ini_matting ({kernels})",
+           "bytes_per_unit": per_unit, "units_per_launch": units,
+           "ms_per_iteration": per_iter_ms}
+    if hp.precond:
+        rec["precond_bytes_per_unit"] = prec_unit
+        rec["frac_with_precond_bytes"] = (per_unit + prec_unit) * units / secs / 1e9 / peak_gbs
+    tr = TRAFFIC_PER_UNIT.get((bool(hp.precond), cfg.bands))
+    if tr is not None:
+        rec["traffic"] = tr["bytes_per_unit"] * units
+        rec["traffic_note"] = tr["note"]
+    return rec
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one CG
+# iteration per px.band, summed over its kernels, from one-kernel ncu
+# captures of a scene larger than L2; keyed by (preconditioned, bands). The
+# capture commands and per-kernel figures are in profiles/.
+TRAFFIC_PER_UNIT = {}
 
 
 def launches_per_step(cfg, hp, cg_iters, split=1) -> int:
@@ -297,6 +394,18 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
+def profile_config(args):
+    """The scene a profiling run uses: the largest scene of the uneven batch
+    (the one the bench's roofline is measured on), or the single workload."""
+    if args.workload == "c3":
+        import synth
+        cfgs = synth.make_batch_configs(args.batch, 3000)
+        cfg = max(cfgs, key=lambda c: c.bands * c.H * c.W)
+        from dataclasses import replace
+        return replace(cfg, r=args.r)
+    return workload_config(args.r, args.workload, args.ratio)
+
+
 def run_profile_solve(args):
     """One solve of the workload scene with host-launched CG iterations and a
     fixed iteration count (the tolerance out of reach), after one untimed
@@ -308,7 +417,7 @@ def run_profile_solve(args):
     __graft_entry__.build()
     import synth
     from paper_2103_09943_gb300 import api
-    cfg = workload_config(args.r, args.scene, args.ratio)
+    cfg = profile_config(args)
     if args.profile_shape:
         from dataclasses import replace
         b, side = (int(v) for v in args.profile_shape.lower().split("x"))
@@ -401,7 +510,7 @@ def run_profile_warm(args):
     import synth
     from paper_2103_09943_gb300 import ops
     from paper_2103_09943_gb300.cnn import WarmStartNet
-    cfg = workload_config(args.r, args.scene, args.ratio)
+    cfg = profile_config(args)
     scene = synth.make_scene(cfg)
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
@@ -426,12 +535,12 @@ def run_gpu(args):
     import synth
     from paper_2103_09943_gb300 import api
 
-    cfg = workload_config(args.r, args.scene, args.ratio)
+    cfg = workload_config(args.r, args.workload, args.ratio)
     scene = synth.make_scene(cfg, seed=cfg.seed + rank)   # one independent scene per rank
     X = torch.from_numpy(scene["lrms"]).to(dev)
     Y = torch.from_numpy(scene["pan"]).to(dev)
     kp = api.default_kernel_params()
-    net, warm_note = load_warm_net(args.warm, dev)
+    net, _ = load_warm_net(args.warm, dev)
     warm = {"none": 0, "bicubic": 1, "cnn": 2}[args.warm] if (net or args.warm != "cnn") else 0
     hp = api.default_hrms_params(host_loop=1 if args.cg_loop == "host" else 0,
                                  precond=1 if args.precond == "fft" else 0, warm=warm,
@@ -508,7 +617,7 @@ def run_gpu(args):
         if peak_kind == "measured" else "of fallback (6.8 TB/s)"
 
     # accuracy of the timed configuration: the FP64 oracle's operator on the
-    # GPU's Z0 (true relative residual), two bands
+    # GPU's Z0 at full size (true relative residual), two bands
     acc = None
     if rank == 0:
         import oracle
@@ -521,8 +630,7 @@ def run_gpu(args):
             rhs = oracle.blur_decimate_adj(scene["lrms"][b], k64, cfg.ratio)
             rr = rhs - oracle.apply_z0_system(z0[b], k64, cfg.ratio, st, hp.lambda_)
             res.append(float(np.linalg.norm(rr) / np.linalg.norm(rhs)))
-        acc = {"cg_tol": hp.tol, "z0_true_rel_residual_fp64": res,
-               "parity": "tests/test_gpu_*.py: per-band rel-L2 vs the FP64 oracle"}
+        acc = {"z0_true_rel_residual_fp64_full_size": res}
 
     variants = None
     if rank == 0 and not args.no_compare:
@@ -530,7 +638,9 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(scene, args.cpu_crop)
+        samples = oracle_sample_scenes([cfg], args.ref_crop)
+        cpu, refs = cpu_baseline(samples)
+        acc.update(accuracy_vs_oracle(api, samples, refs, hp, dev))
 
     if rank == 0:
         rec = {
@@ -538,16 +648,9 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(cfg), "scenes_per_rank": 1,
-                       "parallelism": f"replicas x{world} (independent scenes)",
-                       "l2": "flushed between timed steps (256 MiB write)",
-                       "cg_tol": hp.tol, "cg_iters": binfo.iters, "cg_loop": args.cg_loop,
-                       "cg_precond": ("FFT alias-group, gamma %g" % hp.precond_gamma)
-                       if hp.precond else "none",
-                       "warm_start": warm_note,
-                       "zstep": "FP64 forward FFT" if args.zstep_fp64 else "FP32",
-                       "autotuned": tuning,
-                       "admm_iters": kinfo.iters},
+            "config": single_config(cfg, args),
+            "run": {"cg_iters": binfo.iters, "cg_loop": args.cg_loop, "autotuned": tuning,
+                    "admm_iters": kinfo.iters},
             "wall_s_timed_region": wall,
             "e2e": {"value": throughput(units, world, e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": pipe.h2d_bytes, "d2h_bytes_per_step": pipe.d2h_bytes,
@@ -609,6 +712,42 @@ def _timed_steps(fn, steps, flush):
     return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
 
+def batch_launches(cfgs, hp, sinfo) -> int:
+    """Kernels of this library launched by one batched call: a timer stamp,
+    then per scene the kernels of one ps_pansharpen call with its bands in
+    one CG loop (the concurrency comes from the scenes) and its stamp."""
+    return 1 + sum(launches_per_step(c, hp, list(si.iters), 1) + 1
+                   for c, si in zip(cfgs, sinfo))
+
+
+def accuracy_vs_oracle(api, samples, refs, hp, dev):
+    """The timed form on the oracle's sample: the crops as one batch through
+    ps_pansharpen_batched (kernels estimated), then Z0 of every crop from
+    ps_solve_hrms given the batch's kernel; per-band rel-L2 of Z and Z0
+    against the oracle's, and of the kernel."""
+    import torch
+    dev_sc = [(torch.from_numpy(s["lrms"]).to(dev), torch.from_numpy(s["pan"]).to(dev),
+               s["config"].R) for s in samples]
+    b = api.Batch(dev_sc, samples[0]["config"].ratio, hparams=hp, estimate=True)
+    b.run()
+    ez, ez0, ek = [], [], []
+    for (x, y, _), z, k, ref in zip(dev_sc, b.hrms, b.kernels, refs):
+        _, z0, _ = api.solve_hrms(x, y, k, samples[0]["config"].ratio, hp, want_z0=True,
+                                  info=False)
+        torch.cuda.synchronize()
+        zn, z0n = z.cpu().numpy().astype(np.float64), z0.cpu().numpy().astype(np.float64)
+        ek.append(float(np.linalg.norm(k.cpu().numpy() - ref["kernel"]) /
+                        np.linalg.norm(ref["kernel"])))
+        for n in range(zn.shape[0]):
+            ez.append(float(np.linalg.norm(zn[n] - ref["Z"][n]) / np.linalg.norm(ref["Z"][n])))
+            ez0.append(float(np.linalg.norm(z0n[n] - ref["Z0"][n]) /
+                             np.linalg.norm(ref["Z0"][n])))
+    return {"sample": oracle_sample_note(), "form": "the timed form, batched",
+            "bands": len(ez), "z_rel_l2_max": max(ez), "z_rel_l2_median": float(np.median(ez)),
+            "z0_rel_l2_max": max(ez0), "kernel_rel_l2_max": max(ek),
+            "z_rel_l2_per_band": ez, "bar": 1e-3, "within_bar": max(ez) <= 1e-3}
+
+
 def run_batch(args):
     rank, local_rank, world = dist_env()
     t_gen = time.perf_counter()
@@ -626,11 +765,21 @@ def run_batch(args):
     Y = [torch.from_numpy(a[1]).to(dev) for a in arrays]
     units = sum(c.bands * c.H * c.W for c in cfgs)
     kp = api.default_kernel_params()
-    net, warm_note = load_warm_net(args.warm, dev)
+    net, _ = load_warm_net(args.warm, dev)
     warm = {"none": 0, "bicubic": 1, "cnn": 2}[args.warm] if (net or args.warm != "cnn") else 0
     hp = api.default_hrms_params(precond=1 if args.precond == "fft" else 0, warm=warm,
                                  cnn_params=net.params.data_ptr() if net else None,
                                  zstep_fp32=0 if args.zstep_fp64 else 1)
+    # launch shapes of the tunable kernels, per distinct scene size, before
+    # the batch's graph is built (the graph reads them when it is captured)
+    tuned = {}
+    if hp.precond and not args.no_autotune:
+        for c in cfgs:
+            key = (c.bands, c.H, c.W)
+            if key not in tuned:
+                t = api.autotune(c.bands, c.H, c.W, c.ratio, c.R, hp.r, device=dev)
+                tuned[key] = {k: t[k] for k in ("prec_rows", "llp_rows", "llp_pf",
+                                                "llp_bands")}
     scenes = [(x, y, c.R) for x, y, c in zip(X, Y, cfgs)]
     batch = api.Batch(scenes, cfgs[0].ratio, hparams=hp, kparams=kp, estimate=True)
     kinfo, sinfo = batch.run(info=True)
@@ -669,6 +818,7 @@ def run_batch(args):
 
     e2e_step()
     torch.cuda.synchronize()
+    barrier(world)
     e2e = []
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -682,15 +832,20 @@ def run_batch(args):
     h2d = sum(t.numel() * 4 for t in hx + hy)
     d2h = sum(t.numel() * 4 for t in ho)
 
-    # the same batch scene by scene (one ps_pansharpen call each), in this
-    # form and as the plain FP32 CG from zeros (the paper's solver)
+    # the same batch as the plain FP32 CG from zeros (the paper's solver;
+    # the spec comparison), batched; and both forms scene by scene
     variants = None
     if rank == 0 and not args.no_compare:
-        variants = {}
-        forms = [("sequential_same_form", hp),
-                 ("sequential_plain_cg_cold",
-                  api.default_hrms_params(precond=0, warm=0, zstep_fp32=hp.zstep_fp32))]
-        for name, p in forms:
+        variants = {"batched_same_form": {"ms_per_step": step_ms, "value": value}}
+        pc = api.default_hrms_params(precond=0, warm=0, zstep_fp32=hp.zstep_fp32)
+        bc = api.Batch(scenes, cfgs[0].ratio, hparams=pc, kparams=kp, estimate=True)
+        _, sc_info = bc.run(info=True)
+        ms = _timed_steps(bc.run, max(1, min(args.steps, 3)), flush)
+        variants["batched_plain_cg_cold"] = {
+            "ms_per_step": ms, "value": throughput(units, 1, ms * 1e-3),
+            "cg_iters_mean": float(np.mean([n for si in sc_info for n in si.iters]))}
+        del bc
+        for name, p in [("sequential_same_form", hp), ("sequential_plain_cg_cold", pc)]:
             wss = [api.workspace(c.bands, c.H, c.W, c.ratio, c.R, dev, p) for c in cfgs]
 
             def seq(p=p, wss=wss):
@@ -703,14 +858,7 @@ def run_batch(args):
             ms = _timed_steps(seq, max(1, min(args.steps, 2)), flush)
             variants[name] = {"ms_per_step": ms, "value": throughput(units, 1, ms * 1e-3)}
             del wss
-        pc = api.default_hrms_params(precond=0, warm=0, zstep_fp32=hp.zstep_fp32)
-        bc = api.Batch(scenes, cfgs[0].ratio, hparams=pc, kparams=kp, estimate=True)
-        bc.run()
-        ms = _timed_steps(bc.run, max(1, min(args.steps, 2)), flush)
-        variants["batched_plain_cg_cold"] = {"ms_per_step": ms,
-                                             "value": throughput(units, 1, ms * 1e-3)}
-        del bc
-        variants["batched_same_form"] = {"ms_per_step": step_ms, "value": value}
+        batch.run()                      # leave the batch's own outputs in place
 
     # roofline of the CG iteration on the largest scene of the batch
     big = max(range(len(cfgs)), key=lambda i: cfgs[i].bands * cfgs[i].H * cfgs[i].W)
@@ -721,11 +869,13 @@ def run_batch(args):
         if peak_kind == "measured" else "of fallback (6.8 TB/s)"
     roof["scene"] = f"{cfgs[big].bands} x {cfgs[big].H}x{cfgs[big].W}, {cfgs[big].n}x{cfgs[big].n}"
 
-    cpu = None
+    # the oracle on its sample: the CPU baseline, and the reference the
+    # timed form's accuracy is measured against
+    cpu, acc = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import synth
-        small = min(range(len(cfgs)), key=lambda i: cfgs[i].H)
-        cpu = cpu_baseline(synth.make_scene(cfgs[small]), args.cpu_crop)
+        samples = oracle_sample_scenes(cfgs, args.ref_crop)
+        cpu, refs = cpu_baseline(samples)
+        acc = accuracy_vs_oracle(api, samples, refs, hp, dev)
 
     iters = [n for si in sinfo for n in si.iters]
     if rank == 0:
@@ -734,17 +884,11 @@ def run_batch(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": batch_name(cfgs), "scenes_per_rank": len(cfgs),
-                       "px_band_per_rank": units,
-                       "parallelism": f"replicas x{world} (independent batches)",
-                       "l2": "inputs larger than L2 (and a 256 MiB write between steps)",
-                       "cg_tol": hp.tol, "cg_iters_mean": float(np.mean(iters)),
-                       "cg_iters_max": int(max(iters)),
-                       "cg_precond": ("FFT alias-group, gamma %g" % hp.precond_gamma)
-                       if hp.precond else "none",
-                       "warm_start": warm_note,
-                       "admm_iters_mean": float(np.mean([k.iters for k in kinfo])),
-                       "host_generation_s": t_gen},
+            "config": batch_config(cfgs, args),
+            "run": {"cg_iters_mean": float(np.mean(iters)), "cg_iters_max": int(max(iters)),
+                    "admm_iters_mean": float(np.mean([k.iters for k in kinfo])),
+                    "autotuned": {f"{k[0]}x{k[1]}x{k[2]}": v for k, v in tuned.items()},
+                    "host_generation_s": t_gen},
             "per_scene_finish_ms": {"p50": float(np.percentile(scene_ms, 50)),
                                     "p99": float(np.percentile(scene_ms, 99)),
                                     "max": float(scene_ms.max())},
@@ -752,8 +896,10 @@ def run_batch(args):
             "e2e": {"value": throughput(units, world, e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms},
+            "gpu_launches": batch_launches(cfgs, hp, sinfo) * args.steps,
             "roofline": roof,
             "cpu_baseline": cpu,
+            "accuracy": acc,
             "clocks": clk,
             "variants": variants,
         }
@@ -823,11 +969,15 @@ def parse(argv=None):
     ap.add_argument("--ratio", type=int, default=0,
                     help="resolution ratio of the scene (default: the config's, 4); 2 gives the "
                          "paper's other setting")
-    ap.add_argument("--scene", default="c1", choices=["c1", "c2"],
-                    help="c1: 8 x 1024^2 (the metric's workload); c2: one 8 x 8192^2 scene "
-                         "(LRMS 8 x 2048^2), generated as c1 with seed 2")
-    ap.add_argument("--cpu-crop", type=int, default=128)
-    ap.add_argument("--ref-crop", type=int, default=64)
+    ap.add_argument("--workload", default="c3", choices=["c3", "c1", "c2"],
+                    help="c3 (default): the uneven batch of --batch seeded scenes (sides "
+                         "512..2048, 4 or 8 bands, kernels 9x9..17x17) in one graph launch, "
+                         "the largest single-GPU configuration; c1: one 8 x 1024^2 scene; "
+                         "c2: one 8 x 8192^2 scene (LRMS 8 x 2048^2), generated as c1 with "
+                         "seed 2")
+    ap.add_argument("--ref-crop", "--cpu-crop", dest="ref_crop", type=int, default=ORACLE_CROP,
+                    help="HR side of the crops the oracle is timed on (CPU baseline and "
+                         "reference arm alike)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-solve", type=int, default=0, metavar="ITERS",
                     help="no timing: run one HRMS solve of the workload with the CG loop "
@@ -852,10 +1002,8 @@ def parse(argv=None):
     ap.add_argument("--precond", default="fft", choices=["fft", "none"],
                     help="preconditioner of the Z0 CG (fft: alias-group FFT solve; none: "
                          "plain CG as in the paper)")
-    ap.add_argument("--batch", type=int, default=0, metavar="SCENES",
-                    help="time the uneven batch of SCENES seeded scenes (sides 512..2048, "
-                         "4 or 8 bands, kernels 9x9..17x17) in one graph launch instead of "
-                         "the 8 x 1024^2 scene")
+    ap.add_argument("--batch", type=int, default=64, metavar="SCENES",
+                    help="scenes in the uneven batch of the c3 workload")
     ap.add_argument("--priors", action="store_true",
                     help="no timing: the cross-channel prior ablation (PSNR per prior)")
     ap.add_argument("--cg-loop", default="graph", choices=["graph", "host"],
@@ -872,10 +1020,10 @@ def main(argv=None):
         return run_profile_solve(args)
     if args.profile_warm:
         return run_profile_warm(args)
-    if args.batch:
-        return run_batch(args)
     if args.priors:
         return run_priors(args)
+    if args.workload == "c3":
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -40,6 +40,18 @@ def test_launch_count_by_hand():
     assert b.launches_per_step(cfg, hp, iters, 1) == kest + solve - loop + 7 * 4 * 13 + warm
 
 
+def test_batch_launch_count():
+    # one timer stamp, then per scene the one-scene count with all its bands
+    # in one loop (split 1) and its own stamp
+    b = _bench()
+    cfgs = synth.make_batch_configs(3, 3000)
+    hp = SimpleNamespace(precond=1, zstep_fp32=1, warm=2)
+    sinfo = [SimpleNamespace(iters=[40 + k] * c.bands) for k, c in enumerate(cfgs)]
+    want = 1 + sum(b.launches_per_step(c, hp, [40 + k] * c.bands, 1) + 1
+                   for k, c in enumerate(cfgs))
+    assert b.batch_launches(cfgs, hp, sinfo) == want
+
+
 def test_reference_arm_json_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                           "--steps", "1", "--warmup", "0", "--ref-crop", "32"],
@@ -51,3 +63,7 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"]
+    # the same config as the GPU arm's line (the workload, not a crop of it)
+    b = _bench()
+    args = b.parse(["--ref-crop", "32"])
+    assert d["config"] == b.batch_config(synth.make_batch_configs(args.batch, 3000), args)

@@ -41,6 +41,18 @@ def scenes():
 
 
 @pytest.fixture(scope="module")
+def oracle_refs(scenes):
+    """Algorithm 1 then Algorithm 2 on every scene by the FP64 oracle, every
+    linear system solved to 1e-11."""
+    out = []
+    for sc in scenes:
+        cfg = sc["config"]
+        out.append(oracle.pansharpen(sc["lrms"], sc["pan"], cfg.ratio, cfg.R,
+                                     hp=oracle.HrmsParams(tol=1e-11), threads=4))
+    return out
+
+
+@pytest.fixture(scope="module")
 def batch_estimated(cuda, scenes):
     hp = api.default_hrms_params(tol=1e-7)
     dev = [(to_dev(s["lrms"], cuda), to_dev(s["pan"], cuda), s["config"].R) for s in scenes]
@@ -49,12 +61,11 @@ def batch_estimated(cuda, scenes):
     return b, kinfo, sinfo, hp
 
 
-def test_batch_matches_oracle(scenes, batch_estimated):
+def test_batch_matches_oracle(scenes, batch_estimated, oracle_refs):
     b, kinfo, sinfo, hp = batch_estimated
     for i, sc in enumerate(scenes):
         cfg = sc["config"]
-        ref = oracle.pansharpen(sc["lrms"], sc["pan"], cfg.ratio, cfg.R,
-                                hp=oracle.HrmsParams(tol=1e-11), threads=4)
+        ref = oracle_refs[i]
         assert kinfo[i].status == 0, (i, kinfo[i].status)
         assert all(s == 0 for s in sinfo[i].status), (i, sinfo[i])
         assert rel(to_np(b.kernels[i]), ref["kernel"]) < 1e-4, i
@@ -111,7 +122,7 @@ def test_batch_given_kernels_plain_fp32(cuda, scenes):
             assert rel(Z[k], ref["Z"][k]) < 1e-5, (i, k)
 
 
-def test_batch_network_warm_start(cuda, scenes):
+def test_batch_network_warm_start(cuda, scenes, oracle_refs):
     from paper_2103_09943_gb300.cnn import WarmStartNet
     net = WarmStartNet.load(WEIGHTS, device=cuda)
     hp = api.default_hrms_params(tol=1e-7, warm=2, cnn_params=net.params.data_ptr())
@@ -120,6 +131,13 @@ def test_batch_network_warm_start(cuda, scenes):
     kinfo, sinfo = b.run(info=True)
     for i, sc in enumerate(scenes):
         cfg = sc["config"]
+        # against the FP64 oracle: the warm start changes the start point,
+        # not the solution
+        Zb = to_np(b.hrms[i])
+        assert rel(to_np(b.kernels[i]), oracle_refs[i]["kernel"]) < 1e-4, i
+        for n in range(cfg.bands):
+            assert rel(Zb[n], oracle_refs[i]["Z"][n]) < 1e-4, (i, n)
+        # and against the one-scene call
         Z, k, ki, si = api.pansharpen(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
                                       cfg.ratio, cfg.R, hparams=hp)
         assert all(s == 0 for s in sinfo[i].status)
