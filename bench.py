@@ -359,17 +359,18 @@ def launches_per_step(cfg, hp, cg_iters, split=1) -> int:
     """Kernels of this library launched by one ps_pansharpen call.
     Kernel estimate: 4 (omega) + 4 (f, E^T E lags and assembly, E^T f) +
     Cholesky (1 + per 32-column panel: diagonal, and below it panel and
-    trailing update) + 3 (solve, inverse, ADMM). HRMS solve: PAN statistics,
-    4 for the kernel spectrum (two twiddle tables, spectrum, FP32 copy),
-    right-hand side, reset, init (+3 for z0 = P^{-1} r0), then the CG loop:
-    per branch of bands (split on band pairs), bodies of four iterations of
-    4 (plain) or 7 (preconditioned) kernels until its bands stop; then the Z
-    step (4 in FP32: fused right-hand side, 3 preconditioner passes; 8 in
-    FP64). Warm start: bicubic, the network (4 weight packs, first layer,
-    4 convolutions) and A z_init (2)."""
+    trailing update) + 3 (solve, inverse, ADMM) + the status collector.
+    HRMS solve: PAN statistics, 4 for the kernel spectrum (two twiddle
+    tables, spectrum, FP32 copy), right-hand side, reset, init (+3 for
+    z0 = P^{-1} r0), then the CG loop: per branch of bands (split on band
+    pairs), bodies of four iterations of 4 (plain) or 7 (preconditioned)
+    kernels until its bands stop; then the Z step (4 in FP32: fused
+    right-hand side, 3 preconditioner passes; 8 in FP64) and the status
+    collector. Warm start: bicubic, the network (4 weight packs, first
+    layer, 4 convolutions) and A z_init (2)."""
     nt = cfg.n * cfg.n
     panels = (nt + 31) // 32
-    kest = 4 + 4 + (1 + panels + 2 * (panels - 1)) + 3
+    kest = 4 + 4 + (1 + panels + 2 * (panels - 1)) + 3 + 1
     per_iter = 7 if hp.precond else 4
     pairs = (cfg.bands + 1) // 2
     bounds = [min(cfg.bands, 2 * ((pairs * k) // split)) for k in range(split + 1)]
@@ -379,7 +380,7 @@ def launches_per_step(cfg, hp, cg_iters, split=1) -> int:
         if its:
             loop += per_iter * 4 * max(1, math.ceil(max(its) / 4))
     zstep = 4 if hp.zstep_fp32 else 8
-    solve = 1 + 4 + 1 + 2 + (3 if hp.precond else 0) + loop + zstep
+    solve = 1 + 4 + 1 + 2 + (3 if hp.precond else 0) + loop + zstep + 1
     warm = {0: 0, 1: 1 + 2, 2: 1 + 9 + 2}[hp.warm]
     return kest + solve + warm
 

@@ -65,6 +65,11 @@ typedef struct ps_kernel_params {
     float rho;          /* multiplier step of Eq. subproblems (0.5)           */
     int t_max;          /* iteration cap of Algorithm 1 (10000)               */
     float th;           /* stop when ||u^t - u^{t+1}|| / ||u^{t+1}|| < th (1e-5) */
+    unsigned long long band_mask; /* the LRMS channels X' of Eq. objective1,
+                           those spectrally overlapped with the PAN (Sec. II,
+                           N' <= N): bit b set takes band b. 0 (default)
+                           takes all N bands. Bits at or above N are an
+                           error (PS_ERR_INVALID_ARG).                        */
 } ps_kernel_params;
 
 /* Cross-channel prior of Algorithm 2 (Sec. IV-D, Table III): the filter F_d
@@ -154,6 +159,11 @@ typedef struct ps_band_info {
     int status;          /* PS_OK, PS_ERR_NOT_CONVERGED, _NONFINITE, _BREAKDOWN */
     int iters;           /* CG iterations taken                                */
     double rel_residual; /* final recursive ||r|| / ||b||                      */
+    float ms;            /* device time of this band's Z0 solve: from the
+                            solve's initialisation to the end of the CG
+                            iteration in which the band stopped (the
+                            device's global timer). The bands of a call run
+                            together, so their times overlap.              */
 } ps_band_info;
 
 /* Result of the kernel estimate. */
@@ -166,6 +176,17 @@ typedef struct ps_kernel_info {
 void ps_default_kernel_params(ps_kernel_params *h_params);
 void ps_default_hrms_params(ps_hrms_params *h_params);
 const char *ps_status_string(int status);
+
+/* Statuses the device detects (a band's CG not converged, non-finite or in
+ * breakdown; the kernel estimate not converged) land in h_info when a call
+ * is given one, and are also recorded as a sticky status: the first such
+ * status since the last ps_sync_status in the current CUDA context. This
+ * call waits for the work queued on `stream`, returns that status (PS_OK
+ * when none, PS_ERR_CUDA when the wait fails) and clears it, so that calls
+ * made without h_info (which return before their work runs) can be checked
+ * afterwards. Waits that give up inside the warm-start network are reported
+ * by ps_cnn_sync_status. */
+ps_status ps_sync_status(void *stream);
 
 /* Launch choices of the tunable kernels of ps_solve_hrms for one size, and
  * the times (microseconds, one launch on the workload's sizes) that picked
@@ -209,15 +230,16 @@ size_t ps_workspace_size(int N, int H, int W, int ratio, int R,
 
 /*
  * Algorithm 1 (Sec. III-A): blur kernel estimation.
- *   omega: spectral weights of Eq. objective3, in closed form, unless
- *          d_omega_in is non-NULL (N floats, used as given);
- *   E^T E, E^T f of Eq. z_solution with E = D C(Y), f = X omega, accumulated
- *          in FP64, and the Cholesky factor of E^T E + mu3 I;
+ *   omega: spectral weights of Eq. objective3 over the bands X' that
+ *          h_params->band_mask selects (all N when it is 0), in closed form,
+ *          unless d_omega_in is non-NULL (N floats, used as given; entries
+ *          of bands outside X' are ignored);
+ *   E^T E, E^T f of Eq. z_solution with E = D C(Y), f = X' omega,
+ *          accumulated in FP64, and the Cholesky factor of E^T E + mu3 I;
  *   the generalized ADMM of Eq. subproblems until
  *          ||u^t - u^{t+1}|| / ||u^{t+1}|| < th or t_max iterations.
- * All N bands are taken as the X' of Eq. objective1.
  * Out: d_kernel (n x n, in the simplex of Eq. simplex), d_omega_out (N floats,
- * may be NULL).
+ * may be NULL): the weight of every band of X', 0 for the other bands.
  */
 ps_status ps_estimate_kernel(const float *d_lrms, const float *d_pan, int N,
                              int H, int W, int ratio, int R,
@@ -277,6 +299,8 @@ typedef struct ps_scene {
     float *kernel;       /* n x n, n = 2R + 1: written when the call
                             estimates the kernel, read otherwise           */
     int N, H, W, ratio, R;
+    unsigned long long band_mask; /* X' of this scene (bit b: band b);
+                            0 takes h_kparams->band_mask                   */
 } ps_scene;
 
 /* Workspace bytes of ps_pansharpen_batched for these scenes: a header of

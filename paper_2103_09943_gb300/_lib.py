@@ -18,7 +18,8 @@ class KernelParams(ctypes.Structure):
                 ("alpha1", ctypes.c_float), ("alpha2", ctypes.c_float),
                 ("mu1", ctypes.c_float), ("mu2", ctypes.c_float),
                 ("mu3", ctypes.c_float), ("rho", ctypes.c_float),
-                ("t_max", ctypes.c_int), ("th", ctypes.c_float)]
+                ("t_max", ctypes.c_int), ("th", ctypes.c_float),
+                ("band_mask", ctypes.c_ulonglong)]
 
 
 class HrmsParams(ctypes.Structure):
@@ -42,7 +43,7 @@ class Tuning(ctypes.Structure):
 
 class BandInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
-                ("rel_residual", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("ms", ctypes.c_float)]
 
 
 class KernelInfo(ctypes.Structure):
@@ -54,7 +55,8 @@ class Scene(ctypes.Structure):
     _fields_ = [("lrms", ctypes.c_void_p), ("pan", ctypes.c_void_p),
                 ("hrms", ctypes.c_void_p), ("kernel", ctypes.c_void_p),
                 ("N", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
-                ("ratio", ctypes.c_int), ("R", ctypes.c_int)]
+                ("ratio", ctypes.c_int), ("R", ctypes.c_int),
+                ("band_mask", ctypes.c_ulonglong)]
 
 
 _P = ctypes.c_void_p
@@ -67,6 +69,7 @@ SIGNATURES = {
     "ps_default_kernel_params": (None, [ctypes.POINTER(KernelParams)]),
     "ps_default_hrms_params": (None, [ctypes.POINTER(HrmsParams)]),
     "ps_status_string": (ctypes.c_char_p, [_I]),
+    "ps_sync_status": (_I, [_P]),
     "ps_workspace_size": (_Z, [_I, _I, _I, _I, _I, _P]),
     "ps_estimate_kernel": (_I, [_P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(KernelParams),
                                 _P, _P, _P, ctypes.POINTER(KernelInfo), _P, _Z, _P]),

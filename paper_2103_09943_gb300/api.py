@@ -49,6 +49,17 @@ def default_kernel_params(**kw) -> KernelParams:
     return p
 
 
+def band_mask(bands) -> int:
+    """The ps_kernel_params.band_mask of the LRMS channels X' (Eq. objective1)
+    given as band indices; None or empty: all bands (0)."""
+    m = 0
+    for b in bands or ():
+        if not 0 <= int(b) < 64:
+            raise ValueError("band index out of range")
+        m |= 1 << int(b)
+    return m
+
+
 def default_hrms_params(**kw) -> HrmsParams:
     p = HrmsParams()
     _lib.load().ps_default_hrms_params(ctypes.byref(p))
@@ -109,6 +120,18 @@ class SolveInfo:
     status: list
     iters: list
     rel_residual: list
+    ms: list          # device time of each band's Z0 solve (ps_band_info.ms)
+
+
+def _solve_info(bi):
+    return SolveInfo([b.status for b in bi], [b.iters for b in bi],
+                     [b.rel_residual for b in bi], [b.ms for b in bi])
+
+
+def sync_status() -> int:
+    """ps_sync_status on the current stream: waits for it, returns and clears
+    the first device-detected status since the last read (0: none)."""
+    return int(_lib.load().ps_sync_status(_stream()))
 
 
 def estimate_kernel(lrms, pan, ratio: int, R: int, params: KernelParams | None = None,
@@ -149,8 +172,7 @@ def solve_hrms(lrms, pan, kernel, ratio: int, params: HrmsParams | None = None,
         bi if info else None, _ptr(ws), ws.numel(), _stream()))
     si = None
     if info:
-        si = SolveInfo([b.status for b in bi], [b.iters for b in bi],
-                       [b.rel_residual for b in bi])
+        si = _solve_info(bi)
     return hr, z0, si
 
 
@@ -178,15 +200,15 @@ def pansharpen(lrms, pan, ratio: int, R: int, kparams: KernelParams | None = Non
         _ptr(ws), ws.numel(), _stream()))
     si = None
     if info:
-        si = SolveInfo([b.status for b in bi], [b.iters for b in bi],
-                       [b.rel_residual for b in bi])
+        si = _solve_info(bi)
     return hr, kern, (ki if info else None), si
 
 
 class Batch:
     """Many scenes of uneven sizes in one graph launch (ps_pansharpen_batched).
 
-    scenes: list of (lrms (N,h,w), pan (H,W), R) on the device. Outputs
+    scenes: list of (lrms (N,h,w), pan (H,W), R) on the device, or
+    (lrms, pan, R, band_mask) with the scene's own X' (see band_mask()). Outputs
     (hrms per scene, kernel per scene) and the workspace are allocated once;
     run() launches the whole batch, estimating every kernel when
     estimate=True, else using the kernels in self.kernels (fill them first).
@@ -198,7 +220,9 @@ class Batch:
         self.kp = (kparams or default_kernel_params()) if estimate else None
         self.inputs, self.hrms, self.kernels = [], [], []
         arr = (Scene * len(scenes))()
-        for i, (lrms, pan, R) in enumerate(scenes):
+        for i, sc in enumerate(scenes):
+            lrms, pan, R = sc[:3]
+            mask = int(sc[3]) if len(sc) > 3 else 0
             _f32(lrms, "lrms"), _f32(pan, "pan")
             N = lrms.shape[0]
             H, W = pan.shape
@@ -208,7 +232,7 @@ class Batch:
             self.hrms.append(hr)
             self.kernels.append(kern)
             arr[i] = Scene(lrms.data_ptr(), pan.data_ptr(), hr.data_ptr(), kern.data_ptr(),
-                           N, H, W, ratio, R)
+                           N, H, W, ratio, R, mask)
         self.scenes = arr
         self.count = len(scenes)
         self.bands = sum(t.shape[0] for t in self.hrms)
@@ -230,8 +254,7 @@ class Batch:
         out, k = [], 0
         for hr in self.hrms:
             n = hr.shape[0]
-            out.append(SolveInfo([b.status for b in bi[k:k + n]], [b.iters for b in bi[k:k + n]],
-                                 [b.rel_residual for b in bi[k:k + n]]))
+            out.append(_solve_info(bi[k:k + n]))
             k += n
         return (list(ki) if ki is not None else None), out
 

@@ -32,6 +32,28 @@ ps_status ps::check_dims(int N, int H, int W, int c, int R) {
 
 namespace {
 
+// First non-OK status a device-side check of this library recorded in the
+// current CUDA context since the last ps_sync_status (0: none): a band's CG
+// status (not converged, non-finite, breakdown) or the kernel estimate's.
+__device__ int g_sticky_status;
+
+// Run at the end of every solve (bands) and kernel estimate (kinfo).
+__global__ void collect_status_kernel(const CgBand *bands, int N, const int *kinfo) {
+    if (threadIdx.x != 0) return;
+    int s = 0;
+    for (int b = 0; b < N && !s; ++b) s = bands[b].status;
+    if (!s && kinfo) s = kinfo[1];
+    if (s) atomicCAS(&g_sticky_status, 0, s);
+}
+
+void launch_collect_status(const CgBand *bands, int N, const int *kinfo, cudaStream_t st) {
+    collect_status_kernel<<<1, 32, 0, st>>>(bands, N, kinfo);
+}
+
+}  // namespace
+
+namespace {
+
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -159,6 +181,12 @@ ps_status check_kernel_params(const ps_kernel_params *p) {
         return PS_ERR_INVALID_ARG;
     if (!(p->mu1 > 0.f) || !(p->mu2 > 0.f) || !(p->mu3 > 0.f)) return PS_ERR_INVALID_ARG;
     if (!(p->rho > 0.f) || p->t_max < 1 || !(p->th >= 0.f)) return PS_ERR_INVALID_ARG;
+    return PS_OK;
+}
+
+// The X' mask of Eq. objective1 selects bands that exist (0: all).
+ps_status check_band_mask(unsigned long long mask, int N) {
+    if (N < 64 && (mask >> N) != 0ull) return PS_ERR_INVALID_ARG;
     return PS_OK;
 }
 
@@ -987,8 +1015,10 @@ ps_status solve_epilogue(const SolveCall &sc, const CgLoopArgs &a, cudaStream_t 
     const ps_hrms_params *p = &sc.p;
     const float lam_z =
         p->lambda * (p->exact_weight ? (float)((2 * p->r + 1) * (2 * p->r + 1)) : 1.0f);
-    return run_zstep(sc.ws, sc.lrms, a.x, sc.u, sc.N, sc.H, sc.W, sc.c, sc.R, p->r, lam_z,
-                     sc.hrms, st, &a.po, p->zstep_fp32);
+    const ps_status s = run_zstep(sc.ws, sc.lrms, a.x, sc.u, sc.N, sc.H, sc.W, sc.c, sc.R,
+                                  p->r, lam_z, sc.hrms, st, &a.po, p->zstep_fp32);
+    if (s == PS_OK) launch_collect_status(a.bands, sc.N, nullptr, st);
+    return s;
 }
 
 // Per-band CG results (after the work that wrote them has finished).
@@ -1001,6 +1031,9 @@ ps_status read_band_info(const CgBand *d_bands, int N, ps_band_info *h_info) {
         h_info[b].status = hb[b].status;
         h_info[b].iters = hb[b].iters;
         h_info[b].rel_residual = hb[b].bb > 0.0 ? sqrt(hb[b].rr / hb[b].bb) : 0.0;
+        h_info[b].ms = hb[b].t_done > hb[b].t_start
+                           ? (float)((double)(hb[b].t_done - hb[b].t_start) * 1e-6)
+                           : 0.0f;
     }
     return PS_OK;
 }
@@ -1078,10 +1111,14 @@ ps_status build_batch_graph(const ps_scene *scenes, int count, const ps_kernel_p
         s = capture_child(graph, &root, 1, capture,
                           [&](cudaStream_t st) {
                               ps_status e = PS_OK;
-                              if (kp)
+                              if (kp) {
+                                  // this scene's X' (Eq. objective1)
+                                  ps_kernel_params kq = *kp;
+                                  if (q.band_mask) kq.band_mask = q.band_mask;
                                   e = ps_estimate_kernel(q.lrms, q.pan, q.N, q.H, q.W, q.ratio,
-                                                         q.R, kp, nullptr, q.kernel, nullptr,
+                                                         q.R, &kq, nullptr, q.kernel, nullptr,
                                                          nullptr, sc.ws.base, sc.ws_bytes, st);
+                              }
                               if (e == PS_OK) e = solve_prelude(sc, st, &a);
                               return e;
                           },
@@ -1159,6 +1196,7 @@ void ps_default_kernel_params(ps_kernel_params *p) {
     p->rho = 0.5f;
     p->t_max = 10000;
     p->th = 1e-5f;
+    p->band_mask = 0ull;
 }
 
 void ps_default_hrms_params(ps_hrms_params *p) {
@@ -1195,6 +1233,16 @@ const char *ps_status_string(int s) {
         case PS_ERR_TIMEOUT: return "a bounded device-side wait gave up";
         default: return "unknown status";
     }
+}
+
+ps_status ps_sync_status(void *stream) {
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return PS_ERR_CUDA;
+    int h = 0;
+    const int zero = 0;
+    if (cudaMemcpyFromSymbol(&h, g_sticky_status, sizeof(int)) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_sticky_status, &zero, sizeof(int)) != cudaSuccess)
+        return PS_ERR_CUDA;
+    return (ps_status)h;
 }
 
 size_t ps_workspace_size(int N, int H, int W, int ratio, int R, const ps_hrms_params *hp) {
@@ -1252,6 +1300,7 @@ ps_status estimate_kernel_impl(const float *d_lrms, const float *d_pan, int N, i
     ps_status s;
     if ((s = check_dims(N, H, W, ratio, R)) != PS_OK) return s;
     if ((s = check_kernel_params(p)) != PS_OK) return s;
+    if ((s = check_band_mask(p->band_mask, N)) != PS_OK) return s;
     if (!d_lrms || !d_pan || !d_kernel) return PS_ERR_INVALID_ARG;
     Ws ws;
     if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
@@ -1269,17 +1318,18 @@ ps_status estimate_kernel_impl(const float *d_lrms, const float *d_pan, int N, i
     if (cudaEventRecord(k2.fork, st) != cudaSuccess ||
         cudaStreamWaitEvent(k2.s, k2.fork, 0) != cudaSuccess)
         return PS_ERR_CUDA;
+    // omega over the bands X' of Eq. objective1 (zeros for the others), so
+    // that f = X omega below is X' omega
     if (d_omega_in) {
-        if (omega != d_omega_in &&
-            cudaMemcpyAsync(omega, d_omega_in, N * sizeof(float), cudaMemcpyDeviceToDevice,
-                            k2.s) != cudaSuccess)
-            return PS_ERR_CUDA;
+        launch_omega_mask(d_omega_in, p->band_mask, N, omega, k2.s);
     } else {
+        const BandSel sel = band_sel(p->band_mask, N);
         float *Aw = ws.at<float>(ws.L.v);
-        launch_box_lr(d_lrms, N, h, w, p->l, Aw, k2.s);
+        launch_box_lr(d_lrms, sel, h, w, p->l, Aw, k2.s);
         launch_box_hr_dec(d_pan, H, W, c, c * p->l, ws.at<float>(ws.L.bvec), k2.s);
-        launch_omega_normal(Aw, ws.at<float>(ws.L.bvec), N, hw, ws.at<double>(ws.L.G), k2.s);
-        launch_omega_solve(ws.at<double>(ws.L.G), N, p->lambda_omega, omega, k2.s);
+        launch_omega_normal(Aw, ws.at<float>(ws.L.bvec), sel.n, hw, ws.at<double>(ws.L.G),
+                            k2.s);
+        launch_omega_solve(ws.at<double>(ws.L.G), sel, N, p->lambda_omega, omega, k2.s);
     }
     float *f = ws.at<float>(ws.L.f);
     launch_combine_f(d_lrms, omega, N, hw, f, k2.s);
@@ -1298,6 +1348,7 @@ ps_status estimate_kernel_impl(const float *d_lrms, const float *d_pan, int N, i
     int *ki = ws.at<int>(ws.L.kinfo);
     launch_admm(ws.at<float>(ws.L.Q), ws.at<double>(ws.L.zf), R, *p, d_kernel, ki, ki + 1,
                 reinterpret_cast<double *>(ki + 2), st);
+    launch_collect_status(nullptr, 0, ki, st);
     if ((s = last_launch()) != PS_OK) return s;
     if (h_info) return read_kernel_info(ws, st, h_info);
     return PS_OK;
@@ -1512,6 +1563,7 @@ ps_status ps_pansharpen(const float *d_lrms, const float *d_pan, int N, int H, i
     if ((s = check_fft_dims(H, W)) != PS_OK) return s;
     if ((s = check_hrms(hp)) != PS_OK) return s;
     if ((s = check_kernel_params(kp)) != PS_OK) return s;
+    if ((s = check_band_mask(kp->band_mask, N)) != PS_OK) return s;
     Ws ws;
     if ((s = bind_ws(d_ws, ws_bytes, N, H, W, ratio, R, &ws)) != PS_OK) return s;
     float *kern = d_kernel_out ? d_kernel_out : ws.at<float>(ws.L.kern);
@@ -1572,6 +1624,9 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
         const ps_scene &q = scenes[i];
         if ((s = check_dims(q.N, q.H, q.W, q.ratio, q.R)) != PS_OK) return s;
         if (!q.kernel) return PS_ERR_INVALID_ARG;
+        if (kp && (s = check_band_mask(q.band_mask ? q.band_mask : kp->band_mask, q.N)) !=
+                      PS_OK)
+            return s;
     }
     if (ws_bytes < ps_batch_workspace_size(scenes, count, hp)) return PS_ERR_WORKSPACE;
     char *base = static_cast<char *>(d_ws);
@@ -1620,6 +1675,7 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
         key_put(key, kp->rho);
         key_put(key, kp->t_max);
         key_put(key, kp->th);
+        key_put(key, kp->band_mask);
     }
     for (int i = 0; i < count; ++i) {
         const ps_scene &q = scenes[i];
@@ -1629,6 +1685,7 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
         key_put(key, q.kernel);
         const int dims[5] = {q.N, q.H, q.W, q.ratio, q.R};
         key_put(key, dims);
+        key_put(key, q.band_mask);
         const Tuning t = tuning_get(dev, q.N, q.H, q.W, q.ratio, hp->r);
         const int tk[5] = {t.prec_rows, t.llp_rows, t.split, t.llp_pf, t.llp_bands};
         key_put(key, tk);
@@ -2108,10 +2165,11 @@ ps_status ps_op_omega(const float *d_lrms, const float *d_pan, int N, int H, int
     cudaStream_t st = (cudaStream_t)stream;
     const int h = H / ratio, w = W / ratio;
     float *Aw = ws.at<float>(ws.L.v);
-    launch_box_lr(d_lrms, N, h, w, l, Aw, st);
+    const BandSel all = band_sel(0ull, N);
+    launch_box_lr(d_lrms, all, h, w, l, Aw, st);
     launch_box_hr_dec(d_pan, H, W, ratio, ratio * l, ws.at<float>(ws.L.bvec), st);
     launch_omega_normal(Aw, ws.at<float>(ws.L.bvec), N, h * w, ws.at<double>(ws.L.G), st);
-    launch_omega_solve(ws.at<double>(ws.L.G), N, lambda_omega, d_omega, st);
+    launch_omega_solve(ws.at<double>(ws.L.G), all, N, lambda_omega, d_omega, st);
     return last_launch();
 }
 
@@ -2156,6 +2214,7 @@ ps_status ps_op_admm(const double *d_EtE, const double *d_Etf, int R, const ps_k
     int *ki = ws.at<int>(ws.L.kinfo);
     launch_admm(ws.at<float>(ws.L.Q), ws.at<double>(ws.L.zf), R, *p, d_kernel, ki, ki + 1,
                 reinterpret_cast<double *>(ki + 2), st);
+    launch_collect_status(nullptr, 0, ki, st);
     if ((s = last_launch()) != PS_OK) return s;
     if (h_info) return read_kernel_info(ws, st, h_info);
     return PS_OK;

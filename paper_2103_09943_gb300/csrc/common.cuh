@@ -43,7 +43,16 @@ struct CgBand {
     unsigned int cnt_update;
     unsigned int cnt_init;
     unsigned int cnt_prec;    // CTAs of the preconditioner's last kernel (per band pair)
+    unsigned long long t_start;  // device global timer (ns) when the solve was reset
+    unsigned long long t_done;   // ... when the control kernel first saw the band stopped
 };
+
+// The device's global nanosecond timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    return v;
+}
 
 struct CgGlobal {
     double tol;               // relative residual target

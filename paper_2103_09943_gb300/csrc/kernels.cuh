@@ -208,12 +208,23 @@ void launch_bicubic_up(const float *X, int N, int h, int w, int c, float *out,
                        cudaStream_t st);
 
 // kest.cu
-void launch_box_lr(const float *X, int N, int h, int w, int l, float *out, cudaStream_t st);
+// The LRMS channels X' of Eq. objective1 a kernel estimate reads: n band
+// indices in increasing order (all N when the mask is 0).
+struct BandSel {
+    int n;
+    unsigned char idx[kMaxBands];
+};
+BandSel band_sel(unsigned long long mask, int N);
+void launch_box_lr(const float *X, const BandSel &sel, int h, int w, int l, float *out,
+                   cudaStream_t st);
 void launch_box_hr_dec(const float *Y, int H, int W, int c, int half, float *out,
                        cudaStream_t st);
 void launch_omega_normal(const float *A, const float *bv, int N, int hw, double *G,
                          cudaStream_t st);
-void launch_omega_solve(double *G, int N, float lambda_omega, float *omega, cudaStream_t st);
+void launch_omega_solve(double *G, const BandSel &sel, int N, float lambda_omega, float *omega,
+                        cudaStream_t st);
+void launch_omega_mask(const float *in, unsigned long long mask, int N, float *out,
+                       cudaStream_t st);
 void launch_combine_f(const float *X, const float *omega, int N, int hw, float *f,
                       cudaStream_t st);
 void launch_ete_lags(const float *Y, int H, int W, int c, int R, double *lags,

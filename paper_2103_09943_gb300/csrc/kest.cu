@@ -41,21 +41,31 @@ __device__ __forceinline__ void df_acc(float a, float b, float &s, float &c) {
 // ---------------------------------------------------------------------------
 // omega (Eq. objective3)
 // ---------------------------------------------------------------------------
-__global__ void box_lr_kernel(const float *__restrict__ X, int h, int w, int l,
+BandSel band_sel(unsigned long long mask, int N) {
+    BandSel s;
+    s.n = 0;
+    for (int b = 0; b < N && b < kMaxBands; ++b)
+        if (!mask || ((mask >> b) & 1ull)) s.idx[s.n++] = (unsigned char)b;
+    return s;
+}
+
+// B(u1) X'_z for the z-th selected band, into row z of `out`.
+__global__ void box_lr_kernel(const float *__restrict__ X, BandSel sel, int h, int w, int l,
                               float *__restrict__ out) {
-    const int b = blockIdx.z;
+    const int z = blockIdx.z, b = sel.idx[z];
     const int y = blockIdx.y * 8 + threadIdx.y, x = blockIdx.x * 32 + threadIdx.x;
     if (y >= h || x >= w) return;
     const float *Xb = X + (size_t)b * h * w;
     float s = 0.f;
     for (int dy = -l; dy <= l; ++dy)
         for (int dx = -l; dx <= l; ++dx) s += Xb[(size_t)wrapk(y + dy, h) * w + wrapk(x + dx, w)];
-    out[(size_t)b * h * w + (size_t)y * w + x] = s / (float)((2 * l + 1) * (2 * l + 1));
+    out[(size_t)z * h * w + (size_t)y * w + x] = s / (float)((2 * l + 1) * (2 * l + 1));
 }
 
-void launch_box_lr(const float *X, int N, int h, int w, int l, float *out, cudaStream_t st) {
-    dim3 blk(32, 8), grd((w + 31) / 32, (h + 7) / 8, N);
-    box_lr_kernel<<<grd, blk, 0, st>>>(X, h, w, l, out);
+void launch_box_lr(const float *X, const BandSel &sel, int h, int w, int l, float *out,
+                   cudaStream_t st) {
+    dim3 blk(32, 8), grd((w + 31) / 32, (h + 7) / 8, sel.n);
+    box_lr_kernel<<<grd, blk, 0, st>>>(X, sel, h, w, l, out);
 }
 
 // D B(u2) Y with u2 the (2 half + 1)^2 unit box: one thread per LR site.
@@ -117,9 +127,13 @@ void launch_omega_normal(const float *A, const float *bv, int N, int hw, double 
     omega_normal_kernel<<<nblk, 256, 0, st>>>(A, bv, N, hw, G);
 }
 
-// (A^T A + lambda_omega G^T G) omega = A^T b by Cholesky, one thread (N <= 64).
-__global__ void omega_solve_kernel(double *G, int N, float lam, float *omega) {
+// (A^T A + lambda_omega G^T G) omega = A^T b by Cholesky over the N'
+// selected bands, one thread (N' <= 64); G holds the N' x N' normal matrix,
+// G the first differences of consecutive selected weights. The weights go to
+// their bands' slots of omega (N entries), zeros to the other bands.
+__global__ void omega_solve_kernel(double *G, BandSel sel, int Nall, float lam, float *omega) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int N = sel.n;
     double *M = G;                 // N x N, overwritten
     double *rhs = G + (size_t)N * N;
     for (int i = 0; i < N; ++i) {
@@ -152,11 +166,25 @@ __global__ void omega_solve_kernel(double *G, int N, float lam, float *omega) {
         for (int t = i + 1; t < N; ++t) v -= M[(size_t)t * N + i] * rhs[t];
         rhs[i] = v / M[(size_t)i * N + i];
     }
-    for (int i = 0; i < N; ++i) omega[i] = (float)rhs[i];
+    for (int b = 0; b < Nall; ++b) omega[b] = 0.f;
+    for (int i = 0; i < N; ++i) omega[sel.idx[i]] = (float)rhs[i];
 }
 
-void launch_omega_solve(double *G, int N, float lambda_omega, float *omega, cudaStream_t st) {
-    omega_solve_kernel<<<1, 32, 0, st>>>(G, N, lambda_omega, omega);
+void launch_omega_solve(double *G, const BandSel &sel, int N, float lambda_omega, float *omega,
+                        cudaStream_t st) {
+    omega_solve_kernel<<<1, 32, 0, st>>>(G, sel, N, lambda_omega, omega);
+}
+
+// Given weights restricted to X': out[b] = in[b] for the bands of the mask
+// (all when 0), 0 for the others (in and out may be the same array).
+__global__ void omega_mask_kernel(const float *in, unsigned long long mask, int N, float *out) {
+    const int b = threadIdx.x;
+    if (b < N) out[b] = (!mask || ((mask >> b) & 1ull)) ? in[b] : 0.f;
+}
+
+void launch_omega_mask(const float *in, unsigned long long mask, int N, float *out,
+                       cudaStream_t st) {
+    omega_mask_kernel<<<1, 64, 0, st>>>(in, mask, N, out);
 }
 
 __global__ void combine_f_kernel(const float *__restrict__ X, const float *__restrict__ om,

@@ -607,8 +607,10 @@ void launch_llp(const LlpArgs &a, int mode, int r, int N, cudaStream_t st) {
 __global__ void cg_reset_kernel(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter,
                                 int precond, int rule) {
     const int t = threadIdx.x;
+    const unsigned long long now = global_ns();
     for (int b = t; b < N; b += blockDim.x) {
         CgBand z = {};
+        z.t_start = now;
         bands[b] = z;
     }
     // every loop-control record of the solve (one per branch loop), alike
@@ -799,6 +801,9 @@ __global__ void cg_control_kernel(CgBand *bands, CgGlobal *g, int N, int use_con
         active += __shfl_xor_sync(0xffffffffu, active, o);
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
+    // lane 0 decides; every lane then stamps its bands' stop time (a band
+    // that stopped in this iteration, or every band when the loop ends here)
+    int ending = 0;
     if (lane == 0) {
         unsigned int cond = 1u;
         if (g->stop) {
@@ -810,10 +815,15 @@ __global__ void cg_control_kernel(CgBand *bands, CgGlobal *g, int N, int use_con
             if (active == 0 || g->iter >= g->max_iter) {
                 g->stop = 1;
                 cond = 0u;
+                ending = 1;
             }
         }
         if (use_cond) cudaGraphSetConditional(handle, cond);
     }
+    ending = __shfl_sync(0xffffffffu, ending, 0);
+    const unsigned long long now = global_ns();
+    for (int b = lane; b < N; b += 32)
+        if (bands[b].t_done == 0ull && (bands[b].done || ending)) bands[b].t_done = now;
 }
 
 void launch_cg_reset(CgBand *bands, CgGlobal *g, int N, double tol, int max_iter, int precond,

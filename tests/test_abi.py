@@ -170,6 +170,15 @@ def test_argument_errors_return_before_launch(lib):
     st = lib.ps_pansharpen(fake, fake, 4, 256, 256, 4, 17, ctypes.byref(kp), ctypes.byref(hp),
                            fake, None, None, None, fake, 1 << 30, None)
     assert st == 1                                                  # R > 16
+    # the X' mask of Eq. objective1 may select only bands that exist
+    bk = KernelParams.from_buffer_copy(kp)
+    bk.band_mask = 1 << 4                                           # band 4 of 4
+    st = lib.ps_estimate_kernel(fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bk), None, fake,
+                                None, None, fake, 1 << 30, None)
+    assert st == 1
+    st = lib.ps_pansharpen(fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bk), ctypes.byref(hp),
+                           fake, None, None, None, fake, 1 << 30, None)
+    assert st == 1
 
 
 def test_noalloc_shape_limits_are_its_twins(lib):
@@ -229,6 +238,16 @@ def test_batched_argument_errors_return_before_launch(lib):
     arr[1].H = 768
     arr[2].kernel = None
     assert lib.ps_pansharpen_batched(arr, 3, ctypes.byref(kp), ctypes.byref(hp), None, None,
+                                     ws, need, None) == 1
+    arr[2].kernel = f
+    # a scene's X' mask selects bands that exist in that scene
+    arr[0].band_mask = 1 << 5                                       # scene 0 has 4 bands
+    assert lib.ps_pansharpen_batched(arr, 3, ctypes.byref(kp), ctypes.byref(hp), None, None,
+                                     ws, need, None) == 1
+    arr[0].band_mask = 0
+    bk = KernelParams.from_buffer_copy(kp)
+    bk.band_mask = 1 << 6                                           # fine for the 8-band scene only
+    assert lib.ps_pansharpen_batched(arr, 3, ctypes.byref(bk), ctypes.byref(hp), None, None,
                                      ws, need, None) == 1
 
 

@@ -27,13 +27,14 @@ def test_launch_count_by_hand():
     iters = [47, 50, 44, 47, 48, 44, 47, 47]
     # kernel estimate: omega 4, f + lags + assembly + E^T f 4, Cholesky of
     # 289 unknowns in 10 panels (add_diag, 10 diagonal tiles, 9 panels, 9
-    # updates), solve, inverse, ADMM
-    kest = 4 + 4 + (1 + 10 + 9 + 9) + 3
+    # updates), solve, inverse, ADMM, status collector
+    kest = 4 + 4 + (1 + 10 + 9 + 9) + 3 + 1
     # four branch loops of band pairs; maxima 50, 47, 48, 47 -> 13, 12, 12, 12
     # bodies of four iterations of 7 kernels
     loop = 7 * 4 * (13 + 12 + 12 + 12)
-    # PAN stats, spectrum 4, rhs, reset, init, z0 = P^-1 r0 (3), FP32 Z step 4
-    solve = 1 + 4 + 1 + 2 + 3 + loop + 4
+    # PAN stats, spectrum 4, rhs, reset, init, z0 = P^-1 r0 (3), FP32 Z step 4,
+    # status collector
+    solve = 1 + 4 + 1 + 2 + 3 + loop + 4 + 1
     warm = 1 + 9 + 2
     assert b.launches_per_step(cfg, hp, iters, 4) == kest + solve + warm
     # one loop over all bands: max 50 -> 13 bodies

@@ -79,3 +79,43 @@ def test_planted_kernel_recovery_on_gpu(cuda):
     k, _, info = api.estimate_kernel(to_dev(X, cuda), to_dev(Y, cuda), 4, 3, kp,
                                      omega=to_dev(w, cuda))
     assert oracle.kernel_error_pct(to_np(k), u_true) < 1.0
+
+
+def test_estimate_kernel_on_a_band_subset(cuda):
+    # X' of Eq. objective1 a strict subset (bands 0 and 2 of the 4-band
+    # scene): omega over X' (zeros for the other bands), f = X' omega, the
+    # ADMM on the resulting normal equations; against the oracle's estimate
+    # over the same subset. The same mask through ps_pansharpen, with omega
+    # given (entries outside X' ignored), and per scene in a batch.
+    sc = synth.make_scene("c0")
+    cfg = sc["config"]
+    bands = [0, 2]
+    kp = api.default_kernel_params(band_mask=api.band_mask(bands))
+    X, Y = to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda)
+    ref_k, ref_om, res = oracle.estimate_kernel(sc["lrms"], sc["pan"], cfg.ratio, cfg.R,
+                                                bands=bands)
+    k, om, info = api.estimate_kernel(X, Y, cfg.ratio, cfg.R, kp)
+    om, k = to_np(om), to_np(k)
+    assert rel(om[bands], ref_om) < 1e-5
+    assert np.all(om[[1, 3]] == 0.0)
+    assert rel(k, ref_k) < 1e-4
+    assert info.iters == pytest.approx(res.iters, abs=3)
+    # the subset changes the estimate: omega over all bands differs
+    _, om_all, _ = api.estimate_kernel(X, Y, cfg.ratio, cfg.R)
+    assert rel(to_np(om_all)[bands], ref_om) > 1e-3
+    # omega given: the entries of bands outside X' do not count
+    om_in = to_dev(np.array([0.3, 5.0, 0.7, -2.0]), cuda)
+    k2, om2, _ = api.estimate_kernel(X, Y, cfg.ratio, cfg.R, kp, omega=om_in)
+    ref_k2, _, _ = oracle.estimate_kernel(sc["lrms"], sc["pan"], cfg.ratio, cfg.R,
+                                          omega=np.array([0.3, 0.7]), bands=bands)
+    assert rel(to_np(k2), ref_k2) < 1e-4
+    assert np.allclose(to_np(om2), [0.3, 0.0, 0.7, 0.0])
+    # ps_pansharpen and a batch (the scene's own mask) take the same X'
+    _, k3, _, _ = api.pansharpen(X, Y, cfg.ratio, cfg.R, kparams=kp)
+    assert rel(to_np(k3), k) < 1e-6
+    b = api.Batch([(X, Y, cfg.R, api.band_mask(bands)), (X, Y, cfg.R)], cfg.ratio,
+                  kparams=api.default_kernel_params())
+    b.run()
+    assert rel(to_np(b.kernels[0]), k) < 1e-6
+    k_all, _, _ = api.estimate_kernel(X, Y, cfg.ratio, cfg.R)
+    assert rel(to_np(b.kernels[1]), to_np(k_all)) < 1e-6

@@ -200,3 +200,48 @@ def test_zstep_fp32_within_its_bound(cuda, c0_oracle):
         assert rel(out[1][1][b], out[0][1][b]) < 1e-6   # same Z0
         assert rel(out[1][0][b], out[0][0][b]) < 3e-5
         assert rel(out[1][0][b], ref["Z"][b]) < 3e-5
+
+
+def test_sticky_status_after_calls_without_info(cuda):
+    # Calls without h_info return before their work runs; ps_sync_status waits
+    # for the stream and reports (then clears) the first device-detected
+    # status of the calls since the last read: here a band stopped on a
+    # non-finite value, then nothing.
+    sc = _scene(synth.CONFIGS["c0"])
+    cfg = sc["config"]
+    Xd, Yd = to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda)
+    Kd = to_dev(sc["kernel"], cuda)
+    assert api.sync_status() in (0, 5, 6, 7)     # whatever earlier tests left
+    api.solve_hrms(Xd, Yd, Kd, cfg.ratio, info=False)
+    assert api.sync_status() == 0
+    X = sc["lrms"].copy()
+    X[2, 5, 7] = np.nan
+    api.solve_hrms(to_dev(X, cuda), Yd, Kd, cfg.ratio, info=False)
+    api.solve_hrms(Xd, Yd, Kd, cfg.ratio, api.default_hrms_params(tol=1e-12, max_iter=3),
+                   info=False)
+    assert api.sync_status() == 6                 # the first one recorded
+    assert api.sync_status() == 0                 # and cleared
+    api.solve_hrms(Xd, Yd, Kd, cfg.ratio, api.default_hrms_params(tol=1e-12, max_iter=3),
+                   info=False)
+    assert api.sync_status() == 5
+
+
+def test_band_solve_times(cuda):
+    # Per-band device time of the Z0 solve: positive, within the call's own
+    # time, and longer for a band that ran more iterations in the same loop.
+    sc = _scene(synth.CONFIGS["c0"])
+    cfg = sc["config"]
+    X = sc["lrms"].copy()
+    X[1] = 0.0                                  # stops before its first iteration
+    hp = api.default_hrms_params(precond=0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    _, _, info = api.solve_hrms(to_dev(X, cuda), to_dev(sc["pan"], cuda),
+                                to_dev(sc["kernel"], cuda), cfg.ratio, hp)
+    b.record()
+    torch.cuda.synchronize()
+    total = a.elapsed_time(b)
+    ms = info.ms
+    assert all(0.0 < t <= total * 1.05 for t in ms), (ms, total)
+    assert ms[1] < min(ms[0], ms[2], ms[3]), ms
+    assert info.iters[1] == 0 and min(info.iters[0], info.iters[2], info.iters[3]) > 20

@@ -152,6 +152,29 @@ def test_omega_exact_recovery_without_blur():
     np.testing.assert_allclose(om, w, rtol=1e-9)
 
 
+def test_omega_over_a_band_subset():
+    # X' of Eq. objective1: a PAN made of bands {0, 2} only. Over that subset
+    # the weights are recovered exactly (no blur, no noise, l = 0); the
+    # kernel estimate restricted to it combines only those bands, and with
+    # the weights given it equals the estimate from f = X' omega by hand.
+    Z, _, X, u, w = _noiseless_scene(blur=True, H=64)
+    bands = [0, 2]
+    wt = np.array([0.6, 0.4])
+    Y = np.tensordot(wt, Z[bands], axes=1)
+    Xn = Z[:, ::4, ::4]                  # unblurred LRMS for the exact recovery
+    np.testing.assert_allclose(oracle.estimate_omega(Xn, Y, 4, 0, 0.0, bands=bands), wt,
+                               rtol=1e-9)
+    # all four bands: the least-squares fit still finds the PAN's mix
+    om4 = oracle.estimate_omega(Xn, Y, 4, 0, 0.0)
+    np.testing.assert_allclose(om4[bands], wt, rtol=1e-6)
+    np.testing.assert_allclose(om4[[1, 3]], 0.0, atol=1e-6)
+    kp = oracle.KernelParams(t_max=200)
+    k_sub, om_sub, _ = oracle.estimate_kernel(X, Y, 4, 3, kp, omega=wt, bands=bands)
+    f = np.tensordot(wt, X[bands], axes=1)
+    EtE, Etf = oracle.kernel_normal_eq(Y, f, 4, 3)
+    np.testing.assert_allclose(k_sub, oracle.admm(EtE, Etf, 3, kp).kernel, atol=1e-14)
+
+
 def test_omega_regularised_matches_lstsq():
     from scipy import ndimage
     Z, Y, X, _, w = _noiseless_scene(H=64)
