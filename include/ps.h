@@ -202,6 +202,12 @@ typedef struct ps_tuning {
     float split_us[3];   /* two CG iterations, candidates 1, 2, 4 branches   */
     int llp_bands;       /* bands per CTA of that LLP kernel (1, 2)          */
     float llp2_us[2];    /* two bands per CTA: long, short walk (2 ahead)    */
+    int prec_impl;       /* preconditioner passes: 1 shared-memory (any size),
+                            2 register-resident (power-of-two sides 256 ..
+                            4096, ratios 2 and 4); 0 the default (2 where it
+                            applies)                                        */
+    float prec_impl_us[2]; /* one application: candidates 1 (its best row
+                            count), 2                                        */
 } ps_tuning;
 
 /* Autotuner: times every candidate of each tunable kernel on N bands of
@@ -218,7 +224,8 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r,
 /* The launch choices recorded for these sizes on the current device (all
  * zero: the defaults), and their replacement, e.g. with choices an earlier
  * process's ps_autotune found. Only the choice fields (prec_rows, llp_rows,
- * llp_pf, split, llp_bands) are read or written; 0 keeps a default. */
+ * llp_pf, split, llp_bands, prec_impl) are read or written; 0 keeps a
+ * default. */
 ps_status ps_get_tuning(int N, int H, int W, int ratio, int r, ps_tuning *h_out);
 ps_status ps_set_tuning(int N, int H, int W, int ratio, int r, const ps_tuning *h_in);
 

@@ -71,8 +71,9 @@ ps_status ps_op_zstep(const float *d_lrms, const float *d_z0, int N, int H,
  * z_b = P^{-1} r_b with P = B^T D^T D B + lambda_gamma L^T L, the operator of
  * Eq. Z_solution at weight lambda_gamma, solved exactly in the Fourier domain
  * per alias group of ratio^2 frequencies, FP32. N x H x W in and out (device,
- * caller-owned, not aliased). H, W of the form 2^a 3^b.
- * Workspace: ps_op_workspace_size. */
+ * caller-owned, not aliased). H, W of the form 2^a 3^b. The passes are those
+ * ps_set_tuning recorded for (N, H, W, ratio, r = 1) (prec_impl, prec_rows),
+ * else the defaults. Workspace: ps_op_workspace_size. */
 ps_status ps_op_precond(const float *d_r, int N, int H, int W, int ratio,
                         const float *d_kernel, int R, float lambda_gamma,
                         float *d_z, void *d_ws, size_t ws_bytes, void *stream);

@@ -97,12 +97,15 @@ def autotune(N, H, W, ratio, R, r=1, ws=None, device=None, lrms=None, pan=None,
             "llp_bands": t.llp_bands,
             "llp2_us": {w: round(v, 2) for w, v in zip(("long/2", "short/2"), t.llp2_us) if v},
             "split": t.split,
-            "split_us": {str(k): round(v, 2) for k, v in zip((1, 2, 4), t.split_us) if v}}
+            "split_us": {str(k): round(v, 2) for k, v in zip((1, 2, 4), t.split_us) if v},
+            "prec_impl": t.prec_impl,
+            "prec_impl_us": {n: round(v, 2) for n, v in zip(("smem", "reg"), t.prec_impl_us)
+                             if v}}
 
 
 def set_tuning(N, H, W, ratio, r=1, **choices) -> None:
     """Record launch choices for these sizes (ps_set_tuning): prec_rows,
-    llp_rows, llp_pf, split, llp_bands; 0 or absent keeps a default."""
+    llp_rows, llp_pf, split, llp_bands, prec_impl; 0 or absent keeps a default."""
     t = Tuning()
     for k, v in choices.items():
         setattr(t, k, v)
@@ -112,7 +115,8 @@ def set_tuning(N, H, W, ratio, r=1, **choices) -> None:
 def get_tuning(N, H, W, ratio, r=1) -> dict:
     t = Tuning()
     _check(_lib.load().ps_get_tuning(N, H, W, ratio, r, ctypes.byref(t)))
-    return {k: getattr(t, k) for k in ("prec_rows", "llp_rows", "llp_pf", "split", "llp_bands")}
+    return {k: getattr(t, k) for k in ("prec_rows", "llp_rows", "llp_pf", "split", "llp_bands",
+                                       "prec_impl")}
 
 
 @dataclass

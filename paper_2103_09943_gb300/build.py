@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libps.so")
-SOURCES = ["operators.cu", "cg_fast.cu", "llp2.cu", "fft.cu", "precond.cu", "warm.cu", "cnn.cu", "cnn_core.cu", "kest.cu", "api.cu", "noalloc.cu", "tune.cu", "prior.cu", "cg_fast_wide.cu", "precond_wide.cu", "diag.cu"]
+SOURCES = ["operators.cu", "cg_fast.cu", "llp2.cu", "fft.cu", "precond.cu", "warm.cu", "cnn.cu", "cnn_core.cu", "kest.cu", "api.cu", "noalloc.cu", "tune.cu", "prior.cu", "cg_fast_wide.cu", "precond_wide.cu", "diag.cu", "precond_reg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include"), "-I" + SRC]

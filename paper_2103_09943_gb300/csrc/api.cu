@@ -443,6 +443,7 @@ void enqueue_bands(const CgLoopArgs &a, int b0, int n, const float *p_old, float
         pa.N = n;
         pa.bands = bands;
         pa.rows = a.tune.prec_rows;
+        pa.impl = a.tune.prec_impl;
         launch_precond(pa, st);
     }
 }
@@ -1426,6 +1427,7 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
                                  2e-4f, nullptr, nullptr);
     const int trs[4] = {1, 2, 4, 8};
     float bestp = 1e30f;
+    pa.impl = 1;  // the shared-memory passes, whose row passes take this knob
     for (int k = 0; k < 4; ++k) {
         if (!precond_rows_ok(H, W, ratio, trs[k])) continue;
         pa.rows = trs[k];
@@ -1434,6 +1436,15 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
             bestp = out.prec_us[k];
             out.prec_rows = trs[k];
         }
+    }
+    // the register-resident passes against the best of those
+    out.prec_impl = 1;
+    out.prec_impl_us[0] = bestp;
+    if (precond_reg_supported(H, W, ratio)) {
+        pa.impl = 2;
+        pa.rows = 0;
+        out.prec_impl_us[1] = timed([&] { launch_precond(pa, st); });
+        if (out.prec_impl_us[1] < bestp) out.prec_impl = 2;
     }
     LlpArgs la = {};
     la.in = ws.at<float>(ws.L.pA);
@@ -1492,7 +1503,7 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
             if (splits[k] > 1 && N < 2 * splits[k]) continue;
             tuning_set(dev, N, H, W, ratio, r,
                        Tuning{out.prec_rows, out.llp_rows, splits[k], out.llp_pf,
-                              out.llp_bands});
+                              out.llp_bands, out.prec_impl});
             float best = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, st);
@@ -1516,7 +1527,8 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
     cudaEventDestroy(e1);
     if ((s = last_launch()) != PS_OK) return s;
     tuning_set(dev, N, H, W, ratio, r,
-               Tuning{out.prec_rows, out.llp_rows, out.split, out.llp_pf, out.llp_bands});
+               Tuning{out.prec_rows, out.llp_rows, out.split, out.llp_pf, out.llp_bands,
+                      out.prec_impl});
     if (h_out) *h_out = out;
     return PS_OK;
 }
@@ -1532,6 +1544,7 @@ ps_status ps_get_tuning(int N, int H, int W, int ratio, int r, ps_tuning *h_out)
     h_out->llp_pf = t.llp_pf;
     h_out->split = t.split;
     h_out->llp_bands = t.llp_bands;
+    h_out->prec_impl = t.prec_impl;
     return PS_OK;
 }
 
@@ -1547,10 +1560,13 @@ ps_status ps_set_tuning(int N, int H, int W, int ratio, int r, const ps_tuning *
     if (t.llp_pf && t.llp_pf != 2 && t.llp_pf != 4 && t.llp_pf != 6) return PS_ERR_INVALID_ARG;
     if (t.split && t.split != 1 && t.split != 2 && t.split != 4) return PS_ERR_INVALID_ARG;
     if (t.llp_bands && t.llp_bands != 1 && t.llp_bands != 2) return PS_ERR_INVALID_ARG;
+    if (t.prec_impl < 0 || t.prec_impl > 2 ||
+        (t.prec_impl == 2 && !precond_reg_supported(H, W, ratio)))
+        return PS_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PS_ERR_CUDA;
     tuning_set(dev, N, H, W, ratio, r, Tuning{t.prec_rows, t.llp_rows, t.split, t.llp_pf,
-                                              t.llp_bands});
+                                              t.llp_bands, t.prec_impl});
     return PS_OK;
 }
 
@@ -1687,7 +1703,8 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
         key_put(key, dims);
         key_put(key, q.band_mask);
         const Tuning t = tuning_get(dev, q.N, q.H, q.W, q.ratio, hp->r);
-        const int tk[5] = {t.prec_rows, t.llp_rows, t.split, t.llp_pf, t.llp_bands};
+        const int tk[6] = {t.prec_rows, t.llp_rows, t.split, t.llp_pf, t.llp_bands,
+                           t.prec_impl};
         key_put(key, tk);
     }
     cudaGraphExec_t exec = nullptr;
@@ -2147,8 +2164,13 @@ ps_status ps_op_precond(const float *d_r, int N, int H, int W, int ratio, const 
     if ((s = ensure_device(nullptr)) != PS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = prepare_spectrum(ws, d_kernel, H, W, R, st)) != PS_OK) return s;
-    launch_precond(make_prec_args(ws, d_r, d_z, N, H, W, ratio, lambda_gamma, nullptr, nullptr),
-                   st);
+    PrecArgs pa = make_prec_args(ws, d_r, d_z, N, H, W, ratio, lambda_gamma, nullptr, nullptr);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PS_ERR_CUDA;
+    const Tuning t = tuning_get(dev, N, H, W, ratio, 1);  // the recorded implementation
+    pa.impl = t.prec_impl;
+    pa.rows = t.prec_rows;
+    launch_precond(pa, st);
     return last_launch();
 }
 

@@ -134,8 +134,15 @@ struct PrecArgs {
     CgBand *bands;        // NULL: plain operator (no r^T z, no skipping)
     const CgGlobal *g;
     int rows;             // rows per CTA of the row passes (0: the plan's choice)
+    int impl;             // 0: register-resident passes where supported, else the
+                          // shared-memory ones; 1: shared-memory; 2: register-resident
 };
 bool precond_supported(int H, int W, int c);
+// precond_reg.cu: the register-resident passes (power-of-two sides 256..4096,
+// ratios 2 and 4); launch_precond_reg returns false for other sizes
+bool precond_reg_supported(int H, int W, int c);
+bool launch_precond_reg(const PrecArgs &a, cudaStream_t st);
+cudaError_t precond_reg_set_attrs();
 bool precond_rows_ok(int H, int W, int c, int tr);
 void launch_precond(const PrecArgs &a, cudaStream_t st);
 void launch_spectrum_to_f32(const double2 *in, float2 *out, size_t n, cudaStream_t st);
@@ -198,6 +205,7 @@ struct Tuning {
     int split;      // parallel branches of the CG iteration (0: default)
     int llp_pf;     // rows the LLP kernel's loads run ahead (0: default)
     int llp_bands;  // bands per CTA of the CG-loop LLP kernel (0: 1)
+    int prec_impl;  // preconditioner passes: 0 default, 1 shared-memory, 2 register-resident
 };
 Tuning tuning_get(int dev, int N, int H, int W, int c, int r);
 void launch_fill(float *p, size_t n, float v, cudaStream_t st);

@@ -592,6 +592,7 @@ bool precond_supported(int H, int W, int c) {
 }
 
 void launch_precond(const PrecArgs &a, cudaStream_t st) {
+    if (a.impl != 1 && launch_precond_reg(a, st)) return;
     PrecPlan pl;
     if (!make_prec_plan(a.H, a.W, a.c, &pl)) return;  // callers check precond_supported
     if (a.rows && a.rows != pl.rg.TR && prec_rows_valid(pl, a.H, a.W, a.rows)) {
@@ -648,6 +649,7 @@ cudaError_t precond_set_attrs() {
     if (e == cudaSuccess) e = set_attrs_c<6>();
     if (e == cudaSuccess) e = set_attrs_c<8>();
     if (e == cudaSuccess) e = precond_set_attrs_wide();
+    if (e == cudaSuccess) e = precond_reg_set_attrs();
     return e;
 }
 #endif  // PS_PREC_WIDE

@@ -1,0 +1,547 @@
+// Register-resident passes of the Z0 preconditioner P^{-1} (and of the FP32
+// Z step, which applies the same operator at weight lambda) for power-of-two
+// sides 256 .. 4096 and ratios 2 and 4; other sizes keep the shared-memory
+// passes of precond.cu.
+//
+// P = B^T D^T D B + lam L^T L is block diagonal over alias groups of c^2
+// frequencies (ky0 + p h, kx0 + q w), p, q < c (Eq. Z_solution's structure):
+// z = P^{-1} r is a forward 2-D FFT, one rank-one solve per group, an inverse
+// 2-D FFT. Three kernels, as before: row FFTs of r (two bands packed as one
+// complex image) stored transposed, the column pass (column FFTs, the group
+// solves, inverse column FFTs), and the inverse row FFTs with z and r^T z.
+//
+// Each length-L transform (L = 16 T) is held by T threads, 16 values each,
+// in registers: three Stockham stages (radix 16, 16, L / 256; two for
+// L = 256) with two exchanges (one) through shared memory. The first stage reads its inputs,
+// positions t + T e (e < 16), straight from global memory, and the last
+// leaves its outputs, positions t + T i (i < 16), in registers. In the
+// column pass the members ky0 + p h of a group then lie in the registers of
+// one thread for every column q (h is a multiple of T when c divides 16), and
+// the c threads of the c columns sit in adjacent lanes: the group solve runs
+// in registers with lane shuffles, and the inverse transform starts from the
+// registers it leaves.
+#include <math.h>
+
+#include "common.cuh"
+#include "fft_dev.cuh"
+#include "kernels.cuh"
+
+namespace ps {
+
+namespace {
+
+constexpr int kRegRows = 4;  // rows per CTA of the row passes
+
+// Shared-memory row stride (float2) for a padded row of length L: prow_len
+// rounded up to 4 mod 16, so that rows r = 0..3 of a CTA start 8 r banks
+// apart and the accesses of a warp (4 rows x 8 consecutive positions) take
+// the minimum two wavefronts.
+__host__ __device__ constexpr int reg_ld(int L) {
+    return ((prow_len(L) + 11) / 16) * 16 + 4;
+}
+
+__device__ __forceinline__ float2 cmul2(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // conj(a) b
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+// w^e for e = 1 .. R-1 from the table tw (tw[m] = exp(-2 pi i m / L)):
+// w = tw[k s] and its powers 2, 4, 8 read from the table, the others their
+// products (at most three factors), conjugated for the inverse.
+template <int R>
+__device__ __forceinline__ void twiddle_powers(const float2 *__restrict__ tw, int ks, int L,
+                                               bool inverse, float2 (&w)[R]) {
+    const float sgn = inverse ? -1.0f : 1.0f;
+    auto ld = [&](int m) {
+        float2 v = __ldg(tw + (m & (L - 1)));
+        v.y *= sgn;
+        return v;
+    };
+    w[0] = make_float2(1.f, 0.f);
+    if (R > 1) w[1] = ld(ks);
+    if (R > 2) w[2] = ld(2 * ks);
+    if (R > 4) w[4] = ld(4 * ks);
+    if (R > 8) w[8] = ld(8 * ks);
+#pragma unroll
+    for (int e = 3; e < R; ++e) {
+        if (e == 4 || e == 8) continue;
+        const int hi = (e >= 8) ? 8 : ((e >= 4) ? 4 : 2);
+        w[e] = cmul2(w[hi], w[e - hi]);
+    }
+}
+
+// One Stockham stage of radix R on the 16 values of this thread: butterfly
+// b (j = t + b T, k = j mod Ns) holds its R inputs in v[b R + e]. Twiddles
+// w_{Ns R}^{e k}, then the radix-R DFT in registers.
+template <int L, int R>
+__device__ __forceinline__ void reg_stage(float2 (&v)[16], int t, int Ns,
+                                          const float2 *__restrict__ tw, bool inverse) {
+    constexpr int T = L / 16, NB = 16 / R;
+    const float sg = inverse ? 1.0f : -1.0f;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = t + b * T, k = j & (Ns - 1);
+        if (Ns > 1) {
+            float2 w[R];
+            twiddle_powers<R>(tw, k * (L / (Ns * R)), L, inverse, w);
+#pragma unroll
+            for (int e = 1; e < R; ++e) v[b * R + e] = cmul2(v[b * R + e], w[e]);
+        }
+        dft_reg<R>(&v[b * R], sg);
+    }
+}
+
+// Outputs of a stage (Ns, R) to the shared row: element e of butterfly j to
+// position (j - k) R + k + e Ns.
+template <int L, int R>
+__device__ __forceinline__ void reg_write(float2 *a, const float2 (&v)[16], int t, int Ns) {
+    constexpr int T = L / 16, NB = 16 / R;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = t + b * T, k = j & (Ns - 1), base = (j - k) * R + k;
+#pragma unroll
+        for (int e = 0; e < R; ++e) a[prow(base + e * Ns)] = v[b * R + e];
+    }
+}
+
+// Inputs of a radix-R stage from the shared row: element e of butterfly j at
+// position j + e L / R.
+template <int L, int R>
+__device__ __forceinline__ void reg_read(const float2 *a, float2 (&v)[16], int t) {
+    constexpr int T = L / 16, NB = 16 / R, M = L / R;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = t + b * T;
+#pragma unroll
+        for (int e = 0; e < R; ++e) v[b * R + e] = a[prow(j + e * M)];
+    }
+}
+
+// The whole transform of one row of length L in place on v: inputs v[e] at
+// positions t + T e, outputs v[i] at positions t + T i. `a` is this row's
+// shared buffer (prow-padded). Every thread of the CTA must call it; it
+// begins with the first stage in registers and ends in registers. With
+// `reused`, a barrier precedes its first shared write (the buffer is still
+// being read by a previous transform); none follows its last read.
+template <int L>
+__device__ __forceinline__ void reg_fft(float2 (&v)[16], float2 *a, int t,
+                                        const float2 *__restrict__ tw, bool inverse,
+                                        bool reused) {
+    // L = 256: stages 16, 16; L >= 512: 16, 16, L / 256
+    constexpr int R3 = (L >= 512) ? L / 256 : 1, NB3 = 16 / R3;
+    static_assert(L >= 256 && L <= 4096 && (L & (L - 1)) == 0, "register FFT lengths");
+    reg_stage<L, 16>(v, t, 1, tw, inverse);
+    if (reused) __syncthreads();
+    reg_write<L, 16>(a, v, t, 1);
+    __syncthreads();
+    reg_read<L, 16>(a, v, t);
+    reg_stage<L, 16>(v, t, 16, tw, inverse);
+    if (L == 256) return;  // the second stage was the last: v[e] at t + 16 e
+    __syncthreads();
+    reg_write<L, 16>(a, v, t, 16);
+    __syncthreads();
+    reg_read<L, R3>(a, v, t);
+    reg_stage<L, R3>(v, t, 256, tw, inverse);
+    // butterfly b's output e sits at t + T (b + e NB3): reorder to v[i]
+    if (NB3 > 1) {
+        float2 o[16];
+#pragma unroll
+        for (int b = 0; b < NB3; ++b)
+#pragma unroll
+            for (int e = 0; e < R3; ++e) o[b + e * NB3] = v[b * R3 + e];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = o[i];
+    }
+}
+
+
+__device__ __forceinline__ bool reg_image_idle(const PrecArgs &a, int k) {
+    if (!a.bands) return false;
+    if (a.g->stop) return true;
+    const bool d0 = a.bands[2 * k].done != 0;
+    const bool d1 = (2 * k + 1 >= a.N) || a.bands[2 * k + 1].done != 0;
+    return d0 && d1;
+}
+
+// Lane layout of the row passes: the kRegRows rows of a CTA interleave in
+// every warp (row = lane mod kRegRows), so that the transposed spectrum
+// accesses of a warp cover whole 32-byte runs of kRegRows rows.
+__device__ __forceinline__ void row_lane(int &row, int &t) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    row = lane % kRegRows;
+    t = lane / kRegRows + (32 / kRegRows) * warp;
+}
+
+// ---------------------------------------------------------------------------
+// Forward row pass: rows y0 .. y0 + 3 of bands 2k (real part) and 2k + 1
+// (imaginary part), stored transposed: spec[k][kx][y].
+// ---------------------------------------------------------------------------
+// (every shape at <= 64 registers a thread: 1024 threads, 32 warps, an SM)
+template <int W>
+__global__ void __launch_bounds__(kRegRows * W / 16, 1024 / (kRegRows * W / 16))
+    prec_rows_fwd_reg_kernel(PrecArgs a) {
+    constexpr int T = W / 16, LD = reg_ld(W);
+    extern __shared__ __align__(16) float2 rsm[];
+    const int k = blockIdx.y;
+    if (reg_image_idle(a, k)) return;
+    int row, t;
+    row_lane(row, t);
+    const int H = a.H, y = blockIdx.x * kRegRows + row;
+    const size_t HW = (size_t)H * W;
+    // a finished band enters as zeros, so that it cannot disturb the band it
+    // shares the image with
+    const float *r0 = a.r + (size_t)(2 * k) * HW + (size_t)y * W;
+    const float *r1 = (2 * k + 1 < a.N) ? r0 + HW : nullptr;
+    if (a.bands && a.bands[2 * k].done) r0 = nullptr;
+    if (a.bands && r1 && a.bands[2 * k + 1].done) r1 = nullptr;
+    float2 v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int x = t + T * e;
+        v[e] = make_float2(r0 ? __ldg(r0 + x) : 0.f, r1 ? __ldg(r1 + x) : 0.f);
+    }
+    reg_fft<W>(v, rsm + row * LD, t, a.twW, false, false);
+    float2 *S = a.spec + (size_t)k * HW + y;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) S[(size_t)(t + T * i) * H] = v[i];
+}
+
+// ---------------------------------------------------------------------------
+// Column pass: columns kx0 + q w (q < C) of image k. Lane q + C u of warp
+// w serves column q, t = u + (32 / C) w.
+// ---------------------------------------------------------------------------
+__constant__ float2 c_cs32[16];  // (cos, sin) of pi i / 16
+
+// The group solve of ((1/C^2) v v^H + diag(t)) x = s for every group whose
+// members this thread holds (ky0 = t + T g, p = 0 .. C-1 at ky0 + p h, in
+// registers v[g + (16 / C) p]); the C columns are the C adjacent lanes.
+// v_j = conj(B^_j), t_j = lam S^_j^2, S^ = 4 sin^2(pi ky / H) + 4 sin^2(pi kx
+// / W). With m the member of smallest t (the separable minimum: smallest
+// sin^2 in ky, then in kx) the system is solved as the Z step's rank-one
+// form, which stays exact for t_m = 0 (the DC group):
+//   s = (conj(v_m) r_m + t_m n) / (t_m + (|v_m|^2 + t_m d) / C^2),
+//   n = sum_{j != m} conj(v_j) r_j / t_j,  d = sum_{j != m} |v_j|^2 / t_j,
+//   x_j = (r_j - v_j s / C^2) / t_j  (j != m),
+//   x_m = (s - sum_{j != m} conj(v_j) x_j) / conj(v_m)  if C^2 t_m < |v_m|^2,
+//         (r_m - v_m s / C^2) / t_m                     otherwise.
+// `scale` folds in 1/(H W) of the inverse transform.
+template <int H, int C>
+__device__ __forceinline__ void reg_group_solve(float2 (&v)[16], int t, int q, int kx, int W,
+                                                const float2 *__restrict__ bcol, float lam,
+                                                float scale) {
+    constexpr int T = H / 16, G = 16 / C;
+    constexpr float icc = 1.0f / (float)(C * C);
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, base = lane - q;
+    // sin^2 in x for this column; the column of the group's smallest one
+    const float sxv = sinpif((float)kx / (float)W);
+    const float sx2 = sxv * sxv;
+    float best = sx2;
+    int qm = q;
+#pragma unroll
+    for (int o = 1; o < C; o <<= 1) {
+        const float ob = __shfl_xor_sync(full, best, o);
+        const int oq = __shfl_xor_sync(full, qm, o);
+        if (ob < best || (ob == best && oq < qm)) {
+            best = ob;
+            qm = oq;
+        }
+    }
+    // sin(pi (t + T i) / H) = sin(pi t / H + pi i / 16) by angle addition
+    float s0, c0;
+    sincospif((float)t / (float)H, &s0, &c0);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        // (indices into the register arrays stay compile-time constants: the
+        // member m is selected by comparisons, never by a computed index)
+        float tj[C];
+        float2 vj[C];
+        int pm = 0;
+        float smin = 0.f;
+#pragma unroll
+        for (int p = 0; p < C; ++p) {
+            const int i = g + G * p;
+            const float2 cs = c_cs32[i];
+            const float sy = s0 * cs.x + c0 * cs.y;
+            const float sy2 = sy * sy;
+            if (p == 0 || sy2 < smin) {
+                smin = sy2;
+                pm = p;
+            }
+            const float S = 4.0f * (sy2 + sx2);
+            tj[p] = lam * S * S;
+            const float2 b = __ldg(bcol + t + T * i);
+            vj[p] = make_float2(b.x, -b.y);
+        }
+        const bool mlane = (q == qm);
+        // n and d over the members other than m
+        float2 num = make_float2(0.f, 0.f);
+        float dsum = 0.f;
+#pragma unroll
+        for (int p = 0; p < C; ++p) {
+            if (mlane && p == pm) continue;
+            const float it = __frcp_rn(tj[p]);
+            const float2 cr = cmulc(vj[p], v[g + G * p]);
+            num.x = fmaf(cr.x, it, num.x);
+            num.y = fmaf(cr.y, it, num.y);
+            dsum = fmaf(vj[p].x * vj[p].x + vj[p].y * vj[p].y, it, dsum);
+        }
+#pragma unroll
+        for (int o = 1; o < C; o <<= 1) {
+            num.x += __shfl_xor_sync(full, num.x, o);
+            num.y += __shfl_xor_sync(full, num.y, o);
+            dsum += __shfl_xor_sync(full, dsum, o);
+        }
+        float2 sv = make_float2(0.f, 0.f), vm = make_float2(0.f, 0.f), rm = sv;
+        float tm = 0.f;
+        if (mlane) {
+#pragma unroll
+            for (int p = 0; p < C; ++p)
+                if (p == pm) {
+                    vm = vj[p];
+                    rm = v[g + G * p];
+                    tm = tj[p];
+                }
+            const float vm2 = vm.x * vm.x + vm.y * vm.y;
+            const float iden = 1.0f / (tm + (vm2 + tm * dsum) * icc);
+            const float2 cr = cmulc(vm, rm);
+            sv = make_float2((cr.x + tm * num.x) * iden, (cr.y + tm * num.y) * iden);
+        }
+        sv.x = __shfl_sync(full, sv.x, base + qm);
+        sv.y = __shfl_sync(full, sv.y, base + qm);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int p = 0; p < C; ++p) {
+            if (mlane && p == pm) continue;
+            const float it = __frcp_rn(tj[p]);
+            const float2 vs = cmul2(vj[p], sv);
+            const float2 r = v[g + G * p];
+            const float2 x = make_float2((r.x - vs.x * icc) * it, (r.y - vs.y * icc) * it);
+            const float2 cx = cmulc(vj[p], x);
+            acc.x += cx.x;
+            acc.y += cx.y;
+            v[g + G * p] = make_float2(x.x * scale, x.y * scale);
+        }
+#pragma unroll
+        for (int o = 1; o < C; o <<= 1) {
+            acc.x += __shfl_xor_sync(full, acc.x, o);
+            acc.y += __shfl_xor_sync(full, acc.y, o);
+        }
+        if (mlane) {
+            const float vm2 = vm.x * vm.x + vm.y * vm.y;
+            float2 xm;
+            if ((float)(C * C) * tm < vm2) {
+                const float2 d = make_float2(sv.x - acc.x, sv.y - acc.y);
+                const float iv = 1.0f / vm2;
+                xm = make_float2((d.x * vm.x - d.y * vm.y) * iv, (d.y * vm.x + d.x * vm.y) * iv);
+            } else {
+                const float2 vs = cmul2(vm, sv);
+                xm = make_float2((rm.x - vs.x * icc) / tm, (rm.y - vs.y * icc) / tm);
+            }
+#pragma unroll
+            for (int p = 0; p < C; ++p)
+                if (p == pm) v[g + G * p] = make_float2(xm.x * scale, xm.y * scale);
+        }
+    }
+}
+
+template <int H, int C>
+__global__ void __launch_bounds__(C * H / 16, 1024 / (C * H / 16))
+    prec_cols_reg_kernel(PrecArgs a, float scale) {
+    constexpr int T = H / 16, LD = reg_ld(H);
+    extern __shared__ __align__(16) float2 csm[];
+    const int k = blockIdx.y, kx0 = blockIdx.x;
+    if (reg_image_idle(a, k)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane % C, t = lane / C + (32 / C) * warp;
+    const int W = a.W, kx = kx0 + q * (W / C);
+    float2 *S = a.spec + (size_t)k * H * W + (size_t)kx * H;
+    float2 v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = S[t + T * e];
+    float2 *col = csm + q * LD;
+    reg_fft<H>(v, col, t, a.twH, false, false);
+    reg_group_solve<H, C>(v, t, q, kx, W, a.bh + (size_t)kx * H, a.lam, scale);
+    reg_fft<H>(v, col, t, a.twH, true, true);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) S[t + T * i] = v[i];
+}
+
+// ---------------------------------------------------------------------------
+// Inverse row pass: transposed load, inverse row FFTs, z = (real, imaginary)
+// of the two bands, and their r^T z; the band pair's last CTA sets beta and
+// the next alpha numerator (preconditioned CG).
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kRegRows * W / 16, 1024 / (kRegRows * W / 16))
+    prec_rows_inv_reg_kernel(PrecArgs a) {
+    constexpr int T = W / 16, LD = reg_ld(W);
+    extern __shared__ __align__(16) float2 rsm[];
+    __shared__ double red[2][32];
+    const int k = blockIdx.y;
+    if (reg_image_idle(a, k)) return;
+    int row, t;
+    row_lane(row, t);
+    const int H = a.H, y = blockIdx.x * kRegRows + row;
+    const size_t HW = (size_t)H * W;
+    const float2 *S = a.spec + (size_t)k * HW + y;
+    float2 v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = S[(size_t)(t + T * e) * H];
+    reg_fft<W>(v, rsm + row * LD, t, a.twW, true, false);
+    const size_t o0 = (size_t)(2 * k) * HW + (size_t)y * W;
+    const bool two = 2 * k + 1 < a.N;
+    float *z0 = a.z + o0, *z1 = a.z + o0 + HW;
+    const float *q0 = a.r + o0, *q1 = a.r + o0 + HW;
+    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int x = t + T * i;
+        z0[x] = v[i].x;
+        if (two) z1[x] = v[i].y;
+        if (a.bands) {
+            d0 = fmaf(__ldg(q0 + x), v[i].x, d0);
+            if (two) d1 = fmaf(__ldg(q1 + x), v[i].y, d1);
+        }
+    }
+    if (!a.bands) return;
+    double s0 = d0, s1 = d1;
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = s0;
+        red[1][warp] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double t0 = 0.0, t1 = 0.0;
+    for (int j = 0; j < nw; ++j) {
+        t0 += red[0][j];
+        t1 += red[1][j];
+    }
+    CgBand *b0 = a.bands + 2 * k;
+    CgBand *b1 = two ? b0 + 1 : nullptr;
+    atomicAdd(&b0->rz_new, t0);
+    if (b1) atomicAdd(&b1->rz_new, t1);
+    __threadfence();
+    const unsigned int cnt = atomicAdd(&b0->cnt_prec, 1u);
+    if (cnt != gridDim.x - 1) return;
+    __threadfence();
+    b0->cnt_prec = 0u;
+    for (int j = 0; j < (two ? 2 : 1); ++j) {
+        CgBand *bd = b0 + j;
+        const double rz = atomicAdd(&bd->rz_new, 0.0);
+        bd->rz_new = 0.0;
+        if (bd->done) continue;
+        if (!isfinite(rz)) {
+            bd->status = PS_ERR_NONFINITE;
+            bd->done = 1;
+        } else if (!(rz > 0.0)) {
+            bd->status = PS_ERR_BREAKDOWN;
+            bd->done = 1;
+        } else {
+            // first application (before any iteration): p = z
+            bd->beta = bd->iters > 0 ? rz / bd->rho : 0.0;
+            bd->rho = rz;
+        }
+    }
+}
+
+template <int L>
+size_t reg_row_smem() {
+    return (size_t)kRegRows * reg_ld(L) * sizeof(float2);
+}
+
+template <int H, int C>
+size_t reg_col_smem() {
+    return (size_t)C * reg_ld(H) * sizeof(float2);
+}
+
+template <int W>
+void launch_rows_reg(const PrecArgs &a, bool inverse, cudaStream_t st) {
+    const dim3 grd(a.H / kRegRows, (a.N + 1) / 2), blk(kRegRows * W / 16);
+    if (inverse)
+        prec_rows_inv_reg_kernel<W><<<grd, blk, reg_row_smem<W>(), st>>>(a);
+    else
+        prec_rows_fwd_reg_kernel<W><<<grd, blk, reg_row_smem<W>(), st>>>(a);
+}
+
+template <int H, int C>
+void launch_cols_reg(const PrecArgs &a, float scale, cudaStream_t st) {
+    const dim3 grd(a.W / C, (a.N + 1) / 2), blk(C * H / 16);
+    prec_cols_reg_kernel<H, C><<<grd, blk, reg_col_smem<H, C>(), st>>>(a, scale);
+}
+
+bool reg_len_ok(int L) { return L == 256 || L == 512 || L == 1024 || L == 2048 || L == 4096; }
+
+template <int W>
+bool rows_dispatch(const PrecArgs &a, bool inverse, cudaStream_t st) {
+    if (a.W != W) return false;
+    launch_rows_reg<W>(a, inverse, st);
+    return true;
+}
+
+template <int H>
+bool cols_dispatch(const PrecArgs &a, float scale, cudaStream_t st) {
+    if (a.H != H) return false;
+    if (a.c == 2) launch_cols_reg<H, 2>(a, scale, st);
+    else launch_cols_reg<H, 4>(a, scale, st);
+    return true;
+}
+
+template <class F>
+cudaError_t reg_attr(F *f, size_t bytes) {
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int L>
+cudaError_t reg_attrs_len() {
+    cudaError_t e = reg_attr(prec_rows_fwd_reg_kernel<L>, reg_row_smem<L>());
+    if (e == cudaSuccess) e = reg_attr(prec_rows_inv_reg_kernel<L>, reg_row_smem<L>());
+    if (e == cudaSuccess) e = reg_attr(prec_cols_reg_kernel<L, 2>, reg_col_smem<L, 2>());
+    if (e == cudaSuccess) e = reg_attr(prec_cols_reg_kernel<L, 4>, reg_col_smem<L, 4>());
+    return e;
+}
+
+}  // namespace
+
+bool precond_reg_supported(int H, int W, int c) {
+    return reg_len_ok(H) && reg_len_ok(W) && (c == 2 || c == 4) && H % kRegRows == 0;
+}
+
+bool launch_precond_reg(const PrecArgs &a, cudaStream_t st) {
+    if (!precond_reg_supported(a.H, a.W, a.c)) return false;
+    const float scale = 1.0f / ((float)a.H * (float)a.W);
+    rows_dispatch<256>(a, false, st) || rows_dispatch<512>(a, false, st) ||
+        rows_dispatch<1024>(a, false, st) || rows_dispatch<2048>(a, false, st) ||
+        rows_dispatch<4096>(a, false, st);
+    cols_dispatch<256>(a, scale, st) || cols_dispatch<512>(a, scale, st) ||
+        cols_dispatch<1024>(a, scale, st) || cols_dispatch<2048>(a, scale, st) ||
+        cols_dispatch<4096>(a, scale, st);
+    rows_dispatch<256>(a, true, st) || rows_dispatch<512>(a, true, st) ||
+        rows_dispatch<1024>(a, true, st) || rows_dispatch<2048>(a, true, st) ||
+        rows_dispatch<4096>(a, true, st);
+    return true;
+}
+
+cudaError_t precond_reg_set_attrs() {
+    float2 cs[16];
+    for (int i = 0; i < 16; ++i) {
+        const double th = M_PI * i / 16.0;
+        cs[i] = make_float2((float)cos(th), (float)sin(th));
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_cs32, cs, sizeof(cs));
+    if (e == cudaSuccess) e = reg_attrs_len<256>();
+    if (e == cudaSuccess) e = reg_attrs_len<512>();
+    if (e == cudaSuccess) e = reg_attrs_len<1024>();
+    if (e == cudaSuccess) e = reg_attrs_len<2048>();
+    if (e == cudaSuccess) e = reg_attrs_len<4096>();
+    return e;
+}
+
+}  // namespace ps

@@ -46,6 +46,38 @@ def test_precond_matches_oracle(cuda, N, H, W, c, R, lg):
         assert rel(z[b], ref) < PREC_TOL, b
 
 
+@pytest.mark.parametrize("N,H,W,c,R,lg", [
+    (2, 256, 256, 4, 3, 8e-4),
+    (5, 256, 512, 4, 4, 8e-4),    # odd band count, non-square
+    (2, 512, 512, 2, 4, 1e-2),    # ratio 2
+    (1, 1024, 256, 4, 5, 8e-4),
+    (3, 2048, 256, 4, 3, 8e-4),
+    (1, 256, 4096, 2, 3, 1e-2),   # 4096-wide rows (1024-thread row CTAs)
+    (1, 4096, 256, 4, 3, 8e-4),   # 4 columns of 4096 (1024-thread column CTAs)
+])
+def test_register_and_shared_passes_match_oracle(cuda, N, H, W, c, R, lg):
+    # The register-resident passes (power-of-two sides, ratios 2 and 4) and
+    # the shared-memory passes, each forced through the recorded tuning,
+    # against the oracle's P^{-1} and against each other.
+    rng = np.random.default_rng(N * 7000 + H + 3 * W + c)
+    u = rand_kernel(R, rng)
+    r = rng.standard_normal((N, H, W)) * 5.0
+    r += np.cumsum(np.cumsum(rng.standard_normal((N, H, W)), axis=1), axis=2) * 0.1
+    rd, ud = to_dev(r, cuda), to_dev(u, cuda)
+    out = {}
+    try:
+        for impl in (1, 2):
+            api.set_tuning(N, H, W, c, 1, prec_impl=impl)
+            out[impl] = to_np(ops.precond(rd, ud, c, lg))
+    finally:
+        api.set_tuning(N, H, W, c, 1, prec_impl=0)
+    for b in range(N):
+        ref = oracle.precond_apply(r[b].astype(np.float32), u.astype(np.float32), c, lg)
+        assert rel(out[2][b], ref) < PREC_TOL, b
+        assert rel(out[1][b], ref) < PREC_TOL, b
+        assert rel(out[2][b], out[1][b]) < PREC_TOL, b
+
+
 def test_precond_bands_do_not_mix(cuda):
     # bands 2k and 2k+1 share one complex transform: band 1 = 0 must give 0
     rng = np.random.default_rng(9)
