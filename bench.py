@@ -410,7 +410,8 @@ def profile_config(args):
 def run_profile_solve(args):
     """One solve of the workload scene with host-launched CG iterations and a
     fixed iteration count (the tolerance out of reach), after one untimed
-    solve, so that a profiler sees every kernel of the loop."""
+    solve, so that a profiler sees every kernel of the loop; the bands run as
+    one branch, so every launch covers all of them."""
     import torch
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
@@ -431,6 +432,8 @@ def run_profile_solve(args):
     K = torch.from_numpy(scene["kernel"]).to(dev)
     hp = api.default_hrms_params(host_loop=1, tol=1e-30, max_iter=args.profile_solve,
                                  precond=1 if args.precond == "fft" else 0)
+    # one branch, as inside the batched call: every launch covers all bands
+    api.set_tuning(cfg.bands, cfg.H, cfg.W, cfg.ratio, hp.r, split=1)
     for _ in range(2):
         api.solve_hrms(X, Y, K, cfg.ratio, hp, info=False)
     torch.cuda.synchronize()

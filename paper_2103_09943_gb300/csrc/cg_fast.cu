@@ -157,6 +157,152 @@ __global__ void __launch_bounds__(128) db_site_kernel(const float *__restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// v = D B(u) p_new, register-blocked: a CTA of 128 threads covers 16 x 32 LR
+// sites; thread (g, kyl) takes the four sites kx0 + 4 g + s (s < 4) of row
+// ky0 + kyl. The footprint is stored as C phase planes (HR column x in plane
+// x mod C at entry x div C), so for a tap row i the samples of the four
+// sites and of every tap column lie in C short runs of consecutive entries:
+// per tap row the thread loads NCH aligned float4 of each plane into
+// registers and feeds its four accumulators from them, one broadcast load of
+// the weight per tap (about a quarter of the shared loads of one load per
+// sample and site).
+// ---------------------------------------------------------------------------
+constexpr int S4_GX = 8, S4_TY = 16, S4_TX = 4 * S4_GX;
+
+template <int C, int R>
+struct Site4Dims {
+    static constexpr int n = 2 * R + 1;
+    static constexpr int FY = C * S4_TY + 2 * R;
+    static constexpr int FX = C * S4_TX + 2 * R;
+    static constexpr int MMAX = (n + C - 1) / C;       // taps per plane, at most
+    static constexpr int NCH = (3 + MMAX + 3) / 4;     // float4 runs per plane and tap row
+    static constexpr int FXc = (FX + C - 1) / C;
+    static constexpr int FXr = 4 * (S4_GX - 1) + 4 * NCH;
+    static constexpr int FXp = (((FXc > FXr) ? FXc : FXr) + 3) & ~3;
+    static constexpr int plane = FY * FXp;             // a multiple of 4
+    static constexpr int uoff = (n * n + 3) & ~3;
+    static constexpr int smem_floats = uoff + C * plane;
+};
+
+template <int C, int R>
+__global__ void __launch_bounds__(128) db_site4_kernel(const float *__restrict__ src,
+                                                       const float *__restrict__ rsrc,
+                                                       float *__restrict__ pdst, CgBand *bands,
+                                                       const CgGlobal *g, int cg, int H, int W,
+                                                       const float *__restrict__ u,
+                                                       float *__restrict__ v) {
+    using D = Site4Dims<C, R>;
+    extern __shared__ __align__(16) float sm4[];
+    __shared__ float vred[4];
+    const int b = blockIdx.z;
+    float beta = 0.0f;
+    bool use_old = false;
+    if (cg) {
+        if (g->stop || bands[b].done) return;
+        const double bd = bands[b].beta;
+        beta = (float)bd;
+        use_old = bd != 0.0;
+    }
+    const int h = H / C, w = W / C;
+    const size_t HW = (size_t)H * W;
+    float *su = sm4;
+    float *sp = sm4 + D::uoff;
+    const int ky0 = blockIdx.y * S4_TY, kx0 = blockIdx.x * S4_TX;
+    const int oy = C * ky0 - R, ox = C * kx0 - R;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    for (int k = tid; k < D::n * D::n; k += 128) su[k] = u[k];
+    const float *S = src + (size_t)b * HW;
+    const float *Rr = cg ? rsrc + (size_t)b * HW : nullptr;
+    float *P = cg ? pdst + (size_t)b * HW : nullptr;
+    // fill (p_new = r + beta p_old fused into the load; own pixels stored)
+    constexpr int NXW = (D::FX + 31) / 32;
+    const int gx0 = wrap_mod(ox + tx, W);
+#pragma unroll 2
+    for (int yy = ty; yy < D::FY; yy += 4) {
+        const size_t grow = (size_t)wrap_mod(oy + yy, H) * W;
+        const bool own_row = cg && yy >= R && yy < R + C * S4_TY && C * ky0 + (yy - R) < H;
+        float rv[NXW], pv[NXW];
+        int gx = gx0;
+#pragma unroll
+        for (int m = 0; m < NXW; ++m) {
+            if (tx + 32 * m < D::FX) {
+                const size_t gi = grow + gx;
+                if (cg) {
+                    rv[m] = Rr[gi];
+                    pv[m] = use_old ? S[gi] : 0.0f;
+                } else {
+                    rv[m] = S[gi];
+                    pv[m] = 0.0f;
+                }
+            }
+            gx += 32;
+            while (gx >= W) gx -= W;
+        }
+#pragma unroll
+        for (int m = 0; m < NXW; ++m) {
+            const int xx = tx + 32 * m;
+            if (xx < D::FX) {
+                const float val = (cg && use_old) ? fmaf(beta, pv[m], rv[m]) : rv[m];
+                if (own_row && xx >= R && xx < R + C * S4_TX) {
+                    const int hx = C * kx0 + (xx - R);
+                    if (hx < W) P[(size_t)(C * ky0 + (yy - R)) * W + hx] = val;
+                }
+                sp[(xx % C) * D::plane + yy * D::FXp + xx / C] = val;
+            }
+        }
+    }
+    __syncthreads();
+    // site (kyl, 4 g + s); tap (i, j = R - jj) reads footprint row
+    // C kyl + R - i, plane jj mod C, entry 4 g + s + jj div C
+    const int gq = tid & (S4_GX - 1), kyl = tid >> 3;
+    const float *rowbase = sp + (C * kyl + R) * D::FXp + 4 * gq;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = -R; i <= R; ++i) {
+        const float *rp = rowbase - i * D::FXp;
+        float vals[C][4 * D::NCH];
+#pragma unroll
+        for (int p = 0; p < C; ++p)
+#pragma unroll
+            for (int c = 0; c < D::NCH; ++c) {
+                const float4 q = *reinterpret_cast<const float4 *>(rp + p * D::plane + 4 * c);
+                vals[p][4 * c] = q.x;
+                vals[p][4 * c + 1] = q.y;
+                vals[p][4 * c + 2] = q.z;
+                vals[p][4 * c + 3] = q.w;
+            }
+#pragma unroll
+        for (int jj = 0; jj <= 2 * R; ++jj) {
+            const float wv = su[(i + R) * D::n + (2 * R - jj)];
+#pragma unroll
+            for (int s2 = 0; s2 < 4; ++s2)
+                acc[s2] = fmaf(wv, vals[jj % C][jj / C + s2], acc[s2]);
+        }
+    }
+    const int ky = ky0 + kyl;
+    float vv = 0.0f;
+    if (ky < h) {
+        float *vrow = v + (size_t)b * h * w + (size_t)ky * w;
+#pragma unroll
+        for (int s2 = 0; s2 < 4; ++s2) {
+            const int kx = kx0 + 4 * gq + s2;
+            if (kx < w) {
+                vrow[kx] = acc[s2];
+                vv = fmaf(acc[s2], acc[s2], vv);
+            }
+        }
+    }
+    if (cg) {
+        for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
+        if (tx == 0) vred[ty] = vv;
+        __syncthreads();
+        if (tid == 0)
+            atomicAdd(&bands[b].vv, (double)vred[0] + (double)vred[1] + (double)vred[2] +
+                                        (double)vred[3]);
+    }
+}
+
 template <int C>
 struct VecT;
 template <>
@@ -323,9 +469,9 @@ bool launch_pair(int which, const float *a0, const float *a1, float *a2, CgBand 
                  float *x, float *r, const float *q, cudaStream_t st) {
     const int h = H / C, w = W / C;
     if (which == 0) {
-        using D = SiteDims<C, R>;
-        dim3 blk(SITE_TX, SITE_TYT), grd((w + SITE_TX - 1) / SITE_TX, (h + SITE_TY - 1) / SITE_TY, N);
-        db_site_kernel<C, R><<<grd, blk, D::smem_floats * sizeof(float), st>>>(
+        using D = Site4Dims<C, R>;
+        dim3 grd((w + S4_TX - 1) / S4_TX, (h + S4_TY - 1) / S4_TY, N);
+        db_site4_kernel<C, R><<<grd, 128, D::smem_floats * sizeof(float), st>>>(
             a0, a1, a2, bands, g, cg, H, W, u, v);
     } else {
         dim3 grd((w + 127) / 128, h, N);
@@ -365,8 +511,14 @@ bool dispatch(int C, int R, int which, const float *a0, const float *a1, float *
 
 template <int C, int R>
 cudaError_t set_attr_one() {
-    return cudaFuncSetAttribute(db_site_kernel<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(SiteDims<C, R>::smem_floats * sizeof(float)));
+    cudaError_t e = cudaFuncSetAttribute(db_site_kernel<C, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(SiteDims<C, R>::smem_floats * sizeof(float)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(db_site4_kernel<C, R>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(Site4Dims<C, R>::smem_floats * sizeof(float)));
+    return e;
 }
 
 template <int C>

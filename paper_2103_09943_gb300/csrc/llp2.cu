@@ -68,14 +68,16 @@ __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
     constexpr float nw = (float)(NB * NB);
     constexpr float inw = 1.0f / nw;
     __shared__ double red[kWarps];
-    const int b = blockIdx.z;
+    // band-minor grid: the CTAs of all bands of one strip run together and
+    // read the shared PAN statistics once from memory, the rest from L2
+    const int b = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (a.g->stop || a.bands[b].done) return;
     const int H = a.H, W = a.W;
     const int HWi = H * W;
     const size_t HW = (size_t)HWi;
-    const int x0 = blockIdx.x * VALID;
-    const int y0 = (blockIdx.y * kWarps + warp) * TY;
+    const int x0 = blockIdx.y * VALID;
+    const int y0 = (blockIdx.z * kWarps + warp) * TY;
     const int xl = x0 - G + 2 * lane;  // even; W is even, so xl + 1 wraps with xl
     const int gx = wrap2(xl, W);
     const bool out_lane = lane >= G / 2 && lane < 32 - G / 2 && xl < W;
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
         CgBand *bd = a.bands + b;
         atomicAdd(&bd->pAp, tot);
         __threadfence();
-        const unsigned int nblk = gridDim.x * gridDim.y;
+        const unsigned int nblk = gridDim.y * gridDim.z;  // CTAs of this band
         const unsigned int t = atomicAdd(&bd->cnt_apply, 1u);
         if (t == nblk - 1) {
             __threadfence();
@@ -517,7 +519,7 @@ template <int RW, int TY, int PF>
 void launch_ty(const LlpArgs &a, int N, cudaStream_t st) {
     constexpr int G = 2 * RW + 2, VALID = 64 - 2 * G;
     const int rows = TY * kWarps;
-    dim3 grd((a.W + VALID - 1) / VALID, (a.H + rows - 1) / rows, N);
+    dim3 grd(N, (a.W + VALID - 1) / VALID, (a.H + rows - 1) / rows);
     llp_cgq2_kernel<RW, TY, PF><<<grd, 32 * kWarps, 0, st>>>(a);
 }
 

@@ -393,17 +393,33 @@ __global__ void __launch_bounds__(kRegRows * W / 16, 1024 / (kRegRows * W / 16))
     reg_fft<W>(v, rsm + row * LD, t, a.twW, true, false);
     const size_t o0 = (size_t)(2 * k) * HW + (size_t)y * W;
     const bool two = 2 * k + 1 < a.N;
-    float *z0 = a.z + o0, *z1 = a.z + o0 + HW;
-    const float *q0 = a.r + o0, *q1 = a.r + o0 + HW;
+    float *__restrict__ z0 = a.z + o0;
+    float *__restrict__ z1 = a.z + o0 + HW;
+    const float *__restrict__ q0 = a.r + o0;
+    const float *__restrict__ q1 = a.r + o0 + HW;
     float d0 = 0.f, d1 = 0.f;
+    // r for r^T z in chunks of 8 positions, all loads of a chunk in flight
+    // before its stores
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const int x = t + T * i;
-        z0[x] = v[i].x;
-        if (two) z1[x] = v[i].y;
+    for (int i0 = 0; i0 < 16; i0 += 8) {
+        float ra[8], rb[8];
         if (a.bands) {
-            d0 = fmaf(__ldg(q0 + x), v[i].x, d0);
-            if (two) d1 = fmaf(__ldg(q1 + x), v[i].y, d1);
+#pragma unroll
+            for (int ii = 0; ii < 8; ++ii) {
+                const int x = t + T * (i0 + ii);
+                ra[ii] = __ldg(q0 + x);
+                rb[ii] = two ? __ldg(q1 + x) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+            const int x = t + T * (i0 + ii);
+            z0[x] = v[i0 + ii].x;
+            if (two) z1[x] = v[i0 + ii].y;
+            if (a.bands) {
+                d0 = fmaf(ra[ii], v[i0 + ii].x, d0);
+                d1 = fmaf(rb[ii], v[i0 + ii].y, d1);
+            }
         }
     }
     if (!a.bands) return;
