@@ -208,6 +208,11 @@ typedef struct ps_tuning {
                             applies)                                        */
     float prec_impl_us[2]; /* one application: candidates 1 (its best row
                             count), 2                                        */
+    int db_impl;         /* blur-decimate D B p of the CG loop: 1 one load
+                            per sample and LR site, 2 four LR sites a thread
+                            from register runs of the phase planes; 0 the
+                            default (1)                                      */
+    float db_impl_us[2]; /* one launch: candidates 1, 2                      */
 } ps_tuning;
 
 /* Autotuner: times every candidate of each tunable kernel on N bands of
@@ -224,8 +229,8 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r,
 /* The launch choices recorded for these sizes on the current device (all
  * zero: the defaults), and their replacement, e.g. with choices an earlier
  * process's ps_autotune found. Only the choice fields (prec_rows, llp_rows,
- * llp_pf, split, llp_bands, prec_impl) are read or written; 0 keeps a
- * default. */
+ * llp_pf, split, llp_bands, prec_impl, db_impl) are read or written; 0 keeps
+ * a default. */
 ps_status ps_get_tuning(int N, int H, int W, int ratio, int r, ps_tuning *h_out);
 ps_status ps_set_tuning(int N, int H, int W, int ratio, int r, const ps_tuning *h_in);
 

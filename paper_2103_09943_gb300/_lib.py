@@ -39,7 +39,8 @@ class Tuning(ctypes.Structure):
                 ("llp_us", ctypes.c_float * 6), ("split", ctypes.c_int),
                 ("split_us", ctypes.c_float * 3), ("llp_bands", ctypes.c_int),
                 ("llp2_us", ctypes.c_float * 2), ("prec_impl", ctypes.c_int),
-                ("prec_impl_us", ctypes.c_float * 2)]
+                ("prec_impl_us", ctypes.c_float * 2), ("db_impl", ctypes.c_int),
+                ("db_impl_us", ctypes.c_float * 2)]
 
 
 class BandInfo(ctypes.Structure):

@@ -100,12 +100,15 @@ def autotune(N, H, W, ratio, R, r=1, ws=None, device=None, lrms=None, pan=None,
             "split_us": {str(k): round(v, 2) for k, v in zip((1, 2, 4), t.split_us) if v},
             "prec_impl": t.prec_impl,
             "prec_impl_us": {n: round(v, 2) for n, v in zip(("smem", "reg"), t.prec_impl_us)
-                             if v}}
+                             if v},
+            "db_impl": t.db_impl,
+            "db_impl_us": {n: round(v, 2) for n, v in zip(("site", "runs"), t.db_impl_us) if v}}
 
 
 def set_tuning(N, H, W, ratio, r=1, **choices) -> None:
     """Record launch choices for these sizes (ps_set_tuning): prec_rows,
-    llp_rows, llp_pf, split, llp_bands, prec_impl; 0 or absent keeps a default."""
+    llp_rows, llp_pf, split, llp_bands, prec_impl, db_impl; 0 or absent keeps a
+    default."""
     t = Tuning()
     for k, v in choices.items():
         setattr(t, k, v)
@@ -116,7 +119,7 @@ def get_tuning(N, H, W, ratio, r=1) -> dict:
     t = Tuning()
     _check(_lib.load().ps_get_tuning(N, H, W, ratio, r, ctypes.byref(t)))
     return {k: getattr(t, k) for k in ("prec_rows", "llp_rows", "llp_pf", "split", "llp_bands",
-                                       "prec_impl")}
+                                       "prec_impl", "db_impl")}
 
 
 @dataclass

@@ -411,7 +411,7 @@ void enqueue_bands(const CgLoopArgs &a, int b0, int n, const float *p_old, float
     float *v = a.v + (size_t)b0 * hw;
     // p_new = (z or r) + beta p_old, formed inside the blur-decimate load
     launch_db(p_old + o, (a.precond ? a.pa.z : a.rv) + o, p_new + o, bands, a.g, 1, n, a.H, a.W,
-              a.c, a.u, a.R, v, st);
+              a.c, a.u, a.R, v, st, a.tune.db_impl);
     LlpArgs la = {};
     la.in = p_new + o;
     la.lr = v;
@@ -1437,6 +1437,22 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
             out.prec_rows = trs[k];
         }
     }
+    // the blur-decimate variants of the CG loop (p_new = z + beta p_old fused)
+    {
+        const float *uu = ws.at<float>(ws.L.kern);
+        out.db_impl = 1;
+        float bestd = 1e30f;
+        for (int k = 0; k < 2; ++k) {
+            out.db_impl_us[k] = timed([&] {
+                launch_db(ws.at<float>(ws.L.pA), ws.at<float>(ws.L.z), ws.at<float>(ws.L.pB),
+                          bands, g, 1, N, H, W, ratio, uu, R, ws.at<float>(ws.L.v), st, k + 1);
+            });
+            if (out.db_impl_us[k] < bestd) {
+                bestd = out.db_impl_us[k];
+                out.db_impl = k + 1;
+            }
+        }
+    }
     // the register-resident passes against the best of those
     out.prec_impl = 1;
     out.prec_impl_us[0] = bestp;
@@ -1503,7 +1519,7 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
             if (splits[k] > 1 && N < 2 * splits[k]) continue;
             tuning_set(dev, N, H, W, ratio, r,
                        Tuning{out.prec_rows, out.llp_rows, splits[k], out.llp_pf,
-                              out.llp_bands, out.prec_impl});
+                              out.llp_bands, out.prec_impl, out.db_impl});
             float best = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, st);
@@ -1528,7 +1544,7 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
     if ((s = last_launch()) != PS_OK) return s;
     tuning_set(dev, N, H, W, ratio, r,
                Tuning{out.prec_rows, out.llp_rows, out.split, out.llp_pf, out.llp_bands,
-                      out.prec_impl});
+                      out.prec_impl, out.db_impl});
     if (h_out) *h_out = out;
     return PS_OK;
 }
@@ -1545,6 +1561,7 @@ ps_status ps_get_tuning(int N, int H, int W, int ratio, int r, ps_tuning *h_out)
     h_out->split = t.split;
     h_out->llp_bands = t.llp_bands;
     h_out->prec_impl = t.prec_impl;
+    h_out->db_impl = t.db_impl;
     return PS_OK;
 }
 
@@ -1563,10 +1580,11 @@ ps_status ps_set_tuning(int N, int H, int W, int ratio, int r, const ps_tuning *
     if (t.prec_impl < 0 || t.prec_impl > 2 ||
         (t.prec_impl == 2 && !precond_reg_supported(H, W, ratio)))
         return PS_ERR_INVALID_ARG;
+    if (t.db_impl < 0 || t.db_impl > 2) return PS_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PS_ERR_CUDA;
     tuning_set(dev, N, H, W, ratio, r, Tuning{t.prec_rows, t.llp_rows, t.split, t.llp_pf,
-                                              t.llp_bands, t.prec_impl});
+                                              t.llp_bands, t.prec_impl, t.db_impl});
     return PS_OK;
 }
 
@@ -1703,8 +1721,8 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
         key_put(key, dims);
         key_put(key, q.band_mask);
         const Tuning t = tuning_get(dev, q.N, q.H, q.W, q.ratio, hp->r);
-        const int tk[6] = {t.prec_rows, t.llp_rows, t.split, t.llp_pf, t.llp_bands,
-                           t.prec_impl};
+        const int tk[7] = {t.prec_rows, t.llp_rows, t.split, t.llp_pf, t.llp_bands,
+                           t.prec_impl, t.db_impl};
         key_put(key, tk);
     }
     cudaGraphExec_t exec = nullptr;

@@ -158,7 +158,9 @@ __global__ void __launch_bounds__(128) db_site_kernel(const float *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// v = D B(u) p_new, register-blocked: a CTA of 128 threads covers 16 x 32 LR
+// v = D B(u) p_new, register-blocked (the autotuner's db_impl = 2; measured
+// 5-10 % faster than db_site_kernel at 1024^2 with R = 6..8, slower at 512^2
+// and 2048^2): a CTA of 128 threads covers 16 x 32 LR
 // sites; thread (g, kyl) takes the four sites kx0 + 4 g + s (s < 4) of row
 // ky0 + kyl. The footprint is stored as C phase planes (HR column x in plane
 // x mod C at entry x div C), so for a tap row i the samples of the four
@@ -466,9 +468,14 @@ __global__ void __launch_bounds__(128) cg_update_site_kernel(
 template <int C, int R>
 bool launch_pair(int which, const float *a0, const float *a1, float *a2, CgBand *bands,
                  const CgGlobal *g, int cg, int N, int H, int W, const float *u, float *v,
-                 float *x, float *r, const float *q, cudaStream_t st) {
+                 float *x, float *r, const float *q, cudaStream_t st, int impl) {
     const int h = H / C, w = W / C;
-    if (which == 0) {
+    if (which == 0 && impl != 2) {
+        using D = SiteDims<C, R>;
+        dim3 blk(SITE_TX, SITE_TYT), grd((w + SITE_TX - 1) / SITE_TX, (h + SITE_TY - 1) / SITE_TY, N);
+        db_site_kernel<C, R><<<grd, blk, D::smem_floats * sizeof(float), st>>>(
+            a0, a1, a2, bands, g, cg, H, W, u, v);
+    } else if (which == 0) {
         using D = Site4Dims<C, R>;
         dim3 grd((w + S4_TX - 1) / S4_TX, (h + S4_TY - 1) / S4_TY, N);
         db_site4_kernel<C, R><<<grd, 128, D::smem_floats * sizeof(float), st>>>(
@@ -483,12 +490,12 @@ bool launch_pair(int which, const float *a0, const float *a1, float *a2, CgBand 
 template <int C>
 bool dispatch_r(int R, int which, const float *a0, const float *a1, float *a2, CgBand *bands,
                 const CgGlobal *g, int cg, int N, int H, int W, const float *u, float *v,
-                float *x, float *r, const float *q, cudaStream_t st) {
+                float *x, float *r, const float *q, cudaStream_t st, int impl) {
     switch (R) {
 #define PS_CASE(RR)                                                                          \
     case RR:                                                                                 \
         return launch_pair<C, RR>(which, a0, a1, a2, bands, g, cg, N, H, W, u, v, x, r, q, \
-                                  st);
+                                  st, impl);
 #ifdef PS_SITE_WIDE
         PS_CASE(12) PS_CASE(14) PS_CASE(16)
 #else
@@ -501,10 +508,12 @@ bool dispatch_r(int R, int which, const float *a0, const float *a1, float *a2, C
 
 bool dispatch(int C, int R, int which, const float *a0, const float *a1, float *a2,
               CgBand *bands, const CgGlobal *g, int cg, int N, int H, int W, const float *u,
-              float *v, float *x, float *r, const float *q, cudaStream_t st) {
-    if (C == 4) return dispatch_r<4>(R, which, a0, a1, a2, bands, g, cg, N, H, W, u, v, x, r, q, st);
+              float *v, float *x, float *r, const float *q, cudaStream_t st, int impl = 0) {
+    if (C == 4)
+        return dispatch_r<4>(R, which, a0, a1, a2, bands, g, cg, N, H, W, u, v, x, r, q, st, impl);
 #ifndef PS_SITE_WIDE
-    if (C == 2) return dispatch_r<2>(R, which, a0, a1, a2, bands, g, cg, N, H, W, u, v, x, r, q, st);
+    if (C == 2)
+        return dispatch_r<2>(R, which, a0, a1, a2, bands, g, cg, N, H, W, u, v, x, r, q, st, impl);
 #endif
     return false;
 }
@@ -539,13 +548,14 @@ cudaError_t set_attrs_c() {
 
 bool PS_SITE_FN(launch_db_fast)(const float *src, const float *rsrc, float *pdst,
                                 CgBand *bands, const CgGlobal *g, int cg, int N, int H, int W,
-                                int c, const float *u, int R, float *v, cudaStream_t st) {
+                                int c, const float *u, int R, float *v, cudaStream_t st,
+                                int impl) {
 #ifndef PS_SITE_WIDE
     if (R > 8)
-        return launch_db_fast_wide(src, rsrc, pdst, bands, g, cg, N, H, W, c, u, R, v, st);
+        return launch_db_fast_wide(src, rsrc, pdst, bands, g, cg, N, H, W, c, u, R, v, st, impl);
 #endif
     return dispatch(c, R, 0, src, rsrc, pdst, bands, g, cg, N, H, W, u, v, nullptr, nullptr,
-                    nullptr, st);
+                    nullptr, st, impl);
 }
 
 bool PS_SITE_FN(launch_cg_update_fast)(float *x, float *r, const float *p, const float *q,

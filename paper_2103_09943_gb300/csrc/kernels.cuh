@@ -37,9 +37,11 @@ void launch_pan_stats(const float *Y, int H, int W, int r, float eps, float *I, 
                       float *s, float4 *st4, cudaStream_t st);
 void launch_pack_stats(const float *I, const float *mu, const float *s, size_t n, float4 *st4,
                        cudaStream_t st);
+// impl: the blur-decimate variant of cg_fast.cu (0 or 1: one load per sample
+// and LR site; 2: four sites a thread from register runs)
 void launch_db(const float *src, const float *rsrc, float *pdst, const CgBand *bands,
                const CgGlobal *g, int cg, int N, int H, int W, int c, const float *u, int R,
-               float *v, cudaStream_t st);
+               float *v, cudaStream_t st, int impl = 0);
 void launch_adj(const float *v, int N, int H, int W, int c, const float *u, int R, float *z,
                 cudaStream_t st);
 void launch_llp(const LlpArgs &a, int mode, int r, int N, cudaStream_t st);
@@ -61,7 +63,7 @@ size_t llp_smem_bytes(int r);
 // return false when no specialisation covers (c, R)
 bool launch_db_fast(const float *src, const float *rsrc, float *pdst, CgBand *bands,
                     const CgGlobal *g, int cg, int N, int H, int W, int c, const float *u, int R,
-                    float *v, cudaStream_t st);
+                    float *v, cudaStream_t st, int impl);
 bool launch_cg_update_fast(float *x, float *r, const float *p, const float *q, const float *v,
                            const float *u, int R, int c, int N, int H, int W, CgBand *bands,
                            const CgGlobal *g, cudaStream_t st);
@@ -69,7 +71,7 @@ cudaError_t cg_fast_set_attrs();
 // the same for ratio 4 and radii 12, 14, 16 (cg_fast_wide.cu)
 bool launch_db_fast_wide(const float *src, const float *rsrc, float *pdst, CgBand *bands,
                          const CgGlobal *g, int cg, int N, int H, int W, int c, const float *u,
-                         int R, float *v, cudaStream_t st);
+                         int R, float *v, cudaStream_t st, int impl);
 bool launch_cg_update_fast_wide(float *x, float *r, const float *p, const float *q,
                                 const float *v, const float *u, int R, int c, int N, int H,
                                 int W, CgBand *bands, const CgGlobal *g, cudaStream_t st);
@@ -206,6 +208,7 @@ struct Tuning {
     int llp_pf;     // rows the LLP kernel's loads run ahead (0: default)
     int llp_bands;  // bands per CTA of the CG-loop LLP kernel (0: 1)
     int prec_impl;  // preconditioner passes: 0 default, 1 shared-memory, 2 register-resident
+    int db_impl;    // blur-decimate of the CG loop: 0 default, 1 per-site loads, 2 register runs
 };
 Tuning tuning_get(int dev, int N, int H, int W, int c, int r);
 void launch_fill(float *p, size_t n, float v, cudaStream_t st);

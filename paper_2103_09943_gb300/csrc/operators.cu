@@ -225,9 +225,9 @@ size_t db_smem_bytes(int c, int R) {
 
 void launch_db(const float *src, const float *rsrc, float *pdst, const CgBand *bands,
                const CgGlobal *g, int cg, int N, int H, int W, int c, const float *u,
-               int R, float *v, cudaStream_t st) {
+               int R, float *v, cudaStream_t st, int impl) {
     if (launch_db_fast(src, rsrc, pdst, const_cast<CgBand *>(bands), g, cg, N, H, W, c, u, R, v,
-                       st))
+                       st, impl))
         return;
     const int h = H / c, w = W / c;
     dim3 blk(DB_TLX, DB_TY), grd((w + DB_TLX - 1) / DB_TLX, (h + DB_TLY - 1) / DB_TLY, N);
