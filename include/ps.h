@@ -194,7 +194,9 @@ ps_status ps_sync_status(void *stream);
 typedef struct ps_tuning {
     int prec_rows;       /* rows per CTA of the preconditioner's row FFTs   */
     int llp_rows;        /* output rows per warp of the CG loop's LLP kernel */
-    int llp_pf;          /* rows its loads run ahead (2, 4, 6)              */
+    int llp_pf;          /* rows its loads run ahead (2, 4, 6 in registers;
+                            8: a ring of 8 rows filled by asynchronous
+                            copies into shared memory)                      */
     float prec_us[4];    /* candidates 1, 2, 4, 8 rows                      */
     float llp_us[6];     /* candidates: long walk with 2, 4, 6 rows ahead,
                             then the short walk                             */
@@ -213,6 +215,7 @@ typedef struct ps_tuning {
                             from register runs of the phase planes; 0 the
                             default (1)                                      */
     float db_impl_us[2]; /* one launch: candidates 1, 2                      */
+    float llp_ring_us[2]; /* LLP kernel with the ring: long, short walk      */
 } ps_tuning;
 
 /* Autotuner: times every candidate of each tunable kernel on N bands of

@@ -101,6 +101,8 @@ def autotune(N, H, W, ratio, R, r=1, ws=None, device=None, lrms=None, pan=None,
             "prec_impl": t.prec_impl,
             "prec_impl_us": {n: round(v, 2) for n, v in zip(("smem", "reg"), t.prec_impl_us)
                              if v},
+            "llp_ring_us": {w: round(v, 2) for w, v in zip(("long", "short"), t.llp_ring_us)
+                            if v},
             "db_impl": t.db_impl,
             "db_impl_us": {n: round(v, 2) for n, v in zip(("site", "runs"), t.db_impl_us) if v}}
 

@@ -1489,6 +1489,18 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
             }
         }
     }
+    // the shared-memory ring of asynchronous copies, long and short walks
+    for (int k = 0; k < 2; ++k) {
+        la.ty = llp_cgq2_rows(r, k);
+        la.pf = 8;
+        const float us = timed([&] { launch_llp_cgq2(la, r, N, st); });
+        out.llp_ring_us[k] = us;
+        if (us < bestl) {
+            bestl = us;
+            out.llp_rows = la.ty;
+            out.llp_pf = 8;
+        }
+    }
     // two bands per CTA (shared statistics), long and short walks
     out.llp_bands = 1;
     for (int k = 0; k < 2 && N >= 2; ++k) {
@@ -1574,7 +1586,8 @@ ps_status ps_set_tuning(int N, int H, int W, int ratio, int r, const ps_tuning *
     if (t.prec_rows && !precond_rows_ok(H, W, ratio, t.prec_rows)) return PS_ERR_INVALID_ARG;
     if (t.llp_rows && t.llp_rows != llp_cgq2_rows(r, 0) && t.llp_rows != llp_cgq2_rows(r, 1))
         return PS_ERR_INVALID_ARG;
-    if (t.llp_pf && t.llp_pf != 2 && t.llp_pf != 4 && t.llp_pf != 6) return PS_ERR_INVALID_ARG;
+    if (t.llp_pf && t.llp_pf != 2 && t.llp_pf != 4 && t.llp_pf != 6 && t.llp_pf != 8)
+        return PS_ERR_INVALID_ARG;
     if (t.split && t.split != 1 && t.split != 2 && t.split != 4) return PS_ERR_INVALID_ARG;
     if (t.llp_bands && t.llp_bands != 1 && t.llp_bands != 2) return PS_ERR_INVALID_ARG;
     if (t.prec_impl < 0 || t.prec_impl > 2 ||

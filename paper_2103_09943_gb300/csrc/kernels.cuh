@@ -28,7 +28,8 @@ struct LlpArgs {
     const CgGlobal *g;
     int cg;
     int ty;             // CG mode: output rows per warp (0: default)
-    int pf;             // CG mode: rows the loads run ahead (2, 4 or 6; 0: 2)
+    int pf;             // CG mode: rows the loads run ahead (2, 4 or 6 in registers,
+                        // 8: a ring of 8 rows in shared memory; 0: 2)
     int nbd;            // CG mode: bands per CTA (1 or 2; 0: 1)
 };
 

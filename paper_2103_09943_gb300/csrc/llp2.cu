@@ -60,8 +60,39 @@ struct Llp2Rows {
     static constexpr int UNR = (RW == 1) ? 3 : 1;
 };
 
+// Asynchronous copies global -> shared (sm_80+ cp.async); each lane copies
+// and later reads only its own bytes, so waiting on its own groups suffices.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One ring slot of a warp: its 64 columns of p and the statistics of both
+// columns of every lane, each array contiguous over the lanes.
+struct LlpSlot {
+    float2 p[32];
+    float4 s0[32], s1[32];
+};
+constexpr int kRing = 8;  // rows the ring holds (PF = kRing selects it)
+
 template <int RW, int TY, int PF>
 __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
+    // PF < kRing: the loads run PF rows ahead in registers; PF == kRing: they
+    // run kRing - 1 rows ahead as asynchronous copies into a ring of kRing
+    // rows per warp in shared memory
+    constexpr bool RING = (PF == kRing);
+    __shared__ LlpSlot ring[RING ? kWarps * kRing : 1];
     constexpr int G = 2 * RW + 2;
     constexpr int VALID = 64 - 2 * G;
     constexpr int NB = 2 * RW + 1;
@@ -100,40 +131,74 @@ __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
             for (int d = 0; d <= RW; ++d) mub[e][d] = sb[e][d] = 0.f;
         }
         float mm2[2] = {0.f, 0.f}, mm1[2] = {0.f, 0.f}, m0[2] = {0.f, 0.f};
-        // loads run PF rows ahead of their use
-        float2 qp[PF];
-        float4 qs0[PF], qs1[PF];
+        // loads run PF rows ahead of their use (registers), or kRing - 1
+        // rows ahead (the ring)
+        constexpr int PFR = RING ? 1 : PF;
+        float2 qp[PFR];
+        float4 qs0[PFR], qs1[PFR];
         constexpr int PH = ((G + 1 + 2) / 3) * 3;
         float2 ph[PH];
 #pragma unroll
         for (int d = 0; d < PH; ++d) ph[d] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < PF; ++k) {
-            qp[k] = *reinterpret_cast<const float2 *>(in + rowIn + gx);
-            qs0[k] = st4[rowA + gx];
-            qs1[k] = st4[rowA + gx + 1];
+        LlpSlot *wr = ring + (RING ? warp * kRing : 0);
+        int slot = 0;
+        auto issue = [&](int sl) {
+            cp_async8(&wr[sl].p[lane], in + rowIn + gx);
+            cp_async16(&wr[sl].s0[lane], st4 + rowA + gx);
+            cp_async16(&wr[sl].s1[lane], st4 + rowA + gx + 1);
+            cp_async_commit();
             rowIn += W;
             if (rowIn == HWi) rowIn = 0;
             rowA += W;
             if (rowA == HWi) rowA = 0;
+        };
+        if constexpr (RING) {
+#pragma unroll
+            for (int k = 0; k < kRing - 1; ++k) issue(k);
+        } else {
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                qp[k] = *reinterpret_cast<const float2 *>(in + rowIn + gx);
+                qs0[k] = st4[rowA + gx];
+                qs1[k] = st4[rowA + gx + 1];
+                rowIn += W;
+                if (rowIn == HWi) rowIn = 0;
+                rowA += W;
+                if (rowA == HWi) rowA = 0;
+            }
         }
 
         auto advance = [&]() -> float2 {
-            const float2 pin = qp[0];
-            const float4 s0 = qs0[0], s1 = qs1[0];
+            float2 pin;
+            float4 s0, s1;
+            if constexpr (RING) {
+                // this row's copies have landed once at most kRing - 2
+                // younger groups are pending; its slot is read, then the
+                // slot consumed one step earlier is refilled
+                cp_async_wait<kRing - 2>();
+                pin = wr[slot].p[lane];
+                s0 = wr[slot].s0[lane];
+                s1 = wr[slot].s1[lane];
+                issue(slot == 0 ? kRing - 1 : slot - 1);
+                slot = (slot == kRing - 1) ? 0 : slot + 1;
+            } else {
+                pin = qp[0];
+                s0 = qs0[0];
+                s1 = qs1[0];
 #pragma unroll
-            for (int k = 0; k < PF - 1; ++k) {
-                qp[k] = qp[k + 1];
-                qs0[k] = qs0[k + 1];
-                qs1[k] = qs1[k + 1];
+                for (int k = 0; k < PF - 1; ++k) {
+                    qp[k] = qp[k + 1];
+                    qs0[k] = qs0[k + 1];
+                    qs1[k] = qs1[k + 1];
+                }
+                qp[PF - 1] = *reinterpret_cast<const float2 *>(in + rowIn + gx);
+                qs0[PF - 1] = st4[rowA + gx];
+                qs1[PF - 1] = st4[rowA + gx + 1];
+                rowIn += W;
+                if (rowIn == HWi) rowIn = 0;
+                rowA += W;
+                if (rowA == HWi) rowA = 0;
             }
-            qp[PF - 1] = *reinterpret_cast<const float2 *>(in + rowIn + gx);
-            qs0[PF - 1] = st4[rowA + gx];
-            qs1[PF - 1] = st4[rowA + gx + 1];
-            rowIn += W;
-            if (rowIn == HWi) rowIn = 0;
-            rowA += W;
-            if (rowA == HWi) rowA = 0;
 #pragma unroll
             for (int d = 0; d < PH - 1; ++d) ph[d] = ph[d + 1];
             ph[PH - 1] = pin;
@@ -232,6 +297,7 @@ __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
             rowD += W;
             if (rowD == HWi) rowD = 0;
         }
+        if constexpr (RING) cp_async_wait<0>();
     }
     double pd = (double)part;
     for (int o = 16; o > 0; o >>= 1) pd += __shfl_xor_sync(kFull, pd, o);
@@ -527,6 +593,8 @@ template <int RW, int TY>
 void launch_pf(const LlpArgs &a, int N, cudaStream_t st) {
     if (a.nbd == 2)
         launch_ty2<RW, TY, 2>(a, N, st);
+    else if (a.pf == kRing)
+        launch_ty<RW, TY, kRing>(a, N, st);
     else if (a.pf == 6)
         launch_ty<RW, TY, 6>(a, N, st);
     else if (a.pf == 4)

@@ -245,3 +245,25 @@ def test_band_solve_times(cuda):
     assert all(0.0 < t <= total * 1.05 for t in ms), (ms, total)
     assert ms[1] < min(ms[0], ms[2], ms[3]), ms
     assert info.iters[1] == 0 and min(info.iters[0], info.iters[2], info.iters[3]) > 20
+
+
+@pytest.mark.parametrize("pf,db", [(8, 1), (2, 2), (8, 2)])
+def test_loop_kernel_variants_match_oracle(cuda, c0_oracle, pf, db):
+    # The CG loop's tunable kernel variants (the LLP kernel's loads through
+    # the shared-memory ring, pf = 8; the register-run blur-decimate,
+    # db = 2), forced through the recorded tuning: the same Z0 and Z as the
+    # oracle, at the plain-form bar.
+    sc, ref = c0_oracle
+    cfg = sc["config"]
+    hp = api.default_hrms_params(tol=1e-8, max_iter=5000)
+    try:
+        api.set_tuning(cfg.bands, cfg.H, cfg.W, cfg.ratio, 1, llp_pf=pf, db_impl=db)
+        Z, Z0, info = api.solve_hrms(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                     to_dev(sc["kernel"], cuda), cfg.ratio, hp, want_z0=True)
+    finally:
+        api.set_tuning(cfg.bands, cfg.H, cfg.W, cfg.ratio, 1)
+    Z, Z0 = to_np(Z), to_np(Z0)
+    assert all(s == 0 for s in info.status), info
+    for b in range(cfg.bands):
+        assert rel(Z0[b], ref["Z0"][b]) < PLAIN_TOL, b
+        assert rel(Z[b], ref["Z"][b]) < PLAIN_TOL, b
