@@ -15,7 +15,6 @@
 //              (Eq. u_p_solution), multiplier updates, stop test
 #include <math.h>
 
-#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -830,16 +829,18 @@ size_t admm_state_bytes(int R) {
 
 constexpr size_t kAdmmMaxSmem = 227 * 1024;
 
-// Q (nt x nt) as FP16 after the state, when the whole fits in shared memory.
+// Q (nt x nt, FP32) after the state, when the whole fits in shared memory
+// (n <= 13); larger kernels read it from global memory, where it stays in
+// L1 and L2 across the iterations.
 __host__ __device__ inline bool admm_q_fits(int R, size_t state) {
     const size_t nt = (size_t)(2 * R + 1) * (2 * R + 1);
-    return state + nt * nt * 2 <= kAdmmMaxSmem;
+    return state + nt * nt * sizeof(float) <= kAdmmMaxSmem;
 }
 
 size_t admm_smem_bytes(int R) {
     const size_t st = admm_state_bytes(R);
     const size_t nt = (size_t)(2 * R + 1) * (2 * R + 1);
-    return admm_q_fits(R, st) ? st + nt * nt * 2 : st;
+    return admm_q_fits(R, st) ? st + nt * nt * sizeof(float) : st;
 }
 
 __device__ __forceinline__ bool admm_q_in_smem(int R) {
@@ -881,12 +882,10 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
     const int chunk = (nt + parts - 1) / parts;
     float *pbuf = reinterpret_cast<float *>(T0);
     int *pcnt = reinterpret_cast<int *>(T0) + 3 * ntp;
-    // Q in shared memory as FP16 when it fits: its product enters z at most
-    // ~2.5e-4 of z's size (mu3 dominated by E^T E), so FP16's 4.9e-4 relative
-    // rounding costs ~1e-7 of z; otherwise Q is read from global memory
-    __half *qh = admm_q_in_smem(R) ? reinterpret_cast<__half *>(flag + 4) : nullptr;
-    if (qh)
-        for (int i = tid; i < nt * nt; i += nthr) qh[i] = __float2half_rn(Q[i]);
+    // Q (FP32) in shared memory when it fits, else read from global memory
+    float *qs = admm_q_in_smem(R) ? reinterpret_cast<float *>(flag + 4) : nullptr;
+    if (qs)
+        for (int i = tid; i < nt * nt; i += nthr) qs[i] = Q[i];
 
     const float a1 = p.alpha1 * p.mu1, a2 = p.alpha2 * p.mu2;
     for (int k = tid; k < nt; k += nthr) {
@@ -942,14 +941,14 @@ __global__ void __launch_bounds__(1024) admm_kernel(const float *__restrict__ Q,
             const int m0 = part * chunk, m1 = min(nt, m0 + chunk);
             float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
             int m = m0;
-            if (qh) {
+            if (qs) {
                 for (; m + 3 < m1; m += 4) {
-                    c0 = fmaf(__half2float(qh[m * nt + k]), wv[m], c0);
-                    c1 = fmaf(__half2float(qh[(m + 1) * nt + k]), wv[m + 1], c1);
-                    c2 = fmaf(__half2float(qh[(m + 2) * nt + k]), wv[m + 2], c2);
-                    c3 = fmaf(__half2float(qh[(m + 3) * nt + k]), wv[m + 3], c3);
+                    c0 = fmaf(qs[m * nt + k], wv[m], c0);
+                    c1 = fmaf(qs[(m + 1) * nt + k], wv[m + 1], c1);
+                    c2 = fmaf(qs[(m + 2) * nt + k], wv[m + 2], c2);
+                    c3 = fmaf(qs[(m + 3) * nt + k], wv[m + 3], c3);
                 }
-                for (; m < m1; ++m) c0 = fmaf(__half2float(qh[m * nt + k]), wv[m], c0);
+                for (; m < m1; ++m) c0 = fmaf(qs[m * nt + k], wv[m], c0);
             } else {
                 for (; m + 3 < m1; m += 4) {
                     c0 = fmaf(__ldg(Q + (size_t)m * nt + k), wv[m], c0);
