@@ -110,7 +110,10 @@ typedef struct ps_hrms_params {
                            are unchanged; the iteration count drops.
                            2: diagonal, P^{-1} = diag(s) with s > 0 per pixel
                            and band, from precond_diag or from the learned
-                           diagonal network diag_params.                   */
+                           diagonal network diag_params.
+                           3: Jacobi, P^{-1} = diag(A)^{-1} with A the Z0
+                           operator itself (its exact diagonal, computed
+                           once per solve; see ps_op_jacobi_diag).         */
     float precond_gamma; /* gamma of P (default 4; any value in [1, 8] gives
                            about the same iteration counts)                   */
     int warm;           /* start point of the Z0 CG when d_z_init is NULL.

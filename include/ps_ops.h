@@ -37,6 +37,19 @@ ps_status ps_op_blur_decimate_adj(const float *d_v, int N, int H, int W,
 ps_status ps_op_pan_stats(const float *d_pan, int H, int W, int r, float eps,
                           float *d_I, float *d_mu, float *d_s, void *stream);
 
+/* diag(A) of the operator A = B^T D^T D B + lambda L^T M L of
+ * Eq. Z_ini_matting (the same for every band), H x W into d_diag: the sum of
+ * u(i, j)^2 over the taps that meet the pixel at an LR site, plus lambda
+ * times the sum over the pixel's 5-point stencil pairs (a, b) of
+ * L_ma L_mb M_ab, M_ab from Eq. matting_matrix (denominator sigma^2 + eps)
+ * with (I, mu, s) as from ps_op_pan_stats. Its inverse is the Jacobi
+ * preconditioner of ps_hrms_params.precond = 3. Workspace:
+ * ps_op_workspace_size(1, H, W, ratio, R). */
+ps_status ps_op_jacobi_diag(int H, int W, int ratio, const float *d_kernel, int R,
+                            const float *d_I, const float *d_mu, const float *d_s, int r,
+                            float lambda, float *d_diag, void *d_ws, size_t ws_bytes,
+                            void *stream);
+
 /* out_b = (B^T D^T D B + lambda L^T M L) z_b, the operator of
  * Eq. Z_ini_matting, with M the matting matrix of I (Eq. matting_matrix,
  * denominator sigma^2 + eps) applied matrix-free from (I, mu, s).

@@ -19,8 +19,8 @@ from .fbmp import (PRIORS, apply_z0_prior, apply_zstep_prior, cg_op, filt, filt_
                    apply_zstep_system, bicubic_up, blur_decimate, blur_decimate_adj,
                    box_filter, cg_solve, estimate_kernel, estimate_omega,
                    guided_filter, kernel_error_pct, kernel_normal_eq,
-                   laplacian, matting_apply, pan_stats, pansharpen, pcg_diag_solve, pcg_solve,
-                   precond_apply, psnr, rel_l2, simplex_project, solve_band,
+                   jacobi_diag, laplacian, matting_apply, pan_stats, pansharpen,
+                   pcg_diag_solve, pcg_solve, precond_apply, psnr, rel_l2, simplex_project, solve_band,
                    solve_hrms, up_solve)
 
 __all__ = [
@@ -31,7 +31,7 @@ __all__ = [
     "apply_z0_system", "apply_zstep_system", "bicubic_up", "blur_decimate",
     "blur_decimate_adj", "box_filter", "cg_solve", "estimate_kernel",
     "estimate_omega", "guided_filter", "kernel_error_pct", "kernel_normal_eq",
-    "laplacian", "matting_apply", "pan_stats", "pansharpen", "pcg_diag_solve", "pcg_solve",
-    "precond_apply", "psnr", "rel_l2",
+    "jacobi_diag", "laplacian", "matting_apply", "pan_stats", "pansharpen", "pcg_diag_solve",
+    "pcg_solve", "precond_apply", "psnr", "rel_l2",
     "simplex_project", "solve_band", "solve_hrms", "up_solve",
 ]

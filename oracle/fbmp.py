@@ -246,6 +246,53 @@ def pcg_solve(b, u, c: int, lam: float, st: PanStats, gamma: float, x0=None,
     return x, max_iter, rel
 
 
+def jacobi_diag(u, c: int, st: PanStats, lam: float) -> np.ndarray:
+    """The diagonal of the Z0 operator A = B^T D^T D B + lam L^T M L of
+    Eq. Z_ini_matting (L symmetric), pixel by pixel, from its definition.
+    Data part: (B^T D^T D B)_{mm} is the sum over LR sites q of (D B)_{qm}^2;
+    pixel m = (y, x) meets site (k, l) through the tap (c k - y, c l - x), so
+    it is the sum of u(i, j)^2 over the taps with i = -y and j = -x mod c.
+    Prior part: (L M L)_{mm} = sum over a, b in the 5-point stencil of m of
+    L_{ma} M_{ab} L_{bm}, with M_{ab} the sum over the windows w_k holding
+    both a and b of delta_ab - (1 + (I_a - mu_k)(I_b - mu_k) s_k) / |w|
+    (Eq. matting_matrix, denominator sigma_k^2 + eps). The Jacobi
+    preconditioner of the Z0 CG is its inverse (an extension: the paper runs
+    plain CG)."""
+    u = f64(u)
+    H, W = st.I.shape
+    R = u.shape[0] // 2
+    y = np.arange(H)[:, None]
+    x = np.arange(W)[None, :]
+    data = np.zeros((H, W))
+    for i in range(-R, R + 1):
+        for j in range(-R, R + 1):
+            hit = ((y + i) % c == 0) & ((x + j) % c == 0)
+            data += np.where(hit, u[i + R, j + R] ** 2, 0.0)
+    r = st.r
+    nw = float((2 * r + 1) ** 2)
+
+    def at(a, dy, dx):   # value at pixel (y + dy, x + dx) on the torus
+        return np.roll(a, (-dy, -dx), axis=(0, 1))
+
+    stencil = [((0, 0), 4.0), ((-1, 0), -1.0), ((1, 0), -1.0), ((0, -1), -1.0), ((0, 1), -1.0)]
+    prior = np.zeros((H, W))
+    for da, la in stencil:
+        Ia = at(st.I, *da)
+        for db, lb in stencil:
+            Ib = at(st.I, *db)
+            Mab = np.zeros((H, W))
+            for ky in range(-r - 1, r + 2):
+                for kx in range(-r - 1, r + 2):
+                    inside = all(abs(k - d) <= r for k, d in ((ky, da[0]), (kx, da[1]),
+                                                              (ky, db[0]), (kx, db[1])))
+                    if not inside:
+                        continue
+                    mu_k, s_k = at(st.mu, ky, kx), at(st.s, ky, kx)
+                    Mab += (1.0 if da == db else 0.0) - (1.0 + (Ia - mu_k) * (Ib - mu_k) * s_k) / nw
+            prior += la * lb * Mab
+    return data + lam * prior
+
+
 def pcg_diag_solve(b, u, c: int, lam: float, st: PanStats, s, x0=None, tol: float = 1e-12,
                    max_iter: int = 100000):
     """Preconditioned CG on the Z0 system of Eq. Z_ini_matting with a diagonal

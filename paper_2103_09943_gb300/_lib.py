@@ -91,6 +91,7 @@ SIGNATURES = {
     "ps_op_blur_decimate": (_I, [_P, _I, _I, _I, _I, _P, _I, _P, _P]),
     "ps_op_blur_decimate_adj": (_I, [_P, _I, _I, _I, _I, _P, _I, _P, _P]),
     "ps_op_pan_stats": (_I, [_P, _I, _I, _I, _F, _P, _P, _P, _P]),
+    "ps_op_jacobi_diag": (_I, [_I, _I, _I, _P, _I, _P, _P, _P, _I, _F, _P, _P, _Z, _P]),
     "ps_op_apply_z0": (_I, [_P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _I, _F, _P, _P, _Z, _P]),
     "ps_op_guided_filter": (_I, [_P, _I, _I, _I, _P, _P, _P, _I, _P, _P, _Z, _P]),
     "ps_op_zstep": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _I, _F, _I, _P, _P, _Z,

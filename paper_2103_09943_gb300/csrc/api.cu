@@ -161,7 +161,7 @@ ps_status check_hrms(const ps_hrms_params *p) {
         return PS_ERR_INVALID_ARG;
     if (!isfinite(p->lambda) || !isfinite(p->eps) || !isfinite(p->tol))
         return PS_ERR_INVALID_ARG;
-    if (p->precond < 0 || p->precond > 2) return PS_ERR_INVALID_ARG;
+    if (p->precond < 0 || p->precond > 3) return PS_ERR_INVALID_ARG;
     if (p->precond == 1 && (!(p->precond_gamma > 0.f) || !isfinite(p->precond_gamma)))
         return PS_ERR_INVALID_ARG;
     if (p->precond == 2 && !p->precond_diag && !p->diag_params) return PS_ERR_INVALID_ARG;
@@ -936,6 +936,12 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
             return s;
         launch_diag_head(net_out, s_buf, (size_t)N * HW, 1.0f / 64.0f, st);
         sd = s_buf;
+    } else if (p->precond == 3) {
+        // Jacobi: s = 1 / diag(A), one copy per band, in the unused spectrum
+        // buffer; the loop then runs the diagonal preconditioner
+        float *s_buf = ws.at<float>(ws.L.spec);
+        launch_jacobi_diag(st4, d_kernel, R, c, H, W, p->r, p->lambda, N, 1, s_buf, st);
+        sd = s_buf;
     }
     if (!side) launch_adj(d_lrms, N, H, W, c, d_kernel, R, rv, st);  // b = B^T D^T X
     if (!d_z_init && p->warm >= 1 && !sc.early) {
@@ -983,7 +989,7 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
     launch_cg_init(rv, d_z_init ? ap : nullptr, d_z_init, x, rv, N, HW, bands, g, st);
     PrecArgs pa;
     memset(&pa, 0, sizeof(pa));
-    if (p->precond == 2) {
+    if (p->precond == 2 || p->precond == 3) {
         // z0 = s r0, rho = r0^T z0
         pa.r = rv;
         pa.z = ws.at<float>(ws.L.z);
@@ -1003,7 +1009,7 @@ ps_status solve_prelude(const SolveCall &sc, cudaStream_t st, CgLoopArgs *a) {
     a->x = x; a->rv = rv; a->pA = ws.at<float>(ws.L.pA); a->pB = ws.at<float>(ws.L.pB);
     a->ap = ap; a->v = v;
     a->bands = bands; a->g = g;
-    a->precond = p->precond;
+    a->precond = p->precond == 3 ? 2 : p->precond;  // Jacobi runs the diagonal loop
     a->pa = pa;
     a->sd = sd;
     a->tune = tuning_get(a->dev, N, H, W, c, p->r);
@@ -1862,6 +1868,24 @@ ps_status ps_op_apply_z0(const float *d_z, int N, int H, int W, int ratio,
     la.lam = lambda;
     la.out = d_out;
     launch_llp(la, LLP_APPLY, r, N, st);
+    return last_launch();
+}
+
+ps_status ps_op_jacobi_diag(int H, int W, int ratio, const float *d_kernel, int R,
+                            const float *d_I, const float *d_mu, const float *d_s, int r,
+                            float lambda, float *d_diag, void *d_ws, size_t ws_bytes,
+                            void *stream) {
+    ps_status s;
+    if ((s = check_dims(1, H, W, ratio, R)) != PS_OK) return s;
+    if (r < 1 || r > kMaxWinR || !isfinite(lambda)) return PS_ERR_INVALID_ARG;
+    if (!d_kernel || !d_I || !d_mu || !d_s || !d_diag) return PS_ERR_INVALID_ARG;
+    Ws ws;
+    if ((s = bind_ws(d_ws, ws_bytes, 1, H, W, ratio, R, &ws)) != PS_OK) return s;
+    if ((s = ensure_device(nullptr)) != PS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float4 *st4 = ws.at<float4>(ws.L.st4);
+    launch_pack_stats(d_I, d_mu, d_s, (size_t)H * W, st4, st);
+    launch_jacobi_diag(st4, d_kernel, R, ratio, H, W, r, lambda, 1, 0, d_diag, st);
     return last_launch();
 }
 

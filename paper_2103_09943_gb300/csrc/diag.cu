@@ -65,6 +65,78 @@ __global__ void __launch_bounds__(256) diag_head_kernel(const float4 *__restrict
     }
 }
 
+// diag(A) of the Z0 operator A = B^T D^T D B + lam L^T M L (Eq.
+// Z_ini_matting), one thread per pixel m = (y, x). Data part: the sum of
+// u(i, j)^2 over the taps with i = -y, j = -x (mod c), one of c^2 phase sums
+// formed first in shared memory. Prior part: sum over a, b in the 5-point
+// stencil of m of L_ma L_mb M_ab, M_ab summed over the windows w_k (centres
+// within RW + 1 of m) holding a and b: delta_ab - (1 + (I_a - mu_k)(I_b -
+// mu_k) s_k) / |w| (Eq. matting_matrix). Written N times (once per band),
+// inverted when `invert` (the Jacobi preconditioner s = 1 / diag(A)).
+template <int RW>
+__global__ void __launch_bounds__(256) jacobi_diag_kernel(const float4 *__restrict__ st4,
+                                                          const float *__restrict__ u, int R,
+                                                          int c, int H, int W, float lam,
+                                                          int N, int invert,
+                                                          float *__restrict__ out) {
+    __shared__ float ph[kMaxRatio * kMaxRatio];
+    const int n = 2 * R + 1;
+    for (int q = threadIdx.y * blockDim.x + threadIdx.x; q < c * c; q += blockDim.x * blockDim.y) {
+        const int a = q / c, b = q - (q / c) * c;
+        float acc = 0.f;
+        for (int i = -R; i <= R; ++i) {
+            if ((((i % c) + c) % c) != a) continue;
+            for (int j = -R; j <= R; ++j)
+                if ((((j % c) + c) % c) == b) {
+                    const float t = u[(i + R) * n + (j + R)];
+                    acc = fmaf(t, t, acc);
+                }
+        }
+        ph[q] = acc;
+    }
+    __syncthreads();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const float data = ph[((c - y % c) % c) * c + ((c - x % c) % c)];
+    constexpr int sy[5] = {0, -1, 1, 0, 0}, sx[5] = {0, 0, 0, -1, 1};
+    constexpr float lw[5] = {4.f, -1.f, -1.f, -1.f, -1.f};
+    constexpr float inw = 1.0f / (float)((2 * RW + 1) * (2 * RW + 1));
+    float Ia[5];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) Ia[a] = __ldg(&st4[(size_t)wrapi(y + sy[a], H) * W + wrapi(x + sx[a], W)]).x;
+    float prior = 0.f;
+#pragma unroll
+    for (int ky = -RW - 1; ky <= RW + 1; ++ky)
+#pragma unroll
+        for (int kx = -RW - 1; kx <= RW + 1; ++kx) {
+            bool in[5], any = false;
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+                const int dy = ky - sy[a], dx = kx - sx[a];
+                in[a] = dy >= -RW && dy <= RW && dx >= -RW && dx <= RW;
+                any = any || in[a];
+            }
+            if (!any) continue;
+            const float4 q = __ldg(&st4[(size_t)wrapi(y + ky, H) * W + wrapi(x + kx, W)]);
+            const float mu = q.y, sk = q.z;
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+                if (!in[a]) continue;
+                const float da = (Ia[a] - mu) * sk;
+#pragma unroll
+                for (int b = 0; b < 5; ++b) {
+                    if (!in[b]) continue;
+                    const float term = (a == b ? 1.f : 0.f) - inw * fmaf(da, Ia[b] - mu, 1.f);
+                    prior = fmaf(lw[a] * lw[b], term, prior);
+                }
+            }
+        }
+    const float d = fmaf(lam, prior, data);
+    const float v = invert ? 1.0f / d : d;
+    const size_t HW = (size_t)H * W, m = (size_t)y * W + x;
+    for (int b = 0; b < N; ++b) out[b * HW + m] = v;
+}
+
 int sm_count() {
     static int n = 0;
     if (!n) {
@@ -89,6 +161,17 @@ void launch_diag_precond(const float *r, const float *s, float *z, int N, size_t
     diag_precond_kernel<<<dim3((unsigned)per, N), 256, 0, st>>>(
         reinterpret_cast<const float4 *>(r), reinterpret_cast<const float4 *>(s),
         reinterpret_cast<float4 *>(z), n4, bands);
+}
+
+void launch_jacobi_diag(const float4 *st4, const float *u, int R, int c, int H, int W, int r,
+                        float lam, int N, int invert, float *out, cudaStream_t st) {
+    const dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
+    switch (r) {
+        case 1: jacobi_diag_kernel<1><<<grd, blk, 0, st>>>(st4, u, R, c, H, W, lam, N, invert, out); break;
+        case 2: jacobi_diag_kernel<2><<<grd, blk, 0, st>>>(st4, u, R, c, H, W, lam, N, invert, out); break;
+        case 3: jacobi_diag_kernel<3><<<grd, blk, 0, st>>>(st4, u, R, c, H, W, lam, N, invert, out); break;
+        default: jacobi_diag_kernel<4><<<grd, blk, 0, st>>>(st4, u, R, c, H, W, lam, N, invert, out); break;
+    }
 }
 
 void launch_diag_head(const float *zd, float *s, size_t n, float floor_, cudaStream_t st) {

@@ -105,6 +105,9 @@ cudaError_t fft_set_attrs();
 // head s = max((zd - up) / 255, floor) of the diagonal network
 void launch_diag_precond(const float *r, const float *s, float *z, int N, size_t HW,
                          CgBand *bands, cudaStream_t st);
+// diag(A) of the Z0 operator (or its inverse), N copies of H x W
+void launch_jacobi_diag(const float4 *st4, const float *u, int R, int c, int H, int W, int r,
+                        float lam, int N, int invert, float *out, cudaStream_t st);
 void launch_diag_head(const float *zd, float *s, size_t n, float floor_, cudaStream_t st);
 
 // prior.cu: the alternative cross-channel priors

@@ -60,6 +60,20 @@ def apply_z0(z, kernel, ratio, I, mu, s, r, lam):
     return out
 
 
+def jacobi_diag(kernel, ratio, I, mu, s, r, lam):
+    """diag(B^T D^T D B + lam L^T M L) of shape (H, W) (ps_op_jacobi_diag)."""
+    H, W = I.shape
+    for t, nm in ((kernel, "kernel"), (I, "I"), (mu, "mu"), (s, "s")):
+        _f32(t, nm)
+    R = kernel.shape[0] // 2
+    out = torch.empty((H, W), dtype=torch.float32, device=I.device)
+    ws = _ws(1, H, W, ratio, R, I.device)
+    _check(_lib.load().ps_op_jacobi_diag(H, W, ratio, _ptr(kernel), R, _ptr(I), _ptr(mu), _ptr(s),
+                                         r, ctypes.c_float(lam), _ptr(out), _ptr(ws), ws.numel(),
+                                         _stream()))
+    return out
+
+
 def guided_filter(q, I, mu, s, r):
     """Guided filter of q (N, H, W) with guide I."""
     N, H, W = q.shape

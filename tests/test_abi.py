@@ -120,10 +120,10 @@ def test_argument_errors_return_before_launch(lib):
     st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
                            None, None, fake, 1 << 30, None)
     assert st == 1
-    # the diagonal preconditioner: a selector in 0..2, a 16-byte aligned
+    # the diagonal preconditioner: a selector in 0..3, a 16-byte aligned
     # diagonal, and room for the diagonal network when it supplies s
     bad = HrmsParams.from_buffer_copy(hp)
-    bad.precond = 3
+    bad.precond = 4
     bad.precond_diag = 0x1000
     st = lib.ps_solve_hrms(fake, fake, fake, 4, 256, 256, 4, 4, ctypes.byref(bad), None, fake,
                            None, None, fake, 1 << 30, None)

@@ -71,3 +71,41 @@ def test_trained_network_saves_iterations(cuda):
     assert rel(z_cnn, z0) < 0.8 * rel(up, z0)
     assert out[2][1] < 0.85 * out[0][1], (out[0][1], out[2][1])
     assert rel(out[2][0], z0) < 1e-3
+
+
+def test_heldout_warm_start_matches_oracle_on_crops(cuda):
+    # The held-out scenes of the warm start's evaluation (seeds 5000 and up,
+    # 8 x 2048^2 generated with the training generator's shape density):
+    # 256 x 256 crops of the first two, each its own periodic scene, through
+    # ps_pansharpen with the network's warm start and the preconditioned CG
+    # (tolerance 1e-6), against the FP64 oracle (Algorithm 1, then Algorithm 2
+    # with every linear system solved to 1e-11): every band within rel-L2
+    # 1e-3, the bar of the mixed-precision, warm-started form.
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2103_09943_gb300 import cnn, eval_warm
+    wpath = os.path.join(os.path.dirname(cnn.__file__), "weights", "warm_cnn.npz")
+    net = cnn.WarmStartNet.load(wpath, device=cuda)
+    crops = [synth.crop_scene(synth.make_scene(c), 256)
+             for c in eval_warm.scene_configs(2, 2048, 5000)]
+
+    def ref(sc):
+        cfg = sc["config"]
+        return oracle.pansharpen(sc["lrms"], sc["pan"], cfg.ratio, cfg.R,
+                                 hp=oracle.HrmsParams(tol=1e-11), threads=cfg.bands)
+
+    with ThreadPoolExecutor(max_workers=len(crops)) as ex:
+        refs = list(ex.map(ref, crops))
+    hp = api.default_hrms_params(precond=1, warm=2, cnn_params=net.params.data_ptr(),
+                                 zstep_fp32=1, tol=1e-6)
+    for sc, r in zip(crops, refs):
+        cfg = sc["config"]
+        Z, K, kinfo, info = api.pansharpen(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
+                                           cfg.ratio, cfg.R, hparams=hp)
+        assert all(s == 0 for s in info.status), info
+        Z = to_np(Z)
+        err = [rel(Z[b], r["Z"][b]) for b in range(cfg.bands)]
+        print(f"\nheld-out seed {cfg.seed} 256^2 crop, CG iters {info.iters}: kernel "
+              f"{rel(to_np(K), r['kernel']):.2e}; Z per band {['%.2e' % e for e in err]}")
+        assert rel(to_np(K), r["kernel"]) < 1e-4
+        assert max(err) < 1e-3

@@ -148,3 +148,29 @@ def test_diag_fit_is_the_one_step_error():
     s = cnn.diag_head(up[:2, :2] + cnn.SCALE * c, up[:2, :2])
     np.testing.assert_allclose(s, [[2.0, cnn.DIAG_FLOOR], [cnn.DIAG_FLOOR, cnn.DIAG_FLOOR]],
                                rtol=1e-12)
+
+
+@pytest.mark.parametrize("H,W,c,R,r,lam", [(16, 16, 4, 2, 1, 2e-2), (12, 20, 2, 3, 1, 5e-3),
+                                           (18, 12, 3, 2, 2, 1e-1)])
+def test_jacobi_diag_is_the_dense_operators_diagonal(H, W, c, R, r, lam):
+    # diag(B^T D^T D B + lam L^T M L) assembled entry by entry (dense matrices
+    # from the definitions), against the oracle's per-pixel formula; a
+    # non-square torus, ratios 2-4, window radius 1 and 2
+    rng = np.random.default_rng(H * W + c + R + r)
+    u = kern(R, rng)
+    Y = rng.random((H, W)) * 255
+    A, *_ = _dense_A(H, W, c, u, Y, r, 1.0, lam)
+    st = oracle.pan_stats(Y, r, 1.0)
+    d = oracle.jacobi_diag(u, c, st, lam)
+    np.testing.assert_allclose(d.ravel(), np.diag(A), rtol=1e-11, atol=1e-12)
+    assert d.min() > 0
+
+
+def test_jacobi_pcg_reaches_the_dense_solution():
+    # the Jacobi preconditioner, s = 1 / diag(A), in the oracle's diagonal PCG
+    t = _tiny(13)
+    s = 1.0 / oracle.jacobi_diag(t["u"], t["c"], t["st"], t["lam"])
+    assert np.allclose(s.ravel(), 1.0 / np.diag(t["A"]), rtol=1e-11)
+    ref = np.linalg.solve(t["A"], t["b"].ravel()).reshape(t["H"], t["W"])
+    z, it, rel = oracle.pcg_diag_solve(t["b"], t["u"], t["c"], t["lam"], t["st"], s, tol=1e-12)
+    assert oracle.rel_l2(z, ref) < 1e-9
