@@ -503,6 +503,36 @@ def compare_variants(api, X, Y, cfg, kp, net, dev, steps=3):
     return out
 
 
+def run_profile_batch(args):
+    """No timing: the uneven batch's scenes one by one through ps_pansharpen in
+    the bench's form, the CG loop launched from the host (the batch runs every
+    scene's loop inside one graph, where a profiler does not see the loop's
+    kernels), once after one untimed pass; for launch lists of the bench's
+    kernels."""
+    cfgs, arrays = make_batch_scenes(args.batch, 3000)
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2103_09943_gb300 import api
+    net, _ = load_warm_net(args.warm, dev)
+    warm = {"none": 0, "bicubic": 1, "cnn": 2}[args.warm] if (net or args.warm != "cnn") else 0
+    hp = api.default_hrms_params(precond=1 if args.precond == "fft" else 0, warm=warm,
+                                 cnn_params=net.params.data_ptr() if net else None,
+                                 zstep_fp32=0 if args.zstep_fp64 else 1, host_loop=1)
+    kp = api.default_kernel_params()
+    scenes = [(torch.from_numpy(a[0]).to(dev), torch.from_numpy(a[1]).to(dev), c)
+              for a, c in zip(arrays, cfgs)]
+    for _ in range(2):
+        for X, Y, c in scenes:
+            api.set_tuning(c.bands, c.H, c.W, c.ratio, hp.r, split=1)   # as in the batch
+            api.pansharpen(X, Y, c.ratio, c.R, kp, hp, info=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_batch": len(cfgs), "workload": batch_name(cfgs)}))
+    return 0
+
+
 def run_profile_warm(args):
     """The warm-start network's inference on the workload's 8 bands (trained
     weights when present, else the seeded initial ones), three times."""
@@ -990,6 +1020,9 @@ def parse(argv=None):
                     help="with --profile-solve: B bands of S x S instead of the workload's "
                          "size (the same scene recipe), e.g. 2x4096 for a case whose vectors "
                          "exceed the L2 cache")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="no timing: the batch's scenes one by one in the bench's form with "
+                         "host-launched CG loops, twice (for profiler launch lists)")
     ap.add_argument("--profile-warm", action="store_true",
                     help="no timing: run the warm-start network on the workload's bicubic "
                          "upsampling and PAN three times (for profiler captures)")
@@ -1024,6 +1057,8 @@ def main(argv=None):
         return run_profile_solve(args)
     if args.profile_warm:
         return run_profile_warm(args)
+    if args.profile_batch:
+        return run_profile_batch(args)
     if args.priors:
         return run_priors(args)
     if args.workload == "c3":

@@ -45,7 +45,7 @@ def test_warm_start_reaches_the_same_solution(cuda):
 
 def test_trained_network_saves_iterations(cuda):
     # a held-out scene of the 8-band 1024 x 1024 workload (seed outside the
-    # training seeds 1000-1159): the committed network's start is closer to Z0
+    # training seeds 1000-2999): the committed network's start is closer to Z0
     # than the bicubic one and cuts the preconditioned CG's iterations, and
     # both starts reach the same Z0
     import os
