@@ -504,12 +504,17 @@ def compare_variants(api, X, Y, cfg, kp, net, dev, steps=3):
 
 
 def run_profile_batch(args):
-    """No timing: the uneven batch's scenes one by one through ps_pansharpen in
-    the bench's form, the CG loop launched from the host (the batch runs every
-    scene's loop inside one graph, where a profiler does not see the loop's
-    kernels), once after one untimed pass; for launch lists of the bench's
-    kernels."""
+    """No timing: scenes of the uneven batch one by one through ps_pansharpen
+    in the bench's form, the CG loop launched from the host (the batch runs
+    every scene's loop inside one graph, where a profiler does not see the
+    loop's kernels), one pass; for launch lists of the bench's kernels. With
+    --profile-scenes K, K scenes evenly spaced over the batch (a profiler
+    serialises every launch: the whole batch is tens of thousands)."""
     cfgs, arrays = make_batch_scenes(args.batch, 3000)
+    if args.profile_scenes:
+        step = max(1, len(cfgs) // args.profile_scenes)
+        pick = list(range(0, len(cfgs), step))[:args.profile_scenes]
+        cfgs, arrays = [cfgs[i] for i in pick], [arrays[i] for i in pick]
     import torch
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
@@ -524,12 +529,12 @@ def run_profile_batch(args):
     kp = api.default_kernel_params()
     scenes = [(torch.from_numpy(a[0]).to(dev), torch.from_numpy(a[1]).to(dev), c)
               for a, c in zip(arrays, cfgs)]
-    for _ in range(2):
-        for X, Y, c in scenes:
-            api.set_tuning(c.bands, c.H, c.W, c.ratio, hp.r, split=1)   # as in the batch
-            api.pansharpen(X, Y, c.ratio, c.R, kp, hp, info=False)
+    for X, Y, c in scenes:
+        api.set_tuning(c.bands, c.H, c.W, c.ratio, hp.r, split=1)   # as in the batch
+        api.pansharpen(X, Y, c.ratio, c.R, kp, hp, info=False)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_batch": len(cfgs), "workload": batch_name(cfgs)}))
+    print(json.dumps({"profile_batch": len(cfgs),
+                      "scenes": [f"{c.bands}x{c.H}x{c.W} R{c.R}" for c in cfgs]}))
     return 0
 
 
@@ -1022,7 +1027,9 @@ def parse(argv=None):
                          "exceed the L2 cache")
     ap.add_argument("--profile-batch", action="store_true",
                     help="no timing: the batch's scenes one by one in the bench's form with "
-                         "host-launched CG loops, twice (for profiler launch lists)")
+                         "host-launched CG loops, once (for profiler launch lists)")
+    ap.add_argument("--profile-scenes", type=int, default=0, metavar="K",
+                    help="with --profile-batch: K scenes evenly spaced over the batch")
     ap.add_argument("--profile-warm", action="store_true",
                     help="no timing: run the warm-start network on the workload's bicubic "
                          "upsampling and PAN three times (for profiler captures)")
