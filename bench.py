@@ -352,7 +352,13 @@ def cg_iteration_roofline(api, X, Y, kern, cfg, hp, peak_gbs, dev):
 # iteration per px.band, summed over its kernels, from one-kernel ncu
 # captures of a scene larger than L2; keyed by (preconditioned, bands). The
 # capture commands and per-kernel figures are in profiles/.
-TRAFFIC_PER_UNIT = {}
+TRAFFIC_PER_UNIT = {
+    (True, 8): {"bytes_per_unit": 70.44,
+                "note": "sum over db_site, llp_cgq2, cg_update_site and the three register-resident "
+                        "preconditioner passes of dram__bytes_read.sum + dram__bytes_write.sum, one "
+                        "ncu capture per kernel at 8 x 2048^2 (the roofline scene, cold caches): "
+                        "profiles/cg_iteration_8x2048_dram.md"},
+}
 
 
 def launches_per_step(cfg, hp, cg_iters, split=1) -> int:
