@@ -54,6 +54,11 @@ def test_precond_matches_oracle(cuda, N, H, W, c, R, lg):
     (3, 2048, 256, 4, 3, 8e-4),
     (1, 256, 4096, 2, 3, 1e-2),   # 4096-wide rows (1024-thread row CTAs)
     (1, 4096, 256, 4, 3, 8e-4),   # 4 columns of 4096 (1024-thread column CTAs)
+    (2, 768, 768, 4, 4, 8e-4),    # 3 * 2^k: 24 values a thread, radices 24, 4, 8
+    (3, 1536, 384, 4, 5, 8e-4),   # 24, 8, 8 columns; 24, 4, 4 rows; odd band count
+    (1, 384, 1536, 2, 3, 1e-2),   # ratio 2 with 24 values a thread
+    (2, 768, 1024, 4, 4, 8e-4),   # 3 * 2^k columns, power-of-two rows
+    (2, 2048, 768, 4, 3, 8e-4),   # power-of-two columns, 3 * 2^k rows
 ])
 def test_register_and_shared_passes_match_oracle(cuda, N, H, W, c, R, lg):
     # The register-resident passes (power-of-two sides, ratios 2 and 4) and
