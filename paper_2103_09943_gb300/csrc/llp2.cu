@@ -49,16 +49,19 @@ __device__ __forceinline__ float hsum(float v0, float v1) {
     }
 }
 
-// Output rows per warp: a multiple of 3 for r = 1, so that the 3-deep rolling
-// buffers cycle within the 3-way unrolled walk. Two lengths per radius (the
-// autotuner picks): longer walks spend less on the 2G halo rows, shorter
-// ones give more warps.
+// Output rows per warp, two lengths per radius (the autotuner picks): longer
+// walks spend less on the 2G halo rows, shorter ones give more warps. For
+// r = 1 the whole walk (2G + rows) is a multiple of 12, so that it splits
+// into whole unrolled blocks (below).
 template <int RW>
 struct Llp2Rows {
-    static constexpr int LONG = (RW == 1) ? 66 : 64;
-    static constexpr int SHORT = (RW == 1) ? 33 : 32;
+    static constexpr int LONG = 64;
+    static constexpr int SHORT = (RW == 1) ? 28 : 32;
     static constexpr int UNR = (RW == 1) ? 3 : 1;
 };
+
+constexpr int llp_gcd(int a, int b) { return b ? llp_gcd(b, a % b) : a; }
+constexpr int llp_lcm(int a, int b) { return a / llp_gcd(a, b) * b; }
 
 // Asynchronous copies global -> shared (sm_80+ cp.async); each lane copies
 // and later reads only its own bytes, so waiting on its own groups suffices.
@@ -281,22 +284,37 @@ __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
                                4.0f * mm1[1] - mm2[1] - m0[1] - ql1 - qr1);
         };
 
-        for (int step = 0; step < 2 * G; ++step) (void)advance();
         float2 *outb = reinterpret_cast<float2 *>(a.out + (size_t)b * HW);
-#pragma unroll Llp2Rows<RW>::UNR
-        for (int yy = 0; yy < TY; ++yy) {
+        // The walk: 2G rows that fill the chain, then TY output rows. Every
+        // rolling buffer shifts by one slot a row; in blocks of U rows, U a
+        // multiple of every buffer's depth, each slot keeps one register
+        // across the loop, so no register with a load in flight is ever
+        // copied (a copy would wait for that load).
+        constexpr int U = llp_lcm(Llp2Rows<RW>::UNR, PFR);
+        constexpr int TOT = 2 * G + TY;
+        int yy = -2 * G;
+        auto row = [&]() {
             float2 val = advance();
-            if (out_lane && y0 + yy < H) {
-                val.x *= a.lam;
-                val.y *= a.lam;
-                outb[(rowD + gx) >> 1] = val;
-                // the output row is the input row of G steps ago
-                const float2 pv = ph[PH - 1 - G];
-                part = fmaf(pv.x, val.x, fmaf(pv.y, val.y, part));
+            if (yy >= 0) {
+                if (out_lane && y0 + yy < H) {
+                    val.x *= a.lam;
+                    val.y *= a.lam;
+                    outb[(rowD + gx) >> 1] = val;
+                    // the output row is the input row of G steps ago
+                    const float2 pv = ph[PH - 1 - G];
+                    part = fmaf(pv.x, val.x, fmaf(pv.y, val.y, part));
+                }
+                rowD += W;
+                if (rowD == HWi) rowD = 0;
             }
-            rowD += W;
-            if (rowD == HWi) rowD = 0;
+            ++yy;
+        };
+        int s = 0;
+        for (; s + U <= TOT; s += U) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) row();
         }
+        for (; s < TOT; ++s) row();
         if constexpr (RING) cp_async_wait<0>();
     }
     double pd = (double)part;
@@ -512,28 +530,39 @@ __global__ void __launch_bounds__(128) llp_cgq2b_kernel(LlpArgs a) {
             }
         };
 
-        float2 val[2];
-        for (int step = 0; step < 2 * G; ++step) advance(val);
         float2 *out0 = reinterpret_cast<float2 *>(a.out + (size_t)b0 * HW);
         float2 *out1 = reinterpret_cast<float2 *>(a.out + (size_t)(b0 + 1) * HW);
-#pragma unroll Llp2Rows<RW>::UNR
-        for (int yy = 0; yy < TY; ++yy) {
+        // the walk in whole blocks of U rows, as in the one-band kernel
+        constexpr int U = llp_lcm(Llp2Rows<RW>::UNR, PF);
+        constexpr int TOT = 2 * G + TY;
+        int yy = -2 * G;
+        auto row = [&]() {
+            float2 val[2];
             advance(val);
-            if (out_lane && y0 + yy < H) {
+            if (yy >= 0) {
+                if (out_lane && y0 + yy < H) {
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    if (q == 1 && !two) break;
-                    val[q].x *= a.lam;
-                    val[q].y *= a.lam;
-                    (q ? out1 : out0)[(rowD + gx) >> 1] = val[q];
-                    // the output row is the input row of G steps ago
-                    const float2 pv = ph[q][PH - 1 - G];
-                    part[q] = fmaf(pv.x, val[q].x, fmaf(pv.y, val[q].y, part[q]));
+                    for (int q = 0; q < 2; ++q) {
+                        if (q == 1 && !two) break;
+                        val[q].x *= a.lam;
+                        val[q].y *= a.lam;
+                        (q ? out1 : out0)[(rowD + gx) >> 1] = val[q];
+                        // the output row is the input row of G steps ago
+                        const float2 pv = ph[q][PH - 1 - G];
+                        part[q] = fmaf(pv.x, val[q].x, fmaf(pv.y, val[q].y, part[q]));
+                    }
                 }
+                rowD += W;
+                if (rowD == HWi) rowD = 0;
             }
-            rowD += W;
-            if (rowD == HWi) rowD = 0;
+            ++yy;
+        };
+        int s = 0;
+        for (; s + U <= TOT; s += U) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) row();
         }
+        for (; s < TOT; ++s) row();
     }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
