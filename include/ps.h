@@ -197,11 +197,11 @@ ps_status ps_sync_status(void *stream);
 typedef struct ps_tuning {
     int prec_rows;       /* rows per CTA of the preconditioner's row FFTs   */
     int llp_rows;        /* output rows per warp of the CG loop's LLP kernel */
-    int llp_pf;          /* rows its loads run ahead (2, 4, 6 in registers;
+    int llp_pf;          /* rows its loads run ahead (2, 3, 4 in registers;
                             8: a ring of 8 rows filled by asynchronous
                             copies into shared memory)                      */
     float prec_us[4];    /* candidates 1, 2, 4, 8 rows                      */
-    float llp_us[6];     /* candidates: long walk with 2, 4, 6 rows ahead,
+    float llp_us[6];     /* candidates: long walk with 2, 3, 4 rows ahead,
                             then the short walk                             */
     int split;           /* parallel branches of a CG iteration (1, 2, 4)    */
     float split_us[3];   /* two CG iterations, candidates 1, 2, 4 branches   */
@@ -219,6 +219,13 @@ typedef struct ps_tuning {
                             default (1)                                      */
     float db_impl_us[2]; /* one launch: candidates 1, 2                      */
     float llp_ring_us[2]; /* LLP kernel with the ring: long, short walk      */
+    int llp_form;        /* form of that LLP kernel: 1 the general walk (two
+                            columns a lane, any r); for r = 1 only, with one
+                            band per CTA, 2 or 4 rows ahead and 64 or 32 rows
+                            a warp: 2 the lean two-column walk, 4 four columns
+                            a lane (W % 4 == 0); 0 the default (1)           */
+    float llp_lean_us[8]; /* the lean walks: form 2 long walk with 2, 4 rows
+                            ahead, short walk with 2, 4; then form 4 alike    */
 } ps_tuning;
 
 /* Autotuner: times every candidate of each tunable kernel on N bands of
@@ -235,8 +242,8 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r,
 /* The launch choices recorded for these sizes on the current device (all
  * zero: the defaults), and their replacement, e.g. with choices an earlier
  * process's ps_autotune found. Only the choice fields (prec_rows, llp_rows,
- * llp_pf, split, llp_bands, prec_impl, db_impl) are read or written; 0 keeps
- * a default. */
+ * llp_pf, split, llp_bands, prec_impl, db_impl, llp_form) are read or
+ * written; 0 keeps a default. */
 ps_status ps_get_tuning(int N, int H, int W, int ratio, int r, ps_tuning *h_out);
 ps_status ps_set_tuning(int N, int H, int W, int ratio, int r, const ps_tuning *h_in);
 

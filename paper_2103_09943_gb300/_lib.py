@@ -40,7 +40,8 @@ class Tuning(ctypes.Structure):
                 ("split_us", ctypes.c_float * 3), ("llp_bands", ctypes.c_int),
                 ("llp2_us", ctypes.c_float * 2), ("prec_impl", ctypes.c_int),
                 ("prec_impl_us", ctypes.c_float * 2), ("db_impl", ctypes.c_int),
-                ("db_impl_us", ctypes.c_float * 2), ("llp_ring_us", ctypes.c_float * 2)]
+                ("db_impl_us", ctypes.c_float * 2), ("llp_ring_us", ctypes.c_float * 2),
+                ("llp_form", ctypes.c_int), ("llp_lean_us", ctypes.c_float * 8)]
 
 
 class BandInfo(ctypes.Structure):

@@ -93,7 +93,7 @@ def autotune(N, H, W, ratio, R, r=1, ws=None, device=None, lrms=None, pan=None,
             "prec_us": {str(k): round(v, 2) for k, v in zip((1, 2, 4, 8), t.prec_us) if v},
             "llp_pf": t.llp_pf,
             "llp_us": {f"{w}/{pf}": round(t.llp_us[3 * i + j], 2)
-                       for i, w in enumerate(("long", "short")) for j, pf in enumerate((2, 4, 6))},
+                       for i, w in enumerate(("long", "short")) for j, pf in enumerate((2, 3, 4))},
             "llp_bands": t.llp_bands,
             "llp2_us": {w: round(v, 2) for w, v in zip(("long/2", "short/2"), t.llp2_us) if v},
             "split": t.split,
@@ -104,13 +104,18 @@ def autotune(N, H, W, ratio, R, r=1, ws=None, device=None, lrms=None, pan=None,
             "llp_ring_us": {w: round(v, 2) for w, v in zip(("long", "short"), t.llp_ring_us)
                             if v},
             "db_impl": t.db_impl,
-            "db_impl_us": {n: round(v, 2) for n, v in zip(("site", "runs"), t.db_impl_us) if v}}
+            "db_impl_us": {n: round(v, 2) for n, v in zip(("site", "runs"), t.db_impl_us) if v},
+            "llp_form": t.llp_form,
+            "llp_lean_us": {f"form{f}/{w}/{pf}": round(t.llp_lean_us[4 * h + 2 * i + j], 2)
+                            for h, f in enumerate((2, 4))
+                            for i, w in enumerate(("long", "short"))
+                            for j, pf in enumerate((2, 4)) if t.llp_lean_us[4 * h + 2 * i + j]}}
 
 
 def set_tuning(N, H, W, ratio, r=1, **choices) -> None:
     """Record launch choices for these sizes (ps_set_tuning): prec_rows,
-    llp_rows, llp_pf, split, llp_bands, prec_impl, db_impl; 0 or absent keeps a
-    default."""
+    llp_rows, llp_pf, split, llp_bands, prec_impl, db_impl, llp_form; 0 or absent
+    keeps a default."""
     t = Tuning()
     for k, v in choices.items():
         setattr(t, k, v)
@@ -121,7 +126,7 @@ def get_tuning(N, H, W, ratio, r=1) -> dict:
     t = Tuning()
     _check(_lib.load().ps_get_tuning(N, H, W, ratio, r, ctypes.byref(t)))
     return {k: getattr(t, k) for k in ("prec_rows", "llp_rows", "llp_pf", "split", "llp_bands",
-                                       "prec_impl", "db_impl")}
+                                       "prec_impl", "db_impl", "llp_form")}
 
 
 @dataclass

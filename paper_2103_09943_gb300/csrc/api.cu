@@ -430,6 +430,7 @@ void enqueue_bands(const CgLoopArgs &a, int b0, int n, const float *p_old, float
     la.ty = a.tune.llp_rows;
     la.pf = a.tune.llp_pf;
     la.nbd = a.tune.llp_bands;
+    la.form = a.tune.llp_form;
     launch_llp_cgq2(la, a.r, n, st);
     launch_cg_update(a.x + o, a.rv + o, p_new + o, a.ap + o, v, a.u, a.R, a.c, n, a.H, a.W, bands,
                      a.g, st);
@@ -1481,7 +1482,7 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
     la.g = g;
     la.cg = 1;
     float bestl = 1e30f;
-    const int pfs[3] = {2, 4, 6};
+    const int pfs[3] = {2, 3, 4};
     for (int k = 0; k < 2; ++k) {
         for (int q = 0; q < 3; ++q) {
             la.ty = llp_cgq2_rows(r, k);
@@ -1507,6 +1508,30 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
             out.llp_pf = 8;
         }
     }
+    // the lean walks (r = 1): two and four columns a lane, long and short
+    // walks, 2 and 4 rows ahead
+    out.llp_form = 1;
+    const int forms[2] = {2, 4};
+    for (int f = 0; f < 2; ++f) {
+        if (!llp_lean_supported(forms[f], r, W)) continue;
+        const int pf4[2] = {2, 4};
+        la.form = forms[f];
+        for (int k = 0; k < 2; ++k) {
+            for (int q = 0; q < 2; ++q) {
+                la.ty = llp_lean_rows(k);
+                la.pf = pf4[q];
+                const float us = timed([&] { launch_llp_cgq2(la, r, N, st); });
+                out.llp_lean_us[f * 4 + k * 2 + q] = us;
+                if (us < bestl) {
+                    bestl = us;
+                    out.llp_rows = la.ty;
+                    out.llp_pf = la.pf;
+                    out.llp_form = forms[f];
+                }
+            }
+        }
+        la.form = 0;
+    }
     // two bands per CTA (shared statistics), long and short walks
     out.llp_bands = 1;
     for (int k = 0; k < 2 && N >= 2; ++k) {
@@ -1520,6 +1545,7 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
             out.llp_rows = la.ty;
             out.llp_pf = la.pf;
             out.llp_bands = 2;
+            out.llp_form = 1;
         }
     }
     // branches of the CG iteration, when the scene is given: whole solves of
@@ -1537,7 +1563,7 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
             if (splits[k] > 1 && N < 2 * splits[k]) continue;
             tuning_set(dev, N, H, W, ratio, r,
                        Tuning{out.prec_rows, out.llp_rows, splits[k], out.llp_pf,
-                              out.llp_bands, out.prec_impl, out.db_impl});
+                              out.llp_bands, out.prec_impl, out.db_impl, out.llp_form});
             float best = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, st);
@@ -1562,7 +1588,7 @@ ps_status ps_autotune(int N, int H, int W, int ratio, int R, int r, const float 
     if ((s = last_launch()) != PS_OK) return s;
     tuning_set(dev, N, H, W, ratio, r,
                Tuning{out.prec_rows, out.llp_rows, out.split, out.llp_pf, out.llp_bands,
-                      out.prec_impl, out.db_impl});
+                      out.prec_impl, out.db_impl, out.llp_form});
     if (h_out) *h_out = out;
     return PS_OK;
 }
@@ -1580,6 +1606,7 @@ ps_status ps_get_tuning(int N, int H, int W, int ratio, int r, ps_tuning *h_out)
     h_out->llp_bands = t.llp_bands;
     h_out->prec_impl = t.prec_impl;
     h_out->db_impl = t.db_impl;
+    h_out->llp_form = t.llp_form;
     return PS_OK;
 }
 
@@ -1590,9 +1617,16 @@ ps_status ps_set_tuning(int N, int H, int W, int ratio, int r, const ps_tuning *
     if (r < 1 || r > kMaxWinR) return PS_ERR_INVALID_ARG;
     const ps_tuning &t = *h_in;
     if (t.prec_rows && !precond_rows_ok(H, W, ratio, t.prec_rows)) return PS_ERR_INVALID_ARG;
-    if (t.llp_rows && t.llp_rows != llp_cgq2_rows(r, 0) && t.llp_rows != llp_cgq2_rows(r, 1))
+    if (t.llp_form < 0 || t.llp_form == 3 || t.llp_form > 4) return PS_ERR_INVALID_ARG;
+    const bool lean = t.llp_form >= 2;
+    if (lean && (!llp_lean_supported(t.llp_form, r, W) || t.llp_bands == 2 || t.llp_pf == 3 ||
+                 t.llp_pf == 8))
         return PS_ERR_INVALID_ARG;
-    if (t.llp_pf && t.llp_pf != 2 && t.llp_pf != 4 && t.llp_pf != 6 && t.llp_pf != 8)
+    if (lean ? (t.llp_rows && t.llp_rows != llp_lean_rows(0) && t.llp_rows != llp_lean_rows(1))
+             : (t.llp_rows && t.llp_rows != llp_cgq2_rows(r, 0) &&
+                t.llp_rows != llp_cgq2_rows(r, 1)))
+        return PS_ERR_INVALID_ARG;
+    if (t.llp_pf && t.llp_pf != 2 && t.llp_pf != 3 && t.llp_pf != 4 && t.llp_pf != 8)
         return PS_ERR_INVALID_ARG;
     if (t.split && t.split != 1 && t.split != 2 && t.split != 4) return PS_ERR_INVALID_ARG;
     if (t.llp_bands && t.llp_bands != 1 && t.llp_bands != 2) return PS_ERR_INVALID_ARG;
@@ -1603,7 +1637,8 @@ ps_status ps_set_tuning(int N, int H, int W, int ratio, int r, const ps_tuning *
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PS_ERR_CUDA;
     tuning_set(dev, N, H, W, ratio, r, Tuning{t.prec_rows, t.llp_rows, t.split, t.llp_pf,
-                                              t.llp_bands, t.prec_impl, t.db_impl});
+                                              t.llp_bands, t.prec_impl, t.db_impl,
+                                              t.llp_form});
     return PS_OK;
 }
 
@@ -1740,8 +1775,8 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
         key_put(key, dims);
         key_put(key, q.band_mask);
         const Tuning t = tuning_get(dev, q.N, q.H, q.W, q.ratio, hp->r);
-        const int tk[7] = {t.prec_rows, t.llp_rows, t.split, t.llp_pf, t.llp_bands,
-                           t.prec_impl, t.db_impl};
+        const int tk[8] = {t.prec_rows, t.llp_rows, t.split, t.llp_pf, t.llp_bands,
+                           t.prec_impl, t.db_impl, t.llp_form};
         key_put(key, tk);
     }
     cudaGraphExec_t exec = nullptr;

@@ -31,6 +31,9 @@ struct LlpArgs {
     int pf;             // CG mode: rows the loads run ahead (2, 4 or 6 in registers,
                         // 8: a ring of 8 rows in shared memory; 0: 2)
     int nbd;            // CG mode: bands per CTA (1 or 2; 0: 1)
+    int form;           // CG mode: 0 or 1 the general walk; for r = 1 and one band
+                        // per CTA, 2 the lean two-column walk, 4 four columns a
+                        // lane (W % 4 == 0); the lean walks take pf 2 or 4
 };
 
 // operators.cu
@@ -203,6 +206,9 @@ void launch_cnn_adam(float *p, const float *g, float *m, float *v, int n, int st
 // rows per warp from LlpArgs::ty (llp_cgq2_rows(r, 0) long, (r, 1) short)
 void launch_llp_cgq2(const LlpArgs &a, int r, int N, cudaStream_t st);
 int llp_cgq2_rows(int r, int which);
+// the lean walks (form 2, 4): whether one applies, and their rows per warp
+bool llp_lean_supported(int form, int r, int W);
+int llp_lean_rows(int which);
 
 // tune.cu: launch choices of the tunable kernels per problem size
 struct Tuning {
@@ -213,6 +219,7 @@ struct Tuning {
     int llp_bands;  // bands per CTA of the CG-loop LLP kernel (0: 1)
     int prec_impl;  // preconditioner passes: 0 default, 1 shared-memory, 2 register-resident
     int db_impl;    // blur-decimate of the CG loop: 0 default, 1 per-site loads, 2 register runs
+    int llp_form;   // CG-loop LLP kernel: 0 default (1), 1 general, 2 lean two-column, 4 four-column
 };
 Tuning tuning_get(int dev, int N, int H, int W, int c, int r);
 void launch_fill(float *p, size_t n, float v, cudaStream_t st);

@@ -50,15 +50,19 @@ __device__ __forceinline__ float hsum(float v0, float v1) {
 }
 
 // Output rows per warp, two lengths per radius (the autotuner picks): longer
-// walks spend less on the 2G halo rows, shorter ones give more warps. For
-// r = 1 the whole walk (2G + rows) is a multiple of 12, so that it splits
-// into whole unrolled blocks (below).
+// walks spend less on the 2G halo rows, shorter ones give more warps. UNR is
+// the depth of the rolling buffers that the walk's unrolled blocks must
+// respect (3 for r = 1).
 template <int RW>
 struct Llp2Rows {
-    static constexpr int LONG = 64;
-    static constexpr int SHORT = (RW == 1) ? 28 : 32;
+    static constexpr int LONG = (RW == 1) ? 66 : 64;
+    static constexpr int SHORT = (RW == 1) ? 33 : 32;
     static constexpr int UNR = (RW == 1) ? 3 : 1;
 };
+
+// rows per warp of the lean kernels (r = 1): long and short walks
+constexpr int kQ4Long = 64;
+constexpr int kQ4Short = 32;
 
 constexpr int llp_gcd(int a, int b) { return b ? llp_gcd(b, a % b) : a; }
 constexpr int llp_lcm(int a, int b) { return a / llp_gcd(a, b) * b; }
@@ -88,6 +92,31 @@ struct LlpSlot {
     float4 s0[32], s1[32];
 };
 constexpr int kRing = 8;  // rows the ring holds (PF = kRing selects it)
+
+// Last CTA of a band: p^T A p = ||D B p||^2 + p^T (lam L^T M L) p, then
+// alpha = rho / p^T A p, or the band stops with its status.
+__device__ void llp_cg_finish(CgBand *bd, double tot, unsigned int nblk) {
+    atomicAdd(&bd->pAp, tot);
+    __threadfence();
+    const unsigned int t = atomicAdd(&bd->cnt_apply, 1u);
+    if (t == nblk - 1) {
+        __threadfence();
+        const double pAp = atomicAdd(&bd->pAp, 0.0) + bd->vv;
+        const double rho = bd->rho;
+        bd->cnt_apply = 0u;
+        if (!isfinite(pAp)) {
+            bd->status = PS_ERR_NONFINITE;
+            bd->done = 1;
+            bd->alpha = 0.0;
+        } else if (!(pAp > 0.0)) {
+            bd->status = PS_ERR_BREAKDOWN;
+            bd->done = 1;
+            bd->alpha = 0.0;
+        } else {
+            bd->alpha = rho / pAp;
+        }
+    }
+}
 
 template <int RW, int TY, int PF>
 __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
@@ -285,36 +314,36 @@ __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
         };
 
         float2 *outb = reinterpret_cast<float2 *>(a.out + (size_t)b * HW);
-        // The walk: 2G rows that fill the chain, then TY output rows. Every
-        // rolling buffer shifts by one slot a row; in blocks of U rows, U a
-        // multiple of every buffer's depth, each slot keeps one register
-        // across the loop, so no register with a load in flight is ever
-        // copied (a copy would wait for that load).
+        // The walk: 2G rows that fill the chain (unrolled), then TY output
+        // rows. Every rolling buffer shifts by one slot a row; in loop blocks
+        // of U rows, U a multiple of every buffer's depth, each slot keeps one
+        // register across the loop, so no register holding a load in flight
+        // is copied (a copy would wait for that load). The TY % U rows left
+        // over are unrolled after the loop.
+#pragma unroll
+        for (int k = 0; k < 2 * G; ++k) (void)advance();
         constexpr int U = llp_lcm(Llp2Rows<RW>::UNR, PFR);
-        constexpr int TOT = 2 * G + TY;
-        int yy = -2 * G;
+        int yy = 0;
         auto row = [&]() {
             float2 val = advance();
-            if (yy >= 0) {
-                if (out_lane && y0 + yy < H) {
-                    val.x *= a.lam;
-                    val.y *= a.lam;
-                    outb[(rowD + gx) >> 1] = val;
-                    // the output row is the input row of G steps ago
-                    const float2 pv = ph[PH - 1 - G];
-                    part = fmaf(pv.x, val.x, fmaf(pv.y, val.y, part));
-                }
-                rowD += W;
-                if (rowD == HWi) rowD = 0;
+            if (out_lane && y0 + yy < H) {
+                val.x *= a.lam;
+                val.y *= a.lam;
+                outb[(rowD + gx) >> 1] = val;
+                // the output row is the input row of G steps ago
+                const float2 pv = ph[PH - 1 - G];
+                part = fmaf(pv.x, val.x, fmaf(pv.y, val.y, part));
             }
+            rowD += W;
+            if (rowD == HWi) rowD = 0;
             ++yy;
         };
-        int s = 0;
-        for (; s + U <= TOT; s += U) {
+        for (int blk = 0; blk < TY / U; ++blk) {
 #pragma unroll
             for (int u = 0; u < U; ++u) row();
         }
-        for (; s < TOT; ++s) row();
+#pragma unroll
+        for (int u = 0; u < TY % U; ++u) row();
         if constexpr (RING) cp_async_wait<0>();
     }
     double pd = (double)part;
@@ -324,29 +353,234 @@ __global__ void __launch_bounds__(128) llp_cgq2_kernel(LlpArgs a) {
     if (tid == 0) {
         double tot = 0.0;
         for (int k = 0; k < kWarps; ++k) tot += red[k];
-        CgBand *bd = a.bands + b;
-        atomicAdd(&bd->pAp, tot);
-        __threadfence();
-        const unsigned int nblk = gridDim.y * gridDim.z;  // CTAs of this band
-        const unsigned int t = atomicAdd(&bd->cnt_apply, 1u);
-        if (t == nblk - 1) {
-            __threadfence();
-            // p^T A p = ||D B p||^2 + p^T (lam L^T M L) p
-            const double pAp = atomicAdd(&bd->pAp, 0.0) + bd->vv;
-            const double rho = bd->rho;
-            bd->cnt_apply = 0u;
-            if (!isfinite(pAp)) {
-                bd->status = PS_ERR_NONFINITE;
-                bd->done = 1;
-                bd->alpha = 0.0;
-            } else if (!(pAp > 0.0)) {
-                bd->status = PS_ERR_BREAKDOWN;
-                bd->done = 1;
-                bd->alpha = 0.0;
-            } else {
-                bd->alpha = rho / pAp;
-            }
+        llp_cg_finish(a.bands + b, tot, gridDim.y * gridDim.z);  // CTAs of this band
+    }
+}
+
+// Horizontal 3-sums of a row held as C adjacent columns a lane; the columns
+// beyond the lane's come from its neighbours.
+template <int C>
+__device__ __forceinline__ void hsumc(const float v[C], float h[C]) {
+    const float l = __shfl_up_sync(kFull, v[C - 1], 1u);
+    const float r = __shfl_down_sync(kFull, v[0], 1u);
+    if constexpr (C == 4) {
+        const float s01 = v[0] + v[1], s23 = v[2] + v[3];
+        h[0] = l + s01;
+        h[1] = s01 + v[2];
+        h[2] = v[1] + s23;
+        h[3] = s23 + r;
+    } else {
+        const float s01 = v[0] + v[1];
+        h[0] = l + s01;
+        h[1] = s01 + r;
+    }
+}
+
+template <int C> struct VecC;
+template <> struct VecC<2> {
+    using T = float2;
+    __device__ static void get(const T &v, float *o) { o[0] = v.x; o[1] = v.y; }
+    __device__ static T make(const float *o, float s) { return make_float2(o[0] * s, o[1] * s); }
+};
+template <> struct VecC<4> {
+    using T = float4;
+    __device__ static void get(const T &v, float *o) {
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    __device__ static T make(const float *o, float s) {
+        return make_float4(o[0] * s, o[1] * s, o[2] * s, o[3] * s);
+    }
+};
+
+// The same chain for 3 x 3 windows (r = 1) with C = 2 or 4 adjacent columns
+// a lane, written for few registers: the vertical 3-sums keep two registers a
+// quantity (the newest row and the sum of the two newest), and since the
+// periodic L is symmetric, p^T (L M L p) = (L p)^T M (L p): the partial sums
+// take alpha . (M alpha) at each output pixel, so p needs no delay buffer.
+// A strip is 32 C columns with G / C lanes of halo on each side (56 output
+// columns for C = 2, 120 for C = 4), one vector of C values of p a row.
+// Requires W % C == 0 (a lane's columns never wrap apart).
+template <int C, int TY, int PF>
+__global__ void __launch_bounds__(128) llp_cgqc_kernel(LlpArgs a) {
+    using V = VecC<C>;
+    using VT = typename V::T;
+    constexpr int G = 4;
+    constexpr int GL = G / C;  // halo lanes
+    constexpr int VALID = 32 * C - 2 * G;
+    constexpr float nw = 9.0f;
+    constexpr float inw = 1.0f / 9.0f;
+    __shared__ double red[kWarps];
+    const int b = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (a.g->stop || a.bands[b].done) return;
+    const int H = a.H, W = a.W;
+    const int HWi = H * W;
+    const size_t HW = (size_t)HWi;
+    const int x0 = blockIdx.y * VALID;
+    const int y0 = (blockIdx.z * kWarps + warp) * TY;
+    const int xl = x0 - G + C * lane;  // a multiple of C, as is W
+    const int gx = wrap2(xl, W);
+    const bool out_lane = lane >= GL && lane < 32 - GL && xl < W;
+    const float *in = a.in + (size_t)b * HW;
+    const float4 *st4 = a.st4;
+    float part = 0.0f;
+
+    if (y0 < H) {
+        int rowIn = wrap2(y0 - G, H) * W;
+        int rowA = wrap2(y0 - G - 1, H) * W;
+        int rowD = wrap2(y0, H) * W;
+        // with input row i: p of rows i-2, i-1; the vertical 3-sum state of
+        // the first windows (alpha, I alpha: newest row i-2 and the sum of
+        // rows i-2, i-3), mu and s of row i-2, the second windows' state
+        // (a, b), alpha and I of rows i-3, i-2, M alpha of rows i-5, i-4 and
+        // alpha of row i-4
+        float pA[C], pB[C], h1n[C], h1s[C], h2n[C], h2s[C], mup[C], sp[C];
+        float g1n[C], g1s[C], g2n[C], g2s[C], aA[C], aB[C], iA[C], iB[C];
+        float mm2[C], mm1[C], ap1[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            pA[c] = pB[c] = h1n[c] = h1s[c] = h2n[c] = h2s[c] = mup[c] = sp[c] = 0.f;
+            g1n[c] = g1s[c] = g2n[c] = g2s[c] = aA[c] = aB[c] = iA[c] = iB[c] = 0.f;
+            mm2[c] = mm1[c] = ap1[c] = 0.f;
         }
+        VT qp[PF];
+        float4 qs[PF][C];
+        auto load = [&](int k) {
+            qp[k] = *reinterpret_cast<const VT *>(in + rowIn + gx);
+#pragma unroll
+            for (int c = 0; c < C; ++c) qs[k][c] = st4[rowA + gx + c];
+            rowIn += W;
+            if (rowIn == HWi) rowIn = 0;
+            rowA += W;
+            if (rowA == HWi) rowA = 0;
+        };
+#pragma unroll
+        for (int k = 0; k < PF; ++k) load(k);
+
+        // one row: consumes input row i (stats row i-1), returns L M alpha of
+        // row i-4 and alpha . M alpha of that row in *dot
+        auto advance = [&](float *dot) -> VT {
+            float pin[C];
+            V::get(qp[0], pin);
+            float4 sv[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) sv[c] = qs[0][c];
+#pragma unroll
+            for (int k = 0; k < PF - 1; ++k) {
+                qp[k] = qp[k + 1];
+#pragma unroll
+                for (int c = 0; c < C; ++c) qs[k][c] = qs[k + 1][c];
+            }
+            load(PF - 1);
+            // alpha = L p on row i-1
+            const float pl = __shfl_up_sync(kFull, pB[C - 1], 1u);
+            const float pr = __shfl_down_sync(kFull, pB[0], 1u);
+            float al[C], iv[C], ia[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float left = c ? pB[c - 1] : pl;
+                const float right = c < C - 1 ? pB[c + 1] : pr;
+                al[c] = 4.0f * pB[c] - pA[c] - pin[c] - left - right;
+                iv[c] = sv[c].x;
+                ia[c] = iv[c] * al[c];
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) {  // after every column read its neighbours
+                pA[c] = pB[c];
+                pB[c] = pin[c];
+            }
+            float h1[C], h2[C];
+            hsumc<C>(al, h1);
+            hsumc<C>(ia, h2);
+            // first windows, centred on row i-2: a, b of Eq. matting_matrix
+            float av[C], bv[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float v1 = h1[c] + h1s[c], v2 = h2[c] + h2s[c];
+                h1s[c] = h1[c] + h1n[c];
+                h1n[c] = h1[c];
+                h2s[c] = h2[c] + h2n[c];
+                h2n[c] = h2[c];
+                const float ma = v1 * inw, mia = v2 * inw;
+                av[c] = (mia - mup[c] * ma) * sp[c];
+                bv[c] = ma - av[c] * mup[c];
+                mup[c] = sv[c].y;
+                sp[c] = sv[c].z;
+            }
+            float g1[C], g2[C];
+            hsumc<C>(av, g1);
+            hsumc<C>(bv, g2);
+            // second windows, centred on row i-3: M alpha there
+            float m0[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float sa = g1[c] + g1s[c], sb = g2[c] + g2s[c];
+                g1s[c] = g1[c] + g1n[c];
+                g1n[c] = g1[c];
+                g2s[c] = g2[c] + g2n[c];
+                g2n[c] = g2[c];
+                m0[c] = nw * aA[c] - sa * iA[c] - sb;
+            }
+            // L M alpha on row i-4
+            const float ml = __shfl_up_sync(kFull, mm1[C - 1], 1u);
+            const float mr = __shfl_down_sync(kFull, mm1[0], 1u);
+            float q[C], d = 0.0f;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float left = c ? mm1[c - 1] : ml;
+                const float right = c < C - 1 ? mm1[c + 1] : mr;
+                q[c] = 4.0f * mm1[c] - mm2[c] - m0[c] - left - right;
+                d = fmaf(ap1[c], mm1[c], d);
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                mm2[c] = mm1[c];
+                mm1[c] = m0[c];
+                ap1[c] = aA[c];
+                aA[c] = aB[c];
+                aB[c] = al[c];
+                iA[c] = iB[c];
+                iB[c] = iv[c];
+            }
+            *dot = d;
+            return V::make(q, 1.0f);
+        };
+
+        // unrolled fill of the chain, then loop blocks of U rows (every
+        // rotating buffer has depth 2 or PF) and the unrolled rest
+        float dot;
+#pragma unroll
+        for (int k = 0; k < 2 * G; ++k) (void)advance(&dot);
+        constexpr int U = llp_lcm(2, PF);
+        VT *outb = reinterpret_cast<VT *>(a.out + (size_t)b * HW);
+        int yy = 0;
+        auto row = [&]() {
+            const VT val = advance(&dot);
+            if (out_lane && y0 + yy < H) {
+                float o[C];
+                V::get(val, o);
+                outb[(rowD + gx) / C] = V::make(o, a.lam);
+                part += dot;
+            }
+            rowD += W;
+            if (rowD == HWi) rowD = 0;
+            ++yy;
+        };
+        for (int blk = 0; blk < TY / U; ++blk) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) row();
+        }
+#pragma unroll
+        for (int u = 0; u < TY % U; ++u) row();
+    }
+    double pd = (double)part * (double)a.lam;
+    for (int o = 16; o > 0; o >>= 1) pd += __shfl_xor_sync(kFull, pd, o);
+    if (lane == 0) red[warp] = pd;
+    __syncthreads();
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < kWarps; ++k) tot += red[k];
+        llp_cg_finish(a.bands + b, tot, gridDim.y * gridDim.z);
     }
 }
 
@@ -532,37 +766,37 @@ __global__ void __launch_bounds__(128) llp_cgq2b_kernel(LlpArgs a) {
 
         float2 *out0 = reinterpret_cast<float2 *>(a.out + (size_t)b0 * HW);
         float2 *out1 = reinterpret_cast<float2 *>(a.out + (size_t)(b0 + 1) * HW);
-        // the walk in whole blocks of U rows, as in the one-band kernel
-        constexpr int U = llp_lcm(Llp2Rows<RW>::UNR, PF);
-        constexpr int TOT = 2 * G + TY;
-        int yy = -2 * G;
-        auto row = [&]() {
-            float2 val[2];
-            advance(val);
-            if (yy >= 0) {
-                if (out_lane && y0 + yy < H) {
+        // the walk as in the one-band kernel: unrolled fill, loop blocks of
+        // U rows, unrolled rest
+        float2 val[2];
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        if (q == 1 && !two) break;
-                        val[q].x *= a.lam;
-                        val[q].y *= a.lam;
-                        (q ? out1 : out0)[(rowD + gx) >> 1] = val[q];
-                        // the output row is the input row of G steps ago
-                        const float2 pv = ph[q][PH - 1 - G];
-                        part[q] = fmaf(pv.x, val[q].x, fmaf(pv.y, val[q].y, part[q]));
-                    }
+        for (int k = 0; k < 2 * G; ++k) advance(val);
+        constexpr int U = llp_lcm(Llp2Rows<RW>::UNR, PF);
+        int yy = 0;
+        auto row = [&]() {
+            advance(val);
+            if (out_lane && y0 + yy < H) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    if (q == 1 && !two) break;
+                    val[q].x *= a.lam;
+                    val[q].y *= a.lam;
+                    (q ? out1 : out0)[(rowD + gx) >> 1] = val[q];
+                    // the output row is the input row of G steps ago
+                    const float2 pv = ph[q][PH - 1 - G];
+                    part[q] = fmaf(pv.x, val[q].x, fmaf(pv.y, val[q].y, part[q]));
                 }
-                rowD += W;
-                if (rowD == HWi) rowD = 0;
             }
+            rowD += W;
+            if (rowD == HWi) rowD = 0;
             ++yy;
         };
-        int s = 0;
-        for (; s + U <= TOT; s += U) {
+        for (int blk = 0; blk < TY / U; ++blk) {
 #pragma unroll
             for (int u = 0; u < U; ++u) row();
         }
-        for (; s < TOT; ++s) row();
+#pragma unroll
+        for (int u = 0; u < TY % U; ++u) row();
     }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -618,14 +852,30 @@ void launch_ty(const LlpArgs &a, int N, cudaStream_t st) {
     llp_cgq2_kernel<RW, TY, PF><<<grd, 32 * kWarps, 0, st>>>(a);
 }
 
+template <int C, int TY, int PF>
+void launch_qc(const LlpArgs &a, int N, cudaStream_t st) {
+    constexpr int VALID = 32 * C - 8;
+    const int rows = TY * kWarps;
+    dim3 grd(N, (a.W + VALID - 1) / VALID, (a.H + rows - 1) / rows);
+    llp_cgqc_kernel<C, TY, PF><<<grd, 32 * kWarps, 0, st>>>(a);
+}
+
+template <int C, int TY>
+void launch_qc_pf(const LlpArgs &a, int N, cudaStream_t st) {
+    if (a.pf == 4)
+        launch_qc<C, TY, 4>(a, N, st);
+    else
+        launch_qc<C, TY, 2>(a, N, st);
+}
+
 template <int RW, int TY>
 void launch_pf(const LlpArgs &a, int N, cudaStream_t st) {
     if (a.nbd == 2)
         launch_ty2<RW, TY, 2>(a, N, st);
     else if (a.pf == kRing)
         launch_ty<RW, TY, kRing>(a, N, st);
-    else if (a.pf == 6)
-        launch_ty<RW, TY, 6>(a, N, st);
+    else if (a.pf == 3)
+        launch_ty<RW, TY, 3>(a, N, st);
     else if (a.pf == 4)
         launch_ty<RW, TY, 4>(a, N, st);
     else
@@ -642,6 +892,8 @@ void launch_r(const LlpArgs &a, int N, cudaStream_t st) {
 
 }  // namespace
 
+int llp_lean_rows(int which) { return which ? kQ4Short : kQ4Long; }
+
 int llp_cgq2_rows(int r, int which) {
     switch (r) {
         case 1: return which ? Llp2Rows<1>::SHORT : Llp2Rows<1>::LONG;
@@ -651,7 +903,25 @@ int llp_cgq2_rows(int r, int which) {
     }
 }
 
+bool llp_lean_supported(int form, int r, int W) {
+    return r == 1 && (form == 2 ? W % 2 == 0 : form == 4 && W % 4 == 0);
+}
+
 void launch_llp_cgq2(const LlpArgs &a, int r, int N, cudaStream_t st) {
+    if (a.nbd != 2 && llp_lean_supported(a.form, r, a.W)) {
+        if (a.form == 4) {
+            if (a.ty == kQ4Short)
+                launch_qc_pf<4, kQ4Short>(a, N, st);
+            else
+                launch_qc_pf<4, kQ4Long>(a, N, st);
+        } else {
+            if (a.ty == kQ4Short)
+                launch_qc_pf<2, kQ4Short>(a, N, st);
+            else
+                launch_qc_pf<2, kQ4Long>(a, N, st);
+        }
+        return;
+    }
     switch (r) {
         case 1: launch_r<1>(a, N, st); break;
         case 2: launch_r<2>(a, N, st); break;

@@ -25,7 +25,7 @@ Tuning tuning_get(int dev, int N, int H, int W, int c, int r) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (const Entry &e : g_tune)
         if (e.dev == dev && e.N == N && e.H == H && e.W == W && e.c == c && e.r == r) return e.t;
-    return Tuning{0, 0, 0, 0, 0, 0, 0};
+    return Tuning{0, 0, 0, 0, 0, 0, 0, 0};
 }
 
 void tuning_set(int dev, int N, int H, int W, int c, int r, const Tuning &t) {

@@ -260,7 +260,17 @@ def test_tuning_arguments(lib):
     assert lib.ps_set_tuning(4, 256, 256, 4, 1, ctypes.byref(t)) == 1
     t.llp_bands, t.llp_pf = 2, 5
     assert lib.ps_set_tuning(4, 256, 256, 4, 1, ctypes.byref(t)) == 1
-    t.llp_pf = 4
+    t.llp_pf, t.llp_form = 4, 3
+    assert lib.ps_set_tuning(4, 256, 256, 4, 1, ctypes.byref(t)) == 1
+    t.llp_form = 4                                 # lean walks: one band per CTA only
+    assert lib.ps_set_tuning(4, 256, 256, 4, 1, ctypes.byref(t)) == 1
+    t.llp_bands = 1
+    assert lib.ps_set_tuning(4, 256, 256, 4, 2, ctypes.byref(t)) == 1   # and r = 1 only
+    t.llp_rows = 66                                # the general walk's length
+    assert lib.ps_set_tuning(4, 256, 256, 4, 1, ctypes.byref(t)) == 1
+    t.llp_rows, t.llp_form, t.llp_pf = 0, 2, 3     # lean walks: 2 or 4 rows ahead
+    assert lib.ps_set_tuning(4, 256, 256, 4, 1, ctypes.byref(t)) == 1
+    t.llp_form, t.llp_pf, t.llp_bands = 0, 4, 2
     assert lib.ps_set_tuning(4, 250, 256, 4, 1, ctypes.byref(t)) == 2   # H % ratio
     assert lib.ps_set_tuning(4, 256, 256, 4, 1, None) == 1
 

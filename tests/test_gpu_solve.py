@@ -247,17 +247,21 @@ def test_band_solve_times(cuda):
     assert info.iters[1] == 0 and min(info.iters[0], info.iters[2], info.iters[3]) > 20
 
 
-@pytest.mark.parametrize("pf,db", [(8, 1), (2, 2), (8, 2)])
-def test_loop_kernel_variants_match_oracle(cuda, c0_oracle, pf, db):
+@pytest.mark.parametrize("pf,db,form,rows", [(8, 1, 0, 0), (2, 2, 0, 0), (8, 2, 0, 0),
+                                             (3, 1, 0, 0), (4, 1, 0, 0), (2, 1, 4, 64),
+                                             (4, 1, 4, 32), (4, 1, 2, 64), (2, 1, 2, 32)])
+def test_loop_kernel_variants_match_oracle(cuda, c0_oracle, pf, db, form, rows):
     # The CG loop's tunable kernel variants (the LLP kernel's loads through
-    # the shared-memory ring, pf = 8; the register-run blur-decimate,
-    # db = 2), forced through the recorded tuning: the same Z0 and Z as the
-    # oracle, at the plain-form bar.
+    # the shared-memory ring, pf = 8, or 3 or 4 rows ahead in registers; the
+    # lean two- and four-column walks, form = 2, 4, long and short; the
+    # register-run blur-decimate, db = 2), forced through the recorded tuning:
+    # the same Z0 and Z as the oracle, at the plain-form bar.
     sc, ref = c0_oracle
     cfg = sc["config"]
     hp = api.default_hrms_params(tol=1e-8, max_iter=5000)
     try:
-        api.set_tuning(cfg.bands, cfg.H, cfg.W, cfg.ratio, 1, llp_pf=pf, db_impl=db)
+        api.set_tuning(cfg.bands, cfg.H, cfg.W, cfg.ratio, 1, llp_pf=pf, db_impl=db,
+                       llp_form=form, llp_rows=rows)
         Z, Z0, info = api.solve_hrms(to_dev(sc["lrms"], cuda), to_dev(sc["pan"], cuda),
                                      to_dev(sc["kernel"], cuda), cfg.ratio, hp, want_z0=True)
     finally:
