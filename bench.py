@@ -860,18 +860,15 @@ def run_batch(args):
     value = throughput(units, world, step_ms * 1e-3)
 
     # end to end: pinned host inputs copied in and every HRMS copied out
-    # inside the timed region
+    # inside the timed region, by the batched call itself (host staging:
+    # each scene's copies are nodes of its branch of the batch graph, so they
+    # overlap the other scenes' work)
     hx = [torch.from_numpy(a[0]).pin_memory() for a in arrays]
     hy = [torch.from_numpy(a[1]).pin_memory() for a in arrays]
-    ho = [torch.empty(t.shape, dtype=torch.float32).pin_memory() for t in batch.hrms]
+    ho = batch.stage_host(list(zip(hx, hy)))
 
     def e2e_step():
-        for (x, y), a, b in zip(batch.inputs, hx, hy):
-            x.copy_(a, non_blocking=True)
-            y.copy_(b, non_blocking=True)
         batch.run()
-        for o, t in zip(ho, batch.hrms):
-            o.copy_(t, non_blocking=True)
 
     e2e_step()
     torch.cuda.synchronize()

@@ -326,6 +326,15 @@ typedef struct ps_scene {
     int N, H, W, ratio, R;
     unsigned long long band_mask; /* X' of this scene (bit b: band b);
                             0 takes h_kparams->band_mask                   */
+    /* Optional host copies in page-locked host memory (e.g. cudaHostAlloc;
+     * NULL: none). The scene's branch of the batch graph first copies h_lrms
+     * into lrms and h_pan into pan, and after its Z step copies hrms into
+     * h_hrms. The copies are nodes of the batch's graph, so they overlap the
+     * other scenes' work. A host pointer that is not page-locked is
+     * PS_ERR_INVALID_ARG. */
+    const float *h_lrms; /* N x h x w                                      */
+    const float *h_pan;  /* H x W                                          */
+    float *h_hrms;       /* N x H x W                                      */
 } ps_scene;
 
 /* Workspace bytes of ps_pansharpen_batched for these scenes: a header of

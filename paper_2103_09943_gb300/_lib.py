@@ -59,7 +59,8 @@ class Scene(ctypes.Structure):
                 ("hrms", ctypes.c_void_p), ("kernel", ctypes.c_void_p),
                 ("N", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
                 ("ratio", ctypes.c_int), ("R", ctypes.c_int),
-                ("band_mask", ctypes.c_ulonglong)]
+                ("band_mask", ctypes.c_ulonglong), ("h_lrms", ctypes.c_void_p),
+                ("h_pan", ctypes.c_void_p), ("h_hrms", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p

@@ -226,6 +226,8 @@ class Batch:
     (hrms per scene, kernel per scene) and the workspace are allocated once;
     run() launches the whole batch, estimating every kernel when
     estimate=True, else using the kernels in self.kernels (fill them first).
+    stage_host() makes every run copy the scenes' inputs from page-locked host
+    tensors and their HRMS back to page-locked host tensors inside the graph.
     """
 
     def __init__(self, scenes, ratio: int, hparams: HrmsParams | None = None,
@@ -271,6 +273,25 @@ class Batch:
             out.append(_solve_info(bi[k:k + n]))
             k += n
         return (list(ki) if ki is not None else None), out
+
+    def stage_host(self, h_inputs, h_hrms=None):
+        """From the next run on, copy each scene's (lrms, pan) from the
+        page-locked host tensors h_inputs[i] into its device inputs, and its
+        HRMS back into h_hrms[i] (allocated page-locked when None), as nodes of
+        the batch's graph. Returns the host HRMS tensors."""
+        if h_hrms is None:
+            h_hrms = [torch.empty(t.shape, dtype=torch.float32).pin_memory() for t in self.hrms]
+        for i, ((hx, hy), ho) in enumerate(zip(h_inputs, h_hrms)):
+            dx, dy = self.inputs[i]
+            for h, d in ((hx, dx), (hy, dy), (ho, self.hrms[i])):
+                if (h.device.type != "cpu" or not h.is_pinned() or h.shape != d.shape
+                        or h.dtype != torch.float32 or not h.is_contiguous()):
+                    raise PsError("host staging needs page-locked contiguous float32 tensors "
+                                  "of the scene's shapes")
+            self.scenes[i].h_lrms, self.scenes[i].h_pan = hx.data_ptr(), hy.data_ptr()
+            self.scenes[i].h_hrms = ho.data_ptr()
+        self._host = (list(h_inputs), list(h_hrms))     # kept alive with the batch
+        return self._host[1]
 
     def scene_ms(self) -> list:
         """Finish time of every scene of the last run, ms after it started."""

@@ -1119,7 +1119,19 @@ ps_status build_batch_graph(const ps_scene *scenes, int count, const ps_kernel_p
         s = capture_child(graph, &root, 1, capture,
                           [&](cudaStream_t st) {
                               ps_status e = PS_OK;
-                              if (kp) {
+                              // the scene's inputs from page-locked host memory
+                              const size_t nl = (size_t)q.N * (q.H / q.ratio) * (q.W / q.ratio);
+                              if (q.h_lrms &&
+                                  cudaMemcpyAsync(const_cast<float *>(q.lrms), q.h_lrms,
+                                                  nl * sizeof(float), cudaMemcpyHostToDevice,
+                                                  st) != cudaSuccess)
+                                  e = PS_ERR_CUDA;
+                              if (e == PS_OK && q.h_pan &&
+                                  cudaMemcpyAsync(const_cast<float *>(q.pan), q.h_pan,
+                                                  (size_t)q.H * q.W * sizeof(float),
+                                                  cudaMemcpyHostToDevice, st) != cudaSuccess)
+                                  e = PS_ERR_CUDA;
+                              if (e == PS_OK && kp) {
                                   // this scene's X' (Eq. objective1)
                                   ps_kernel_params kq = *kp;
                                   if (q.band_mask) kq.band_mask = q.band_mask;
@@ -1141,7 +1153,15 @@ ps_status build_batch_graph(const ps_scene *scenes, int count, const ps_kernel_p
                               [&](cudaStream_t st) {
                                   ps_status e = solve_epilogue(sc, a, st);
                                   launch_stamp(stamps + 1 + i, st);
-                                  return e == PS_OK ? last_launch() : e;
+                                  if (e == PS_OK) e = last_launch();
+                                  // the HRMS back to page-locked host memory
+                                  if (e == PS_OK && q.h_hrms &&
+                                      cudaMemcpyAsync(q.h_hrms, q.hrms,
+                                                      (size_t)q.N * q.H * q.W * sizeof(float),
+                                                      cudaMemcpyDeviceToHost,
+                                                      st) != cudaSuccess)
+                                      e = PS_ERR_CUDA;
+                                  return e;
                               },
                               &post);
     }
@@ -1715,6 +1735,15 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
         if (kp && (s = check_band_mask(q.band_mask ? q.band_mask : kp->band_mask, q.N)) !=
                       PS_OK)
             return s;
+        const void *hp3[3] = {q.h_lrms, q.h_pan, q.h_hrms};
+        for (const void *h : hp3) {
+            if (!h) continue;
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, h) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+                cudaGetLastError();
+                return PS_ERR_INVALID_ARG;
+            }
+        }
     }
     if (ws_bytes < ps_batch_workspace_size(scenes, count, hp)) return PS_ERR_WORKSPACE;
     char *base = static_cast<char *>(d_ws);
@@ -1774,6 +1803,9 @@ ps_status ps_pansharpen_batched(const ps_scene *scenes, int count, const ps_kern
         const int dims[5] = {q.N, q.H, q.W, q.ratio, q.R};
         key_put(key, dims);
         key_put(key, q.band_mask);
+        key_put(key, q.h_lrms);
+        key_put(key, q.h_pan);
+        key_put(key, q.h_hrms);
         const Tuning t = tuning_get(dev, q.N, q.H, q.W, q.ratio, hp->r);
         const int tk[8] = {t.prec_rows, t.llp_rows, t.split, t.llp_pf, t.llp_bands,
                            t.prec_impl, t.db_impl, t.llp_form};

@@ -161,3 +161,30 @@ def test_batch_with_an_alternative_prior_and_the_paper_rule(cuda, scenes):
         for n in range(cfg.bands):
             assert abs(si.iters[n] - sinfo[i].iters[n]) <= 1, (i, n)
         assert rel(to_np(b.hrms[i]), to_np(Z)) < 1e-5, i
+
+
+def test_batch_host_staging(cuda, scenes, batch_estimated):
+    # The scenes' inputs copied from page-locked host tensors and every HRMS
+    # copied back to page-locked host tensors by the batch graph itself: the
+    # device inputs start as zeros, so a result equal to the device-only
+    # batch's shows the copies ran before the work; the host HRMS is the
+    # device HRMS of the same run, byte for byte.
+    ref, _, _, hp = batch_estimated
+    dev = [(torch.zeros(s["lrms"].shape, dtype=torch.float32, device=cuda),
+            torch.zeros(s["pan"].shape, dtype=torch.float32, device=cuda), s["config"].R)
+           for s in scenes]
+    b = api.Batch(dev, ratio=4, hparams=hp, estimate=True)
+    hin = [(torch.from_numpy(np.ascontiguousarray(s["lrms"], dtype=np.float32)).pin_memory(),
+            torch.from_numpy(np.ascontiguousarray(s["pan"], dtype=np.float32)).pin_memory())
+           for s in scenes]
+    hout = b.stage_host(hin)
+    kinfo, sinfo = b.run(info=True)
+    for i in range(len(scenes)):
+        assert kinfo[i].status == 0 and all(s == 0 for s in sinfo[i].status), i
+        assert np.array_equal(hout[i].numpy(), to_np(b.hrms[i])), i
+        assert rel(hout[i].numpy(), to_np(ref.hrms[i])) < 1e-6, i
+    # a host pointer that is not page-locked is refused before any work
+    pageable = np.zeros(scenes[0]["lrms"].shape, dtype=np.float32)
+    b.scenes[0].h_lrms = pageable.ctypes.data
+    with pytest.raises(api.PsError, match="status 1"):
+        b.run()
