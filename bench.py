@@ -834,7 +834,8 @@ def run_batch(args):
         for c in cfgs:
             key = (c.bands, c.H, c.W)
             if key not in tuned:
-                t = api.autotune(c.bands, c.H, c.W, c.ratio, c.R, hp.r, device=dev)
+                t = api.autotune(c.bands, c.H, c.W, c.ratio, c.R, hp.r, device=dev,
+                                 cache=args.tuning_cache)
                 tuned[key] = {k: t[k] for k in ("prec_rows", "llp_rows", "llp_pf",
                                                 "llp_bands", "llp_form")}
     scenes = [(x, y, c.R) for x, y, c in zip(X, Y, cfgs)]
@@ -1056,6 +1057,9 @@ def parse(argv=None):
                          "of all-FP32")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (default launch shapes; for profiler launch lists)")
+    ap.add_argument("--tuning-cache", default=None, metavar="JSON",
+                    help="autotuner records keyed by GPU name and sizes: reuse a record found "
+                         "there instead of timing, add new ones (default: tune every run)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the timing of the plain-CG / PCG / warm-start forms")
     ap.add_argument("--precond", default="fft", choices=["fft", "none"],

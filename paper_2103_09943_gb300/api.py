@@ -8,6 +8,9 @@ allocated with torch (the library itself allocates nothing).
 from __future__ import annotations
 
 import ctypes
+import json
+import os
+import tempfile
 from dataclasses import dataclass
 
 import torch
@@ -80,16 +83,67 @@ def workspace(N, H, W, ratio, R, device=None, hparams: HrmsParams | None = None)
     return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
 
 
+TUNING_CHOICES = ("prec_rows", "llp_rows", "llp_pf", "split", "llp_bands", "prec_impl",
+                  "db_impl", "llp_form")
+TUNING_CACHE_VERSION = 1
+
+
+def tuning_cache_key(gpu: str, N, H, W, ratio, R, r, with_scene: bool) -> str:
+    """Key of one autotuner record in a tuning cache file: the GPU's name and
+    the sizes the choices were timed on."""
+    return f"{gpu}|N={N}|H={H}|W={W}|ratio={ratio}|R={R}|r={r}|scene={int(bool(with_scene))}"
+
+
+def read_tuning_cache(path: str) -> dict:
+    """The records of a tuning cache file (JSON), {} when it does not exist or
+    was written by another format version."""
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        doc = json.load(fh)
+    if not isinstance(doc, dict) or doc.get("version") != TUNING_CACHE_VERSION:
+        return {}
+    return dict(doc.get("entries", {}))
+
+
+def write_tuning_cache(path: str, entries: dict) -> None:
+    """Write the records atomically (a temporary file in the same folder,
+    then a rename), so that a reader never sees a half-written file."""
+    folder = os.path.dirname(os.path.abspath(path))
+    fd, tmp = tempfile.mkstemp(prefix=".tuning-", suffix=".json", dir=folder)
+    try:
+        with os.fdopen(fd, "w") as fh:
+            json.dump({"version": TUNING_CACHE_VERSION, "entries": entries}, fh, indent=1,
+                      sort_keys=True)
+        os.replace(tmp, path)
+    except BaseException:
+        if os.path.exists(tmp):
+            os.unlink(tmp)
+        raise
+
+
 def autotune(N, H, W, ratio, R, r=1, ws=None, device=None, lrms=None, pan=None,
-             kernel=None) -> dict:
+             kernel=None, cache: str | None = None) -> dict:
     """Times the candidate launch shapes of the tunable kernels on these sizes
     and records the fastest for later solves (ps_autotune); with a scene
-    (lrms, pan, kernel) also the number of parallel CG branches."""
+    (lrms, pan, kernel) also the number of parallel CG branches. With cache, a
+    JSON file keyed by the GPU's name and the sizes: a record found there is
+    applied (ps_set_tuning) instead of timing, and a new result is added."""
+    key = None
+    if cache is not None:
+        dev = torch.device(device) if device is not None else torch.device("cuda")
+        key = tuning_cache_key(torch.cuda.get_device_name(dev), N, H, W, ratio, R, r,
+                               lrms is not None)
+        rec = read_tuning_cache(cache).get(key)
+        if rec is not None:
+            choices = {k: int(rec["choices"][k]) for k in TUNING_CHOICES}
+            set_tuning(N, H, W, ratio, r, **choices)
+            return {**choices, "cached": True}
     ws = ws if ws is not None else workspace(N, H, W, ratio, R, device)
     t = Tuning()
     _check(_lib.load().ps_autotune(N, H, W, ratio, R, r, _ptr(lrms), _ptr(pan), _ptr(kernel),
                                    _ptr(ws), ws.numel(), _stream(), ctypes.byref(t)))
-    return {"prec_rows": t.prec_rows, "llp_rows": t.llp_rows,
+    out = {"prec_rows": t.prec_rows, "llp_rows": t.llp_rows,
             "prec_us": {str(k): round(v, 2) for k, v in zip((1, 2, 4, 8), t.prec_us) if v},
             "llp_pf": t.llp_pf,
             "llp_us": {f"{w}/{pf}": round(t.llp_us[3 * i + j], 2)
@@ -110,6 +164,11 @@ def autotune(N, H, W, ratio, R, r=1, ws=None, device=None, lrms=None, pan=None,
                             for h, f in enumerate((2, 4))
                             for i, w in enumerate(("long", "short"))
                             for j, pf in enumerate((2, 4)) if t.llp_lean_us[4 * h + 2 * i + j]}}
+    if key is not None:
+        entries = read_tuning_cache(cache)
+        entries[key] = {"choices": {k: out[k] for k in TUNING_CHOICES}}
+        write_tuning_cache(cache, entries)
+    return out
 
 
 def set_tuning(N, H, W, ratio, r=1, **choices) -> None:
