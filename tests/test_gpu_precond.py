@@ -179,6 +179,24 @@ def test_autotune_picks_valid_shapes_and_keeps_parity(cuda, c0_ref):
         assert rel(to_np(Z)[b], ref["Z"][b]) < 1e-5
 
 
+def test_autotune_cache_roundtrip(cuda, tmp_path):
+    # the first call times and writes its record; after the recorded choice is
+    # cleared, the second call applies the record without timing
+    path = str(tmp_path / "tuning.json")
+    N, H, W, ratio, R = 4, 256, 256, 4, 5
+    try:
+        t = api.autotune(N, H, W, ratio, R, 1, device=cuda, cache=path)
+        assert "cached" not in t and api.read_tuning_cache(path)
+        api.set_tuning(N, H, W, ratio, 1)
+        assert all(v == 0 for v in api.get_tuning(N, H, W, ratio, 1).values())
+        t2 = api.autotune(N, H, W, ratio, R, 1, device=cuda, cache=path)
+        assert t2["cached"] is True
+        got = api.get_tuning(N, H, W, ratio, 1)
+        assert got == {k: t[k] for k in api.TUNING_CHOICES}
+    finally:
+        api.set_tuning(N, H, W, ratio, 1)
+
+
 @pytest.mark.parametrize("split", [1, 2])
 def test_two_band_llp_kernel_reaches_the_oracle(cuda, c0_ref, split):
     # the CG-loop LLP kernel that walks two bands per CTA (shared PAN

@@ -163,6 +163,24 @@ def test_matting_null_space_and_symmetry():
                - np.vdot(a, oracle.matting_apply(b, st))) < 1e-10
 
 
+def test_prior_quadratic_form_through_alpha():
+    # The CG loop's lean LLP walks sum alpha . (M alpha), alpha = L p, for
+    # p^T (L^T M L p): equal because the periodic 5-point L is symmetric. On
+    # the oracle's operators, with the sum written pixel by pixel here.
+    H, W, r = 14, 10, 1
+    st = oracle.pan_stats(rand(H, W) * 20, r, 0.3)
+    p = rand(H, W)
+    alpha = oracle.laplacian(p)
+    m_alpha = oracle.matting_apply(alpha, st)
+    lhs = np.vdot(p, oracle.laplacian(m_alpha))
+    rhs = 0.0
+    for y in range(H):
+        for x in range(W):
+            rhs += alpha[y, x] * m_alpha[y, x]
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+    assert rhs > 0.0                                         # M is positive semidefinite
+
+
 def test_guided_filter_textbook():
     # He et al.'s guided filter with explicit per-window fits, written here.
     H, W, r, eps = 10, 9, 1, 0.25
