@@ -518,6 +518,10 @@ def compare_variants(api, X, Y, cfg, kp, net, dev, steps=3):
                      "kernel": f"{2 * R + 1}x{2 * R + 1}",
                      "stop": ("relative change < %g" % hp.tol) if hp.stop_rule
                      else ("relative residual <= %g" % hp.tol)}
+        # one variant's workspace at a time (8 x 8192^2 takes tens of GB)
+        del ws
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
     return out
 
 
@@ -663,6 +667,7 @@ def run_gpu(args):
         b.synchronize()                               # the host has the result
         e2e.append(a.elapsed_time(b))
     e2e_ms = reduce_max(float(np.mean(e2e)), world, dev)
+    h2d_bytes, d2h_bytes = pipe.h2d_bytes, pipe.d2h_bytes
 
     # launches of our kernels per step
     split = (tuning or {}).get("split") or (2 if cfg.bands >= 4 else 1)
@@ -691,6 +696,9 @@ def run_gpu(args):
 
     variants = None
     if rank == 0 and not args.no_compare:
+        del pipe                      # its workspace: tens of GB at 8 x 8192^2
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
         variants = compare_variants(api, X, Y, cfg, kp, net, dev)
 
     cpu = None
@@ -710,7 +718,7 @@ def run_gpu(args):
                     "admm_iters": kinfo.iters},
             "wall_s_timed_region": wall,
             "e2e": {"value": throughput(units, world, e2e_ms * 1e-3), "unit": UNIT,
-                    "h2d_bytes_per_step": pipe.h2d_bytes, "d2h_bytes_per_step": pipe.d2h_bytes,
+                    "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
                     "ms_per_step": e2e_ms},
             "gpu_launches": n_launch * args.steps,
             "roofline": roof,

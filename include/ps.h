@@ -207,10 +207,16 @@ typedef struct ps_tuning {
     float split_us[3];   /* two CG iterations, candidates 1, 2, 4 branches   */
     int llp_bands;       /* bands per CTA of that LLP kernel (1, 2)          */
     float llp2_us[2];    /* two bands per CTA: long, short walk (2 ahead)    */
-    int prec_impl;       /* preconditioner passes: 1 shared-memory (any size),
+    int prec_impl;       /* preconditioner passes: 1 shared-memory (any size;
+                            for power-of-two columns too long for one CTA,
+                            e.g. 8192 at ratio 4, the column pass splits each
+                            alias-group set over a cluster of two CTAs),
                             2 register-resident (power-of-two sides 256 ..
-                            4096, ratios 2 and 4); 0 the default (2 where it
-                            applies)                                        */
+                            4096, 384, 768, 1536; ratios 2 and 4), 3 the
+                            shared-memory passes with that cluster column
+                            pass at any power-of-two size with an even ratio
+                            (not timed by the autotuner); 0 the default (2
+                            where it applies)                               */
     float prec_impl_us[2]; /* one application: candidates 1 (its best row
                             count), 2                                        */
     int db_impl;         /* blur-decimate D B p of the CG loop: 1 one load

@@ -1650,8 +1650,9 @@ ps_status ps_set_tuning(int N, int H, int W, int ratio, int r, const ps_tuning *
         return PS_ERR_INVALID_ARG;
     if (t.split && t.split != 1 && t.split != 2 && t.split != 4) return PS_ERR_INVALID_ARG;
     if (t.llp_bands && t.llp_bands != 1 && t.llp_bands != 2) return PS_ERR_INVALID_ARG;
-    if (t.prec_impl < 0 || t.prec_impl > 2 ||
-        (t.prec_impl == 2 && !precond_reg_supported(H, W, ratio)))
+    if (t.prec_impl < 0 || t.prec_impl > 3 ||
+        (t.prec_impl == 2 && !precond_reg_supported(H, W, ratio)) ||
+        (t.prec_impl == 3 && !precond_cluster_supported(H, W, ratio)))
         return PS_ERR_INVALID_ARG;
     if (t.db_impl < 0 || t.db_impl > 2) return PS_ERR_INVALID_ARG;
     int dev = 0;

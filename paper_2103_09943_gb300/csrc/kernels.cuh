@@ -150,6 +150,8 @@ bool precond_supported(int H, int W, int c);
 // precond_reg.cu: the register-resident passes (power-of-two sides 256..4096,
 // ratios 2 and 4); launch_precond_reg returns false for other sizes
 bool precond_reg_supported(int H, int W, int c);
+// the shared-memory passes with the column pass over two-CTA clusters
+bool precond_cluster_supported(int H, int W, int c);
 bool launch_precond_reg(const PrecArgs &a, cudaStream_t st);
 cudaError_t precond_reg_set_attrs();
 bool precond_rows_ok(int H, int W, int c, int tr);

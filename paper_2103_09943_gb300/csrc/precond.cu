@@ -28,6 +28,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "fft_dev.cuh"
 #include "kernels.cuh"
@@ -276,6 +278,56 @@ __global__ void __launch_bounds__(MAXT, 1024 / MAXT) prec_cols_kernel(PrecArgs a
     }
 }
 
+// The same column pass for power-of-two sides whose C columns do not fit one
+// CTA (H = 8192 at ratio 4): the C columns of an alias-group set are split
+// over a cluster of two CTAs, C / 2 each. Each CTA transforms its own columns
+// in its shared memory; the group solves read and write the other CTA's
+// columns through distributed shared memory, each CTA taking half of the
+// groups; the cluster's barriers order the three phases, so no CTA writes a
+// peer's columns before they are transformed or leaves while its own are read.
+template <int C>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024, 1)
+    prec_cols_cluster_kernel(PrecArgs a, int tpr, int ld, float scale) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) float2 psm[];
+    constexpr int CL = C / 2;  // columns a CTA
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int k = blockIdx.y, kx0 = blockIdx.x >> 1;
+    if (image_idle(a, k)) return;  // both CTAs of a cluster see the same image
+    const int H = a.H, W = a.W, h = H / C, w = W / C;
+    float2 *S = a.spec + (size_t)k * H * W;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < CL * H / 2; i += blockDim.x) {
+        const int ql = (2 * i) / H, y = 2 * i - ql * H;
+        const float4 v =
+            *reinterpret_cast<const float4 *>(S + (size_t)(kx0 + (rank * CL + ql) * w) * H + y);
+        psm[ql * ld + ix<true>(y)] = make_float2(v.x, v.y);
+        psm[ql * ld + ix<true>(y + 1)] = make_float2(v.z, v.w);
+    }
+    __syncthreads();
+    const int row = threadIdx.x / tpr, t = threadIdx.x - row * tpr;
+    fft_p2_row(psm + row * ld, H, a.twH, false, t, tpr);
+    cluster.sync();
+    float2 *cols0 = rank == 0 ? psm : cluster.map_shared_rank(psm, 0);
+    float2 *cols1 = rank == 1 ? psm : cluster.map_shared_rank(psm, 1);
+    const int g0 = rank * (h / 2), g1 = g0 + h / 2;
+    for (int ky0 = g0 + threadIdx.x; ky0 < g1; ky0 += blockDim.x) {
+        auto at = [&](int p, int q) -> float2 & {
+            return (q < CL ? cols0 : cols1)[(q % CL) * ld + ix<true>(ky0 + p * h)];
+        };
+        group_solve_f<C>(at, a.bh, ky0, kx0, H, W, a.lam, scale);
+    }
+    cluster.sync();
+    fft_p2_row(psm + row * ld, H, a.twH, true, t, tpr);
+    for (int i = threadIdx.x; i < CL * H / 2; i += blockDim.x) {
+        const int ql = (2 * i) / H, y = 2 * i - ql * H;
+        const float2 e0 = psm[ql * ld + ix<true>(y)], e1 = psm[ql * ld + ix<true>(y + 1)];
+        *reinterpret_cast<float4 *>(S + (size_t)(kx0 + (rank * CL + ql) * w) * H + y) =
+            make_float4(e0.x, e0.y, e1.x, e1.y);
+    }
+}
+
 // Fallback column passes: FFTs of whole columns (one per CTA) and the group
 // solves over global memory.
 template <bool P2>
@@ -430,6 +482,7 @@ struct PrecPlan {
     int col_per;        // fused column pass: values per thread (generic FFT)
     int col_tpr, col_ld;
     size_t col_smem;    // 0: fallback column passes
+    bool col_cluster;   // the column pass split over a cluster of two CTAs
     int fb_tpr;         // fallback column FFT
     size_t fb_smem;
 };
@@ -450,9 +503,11 @@ bool make_prec_plan(int H, int W, int C, PrecPlan *pl) {
     pl->rg.tpr = tpr;
     pl->rg.ld = round16(row_len) + kRowPad;
     pl->row_smem = row_bytes(TR);
-    // columns: the C columns of one alias-group set in one CTA when they fit
+    // columns: the C columns of one alias-group set in one CTA when they fit,
+    // else (power-of-two sides, C even) half of them in each CTA of a pair
     pl->col_smem = 0;
     pl->col_per = 0;
+    pl->col_cluster = false;
     if (pl->p2) {
         const int ct = H / 16;
         const size_t bytes = (size_t)C * prow_len(H) * sizeof(float2);
@@ -460,6 +515,11 @@ bool make_prec_plan(int H, int W, int C, PrecPlan *pl) {
             pl->col_tpr = ct;
             pl->col_ld = prow_len(H);
             pl->col_smem = bytes;
+        } else if (C % 2 == 0 && (C / 2) * ct <= 1024 && bytes / 2 <= (size_t)kPrecMaxSmem) {
+            pl->col_tpr = ct;
+            pl->col_ld = prow_len(H);
+            pl->col_smem = bytes / 2;
+            pl->col_cluster = true;
         }
         pl->fb_tpr = H / 16;
         pl->fb_smem = (size_t)prow_len(H) * sizeof(float2);
@@ -501,6 +561,14 @@ void launch_cols_shape(const PrecArgs &a, const PrecPlan &pl, dim3 grd, dim3 blk
 template <int C>
 void launch_cols(const PrecArgs &a, const PrecPlan &pl, float scale, cudaStream_t st) {
     const int w = a.W / C, nimg = (a.N + 1) / 2;
+    if constexpr (C % 2 == 0) {
+        if (pl.col_cluster) {
+            const dim3 grd(2 * w, nimg), blk((C / 2) * pl.col_tpr);
+            prec_cols_cluster_kernel<C><<<grd, blk, pl.col_smem, st>>>(a, pl.col_tpr, pl.col_ld,
+                                                                     scale);
+            return;
+        }
+    }
     if (pl.col_smem) {
         const dim3 grd(w, nimg), blk(C * pl.col_tpr);
         const int shape = col_shape(C * pl.col_tpr);
@@ -591,10 +659,24 @@ bool precond_supported(int H, int W, int c) {
     return make_prec_plan(H, W, c, &pl);
 }
 
+// impl 3: the column pass split over two-CTA clusters even where one CTA
+// would hold it (power-of-two sides, even ratio); for tests of that path
+bool precond_cluster_supported(int H, int W, int c) {
+    return is_pow2(H) && is_pow2(W) && c % 2 == 0 && c <= 8 && H % c == 0 && W % c == 0 &&
+           (c / 2) * (H / 16) <= 1024 &&
+           (size_t)(c / 2) * prow_len(H) * sizeof(float2) <= (size_t)kPrecMaxSmem;
+}
+
 void launch_precond(const PrecArgs &a, cudaStream_t st) {
-    if (a.impl != 1 && launch_precond_reg(a, st)) return;
+    if (a.impl != 1 && a.impl != 3 && launch_precond_reg(a, st)) return;
     PrecPlan pl;
     if (!make_prec_plan(a.H, a.W, a.c, &pl)) return;  // callers check precond_supported
+    if (a.impl == 3 && precond_cluster_supported(a.H, a.W, a.c) && !pl.col_cluster) {
+        pl.col_tpr = a.H / 16;
+        pl.col_ld = prow_len(a.H);
+        pl.col_smem = (size_t)(a.c / 2) * prow_len(a.H) * sizeof(float2);
+        pl.col_cluster = true;
+    }
     if (a.rows && a.rows != pl.rg.TR && prec_rows_valid(pl, a.H, a.W, a.rows)) {
         const int row_len = pl.p2 ? prow_len(a.W) : a.W;
         pl.rg.TR = a.rows;
@@ -643,6 +725,10 @@ cudaError_t precond_set_attrs() {
     if (e == cudaSuccess) e = smem_attr(prec_rows_inv_kernel<false>);
     if (e == cudaSuccess) e = smem_attr(prec_col_fft_kernel<true>);
     if (e == cudaSuccess) e = smem_attr(prec_col_fft_kernel<false>);
+    if (e == cudaSuccess) e = smem_attr(prec_cols_cluster_kernel<2>);
+    if (e == cudaSuccess) e = smem_attr(prec_cols_cluster_kernel<4>);
+    if (e == cudaSuccess) e = smem_attr(prec_cols_cluster_kernel<6>);
+    if (e == cudaSuccess) e = smem_attr(prec_cols_cluster_kernel<8>);
     if (e == cudaSuccess) e = set_attrs_c<2>();
     if (e == cudaSuccess) e = set_attrs_c<3>();
     if (e == cudaSuccess) e = set_attrs_c<4>();

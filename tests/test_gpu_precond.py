@@ -83,6 +83,31 @@ def test_register_and_shared_passes_match_oracle(cuda, N, H, W, c, R, lg):
         assert rel(out[2][b], out[1][b]) < PREC_TOL, b
 
 
+@pytest.mark.parametrize("N,H,W,c,R,lg,impl", [
+    (2, 1024, 512, 4, 5, 8e-4, 3),    # forced: two CTAs of 2 columns each
+    (3, 256, 512, 2, 3, 1e-2, 3),     # forced at ratio 2: one column a CTA, odd band count
+    (1, 8192, 512, 4, 4, 8e-4, 1),    # columns of 8192: the cluster pass by itself
+])
+def test_cluster_column_pass_matches_oracle(cuda, N, H, W, c, R, lg, impl):
+    # The shared-memory passes with the column pass split over two-CTA
+    # clusters (distributed shared memory for the alias-group solves): forced
+    # through the recorded tuning (prec_impl = 3) where one CTA would do, and
+    # taken by itself where the columns of an alias-group set do not fit one
+    # CTA; against the oracle's P^{-1}.
+    rng = np.random.default_rng(N * 9000 + H + 5 * W + c)
+    u = rand_kernel(R, rng)
+    r = rng.standard_normal((N, H, W)) * 5.0
+    r += np.cumsum(np.cumsum(rng.standard_normal((N, H, W)), axis=1), axis=2) * 0.1
+    try:
+        api.set_tuning(N, H, W, c, 1, prec_impl=impl)
+        z = to_np(ops.precond(to_dev(r, cuda), to_dev(u, cuda), c, lg))
+    finally:
+        api.set_tuning(N, H, W, c, 1, prec_impl=0)
+    for b in range(N):
+        ref = oracle.precond_apply(r[b].astype(np.float32), u.astype(np.float32), c, lg)
+        assert rel(z[b], ref) < PREC_TOL, b
+
+
 def test_precond_bands_do_not_mix(cuda):
     # bands 2k and 2k+1 share one complex transform: band 1 = 0 must give 0
     rng = np.random.default_rng(9)
