@@ -30,7 +30,7 @@ PREC_TOL = 5e-5
     (1, 64, 256, 2, 4, 1e-2),     # merged, ratio 2, H / c = 32
     (2, 2048, 256, 4, 4, 8e-4),   # 4 columns of 2048: 512-thread column CTAs
     (1, 4096, 64, 4, 3, 8e-4),    # 4 columns of 4096: 1024-thread column CTAs
-    (1, 1024, 64, 8, 3, 8e-4),    # 8 columns of 1024: 512 threads
+    (1, 1024, 64, 8, 3, 8e-4),    # 8 columns of 1024: a two-CTA cluster, 4 columns each
     (2, 768, 192, 4, 4, 8e-4),    # radix 3, 4 columns of 768: 512 threads
     (1, 1536, 96, 4, 3, 8e-4),    # radix 3, 4 columns of 1536: 1024 threads
 ])
