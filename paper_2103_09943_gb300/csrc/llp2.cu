@@ -1,6 +1,9 @@
 // The prior part of the Z0 operator inside the CG loop, q = lam L M L p with
 // p^T q per band (Eq. Z_ini_matting, matrix-free M of Eq. matting_matrix),
-// two pixels per lane (sm_103a).
+// two pixels per lane (sm_103a). Three forms, chosen per size by the
+// autotuner: the general walk below (any window radius, one or two bands a
+// CTA, loads ahead in registers or in a cp.async ring), and for 3 x 3
+// windows the lean walks with two or four columns a lane (further down).
 //
 // Same register-streaming scheme as the general LLP kernel (a warp walks
 // down a strip of columns keeping every stage of the chain -- Laplacian,
